@@ -1,0 +1,123 @@
+/*
+ * hawkes.h -- C ABI of libhawkes.so: the O(N^2) log-likelihood of the
+ * spatiotemporal Hawkes process with per-event rates, its gradient and its
+ * Hessian diagonal, on one B300 GPU (sm_103a).
+ *
+ * Model (Holbrook, Ji & Suchard, arXiv 2103.03348, Section 2.1, Eq. 1):
+ *
+ *   lambda_n = mu0 * sum_{n'} I[x_n != x_n'] (2 pi tau_x^2)^-1 exp(-|x_n-x_n'|^2 / (2 tau_x^2))
+ *                                            (2 pi tau_t^2)^-1/2 exp(-(t_n-t_n')^2 / (2 tau_t^2))
+ *            + theta0 omega (2 pi h^2)^-1 sum_{t_n' < t_n} exp(r_n') exp(-omega (t_n-t_n'))
+ *                                            exp(-|x_n-x_n'|^2 / (2 h^2))
+ *   Lambda   = mu0 sum_n' [Phi((t_N - t_n')/tau_t) - Phi(-t_n'/tau_t)]
+ *            + theta0 sum_n' exp(r_n') (1 - exp(-omega (t_N - t_n')))        (Appendix A Claim)
+ *   loglik   = sum_n log lambda_n - Lambda                                    (Eq. 1)
+ *
+ * r_n = log theta_n is the per-event log-rate (Section 2.2: theta_n =
+ * exp(z_n + beta^T f(t_n)) for sequenced events, 1 otherwise; the caller forms
+ * r_n and applies the chain rule to z and beta).  The paper's background has
+ * no temporal factor; tau_t = +INFINITY selects exactly that model (the
+ * temporal Gaussian is dropped and Lambda's background part is mu0 * N * t_N).
+ * A finite tau_t gives the background a normalised temporal Gaussian too.
+ * t_N is the last (largest) event time and integration starts at time 0.
+ * Excitation is strict (t_n' < t_n): simultaneous events do not excite each
+ * other.  The background indicator drops sources at exactly the target's
+ * location (the event itself and exact duplicates, compared in FP64).
+ *
+ * Common arguments of the three evaluation calls
+ *   x, y, t, r   DEVICE pointers to n doubles each (locations, times, log-rates),
+ *                in time-ascending order (ties allowed).  Read only.
+ *   n            number of events, 2 <= n <= HAWKES_MAX_EVENTS.
+ *   params       HOST pointer to 6 doubles (mu0, tau_x, tau_t, theta0, omega, h),
+ *                all finite and > 0, except tau_t which may be +INFINITY.
+ *   precision    HAWKES_FP64: every pair in FP64 (libm-accurate exp).
+ *                HAWKES_FP32C: pair terms in FP32 (ex2.approx), each row
+ *                accumulated with compensated (two-level Kahan) FP32, rows
+ *                finished, reduced and logged in FP64; rows whose FP32 sum is
+ *                below 2^-60 are recomputed in FP64.
+ *   ws, ws_bytes DEVICE workspace owned by the caller, at least
+ *                hawkes_workspace_size(n, precision) bytes, 256-byte aligned.
+ *                The library allocates nothing.  Calls that may overlap on the
+ *                GPU need distinct workspaces.
+ *   dev_status   DEVICE pointer to one int; receives a hawkes_status for the
+ *                data-dependent checks (HAWKES_OK, HAWKES_EUNSORTED,
+ *                HAWKES_ENONFINITE, HAWKES_EZERO_INTENSITY).
+ *   stream       cudaStream_t (as void*), may be NULL for the legacy stream.
+ *                Everything is enqueued on it; no call synchronises the host.
+ *
+ * Outputs are DEVICE pointers owned by the caller.  Gradient and Hessian
+ * vectors hold 6 + n doubles: [0..5] w.r.t. (mu0, tau_x, tau_t, theta0,
+ * omega, h) as given (not log-transformed), [6 + m] w.r.t. r_m in input order.
+ * With tau_t = +INFINITY the tau_t entries are 0.
+ *
+ * Errors: the return value reports argument errors synchronously (no GPU work
+ * is enqueued then) and launch failures (HAWKES_ECUDA).  Data-dependent
+ * conditions are written to *dev_status by the GPU: for unsorted or
+ * non-finite inputs every output is NaN; when some lambda_n == 0 even in FP64
+ * the log-likelihood is -INFINITY and the gradient and Hessian are NaN.
+ *
+ * The library keeps no state between calls: every call is independent.
+ */
+#ifndef HAWKES_H
+#define HAWKES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { HAWKES_FP64 = 0, HAWKES_FP32C = 1 } hawkes_precision;
+
+typedef enum {
+    HAWKES_OK = 0,
+    HAWKES_EINVAL = 1,          /* bad argument: n, null pointer, params, precision, alignment */
+    HAWKES_EUNSORTED = 2,       /* t not ascending (device status) */
+    HAWKES_ENONFINITE = 3,      /* NaN/Inf in x, y, t or r (device status) */
+    HAWKES_EWORKSPACE = 4,      /* ws_bytes < hawkes_workspace_size(n, precision) */
+    HAWKES_ECUDA = 5,           /* a CUDA launch or memset failed */
+    HAWKES_EZERO_INTENSITY = 6  /* some lambda_n == 0 (device status) */
+} hawkes_status;
+
+/* Largest supported n (indices are 32-bit inside the kernels). */
+#define HAWKES_MAX_EVENTS (1 << 28)
+
+/* Bytes of device workspace that any of the three calls needs for n events at
+ * this precision (the same size serves all three).  0 for invalid n or
+ * precision. */
+size_t hawkes_workspace_size(int64_t n, int precision);
+
+/* Eq. 1 only: writes *loglik (DEVICE, 1 double).  Row pass (Algorithm 2, step 1)
+ * plus the integral term (Appendix A). */
+int hawkes_loglik(const double *x, const double *y, const double *t, const double *r, int64_t n,
+                  const double params[6], int precision, void *ws, size_t ws_bytes,
+                  double *loglik, int *dev_status, void *stream);
+
+/* Eq. 1 and its gradient: grad (DEVICE, 6 + n doubles, required); loglik may be
+ * NULL.  The log-rate entries are Eq. 4 multiplied by theta_m (Algorithm 2,
+ * step 2); the global entries differentiate Eq. 1 directly. */
+int hawkes_grad(const double *x, const double *y, const double *t, const double *r, int64_t n,
+                const double params[6], int precision, void *ws, size_t ws_bytes,
+                double *loglik, double *grad, int *dev_status, void *stream);
+
+/* Eq. 1, its gradient and the diagonal of its Hessian: hdiag (DEVICE, 6 + n
+ * doubles, required); loglik and grad may be NULL.  The log-rate entries are
+ * Eq. 5 in log-rate coordinates: d2l/dr_m^2 = dl/dr_m - sum_n (theta_m dlambda_n/dtheta_m / lambda_n)^2.
+ * Every pair is visited once by the row pass and once more, within the
+ * causal band, by the column pass. */
+int hawkes_hess_diag(const double *x, const double *y, const double *t, const double *r, int64_t n,
+                     const double params[6], int precision, void *ws, size_t ws_bytes,
+                     double *loglik, double *grad, double *hdiag, int *dev_status, void *stream);
+
+/* Static English description of a hawkes_status code. */
+const char *hawkes_strerror(int status);
+
+/* Library version string. */
+const char *hawkes_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HAWKES_H */

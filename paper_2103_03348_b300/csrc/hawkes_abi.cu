@@ -1,0 +1,190 @@
+// extern "C" entry points of libhawkes.so (declared in include/hawkes.h).
+//
+// Host side only: argument checks, workspace carving, the per-call constants
+// (computed in FP64 from the parameter vector) and the launch sequence.  No
+// host synchronisation and no allocation: everything is enqueued on the
+// caller's stream into the caller's workspace.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "hawkes_internal.cuh"
+
+namespace hk {
+
+static int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+Geometry make_geometry(int64_t n) {
+    Geometry g;
+    g.n = (int)n;
+    g.tiles = ceil_div(g.n, TILE);
+    g.npad = g.tiles * TILE;
+    // Enough (target tile, source chunk) blocks for several waves on 148 SMs
+    // at 4 resident blocks each, without making chunks shorter than one tile.
+    const int target_blocks = 148 * 32;
+    int chunks = ceil_div(target_blocks, g.tiles);
+    if (chunks < 1) chunks = 1;
+    if (chunks > g.tiles) chunks = g.tiles;
+    g.chunk_tiles = ceil_div(g.tiles, chunks);
+    g.n_chunks = ceil_div(g.tiles, g.chunk_tiles);
+    int hs = 1024;
+    while (hs < 2 * g.n) hs <<= 1;
+    g.hash_size = hs;
+    return g;
+}
+
+size_t carve(void *base, const Geometry &g, int precision, Workspace *w) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void * {
+        const size_t o = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return base ? (void *)((char *)base + o) : nullptr;
+    };
+    const size_t np = (size_t)g.npad, nt = (size_t)g.tiles;
+    w->hdr = (int *)take(8 * sizeof(int));
+    w->centre = (double *)take(4 * sizeof(double));
+    w->hash = (int *)take((size_t)g.hash_size * sizeof(int));
+    w->cnt = (int *)take(np * sizeof(int));
+    w->loc = (int *)take(np * sizeof(int));
+    w->gidx = (int *)take(np * sizeof(int));
+    w->tinfo = (int4 *)take(nt * sizeof(int4));
+    w->tbox = (double4_32a *)take(nt * sizeof(double4_32a));
+    const bool f32 = precision == HAWKES_FP32C;
+    w->src32 = f32 ? (float4 *)take(np * sizeof(float4)) : nullptr;
+    w->tstat32 = f32 ? (float4 *)take(nt * sizeof(float4)) : nullptr;
+    w->sufmax = f32 ? (float *)take(nt * sizeof(float)) : nullptr;
+    w->src64 = f32 ? nullptr : (double4_32a *)take(np * sizeof(double4_32a));
+    w->w64 = f32 ? nullptr : (double *)take(np * sizeof(double));
+    w->rowpart = (double *)take((size_t)g.n_chunks * NMOM * np * sizeof(double));
+    w->mom = (double *)take((size_t)NMOM * np * sizeof(double));
+    w->flagged = (int *)take(np * sizeof(int));
+    w->dLr = (double *)take(np * sizeof(double));
+    w->blockpart = (double *)take(nt * ACC_STRIDE * sizeof(double));
+    w->colpart = (double *)take((size_t)g.n_chunks * 2 * np * sizeof(double));
+    return off;
+}
+
+static bool params_valid(const double *p) {
+    for (int k = 0; k < 6; ++k) {
+        if (k == 2 && isinf(p[k]) && p[k] > 0) continue;
+        if (!isfinite(p[k]) || !(p[k] > 0)) return false;
+    }
+    return true;
+}
+
+static Consts make_consts(const Geometry &g, int mode, int precision, const double *p) {
+    Consts c;
+    memset(&c, 0, sizeof(c));
+    c.g = g;
+    c.mode = mode;
+    c.fp32c = precision == HAWKES_FP32C;
+    c.mu0 = p[0]; c.tx = p[1]; c.tt = p[2]; c.th0 = p[3]; c.om = p[4]; c.h = p[5];
+    c.tt_inf = isinf(c.tt) ? 1 : 0;
+    const double two_pi = 6.283185307179586476925286766559;
+    c.A = c.tt_inf ? c.mu0 / (two_pi * c.tx * c.tx)
+                   : c.mu0 / (two_pi * sqrt(two_pi) * c.tx * c.tx * c.tt);
+    c.B = c.th0 * c.om / (two_pi * c.h * c.h);
+    // FP64 pair constants (also used by the FP32C fix-up rows)
+    c.ibx = 1.0 / (2.0 * c.tx * c.tx);
+    c.ibt = c.tt_inf ? 0.0 : 1.0 / (2.0 * c.tt * c.tt);
+    c.ih = 1.0 / (2.0 * c.h * c.h);
+    if (c.fp32c) {
+        // x~ = (x - xc) sqrt(log2(e)/2) / tau_x makes the background's spatial exponent -d~^2;
+        // t~ = (t - tc) omega log2(e) makes the excitation's temporal exponent -dt~.
+        c.sx = sqrt(LOG2E / 2.0) / c.tx;
+        c.st = c.om * LOG2E;
+        c.cbt = c.tt_inf ? 0.0f : (float)(LOG2E / (2.0 * c.tt * c.tt) / (c.st * c.st));
+        c.hh = (float)((c.tx / c.h) * (c.tx / c.h));
+    } else {
+        c.sx = 1.0;
+        c.st = 1.0;
+    }
+    return c;
+}
+
+static int run(const double *x, const double *y, const double *t, const double *r, int64_t n,
+               const double *params, int precision, void *wsp, size_t ws_bytes, int mode,
+               double *loglik, double *grad, double *hdiag, int *dev_status, void *stream) {
+    if (n < 2 || n > HAWKES_MAX_EVENTS) return HAWKES_EINVAL;
+    if (precision != HAWKES_FP64 && precision != HAWKES_FP32C) return HAWKES_EINVAL;
+    if (!x || !y || !t || !r || !params || !wsp || !dev_status) return HAWKES_EINVAL;
+    if (mode == MODE_LL && !loglik) return HAWKES_EINVAL;
+    if (mode == MODE_GRAD && !grad) return HAWKES_EINVAL;
+    if (mode == MODE_HESS && !hdiag) return HAWKES_EINVAL;
+    if (((uintptr_t)wsp & 255) != 0) return HAWKES_EINVAL;
+    if (!params_valid(params)) return HAWKES_EINVAL;
+    const Geometry g = make_geometry(n);
+    Workspace ws;
+    const size_t need = carve(wsp, g, precision, &ws);
+    if (ws_bytes < need) return HAWKES_EWORKSPACE;
+
+    const Consts c = make_consts(g, mode, precision, params);
+    const Inputs in = {x, y, t, r};
+    const Outputs out = {loglik, mode >= MODE_GRAD ? grad : nullptr, mode == MODE_HESS ? hdiag : nullptr, dev_status};
+    cudaStream_t s = (cudaStream_t)stream;
+
+    if (cudaMemsetAsync(ws.hdr, 0, 8 * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
+    if (cudaMemsetAsync(ws.hash, 0xFF, (size_t)g.hash_size * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
+    if (cudaMemsetAsync(ws.cnt, 0, (size_t)g.npad * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
+    if (launch_prep(c, in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
+    if (launch_pack(c, in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
+    if ((c.fp32c ? launch_row32(c, ws, s) : launch_row64(c, ws, s)) != cudaSuccess) return HAWKES_ECUDA;
+    if (launch_combine(c, ws, s) != cudaSuccess) return HAWKES_ECUDA;
+    if (c.fp32c && launch_fixup(c, in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
+    if (launch_epilogue(c, in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
+    if (launch_finalize(c, ws, out, s) != cudaSuccess) return HAWKES_ECUDA;
+    if (mode >= MODE_GRAD) {
+        if ((c.fp32c ? launch_col32(c, in, ws, s) : launch_col64(c, ws, s)) != cudaSuccess) return HAWKES_ECUDA;
+        if (launch_colfinish(c, ws, out, s) != cudaSuccess) return HAWKES_ECUDA;
+    }
+    return HAWKES_OK;
+}
+
+}  // namespace hk
+
+extern "C" {
+
+size_t hawkes_workspace_size(int64_t n, int precision) {
+    if (n < 2 || n > HAWKES_MAX_EVENTS) return 0;
+    if (precision != HAWKES_FP64 && precision != HAWKES_FP32C) return 0;
+    hk::Workspace w;
+    return hk::carve(nullptr, hk::make_geometry(n), precision, &w);
+}
+
+int hawkes_loglik(const double *x, const double *y, const double *t, const double *r, int64_t n,
+                  const double params[6], int precision, void *ws, size_t ws_bytes,
+                  double *loglik, int *dev_status, void *stream) {
+    return hk::run(x, y, t, r, n, params, precision, ws, ws_bytes, hk::MODE_LL, loglik, nullptr, nullptr,
+                   dev_status, stream);
+}
+
+int hawkes_grad(const double *x, const double *y, const double *t, const double *r, int64_t n,
+                const double params[6], int precision, void *ws, size_t ws_bytes,
+                double *loglik, double *grad, int *dev_status, void *stream) {
+    return hk::run(x, y, t, r, n, params, precision, ws, ws_bytes, hk::MODE_GRAD, loglik, grad, nullptr,
+                   dev_status, stream);
+}
+
+int hawkes_hess_diag(const double *x, const double *y, const double *t, const double *r, int64_t n,
+                     const double params[6], int precision, void *ws, size_t ws_bytes,
+                     double *loglik, double *grad, double *hdiag, int *dev_status, void *stream) {
+    return hk::run(x, y, t, r, n, params, precision, ws, ws_bytes, hk::MODE_HESS, loglik, grad, hdiag,
+                   dev_status, stream);
+}
+
+const char *hawkes_strerror(int status) {
+    switch (status) {
+        case HAWKES_OK: return "success";
+        case HAWKES_EINVAL: return "invalid argument (n, null pointer, parameters, precision or workspace alignment)";
+        case HAWKES_EUNSORTED: return "event times are not in ascending order";
+        case HAWKES_ENONFINITE: return "an event coordinate, time or log-rate is not finite";
+        case HAWKES_EWORKSPACE: return "workspace smaller than hawkes_workspace_size(n, precision)";
+        case HAWKES_ECUDA: return "a CUDA launch or memset failed";
+        case HAWKES_EZERO_INTENSITY: return "some event has zero intensity: the log-likelihood is -inf";
+        default: return "unknown status";
+    }
+}
+
+const char *hawkes_version(void) { return "hawkes-b300 0.1 (sm_103a)"; }
+
+}  // extern "C"

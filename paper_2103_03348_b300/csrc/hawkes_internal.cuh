@@ -1,0 +1,169 @@
+// Internal declarations shared by the kernels of libhawkes.so.
+//
+// Data flow of one call (all enqueued on the caller's stream, no host sync):
+//   prep     validate, per-event tie-group start, exact-location dedup, centre
+//   pack     FP32 scaled source pairs + per-tile statistics (FP32C), FP64 copy
+//   row      per (target tile, source chunk): moment sums of the pair terms
+//            (Eq. 1's inner sum and its parameter derivatives)
+//   combine  sum the chunk partials of each row in FP64 (fixed order)
+//   fixup    FP32C only: rows whose FP32 sum is below 2^-60 redone in FP64
+//   epilogue per row: lambda_n, log lambda_n, derivative terms, the integral
+//            term (Appendix A) per event, column-pass weights; block partials
+//   finalize one block: deterministic sum of block partials -> outputs
+//   col      per (source tile, target chunk): Eq. 4 / Eq. 5 column sums
+//   colfin   per source: combine column partials, subtract dLambda/dr_m
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hawkes.h"
+
+namespace hk {
+
+constexpr int TILE = 128;   // events per tile: targets per row block, sources per shared-memory subtile
+constexpr int NMOM = 10;    // row moments (hess mode)
+constexpr int NACC = 13;    // per-row terms reduced across rows: loglik, 6 gradient, 6 Hessian
+constexpr int ACC_STRIDE = 16;
+
+constexpr int MODE_LL = 0, MODE_GRAD = 1, MODE_HESS = 2;
+
+// device status bits (combined into a hawkes_status by finalize)
+constexpr int ST_UNSORTED = 1, ST_NONFINITE = 2, ST_ZERO = 4;
+
+// log2(e) and the FP32C underflow threshold: an exponent (base 2) below this
+// gives exactly 0 from ex2.approx.ftz, so tiles whose bound lies below it are
+// skipped without changing the FP32 result (2 units of margin for rounding).
+constexpr double LOG2E = 1.4426950408889634074;
+constexpr float EXP2_DEAD = -128.0f;
+// rows whose FP32 background and excitation sums are both below 2^-60 are
+// recomputed in FP64 (terms below 2^-126 were flushed to zero in FP32)
+constexpr float TINY_ROW = 8.673617379884035e-19f;  // 2^-60
+
+// Moment index (row pass).  Background terms G, excitation terms E (with exp(r)):
+//   0 sum G        1 sum G d^2     2 sum G dt^2    3 sum G d^4     4 sum G dt^4
+//   5 sum E        6 sum E dt      7 sum E dt^2    8 sum E d^2     9 sum E d^4
+enum { MO_G = 0, MO_GD2 = 1, MO_GT2 = 2, MO_GD4 = 3, MO_GT4 = 4, MO_E = 5, MO_ET = 6, MO_ET2 = 7, MO_ED2 = 8, MO_ED4 = 9 };
+
+struct Geometry {
+    int n, tiles, npad, chunk_tiles, n_chunks, hash_size;
+};
+
+Geometry make_geometry(int64_t n);
+
+// Constants of one call (host-computed in FP64 and passed by value).
+struct Consts {
+    Geometry g;
+    int mode, fp32c, tt_inf;
+    double mu0, tx, tt, th0, om, h;
+    double A, B;          // lambda_n = A * sum G + B * sum E
+    double sx, st;        // FP32C scaled coordinates: x~ = (x - xc) sx, t~ = (t - tc) st; 1 for FP64
+    float cbt, hh;        // FP32C: G = 2^-(d~^2 + cbt dt~^2), E = 2^(r~ - dt~ - hh d~^2)
+    double ibx, ibt, ih;  // FP64:  G = exp(-ibx d^2 - ibt dt^2), E = exp(r - om dt - ih d^2)
+};
+
+// Workspace carving.  Offsets are multiples of 256 bytes.
+struct Workspace {
+    int *hdr;            // [0] status bits, [1] flagged rows, [2] ticket, [3] spare
+    double *centre;      // [4]: xc, yc, tc, tN
+    int *hash;           // [hash_size]
+    int *cnt;            // [npad]  members of each exact-location group (indexed by representative)
+    int *loc;            // [npad]  representative index of the event's location
+    int *gidx;           // [npad]  first index with the same time (tie-group start)
+    int4 *tinfo;         // [tiles] gfirst, glast, has_dup, valid count
+    double4_32a *tbox;       // [tiles] xmin, xmax, ymin, ymax (prep)
+    float4 *src32;       // [npad]  pairs: (-x0,-x1,-y0,-y1),(-t0,-t1,r^0,r^1), r^ = r~ + t~;
+                         //         the r^ slot later holds the column weight g^ = log2(B/lambda) - t~
+    float4 *tstat32;     // [tiles] t~min, t~max, max r^, max g^
+    double4_32a *src64;      // [npad]  (x, y, t, r) FP64 (FP64 path)
+    double *rowpart;     // [n_chunks * NMOM * npad]
+    double *mom;         // [NMOM * npad]
+    int *flagged;        // [npad]
+    double *w64;         // [npad]  FP64 column weight B / lambda_n
+    double *dLr;         // [npad]  dLambda / dr_m
+    double *blockpart;   // [tiles * ACC_STRIDE]
+    float *sufmax;       // [tiles] suffix max of the column weight bound (FP32C)
+    double *colpart;     // [n_chunks * 2 * npad]
+};
+
+size_t carve(void *base, const Geometry &g, int precision, Workspace *ws);  // returns total bytes; base may be NULL
+
+struct Inputs {
+    const double *x, *y, *t, *r;
+};
+
+struct Outputs {
+    double *loglik, *grad, *hdiag;
+    int *dev_status;
+};
+
+// launchers (return cudaGetLastError())
+cudaError_t launch_prep(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s);
+cudaError_t launch_pack(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s);
+cudaError_t launch_row32(const Consts &c, const Workspace &ws, cudaStream_t s);
+cudaError_t launch_row64(const Consts &c, const Workspace &ws, cudaStream_t s);
+cudaError_t launch_combine(const Consts &c, const Workspace &ws, cudaStream_t s);
+cudaError_t launch_fixup(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s);
+cudaError_t launch_epilogue(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s);
+cudaError_t launch_finalize(const Consts &c, const Workspace &ws, const Outputs &out, cudaStream_t s);
+cudaError_t launch_col32(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s);
+cudaError_t launch_col64(const Consts &c, const Workspace &ws, cudaStream_t s);
+cudaError_t launch_colfinish(const Consts &c, const Workspace &ws, const Outputs &out, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 splat(float v) { return make_float2(v, v); }
+
+// Kahan step: s + v with the running compensation c (true sum ~= s - c).
+__device__ __forceinline__ void kahan(float &s, float &c, float v) {
+    const float y = __fsub_rn(v, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+// Deterministic block sum of one double per thread (fixed tree order).
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+#pragma unroll
+    for (int w = NT / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+template <int NT>
+__device__ __forceinline__ float block_max(float v, float *sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+#pragma unroll
+    for (int w = NT / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] = fmaxf(sh[threadIdx.x], sh[threadIdx.x + w]);
+        __syncthreads();
+    }
+    const float r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+#endif  // __CUDACC__
+
+}  // namespace hk

@@ -1,0 +1,109 @@
+// FP32-compensated column pass (Eqs. 4 and 5; Algorithm 2, step 2, redesigned).
+//
+// For every source m the gradient and Hessian diagonal w.r.t. r_m = log theta_m
+// need, over the later targets n (t_n > t_m strictly),
+//     v_nm = B theta_m E'_nm / lambda_n        (the share of lambda_n due to m; 0 <= v <= 1)
+//     C1_m = sum_n v_nm,   C2_m = sum_n v_nm^2
+// because dl/dr_m = C1_m - dLambda/dr_m and d2l/dr_m^2 = C1_m - C2_m - dLambda/dr_m.
+// In the scaled base-2 coordinates of the row pass,
+//     v_nm = 2^(g^_n + r^_m - hh d~^2),  g^_n = log2(B / lambda_n) - t~_n,  r^_m = r~_m + t~_m,
+// where the epilogue stored g^_n in the fourth slot of each packed target.
+//
+// One block of 128 threads owns 128 sources (one per thread) and sweeps a
+// chunk of later target tiles staged in shared memory, two targets per packed
+// f32x2 instruction.  A target tile is skipped when no target follows any
+// source (tie-group index), or when 2^(max g^ + max r^) < 2^-128 so that every
+// term underflows to exactly 0 in FP32; the sweep stops once the suffix max of
+// g^ shows that all later tiles underflow too.  Precision as in the row pass.
+#include "hawkes_internal.cuh"
+
+namespace hk {
+
+template <int MODE, bool MASK>
+__device__ __forceinline__ void col_tile(const float4 *sAB, const int *sG, int npairs, float2 xm, float2 ym,
+                                         float2 rm, int m, float2 nhh2, float2 &c1, float2 &c2) {
+#pragma unroll 4
+    for (int p = 0; p < npairs; ++p) {
+        const float4 A = sAB[2 * p], B = sAB[2 * p + 1];  // (-x, -y) and (-t, g^) of targets 2p, 2p+1
+        const float2 dx = add2(xm, make_float2(A.x, A.y));
+        const float2 dy = add2(ym, make_float2(A.z, A.w));
+        float2 d2 = mul2(dx, dx);
+        d2 = fma2(dy, dy, d2);
+        float2 ex = add2(make_float2(B.z, B.w), rm);
+        ex = fma2(d2, nhh2, ex);
+        float2 v = make_float2(ex2_ftz(ex.x), ex2_ftz(ex.y));
+        if (MASK) {
+            // target n is excited by m iff m < gidx[n] (strictly earlier time)
+            if (!(m < sG[2 * p])) v.x = 0.0f;
+            if (!(m < sG[2 * p + 1])) v.y = 0.0f;
+        }
+        c1 = add2(c1, v);
+        if (MODE == MODE_HESS) c2 = fma2(v, v, c2);
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(TILE, 4) col32_kernel(Consts c, Inputs in, Workspace ws) {
+    const int tile = blockIdx.x, chunk = blockIdx.y;
+    const int m = tile * TILE + threadIdx.x;
+    const int n = c.g.n, npad = c.g.npad;
+    __shared__ float4 sAB[2][TILE];
+    __shared__ int sG[2][TILE];
+
+    float2 xm, ym, rm;
+    {
+        const float *f = reinterpret_cast<const float *>(ws.src32);
+        const int p = m >> 1, l = m & 1;
+        xm = splat(-f[8 * p + 0 + l]);
+        ym = splat(-f[8 * p + 2 + l]);
+        // r^_m = r~_m + t~_m, from the FP64 inputs (the packed slot now holds g^)
+        float r = -1.0e9f;
+        if (m < n) r = (float)(in.r[m] * LOG2E + (in.t[m] - ws.centre[2]) * c.st);
+        rm = splat(r);
+    }
+    const int4 tiM = ws.tinfo[tile];
+    const float4 stM = ws.tstat32[tile];
+    const float2 nhh2 = splat(-c.hh);
+    const int m_first = tile * TILE, m_last = m_first + tiM.w - 1;
+
+    float2 run1 = make_float2(0.f, 0.f), run2 = make_float2(0.f, 0.f);
+    float s1 = 0.f, k1 = 0.f, s2 = 0.f, k2 = 0.f;
+
+    const int ub = tile + chunk * c.g.chunk_tiles;
+    const int ue = min(c.g.tiles, ub + c.g.chunk_tiles);
+    int buf = 0;
+    for (int u = ub; u < ue; ++u) {
+        // uniform decisions for the whole block
+        if (ws.sufmax[u] + stM.z < EXP2_DEAD) break;  // this and every later tile underflow
+        const int4 tiU = ws.tinfo[u];
+        const float4 stU = ws.tstat32[u];
+        if (tiU.y <= m_first) continue;                 // no target of u follows any source
+        if (stU.w + stM.z < EXP2_DEAD) continue;        // every term underflows
+        const int u0 = u * TILE;
+        sAB[buf][threadIdx.x] = ws.src32[(size_t)u0 + threadIdx.x];
+        sG[buf][threadIdx.x] = ws.gidx[(size_t)u0 + threadIdx.x];
+        __syncthreads();
+        const int npairs = (tiU.w + 1) >> 1;
+        const bool all_causal = m_last < tiU.x;
+        if (all_causal) col_tile<MODE, false>(sAB[buf], sG[buf], npairs, xm, ym, rm, m, nhh2, run1, run2);
+        else col_tile<MODE, true>(sAB[buf], sG[buf], npairs, xm, ym, rm, m, nhh2, run1, run2);
+        kahan(s1, k1, __fadd_rn(run1.x, run1.y));
+        run1 = make_float2(0.f, 0.f);
+        if (MODE == MODE_HESS) {
+            kahan(s2, k2, __fadd_rn(run2.x, run2.y));
+            run2 = make_float2(0.f, 0.f);
+        }
+        buf ^= 1;
+    }
+    ws.colpart[((size_t)chunk * 2 + 0) * npad + m] = (double)s1 - (double)k1;
+    if (MODE == MODE_HESS) ws.colpart[((size_t)chunk * 2 + 1) * npad + m] = (double)s2 - (double)k2;
+}
+
+cudaError_t launch_col32(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s) {
+    const dim3 grid(c.g.tiles, c.g.n_chunks);
+    if (c.mode == MODE_HESS) col32_kernel<MODE_HESS><<<grid, TILE, 0, s>>>(c, in, ws);
+    else col32_kernel<MODE_GRAD><<<grid, TILE, 0, s>>>(c, in, ws);
+    return cudaGetLastError();
+}
+
+}  // namespace hk

@@ -1,0 +1,245 @@
+// Row finish, integral term and deterministic reductions (steps a3, a4).
+//
+// combine   mom[k][i] = sum over chunks of the row partials (fixed order, FP64);
+//           FP32C rows with tiny sums are listed for the FP64 fix-up.
+// epilogue  per event n, in FP64:
+//             lambda_n = A sum G + B sum E                          (Eq. 1 inner sum)
+//             q1_p = (d lambda_n / dp) / lambda_n,  q2_p = (d2 lambda_n / dp2) / lambda_n - q1_p^2
+//           from the moments, and the event's share of the integral term
+//             Lambda_n = mu0 [Phi((t_N - t_n)/tau_t) - Phi(-t_n/tau_t)] + theta0 theta_n (1 - e^{-omega (t_N - t_n)})
+//           (Appendix A Claim, background integrated exactly) with its
+//           derivatives; each block writes the 13 block sums of
+//           (log lambda_n - Lambda_n, q1_p - dLambda_n/dp, q2_p - d2Lambda_n/dp2).
+// finalize  one block sums the block partials in a fixed order -> loglik,
+//           gradient[0..5], Hessian diagonal[0..5]; status -> dev_status.
+// colfinish dl/dr_m = C1_m - dLambda/dr_m, d2l/dr_m^2 = C1_m - C2_m - dLambda/dr_m.
+//
+// Derivatives of lambda_n (moments M in raw units, see hawkes_internal.cuh):
+//   mu0:    A S_G / mu0
+//   tau_x:  A (MO_GD2/tx^3 - 2 S_G/tx),   second A (MO_GD4/tx^6 - 7 MO_GD2/tx^4 + 6 S_G/tx^2)
+//   tau_t:  A (MO_GT2/tt^3 - S_G/tt),     second A (MO_GT4/tt^6 - 5 MO_GT2/tt^4 + 2 S_G/tt^2)
+//   theta0: B S_E / theta0
+//   omega:  B (S_E/omega - MO_ET),        second B (MO_ET2 - 2 MO_ET/omega)
+//   h:      B (MO_ED2/h^3 - 2 S_E/h),     second B (MO_ED4/h^6 - 7 MO_ED2/h^4 + 6 S_E/h^2)
+// (from f(s) = s^-k exp(-q/(2 s^2)): f'/f = q/s^3 - k/s, f''/f = (f'/f)^2 - 3q/s^4 + k/s^2).
+#include "hawkes_internal.cuh"
+
+namespace hk {
+
+constexpr int CB_THREADS = 256;
+
+__global__ void __launch_bounds__(CB_THREADS) combine_kernel(Consts c, Workspace ws) {
+    const int i = blockIdx.x * CB_THREADS + threadIdx.x;
+    if (i >= c.g.n) return;
+    const int npad = c.g.npad;
+    double sg = 0.0, se = 0.0;
+    for (int k = 0; k < NMOM; ++k) {
+        const bool used = c.mode == MODE_HESS ||
+                          (c.mode == MODE_GRAD && (k == MO_G || k == MO_GD2 || k == MO_GT2 || k == MO_E || k == MO_ET || k == MO_ED2)) ||
+                          (k == MO_G || k == MO_E);
+        if (!used) continue;
+        double s = 0.0;
+        for (int ch = 0; ch < c.g.n_chunks; ++ch) s += ws.rowpart[((size_t)ch * NMOM + k) * npad + i];
+        ws.mom[(size_t)k * npad + i] = s;
+        if (k == MO_G) sg = s;
+        if (k == MO_E) se = s;
+    }
+    if (c.fp32c && sg < (double)TINY_ROW && se < (double)TINY_ROW) {
+        const int slot = atomicAdd(&ws.hdr[1], 1);
+        ws.flagged[slot] = i;
+    }
+}
+
+cudaError_t launch_combine(const Consts &c, const Workspace &ws, cudaStream_t s) {
+    combine_kernel<<<(c.g.n + CB_THREADS - 1) / CB_THREADS, CB_THREADS, 0, s>>>(c, ws);
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ double std_pdf(double z) { return 0.3989422804014327 * exp(-0.5 * z * z); }
+__device__ __forceinline__ double std_cdf(double z) { return 0.5 * erfc(-z * 0.7071067811865476); }
+
+__global__ void __launch_bounds__(TILE) epilogue_kernel(Consts c, Inputs in, Workspace ws) {
+    __shared__ double sh[TILE];
+    __shared__ float shf[TILE];
+    const int i = blockIdx.x * TILE + threadIdx.x;
+    const int n = c.g.n, npad = c.g.npad;
+    const bool valid = i < n;
+    double acc[NACC];
+#pragma unroll
+    for (int k = 0; k < NACC; ++k) acc[k] = 0.0;
+    float ghat = -INFINITY;
+
+    if (valid) {
+        const int mode = c.mode;
+        auto M = [&](int k) { return ws.mom[(size_t)k * npad + i]; };
+        const double sx2 = c.sx * c.sx, st = c.st, st2 = c.st * c.st;
+        const double SG = M(MO_G), SE = M(MO_E);
+        const double lam = c.A * SG + c.B * SE;
+        double q1[6] = {0, 0, 0, 0, 0, 0}, q2[6] = {0, 0, 0, 0, 0, 0};
+        double ll = 0.0;
+        if (lam > 0.0) {
+            ll = log(lam);
+            if (mode >= MODE_GRAD) {
+                const double a = c.A / lam, b = c.B / lam;
+                const double GD2 = M(MO_GD2) / sx2, GT2 = M(MO_GT2) / st2;
+                const double ET = M(MO_ET) / st, ED2 = M(MO_ED2) / sx2;
+                const double tx = c.tx, tt = c.tt, om = c.om, h = c.h;
+                q1[0] = a * SG / c.mu0;
+                q1[1] = a * (GD2 / (tx * tx * tx) - 2.0 * SG / tx);
+                q1[2] = c.tt_inf ? 0.0 : a * (GT2 / (tt * tt * tt) - SG / tt);
+                q1[3] = b * SE / c.th0;
+                q1[4] = b * (SE / om - ET);
+                q1[5] = b * (ED2 / (h * h * h) - 2.0 * SE / h);
+                if (mode == MODE_HESS) {
+                    const double GD4 = M(MO_GD4) / (sx2 * sx2), GT4 = M(MO_GT4) / (st2 * st2);
+                    const double ET2 = M(MO_ET2) / st2, ED4 = M(MO_ED4) / (sx2 * sx2);
+                    const double tx2 = tx * tx, tt2 = tt * tt, h2 = h * h;
+                    double s2[6];
+                    s2[0] = 0.0;
+                    s2[1] = a * (GD4 / (tx2 * tx2 * tx2) - 7.0 * GD2 / (tx2 * tx2) + 6.0 * SG / tx2);
+                    s2[2] = c.tt_inf ? 0.0 : a * (GT4 / (tt2 * tt2 * tt2) - 5.0 * GT2 / (tt2 * tt2) + 2.0 * SG / tt2);
+                    s2[3] = 0.0;
+                    s2[4] = b * (ET2 - 2.0 * ET / om);
+                    s2[5] = b * (ED4 / (h2 * h2 * h2) - 7.0 * ED2 / (h2 * h2) + 6.0 * SE / h2);
+#pragma unroll
+                    for (int p = 0; p < 6; ++p) q2[p] = s2[p] - q1[p] * q1[p];
+                    if (c.tt_inf) q2[2] = 0.0;
+                }
+            }
+            if (c.fp32c) {
+                // column weight g^ = log2(B / lambda_n) - t~_n (t~_n as packed)
+                const float *f = reinterpret_cast<const float *>(ws.src32);
+                const float tt_n = -f[8 * (i >> 1) + 4 + (i & 1)];
+                ghat = (float)(log2(c.B / lam) - (double)tt_n);
+            } else {
+                ws.w64[i] = c.B / lam;
+            }
+        } else {
+            atomicOr(&ws.hdr[0], ST_ZERO);
+            if (!c.fp32c) ws.w64[i] = 0.0;
+        }
+        if (c.fp32c) {
+            float *f = reinterpret_cast<float *>(ws.src32);
+            f[8 * (i >> 1) + 6 + (i & 1)] = ghat;
+        }
+
+        // this event's share of the integral term and its derivatives
+        const double tN = ws.centre[3];
+        const double ti = in.t[i], a_ = tN - ti, b_ = -ti;
+        const double th = exp(in.r[i]);
+        const double dec = exp(-c.om * a_);
+        const double one_m = -expm1(-c.om * a_);
+        double L = 0.0, dL[6] = {0, 0, 0, 0, 0, 0}, d2L[6] = {0, 0, 0, 0, 0, 0};
+        if (c.tt_inf) {
+            dL[0] = tN;
+        } else {
+            const double tt = c.tt, za = a_ / tt, zb = b_ / tt;
+            const double pa = std_pdf(za), pb = std_pdf(zb);
+            dL[0] = std_cdf(za) - std_cdf(zb);
+            dL[2] = c.mu0 * (-(a_ / (tt * tt)) * pa + (b_ / (tt * tt)) * pb);
+            const double tt3 = tt * tt * tt, tt5 = tt3 * tt * tt;
+            d2L[2] = c.mu0 * (pa * (2.0 * a_ / tt3 - a_ * a_ * a_ / tt5) - pb * (2.0 * b_ / tt3 - b_ * b_ * b_ / tt5));
+        }
+        L = c.mu0 * dL[0] + c.th0 * th * one_m;
+        dL[3] = th * one_m;
+        dL[4] = c.th0 * th * a_ * dec;
+        d2L[4] = -c.th0 * th * a_ * a_ * dec;
+        ws.dLr[i] = c.th0 * th * one_m;
+
+        acc[0] = ll - L;
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+            acc[1 + p] = q1[p] - dL[p];
+            acc[7 + p] = q2[p] - d2L[p];
+        }
+        if (lam <= 0.0) acc[0] = 0.0;  // the status carries the -inf
+    }
+    for (int k = 0; k < NACC; ++k) {
+        const double v = block_sum<TILE>(acc[k], sh);
+        if (threadIdx.x == 0) ws.blockpart[(size_t)blockIdx.x * ACC_STRIDE + k] = v;
+    }
+    if (c.fp32c) {
+        const float gm = block_max<TILE>(ghat, shf);
+        if (threadIdx.x == 0) ws.tstat32[blockIdx.x].w = gm;
+    }
+}
+
+cudaError_t launch_epilogue(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s) {
+    epilogue_kernel<<<c.g.tiles, TILE, 0, s>>>(c, in, ws);
+    return cudaGetLastError();
+}
+
+constexpr int FIN_THREADS = 256;
+
+__global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(Consts c, Workspace ws, Outputs out) {
+    __shared__ double sh[FIN_THREADS];
+    __shared__ double tot[NACC];
+    const int tiles = c.g.tiles;
+    for (int k = 0; k < NACC; ++k) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < tiles; b += FIN_THREADS) s += ws.blockpart[(size_t)b * ACC_STRIDE + k];
+        const double v = block_sum<FIN_THREADS>(s, sh);
+        if (threadIdx.x == 0) tot[k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int bits = ws.hdr[0];
+        int code = HAWKES_OK;
+        if (bits & ST_NONFINITE) code = HAWKES_ENONFINITE;
+        else if (bits & ST_UNSORTED) code = HAWKES_EUNSORTED;
+        else if (bits & ST_ZERO) code = HAWKES_EZERO_INTENSITY;
+        const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+        double ll = tot[0];
+        if (code == HAWKES_ENONFINITE || code == HAWKES_EUNSORTED) ll = qnan;
+        else if (code == HAWKES_EZERO_INTENSITY) ll = -INFINITY;
+        if (out.loglik) *out.loglik = ll;
+        for (int p = 0; p < 6; ++p) {
+            double g = tot[1 + p], hd = tot[7 + p];
+            if (p == 2 && c.tt_inf) { g = 0.0; hd = 0.0; }
+            if (code != HAWKES_OK) { g = qnan; hd = qnan; }
+            if (out.grad) out.grad[p] = g;
+            if (out.hdiag) out.hdiag[p] = hd;
+        }
+        if (out.dev_status) *out.dev_status = code;
+        if (c.fp32c && c.mode >= MODE_GRAD) {
+            // suffix max of the per-tile column weight bound, for the column sweep's stop test
+            float run = -INFINITY;
+            for (int b = tiles - 1; b >= 0; --b) {
+                run = fmaxf(run, ws.tstat32[b].w);
+                ws.sufmax[b] = run;
+            }
+        }
+    }
+}
+
+cudaError_t launch_finalize(const Consts &c, const Workspace &ws, const Outputs &out, cudaStream_t s) {
+    finalize_kernel<<<1, FIN_THREADS, 0, s>>>(c, ws, out);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(CB_THREADS) colfinish_kernel(Consts c, Workspace ws, Outputs out) {
+    const int m = blockIdx.x * CB_THREADS + threadIdx.x;
+    if (m >= c.g.n) return;
+    const int npad = c.g.npad;
+    double c1 = 0.0, c2 = 0.0;
+    for (int ch = 0; ch < c.g.n_chunks; ++ch) {
+        c1 += ws.colpart[((size_t)ch * 2 + 0) * npad + m];
+        if (c.mode == MODE_HESS) c2 += ws.colpart[((size_t)ch * 2 + 1) * npad + m];
+    }
+    const double dl = ws.dLr[m];
+    double g = c1 - dl, hd = c1 - c2 - dl;
+    if (ws.hdr[0] != 0) {
+        const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+        g = qnan;
+        hd = qnan;
+    }
+    if (out.grad) out.grad[6 + m] = g;
+    if (out.hdiag) out.hdiag[6 + m] = hd;
+}
+
+cudaError_t launch_colfinish(const Consts &c, const Workspace &ws, const Outputs &out, cudaStream_t s) {
+    colfinish_kernel<<<(c.g.n + CB_THREADS - 1) / CB_THREADS, CB_THREADS, 0, s>>>(c, ws, out);
+    return cudaGetLastError();
+}
+
+}  // namespace hk

@@ -1,0 +1,181 @@
+// FP32-compensated row and column passes (Eq. 1's inner sum; Eqs. 4-5).
+//
+// Row pass (Algorithm 2, step 1, redesigned): one block of 128 threads owns a
+// tile of 128 time-consecutive targets, one target per thread, and sweeps a
+// chunk of source tiles.  Each source tile (128 events, 2 KB) is staged in
+// shared memory and read back as broadcast float4 pairs, so one packed f32x2
+// instruction evaluates a target against two sources.  With scaled, centred
+// coordinates (x~ = (x - xc) sqrt(log2(e)/2)/tau_x, t~ = (t - tc) omega log2(e))
+// the pair terms are
+//     G = 2^-(d~^2 + cbt dt~^2)                      background (Section 2.1)
+//     E = 2^(r^_s - t~_n - hh d~^2),  r^ = r~ + t~    excitation with theta_s = e^r
+// and the row accumulates the moments listed in hawkes_internal.cuh.
+// Precision: per-thread runs of 64 source pairs in plain FP32 (packed, two
+// lanes), merged after every tile into a Kahan-compensated FP32 sum per
+// moment; the chunk result is written in FP64 and chunks are combined in FP64.
+//
+// Every source tile is classified for the whole block (no divergence):
+//   * excitation skipped when no source precedes any target (exact, by the
+//     tie-group index) or when 2^(max r^ - min t~) is below 2^-128, so every
+//     excitation term would underflow to exactly 0 in FP32;
+//   * masks (causal by tie-group index, background by exact-location group)
+//     only where a tile pair can contain a masked pair: the diagonal tile,
+//     tiles that straddle the causal boundary, and tiles that both hold events
+//     with a duplicated location.
+#include "hawkes_internal.cuh"
+
+namespace hk {
+
+__host__ __device__ constexpr bool mom_used(int mode, int k) {
+    return mode == MODE_HESS ? true
+         : mode == MODE_GRAD ? (k == MO_G || k == MO_GD2 || k == MO_GT2 || k == MO_E || k == MO_ET || k == MO_ED2)
+                             : (k == MO_G || k == MO_E);
+}
+
+struct RowTarget {
+    float2 xn, yn, tn, ntn;  // splatted target coordinates (ntn = -t~_n)
+    int locn, gn;
+};
+
+template <int MODE, bool EXC, bool MASK>
+__device__ __forceinline__ void row_pair(const float4 A, const float4 B, int la, int lb, int si,
+                                         const RowTarget &T, float2 cbt2, float2 nhh2, float2 (&run)[NMOM]) {
+    // A = (-x0, -x1, -y0, -y1), B = (-t0, -t1, r^0, r^1)
+    const float2 dx = add2(T.xn, make_float2(A.x, A.y));
+    const float2 dy = add2(T.yn, make_float2(A.z, A.w));
+    const float2 dt = add2(T.tn, make_float2(B.x, B.y));
+    float2 d2 = mul2(dx, dx);
+    d2 = fma2(dy, dy, d2);
+    const float2 dt2 = mul2(dt, dt);
+    const float2 q = fma2(dt2, cbt2, d2);
+    float2 gb = make_float2(ex2_ftz(-q.x), ex2_ftz(-q.y));
+    if (MASK) {
+        if (la == T.locn) gb.x = 0.0f;
+        if (lb == T.locn) gb.y = 0.0f;
+    }
+    run[MO_G] = add2(run[MO_G], gb);
+    if (MODE >= MODE_GRAD) {
+        run[MO_GD2] = fma2(gb, d2, run[MO_GD2]);
+        run[MO_GT2] = fma2(gb, dt2, run[MO_GT2]);
+    }
+    float2 d4 = make_float2(0.0f, 0.0f);
+    if (MODE == MODE_HESS) {
+        d4 = mul2(d2, d2);
+        const float2 dt4 = mul2(dt2, dt2);
+        run[MO_GD4] = fma2(gb, d4, run[MO_GD4]);
+        run[MO_GT4] = fma2(gb, dt4, run[MO_GT4]);
+    }
+    if (EXC) {
+        float2 ee = add2(make_float2(B.z, B.w), T.ntn);
+        ee = fma2(d2, nhh2, ee);
+        float2 e = make_float2(ex2_ftz(ee.x), ex2_ftz(ee.y));
+        if (MASK) {
+            if (!(si < T.gn)) e.x = 0.0f;
+            if (!(si + 1 < T.gn)) e.y = 0.0f;
+        }
+        run[MO_E] = add2(run[MO_E], e);
+        if (MODE >= MODE_GRAD) {
+            run[MO_ET] = fma2(e, dt, run[MO_ET]);
+            run[MO_ED2] = fma2(e, d2, run[MO_ED2]);
+        }
+        if (MODE == MODE_HESS) {
+            run[MO_ET2] = fma2(e, dt2, run[MO_ET2]);
+            run[MO_ED4] = fma2(e, d4, run[MO_ED4]);
+        }
+    }
+}
+
+template <int MODE, bool EXC, bool MASK>
+__device__ __forceinline__ void row_tile(const float4 *sAB, const int *sLoc, int s0, int npairs,
+                                         const RowTarget &T, float2 cbt2, float2 nhh2, float2 (&run)[NMOM]) {
+#pragma unroll 4
+    for (int p = 0; p < npairs; ++p) {
+        const float4 A = sAB[2 * p], B = sAB[2 * p + 1];
+        int la = 0, lb = 0;
+        if (MASK) { la = sLoc[2 * p]; lb = sLoc[2 * p + 1]; }
+        row_pair<MODE, EXC, MASK>(A, B, la, lb, s0 + 2 * p, T, cbt2, nhh2, run);
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(TILE, 4) row32_kernel(Consts c, Workspace ws) {
+    const int tile = blockIdx.x, chunk = blockIdx.y;
+    const int i = tile * TILE + threadIdx.x;
+    const int npad = c.g.npad;
+    __shared__ float4 sAB[2][TILE];
+    __shared__ int sLoc[2][TILE];
+
+    RowTarget T;
+    {
+        const float *f = reinterpret_cast<const float *>(ws.src32);
+        const int p = i >> 1, l = i & 1;
+        const float x = -f[8 * p + 0 + l], y = -f[8 * p + 2 + l], t = -f[8 * p + 4 + l];
+        T.xn = splat(x); T.yn = splat(y); T.tn = splat(t); T.ntn = splat(-t);
+        T.locn = ws.loc[i];
+        T.gn = ws.gidx[i];
+    }
+    const int4 tiT = ws.tinfo[tile];
+    const float4 stT = ws.tstat32[tile];
+    const float2 cbt2 = splat(c.cbt), nhh2 = splat(-c.hh);
+
+    float2 run[NMOM];
+    float ks[NMOM], kc[NMOM];
+#pragma unroll
+    for (int k = 0; k < NMOM; ++k) { run[k] = make_float2(0.0f, 0.0f); ks[k] = 0.0f; kc[k] = 0.0f; }
+
+    const int sb = chunk * c.g.chunk_tiles;
+    const int se = min(c.g.tiles, sb + c.g.chunk_tiles);
+    // register prefetch of the first source tile
+    float4 pf = make_float4(0.f, 0.f, 0.f, 0.f);
+    int pl = 0;
+    if (sb < se) { pf = ws.src32[(size_t)sb * TILE + threadIdx.x]; pl = ws.loc[(size_t)sb * TILE + threadIdx.x]; }
+    int buf = 0;
+    for (int s = sb; s < se; ++s) {
+        sAB[buf][threadIdx.x] = pf;
+        sLoc[buf][threadIdx.x] = pl;
+        __syncthreads();
+        if (s + 1 < se) {
+            pf = ws.src32[(size_t)(s + 1) * TILE + threadIdx.x];
+            pl = ws.loc[(size_t)(s + 1) * TILE + threadIdx.x];
+        }
+        const int4 tiS = ws.tinfo[s];
+        const float4 stS = ws.tstat32[s];
+        const int s0 = s * TILE;
+        const int npairs = (tiS.w + 1) >> 1;
+        const bool none_causal = s0 >= tiT.y;                // no source precedes any target
+        const bool all_causal = s0 + tiS.w - 1 < tiT.x;      // every source precedes every target
+        const bool exc = !none_causal && (stS.z - stT.x >= EXP2_DEAD);
+        const bool mask = (s == tile) || (tiT.z && tiS.z) || (exc && !all_causal);
+        if (exc) {
+            if (mask) row_tile<MODE, true, true>(sAB[buf], sLoc[buf], s0, npairs, T, cbt2, nhh2, run);
+            else row_tile<MODE, true, false>(sAB[buf], sLoc[buf], s0, npairs, T, cbt2, nhh2, run);
+        } else {
+            if (mask) row_tile<MODE, false, true>(sAB[buf], sLoc[buf], s0, npairs, T, cbt2, nhh2, run);
+            else row_tile<MODE, false, false>(sAB[buf], sLoc[buf], s0, npairs, T, cbt2, nhh2, run);
+        }
+        // merge the tile's run into the compensated sums
+#pragma unroll
+        for (int k = 0; k < NMOM; ++k) {
+            if (mom_used(MODE, k)) {
+                kahan(ks[k], kc[k], __fadd_rn(run[k].x, run[k].y));
+                run[k] = make_float2(0.0f, 0.0f);
+            }
+        }
+        buf ^= 1;
+    }
+#pragma unroll
+    for (int k = 0; k < NMOM; ++k) {
+        if (mom_used(MODE, k))
+            ws.rowpart[((size_t)chunk * NMOM + k) * npad + i] = (double)ks[k] - (double)kc[k];
+    }
+}
+
+cudaError_t launch_row32(const Consts &c, const Workspace &ws, cudaStream_t s) {
+    const dim3 grid(c.g.tiles, c.g.n_chunks);
+    if (c.mode == MODE_HESS) row32_kernel<MODE_HESS><<<grid, TILE, 0, s>>>(c, ws);
+    else if (c.mode == MODE_GRAD) row32_kernel<MODE_GRAD><<<grid, TILE, 0, s>>>(c, ws);
+    else row32_kernel<MODE_LL><<<grid, TILE, 0, s>>>(c, ws);
+    return cudaGetLastError();
+}
+
+}  // namespace hk
