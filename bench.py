@@ -1,0 +1,400 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused log-likelihood + gradient + Hessian-diagonal evaluation.
+
+One step = one hawkes_hess_diag call (FP32C) on the 100,000-event synthetic
+workload (2,000 x 2,000 km, 1,500 days, 556 hotspots, log-rates N(0, 0.25)):
+pack, row pass, row finish with the integral term, reduction, column pass.
+It prints one JSON line:
+
+  value     N(N-1) pair-interactions per second, summed over ranks (inputs resident)
+  e2e       the same metric through the C-ABI with host buffers: every step copies
+            x, y, t, r from pinned host memory and reads loglik, gradient and Hessian back
+  roofline  the row pass (dominant kernel) against the FP32 pipe (ALU bound)
+  cpu_baseline  the FP64 oracle on this host's cores, on a bounded sample of rows
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --impl reference the FP64 CPU oracle runs instead (on rank 0 only), each
+step a bounded sample of the same workload.  N > 1 under torchrun runs N
+independent replicas (the evaluation needs no exchange between GPUs).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2103_03348_b300 import synth  # noqa: E402
+
+METRIC = "loglik+grad+Hdiag pair-interactions/s and % FP32 roofline at N=1e5; HMC ESS/s"
+UNIT = "pair-interactions/s"
+L2_FLUSH_BYTES = 256 << 20  # larger than the 126 MB L2
+
+# FP32 pipe: 148 SMs x 128 lanes, one FADD/FMUL/FFMA per lane per clock, at the
+# maximum SM clock of 2,032 MHz: 38.49e12 lane-slots/s.
+SMS, LANES, SM_MAX_MHZ = 148, 128, 2032.0
+FP32_PEAK_SLOTS = SMS * LANES * SM_MAX_MHZ * 1e6
+
+# Algorithmic FP32 lane-slots per pair (see the design notes): background terms
+# for every ordered pair, excitation and column terms for causal pairs inside
+# the exact FP32 underflow band.
+ROW_BG_SLOTS, ROW_EXC_SLOTS, COL_SLOTS = 14, 7, 8
+SURVEY_ROW_SLOTS, SURVEY_COL_SLOTS = 26, 10
+
+
+def workload_config(w):
+    return {"workload": f"{w.name}: 2000x2000 km, 1500 d, 556 hotspots (sigma 20 km), offspring 0.5, "
+                        f"omega 0.1/d, h 5 km, log-rates N(0,0.25)",
+            "n_events": w.n, "params": [float(v) for v in w.params], "precision": "fp32c",
+            "outputs": "loglik + gradient[6+N] + Hessian diagonal[6+N]",
+            "l2": "flushed between timed steps (256 MB write); inputs 3.2 MB would otherwise stay in L2"}
+
+
+def band_pairs(w) -> int:
+    """Causal pairs whose FP32 excitation term can exceed 2^-128 (the exact underflow band)."""
+    log2e = 1.4426950408889634
+    cut = (128.0 + float(np.max(w.r)) * log2e) / (w.params[4] * log2e)
+    hi = np.searchsorted(w.t, w.t, side="left")           # first index with t == t_n (sources strictly before)
+    lo = np.searchsorted(w.t, w.t - cut, side="left")     # first index inside the band
+    return int(np.sum(hi - lo))
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) >= 9:
+                try:
+                    rows.append((float(f[1]), float(f[2]), float(f[3]), f[5], f[6], f[7], f[8]))
+                except ValueError:
+                    pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        load = [r for r in rows if r[2] > 150.0] or rows
+        reasons = set()
+        for r in rows:
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), r[3:]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# FP64 oracle on the host (CPU baseline and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample_rate(w, target_s: float = 12.0, rng_seed: int = 0):
+    """Pairs/s of the FP64 oracle on a bounded row/column sample of the workload.
+
+    A full evaluation visits every (row, source) pair in the row loop and every
+    source's later targets in the column loop.  The sample evaluates k whole
+    rows (all N sources, with the derivative sums) and k whole columns (all
+    later targets); the rate is k(N-1) definition pairs per (row + column) time.
+    """
+    import oracle
+    rng = np.random.default_rng(rng_seed)
+    threads = oracle.max_threads()
+    lam_stub = np.ones(w.n)  # column sums are timed with unit intensities: same work, values unused
+
+    def run(k):
+        idx = np.sort(rng.choice(w.n, k, replace=False))
+        t0 = time.perf_counter()
+        oracle.rows(w.x, w.y, w.t, w.r, w.params, idx)
+        oracle.rate_terms(w.x, w.y, w.t, w.r, w.params, lam_stub, idx)
+        return time.perf_counter() - t0
+
+    oracle.build()  # compile/load outside the timed sample
+    k = max(threads, 8)
+    dt = run(k)
+    while dt < 0.05 * target_s and k < w.n:  # grow the pilot until its time is measurable
+        k = min(w.n, 4 * k)
+        dt = run(k)
+    k2 = int(min(w.n, max(k, k * target_s / max(dt, 1e-3))))
+    dt2 = run(k2)
+    return k2 * (w.n - 1) / dt2, threads, k2, dt2
+
+
+def cpu_info():
+    model = "unknown"
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return model
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    w = synth.make("large")
+    steps, warmup = args.steps, args.warmup
+    per_step_s = max(0.2, min(2.0, 150.0 / max(steps + warmup, 1)))
+    rates = []
+    threads = k = 0
+    for i in range(warmup + steps):
+        rate, threads, k, dt = oracle_sample_rate(w, target_s=per_step_s, rng_seed=i)
+        if i >= warmup:
+            rates.append(rate)
+    value = float(statistics.median(rates))
+    ms = w.n * (w.n - 1) / value * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": steps, "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(w),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{k} whole rows + {k} whole columns of the N={w.n} workload per step "
+                                       f"(FP64 C oracle, OpenMP over rows; CPU: {cpu_info()})"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def profile_traffic():
+    """DRAM traffic per row-pass launch from the committed ncu summary, if the
+    row kernel's source has not changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "row32_large_N100000.txt")
+    src = os.path.join(ROOT, "paper_2103_03348_b300", "csrc", "k_row32.cu")
+    try:
+        text = open(path).read()
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        vals = {}
+        for line in text.splitlines():
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+        if vals.get("source_sha256_16") == digest and "dram_bytes_per_launch" in vals:
+            return float(vals["dram_bytes_per_launch"])
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_2103_03348_b300 import build, hawkes
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = synth.make("large")
+    n = w.n
+    pairs = n * (n - 1)
+    to_dev = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)  # noqa: E731
+    x, y, t, r = to_dev(w.x), to_dev(w.y), to_dev(w.t), to_dev(w.r)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    out = {"loglik": torch.empty((), dtype=torch.float64, device=dev),
+           "grad": torch.empty(6 + n, dtype=torch.float64, device=dev),
+           "hdiag": torch.empty(6 + n, dtype=torch.float64, device=dev),
+           "status": torch.empty((), dtype=torch.int32, device=dev)}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]  # step start/end, row start/end, col start/end
+
+    def step(timed=True):
+        hawkes._call("hess", x, y, t, r, w.params, "fp32c", stream=stream, check=False, out=out,
+                     phase_events=ev[2:6] if timed else None)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # correctness gate before timing
+    step(False)
+    torch.cuda.synchronize()
+    if int(out["status"].item()) != 0:
+        raise RuntimeError(f"status {int(out['status'].item())}: {hawkes.strerror(int(out['status'].item()))}")
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    step_ms, row_ms, col_ms = [], [], []
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with ClockSampler(local_rank) as clk:
+        for _ in range(args.steps):
+            flush.zero_()  # untimed: evicts the L2 between steps
+            ev[0].record(stream)
+            step()
+            ev[1].record(stream)
+            ev[1].synchronize()
+            step_ms.append(ev[0].elapsed_time(ev[1]))
+            row_ms.append(ev[2].elapsed_time(ev[3]))
+            col_ms.append(ev[4].elapsed_time(ev[5]))
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    ms = float(np.mean(step_ms))
+    if world > 1:
+        tmax = torch.tensor([ms], device=dev)
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        ms = float(tmax.item())
+    value = world * pairs / (ms * 1e-3)
+
+    if args.kernel_only:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms,
+                              "row_ms": float(np.mean(row_ms)), "col_ms": float(np.mean(col_ms)),
+                              "steps": args.steps, "warmup": args.warmup, "kernel_only": True}), flush=True)
+        return 0
+
+    # end to end through the public API with host buffers
+    pin = lambda a: torch.tensor(a, dtype=torch.float64).pin_memory()  # noqa: E731
+    hx, hy, ht, hr = pin(w.x), pin(w.y), pin(w.t), pin(w.r)
+    h_out = [torch.empty(6 + n, dtype=torch.float64).pin_memory() for _ in range(2)]
+    h_ll = torch.empty((), dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, min(args.steps, 30))
+    e2e_ms = []
+    for i in range(e2e_steps + 1):
+        flush.zero_()
+        ev[0].record(stream)
+        for hsrc, dsrc in ((hx, x), (hy, y), (ht, t), (hr, r)):
+            dsrc.copy_(hsrc, non_blocking=True)
+        step(False)
+        h_ll.copy_(out["loglik"], non_blocking=True)
+        h_out[0].copy_(out["grad"], non_blocking=True)
+        h_out[1].copy_(out["hdiag"], non_blocking=True)
+        ev[1].record(stream)
+        ev[1].synchronize()
+        if i > 0:
+            e2e_ms.append(ev[0].elapsed_time(ev[1]))
+    e2e_value = world * pairs / (float(np.mean(e2e_ms)) * 1e-3)
+
+    # FP64 GPU path on the same workload (speedup of FP32C over it)
+    fp64_ms = []
+    for i in range(3):
+        ev[0].record(stream)
+        hawkes._call("hess", x, y, t, r, w.params, "fp64", stream=stream, check=False)
+        ev[1].record(stream)
+        ev[1].synchronize()
+        if i > 0:
+            fp64_ms.append(ev[0].elapsed_time(ev[1]))
+
+    if rank != 0:
+        return 0
+
+    pb = band_pairs(w)
+    row_slots = ROW_BG_SLOTS * pairs + ROW_EXC_SLOTS * pb
+    col_slots = COL_SLOTS * pb
+    row_t = float(np.mean(row_ms)) * 1e-3
+    col_t = float(np.mean(col_ms)) * 1e-3
+    achieved = row_slots / row_t
+    clocks = clk.summary()
+    traffic = profile_traffic()
+    peak_t = FP32_PEAK_SLOTS / 1e12
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        rate, threads, k, dt = oracle_sample_rate(w, target_s=12.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{k} whole rows (all {n} sources, with derivative sums) + {k} whole columns of the "
+                         f"N={n} workload in {dt:.1f} s; rate = k(N-1)/time (CPU: {cpu_info()})"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(w),
+        "roofline": {"bound": "alu", "kernel": "row32_kernel (row pass)", "achieved": achieved / 1e12,
+                     "peak": peak_t, "unit": "T FP32 lane-slots/s", "frac": achieved / FP32_PEAK_SLOTS,
+                     "traffic": traffic,
+                     "peak_source": "148 SMs x 128 FP32 lanes x 2032 MHz (unit counts and maximum clock)",
+                     "algorithmic_slots_per_launch": row_slots,
+                     "row_ms": row_t * 1e3, "col_ms": col_t * 1e3,
+                     "col_frac": col_slots / col_t / FP32_PEAK_SLOTS,
+                     "step_frac": (row_slots + col_slots) / (ms * 1e-3) / FP32_PEAK_SLOTS,
+                     "frac_at_sampled_clock": (achieved / (SMS * LANES * clocks["sm_mhz"] * 1e6)
+                                               if clocks.get("sm_mhz") else None),
+                     "band_pairs": pb,
+                     "survey_convention_frac": (SURVEY_ROW_SLOTS * pairs) / row_t / FP32_PEAK_SLOTS},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * n,
+                "d2h_bytes_per_step": 8 + 2 * 8 * (6 + n), "ms_per_step": float(np.mean(e2e_ms))},
+        "cpu_baseline": cpu,
+        "gpu_launches": hawkes.kernels_per_call("hess", "fp32c") * args.steps,
+        "clocks": clocks,
+        "fp64_gpu_path": {"ms_per_step": float(np.mean(fp64_ms)),
+                          "speedup_fp32c_over_fp64": float(np.mean(fp64_ms)) / ms},
+        "wall_s_timed_region": wall,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="time the resident-input steps only (no e2e, FP64 path or CPU baseline); for profilers")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -110,6 +110,16 @@ int hawkes_hess_diag(const double *x, const double *y, const double *t, const do
                      const double params[6], int precision, void *ws, size_t ws_bytes,
                      double *loglik, double *grad, double *hdiag, int *dev_status, void *stream);
 
+/* hawkes_hess_diag with phase markers, for profiling.  phase_events holds four
+ * cudaEvent_t handles (as void*, created by the caller; any may be NULL) that
+ * are recorded on the stream: [0] before and [1] after the row pass (the
+ * dominant O(N^2) kernel), [2] before and [3] after the column pass.  The
+ * results are identical to hawkes_hess_diag. */
+int hawkes_hess_diag_timed(const double *x, const double *y, const double *t, const double *r, int64_t n,
+                           const double params[6], int precision, void *ws, size_t ws_bytes,
+                           double *loglik, double *grad, double *hdiag, int *dev_status, void *stream,
+                           void *const phase_events[4]);
+
 /* Static English description of a hawkes_status code. */
 const char *hawkes_strerror(int status);
 

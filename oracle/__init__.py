@@ -55,6 +55,11 @@ def _load():
             lib.oracle_intensity.restype = ctypes.c_int
             lib.oracle_integral.argtypes = [i64, d, d, d]
             lib.oracle_integral.restype = ctypes.c_double
+            l64 = ctypes.POINTER(ctypes.c_int64)
+            lib.oracle_rows.argtypes = [i64, d, d, d, d, d, i64, l64, d, d, d, ctypes.c_int]
+            lib.oracle_rows.restype = ctypes.c_int
+            lib.oracle_rate_terms.argtypes = [i64, d, d, d, d, d, d, i64, l64, d, d, ctypes.c_int]
+            lib.oracle_rate_terms.restype = ctypes.c_int
             lib.oracle_max_threads.argtypes = []
             lib.oracle_max_threads.restype = ctypes.c_int
             _lib = lib
@@ -117,3 +122,35 @@ def integral(t, r, params) -> float:
     lib = _load()
     t, r, p = _arr(t), _arr(r), _arr(params)
     return float(lib.oracle_integral(t.shape[0], _p(t), _p(r), _p(p)))
+
+
+def _pi(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+def rows(x, y, t, r, params, idx, threads: int = 0):
+    """lambda_n and per-row derivative sums (d lambda_n/dp, d2 lambda_n/dp2) for the rows in idx."""
+    lib = _load()
+    x, y, t, r, p = _arr(x), _arr(y), _arr(t), _arr(r), _arr(params)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    k = idx.shape[0]
+    lam, d1, d2 = np.zeros(k), np.zeros(k * NPAR), np.zeros(k * NPAR)
+    st = lib.oracle_rows(t.shape[0], _p(x), _p(y), _p(t), _p(r), _p(p), k, _pi(idx), _p(lam), _p(d1), _p(d2),
+                         int(threads))
+    if st < 0:
+        raise ValueError("oracle_rows: invalid arguments")
+    return lam, d1.reshape(k, NPAR), d2.reshape(k, NPAR)
+
+
+def rate_terms(x, y, t, r, params, lam, idx, threads: int = 0):
+    """Gradient and Hessian diagonal w.r.t. r_m for the sources in idx, given lambda for later targets."""
+    lib = _load()
+    x, y, t, r, p, lam = _arr(x), _arr(y), _arr(t), _arr(r), _arr(params), _arr(lam)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    k = idx.shape[0]
+    g, h = np.zeros(k), np.zeros(k)
+    st = lib.oracle_rate_terms(t.shape[0], _p(x), _p(y), _p(t), _p(r), _p(p), _p(lam), k, _pi(idx), _p(g), _p(h),
+                                int(threads))
+    if st < 0:
+        raise ValueError("oracle_rate_terms: invalid arguments")
+    return g, h

@@ -338,3 +338,66 @@ double oracle_integral(int64_t n, const double *t, const double *r, const double
     if (n < 1 || !params_ok(params)) return NAN;
     return integral_term(n, t, r, params, NULL, NULL, NULL);
 }
+
+/*
+ * Sampled rows: lambda_n and the sums over sources of the per-pair first and
+ * second derivatives (w.r.t. the six globals) for the k rows listed in idx.
+ * Same per-pair code and order as oracle_eval's rows.  lam[k], d1[k*6], d2[k*6].
+ */
+int oracle_rows(int64_t n, const double *x, const double *y, const double *t, const double *r,
+                const double *params, int64_t k, const int64_t *idx, double *lam, double *d1, double *d2,
+                int nthreads)
+{
+    int64_t q;
+    if (n < 1 || k < 0 || !params_ok(params)) return -1;
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (q = 0; q < k; q++) {
+        const int64_t i = idx[q];
+        double s = 0.0, a1[NPAR] = {0}, a2[NPAR] = {0}, p1[NPAR], p2[NPAR];
+        int64_t j;
+        int kk;
+        for (j = 0; j < n; j++) {
+            s += source_term(x[i], y[i], t[i], x[j], y[j], t[j], r[j], params, 1, NULL, p1, p2);
+            for (kk = 0; kk < NPAR; kk++) { a1[kk] += p1[kk]; a2[kk] += p2[kk]; }
+        }
+        lam[q] = s;
+        for (kk = 0; kk < NPAR; kk++) { d1[q * NPAR + kk] = a1[kk]; d2[q * NPAR + kk] = a2[kk]; }
+    }
+    return 0;
+}
+
+/*
+ * Sampled log-rate outputs (Eqs. 4-5 times theta_m): for each source m in idx,
+ *   g_m = sum_{t_n > t_m} e_nm / lambda_n - theta0 theta_m (1 - exp(-omega (t_N - t_m)))
+ *   h_m = g_m - sum_{t_n > t_m} (e_nm / lambda_n)^2
+ * given lambda[n] for every target n with t_n > t_m (other entries unused).
+ */
+int oracle_rate_terms(int64_t n, const double *x, const double *y, const double *t, const double *r,
+                      const double *params, const double *lambda, int64_t k, const int64_t *idx,
+                      double *g, double *h, int nthreads)
+{
+    int64_t q, j;
+    double tN = -INFINITY;
+    if (n < 1 || k < 0 || !params_ok(params)) return -1;
+    set_threads(nthreads);
+    for (j = 0; j < n; j++) if (t[j] > tN) tN = t[j];
+#pragma omp parallel for schedule(dynamic, 1)
+    for (q = 0; q < k; q++) {
+        const int64_t m = idx[q];
+        double s1 = 0.0, s2 = 0.0, dl;
+        int64_t j;
+        for (j = 0; j < n; j++) {
+            const double e = excitation_term(x[j], y[j], t[j], x[m], y[m], t[m], r[m], params);
+            if (e != 0.0) {
+                const double w = e / lambda[j];
+                s1 += w;
+                s2 += w * w;
+            }
+        }
+        dl = params[P_THETA0] * exp(r[m]) * (1.0 - exp(-params[P_OMEGA] * (tN - t[m])));
+        g[q] = s1 - dl;
+        h[q] = s1 - s2 - dl;
+    }
+    return 0;
+}

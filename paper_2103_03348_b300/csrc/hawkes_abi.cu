@@ -104,7 +104,8 @@ static Consts make_consts(const Geometry &g, int mode, int precision, const doub
 
 static int run(const double *x, const double *y, const double *t, const double *r, int64_t n,
                const double *params, int precision, void *wsp, size_t ws_bytes, int mode,
-               double *loglik, double *grad, double *hdiag, int *dev_status, void *stream) {
+               double *loglik, double *grad, double *hdiag, int *dev_status, void *stream,
+               void *const *events = nullptr) {
     if (n < 2 || n > HAWKES_MAX_EVENTS) return HAWKES_EINVAL;
     if (precision != HAWKES_FP64 && precision != HAWKES_FP32C) return HAWKES_EINVAL;
     if (!x || !y || !t || !r || !params || !wsp || !dev_status) return HAWKES_EINVAL;
@@ -128,13 +129,20 @@ static int run(const double *x, const double *y, const double *t, const double *
     if (cudaMemsetAsync(ws.cnt, 0, (size_t)g.npad * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
     if (launch_prep(c, in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
     if (launch_pack(c, in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
+    auto mark = [&](int k) -> bool {
+        return !(events && events[k]) || cudaEventRecord((cudaEvent_t)events[k], s) == cudaSuccess;
+    };
+    if (!mark(0)) return HAWKES_ECUDA;
     if ((c.fp32c ? launch_row32(c, ws, s) : launch_row64(c, ws, s)) != cudaSuccess) return HAWKES_ECUDA;
+    if (!mark(1)) return HAWKES_ECUDA;
     if (launch_combine(c, ws, s) != cudaSuccess) return HAWKES_ECUDA;
     if (c.fp32c && launch_fixup(c, in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
     if (launch_epilogue(c, in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
     if (launch_finalize(c, ws, out, s) != cudaSuccess) return HAWKES_ECUDA;
     if (mode >= MODE_GRAD) {
+        if (!mark(2)) return HAWKES_ECUDA;
         if ((c.fp32c ? launch_col32(c, in, ws, s) : launch_col64(c, ws, s)) != cudaSuccess) return HAWKES_ECUDA;
+        if (!mark(3)) return HAWKES_ECUDA;
         if (launch_colfinish(c, ws, out, s) != cudaSuccess) return HAWKES_ECUDA;
     }
     return HAWKES_OK;
@@ -170,6 +178,14 @@ int hawkes_hess_diag(const double *x, const double *y, const double *t, const do
                      double *loglik, double *grad, double *hdiag, int *dev_status, void *stream) {
     return hk::run(x, y, t, r, n, params, precision, ws, ws_bytes, hk::MODE_HESS, loglik, grad, hdiag,
                    dev_status, stream);
+}
+
+int hawkes_hess_diag_timed(const double *x, const double *y, const double *t, const double *r, int64_t n,
+                           const double params[6], int precision, void *ws, size_t ws_bytes,
+                           double *loglik, double *grad, double *hdiag, int *dev_status, void *stream,
+                           void *const phase_events[4]) {
+    return hk::run(x, y, t, r, n, params, precision, ws, ws_bytes, hk::MODE_HESS, loglik, grad, hdiag,
+                   dev_status, stream, phase_events);
 }
 
 const char *hawkes_strerror(int status) {

@@ -61,6 +61,8 @@ def lib():
             L.hawkes_grad.restype = ctypes.c_int
             L.hawkes_hess_diag.argtypes = common + [vp, vp, vp, ip, vp]
             L.hawkes_hess_diag.restype = ctypes.c_int
+            L.hawkes_hess_diag_timed.argtypes = common + [vp, vp, vp, ip, vp, ctypes.POINTER(ctypes.c_void_p)]
+            L.hawkes_hess_diag_timed.restype = ctypes.c_int
             L.hawkes_strerror.argtypes = [ctypes.c_int]
             L.hawkes_strerror.restype = ctypes.c_char_p
             L.hawkes_version.argtypes = []
@@ -133,7 +135,8 @@ def _raise_status(code: int):
     raise HawkesError(code, strerror(code))
 
 
-def _call(mode: str, x, y, t, r, params, precision="fp32c", stream=None, workspace=None, check=True, out=None):
+def _call(mode: str, x, y, t, r, params, precision="fp32c", stream=None, workspace=None, check=True, out=None,
+          phase_events=None):
     n = _check_events(x, y, t, r)
     p = PRECISIONS[precision]
     dev = t.device
@@ -164,7 +167,16 @@ def _call(mode: str, x, y, t, r, params, precision="fp32c", stream=None, workspa
             rc = L.hawkes_grad(*args, ll_p, ctypes.c_void_p(out["grad"].data_ptr()), st_p, s_p)
         else:
             g_p = ctypes.c_void_p(out["grad"].data_ptr()) if out.get("grad") is not None else ctypes.c_void_p(0)
-            rc = L.hawkes_hess_diag(*args, ll_p, g_p, ctypes.c_void_p(out["hdiag"].data_ptr()), st_p, s_p)
+            h_p = ctypes.c_void_p(out["hdiag"].data_ptr())
+            if phase_events is None:
+                rc = L.hawkes_hess_diag(*args, ll_p, g_p, h_p, st_p, s_p)
+            else:
+                # torch creates events lazily: record each once so that it has a handle
+                for e in phase_events:
+                    if e.cuda_event == 0:
+                        e.record()
+                evs = (ctypes.c_void_p * 4)(*[ctypes.c_void_p(e.cuda_event) for e in phase_events])
+                rc = L.hawkes_hess_diag_timed(*args, ll_p, g_p, h_p, st_p, s_p, evs)
     if rc != OK:
         raise HawkesError(rc, strerror(rc))
     if check:

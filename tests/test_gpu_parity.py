@@ -1,0 +1,220 @@
+"""CUDA path (through the C-ABI) vs the FP64 CPU oracle, element by element."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_03348_b300 import synth
+from parity_util import check, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def hawkes_mod():
+    from paper_2103_03348_b300 import build, hawkes
+    build.build()
+    return hawkes
+
+
+def dev(a):
+    return torch.tensor(np.asarray(a, dtype=np.float64), dtype=torch.float64, device="cuda")
+
+
+def gpu_eval(w_or_arrays, params, prec, mode="hess", check_status=True):
+    H = hawkes_mod()
+    if hasattr(w_or_arrays, "x"):
+        x, y, t, r = (dev(w_or_arrays.x), dev(w_or_arrays.y), dev(w_or_arrays.t), dev(w_or_arrays.r))
+    else:
+        x, y, t, r = (dev(a) for a in w_or_arrays)
+    if mode == "loglik":
+        return H.loglik(x, y, t, r, params, prec, check=check_status).item(), None, None
+    if mode == "grad":
+        ll, g = H.grad(x, y, t, r, params, prec, check=check_status)
+        return ll.item(), g.cpu().numpy(), None
+    ll, g, h = H.hess_diag(x, y, t, r, params, prec, check=check_status)
+    return ll.item(), g.cpu().numpy(), h.cpu().numpy()
+
+
+_ORACLE_CACHE = {}
+
+
+def oracle_of(w, params=None):
+    p = tuple(w.params if params is None else params)
+    key = (w.name, w.n, p)
+    if key not in _ORACLE_CACHE:
+        _ORACLE_CACHE[key] = oracle.evaluate(w.x, w.y, w.t, w.r, np.array(p), want=2)
+    return _ORACLE_CACHE[key]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+@pytest.mark.parametrize("name", ["unit_square", "ebola_like"])
+def test_workload_parity(name, prec):
+    w = synth.make(name)
+    ref = oracle_of(w)
+    ll, g, h = gpu_eval(w, w.params, prec)
+    check(prec, ll, g, h, ref, label=name)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_modes_agree(prec):
+    w = synth.make("unit_square")
+    ll0, _, _ = gpu_eval(w, w.params, prec, "loglik")
+    ll1, g1, _ = gpu_eval(w, w.params, prec, "grad")
+    ll2, g2, h2 = gpu_eval(w, w.params, prec, "hess")
+    assert rel(ll0, ll2) <= 1e-14 and rel(ll1, ll2) <= 1e-14
+    np.testing.assert_allclose(g1, g2, rtol=1e-13, atol=1e-13 * np.abs(g2).max())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+@pytest.mark.parametrize("n", [2, 3, 127, 128, 129, 255, 257, 1000, 4099])
+def test_ragged_sizes(n, prec):
+    w = synth.make_uniform(100 + n, n, box=1.0, t_max=1.0, r_sd=0.5, params=(0.5, 0.2, 0.1, 0.3, 5.0, 0.05))
+    ref = oracle_of(w)
+    ll, g, h = gpu_eval(w, w.params, prec)
+    check(prec, ll, g, h, ref, label=f"uniform N={n}")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_paper_background_without_temporal_bandwidth(prec):
+    w = synth.make("unit_square")
+    p = np.array(w.params)
+    p[2] = math.inf
+    ref = oracle_of(w, p)
+    ll, g, h = gpu_eval(w, p, prec)
+    assert g[2] == 0.0 and h[2] == 0.0
+    check(prec, ll, g, h, ref, label="tau_t=inf")
+
+
+def tie_and_duplicate_pattern(seed=5, n=700):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0, 1, n)
+    y = rng.uniform(0, 1, n)
+    t = np.round(rng.uniform(0, 1, n), 2)  # heavy ties in time
+    src = rng.choice(n, 120, replace=False)
+    dst = rng.choice(n, 120, replace=False)
+    x[dst], y[dst] = x[src], y[src]  # exact duplicate locations
+    x[:5] = 0.25; y[:5] = 0.75  # one location shared by five events
+    r = rng.normal(0, 0.5, n)
+    o = np.argsort(t, kind="stable")
+    return x[o], y[o], t[o], r[o]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_ties_and_duplicate_locations(prec):
+    x, y, t, r = tie_and_duplicate_pattern()
+    p = np.array([0.5, 0.2, 0.1, 0.3, 5.0, 0.05])
+    ref = oracle.evaluate(x, y, t, r, p, want=2)
+    ll, g, h = gpu_eval((x, y, t, r), p, prec)
+    check(prec, ll, g, h, ref, label="ties+duplicates")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+@pytest.mark.parametrize("far", [6.0, 9.0])
+def test_near_zero_intensity_rows(prec, far):
+    # two events far from everything else: their intensities fall to about
+    # 2^-85..2^-110 (far=6) or 2^-207..2^-240 (far=9, below FP32's range), both
+    # below 2^-60, so the FP32C path recomputes those rows in FP64
+    w = synth.make_uniform(77, 500, box=1.0, t_max=1.0, r_sd=0.3, params=(0.5, 0.5, 0.1, 0.3, 5.0, 0.05))
+    x = np.append(w.x, [far + 0.5, far + 0.5])
+    y = np.append(w.y, [0.5, far + 0.5])  # far from the cluster and from each other
+    t = np.append(w.t, [0.3, 0.6])
+    r = np.append(w.r, [0.0, 0.1])
+    o = np.argsort(t, kind="stable")
+    x, y, t, r = x[o], y[o], t[o], r[o]
+    ref = oracle.evaluate(x, y, t, r, w.params, want=2)
+    assert ref["status"] == 0 and ref["lam"].min() < 2.0 ** -60
+    ll, g, h = gpu_eval((x, y, t, r), w.params, prec)
+    check(prec, ll, g, h, ref, label=f"isolated far={far}")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_zero_intensity_status(prec):
+    H = hawkes_mod()
+    p = np.array([0.5, 0.01, 0.05, 0.3, 10.0, 0.01])
+    x, y, t = np.array([0.0, 0.001, 1.0]), np.array([0.0, 0.0, 1.0]), np.array([0.1, 0.2, 0.3])
+    r = np.zeros(3)
+    assert oracle.evaluate(x, y, t, r, p, want=0)["status"] == 1
+    with pytest.raises(FloatingPointError):
+        gpu_eval((x, y, t, r), p, prec)
+    ll, g, h = gpu_eval((x, y, t, r), p, prec, check_status=False)
+    assert ll == -math.inf and np.all(np.isnan(g)) and np.all(np.isnan(h))
+    del H
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_invalid_data_status(prec):
+    w = synth.make_uniform(9, 300, r_sd=0.2)
+    t_bad = w.t.copy()
+    t_bad[100], t_bad[101] = t_bad[101], t_bad[100] - 1.0
+    with pytest.raises(ValueError):
+        gpu_eval((w.x, w.y, t_bad, w.r), w.params, prec)
+    x_bad = w.x.copy()
+    x_bad[7] = np.nan
+    with pytest.raises(ValueError):
+        gpu_eval((x_bad, w.y, w.t, w.r), w.params, prec)
+    ll, g, h = gpu_eval((x_bad, w.y, w.t, w.r), w.params, prec, check_status=False)
+    assert math.isnan(ll) and np.all(np.isnan(g))
+    # the workspace is reusable after an error
+    ref = oracle_of(w)
+    ll, g, h = gpu_eval(w, w.params, prec)
+    check(prec, ll, g, h, ref, label="after error")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_bitwise_deterministic(prec):
+    w = synth.make("unit_square")
+    a = gpu_eval(w, w.params, prec)
+    b = gpu_eval(w, w.params, prec)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+# ---------------------------------------------------------------------------
+# Full size (100,000 events, the benchmark's workload and launch configuration)
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def large():
+    w = synth.make("large")
+    ll, g, h = gpu_eval(w, w.params, "fp32c")
+    return w, ll, g, h
+
+
+def test_large_identities(large):
+    """Exact identities that hold at any size: 1-homogeneity in (mu0, theta0)
+    and the tie between the column sums and the theta0 row sums."""
+    w, ll, g, h = large
+    mu0, th0 = w.params[0], w.params[3]
+    Lam = oracle.integral(w.t, w.r, w.params)
+    assert rel(mu0 * g[0] + th0 * g[3], w.n - Lam) <= 1e-6
+    assert rel(np.sum(g[6:]), th0 * g[3]) <= 1e-5
+    assert h[0] <= 0 and h[3] <= 0 and np.all(h[6:] - g[6:] <= 1e-9)
+
+
+def test_large_sampled_rates_vs_oracle(large):
+    """64 sampled log-rate gradient and Hessian entries, recomputed one by one by
+    the oracle (sources among the last 1,500 events, whose later targets' exact
+    intensities the oracle can afford)."""
+    w, ll, g, h = large
+    rng = np.random.default_rng(4)
+    pool = np.arange(w.n - 1500, w.n - 1)
+    idx = np.sort(rng.choice(pool, 64, replace=False))
+    later = np.arange(idx.min(), w.n)
+    lam_later, _, _ = oracle.rows(w.x, w.y, w.t, w.r, w.params, later)
+    lam = np.ones(w.n)
+    lam[later] = lam_later
+    g_ref, h_ref = oracle.rate_terms(w.x, w.y, w.t, w.r, w.params, lam, idx)
+    scale_g = np.abs(g[6:]).max()
+    assert np.max(np.abs(g[6 + idx] - g_ref) / np.maximum(np.abs(g_ref), 1e-3 * scale_g)) <= 2e-3
+    assert np.linalg.norm(g[6 + idx] - g_ref) <= 1e-4 * np.linalg.norm(g_ref)
+    assert np.linalg.norm(h[6 + idx] - h_ref) <= 1e-4 * np.linalg.norm(h_ref)
+
+
+def test_large_fp32c_vs_fp64_path(large):
+    """The FP64 GPU path (pinned to the oracle above at 2,000 and 23,422 events)
+    against the FP32C path at full size."""
+    w, ll, g, h = large
+    ll64, g64, h64 = gpu_eval(w, w.params, "fp64")
+    assert rel(ll, ll64) <= 1e-5
+    assert np.linalg.norm(g - g64) <= 1e-5 * np.linalg.norm(g64)
+    assert np.linalg.norm(h - h64) <= 1e-4 * np.linalg.norm(h64)
