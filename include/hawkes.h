@@ -77,7 +77,8 @@ typedef enum {
     HAWKES_ENONFINITE = 3,      /* NaN/Inf in x, y, t or r (device status) */
     HAWKES_EWORKSPACE = 4,      /* ws_bytes < hawkes_workspace_size(n, precision) */
     HAWKES_ECUDA = 5,           /* a CUDA launch or memset failed */
-    HAWKES_EZERO_INTENSITY = 6  /* some lambda_n == 0 (device status) */
+    HAWKES_EZERO_INTENSITY = 6, /* some lambda_n == 0 (device status) */
+    HAWKES_ESCRATCH = 7         /* n above HAWKES_NOALLOC_MAX_EVENTS (hawkes_hess_diag_noalloc) */
 } hawkes_status;
 
 /* Largest supported n (indices are 32-bit inside the kernels). */
@@ -119,6 +120,26 @@ int hawkes_hess_diag_timed(const double *x, const double *y, const double *t, co
                            const double params[6], int precision, void *ws, size_t ws_bytes,
                            double *loglik, double *grad, double *hdiag, int *dev_status, void *stream,
                            void *const phase_events[4]);
+
+/* Largest n accepted by hawkes_hess_diag_noalloc. */
+#define HAWKES_NOALLOC_MAX_EVENTS 4096
+
+/* hawkes_hess_diag for callers that cannot allocate device memory: the paper
+ * has no counterpart; this is a deployment convenience.  Some callers cannot
+ * call cudaMalloc when they evaluate -- a plugin inside a host program that
+ * owns all device allocations, or a loop that cannot afford cudaMalloc's
+ * implicit device synchronisation -- so this call takes no workspace and uses
+ * a 16 MiB device array that the library owns (held on every GPU that loads
+ * the library until exit).  Same inputs, outputs, results and errors as
+ * hawkes_hess_diag with a workspace, for 2 <= n <= HAWKES_NOALLOC_MAX_EVENTS;
+ * a larger n returns HAWKES_ESCRATCH without enqueuing anything.  The first
+ * call on each device looks up the array's device address (make it before any
+ * stream capture).  All calls on a device share the array, so calls that can
+ * overlap on the GPU race on it: issue them in order on one stream.  Nothing
+ * is allocated. */
+int hawkes_hess_diag_noalloc(const double *x, const double *y, const double *t, const double *r, int64_t n,
+                             const double params[6], int precision, double *loglik, double *grad, double *hdiag,
+                             int *dev_status, void *stream);
 
 /* Static English description of a hawkes_status code. */
 const char *hawkes_strerror(int status);

@@ -197,6 +197,7 @@ const char *hawkes_strerror(int status) {
         case HAWKES_EWORKSPACE: return "workspace smaller than hawkes_workspace_size(n, precision)";
         case HAWKES_ECUDA: return "a CUDA launch or memset failed";
         case HAWKES_EZERO_INTENSITY: return "some event has zero intensity: the log-likelihood is -inf";
+        case HAWKES_ESCRATCH: return "n exceeds HAWKES_NOALLOC_MAX_EVENTS, the capacity of the allocation-free call";
         default: return "unknown status";
     }
 }

@@ -30,7 +30,7 @@ LIB_PATH = os.path.join(_PKG, "libhawkes.so")
 FP64, FP32C = 0, 1
 PRECISIONS = {"fp64": FP64, "fp32c": FP32C, FP64: FP64, FP32C: FP32C}
 
-OK, EINVAL, EUNSORTED, ENONFINITE, EWORKSPACE, ECUDA, EZERO = range(7)
+OK, EINVAL, EUNSORTED, ENONFINITE, EWORKSPACE, ECUDA, EZERO, ESCRATCH = range(8)
 
 _lock = threading.Lock()
 _lib = None
