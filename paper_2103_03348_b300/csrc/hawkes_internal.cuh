@@ -150,6 +150,31 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return r;
 }
 
+// Deterministic block sums of K doubles per thread: a fixed warp-shuffle tree,
+// then the warps' partials summed in warp order.  Thread k < K returns total k
+// (other threads return 0).  sh holds (NT / 32) * K doubles.
+template <int NT, int K>
+__device__ __forceinline__ double block_sum_multi(double (&v)[K], double *sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) sh[warp * K + k] = v[k];
+    }
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x < K) {
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) r += sh[w * K + threadIdx.x];
+    }
+    __syncthreads();
+    return r;
+}
+
 template <int NT>
 __device__ __forceinline__ float block_max(float v, float *sh) {
     sh[threadIdx.x] = v;

@@ -59,7 +59,7 @@ __device__ __forceinline__ double std_pdf(double z) { return 0.3989422804014327 
 __device__ __forceinline__ double std_cdf(double z) { return 0.5 * erfc(-z * 0.7071067811865476); }
 
 __global__ void __launch_bounds__(TILE) epilogue_kernel(Consts c, Inputs in, Workspace ws) {
-    __shared__ double sh[TILE];
+    __shared__ double sh[(TILE / 32) * NACC];
     __shared__ float shf[TILE];
     const int i = blockIdx.x * TILE + threadIdx.x;
     const int n = c.g.n, npad = c.g.npad;
@@ -154,9 +154,9 @@ __global__ void __launch_bounds__(TILE) epilogue_kernel(Consts c, Inputs in, Wor
         }
         if (lam <= 0.0) acc[0] = 0.0;  // the status carries the -inf
     }
-    for (int k = 0; k < NACC; ++k) {
-        const double v = block_sum<TILE>(acc[k], sh);
-        if (threadIdx.x == 0) ws.blockpart[(size_t)blockIdx.x * ACC_STRIDE + k] = v;
+    {
+        const double v = block_sum_multi<TILE, NACC>(acc, sh);
+        if (threadIdx.x < NACC) ws.blockpart[(size_t)blockIdx.x * ACC_STRIDE + threadIdx.x] = v;
     }
     if (c.fp32c) {
         const float gm = block_max<TILE>(ghat, shf);
@@ -172,14 +172,20 @@ cudaError_t launch_epilogue(const Consts &c, const Inputs &in, const Workspace &
 constexpr int FIN_THREADS = 256;
 
 __global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(Consts c, Workspace ws, Outputs out) {
-    __shared__ double sh[FIN_THREADS];
+    __shared__ double sh[(FIN_THREADS / 32) * NACC];
     __shared__ double tot[NACC];
     const int tiles = c.g.tiles;
-    for (int k = 0; k < NACC; ++k) {
-        double s = 0.0;
-        for (int b = threadIdx.x; b < tiles; b += FIN_THREADS) s += ws.blockpart[(size_t)b * ACC_STRIDE + k];
-        const double v = block_sum<FIN_THREADS>(s, sh);
-        if (threadIdx.x == 0) tot[k] = v;
+    {
+        // each thread sums a fixed strided subset of tiles, then one fixed-order block sum
+        double acc[NACC];
+#pragma unroll
+        for (int k = 0; k < NACC; ++k) acc[k] = 0.0;
+        for (int b = threadIdx.x; b < tiles; b += FIN_THREADS) {
+#pragma unroll
+            for (int k = 0; k < NACC; ++k) acc[k] += ws.blockpart[(size_t)b * ACC_STRIDE + k];
+        }
+        const double v = block_sum_multi<FIN_THREADS, NACC>(acc, sh);
+        if (threadIdx.x < NACC) tot[threadIdx.x] = v;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -201,13 +207,30 @@ __global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(Consts c, Workspa
             if (out.hdiag) out.hdiag[p] = hd;
         }
         if (out.dev_status) *out.dev_status = code;
-        if (c.fp32c && c.mode >= MODE_GRAD) {
-            // suffix max of the per-tile column weight bound, for the column sweep's stop test
+    }
+    if (c.fp32c && c.mode >= MODE_GRAD) {
+        // suffix max of the per-tile column weight bound, for the column sweep's stop test:
+        // each thread owns a contiguous segment of tiles; segment maxima are scanned in shared memory
+        __shared__ float seg[FIN_THREADS];
+        const int len = (tiles + FIN_THREADS - 1) / FIN_THREADS;
+        const int b0 = threadIdx.x * len, b1 = min(tiles, b0 + len);
+        float m = -INFINITY;
+        for (int b = b0; b < b1; ++b) m = fmaxf(m, ws.tstat32[b].w);
+        seg[threadIdx.x] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
             float run = -INFINITY;
-            for (int b = tiles - 1; b >= 0; --b) {
-                run = fmaxf(run, ws.tstat32[b].w);
-                ws.sufmax[b] = run;
+            for (int k = FIN_THREADS - 1; k >= 0; --k) {
+                const float v = seg[k];
+                seg[k] = run;  // max over the later segments
+                run = fmaxf(run, v);
             }
+        }
+        __syncthreads();
+        float run = seg[threadIdx.x];
+        for (int b = b1 - 1; b >= b0; --b) {
+            run = fmaxf(run, ws.tstat32[b].w);
+            ws.sufmax[b] = run;
         }
     }
 }

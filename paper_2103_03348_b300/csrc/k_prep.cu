@@ -117,23 +117,35 @@ __global__ void __launch_bounds__(TILE) prep_kernel(Consts c, Inputs in, Workspa
         last = (k == (int)gridDim.x - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
-        // the last block reduces the tile bounds in fixed order
+    if (last) {
+        // the last block reduces the tile bounds (each thread a strided subset, then a tree)
         __threadfence();
         double x0 = INFINITY, x1 = -INFINITY, y0 = INFINITY, y1 = -INFINITY;
-        for (int b = 0; b < (int)gridDim.x; ++b) {
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += TILE) {
             // written by other blocks: read through L2
             const double2 lo = __ldcg(reinterpret_cast<const double2 *>(&ws.tbox[b]));
             const double2 hi = __ldcg(reinterpret_cast<const double2 *>(&ws.tbox[b]) + 1);
-            const double4_32a bb = make_double4_32a(lo.x, lo.y, hi.x, hi.y);
-            x0 = fmin(x0, bb.x); x1 = fmax(x1, bb.y); y0 = fmin(y0, bb.z); y1 = fmax(y1, bb.w);
+            x0 = fmin(x0, lo.x); x1 = fmax(x1, lo.y); y0 = fmin(y0, hi.x); y1 = fmax(y1, hi.y);
         }
-        const double t0 = in.t[0], t1 = in.t[n - 1];
-        ws.centre[0] = isfinite(x0 + x1) ? 0.5 * (x0 + x1) : 0.0;
-        ws.centre[1] = isfinite(y0 + y1) ? 0.5 * (y0 + y1) : 0.0;
-        ws.centre[2] = isfinite(t0 + t1) ? 0.5 * (t0 + t1) : 0.0;
-        ws.centre[3] = t1;  // t_N: the last event time (sorted input)
-        ws.hdr[2] = 0;      // ticket ready for the next call
+        __shared__ double4_32a shb[TILE];
+        shb[threadIdx.x] = make_double4_32a(x0, x1, y0, y1);
+        __syncthreads();
+        for (int w = TILE / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) {
+                const double4_32a a = shb[threadIdx.x], b = shb[threadIdx.x + w];
+                shb[threadIdx.x] = make_double4_32a(fmin(a.x, b.x), fmax(a.y, b.y), fmin(a.z, b.z), fmax(a.w, b.w));
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const double4_32a bb = shb[0];
+            const double t0 = in.t[0], t1 = in.t[n - 1];
+            ws.centre[0] = isfinite(bb.x + bb.y) ? 0.5 * (bb.x + bb.y) : 0.0;
+            ws.centre[1] = isfinite(bb.z + bb.w) ? 0.5 * (bb.z + bb.w) : 0.0;
+            ws.centre[2] = isfinite(t0 + t1) ? 0.5 * (t0 + t1) : 0.0;
+            ws.centre[3] = t1;  // t_N: the last event time (sorted input)
+            ws.hdr[2] = 0;      // ticket ready for the next call
+        }
     }
 }
 
