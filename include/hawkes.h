@@ -121,6 +121,61 @@ int hawkes_hess_diag_timed(const double *x, const double *y, const double *t, co
                            double *loglik, double *grad, double *hdiag, int *dev_status, void *stream,
                            void *const phase_events[4]);
 
+/* ------------------------------------------------------------------------
+ * Adaptively preconditioned HMC (Section 2.3): posterior assembly and leapfrog
+ * pieces.  Sampler coordinates q = (log mu0, log tau_x, log tau_t, log theta0,
+ * log omega, log h, r_{s_1}, ..., r_{s_M}) with s_j the sequenced events.
+ * ------------------------------------------------------------------------ */
+
+/* Prior on each raw global parameter p_k (Section 3.2 uses gamma priors on mu0
+ * and theta0 and inverse-gamma priors on the bandwidths and 1/omega; an
+ * inverse-gamma prior on 1/omega is a gamma prior on omega). */
+enum { HAWKES_PRIOR_GAMMA = 0,      /* density prop. to p^(a-1) exp(-b p): shape a, rate b */
+       HAWKES_PRIOR_INVGAMMA = 1 }; /* density prop. to p^(-a-1) exp(-b / p): shape a, scale b */
+typedef struct {
+    int kind[6];
+    double a[6], b[6];
+} hawkes_prior;
+
+/* Bytes of DEVICE workspace hawkes_posterior needs for M sequenced events. */
+size_t hawkes_posterior_workspace_size(int64_t m);
+
+/* Log posterior (Eq. 3, up to a constant) in sampler coordinates, its gradient
+ * and optionally its Hessian diagonal, from a likelihood evaluation at the same
+ * point:
+ *   log pi(q) = loglik + sum_k [log prior_k(p_k) + log p_k] - 1/2 r_S^T P r_S,
+ * where P = (sigma^2 V)^-1 is the precision of the phylogenetic Brownian prior
+ * on the sequenced log-rates (Eq. 2).
+ *   n, m        events and sequenced events (0 <= m <= n)
+ *   seq_idx     DEVICE int[m]: event index of each sequenced event
+ *   prec        DEVICE double[m*m], row-major P (read only)
+ *   params      HOST double[6]: p = exp(q[0..5]) as used for the likelihood
+ *   prior       HOST priors on the six globals
+ *   q           DEVICE double[6+m]: the sampler state (its r part is read)
+ *   loglik, grad, hdiag   DEVICE outputs of hawkes_grad / hawkes_hess_diag at
+ *               (params, r with r[seq_idx[j]] = q[6+j]); hdiag may be NULL
+ *   ws          DEVICE workspace of hawkes_posterior_workspace_size(m) bytes
+ *   logpost     DEVICE double[1]; grad_q, hdiag_q DEVICE double[6+m]
+ *               (hdiag_q NULL exactly when hdiag is NULL)
+ * Enqueued on stream; returns HAWKES_EINVAL for bad arguments. */
+int hawkes_posterior(int64_t n, int64_t m, const int *seq_idx, const double *prec, const double params[6],
+                     const hawkes_prior *prior, const double *q, const double *loglik, const double *grad,
+                     const double *hdiag, void *ws, size_t ws_bytes, double *logpost, double *grad_q,
+                     double *hdiag_q, void *stream);
+
+/* r[seq_idx[j]] = q[6 + j] for j < m (DEVICE vectors): the sampler's log-rates
+ * into the likelihood's full log-rate vector. */
+int hawkes_hmc_scatter_rates(int64_t m, const int *seq_idx, const double *q, double *r, void *stream);
+
+/* Leapfrog pieces on DEVICE vectors of length k (Section 2.3.2, Hamilton's
+ * equations with a diagonal mass matrix M, minv = 1/diag(M)):
+ *   hawkes_hmc_momentum: p += a * g      (half or full momentum step, a = eps/2 or eps)
+ *   hawkes_hmc_position: q += eps * minv * p
+ *   hawkes_hmc_kinetic:  *out = 1/2 sum minv p^2 */
+int hawkes_hmc_momentum(int64_t k, double *p, const double *g, double a, void *stream);
+int hawkes_hmc_position(int64_t k, double *q, const double *p, const double *minv, double eps, void *stream);
+int hawkes_hmc_kinetic(int64_t k, const double *p, const double *minv, double *out, void *stream);
+
 /* Largest n accepted by hawkes_hess_diag_noalloc. */
 #define HAWKES_NOALLOC_MAX_EVENTS 4096
 

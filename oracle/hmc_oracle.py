@@ -1,0 +1,94 @@
+"""FP64 NumPy oracle of the HMC pieces (Section 2.3): the log posterior in
+sampler coordinates, one leapfrog trajectory, and the effective sample size.
+
+TEST INFRASTRUCTURE: used only by the tests and the bench's CPU legs.
+
+Sampler coordinates q = (log mu0, log tau_x, log tau_t, log theta0, log omega,
+log h, r_{s_1..s_M}).  log pi(q) = l(p, r) + sum_k [log prior_k(p_k) + q_k]
+- 1/2 r_S^T P r_S with p = exp(q[:6]), priors Gamma(shape a, rate b) or
+inverse-Gamma(shape a, scale b) on each p_k (kind 0 / 1), and P the precision
+of the phylogenetic Brownian prior (Eq. 2).  The likelihood and its
+derivatives come from the C oracle.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import evaluate
+
+GAMMA, INVGAMMA = 0, 1
+
+
+def log_prior_terms(p, kind, a, b):
+    """log density (up to constants), first and second derivative, per parameter."""
+    p, a, b = np.asarray(p, float), np.asarray(a, float), np.asarray(b, float)
+    kind = np.asarray(kind)
+    lp = np.where(kind == GAMMA, (a - 1) * np.log(p) - b * p, -(a + 1) * np.log(p) - b / p)
+    d1 = np.where(kind == GAMMA, (a - 1) / p - b, -(a + 1) / p + b / p ** 2)
+    d2 = np.where(kind == GAMMA, -(a - 1) / p ** 2, (a + 1) / p ** 2 - 2 * b / p ** 3)
+    return lp, d1, d2
+
+
+def log_posterior(x, y, t, r_base, seq, prec, prior, q, want_hess=True):
+    """(log pi, grad_q[6+M], hdiag_q[6+M] or None) at q, with the likelihood from the oracle."""
+    q = np.asarray(q, float)
+    p = np.exp(q[:6])
+    r = np.array(r_base, float)
+    seq = np.asarray(seq, np.int64)
+    rs = q[6:]
+    r[seq] = rs
+    o = evaluate(x, y, t, r, p, want=2 if want_hess else 1)
+    lp, d1, d2 = log_prior_terms(p, *prior)
+    Pr = prec @ rs if len(rs) else np.zeros(0)
+    logpost = o["loglik"] + np.sum(lp + q[:6]) - 0.5 * float(rs @ Pr)
+    g = np.empty(6 + len(rs))
+    g[:6] = p * (o["grad"][:6] + d1) + 1.0
+    g[6:] = o["grad"][6 + seq] - Pr
+    h = None
+    if want_hess:
+        h = np.empty(6 + len(rs))
+        h[:6] = p * (o["grad"][:6] + d1) + p ** 2 * (o["hdiag"][:6] + d2)
+        h[6:] = o["hdiag"][6 + seq] - np.diag(prec)
+    return logpost, g, h
+
+
+def leapfrog(q, p, eps, n_steps, minv, grad_fn):
+    """Leapfrog integration of Hamilton's equations with diagonal inverse mass.
+
+    grad_fn(q) -> (log pi, grad).  Returns (q, p, log pi, grad) at the end.
+    """
+    q = np.array(q, float)
+    p = np.array(p, float)
+    lp, g = grad_fn(q)
+    p = p + 0.5 * eps * g
+    for step in range(n_steps):
+        q = q + eps * minv * p
+        lp, g = grad_fn(q)
+        p = p + (eps if step < n_steps - 1 else 0.5 * eps) * g
+    return q, p, lp, g
+
+
+def ess_geyer(x):
+    """Effective sample size by Geyer's initial monotone sequence estimator.
+
+    tau = -1 + 2 sum_m Gamma_m with Gamma_m = rho_{2m} + rho_{2m+1}, summed while
+    positive and made non-increasing; ESS = n / tau.  Autocovariances by direct
+    sums (O(n^2)), which is fine for the chain lengths used in tests.
+    """
+    x = np.asarray(x, float)
+    n = len(x)
+    if n < 4 or np.var(x) == 0:
+        return float(n)
+    xc = x - x.mean()
+    acov = np.array([np.dot(xc[: n - k], xc[k:]) / n for k in range(n)])
+    rho = acov / acov[0]
+    gam = []
+    for m in range(n // 2):
+        gm = rho[2 * m] + rho[2 * m + 1]
+        if gm <= 0:
+            break
+        if gam and gm > gam[-1]:
+            gm = gam[-1]
+        gam.append(gm)
+    tau = -1.0 + 2.0 * sum(gam)
+    return float(n / max(tau, 1e-12))

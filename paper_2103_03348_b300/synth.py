@@ -49,6 +49,7 @@ class Workload:
     r: np.ndarray  # float64 [N], log-rates r_n = log theta_n
     params: np.ndarray  # float64 [6]
     sequenced: np.ndarray  # int64 indices of events whose log-rate is free
+    tree_cov: np.ndarray = None  # [M, M] V of the sequenced events' tree (in `sequenced` order), or None
 
     @property
     def n(self) -> int:
@@ -131,14 +132,16 @@ def cluster_process(rng, n_immigrants, box, t_max, centres, sigma_hot, frac_unif
     return np.concatenate(xs), np.concatenate(ys), np.concatenate(ts)
 
 
-def coalescent_brownian(rng, m, sigma2=1.0, root_var=0.0):
+def coalescent_brownian(rng, m, sigma2=1.0, root_var=0.0, return_cov=False):
     """Tip values of Brownian motion down a random Kingman coalescent tree.
 
     Tips are contemporaneous.  While k lineages remain, the waiting time to the
     next merger is Exp(k(k-1)/2) and a uniformly random pair merges.  The root
     value is N(0, root_var*sigma2); each child is its parent plus N(0, sigma2 *
     branch length).  The tip vector is then N(0, sigma2 V) with V the tree's
-    shared-path-length matrix (Section 2.2, Eq. 2).
+    shared-path-length matrix (Section 2.2, Eq. 2).  With return_cov the tree's
+    V is returned too: V_ij = root_var + (root height - height of the most
+    recent common ancestor of tips i and j); the random draws are unchanged.
     """
     # Build the tree bottom-up: node heights and parent pointers.
     height = np.zeros(2 * m - 1)
@@ -167,7 +170,26 @@ def coalescent_brownian(rng, m, sigma2=1.0, root_var=0.0):
             continue
         bl = height[parent[node]] - height[node]
         value[node] = value[parent[node]] + math.sqrt(sigma2 * bl) * rng.standard_normal()
-    return value[:m]
+    if not return_cov:
+        return value[:m]
+    # V from the tree: for every internal node, the pairs split by it share the
+    # path from the root down to that node
+    children = [[] for _ in range(2 * m - 1)]
+    for node in range(2 * m - 1):
+        if parent[node] >= 0:
+            children[parent[node]].append(node)
+    tips = [[k] if k < m else None for k in range(2 * m - 1)]
+    cov = np.zeros((m, m))
+    for node in range(m, 2 * m - 1):  # children are created before their parent
+        a, b = children[node]
+        shared = root_var + height[root] - height[node]
+        ta, tb = np.array(tips[a]), np.array(tips[b])
+        cov[np.ix_(ta, tb)] = shared
+        cov[np.ix_(tb, ta)] = shared
+        tips[node] = tips[a] + tips[b]
+        tips[a] = tips[b] = None
+    cov[np.arange(m), np.arange(m)] = root_var + height[root]
+    return value[:m], cov
 
 
 def _hotspot_pattern(rng, n_target, box, t_max, n_hot, frac_uniform, branching, omega, sigma_off,
@@ -191,16 +213,24 @@ def make_unit_square(seed: int = 1000, n: int = 2000) -> Workload:
     return _sorted("unit_square_N2000", x, y, t, np.zeros(n), params, np.zeros(n, bool))
 
 
-def make_ebola_like(seed: int = 1001, n: int = 23422, m_seq: int = 1610) -> Workload:
+def make_ebola_like(seed: int = 1001, n: int = 23422, m_seq: int = 1610, box: float = 600.0,
+                    t_max: float = 730.0, n_hot: int = 50) -> Workload:
     rng = np.random.default_rng(seed)
-    x, y, t = _hotspot_pattern(rng, n, 600.0, 730.0, 50, 0.0, 0.5, 0.1, 5.0)
+    x, y, t = _hotspot_pattern(rng, n, box, t_max, n_hot, 0.0, 0.5, 0.1, 5.0)
     r = np.zeros(n)
     seq = rng.choice(n, min(m_seq, n), replace=False)
-    r[seq] = coalescent_brownian(rng, len(seq))
+    r[seq], cov = coalescent_brownian(rng, len(seq), return_cov=True)
     mask = np.zeros(n, bool)
     mask[seq] = True
     params = (0.5, 20.0, 30.0, 0.5, 0.1, 5.0)
-    return _sorted(f"ebola_like_N{n}", x, y, t, r, params, mask)
+    w = _sorted(f"ebola_like_N{n}", x, y, t, r, params, mask)
+    # V in the order of w.sequenced (time-sorted event indices)
+    tip_of = np.full(n, -1, dtype=np.int64)
+    tip_of[seq] = np.arange(len(seq))
+    order = np.argsort(t, kind="stable")
+    tips = tip_of[order[w.sequenced]]
+    w.tree_cov = np.ascontiguousarray(cov[np.ix_(tips, tips)])
+    return w
 
 
 def make_large(seed: int = 1002, n: int = 100_000) -> Workload:

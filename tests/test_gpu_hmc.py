@@ -1,0 +1,118 @@
+"""GPU HMC pieces (posterior assembly, leapfrog kernels, sampler) vs the oracle."""
+import numpy as np
+import pytest
+
+from oracle import hmc_oracle
+from paper_2103_03348_b300 import synth
+from parity_util import FP64_TOL, norm_rel, scaled_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def problem(n=600, m=40, seed=11):
+    w = synth.make_ebola_like(seed=seed, n=n, m_seq=m, box=120.0, t_max=120.0, n_hot=4)
+    prec = np.linalg.inv(w.tree_cov)
+    return w, prec
+
+
+def make_post(w, prec, precision):
+    from paper_2103_03348_b300 import build, hmc
+    build.build()
+    d = lambda a: torch.tensor(np.asarray(a, float), dtype=torch.float64, device="cuda")  # noqa: E731
+    post = hmc.Posterior(d(w.x), d(w.y), d(w.t), d(w.r), torch.tensor(w.sequenced, device="cuda"),
+                         d(prec), hmc.prior_km_days(), precision)
+    return post, hmc
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_posterior_parity(precision):
+    w, prec = problem()
+    post, hmc = make_post(w, prec, precision)
+    q = np.concatenate([np.log(w.params), w.r[w.sequenced]])
+    q[6:] += np.random.default_rng(0).normal(0, 0.3, len(q) - 6)
+    ev = post.evaluate(torch.tensor(q, dtype=torch.float64, device="cuda"), want_hess=True)
+    lp, g, h = ev["logpost"].item(), ev["grad"].cpu().numpy(), ev["hdiag"].cpu().numpy()
+    ref = hmc_oracle.log_posterior(w.x, w.y, w.t, w.r, w.sequenced, prec, hmc.prior_km_days().as_tuple(), q)
+    if precision == "fp64":
+        assert abs(lp - ref[0]) <= FP64_TOL * abs(ref[0])
+        assert scaled_err(g, ref[1]) <= FP64_TOL and scaled_err(h, ref[2]) <= FP64_TOL
+    else:
+        assert abs(lp - ref[0]) <= 1e-5 * abs(ref[0])
+        assert norm_rel(g, ref[1]) <= 1e-5 and norm_rel(h, ref[2]) <= 1e-4
+
+
+def test_leapfrog_trajectory_parity():
+    w, prec = problem()
+    post, hmc = make_post(w, prec, "fp64")
+    prior = hmc.prior_km_days().as_tuple()
+    rng = np.random.default_rng(1)
+    q0 = np.concatenate([np.log(w.params), w.r[w.sequenced]])
+    dim = len(q0)
+    _, _, h0 = hmc_oracle.log_posterior(w.x, w.y, w.t, w.r, w.sequenced, prec, prior, q0)
+    minv = 1.0 / np.maximum(-h0, 1e-2)
+    p0 = rng.normal(size=dim) / np.sqrt(minv)
+    eps, steps = 0.05, 20
+
+    def gf(q):
+        lp, g, _ = hmc_oracle.log_posterior(w.x, w.y, w.t, w.r, w.sequenced, prec, prior, q, want_hess=False)
+        return lp, g
+
+    q_ref, p_ref, lp_ref, _ = hmc_oracle.leapfrog(q0, p0, eps, steps, minv, gf)
+    d = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")  # noqa: E731
+    q, p, mi = d(q0), d(p0), d(minv)
+    g0 = post.evaluate(q)["grad"].clone()
+    scratch = {"logpost": torch.empty((), dtype=torch.float64, device="cuda"),
+               "grad": torch.empty(dim, dtype=torch.float64, device="cuda")}
+    ev = hmc.leapfrog(post, q, p, g0, eps, steps, mi, scratch)
+    assert np.max(np.abs(q.cpu().numpy() - q_ref)) <= 1e-9
+    assert np.max(np.abs(p.cpu().numpy() - p_ref) / np.maximum(np.abs(p_ref), 1.0)) <= 1e-8
+    assert abs(ev["logpost"].item() - lp_ref) <= 1e-9 * abs(lp_ref)
+
+
+class GaussPost:
+    """A Gaussian target with known moments, in the Posterior interface."""
+
+    def __init__(self, sig):
+        self.sig = sig
+        self.dim = sig.numel()
+        self.calls = {"grad": 0, "hess": 0}
+
+    def evaluate(self, q, want_hess=False, out=None):
+        if out is None:
+            out = {"logpost": torch.empty((), dtype=torch.float64, device=q.device),
+                   "grad": torch.empty_like(q), "hdiag": torch.empty_like(q)}
+        out["logpost"].copy_(-0.5 * torch.sum((q / self.sig) ** 2))
+        out["grad"].copy_(-q / self.sig ** 2)
+        if want_hess:
+            out["hdiag"].copy_(-1.0 / self.sig ** 2)
+        self.calls["hess" if want_hess else "grad"] += 1
+        return out
+
+    def status(self):
+        return 0
+
+
+def test_sampler_recovers_gaussian_moments():
+    from paper_2103_03348_b300 import build, hmc
+    build.build()
+    sig = torch.logspace(-1.5, 1.0, 20, dtype=torch.float64, device="cuda")
+    post = GaussPost(sig)
+    q0 = torch.zeros(20, dtype=torch.float64, device="cuda") + 0.3 * sig
+    ch = hmc.sample(post, q0, n_iter=1500, n_warmup=300, n_steps=10, eps0=0.1, mass_every=50, seed=3)
+    s = sig.cpu().numpy()
+    ess = hmc.ess_all(ch.draws)
+    mean, var = ch.draws.mean(0), ch.draws.var(0)
+    assert 0.5 < ch.accept.mean() <= 1.0
+    assert np.all(np.abs(mean) <= 5 * s / np.sqrt(ess))
+    assert np.all(np.abs(var / s ** 2 - 1) <= 5 * np.sqrt(2 / ess) + 0.05)
+
+
+def test_short_chain_on_hawkes_posterior():
+    w, prec = problem()
+    post, hmc = make_post(w, prec, "fp32c")
+    q0 = torch.tensor(np.concatenate([np.log(w.params), w.r[w.sequenced]]), dtype=torch.float64, device="cuda")
+    ch = hmc.sample(post, q0, n_iter=150, n_warmup=150, n_steps=20, eps0=0.02, mass_every=50, seed=5)
+    assert np.all(np.isfinite(ch.logpost))
+    assert 0.4 < ch.accept.mean() <= 1.0
+    assert 0.8 * 300 * 20 <= post.calls["grad"] <= 300 * 20  # divergent warm-up trajectories stop early

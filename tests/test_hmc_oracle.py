@@ -1,0 +1,124 @@
+"""Pins of the HMC oracle (Section 2.3) and of the product's ESS estimator."""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from oracle import hmc_oracle
+from paper_2103_03348_b300 import synth
+
+
+def test_prior_terms_match_scipy_densities():
+    kind = np.array([0, 1, 1, 0, 0, 1])
+    a = np.array([2.0, 1.0, 2.0, 1.0, 2.0, 2.0])
+    b = np.array([2.0, 1112.0, 182.6, 0.001, 182.6, 55.6])
+    p1 = np.array([0.5, 20.0, 30.0, 0.5, 0.1, 5.0])
+    p2 = p1 * 1.37
+    lp1, d1, d2 = hmc_oracle.log_prior_terms(p1, kind, a, b)
+    lp2, _, _ = hmc_oracle.log_prior_terms(p2, kind, a, b)
+
+    def scipy_logpdf(p, k):
+        if kind[k] == 0:
+            return stats.gamma.logpdf(p, a[k], scale=1.0 / b[k])
+        return stats.invgamma.logpdf(p, a[k], scale=b[k])
+
+    for k in range(6):
+        # densities agree up to the normalising constant: compare differences
+        assert abs((lp2[k] - lp1[k]) - (scipy_logpdf(p2[k], k) - scipy_logpdf(p1[k], k))) < 1e-10
+        h = 1e-5 * p1[k]
+        fd1 = (scipy_logpdf(p1[k] + h, k) - scipy_logpdf(p1[k] - h, k)) / (2 * h)
+        h2 = 1e-3 * p1[k]  # a wider step for the second difference (roundoff ~ eps |f| / h^2)
+        fd2 = (scipy_logpdf(p1[k] + h2, k) - 2 * scipy_logpdf(p1[k], k) + scipy_logpdf(p1[k] - h2, k)) / h2 ** 2
+        assert abs(d1[k] - fd1) <= 1e-6 * max(1.0, abs(fd1))
+        assert abs(d2[k] - fd2) <= 1e-4 * abs(d2[k]) + 1e-8 / p1[k] ** 2
+
+
+def small_problem(n=60, m=8, seed=3):
+    w = synth.make_ebola_like(seed=seed, n=n, m_seq=m, box=100.0, t_max=60.0, n_hot=3)
+    prec = np.linalg.inv(w.tree_cov)
+    prior = (np.array([0, 1, 1, 0, 0, 1]), np.array([2.0, 1.0, 2.0, 1.0, 2.0, 2.0]),
+             np.array([2.0, 1112.0, 182.6, 0.001, 182.6, 55.6]))
+    q = np.concatenate([np.log(w.params), w.r[w.sequenced]])
+    return w, prec, prior, q
+
+
+def test_log_posterior_finite_differences():
+    w, prec, prior, q = small_problem()
+    lp, g, h = hmc_oracle.log_posterior(w.x, w.y, w.t, w.r, w.sequenced, prec, prior, q)
+
+    def f(qq):
+        return hmc_oracle.log_posterior(w.x, w.y, w.t, w.r, w.sequenced, prec, prior, qq, want_hess=False)
+
+    for k in range(len(q)):
+        step = 1e-4
+
+        def dd(hh, k=k):
+            qp, qm = q.copy(), q.copy()
+            qp[k] += hh
+            qm[k] -= hh
+            a, b = f(qp), f(qm)
+            return (a[0] - b[0]) / (2 * hh), (a[1][k] - b[1][k]) / (2 * hh)
+
+        (g1, h1), (g2, h2) = dd(step), dd(step / 2)
+        g_fd, h_fd = (4 * g2 - g1) / 3, (4 * h2 - h1) / 3
+        assert abs(g[k] - g_fd) <= 1e-7 * max(1.0, abs(g_fd)), (k, g[k], g_fd)
+        assert abs(h[k] - h_fd) <= 1e-6 * max(1.0, abs(h_fd)), (k, h[k], h_fd)
+
+
+def test_leapfrog_harmonic_oscillator_closed_form():
+    # log pi = -q^2/2, unit mass: one leapfrog step is the linear map
+    # [[1 - e^2/2, e], [-e (1 - e^2/4), 1 - e^2/2]]
+    eps, steps = 0.3, 17
+    A = np.array([[1 - eps ** 2 / 2, eps], [-eps * (1 - eps ** 2 / 4), 1 - eps ** 2 / 2]])
+    q0, p0 = np.array([0.7]), np.array([-1.1])
+    q, p, _, _ = hmc_oracle.leapfrog(q0, p0, eps, steps, np.ones(1), lambda x: (-0.5 * x @ x, -x))
+    ref = np.linalg.matrix_power(A, steps) @ np.array([q0[0], p0[0]])
+    assert np.allclose([q[0], p[0]], ref, rtol=1e-13, atol=1e-14)
+
+
+def test_leapfrog_reversible_and_second_order():
+    rng = np.random.default_rng(0)
+    prec = np.diag(rng.uniform(0.5, 4.0, 5))
+
+    def gf(x):
+        return -0.5 * x @ prec @ x, -prec @ x
+
+    q0, p0 = rng.normal(size=5), rng.normal(size=5)
+    minv = np.full(5, 0.8)
+    q1, p1, _, _ = hmc_oracle.leapfrog(q0, p0, 0.1, 25, minv, gf)
+    q2, p2, _, _ = hmc_oracle.leapfrog(q1, -p1, 0.1, 25, minv, gf)
+    assert np.allclose(q2, q0, atol=1e-12) and np.allclose(-p2, p0, atol=1e-12)
+
+    def energy_err(eps):
+        q, p, lp, _ = hmc_oracle.leapfrog(q0, p0, eps, int(round(1.0 / eps)), minv, gf)
+        return abs((-lp + 0.5 * np.sum(minv * p * p)) - (-gf(q0)[0] + 0.5 * np.sum(minv * p0 * p0)))
+
+    e1, e2 = energy_err(0.1), energy_err(0.05)
+    assert 3.0 < e1 / e2 < 5.0  # energy error is O(eps^2)
+
+
+def ar1(rho, n, seed):
+    rng = np.random.default_rng(seed)
+    x = np.empty(n)
+    x[0] = rng.normal() / math.sqrt(1 - rho ** 2)
+    e = rng.normal(size=n)
+    for i in range(1, n):
+        x[i] = rho * x[i - 1] + e[i]
+    return x
+
+
+@pytest.mark.parametrize("rho", [0.0, 0.5, 0.9])
+def test_ess_of_ar1_chains(rho):
+    n = 8000
+    x = ar1(rho, n, seed=int(rho * 10))
+    ess = hmc_oracle.ess_geyer(x)
+    expected = n * (1 - rho) / (1 + rho)  # n / integrated autocorrelation time
+    assert abs(ess / expected - 1) < 0.2, (ess, expected)
+
+
+def test_product_ess_matches_oracle():
+    from paper_2103_03348_b300 import hmc
+    for rho, seed in ((0.3, 1), (0.95, 2)):
+        x = ar1(rho, 3000, seed)
+        assert abs(hmc.ess(x) / hmc_oracle.ess_geyer(x) - 1) < 1e-9
