@@ -111,6 +111,23 @@ int hawkes_hess_diag(const double *x, const double *y, const double *t, const do
                      const double params[6], int precision, void *ws, size_t ws_bytes,
                      double *loglik, double *grad, double *hdiag, int *dev_status, void *stream);
 
+/* Mode of hawkes_eval_device_params. */
+enum { HAWKES_MODE_LOGLIK = 0, HAWKES_MODE_GRAD = 1, HAWKES_MODE_HESS = 2 };
+
+/* The three evaluations with the parameter vector in DEVICE memory, so that a
+ * caller whose parameters are produced on the GPU (a sampler's state) needs no
+ * host round trip between evaluations.  params_dev: DEVICE double[6] in the
+ * usual order; with log_params != 0 it holds their logarithms (the first six
+ * sampler coordinates).  mode selects loglik / + grad / + hdiag exactly as
+ * hawkes_loglik / hawkes_grad / hawkes_hess_diag (loglik is required for
+ * mode 0, grad for mode 1, hdiag for mode 2).  Parameters that are not finite
+ * and positive are found on the GPU: *dev_status = HAWKES_EINVAL and every
+ * output is NaN. */
+int hawkes_eval_device_params(const double *x, const double *y, const double *t, const double *r, int64_t n,
+                              const double *params_dev, int log_params, int precision, int mode, void *ws,
+                              size_t ws_bytes, double *loglik, double *grad, double *hdiag, int *dev_status,
+                              void *stream);
+
 /* hawkes_hess_diag with phase markers, for profiling.  phase_events holds four
  * cudaEvent_t handles (as void*, created by the caller; any may be NULL) that
  * are recorded on the stream: [0] before and [1] after the row pass (the
@@ -149,16 +166,16 @@ size_t hawkes_posterior_workspace_size(int64_t m);
  *   n, m        events and sequenced events (0 <= m <= n)
  *   seq_idx     DEVICE int[m]: event index of each sequenced event
  *   prec        DEVICE double[m*m], row-major P (read only)
- *   params      HOST double[6]: p = exp(q[0..5]) as used for the likelihood
  *   prior       HOST priors on the six globals
- *   q           DEVICE double[6+m]: the sampler state (its r part is read)
- *   loglik, grad, hdiag   DEVICE outputs of hawkes_grad / hawkes_hess_diag at
- *               (params, r with r[seq_idx[j]] = q[6+j]); hdiag may be NULL
+ *   q           DEVICE double[6+m]: the sampler state; p = exp(q[0..5])
+ *   loglik, grad, hdiag   DEVICE outputs of the likelihood evaluation at
+ *               (p, r with r[seq_idx[j]] = q[6+j]); hdiag may be NULL
+ * A q whose p is not finite and positive gives log pi = -inf.
  *   ws          DEVICE workspace of hawkes_posterior_workspace_size(m) bytes
  *   logpost     DEVICE double[1]; grad_q, hdiag_q DEVICE double[6+m]
  *               (hdiag_q NULL exactly when hdiag is NULL)
  * Enqueued on stream; returns HAWKES_EINVAL for bad arguments. */
-int hawkes_posterior(int64_t n, int64_t m, const int *seq_idx, const double *prec, const double params[6],
+int hawkes_posterior(int64_t n, int64_t m, const int *seq_idx, const double *prec,
                      const hawkes_prior *prior, const double *q, const double *loglik, const double *grad,
                      const double *hdiag, void *ws, size_t ws_bytes, double *logpost, double *grad_q,
                      double *hdiag_q, void *stream);

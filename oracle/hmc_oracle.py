@@ -72,7 +72,8 @@ def ess_geyer(x):
     """Effective sample size by Geyer's initial monotone sequence estimator.
 
     tau = -1 + 2 sum_m Gamma_m with Gamma_m = rho_{2m} + rho_{2m+1}, summed while
-    positive and made non-increasing; ESS = n / tau.  Autocovariances by direct
+    positive and made non-increasing; ESS = n / tau with tau floored at
+    1/log10(n) (an antithetic chain's ESS is capped at n log10(n)).  Autocovariances by direct
     sums (O(n^2)), which is fine for the chain lengths used in tests.
     """
     x = np.asarray(x, float)
@@ -91,4 +92,4 @@ def ess_geyer(x):
             gm = gam[-1]
         gam.append(gm)
     tau = -1.0 + 2.0 * sum(gam)
-    return float(n / max(tau, 1e-12))
+    return float(n / max(tau, 1.0 / np.log10(n)))

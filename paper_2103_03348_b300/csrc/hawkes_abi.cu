@@ -1,9 +1,10 @@
 // extern "C" entry points of libhawkes.so (declared in include/hawkes.h).
 //
-// Host side only: argument checks, workspace carving, the per-call constants
-// (computed in FP64 from the parameter vector) and the launch sequence.  No
-// host synchronisation and no allocation: everything is enqueued on the
-// caller's stream into the caller's workspace.
+// Argument checks, workspace carving and the launch sequence, plus the one-thread
+// setup kernel that derives the per-call constants from the parameter vector
+// (given on the host or in device memory).  No host synchronisation and no
+// allocation: everything is enqueued on the caller's stream into the caller's
+// workspace.
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -42,6 +43,7 @@ size_t carve(void *base, const Geometry &g, int precision, Workspace *w) {
     };
     const size_t np = (size_t)g.npad, nt = (size_t)g.tiles;
     w->hdr = (int *)take(8 * sizeof(int));
+    w->derived = (Derived *)take(sizeof(Derived));
     w->centre = (double *)take(4 * sizeof(double));
     w->hash = (int *)take((size_t)g.hash_size * sizeof(int));
     w->cnt = (int *)take(np * sizeof(int));
@@ -72,54 +74,83 @@ static bool params_valid(const double *p) {
     return true;
 }
 
-static Consts make_consts(const Geometry &g, int mode, int precision, const double *p) {
-    Consts c;
-    memset(&c, 0, sizeof(c));
-    c.g = g;
-    c.mode = mode;
-    c.fp32c = precision == HAWKES_FP32C;
-    c.mu0 = p[0]; c.tx = p[1]; c.tt = p[2]; c.th0 = p[3]; c.om = p[4]; c.h = p[5];
-    c.tt_inf = isinf(c.tt) ? 1 : 0;
+// One thread derives every parameter-dependent constant in FP64.  Parameters
+// that are not finite and positive (tau_t may be +inf) set ST_BADPARAM, and
+// finalize then reports HAWKES_EINVAL with NaN outputs.
+__global__ void setup_kernel(ParamSource ps, int fp32c, Derived *out, int *hdr) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double p[6];
+    bool ok = true;
+    for (int k = 0; k < 6; ++k) {
+        p[k] = ps.dev ? (ps.log_scale ? exp(ps.dev[k]) : ps.dev[k]) : ps.v[k];
+        if (k == 2 && isinf(p[k]) && p[k] > 0) continue;
+        if (!isfinite(p[k]) || !(p[k] > 0)) ok = false;
+    }
+    Derived d;
+    d.mu0 = p[0]; d.tx = p[1]; d.tt = p[2]; d.th0 = p[3]; d.om = p[4]; d.h = p[5];
+    d.tt_inf = isinf(d.tt) ? 1 : 0;
     const double two_pi = 6.283185307179586476925286766559;
-    c.A = c.tt_inf ? c.mu0 / (two_pi * c.tx * c.tx)
-                   : c.mu0 / (two_pi * sqrt(two_pi) * c.tx * c.tx * c.tt);
-    c.B = c.th0 * c.om / (two_pi * c.h * c.h);
+    d.A = d.tt_inf ? d.mu0 / (two_pi * d.tx * d.tx) : d.mu0 / (two_pi * sqrt(two_pi) * d.tx * d.tx * d.tt);
+    d.B = d.th0 * d.om / (two_pi * d.h * d.h);
     // FP64 pair constants (also used by the FP32C fix-up rows)
-    c.ibx = 1.0 / (2.0 * c.tx * c.tx);
-    c.ibt = c.tt_inf ? 0.0 : 1.0 / (2.0 * c.tt * c.tt);
-    c.ih = 1.0 / (2.0 * c.h * c.h);
-    if (c.fp32c) {
+    d.ibx = 1.0 / (2.0 * d.tx * d.tx);
+    d.ibt = d.tt_inf ? 0.0 : 1.0 / (2.0 * d.tt * d.tt);
+    d.ih = 1.0 / (2.0 * d.h * d.h);
+    if (fp32c) {
         // x~ = (x - xc) sqrt(log2(e)/2) / tau_x makes the background's spatial exponent -d~^2;
         // t~ = (t - tc) omega log2(e) makes the excitation's temporal exponent -dt~.
-        c.sx = sqrt(LOG2E / 2.0) / c.tx;
-        c.st = c.om * LOG2E;
-        c.cbt = c.tt_inf ? 0.0f : (float)(LOG2E / (2.0 * c.tt * c.tt) / (c.st * c.st));
-        c.hh = (float)((c.tx / c.h) * (c.tx / c.h));
+        d.sx = sqrt(LOG2E / 2.0) / d.tx;
+        d.st = d.om * LOG2E;
+        d.cbt = d.tt_inf ? 0.0f : (float)(LOG2E / (2.0 * d.tt * d.tt) / (d.st * d.st));
+        d.hh = (float)((d.tx / d.h) * (d.tx / d.h));
     } else {
-        c.sx = 1.0;
-        c.st = 1.0;
+        d.sx = 1.0;
+        d.st = 1.0;
+        d.cbt = 0.0f;
+        d.hh = 0.0f;
     }
-    return c;
+    d.valid = ok ? 1 : 0;
+    if (!ok) atomicOr(&hdr[0], ST_BADPARAM);
+    *out = d;
+}
+
+cudaError_t launch_setup(const Consts &c, const ParamSource &ps, const Workspace &ws, cudaStream_t s) {
+    setup_kernel<<<1, 32, 0, s>>>(ps, c.fp32c, ws.derived, ws.hdr);
+    return cudaGetLastError();
 }
 
 static int run(const double *x, const double *y, const double *t, const double *r, int64_t n,
-               const double *params, int precision, void *wsp, size_t ws_bytes, int mode,
-               double *loglik, double *grad, double *hdiag, int *dev_status, void *stream,
+               const double *params, const double *params_dev, int log_params, int precision, void *wsp,
+               size_t ws_bytes, int mode, double *loglik, double *grad, double *hdiag, int *dev_status, void *stream,
                void *const *events = nullptr) {
     if (n < 2 || n > HAWKES_MAX_EVENTS) return HAWKES_EINVAL;
     if (precision != HAWKES_FP64 && precision != HAWKES_FP32C) return HAWKES_EINVAL;
-    if (!x || !y || !t || !r || !params || !wsp || !dev_status) return HAWKES_EINVAL;
+    if (mode != MODE_LL && mode != MODE_GRAD && mode != MODE_HESS) return HAWKES_EINVAL;
+    if (!x || !y || !t || !r || !(params || params_dev) || !wsp || !dev_status) return HAWKES_EINVAL;
     if (mode == MODE_LL && !loglik) return HAWKES_EINVAL;
     if (mode == MODE_GRAD && !grad) return HAWKES_EINVAL;
     if (mode == MODE_HESS && !hdiag) return HAWKES_EINVAL;
     if (((uintptr_t)wsp & 255) != 0) return HAWKES_EINVAL;
-    if (!params_valid(params)) return HAWKES_EINVAL;
+    if (params && !params_valid(params)) return HAWKES_EINVAL;
     const Geometry g = make_geometry(n);
     Workspace ws;
     const size_t need = carve(wsp, g, precision, &ws);
     if (ws_bytes < need) return HAWKES_EWORKSPACE;
 
-    const Consts c = make_consts(g, mode, precision, params);
+    Consts c;
+    memset(&c, 0, sizeof(c));
+    c.g = g;
+    c.mode = mode;
+    c.fp32c = precision == HAWKES_FP32C;
+    c.d = ws.derived;
+    ParamSource ps;
+    memset(&ps, 0, sizeof(ps));
+    if (params) {
+        for (int k = 0; k < 6; ++k) ps.v[k] = params[k];
+    } else {
+        ps.dev = params_dev;
+        ps.log_scale = log_params ? 1 : 0;
+    }
     const Inputs in = {x, y, t, r};
     const Outputs out = {loglik, mode >= MODE_GRAD ? grad : nullptr, mode == MODE_HESS ? hdiag : nullptr, dev_status};
     cudaStream_t s = (cudaStream_t)stream;
@@ -127,6 +158,7 @@ static int run(const double *x, const double *y, const double *t, const double *
     if (cudaMemsetAsync(ws.hdr, 0, 8 * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
     if (cudaMemsetAsync(ws.hash, 0xFF, (size_t)g.hash_size * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
     if (cudaMemsetAsync(ws.cnt, 0, (size_t)g.npad * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
+    if (launch_setup(c, ps, ws, s) != cudaSuccess) return HAWKES_ECUDA;
     if (launch_prep(c, in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
     if (launch_pack(c, in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
     auto mark = [&](int k) -> bool {
@@ -162,21 +194,21 @@ size_t hawkes_workspace_size(int64_t n, int precision) {
 int hawkes_loglik(const double *x, const double *y, const double *t, const double *r, int64_t n,
                   const double params[6], int precision, void *ws, size_t ws_bytes,
                   double *loglik, int *dev_status, void *stream) {
-    return hk::run(x, y, t, r, n, params, precision, ws, ws_bytes, hk::MODE_LL, loglik, nullptr, nullptr,
+    return hk::run(x, y, t, r, n, params, nullptr, 0, precision, ws, ws_bytes, hk::MODE_LL, loglik, nullptr, nullptr,
                    dev_status, stream);
 }
 
 int hawkes_grad(const double *x, const double *y, const double *t, const double *r, int64_t n,
                 const double params[6], int precision, void *ws, size_t ws_bytes,
                 double *loglik, double *grad, int *dev_status, void *stream) {
-    return hk::run(x, y, t, r, n, params, precision, ws, ws_bytes, hk::MODE_GRAD, loglik, grad, nullptr,
+    return hk::run(x, y, t, r, n, params, nullptr, 0, precision, ws, ws_bytes, hk::MODE_GRAD, loglik, grad, nullptr,
                    dev_status, stream);
 }
 
 int hawkes_hess_diag(const double *x, const double *y, const double *t, const double *r, int64_t n,
                      const double params[6], int precision, void *ws, size_t ws_bytes,
                      double *loglik, double *grad, double *hdiag, int *dev_status, void *stream) {
-    return hk::run(x, y, t, r, n, params, precision, ws, ws_bytes, hk::MODE_HESS, loglik, grad, hdiag,
+    return hk::run(x, y, t, r, n, params, nullptr, 0, precision, ws, ws_bytes, hk::MODE_HESS, loglik, grad, hdiag,
                    dev_status, stream);
 }
 
@@ -184,8 +216,17 @@ int hawkes_hess_diag_timed(const double *x, const double *y, const double *t, co
                            const double params[6], int precision, void *ws, size_t ws_bytes,
                            double *loglik, double *grad, double *hdiag, int *dev_status, void *stream,
                            void *const phase_events[4]) {
-    return hk::run(x, y, t, r, n, params, precision, ws, ws_bytes, hk::MODE_HESS, loglik, grad, hdiag,
+    return hk::run(x, y, t, r, n, params, nullptr, 0, precision, ws, ws_bytes, hk::MODE_HESS, loglik, grad, hdiag,
                    dev_status, stream, phase_events);
+}
+
+int hawkes_eval_device_params(const double *x, const double *y, const double *t, const double *r, int64_t n,
+                              const double *params_dev, int log_params, int precision, int mode, void *ws,
+                              size_t ws_bytes, double *loglik, double *grad, double *hdiag, int *dev_status,
+                              void *stream) {
+    if (!params_dev) return HAWKES_EINVAL;
+    return hk::run(x, y, t, r, n, nullptr, params_dev, log_params, precision, ws, ws_bytes, mode, loglik, grad,
+                   hdiag, dev_status, stream);
 }
 
 const char *hawkes_strerror(int status) {

@@ -29,7 +29,7 @@ constexpr int ACC_STRIDE = 16;
 constexpr int MODE_LL = 0, MODE_GRAD = 1, MODE_HESS = 2;
 
 // device status bits (combined into a hawkes_status by finalize)
-constexpr int ST_UNSORTED = 1, ST_NONFINITE = 2, ST_ZERO = 4;
+constexpr int ST_UNSORTED = 1, ST_NONFINITE = 2, ST_ZERO = 4, ST_BADPARAM = 8;
 
 // log2(e) and the FP32C underflow threshold: an exponent (base 2) below this
 // gives exactly 0 from ex2.approx.ftz, so tiles whose bound lies below it are
@@ -51,20 +51,38 @@ struct Geometry {
 
 Geometry make_geometry(int64_t n);
 
-// Constants of one call (host-computed in FP64 and passed by value).
-struct Consts {
-    Geometry g;
-    int mode, fp32c, tt_inf;
+// Constants derived from the parameter vector.  setup_kernel computes them in
+// FP64 on the device, from host values or from device memory, and every other
+// kernel reads them from the workspace, so a call whose parameters live on the
+// device needs no host round trip.
+struct Derived {
     double mu0, tx, tt, th0, om, h;
     double A, B;          // lambda_n = A * sum G + B * sum E
     double sx, st;        // FP32C scaled coordinates: x~ = (x - xc) sx, t~ = (t - tc) st; 1 for FP64
-    float cbt, hh;        // FP32C: G = 2^-(d~^2 + cbt dt~^2), E = 2^(r~ - dt~ - hh d~^2)
     double ibx, ibt, ih;  // FP64:  G = exp(-ibx d^2 - ibt dt^2), E = exp(r - om dt - ih d^2)
+    float cbt, hh;        // FP32C: G = 2^-(d~^2 + cbt dt~^2), E = 2^(r^_s - t~_n - hh d~^2)
+    int tt_inf, valid;
+};
+
+// Per-call constants known on the host (passed by value to every kernel).
+struct Consts {
+    Geometry g;
+    int mode, fp32c;
+    const Derived *d;  // device: written by setup_kernel
+};
+
+// The parameter vector for setup_kernel: host values, or a device pointer
+// (optionally holding the logarithms of the parameters).
+struct ParamSource {
+    double v[6];
+    const double *dev;
+    int log_scale;
 };
 
 // Workspace carving.  Offsets are multiples of 256 bytes.
 struct Workspace {
     int *hdr;            // [0] status bits, [1] flagged rows, [2] ticket, [3] spare
+    Derived *derived;    // [1]  constants derived from the parameters
     double *centre;      // [4]: xc, yc, tc, tN
     int *hash;           // [hash_size]
     int *cnt;            // [npad]  members of each exact-location group (indexed by representative)
@@ -98,6 +116,7 @@ struct Outputs {
 };
 
 // launchers (return cudaGetLastError())
+cudaError_t launch_setup(const Consts &c, const ParamSource &ps, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_prep(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_pack(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_row32(const Consts &c, const Workspace &ws, cudaStream_t s);

@@ -44,6 +44,7 @@ __device__ __forceinline__ void col_tile(const float4 *sAB, const int *sG, int n
 
 template <int MODE>
 __global__ void __launch_bounds__(TILE, 4) col32_kernel(Consts c, Inputs in, Workspace ws) {
+    const Derived &D = *c.d;
     const int tile = blockIdx.x, chunk = blockIdx.y;
     const int m = tile * TILE + threadIdx.x;
     const int n = c.g.n, npad = c.g.npad;
@@ -58,12 +59,12 @@ __global__ void __launch_bounds__(TILE, 4) col32_kernel(Consts c, Inputs in, Wor
         ym = splat(-f[8 * p + 2 + l]);
         // r^_m = r~_m + t~_m, from the FP64 inputs (the packed slot now holds g^)
         float r = -1.0e9f;
-        if (m < n) r = (float)(in.r[m] * LOG2E + (in.t[m] - ws.centre[2]) * c.st);
+        if (m < n) r = (float)(in.r[m] * LOG2E + (in.t[m] - ws.centre[2]) * D.st);
         rm = splat(r);
     }
     const int4 tiM = ws.tinfo[tile];
     const float4 stM = ws.tstat32[tile];
-    const float2 nhh2 = splat(-c.hh);
+    const float2 nhh2 = splat(-D.hh);
     const int m_first = tile * TILE, m_last = m_first + tiM.w - 1;
 
     float2 run1 = make_float2(0.f, 0.f), run2 = make_float2(0.f, 0.f);

@@ -59,6 +59,7 @@ __device__ __forceinline__ double std_pdf(double z) { return 0.3989422804014327 
 __device__ __forceinline__ double std_cdf(double z) { return 0.5 * erfc(-z * 0.7071067811865476); }
 
 __global__ void __launch_bounds__(TILE) epilogue_kernel(Consts c, Inputs in, Workspace ws) {
+    const Derived &D = *c.d;
     __shared__ double sh[(TILE / 32) * NACC];
     __shared__ float shf[TILE];
     const int i = blockIdx.x * TILE + threadIdx.x;
@@ -72,22 +73,22 @@ __global__ void __launch_bounds__(TILE) epilogue_kernel(Consts c, Inputs in, Wor
     if (valid) {
         const int mode = c.mode;
         auto M = [&](int k) { return ws.mom[(size_t)k * npad + i]; };
-        const double sx2 = c.sx * c.sx, st = c.st, st2 = c.st * c.st;
+        const double sx2 = D.sx * D.sx, st = D.st, st2 = D.st * D.st;
         const double SG = M(MO_G), SE = M(MO_E);
-        const double lam = c.A * SG + c.B * SE;
+        const double lam = D.A * SG + D.B * SE;
         double q1[6] = {0, 0, 0, 0, 0, 0}, q2[6] = {0, 0, 0, 0, 0, 0};
         double ll = 0.0;
         if (lam > 0.0) {
             ll = log(lam);
             if (mode >= MODE_GRAD) {
-                const double a = c.A / lam, b = c.B / lam;
+                const double a = D.A / lam, b = D.B / lam;
                 const double GD2 = M(MO_GD2) / sx2, GT2 = M(MO_GT2) / st2;
                 const double ET = M(MO_ET) / st, ED2 = M(MO_ED2) / sx2;
-                const double tx = c.tx, tt = c.tt, om = c.om, h = c.h;
-                q1[0] = a * SG / c.mu0;
+                const double tx = D.tx, tt = D.tt, om = D.om, h = D.h;
+                q1[0] = a * SG / D.mu0;
                 q1[1] = a * (GD2 / (tx * tx * tx) - 2.0 * SG / tx);
-                q1[2] = c.tt_inf ? 0.0 : a * (GT2 / (tt * tt * tt) - SG / tt);
-                q1[3] = b * SE / c.th0;
+                q1[2] = D.tt_inf ? 0.0 : a * (GT2 / (tt * tt * tt) - SG / tt);
+                q1[3] = b * SE / D.th0;
                 q1[4] = b * (SE / om - ET);
                 q1[5] = b * (ED2 / (h * h * h) - 2.0 * SE / h);
                 if (mode == MODE_HESS) {
@@ -97,22 +98,22 @@ __global__ void __launch_bounds__(TILE) epilogue_kernel(Consts c, Inputs in, Wor
                     double s2[6];
                     s2[0] = 0.0;
                     s2[1] = a * (GD4 / (tx2 * tx2 * tx2) - 7.0 * GD2 / (tx2 * tx2) + 6.0 * SG / tx2);
-                    s2[2] = c.tt_inf ? 0.0 : a * (GT4 / (tt2 * tt2 * tt2) - 5.0 * GT2 / (tt2 * tt2) + 2.0 * SG / tt2);
+                    s2[2] = D.tt_inf ? 0.0 : a * (GT4 / (tt2 * tt2 * tt2) - 5.0 * GT2 / (tt2 * tt2) + 2.0 * SG / tt2);
                     s2[3] = 0.0;
                     s2[4] = b * (ET2 - 2.0 * ET / om);
                     s2[5] = b * (ED4 / (h2 * h2 * h2) - 7.0 * ED2 / (h2 * h2) + 6.0 * SE / h2);
 #pragma unroll
                     for (int p = 0; p < 6; ++p) q2[p] = s2[p] - q1[p] * q1[p];
-                    if (c.tt_inf) q2[2] = 0.0;
+                    if (D.tt_inf) q2[2] = 0.0;
                 }
             }
             if (c.fp32c) {
                 // column weight g^ = log2(B / lambda_n) - t~_n (t~_n as packed)
                 const float *f = reinterpret_cast<const float *>(ws.src32);
                 const float tt_n = -f[8 * (i >> 1) + 4 + (i & 1)];
-                ghat = (float)(log2(c.B / lam) - (double)tt_n);
+                ghat = (float)(log2(D.B / lam) - (double)tt_n);
             } else {
-                ws.w64[i] = c.B / lam;
+                ws.w64[i] = D.B / lam;
             }
         } else {
             atomicOr(&ws.hdr[0], ST_ZERO);
@@ -127,24 +128,24 @@ __global__ void __launch_bounds__(TILE) epilogue_kernel(Consts c, Inputs in, Wor
         const double tN = ws.centre[3];
         const double ti = in.t[i], a_ = tN - ti, b_ = -ti;
         const double th = exp(in.r[i]);
-        const double dec = exp(-c.om * a_);
-        const double one_m = -expm1(-c.om * a_);
+        const double dec = exp(-D.om * a_);
+        const double one_m = -expm1(-D.om * a_);
         double L = 0.0, dL[6] = {0, 0, 0, 0, 0, 0}, d2L[6] = {0, 0, 0, 0, 0, 0};
-        if (c.tt_inf) {
+        if (D.tt_inf) {
             dL[0] = tN;
         } else {
-            const double tt = c.tt, za = a_ / tt, zb = b_ / tt;
+            const double tt = D.tt, za = a_ / tt, zb = b_ / tt;
             const double pa = std_pdf(za), pb = std_pdf(zb);
             dL[0] = std_cdf(za) - std_cdf(zb);
-            dL[2] = c.mu0 * (-(a_ / (tt * tt)) * pa + (b_ / (tt * tt)) * pb);
+            dL[2] = D.mu0 * (-(a_ / (tt * tt)) * pa + (b_ / (tt * tt)) * pb);
             const double tt3 = tt * tt * tt, tt5 = tt3 * tt * tt;
-            d2L[2] = c.mu0 * (pa * (2.0 * a_ / tt3 - a_ * a_ * a_ / tt5) - pb * (2.0 * b_ / tt3 - b_ * b_ * b_ / tt5));
+            d2L[2] = D.mu0 * (pa * (2.0 * a_ / tt3 - a_ * a_ * a_ / tt5) - pb * (2.0 * b_ / tt3 - b_ * b_ * b_ / tt5));
         }
-        L = c.mu0 * dL[0] + c.th0 * th * one_m;
+        L = D.mu0 * dL[0] + D.th0 * th * one_m;
         dL[3] = th * one_m;
-        dL[4] = c.th0 * th * a_ * dec;
-        d2L[4] = -c.th0 * th * a_ * a_ * dec;
-        ws.dLr[i] = c.th0 * th * one_m;
+        dL[4] = D.th0 * th * a_ * dec;
+        d2L[4] = -D.th0 * th * a_ * a_ * dec;
+        ws.dLr[i] = D.th0 * th * one_m;
 
         acc[0] = ll - L;
 #pragma unroll
@@ -172,6 +173,7 @@ cudaError_t launch_epilogue(const Consts &c, const Inputs &in, const Workspace &
 constexpr int FIN_THREADS = 256;
 
 __global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(Consts c, Workspace ws, Outputs out) {
+    const Derived &D = *c.d;
     __shared__ double sh[(FIN_THREADS / 32) * NACC];
     __shared__ double tot[NACC];
     const int tiles = c.g.tiles;
@@ -191,17 +193,18 @@ __global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(Consts c, Workspa
     if (threadIdx.x == 0) {
         const int bits = ws.hdr[0];
         int code = HAWKES_OK;
-        if (bits & ST_NONFINITE) code = HAWKES_ENONFINITE;
+        if (bits & ST_BADPARAM) code = HAWKES_EINVAL;
+        else if (bits & ST_NONFINITE) code = HAWKES_ENONFINITE;
         else if (bits & ST_UNSORTED) code = HAWKES_EUNSORTED;
         else if (bits & ST_ZERO) code = HAWKES_EZERO_INTENSITY;
         const double qnan = __longlong_as_double(0x7ff8000000000000LL);
         double ll = tot[0];
-        if (code == HAWKES_ENONFINITE || code == HAWKES_EUNSORTED) ll = qnan;
+        if (code == HAWKES_ENONFINITE || code == HAWKES_EUNSORTED || code == HAWKES_EINVAL) ll = qnan;
         else if (code == HAWKES_EZERO_INTENSITY) ll = -INFINITY;
         if (out.loglik) *out.loglik = ll;
         for (int p = 0; p < 6; ++p) {
             double g = tot[1 + p], hd = tot[7 + p];
-            if (p == 2 && c.tt_inf) { g = 0.0; hd = 0.0; }
+            if (p == 2 && D.tt_inf) { g = 0.0; hd = 0.0; }
             if (code != HAWKES_OK) { g = qnan; hd = qnan; }
             if (out.grad) out.grad[p] = g;
             if (out.hdiag) out.hdiag[p] = hd;

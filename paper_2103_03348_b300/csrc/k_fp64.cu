@@ -16,17 +16,17 @@ namespace hk {
 template <int MODE>
 __device__ __forceinline__ void accumulate64(double (&a)[NMOM], double xs, double ys, double ts, double rs,
                                              bool bg_on, bool ex_on, double xn, double yn, double tn,
-                                             const Consts &c) {
+                                             const Derived &D) {
     const double dx = xn - xs, dy = yn - ys, dt = tn - ts;
     const double d2 = dx * dx + dy * dy, dt2 = dt * dt;
     if (bg_on) {
-        const double g = exp(-c.ibx * d2 - c.ibt * dt2);
+        const double g = exp(-D.ibx * d2 - D.ibt * dt2);
         a[MO_G] += g;
         if (MODE >= MODE_GRAD) { a[MO_GD2] += g * d2; a[MO_GT2] += g * dt2; }
         if (MODE == MODE_HESS) { a[MO_GD4] += g * d2 * d2; a[MO_GT4] += g * dt2 * dt2; }
     }
     if (ex_on) {
-        const double e = exp(rs - c.om * dt - c.ih * d2);
+        const double e = exp(rs - D.om * dt - D.ih * d2);
         a[MO_E] += e;
         if (MODE >= MODE_GRAD) { a[MO_ET] += e * dt; a[MO_ED2] += e * d2; }
         if (MODE == MODE_HESS) { a[MO_ET2] += e * dt2; a[MO_ED4] += e * d2 * d2; }
@@ -35,6 +35,7 @@ __device__ __forceinline__ void accumulate64(double (&a)[NMOM], double xs, doubl
 
 template <int MODE>
 __global__ void __launch_bounds__(TILE) row64_kernel(Consts c, Workspace ws) {
+    const Derived &D = *c.d;
     const int tile = blockIdx.x, chunk = blockIdx.y;
     const int i = tile * TILE + threadIdx.x;
     const int npad = c.g.npad;
@@ -59,7 +60,7 @@ __global__ void __launch_bounds__(TILE) row64_kernel(Consts c, Workspace ws) {
         for (int j = 0; j < tiS.w; ++j) {
             const double4_32a src = sS[j];
             accumulate64<MODE>(a, src.x, src.y, src.z, src.w, sLoc[j] != locn, !none_causal && (s0 + j < gn),
-                               me.x, me.y, me.z, c);
+                               me.x, me.y, me.z, D);
         }
     }
 #pragma unroll
@@ -80,6 +81,7 @@ cudaError_t launch_row64(const Consts &c, const Workspace &ws, cudaStream_t s) {
 // Column pass in FP64: v_nm = (B / lambda_n) exp(r_m - omega (t_n - t_m) - d^2/(2h^2)).
 template <int MODE>
 __global__ void __launch_bounds__(TILE) col64_kernel(Consts c, Workspace ws) {
+    const Derived &D = *c.d;
     const int tile = blockIdx.x, chunk = blockIdx.y;
     const int m = tile * TILE + threadIdx.x;
     const int npad = c.g.npad;
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(TILE) col64_kernel(Consts c, Workspace ws) {
             if (m < sG[j]) {
                 const double4_32a t = sT[j];
                 const double dx = t.x - me.x, dy = t.y - me.y, dt = t.z - me.z;
-                const double v = sW[j] * exp(me.w - c.om * dt - c.ih * (dx * dx + dy * dy));
+                const double v = sW[j] * exp(me.w - D.om * dt - D.ih * (dx * dx + dy * dy));
                 c1 += v;
                 if (MODE == MODE_HESS) c2 += v * v;
             }
@@ -129,10 +131,11 @@ constexpr int FIX_THREADS = 256;
 constexpr int FIX_BLOCKS = 64;
 
 __global__ void __launch_bounds__(FIX_THREADS) fixup_kernel(Consts c, Inputs in, Workspace ws) {
+    const Derived &D = *c.d;
     __shared__ double sh[FIX_THREADS];
     const int nflag = ws.hdr[1];
     const int n = c.g.n, npad = c.g.npad;
-    const double sx2 = c.sx * c.sx, st = c.st, st2 = c.st * c.st;
+    const double sx2 = D.sx * D.sx, st = D.st, st2 = D.st * D.st;
     for (int e = blockIdx.x; e < nflag; e += gridDim.x) {
         const int i = ws.flagged[e];
         const double xn = in.x[i], yn = in.y[i], tn = in.t[i];
@@ -141,7 +144,7 @@ __global__ void __launch_bounds__(FIX_THREADS) fixup_kernel(Consts c, Inputs in,
 #pragma unroll
         for (int k = 0; k < NMOM; ++k) a[k] = 0.0;
         for (int j = threadIdx.x; j < n; j += FIX_THREADS)
-            accumulate64<MODE_HESS>(a, in.x[j], in.y[j], in.t[j], in.r[j], ws.loc[j] != locn, j < gn, xn, yn, tn, c);
+            accumulate64<MODE_HESS>(a, in.x[j], in.y[j], in.t[j], in.r[j], ws.loc[j] != locn, j < gn, xn, yn, tn, D);
         // raw units -> FP32C scaled units
         const double scale[NMOM] = {1.0, sx2, st2, sx2 * sx2, st2 * st2, 1.0, st, st2, sx2, sx2 * sx2};
 #pragma unroll

@@ -35,17 +35,17 @@ __global__ void __launch_bounds__(MV_THREADS) prec_matvec_kernel(int64_t m, cons
 }
 
 struct PostConsts {
-    double p[6];
     int kind[6];
     double a[6], b[6];
 };
 
 __global__ void __launch_bounds__(ASM_THREADS) posterior_assemble_kernel(
     int64_t m, PostConsts pc, const int *__restrict__ seq, const double *__restrict__ prec,
-    const double *__restrict__ rs, const double *__restrict__ w, const double *__restrict__ loglik,
+    const double *__restrict__ q, const double *__restrict__ w, const double *__restrict__ loglik,
     const double *__restrict__ grad, const double *__restrict__ hdiag, double *__restrict__ logpost,
     double *__restrict__ grad_q, double *__restrict__ hdiag_q) {
     __shared__ double sh[ASM_THREADS];
+    const double *rs = q + 6;  // the sequenced log-rates
     double quad = 0.0;
     for (int64_t j = threadIdx.x; j < m; j += ASM_THREADS) {
         const int i = seq[j];
@@ -56,8 +56,10 @@ __global__ void __launch_bounds__(ASM_THREADS) posterior_assemble_kernel(
     quad = block_sum<ASM_THREADS>(quad, sh);
     if (threadIdx.x == 0) {
         double lp = *loglik - 0.5 * quad;
+        bool ok = true;
         for (int k = 0; k < 6; ++k) {
-            const double p = pc.p[k], a = pc.a[k], b = pc.b[k];
+            const double p = exp(q[k]), a = pc.a[k], b = pc.b[k];
+            if (!isfinite(p) || !(p > 0.0)) ok = false;
             double lpr, d1, d2;
             if (pc.kind[k] == HAWKES_PRIOR_GAMMA) {
                 lpr = (a - 1.0) * log(p) - b * p;
@@ -73,7 +75,7 @@ __global__ void __launch_bounds__(ASM_THREADS) posterior_assemble_kernel(
             grad_q[k] = p * gk + 1.0;
             if (hdiag_q) hdiag_q[k] = p * gk + p * p * (hdiag[k] + d2);
         }
-        *logpost = lp;
+        *logpost = ok ? lp : -INFINITY;
     }
 }
 
@@ -118,21 +120,18 @@ extern "C" {
 
 size_t hawkes_posterior_workspace_size(int64_t m) { return m < 0 ? 0 : (size_t)(m > 0 ? m : 1) * sizeof(double); }
 
-int hawkes_posterior(int64_t n, int64_t m, const int *seq_idx, const double *prec, const double params[6],
-                     const hawkes_prior *prior, const double *q, const double *loglik, const double *grad,
-                     const double *hdiag, void *ws, size_t ws_bytes, double *logpost, double *grad_q,
-                     double *hdiag_q, void *stream) {
-    if (n < 2 || m < 0 || m > n || !params || !prior || !q || !loglik || !grad || !ws || !logpost || !grad_q)
+int hawkes_posterior(int64_t n, int64_t m, const int *seq_idx, const double *prec, const hawkes_prior *prior,
+                     const double *q, const double *loglik, const double *grad, const double *hdiag, void *ws,
+                     size_t ws_bytes, double *logpost, double *grad_q, double *hdiag_q, void *stream) {
+    if (n < 2 || m < 0 || m > n || !prior || !q || !loglik || !grad || !ws || !logpost || !grad_q)
         return HAWKES_EINVAL;
     if (m > 0 && (!seq_idx || !prec)) return HAWKES_EINVAL;
     if ((hdiag == nullptr) != (hdiag_q == nullptr)) return HAWKES_EINVAL;
     if (ws_bytes < hawkes_posterior_workspace_size(m)) return HAWKES_EWORKSPACE;
     hk::PostConsts pc;
     for (int k = 0; k < 6; ++k) {
-        if (!isfinite(params[k]) || !(params[k] > 0)) return HAWKES_EINVAL;
         if (prior->kind[k] != HAWKES_PRIOR_GAMMA && prior->kind[k] != HAWKES_PRIOR_INVGAMMA) return HAWKES_EINVAL;
         if (!(prior->a[k] > 0) || !(prior->b[k] >= 0)) return HAWKES_EINVAL;
-        pc.p[k] = params[k];
         pc.kind[k] = prior->kind[k];
         pc.a[k] = prior->a[k];
         pc.b[k] = prior->b[k];
@@ -145,7 +144,7 @@ int hawkes_posterior(int64_t n, int64_t m, const int *seq_idx, const double *pre
         hk::prec_matvec_kernel<<<blocks, hk::MV_THREADS, 0, s>>>(m, prec, rs, w);
         if (cudaGetLastError() != cudaSuccess) return HAWKES_ECUDA;
     }
-    hk::posterior_assemble_kernel<<<1, hk::ASM_THREADS, 0, s>>>(m, pc, seq_idx, prec, rs, w, loglik, grad, hdiag,
+    hk::posterior_assemble_kernel<<<1, hk::ASM_THREADS, 0, s>>>(m, pc, seq_idx, prec, q, w, loglik, grad, hdiag,
                                                                 logpost, grad_q, hdiag_q);
     return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
 }

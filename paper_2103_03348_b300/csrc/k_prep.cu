@@ -150,6 +150,7 @@ __global__ void __launch_bounds__(TILE) prep_kernel(Consts c, Inputs in, Workspa
 }
 
 __global__ void __launch_bounds__(TILE) pack_kernel(Consts c, Inputs in, Workspace ws) {
+    const Derived &D = *c.d;
     const int n = c.g.n;
     const int i = blockIdx.x * TILE + threadIdx.x;
     const bool valid = i < n;
@@ -165,9 +166,9 @@ __global__ void __launch_bounds__(TILE) pack_kernel(Consts c, Inputs in, Workspa
         if (valid) {
             // stored negated so that target - source is one packed add; the
             // fourth slot holds r^ = r~ + t~ (log-rate and time folded, base 2)
-            xs = -(float)((in.x[i] - xc) * c.sx);
-            ys = -(float)((in.y[i] - yc) * c.sx);
-            const double tsc = (in.t[i] - tc) * c.st;
+            xs = -(float)((in.x[i] - xc) * D.sx);
+            ys = -(float)((in.y[i] - yc) * D.sx);
+            const double tsc = (in.t[i] - tc) * D.st;
             ts = -(float)tsc;
             rs = (float)(in.r[i] * LOG2E + tsc);
             tmin = (float)tsc;

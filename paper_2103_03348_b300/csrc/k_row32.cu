@@ -99,6 +99,7 @@ __device__ __forceinline__ void row_tile(const float4 *sAB, const int *sLoc, int
 
 template <int MODE>
 __global__ void __launch_bounds__(TILE, 4) row32_kernel(Consts c, Workspace ws) {
+    const Derived &D = *c.d;
     const int tile = blockIdx.x, chunk = blockIdx.y;
     const int i = tile * TILE + threadIdx.x;
     const int npad = c.g.npad;
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(TILE, 4) row32_kernel(Consts c, Workspace ws) 
     }
     const int4 tiT = ws.tinfo[tile];
     const float4 stT = ws.tstat32[tile];
-    const float2 cbt2 = splat(c.cbt), nhh2 = splat(-c.hh);
+    const float2 cbt2 = splat(D.cbt), nhh2 = splat(-D.hh);
 
     float2 run[NMOM];
     float ks[NMOM], kc[NMOM];

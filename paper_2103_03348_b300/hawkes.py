@@ -62,6 +62,9 @@ def lib():
             L.hawkes_hess_diag.argtypes = common + [vp, vp, vp, ip, vp]
             L.hawkes_hess_diag.restype = ctypes.c_int
             L.hawkes_hess_diag_timed.argtypes = common + [vp, vp, vp, ip, vp, ctypes.POINTER(ctypes.c_void_p)]
+            L.hawkes_eval_device_params.argtypes = [vp, vp, vp, vp, i64, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                    vp, sz, vp, vp, vp, ip, vp]
+            L.hawkes_eval_device_params.restype = ctypes.c_int
             L.hawkes_hess_diag_timed.restype = ctypes.c_int
             L.hawkes_strerror.argtypes = [ctypes.c_int]
             L.hawkes_strerror.restype = ctypes.c_char_p
@@ -82,7 +85,7 @@ def workspace_size(n: int, precision="fp32c") -> int:
 def kernels_per_call(mode: str, precision="fp32c") -> int:
     """Number of kernels one call launches (memsets excluded)."""
     p = PRECISIONS[precision]
-    k = 6 + (1 if p == FP32C else 0)  # prep, pack, row, combine, [fixup], epilogue, finalize
+    k = 7 + (1 if p == FP32C else 0)  # setup, prep, pack, row, combine, [fixup], epilogue, finalize
     if mode in ("grad", "hess"):
         k += 2  # column pass, column finish
     return k
@@ -135,8 +138,14 @@ def _raise_status(code: int):
     raise HawkesError(code, strerror(code))
 
 
+MODES = {"loglik": 0, "grad": 1, "hess": 2}
+
+
 def _call(mode: str, x, y, t, r, params, precision="fp32c", stream=None, workspace=None, check=True, out=None,
-          phase_events=None):
+          phase_events=None, log_params=False):
+    """One evaluation.  params: a 6-sequence or CPU tensor (passed as a host
+    vector), or a CUDA float64 tensor whose first six entries are read on the
+    device (their logarithms when log_params) with no host round trip."""
     n = _check_events(x, y, t, r)
     p = PRECISIONS[precision]
     dev = t.device
@@ -153,6 +162,27 @@ def _call(mode: str, x, y, t, r, params, precision="fp32c", stream=None, workspa
     elif isinstance(stream, torch.cuda.Stream):
         stream = stream.cuda_stream
     L = lib()
+    if isinstance(params, torch.Tensor) and params.is_cuda:
+        if params.dtype != torch.float64 or not params.is_contiguous() or params.numel() < 6:
+            raise TypeError("device params must be a contiguous float64 CUDA tensor with at least 6 entries")
+        st_p = ctypes.c_void_p(out["status"].data_ptr())
+        ptrs = [ctypes.c_void_p(out[k].data_ptr()) if out.get(k) is not None else ctypes.c_void_p(0)
+                for k in ("loglik", "grad", "hdiag")]
+        if mode != "hess":
+            ptrs[2] = ctypes.c_void_p(0)
+        if mode == "loglik":
+            ptrs[1] = ctypes.c_void_p(0)
+        with torch.cuda.device(dev):
+            rc = L.hawkes_eval_device_params(
+                ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                ctypes.c_void_p(r.data_ptr()), ctypes.c_int64(n), ctypes.c_void_p(params.data_ptr()),
+                int(bool(log_params)), p, MODES[mode], ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()),
+                *ptrs, st_p, ctypes.c_void_p(int(stream)))
+        if rc != OK:
+            raise HawkesError(rc, strerror(rc))
+        if check:
+            _raise_status(int(out["status"].item()))
+        return out
     pa = _params_array(params)
     args = [ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(t.data_ptr()),
             ctypes.c_void_p(r.data_ptr()), ctypes.c_int64(n), pa, ctypes.c_int(p),

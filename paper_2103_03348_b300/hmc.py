@@ -3,11 +3,12 @@ posterior (Section 2.3).
 
 The state q = (log mu0, log tau_x, log tau_t, log theta0, log omega, log h,
 r_{s_1..s_M}) lives on the GPU.  Every leapfrog step runs the library's kernels:
-scatter of the sequenced log-rates, the fused likelihood gradient
-(hawkes_grad), the posterior assembly (priors, log-transform Jacobian,
-phylogenetic Brownian prior through its precision matrix) and the momentum and
-position updates.  Only the six global parameters cross to the host each step,
-because the likelihood takes them as a host vector.
+scatter of the sequenced log-rates, the fused likelihood gradient with the
+globals read from q on the device (hawkes_eval_device_params), the posterior
+assembly (priors, log-transform Jacobian, phylogenetic Brownian prior through
+its precision matrix) and the momentum and position updates.  Nothing crosses
+to the host inside a trajectory; each iteration reads back two energies for
+the accept step.
 
 Adaptation (Section 2.3.2): a diagonal mass matrix from the running average of
 max(-H_qq, floor) over Hessian-diagonal evaluations made every `mass_every`
@@ -71,7 +72,7 @@ def _lib():
         vp, i64, d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
         L.hawkes_posterior_workspace_size.argtypes = [i64]
         L.hawkes_posterior_workspace_size.restype = ctypes.c_size_t
-        L.hawkes_posterior.argtypes = [i64, i64, vp, vp, ctypes.POINTER(d), ctypes.POINTER(_Prior), vp, vp, vp, vp,
+        L.hawkes_posterior.argtypes = [i64, i64, vp, vp, ctypes.POINTER(_Prior), vp, vp, vp, vp,
                                        vp, ctypes.c_size_t, vp, vp, vp, vp]
         L.hawkes_posterior.restype = ctypes.c_int
         L.hawkes_hmc_scatter_rates.argtypes = [i64, vp, vp, vp, vp]
@@ -116,28 +117,24 @@ class Posterior:
         self.calls = {"grad": 0, "hess": 0}
 
     def evaluate(self, q, want_hess=False, out=None):
-        """Fill out = {'logpost', 'grad', ['hdiag']} (device tensors) at q; returns out."""
+        """Fill out = {'logpost', 'grad', ['hdiag']} (device tensors) at q; returns out.
+
+        Everything is enqueued on the current stream: the likelihood reads the
+        six globals from q on the device (as logarithms), so no value crosses to
+        the host.  A q outside the parameter space gives log pi = -inf (or NaN
+        through the likelihood's NaN outputs), which the sampler rejects."""
         L = _lib()
         stream = torch.cuda.current_stream(self.dev).cuda_stream
-        params = torch.exp(q[:6]).cpu().tolist()  # the likelihood takes the globals on the host
         if out is None:
             f64 = dict(dtype=torch.float64, device=self.dev)
             out = {"logpost": torch.empty((), **f64), "grad": torch.empty(self.dim, **f64),
                    "hdiag": torch.empty(self.dim, **f64)}
-        if not all(math.isfinite(v) and v > 0.0 for v in params):
-            # a divergent trajectory left the parameter space: zero density there
-            out["logpost"].fill_(-math.inf)
-            out["grad"].zero_()
-            out["valid"] = False
-            return out
-        out["valid"] = True
         _check(L.hawkes_hmc_scatter_rates(self.m, _ptr(self.seq), _ptr(q), _ptr(self.r), ctypes.c_void_p(stream)))
         mode = "hess" if want_hess else "grad"
-        hawkes._call(mode, self.x, self.y, self.t, self.r, params, self.precision, stream=stream, check=False,
-                     out=self.like)
+        hawkes._call(mode, self.x, self.y, self.t, self.r, q, self.precision, stream=stream, check=False,
+                     out=self.like, log_params=True)
         self.calls[mode] += 1
-        pa = (ctypes.c_double * 6)(*params)
-        _check(L.hawkes_posterior(self.n, self.m, _ptr(self.seq), _ptr(self.prec), pa, ctypes.byref(self.c_prior),
+        _check(L.hawkes_posterior(self.n, self.m, _ptr(self.seq), _ptr(self.prec), ctypes.byref(self.c_prior),
                                   _ptr(q), _ptr(self.like["loglik"]), _ptr(self.like["grad"]),
                                   _ptr(self.like["hdiag"]) if want_hess else ctypes.c_void_p(0),
                                   _ptr(self.ws), ctypes.c_size_t(self.ws.numel()), _ptr(out["logpost"]),
@@ -161,8 +158,6 @@ def leapfrog(post, q, p, g, eps, n_steps, minv, scratch):
     for step in range(n_steps):
         _check(L.hawkes_hmc_position(k, _ptr(q), _ptr(p), _ptr(minv), eps, s))
         ev = post.evaluate(q, out=scratch)
-        if not ev.get("valid", True):
-            break  # diverged: the caller rejects the proposal
         _check(L.hawkes_hmc_momentum(k, _ptr(p), _ptr(ev["grad"]), eps if step < n_steps - 1 else 0.5 * eps, s))
     return ev
 
@@ -225,7 +220,7 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
     q = q0.clone()
     p = torch.empty(dim, **f64)
     cur = post.evaluate(q, want_hess=True)
-    cur = {k: v.clone() for k, v in cur.items() if torch.is_tensor(v)}
+    cur = {k: v.clone() for k, v in cur.items()}
     mass = torch.clamp(-cur["hdiag"], min=mass_floor)
     n_mass = 1
     minv = 1.0 / mass
@@ -253,7 +248,7 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
         h0 = -cur["logpost"].item() + k0.item()
         lp1 = ev["logpost"].item()
         h1 = -lp1 + k1.item()
-        ok_num = ev.get("valid", True) and math.isfinite(lp1) and post.status() == hawkes.OK
+        ok_num = math.isfinite(lp1) and post.status() == hawkes.OK
         a = min(1.0, math.exp(min(0.0, h0 - h1))) if ok_num and math.isfinite(h1) else 0.0
         accepted = rng.uniform() < a
         if accepted:
@@ -287,7 +282,8 @@ def ess(x) -> float:
     """Geyer's initial monotone sequence estimate of the effective sample size of a 1-D chain.
 
     Autocovariances through the FFT; tau = -1 + 2 sum_m Gamma_m, Gamma_m =
-    rho_2m + rho_2m+1 summed while positive and made non-increasing."""
+    rho_2m + rho_2m+1 summed while positive and made non-increasing; tau is kept
+    at or above 1/log10(n), so the ESS never exceeds n log10(n)."""
     x = np.asarray(x, float)
     n = len(x)
     if n < 4 or np.var(x) == 0:
@@ -304,7 +300,7 @@ def ess(x) -> float:
         gm = min(gm, prev)
         tau += 2.0 * gm
         prev = gm
-    return float(n / max(tau, 1e-12))
+    return float(n / max(tau, 1.0 / math.log10(n)))
 
 
 def ess_all(draws) -> np.ndarray:
