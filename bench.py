@@ -11,6 +11,7 @@ It prints one JSON line:
             x, y, t, r from pinned host memory and reads loglik, gradient and Hessian back
   roofline  the row pass (dominant kernel) against the FP32 pipe (ALU bound)
   cpu_baseline  the FP64 oracle on this host's cores, on a bounded sample of rows
+  hmc       ESS/s of a short preconditioned HMC chain on the 23,422-event workload
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -319,6 +320,16 @@ def run_ours(args, rank, world, local_rank):
         if i > 0:
             fp64_ms.append(ev[0].elapsed_time(ev[1]))
 
+    # HMC ESS/s: a short preconditioned chain on the 23,422-event workload with
+    # 1,610 free log-rates (the full 2,000-iteration run is run_hmc's job)
+    hmc_summary = None
+    if not args.no_hmc:
+        from paper_2103_03348_b300 import run_hmc
+        h = run_hmc.run("fp32c", iters=args.hmc_iters, warmup=args.hmc_warmup, device=str(dev))
+        hmc_summary = {k: h[k] for k in ("workload", "n_events", "n_rates", "iters", "warmup", "leapfrog_steps",
+                                         "accept_rate", "sampling_seconds", "ms_per_gradient",
+                                         "ess_globals", "ess_rates", "ess_per_s_globals", "ess_per_s_rates")}
+
     if rank != 0:
         return 0
 
@@ -361,6 +372,7 @@ def run_ours(args, rank, world, local_rank):
         "fp64_gpu_path": {"ms_per_step": float(np.mean(fp64_ms)),
                           "speedup_fp32c_over_fp64": float(np.mean(fp64_ms)) / ms},
         "wall_s_timed_region": wall,
+        "hmc": hmc_summary,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -373,6 +385,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-hmc", action="store_true", help="skip the short HMC chain (ESS/s)")
+    ap.add_argument("--hmc-iters", type=int, default=300)
+    ap.add_argument("--hmc-warmup", type=int, default=100)
     ap.add_argument("--kernel-only", action="store_true",
                     help="time the resident-input steps only (no e2e, FP64 path or CPU baseline); for profilers")
     args = ap.parse_args()

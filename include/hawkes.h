@@ -111,8 +111,12 @@ int hawkes_hess_diag(const double *x, const double *y, const double *t, const do
                      const double params[6], int precision, void *ws, size_t ws_bytes,
                      double *loglik, double *grad, double *hdiag, int *dev_status, void *stream);
 
-/* Mode of hawkes_eval_device_params. */
-enum { HAWKES_MODE_LOGLIK = 0, HAWKES_MODE_GRAD = 1, HAWKES_MODE_HESS = 2 };
+/* Mode of hawkes_eval_device_params.  The GLOBALS modes compute the loglik
+ * and the six global entries of the gradient (and Hessian diagonal) only,
+ * skipping the column pass: entries [6..6+n) of grad/hdiag are left as they
+ * were.  They serve callers that keep the log-rates fixed. */
+enum { HAWKES_MODE_LOGLIK = 0, HAWKES_MODE_GRAD = 1, HAWKES_MODE_HESS = 2,
+       HAWKES_MODE_GRAD_GLOBALS = 3, HAWKES_MODE_HESS_GLOBALS = 4 };
 
 /* The three evaluations with the parameter vector in DEVICE memory, so that a
  * caller whose parameters are produced on the GPU (a sampler's state) needs no
@@ -120,7 +124,7 @@ enum { HAWKES_MODE_LOGLIK = 0, HAWKES_MODE_GRAD = 1, HAWKES_MODE_HESS = 2 };
  * usual order; with log_params != 0 it holds their logarithms (the first six
  * sampler coordinates).  mode selects loglik / + grad / + hdiag exactly as
  * hawkes_loglik / hawkes_grad / hawkes_hess_diag (loglik is required for
- * mode 0, grad for mode 1, hdiag for mode 2).  Parameters that are not finite
+ * mode 0, grad for modes 1 and 3, hdiag for modes 2 and 4).  Parameters that are not finite
  * and positive are found on the GPU: *dev_status = HAWKES_EINVAL and every
  * output is NaN. */
 int hawkes_eval_device_params(const double *x, const double *y, const double *t, const double *r, int64_t n,
@@ -173,7 +177,8 @@ size_t hawkes_posterior_workspace_size(int64_t m);
  * A q whose p is not finite and positive gives log pi = -inf.
  *   ws          DEVICE workspace of hawkes_posterior_workspace_size(m) bytes
  *   logpost     DEVICE double[1]; grad_q, hdiag_q DEVICE double[6+m]
- *               (hdiag_q NULL exactly when hdiag is NULL)
+ *               (grad_q NULL exactly when grad is NULL: then only log pi is
+ *               computed; hdiag_q NULL exactly when hdiag is NULL)
  * Enqueued on stream; returns HAWKES_EINVAL for bad arguments. */
 int hawkes_posterior(int64_t n, int64_t m, const int *seq_idx, const double *prec,
                      const hawkes_prior *prior, const double *q, const double *loglik, const double *grad,
@@ -192,6 +197,38 @@ int hawkes_hmc_scatter_rates(int64_t m, const int *seq_idx, const double *q, dou
 int hawkes_hmc_momentum(int64_t k, double *p, const double *g, double a, void *stream);
 int hawkes_hmc_position(int64_t k, double *q, const double *p, const double *minv, double eps, void *stream);
 int hawkes_hmc_kinetic(int64_t k, const double *p, const double *minv, double *out, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Learned gradient surrogate (the paper has none; the learned part of this
+ * library): a 6 -> 128 -> 128 -> 6 tanh MLP with BF16 weights and FP32
+ * accumulation, mapping standardised log-globals to the standardised gradient
+ * of the log posterior, trained by these calls and used inside HMC leapfrog
+ * trajectories while the exact likelihood keeps the accept step.
+ * Weights: one vector of hawkes_mlp_param_count() values laid out as
+ * W1[128x6], b1[128], W2[128x128], b2[128], W3[6x128], b3[6] (row-major, rows
+ * are outputs).  BF16 arrays are uint16 bit patterns; all pointers DEVICE.
+ * ------------------------------------------------------------------------ */
+size_t hawkes_mlp_param_count(void);
+/* DEVICE workspace bytes for hawkes_mlp_loss_grad with this batch size. */
+size_t hawkes_mlp_workspace_size(int64_t batch);
+/* y[batch x 6] = MLP(x[batch x 6]). */
+int hawkes_mlp_forward(const void *w_bf16, const float *x, int64_t batch, float *y, void *stream);
+/* Mean squared error over batch x 6 outputs and its gradient w.r.t. every
+ * weight (FP32, summed over the batch's 32-sample blocks in a fixed order). */
+int hawkes_mlp_loss_grad(const void *w_bf16, const float *x, const float *target, int64_t batch, void *ws,
+                         size_t ws_bytes, float *grad, float *loss, void *stream);
+/* One Adam step (bias-corrected, step >= 1) on the FP32 master weights and
+ * moments m, v; refreshes the BF16 copy (round to nearest even). */
+int hawkes_mlp_adam(float *w_master, void *w_bf16, float *m, float *v, const float *grad, float lr, float beta1,
+                    float beta2, float eps, int step, void *stream);
+/* Surrogate gradient at one sampler state q[0..5] and, when p is not NULL, the
+ * leapfrog momentum update p[0..5] += a * g, with
+ *   g = mean_g + A (q - mean_q) + sd_g * MLP((q - mean_q) / sd_q):
+ * a linear model of the gradient plus the network's standardised residual.
+ * norm = [mean_q(6), sd_q(6), mean_g(6), sd_g(6), A(6x6, row-major)] (DEVICE
+ * doubles); g_out (DEVICE double[6]) receives g when not NULL. */
+int hawkes_surrogate_momentum(const void *w_bf16, const double *q, double *p, double a, const double *norm,
+                              double *g_out, void *stream);
 
 /* Largest n accepted by hawkes_hess_diag_noalloc. */
 #define HAWKES_NOALLOC_MAX_EVENTS 4096

@@ -125,7 +125,11 @@ static int run(const double *x, const double *y, const double *t, const double *
                void *const *events = nullptr) {
     if (n < 2 || n > HAWKES_MAX_EVENTS) return HAWKES_EINVAL;
     if (precision != HAWKES_FP64 && precision != HAWKES_FP32C) return HAWKES_EINVAL;
-    if (mode != MODE_LL && mode != MODE_GRAD && mode != MODE_HESS) return HAWKES_EINVAL;
+    // modes 3 and 4: gradient / Hessian diagonal of the six globals only (no column pass)
+    if (mode < 0 || mode > 4) return HAWKES_EINVAL;
+    const bool rates = mode == MODE_GRAD || mode == MODE_HESS;
+    if (mode == 3) mode = MODE_GRAD;
+    if (mode == 4) mode = MODE_HESS;
     if (!x || !y || !t || !r || !(params || params_dev) || !wsp || !dev_status) return HAWKES_EINVAL;
     if (mode == MODE_LL && !loglik) return HAWKES_EINVAL;
     if (mode == MODE_GRAD && !grad) return HAWKES_EINVAL;
@@ -171,7 +175,7 @@ static int run(const double *x, const double *y, const double *t, const double *
     if (c.fp32c && launch_fixup(c, in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
     if (launch_epilogue(c, in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
     if (launch_finalize(c, ws, out, s) != cudaSuccess) return HAWKES_ECUDA;
-    if (mode >= MODE_GRAD) {
+    if (mode >= MODE_GRAD && rates) {
         if (!mark(2)) return HAWKES_ECUDA;
         if ((c.fp32c ? launch_col32(c, in, ws, s) : launch_col64(c, ws, s)) != cudaSuccess) return HAWKES_ECUDA;
         if (!mark(3)) return HAWKES_ECUDA;

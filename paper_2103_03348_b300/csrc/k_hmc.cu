@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(ASM_THREADS) posterior_assemble_kernel(
     double quad = 0.0;
     for (int64_t j = threadIdx.x; j < m; j += ASM_THREADS) {
         const int i = seq[j];
-        grad_q[6 + j] = grad[6 + i] - w[j];
+        if (grad_q) grad_q[6 + j] = grad[6 + i] - w[j];
         if (hdiag_q) hdiag_q[6 + j] = hdiag[6 + i] - prec[(size_t)j * m + j];
         quad += rs[j] * w[j];
     }
@@ -70,10 +70,12 @@ __global__ void __launch_bounds__(ASM_THREADS) posterior_assemble_kernel(
                 d1 = -(a + 1.0) / p + b / (p * p);
                 d2 = (a + 1.0) / (p * p) - 2.0 * b / (p * p * p);
             }
-            const double gk = grad[k] + d1;
             lp += lpr + log(p);
-            grad_q[k] = p * gk + 1.0;
-            if (hdiag_q) hdiag_q[k] = p * gk + p * p * (hdiag[k] + d2);
+            if (grad_q) {
+                const double gk = grad[k] + d1;
+                grad_q[k] = p * gk + 1.0;
+                if (hdiag_q) hdiag_q[k] = p * gk + p * p * (hdiag[k] + d2);
+            }
         }
         *logpost = ok ? lp : -INFINITY;
     }
@@ -123,10 +125,11 @@ size_t hawkes_posterior_workspace_size(int64_t m) { return m < 0 ? 0 : (size_t)(
 int hawkes_posterior(int64_t n, int64_t m, const int *seq_idx, const double *prec, const hawkes_prior *prior,
                      const double *q, const double *loglik, const double *grad, const double *hdiag, void *ws,
                      size_t ws_bytes, double *logpost, double *grad_q, double *hdiag_q, void *stream) {
-    if (n < 2 || m < 0 || m > n || !prior || !q || !loglik || !grad || !ws || !logpost || !grad_q)
-        return HAWKES_EINVAL;
+    if (n < 2 || m < 0 || m > n || !prior || !q || !loglik || !ws || !logpost) return HAWKES_EINVAL;
     if (m > 0 && (!seq_idx || !prec)) return HAWKES_EINVAL;
+    if ((grad == nullptr) != (grad_q == nullptr)) return HAWKES_EINVAL;
     if ((hdiag == nullptr) != (hdiag_q == nullptr)) return HAWKES_EINVAL;
+    if (hdiag && !grad) return HAWKES_EINVAL;
     if (ws_bytes < hawkes_posterior_workspace_size(m)) return HAWKES_EWORKSPACE;
     hk::PostConsts pc;
     for (int k = 0; k < 6; ++k) {

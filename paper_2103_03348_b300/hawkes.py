@@ -138,7 +138,7 @@ def _raise_status(code: int):
     raise HawkesError(code, strerror(code))
 
 
-MODES = {"loglik": 0, "grad": 1, "hess": 2}
+MODES = {"loglik": 0, "grad": 1, "hess": 2, "grad_globals": 3, "hess_globals": 4}
 
 
 def _call(mode: str, x, y, t, r, params, precision="fp32c", stream=None, workspace=None, check=True, out=None,
@@ -153,8 +153,8 @@ def _call(mode: str, x, y, t, r, params, precision="fp32c", stream=None, workspa
     if out is None:
         out = {
             "loglik": torch.empty((), dtype=torch.float64, device=dev),
-            "grad": torch.empty(6 + n, dtype=torch.float64, device=dev) if mode in ("grad", "hess") else None,
-            "hdiag": torch.empty(6 + n, dtype=torch.float64, device=dev) if mode == "hess" else None,
+            "grad": torch.empty(6 + n, dtype=torch.float64, device=dev) if mode != "loglik" else None,
+            "hdiag": torch.empty(6 + n, dtype=torch.float64, device=dev) if mode in ("hess", "hess_globals") else None,
             "status": torch.empty((), dtype=torch.int32, device=dev),
         }
     if stream is None:
@@ -168,7 +168,7 @@ def _call(mode: str, x, y, t, r, params, precision="fp32c", stream=None, workspa
         st_p = ctypes.c_void_p(out["status"].data_ptr())
         ptrs = [ctypes.c_void_p(out[k].data_ptr()) if out.get(k) is not None else ctypes.c_void_p(0)
                 for k in ("loglik", "grad", "hdiag")]
-        if mode != "hess":
+        if mode not in ("hess", "hess_globals"):
             ptrs[2] = ctypes.c_void_p(0)
         if mode == "loglik":
             ptrs[1] = ctypes.c_void_p(0)

@@ -130,10 +130,11 @@ class Posterior:
             out = {"logpost": torch.empty((), **f64), "grad": torch.empty(self.dim, **f64),
                    "hdiag": torch.empty(self.dim, **f64)}
         _check(L.hawkes_hmc_scatter_rates(self.m, _ptr(self.seq), _ptr(q), _ptr(self.r), ctypes.c_void_p(stream)))
-        mode = "hess" if want_hess else "grad"
+        # with no free log-rates the column pass is skipped (globals-only modes)
+        mode = ("hess" if want_hess else "grad") if self.m > 0 else ("hess_globals" if want_hess else "grad_globals")
         hawkes._call(mode, self.x, self.y, self.t, self.r, q, self.precision, stream=stream, check=False,
                      out=self.like, log_params=True)
-        self.calls[mode] += 1
+        self.calls["hess" if want_hess else "grad"] += 1
         _check(L.hawkes_posterior(self.n, self.m, _ptr(self.seq), _ptr(self.prec), ctypes.byref(self.c_prior),
                                   _ptr(q), _ptr(self.like["loglik"]), _ptr(self.like["grad"]),
                                   _ptr(self.like["hdiag"]) if want_hess else ctypes.c_void_p(0),
@@ -142,14 +143,31 @@ class Posterior:
                                   ctypes.c_void_p(stream)))
         return out
 
+    def logpost_only(self, q, out):
+        """out['logpost'] = log pi(q) from a log-likelihood-only pass (the exact
+        accept step of surrogate trajectories)."""
+        L = _lib()
+        stream = torch.cuda.current_stream(self.dev).cuda_stream
+        _check(L.hawkes_hmc_scatter_rates(self.m, _ptr(self.seq), _ptr(q), _ptr(self.r), ctypes.c_void_p(stream)))
+        hawkes._call("loglik", self.x, self.y, self.t, self.r, q, self.precision, stream=stream, check=False,
+                     out=self.like, log_params=True)
+        self.calls["loglik"] = self.calls.get("loglik", 0) + 1
+        _check(L.hawkes_posterior(self.n, self.m, _ptr(self.seq), _ptr(self.prec), ctypes.byref(self.c_prior),
+                                  _ptr(q), _ptr(self.like["loglik"]), ctypes.c_void_p(0), ctypes.c_void_p(0),
+                                  _ptr(self.ws), ctypes.c_size_t(self.ws.numel()), _ptr(out["logpost"]),
+                                  ctypes.c_void_p(0), ctypes.c_void_p(0), ctypes.c_void_p(stream)))
+        return out
+
     def status(self):
         return int(self.like["status"].item())
 
 
-def leapfrog(post, q, p, g, eps, n_steps, minv, scratch):
+def leapfrog(post, q, p, g, eps, n_steps, minv, scratch, record=None):
     """n_steps leapfrog steps from (q, p) with gradient g at q; updates q, p in place.
 
-    Returns the evaluation dict at the final position."""
+    record(q, grad), when given, sees every position of the trajectory with its
+    gradient (device tensors, valid until the next step).  Returns the
+    evaluation dict at the final position."""
     L = _lib()
     k = q.numel()
     s = ctypes.c_void_p(torch.cuda.current_stream(q.device).cuda_stream)
@@ -158,6 +176,8 @@ def leapfrog(post, q, p, g, eps, n_steps, minv, scratch):
     for step in range(n_steps):
         _check(L.hawkes_hmc_position(k, _ptr(q), _ptr(p), _ptr(minv), eps, s))
         ev = post.evaluate(q, out=scratch)
+        if record is not None:
+            record(q, ev["grad"])
         _check(L.hawkes_hmc_momentum(k, _ptr(p), _ptr(ev["grad"]), eps if step < n_steps - 1 else 0.5 * eps, s))
     return ev
 
@@ -204,13 +224,16 @@ class Chain:
     warmup_seconds: float
     grad_calls: int
     hess_calls: int
+    last_q: object = None      # device state at the end
+    mass_t: object = None      # device mass matrix at the end
 
 
 def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_every=100, target_accept=0.8,
-           mass_floor=1e-2, seed=0, keep=None):
+           mass_floor=1e-2, seed=0, keep=None, record=None):
     """Run n_warmup + n_iter HMC iterations from q0 (device tensor); returns a Chain.
 
-    keep: optional index array of coordinates to store (all by default)."""
+    keep: optional index array of coordinates to store (all by default);
+    record: optional callback given every leapfrog position and its gradient."""
     dev = q0.device
     gen = torch.Generator(device=dev)
     gen.manual_seed(seed)
@@ -243,7 +266,7 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
         p.mul_(torch.sqrt(mass))
         kinetic(p, minv, k0)
         qn = q.clone()
-        ev = leapfrog(post, qn, p, cur["grad"], eps, n_steps, minv, scratch)
+        ev = leapfrog(post, qn, p, cur["grad"], eps, n_steps, minv, scratch, record)
         kinetic(p, minv, k1)
         h0 = -cur["logpost"].item() + k0.item()
         lp1 = ev["logpost"].item()
@@ -273,9 +296,11 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
             aprob[j] = a
     torch.cuda.synchronize()
     t_end = time.perf_counter()
-    t_sample = t_sample if t_sample is not None else t_end
+    if t_sample is None:  # warm-up only: report the adapted step size
+        t_sample = t_end
+        eps = da.final() if n_warmup > 0 else eps
     return Chain(draws, lps, acc, aprob, eps, mass.cpu().numpy(), t_end - t_sample, t_sample - t_start,
-                 post.calls["grad"], post.calls["hess"])
+                 post.calls["grad"], post.calls["hess"], q, mass)
 
 
 def ess(x) -> float:

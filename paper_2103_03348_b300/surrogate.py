@@ -1,0 +1,307 @@
+"""Learned gradient surrogate for HMC over the six global parameters.
+
+A 6 -> 128 -> 128 -> 6 tanh MLP (BF16 weights, FP32 accumulation, trained by
+the library's own forward/backward and Adam kernels) learns the map from the
+log-globals q to the gradient of the log posterior, from (q, gradient) pairs
+that the exact kernel produces along exact HMC warm-up trajectories.  Sampling
+then integrates each leapfrog trajectory with the surrogate gradient (one fused
+kernel per step) and accepts with the exact log posterior at the end point
+(one log-likelihood pass).  A leapfrog map driven by any smooth vector field
+stays volume preserving and reversible, so the exact Metropolis step keeps
+the exact posterior invariant.  If the acceptance rate collapses the sampler
+falls back to exact gradients.
+
+Inputs and outputs are standardised with the training set's mean and standard
+deviation: g(q) = mean_g + sd_g * MLP((q - mean_q) / sd_q).
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import hawkes, hmc
+
+MI, MH, MO = 6, 128, 6
+
+
+def _lib():
+    L = hmc._lib()
+    if not getattr(L, "_mlp_typed", False):
+        vp, i64, f = ctypes.c_void_p, ctypes.c_int64, ctypes.c_float
+        L.hawkes_mlp_param_count.restype = ctypes.c_size_t
+        L.hawkes_mlp_workspace_size.argtypes = [i64]
+        L.hawkes_mlp_workspace_size.restype = ctypes.c_size_t
+        L.hawkes_mlp_forward.argtypes = [vp, vp, i64, vp, vp]
+        L.hawkes_mlp_loss_grad.argtypes = [vp, vp, vp, i64, vp, ctypes.c_size_t, vp, vp, vp]
+        L.hawkes_mlp_adam.argtypes = [vp, vp, vp, vp, vp, f, f, f, f, ctypes.c_int, vp]
+        L.hawkes_surrogate_momentum.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp, vp]
+        for fn in (L.hawkes_mlp_forward, L.hawkes_mlp_loss_grad, L.hawkes_mlp_adam, L.hawkes_surrogate_momentum):
+            fn.restype = ctypes.c_int
+        L._mlp_typed = True
+    return L
+
+
+_p = hmc._ptr
+_check = hmc._check
+
+
+def _stream(dev):
+    return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+
+class MLP:
+    """Weights (FP32 master + BF16 working copy) and Adam state on the device."""
+
+    def __init__(self, device="cuda", seed=0):
+        L = _lib()
+        self.dev = torch.device(device)
+        self.count = int(L.hawkes_mlp_param_count())
+        rng = np.random.default_rng(seed)
+        w = np.zeros(self.count, np.float32)
+        off = 0
+        for fan_out, fan_in in ((MH, MI), (MH, MH), (MO, MH)):
+            lim = math.sqrt(6.0 / (fan_in + fan_out))  # Glorot uniform, zero biases
+            w[off:off + fan_out * fan_in] = rng.uniform(-lim, lim, fan_out * fan_in)
+            off += fan_out * fan_in + fan_out
+        self.wm = torch.tensor(w, device=self.dev)
+        self.wb = self.wm.to(torch.bfloat16)
+        self.m = torch.zeros_like(self.wm)
+        self.v = torch.zeros_like(self.wm)
+        self.grad = torch.zeros_like(self.wm)
+        self.loss = torch.zeros((), dtype=torch.float32, device=self.dev)
+        self.step = 0
+
+    def loss_grad(self, x, y):
+        L = _lib()
+        ws = torch.empty(int(L.hawkes_mlp_workspace_size(x.shape[0])), dtype=torch.uint8, device=self.dev)
+        _check(L.hawkes_mlp_loss_grad(_p(self.wb), _p(x), _p(y), x.shape[0], _p(ws), ctypes.c_size_t(ws.numel()),
+                                      _p(self.grad), _p(self.loss), _stream(self.dev)))
+        return self.loss, self.grad
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        self.step += 1
+        _check(_lib().hawkes_mlp_adam(_p(self.wm), _p(self.wb), _p(self.m), _p(self.v), _p(self.grad), lr, beta1,
+                                      beta2, eps, self.step, _stream(self.dev)))
+
+    def forward(self, x):
+        y = torch.empty(x.shape[0], MO, dtype=torch.float32, device=self.dev)
+        _check(_lib().hawkes_mlp_forward(_p(self.wb), _p(x), x.shape[0], _p(y), _stream(self.dev)))
+        return y
+
+    def train(self, x, y, epochs=200, batch=256, lr=1e-3, seed=0):
+        """Minibatch Adam on the mean squared error; returns the per-epoch mean loss."""
+        n = x.shape[0]
+        ws = torch.empty(int(_lib().hawkes_mlp_workspace_size(batch)), dtype=torch.uint8, device=self.dev)
+        gen = torch.Generator(device=self.dev)
+        gen.manual_seed(seed)
+        history = []
+        L = _lib()
+        for ep in range(epochs):
+            perm = torch.randperm(n, generator=gen, device=self.dev)
+            tot = torch.zeros((), dtype=torch.float32, device=self.dev)
+            nb = 0
+            lr_ep = lr * 0.5 * (1.0 + math.cos(math.pi * ep / epochs))  # cosine decay
+            for s in range(0, n - batch + 1, batch):
+                idx = perm[s:s + batch]
+                xb, yb = x.index_select(0, idx), y.index_select(0, idx)
+                _check(L.hawkes_mlp_loss_grad(_p(self.wb), _p(xb), _p(yb), batch, _p(ws),
+                                              ctypes.c_size_t(ws.numel()), _p(self.grad), _p(self.loss),
+                                              _stream(self.dev)))
+                self.adam(max(lr_ep, 1e-5))
+                tot += self.loss
+                nb += 1
+            history.append(float(tot.item()) / max(nb, 1))
+        return history
+
+
+@dataclasses.dataclass
+class Surrogate:
+    mlp: MLP
+    norm: torch.Tensor  # [24] doubles: mean_q, sd_q, mean_g, sd_g
+
+    def gradient(self, q):
+        g = torch.empty(MO, dtype=torch.float64, device=q.device)
+        _check(_lib().hawkes_surrogate_momentum(_p(self.mlp.wb), _p(q), ctypes.c_void_p(0), 0.0, _p(self.norm),
+                                                _p(g), _stream(q.device)))
+        return g
+
+
+def fit(q_pairs, g_pairs, epochs=200, batch=256, lr=1e-3, seed=0, holdout=0.1):
+    """Train a surrogate on exact (q, gradient) pairs (device float64 [n, 6]).
+
+    The gradient is modelled as mean_g + A (q - mean_q) (least squares) plus the
+    MLP's standardised residual, so the network only learns what the linear
+    model misses (near the posterior mode the gradient is close to linear).
+    Returns (Surrogate, report); the report's holdout_rel_error is the relative
+    RMS error on held-out pairs, sqrt(sum ||pred - exact||^2 / sum ||exact||^2)."""
+    n = q_pairs.shape[0]
+    gen = torch.Generator(device=q_pairs.device)
+    gen.manual_seed(seed + 1)
+    perm = torch.randperm(n, generator=gen, device=q_pairs.device)
+    n_hold = max(1, int(holdout * n))
+    tr, ho = perm[n_hold:], perm[:n_hold]
+    qt, gt = q_pairs[tr], g_pairs[tr]
+    mq, sq = qt.mean(0), qt.std(0).clamp_min(1e-12)
+    mg = gt.mean(0)
+    # least-squares linear part (a 6 x 6 solve on the host)
+    dq = (qt - mq).cpu().numpy()
+    dg = (gt - mg).cpu().numpy()
+    A = np.linalg.lstsq(dq, dg, rcond=None)[0].T  # dg ~ dq A^T
+    A_t = torch.tensor(A, dtype=torch.float64, device=q_pairs.device)
+    resid = lambda q, g: g - mg - (q - mq) @ A_t.T  # noqa: E731
+    sg = resid(qt, gt).std(0).clamp_min(1e-12)
+    norm = torch.cat([mq, sq, mg, sg, A_t.reshape(-1)]).contiguous()
+    xs = ((q_pairs - mq) / sq).float().contiguous()
+    ys = (resid(q_pairs, g_pairs) / sg).float().contiguous()
+    mlp = MLP(q_pairs.device, seed)
+    t0 = time.perf_counter()
+    hist = mlp.train(xs[tr].contiguous(), ys[tr].contiguous(), epochs, min(batch, len(tr)), lr, seed)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    sur = Surrogate(mlp, norm)
+    qh = q_pairs[ho]
+    pred = mg + (qh - mq) @ A_t.T + mlp.forward(xs[ho].contiguous()).double() * sg
+    lin = mg + (qh - mq) @ A_t.T
+    return sur, {"train_pairs": int(len(tr)), "holdout_pairs": int(n_hold), "epochs": epochs,
+                 "train_seconds": train_s, "final_train_loss": hist[-1],
+                 "holdout_rel_error": relative_error(pred, g_pairs[ho]),
+                 "holdout_median_rel_error": median_rel_error(pred, g_pairs[ho]),
+                 "holdout_rel_error_linear_only": relative_error(lin, g_pairs[ho])}
+
+
+def relative_error(pred, exact):
+    """Relative RMS error: sqrt(sum ||pred - exact||^2 / sum ||exact||^2)."""
+    num = torch.sum((pred - exact) ** 2)
+    den = torch.sum(exact ** 2).clamp_min(1e-300)
+    return float(torch.sqrt(num / den).item())
+
+
+def median_rel_error(pred, exact):
+    """Median over pairs of ||pred - exact||, relative to the RMS of ||exact||:
+    robust to the few warm-up excursions whose gradients are huge."""
+    err = torch.linalg.vector_norm(pred - exact, dim=-1)
+    rms = torch.sqrt(torch.mean(torch.sum(exact ** 2, dim=-1))).clamp_min(1e-300)
+    return float((torch.median(err) / rms).item())
+
+
+def collect_pairs(post, q0, n_pairs, n_steps=20, eps0=0.02, mass_every=50, seed=0, target_accept=0.8,
+                  burn_iters=100):
+    """Exact HMC warm-up over the globals that records (q, gradient) at every
+    leapfrog step after the first `burn_iters` iterations (which move the chain
+    from its start to the posterior); returns (q_pairs, g_pairs, chain state)."""
+    dev = q0.device
+    dim = q0.numel()
+    n_iter = int(math.ceil(n_pairs / n_steps))
+    qs = torch.empty(n_iter * n_steps, dim, dtype=torch.float64, device=dev)
+    gs = torch.empty(n_iter * n_steps, dim, dtype=torch.float64, device=dev)
+    counter = [0]
+    skip = burn_iters * n_steps
+
+    def record(q, g):
+        i = counter[0] - skip
+        if 0 <= i < qs.shape[0]:
+            qs[i].copy_(q)
+            gs[i].copy_(g)
+        counter[0] += 1
+
+    ch = hmc.sample(post, q0, n_iter=0, n_warmup=n_iter + burn_iters, n_steps=n_steps, eps0=eps0,
+                    mass_every=mass_every, seed=seed, target_accept=target_accept, record=record)
+    k = min(max(counter[0] - skip, 0), qs.shape[0])
+    qs, gs = qs[:k], gs[:k]
+    # positions of divergent trajectories (early in the step-size adaptation)
+    # carry non-finite or huge gradients: keep finite pairs whose gradient norm
+    # is within 50x the median
+    ok = torch.isfinite(qs).all(1) & torch.isfinite(gs).all(1)
+    qs, gs = qs[ok], gs[ok]
+    gn = torch.linalg.vector_norm(gs, dim=1)
+    keep = gn <= 50.0 * torch.median(gn)
+    qs, gs = qs[keep][:n_pairs], gs[keep][:n_pairs]
+    return qs.contiguous(), gs.contiguous(), ch
+
+
+def surrogate_leapfrog(sur, q, p, eps, n_steps, minv):
+    """Leapfrog trajectory over the six globals driven by the surrogate gradient."""
+    L = _lib()
+    s = _stream(q.device)
+    w, nrm = _p(sur.mlp.wb), _p(sur.norm)
+    _check(L.hawkes_surrogate_momentum(w, _p(q), _p(p), 0.5 * eps, nrm, ctypes.c_void_p(0), s))
+    for step in range(n_steps):
+        _check(L.hawkes_hmc_position(q.numel(), _p(q), _p(p), _p(minv), eps, s))
+        _check(L.hawkes_surrogate_momentum(w, _p(q), _p(p), eps if step < n_steps - 1 else 0.5 * eps, nrm,
+                                           ctypes.c_void_p(0), s))
+
+
+@dataclasses.dataclass
+class SurrogateChain:
+    draws: np.ndarray
+    accept: np.ndarray
+    seconds: float
+    exact_loglik_calls: int
+    fell_back: bool
+    fallback_at: int
+    monitor_errors: list
+
+
+def sample(post, sur, q0, mass, eps, n_iter, n_steps=20, seed=0, monitor_every=100, fallback_window=50,
+           fallback_rate=0.2):
+    """Surrogate-trajectory HMC with the exact Metropolis accept.
+
+    Every `monitor_every` iterations the exact gradient at the current state
+    judges the surrogate (relative error).  If the acceptance rate over the last
+    `fallback_window` iterations drops below `fallback_rate`, the remaining
+    iterations use exact gradients."""
+    dev = q0.device
+    dim = q0.numel()
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    rng = np.random.default_rng(seed)
+    f64 = dict(dtype=torch.float64, device=dev)
+    q = q0.clone()
+    minv = 1.0 / mass
+    p = torch.empty(dim, **f64)
+    k0, k1 = torch.empty((), **f64), torch.empty((), **f64)
+    cur = {"logpost": torch.empty((), **f64)}
+    post.logpost_only(q, cur)
+    cand = {"logpost": torch.empty((), **f64)}
+    scratch = {"logpost": torch.empty((), **f64), "grad": torch.empty(dim, **f64), "hdiag": torch.empty(dim, **f64)}
+    draws = np.empty((n_iter, dim))
+    acc = np.zeros(n_iter, bool)
+    errors, fell_back, fb_at, calls = [], False, -1, 1
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for it in range(n_iter):
+        torch.randn(dim, generator=gen, out=p, dtype=torch.float64, device=dev)
+        p.mul_(torch.sqrt(mass))
+        hmc.kinetic(p, minv, k0)
+        qn = q.clone()
+        if fell_back:
+            g0 = post.evaluate(q, out=scratch)["grad"].clone()
+            ev = hmc.leapfrog(post, qn, p, g0, eps, n_steps, minv, scratch)
+            cand["logpost"].copy_(ev["logpost"])
+        else:
+            surrogate_leapfrog(sur, qn, p, eps, n_steps, minv)
+            post.logpost_only(qn, cand)
+            calls += 1
+        hmc.kinetic(p, minv, k1)
+        h0 = -cur["logpost"].item() + k0.item()
+        lp1 = cand["logpost"].item()
+        h1 = -lp1 + k1.item()
+        a = min(1.0, math.exp(min(0.0, h0 - h1))) if math.isfinite(lp1) and math.isfinite(h1) else 0.0
+        if rng.uniform() < a:
+            q = qn
+            cur["logpost"].copy_(cand["logpost"])
+            acc[it] = True
+        draws[it] = q.cpu().numpy()
+        if monitor_every and (it + 1) % monitor_every == 0 and not fell_back:
+            exact = post.evaluate(q, out=scratch)["grad"][:MO]
+            errors.append(relative_error(sur.gradient(q)[None], exact[None]))
+        if (not fell_back and it + 1 >= fallback_window
+                and acc[it + 1 - fallback_window:it + 1].mean() < fallback_rate):
+            fell_back, fb_at = True, it + 1
+    torch.cuda.synchronize()
+    return SurrogateChain(draws, acc, time.perf_counter() - t0, calls, fell_back, fb_at, errors)

@@ -219,7 +219,9 @@ def make_ebola_like(seed: int = 1001, n: int = 23422, m_seq: int = 1610, box: fl
     x, y, t = _hotspot_pattern(rng, n, box, t_max, n_hot, 0.0, 0.5, 0.1, 5.0)
     r = np.zeros(n)
     seq = rng.choice(n, min(m_seq, n), replace=False)
-    r[seq], cov = coalescent_brownian(rng, len(seq), return_cov=True)
+    cov = np.zeros((0, 0))
+    if len(seq):
+        r[seq], cov = coalescent_brownian(rng, len(seq), return_cov=True)
     mask = np.zeros(n, bool)
     mask[seq] = True
     params = (0.5, 20.0, 30.0, 0.5, 0.1, 5.0)

@@ -1,0 +1,137 @@
+"""Surrogate MLP kernels vs the FP64 oracle, training, and what the trained
+network gains over exact HMC."""
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as mo
+from paper_2103_03348_b300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# FP32 accumulation over dot products of up to 128 terms: relative error of a
+# few 1e-6 per output; held to 1e-4 on norms and 1e-3 per scaled element.
+MLP_NORM_TOL = 1e-4
+MLP_ELEM_TOL = 1e-3
+
+
+def mod():
+    from paper_2103_03348_b300 import build, surrogate
+    build.build()
+    return surrogate
+
+
+def weights(seed=0):
+    rng = np.random.default_rng(seed)
+    w32 = rng.normal(0, 0.2, mo.PARAM_COUNT).astype(np.float32)
+    wb = torch.tensor(w32, device="cuda").to(torch.bfloat16)
+    return w32, wb, wb.float().cpu().numpy().astype(np.float64)
+
+
+def scaled(a, b):
+    return np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-3 * np.abs(b).max()))
+
+
+@pytest.mark.parametrize("batch", [1, 31, 32, 33, 257])
+def test_forward_and_loss_grad_vs_oracle(batch):
+    S = mod()
+    _, wb, w64 = weights(1)
+    rng = np.random.default_rng(batch)
+    x = rng.normal(size=(batch, 6)).astype(np.float32)
+    t = rng.normal(size=(batch, 6)).astype(np.float32)
+    mlp = S.MLP("cuda")
+    mlp.wb = wb
+    xd, td = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
+    y = mlp.forward(xd).cpu().numpy()
+    y_ref, _ = mo.forward(w64, x.astype(np.float64))
+    assert scaled(y, y_ref) <= MLP_ELEM_TOL
+    loss, g = mlp.loss_grad(xd, td)
+    loss_ref, g_ref = mo.loss_grad(w64, x.astype(np.float64), t.astype(np.float64))
+    assert abs(loss.item() - loss_ref) <= 1e-5 * loss_ref
+    g = g.cpu().numpy()
+    assert np.linalg.norm(g - g_ref) <= MLP_NORM_TOL * np.linalg.norm(g_ref)
+    assert scaled(g, g_ref) <= MLP_ELEM_TOL
+
+
+def test_adam_step_vs_oracle():
+    S = mod()
+    w32, _, _ = weights(2)
+    rng = np.random.default_rng(5)
+    g = rng.normal(0, 1e-2, mo.PARAM_COUNT).astype(np.float32)
+    m0 = rng.normal(0, 1e-3, mo.PARAM_COUNT).astype(np.float32)
+    v0 = rng.uniform(0, 1e-4, mo.PARAM_COUNT).astype(np.float32)
+    mlp = S.MLP("cuda")
+    mlp.wm = torch.tensor(w32, device="cuda")
+    mlp.m, mlp.v = torch.tensor(m0, device="cuda"), torch.tensor(v0, device="cuda")
+    mlp.grad = torch.tensor(g, device="cuda")
+    mlp.step = 6
+    mlp.adam(1e-3)
+    w_ref, m_ref, v_ref = mo.adam_step(w32, m0, v0, g, 1e-3, 0.9, 0.999, 1e-8, 7)
+    wm = mlp.wm.cpu().numpy()
+    assert np.max(np.abs(wm - w_ref)) <= 1e-6 * np.abs(w_ref).max()
+    np.testing.assert_allclose(mlp.m.cpu().numpy(), m_ref, rtol=1e-5, atol=1e-9)
+    np.testing.assert_allclose(mlp.v.cpu().numpy(), v_ref, rtol=1e-5, atol=1e-12)
+    # the BF16 copy is the round-to-nearest-even image of the FP32 master
+    assert np.array_equal(mlp.wb.float().cpu().numpy(), mo.bf16_round(wm))
+
+
+def test_surrogate_gradient_kernel_vs_oracle():
+    S = mod()
+    _, wb, w64 = weights(3)
+    mlp = S.MLP("cuda")
+    mlp.wb = wb
+    rng = np.random.default_rng(9)
+    norm = np.concatenate([rng.normal(size=6), rng.uniform(0.5, 2, 6), rng.normal(size=6) * 100,
+                           rng.uniform(10, 1000, 6), rng.normal(size=36) * 50])
+    sur = S.Surrogate(mlp, torch.tensor(norm, device="cuda"))
+    q = rng.normal(size=6)
+    g = sur.gradient(torch.tensor(q, device="cuda")).cpu().numpy()
+    g_ref = mo.surrogate_gradient(w64, q, norm)
+    assert np.max(np.abs(g - g_ref) / (np.abs(norm[18:24]) + np.abs(g_ref))) <= 1e-5
+
+
+def test_training_learns_a_linear_gradient_field():
+    S = mod()
+    rng = np.random.default_rng(4)
+    A = rng.normal(size=(6, 6))
+    H = -(A @ A.T + 6 * np.eye(6))  # the gradient field of a Gaussian log density: g = H q
+    q = rng.normal(size=(4000, 6))
+    g = q @ H.T
+    qd, gd = torch.tensor(q, device="cuda"), torch.tensor(g, device="cuda")
+    sur, rep = S.fit(qd, gd, epochs=150, batch=256, lr=2e-3)
+    assert rep["holdout_rel_error"] < 0.02, rep
+
+
+def concentrated_posterior():
+    """The 23,422-event pattern with its log-rates fixed at 0: a posterior over
+    the six globals concentrated enough for a smooth surrogate."""
+    from paper_2103_03348_b300 import hmc
+    w = synth.make_ebola_like(m_seq=0)
+    d = lambda a: torch.tensor(np.asarray(a, float), dtype=torch.float64, device="cuda")  # noqa: E731
+    post = hmc.Posterior(d(w.x), d(w.y), d(w.t), d(w.r), torch.zeros(0, dtype=torch.int32, device="cuda"),
+                         torch.zeros(0, dtype=torch.float64, device="cuda"), hmc.prior_km_days(), "fp32c")
+    return w, post, d(np.log(w.params))
+
+
+def test_surrogate_hmc_gains_over_exact_hmc():
+    """What the trained network gains: from the same state, with the same mass
+    matrix and step size, surrogate trajectories (exact accept) reach the
+    effective samples of exact HMC with one exact log-likelihood pass per
+    iteration instead of one gradient pass per leapfrog step."""
+    S = mod()
+    from paper_2103_03348_b300 import hmc
+    w, post, q0 = concentrated_posterior()
+    qp, gp, warm = S.collect_pairs(post, q0, n_pairs=3000, n_steps=20, eps0=0.05, seed=1)
+    sur, rep = S.fit(qp, gp, epochs=200)
+    assert rep["holdout_median_rel_error"] < 0.1, rep
+    n_iter = 300
+    ch_s = S.sample(post, sur, warm.last_q, warm.mass_t, warm.eps, n_iter, n_steps=20, seed=2, monitor_every=100)
+    assert not ch_s.fell_back and ch_s.accept.mean() > 0.5
+    assert max(ch_s.monitor_errors) < 0.1  # the exact kernel judges the surrogate along the chain
+    ch_e = hmc.sample(post, warm.last_q, n_iter=n_iter, n_warmup=0, n_steps=20, eps0=warm.eps, seed=2,
+                      mass_every=10 ** 9)
+    ess_s = hmc.ess_all(ch_s.draws).min()
+    ess_e = hmc.ess_all(ch_e.draws).min()
+    calls_e = ch_e.grad_calls + ch_e.hess_calls
+    assert ess_s / ch_s.exact_loglik_calls > 5 * ess_e / calls_e, (ess_s, ch_s.exact_loglik_calls, ess_e, calls_e)
+    assert ess_s / ch_s.seconds > 2 * ess_e / ch_e.seconds, (ess_s, ch_s.seconds, ess_e, ch_e.seconds)
