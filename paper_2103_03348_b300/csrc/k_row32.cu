@@ -100,7 +100,12 @@ __device__ __forceinline__ void row_tile(const float4 *sAB, const int *sLoc, int
 template <int MODE>
 __global__ void __launch_bounds__(TILE, 4) row32_kernel(Consts c, Workspace ws) {
     const Derived &D = *c.d;
-    const int tile = blockIdx.x, chunk = blockIdx.y;
+    // Chunk order: blocks are dispatched y-major, so y = 0 takes the chunk that
+    // holds the tile itself, y = 1 the chunk before it, and so on, wrapping to
+    // the later (future, background-only) chunks last: the heavy blocks go
+    // first and the light ones fill the tail.
+    const int tile = blockIdx.x;
+    const int chunk = (tile / c.g.chunk_tiles - (int)blockIdx.y + c.g.n_chunks) % c.g.n_chunks;
     const int i = tile * TILE + threadIdx.x;
     const int npad = c.g.npad;
     __shared__ float4 sAB[2][TILE];
