@@ -35,6 +35,11 @@
  *                accumulated with compensated (two-level Kahan) FP32, rows
  *                finished, reduced and logged in FP64; rows whose FP32 sum is
  *                below 2^-60 are recomputed in FP64.
+ *                HAWKES_FP32C_BAND: FP32C that also skips the tile pairs whose
+ *                background terms all lie below 2^-130 because their time gap
+ *                exceeds the background's temporal Gaussian (Section 2.1 with a
+ *                finite tau_t).  Those terms are exactly 0 in FP32, so the results
+ *                equal HAWKES_FP32C's bit for bit; only the work is smaller.
  *   ws, ws_bytes DEVICE workspace owned by the caller, at least
  *                hawkes_workspace_size(n, precision) bytes, 256-byte aligned.
  *                The library allocates nothing.  Calls that may overlap on the
@@ -68,7 +73,7 @@
 extern "C" {
 #endif
 
-typedef enum { HAWKES_FP64 = 0, HAWKES_FP32C = 1 } hawkes_precision;
+typedef enum { HAWKES_FP64 = 0, HAWKES_FP32C = 1, HAWKES_FP32C_BAND = 2 } hawkes_precision;
 
 typedef enum {
     HAWKES_OK = 0,

@@ -51,7 +51,7 @@ size_t carve(void *base, const Geometry &g, int precision, Workspace *w) {
     w->gidx = (int *)take(np * sizeof(int));
     w->tinfo = (int4 *)take(nt * sizeof(int4));
     w->tbox = (double4_32a *)take(nt * sizeof(double4_32a));
-    const bool f32 = precision == HAWKES_FP32C;
+    const bool f32 = precision == HAWKES_FP32C || precision == HAWKES_FP32C_BAND;
     w->src32 = f32 ? (float4 *)take(np * sizeof(float4)) : nullptr;
     w->tstat32 = f32 ? (float4 *)take(nt * sizeof(float4)) : nullptr;
     w->sufmax = f32 ? (float *)take(nt * sizeof(float)) : nullptr;
@@ -124,7 +124,7 @@ static int run(const double *x, const double *y, const double *t, const double *
                size_t ws_bytes, int mode, double *loglik, double *grad, double *hdiag, int *dev_status, void *stream,
                void *const *events = nullptr) {
     if (n < 2 || n > HAWKES_MAX_EVENTS) return HAWKES_EINVAL;
-    if (precision != HAWKES_FP64 && precision != HAWKES_FP32C) return HAWKES_EINVAL;
+    if (precision != HAWKES_FP64 && precision != HAWKES_FP32C && precision != HAWKES_FP32C_BAND) return HAWKES_EINVAL;
     // modes 3 and 4: gradient / Hessian diagonal of the six globals only (no column pass)
     if (mode < 0 || mode > 4) return HAWKES_EINVAL;
     const bool rates = mode == MODE_GRAD || mode == MODE_HESS;
@@ -145,7 +145,8 @@ static int run(const double *x, const double *y, const double *t, const double *
     memset(&c, 0, sizeof(c));
     c.g = g;
     c.mode = mode;
-    c.fp32c = precision == HAWKES_FP32C;
+    c.fp32c = precision == HAWKES_FP32C || precision == HAWKES_FP32C_BAND;
+    c.band = precision == HAWKES_FP32C_BAND;
     c.d = ws.derived;
     ParamSource ps;
     memset(&ps, 0, sizeof(ps));
@@ -190,7 +191,7 @@ extern "C" {
 
 size_t hawkes_workspace_size(int64_t n, int precision) {
     if (n < 2 || n > HAWKES_MAX_EVENTS) return 0;
-    if (precision != HAWKES_FP64 && precision != HAWKES_FP32C) return 0;
+    if (precision != HAWKES_FP64 && precision != HAWKES_FP32C && precision != HAWKES_FP32C_BAND) return 0;
     hk::Workspace w;
     return hk::carve(nullptr, hk::make_geometry(n), precision, &w);
 }

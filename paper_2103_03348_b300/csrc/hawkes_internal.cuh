@@ -36,6 +36,9 @@ constexpr int ST_UNSORTED = 1, ST_NONFINITE = 2, ST_ZERO = 4, ST_BADPARAM = 8;
 // skipped without changing the FP32 result (2 units of margin for rounding).
 constexpr double LOG2E = 1.4426950408889634074;
 constexpr float EXP2_DEAD = -128.0f;
+// background band skipping: a tile pair whose time gap g has cbt g^2 above this
+// has every background term below 2^-130, i.e. exactly 0 in FP32
+constexpr float BG_DEAD = 130.0f;
 // rows whose FP32 background and excitation sums are both below 2^-60 are
 // recomputed in FP64 (terms below 2^-126 were flushed to zero in FP32)
 constexpr float TINY_ROW = 8.673617379884035e-19f;  // 2^-60
@@ -67,7 +70,7 @@ struct Derived {
 // Per-call constants known on the host (passed by value to every kernel).
 struct Consts {
     Geometry g;
-    int mode, fp32c;
+    int mode, fp32c, band;  // band: FP32C with exact background band skipping
     const Derived *d;  // device: written by setup_kernel
 };
 

@@ -14,6 +14,10 @@
 // lanes), merged after every tile into a Kahan-compensated FP32 sum per
 // moment; the chunk result is written in FP64 and chunks are combined in FP64.
 //
+// With band skipping (HAWKES_FP32C_BAND) a tile pair whose time gap g has
+// cbt g^2 > 130 has every background term below 2^-130, exactly 0 in FP32, and
+// its background work is skipped; results are unchanged bit for bit.
+//
 // Every source tile is classified for the whole block (no divergence):
 //   * excitation skipped when no source precedes any target (exact, by the
 //     tie-group index) or when 2^(max r^ - min t~) is below 2^-128, so every
@@ -37,7 +41,7 @@ struct RowTarget {
     int locn, gn;
 };
 
-template <int MODE, bool EXC, bool MASK>
+template <int MODE, bool BG, bool EXC, bool MASK>
 __device__ __forceinline__ void row_pair(const float4 A, const float4 B, int la, int lb, int si,
                                          const RowTarget &T, float2 cbt2, float2 nhh2, float2 (&run)[NMOM]) {
     // A = (-x0, -x1, -y0, -y1), B = (-t0, -t1, r^0, r^1)
@@ -47,23 +51,25 @@ __device__ __forceinline__ void row_pair(const float4 A, const float4 B, int la,
     float2 d2 = mul2(dx, dx);
     d2 = fma2(dy, dy, d2);
     const float2 dt2 = mul2(dt, dt);
-    const float2 q = fma2(dt2, cbt2, d2);
-    float2 gb = make_float2(ex2_ftz(-q.x), ex2_ftz(-q.y));
-    if (MASK) {
-        if (la == T.locn) gb.x = 0.0f;
-        if (lb == T.locn) gb.y = 0.0f;
-    }
-    run[MO_G] = add2(run[MO_G], gb);
-    if (MODE >= MODE_GRAD) {
-        run[MO_GD2] = fma2(gb, d2, run[MO_GD2]);
-        run[MO_GT2] = fma2(gb, dt2, run[MO_GT2]);
-    }
     float2 d4 = make_float2(0.0f, 0.0f);
-    if (MODE == MODE_HESS) {
-        d4 = mul2(d2, d2);
-        const float2 dt4 = mul2(dt2, dt2);
-        run[MO_GD4] = fma2(gb, d4, run[MO_GD4]);
-        run[MO_GT4] = fma2(gb, dt4, run[MO_GT4]);
+    if (MODE == MODE_HESS) d4 = mul2(d2, d2);
+    if (BG) {
+        const float2 q = fma2(dt2, cbt2, d2);
+        float2 gb = make_float2(ex2_ftz(-q.x), ex2_ftz(-q.y));
+        if (MASK) {
+            if (la == T.locn) gb.x = 0.0f;
+            if (lb == T.locn) gb.y = 0.0f;
+        }
+        run[MO_G] = add2(run[MO_G], gb);
+        if (MODE >= MODE_GRAD) {
+            run[MO_GD2] = fma2(gb, d2, run[MO_GD2]);
+            run[MO_GT2] = fma2(gb, dt2, run[MO_GT2]);
+        }
+        if (MODE == MODE_HESS) {
+            const float2 dt4 = mul2(dt2, dt2);
+            run[MO_GD4] = fma2(gb, d4, run[MO_GD4]);
+            run[MO_GT4] = fma2(gb, dt4, run[MO_GT4]);
+        }
     }
     if (EXC) {
         float2 ee = add2(make_float2(B.z, B.w), T.ntn);
@@ -85,19 +91,19 @@ __device__ __forceinline__ void row_pair(const float4 A, const float4 B, int la,
     }
 }
 
-template <int MODE, bool EXC, bool MASK>
+template <int MODE, bool BG, bool EXC, bool MASK>
 __device__ __forceinline__ void row_tile(const float4 *sAB, const int *sLoc, int s0, int npairs,
                                          const RowTarget &T, float2 cbt2, float2 nhh2, float2 (&run)[NMOM]) {
 #pragma unroll 4
     for (int p = 0; p < npairs; ++p) {
         const float4 A = sAB[2 * p], B = sAB[2 * p + 1];
         int la = 0, lb = 0;
-        if (MASK) { la = sLoc[2 * p]; lb = sLoc[2 * p + 1]; }
-        row_pair<MODE, EXC, MASK>(A, B, la, lb, s0 + 2 * p, T, cbt2, nhh2, run);
+        if (MASK && BG) { la = sLoc[2 * p]; lb = sLoc[2 * p + 1]; }
+        row_pair<MODE, BG, EXC, MASK>(A, B, la, lb, s0 + 2 * p, T, cbt2, nhh2, run);
     }
 }
 
-template <int MODE>
+template <int MODE, bool BAND>
 __global__ void __launch_bounds__(TILE, 4) row32_kernel(Consts c, Workspace ws) {
     const Derived &D = *c.d;
     // Chunk order: blocks are dispatched y-major, so y = 0 takes the chunk that
@@ -151,13 +157,24 @@ __global__ void __launch_bounds__(TILE, 4) row32_kernel(Consts c, Workspace ws) 
         const bool none_causal = s0 >= tiT.y;                // no source precedes any target
         const bool all_causal = s0 + tiS.w - 1 < tiT.x;      // every source precedes every target
         const bool exc = !none_causal && (stS.z - stT.x >= EXP2_DEAD);
-        const bool mask = (s == tile) || (tiT.z && tiS.z) || (exc && !all_causal);
-        if (exc) {
-            if (mask) row_tile<MODE, true, true>(sAB[buf], sLoc[buf], s0, npairs, T, cbt2, nhh2, run);
-            else row_tile<MODE, true, false>(sAB[buf], sLoc[buf], s0, npairs, T, cbt2, nhh2, run);
-        } else {
-            if (mask) row_tile<MODE, false, true>(sAB[buf], sLoc[buf], s0, npairs, T, cbt2, nhh2, run);
-            else row_tile<MODE, false, false>(sAB[buf], sLoc[buf], s0, npairs, T, cbt2, nhh2, run);
+        bool bg = true;
+        if (BAND) {
+            // every background term of the tile pair is below 2^-130 when the time gap is wide enough
+            const float gap = fmaxf(fmaxf(stS.x - stT.y, stT.x - stS.y), 0.0f);
+            bg = !(D.cbt * gap * gap > BG_DEAD);
+        }
+        if (bg) {
+            const bool mask = (s == tile) || (tiT.z && tiS.z) || (exc && !all_causal);
+            if (exc) {
+                if (mask) row_tile<MODE, true, true, true>(sAB[buf], sLoc[buf], s0, npairs, T, cbt2, nhh2, run);
+                else row_tile<MODE, true, true, false>(sAB[buf], sLoc[buf], s0, npairs, T, cbt2, nhh2, run);
+            } else {
+                if (mask) row_tile<MODE, true, false, true>(sAB[buf], sLoc[buf], s0, npairs, T, cbt2, nhh2, run);
+                else row_tile<MODE, true, false, false>(sAB[buf], sLoc[buf], s0, npairs, T, cbt2, nhh2, run);
+            }
+        } else if (exc) {
+            if (!all_causal) row_tile<MODE, false, true, true>(sAB[buf], sLoc[buf], s0, npairs, T, cbt2, nhh2, run);
+            else row_tile<MODE, false, true, false>(sAB[buf], sLoc[buf], s0, npairs, T, cbt2, nhh2, run);
         }
         // merge the tile's run into the compensated sums
 #pragma unroll
@@ -178,9 +195,15 @@ __global__ void __launch_bounds__(TILE, 4) row32_kernel(Consts c, Workspace ws) 
 
 cudaError_t launch_row32(const Consts &c, const Workspace &ws, cudaStream_t s) {
     const dim3 grid(c.g.tiles, c.g.n_chunks);
-    if (c.mode == MODE_HESS) row32_kernel<MODE_HESS><<<grid, TILE, 0, s>>>(c, ws);
-    else if (c.mode == MODE_GRAD) row32_kernel<MODE_GRAD><<<grid, TILE, 0, s>>>(c, ws);
-    else row32_kernel<MODE_LL><<<grid, TILE, 0, s>>>(c, ws);
+    if (c.band) {
+        if (c.mode == MODE_HESS) row32_kernel<MODE_HESS, true><<<grid, TILE, 0, s>>>(c, ws);
+        else if (c.mode == MODE_GRAD) row32_kernel<MODE_GRAD, true><<<grid, TILE, 0, s>>>(c, ws);
+        else row32_kernel<MODE_LL, true><<<grid, TILE, 0, s>>>(c, ws);
+    } else {
+        if (c.mode == MODE_HESS) row32_kernel<MODE_HESS, false><<<grid, TILE, 0, s>>>(c, ws);
+        else if (c.mode == MODE_GRAD) row32_kernel<MODE_GRAD, false><<<grid, TILE, 0, s>>>(c, ws);
+        else row32_kernel<MODE_LL, false><<<grid, TILE, 0, s>>>(c, ws);
+    }
     return cudaGetLastError();
 }
 

@@ -27,8 +27,9 @@ import torch
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libhawkes.so")
 
-FP64, FP32C = 0, 1
-PRECISIONS = {"fp64": FP64, "fp32c": FP32C, FP64: FP64, FP32C: FP32C}
+FP64, FP32C, FP32C_BAND = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32c": FP32C, "fp32c_band": FP32C_BAND, FP64: FP64, FP32C: FP32C,
+              FP32C_BAND: FP32C_BAND}
 
 OK, EINVAL, EUNSORTED, ENONFINITE, EWORKSPACE, ECUDA, EZERO, ESCRATCH = range(8)
 
@@ -85,7 +86,7 @@ def workspace_size(n: int, precision="fp32c") -> int:
 def kernels_per_call(mode: str, precision="fp32c") -> int:
     """Number of kernels one call launches (memsets excluded)."""
     p = PRECISIONS[precision]
-    k = 7 + (1 if p == FP32C else 0)  # setup, prep, pack, row, combine, [fixup], epilogue, finalize
+    k = 7 + (1 if p in (FP32C, FP32C_BAND) else 0)  # setup, prep, pack, row, combine, [fixup], epilogue, finalize
     if mode in ("grad", "hess"):
         k += 2  # column pass, column finish
     return k

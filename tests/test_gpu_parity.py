@@ -218,3 +218,23 @@ def test_large_fp32c_vs_fp64_path(large):
     assert rel(ll, ll64) <= 1e-5
     assert np.linalg.norm(g - g64) <= 1e-5 * np.linalg.norm(g64)
     assert np.linalg.norm(h - h64) <= 1e-4 * np.linalg.norm(h64)
+
+
+@pytest.mark.parametrize("name", ["ebola_like", "large"])
+def test_band_skipping_is_bitwise_identical(name):
+    """HAWKES_FP32C_BAND skips only tile pairs whose background terms are all
+    exactly 0 in FP32, so every output equals HAWKES_FP32C's bit for bit."""
+    w = synth.make(name)
+    a = gpu_eval(w, w.params, "fp32c")
+    b = gpu_eval(w, w.params, "fp32c_band")
+    assert a[0] == b[0]
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+def test_band_skipping_with_infinite_tau_t():
+    w = synth.make("unit_square")
+    p = np.array(w.params)
+    p[2] = math.inf
+    a = gpu_eval(w, p, "fp32c")
+    b = gpu_eval(w, p, "fp32c_band")
+    assert a[0] == b[0] and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
