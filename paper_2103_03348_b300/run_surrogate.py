@@ -24,12 +24,13 @@ import torch
 from . import build, hmc, surrogate, synth
 
 
-def run(n=500_000, pairs=20_000, iters=500, exact_iters=50, n_steps=20, seed=0, device="cuda", eps0=0.02):
+def run(n=500_000, pairs=20_000, iters=500, exact_iters=50, n_steps=20, seed=0, device="cuda", eps0=0.02,
+        precision="fp32c_band"):
     build.build()
     w = synth.make_surrogate(n=n)
     d = lambda a: torch.tensor(np.asarray(a, float), dtype=torch.float64, device=device)  # noqa: E731
     post = hmc.Posterior(d(w.x), d(w.y), d(w.t), d(w.r), torch.zeros(0, dtype=torch.int32, device=device),
-                         torch.zeros(0, dtype=torch.float64, device=device), hmc.prior_km_days(), "fp32c")
+                         torch.zeros(0, dtype=torch.float64, device=device), hmc.prior_km_days(), precision)
     q0 = d(np.log(w.params))
     t0 = time.perf_counter()
     qp, gp, warm = surrogate.collect_pairs(post, q0, n_pairs=pairs, n_steps=n_steps, eps0=eps0, seed=seed)
@@ -47,7 +48,7 @@ def run(n=500_000, pairs=20_000, iters=500, exact_iters=50, n_steps=20, seed=0, 
         return {"min": float(np.min(e)), "median": float(np.median(e)), "max": float(np.max(e))}
 
     return {
-        "workload": w.name, "n_events": w.n, "pairs_pair_interactions": w.n * (w.n - 1), "leapfrog_steps": n_steps,
+        "workload": w.name, "n_events": w.n, "precision": precision, "pairs_pair_interactions": w.n * (w.n - 1), "leapfrog_steps": n_steps,
         "warmup": {"pairs": int(qp.shape[0]), "seconds": t_warm, "step_size": warm.eps},
         "training": fit_rep,
         "surrogate_hmc": {"iters": iters, "accept_rate": float(ch_s.accept.mean()), "seconds": ch_s.seconds,
@@ -73,8 +74,9 @@ def main():
     ap.add_argument("--exact-iters", type=int, default=50)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--precision", default="fp32c_band", choices=["fp32c", "fp32c_band", "fp64"])
     a = ap.parse_args()
-    print(json.dumps(run(a.n, a.pairs, a.iters, a.exact_iters, a.steps, a.seed)), flush=True)
+    print(json.dumps(run(a.n, a.pairs, a.iters, a.exact_iters, a.steps, a.seed, precision=a.precision)), flush=True)
 
 
 if __name__ == "__main__":
