@@ -219,7 +219,6 @@ def profile_traffic():
 
 def run_ours(args, rank, world, local_rank):
     import torch
-    import torch.distributed as dist
     from paper_2103_03348_b300 import build, hawkes
 
     build.build()
@@ -242,9 +241,9 @@ def run_ours(args, rank, world, local_rank):
         hawkes._call("hess", x, y, t, r, w.params, "fp32c", stream=stream, check=False, out=out,
                      phase_events=ev[2:6] if timed else None)
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
+    from paper_2103_03348_b300 import replicas
+
+    barrier = replicas.barrier
 
     # correctness gate before timing
     step(False)
@@ -274,12 +273,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     barrier()
     wall = time.perf_counter() - wall0
-    ms = float(np.mean(step_ms))
-    if world > 1:
-        tmax = torch.tensor([ms], device=dev)
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        ms = float(tmax.item())
-    value = world * pairs / (ms * 1e-3)
+    value, ms = replicas.aggregate_throughput(pairs, float(np.mean(step_ms)), dev)
 
     if args.kernel_only:
         if rank == 0:
