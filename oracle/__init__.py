@@ -30,40 +30,57 @@ _lib = None
 NPAR = 6
 
 
-def build(force: bool = False) -> str:
-    """Compile the C oracle into oracle/_build/liboracle.so (idempotent)."""
-    os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
-        tmp = _SO + f".tmp{os.getpid()}"
+def build(force: bool = False, src: str = _SRC, so: str = _SO) -> str:
+    """Compile the C oracle (default: oracle/_build/liboracle.so; idempotent)."""
+    os.makedirs(os.path.dirname(so), exist_ok=True)
+    if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+        tmp = so + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
-               "-std=c99", "-Wall", "-o", tmp, _SRC, "-lm"]
+               "-std=c99", "-Wall", "-o", tmp, src, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _SO)
-    return _SO
+        os.replace(tmp, so)
+    return so
+
+
+def _typed(lib):
+    d = ctypes.POINTER(ctypes.c_double)
+    i64 = ctypes.c_int64
+    l64 = ctypes.POINTER(ctypes.c_int64)
+    lib.oracle_eval.argtypes = [i64, d, d, d, d, d, ctypes.c_int, d, d, d, d, d, ctypes.c_int]
+    lib.oracle_eval.restype = ctypes.c_int
+    lib.oracle_intensity.argtypes = [i64, d, d, d, d, d, i64, d, d, d, d, ctypes.c_int]
+    lib.oracle_intensity.restype = ctypes.c_int
+    lib.oracle_integral.argtypes = [i64, d, d, d]
+    lib.oracle_integral.restype = ctypes.c_double
+    lib.oracle_rows.argtypes = [i64, d, d, d, d, d, i64, l64, d, d, d, ctypes.c_int]
+    lib.oracle_rows.restype = ctypes.c_int
+    lib.oracle_rate_terms.argtypes = [i64, d, d, d, d, d, d, i64, l64, d, d, ctypes.c_int]
+    lib.oracle_rate_terms.restype = ctypes.c_int
+    lib.oracle_max_threads.argtypes = []
+    lib.oracle_max_threads.restype = ctypes.c_int
+    return lib
 
 
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            d = ctypes.POINTER(ctypes.c_double)
-            i64 = ctypes.c_int64
-            lib.oracle_eval.argtypes = [i64, d, d, d, d, d, ctypes.c_int, d, d, d, d, d, ctypes.c_int]
-            lib.oracle_eval.restype = ctypes.c_int
-            lib.oracle_intensity.argtypes = [i64, d, d, d, d, d, i64, d, d, d, d, ctypes.c_int]
-            lib.oracle_intensity.restype = ctypes.c_int
-            lib.oracle_integral.argtypes = [i64, d, d, d]
-            lib.oracle_integral.restype = ctypes.c_double
-            l64 = ctypes.POINTER(ctypes.c_int64)
-            lib.oracle_rows.argtypes = [i64, d, d, d, d, d, i64, l64, d, d, d, ctypes.c_int]
-            lib.oracle_rows.restype = ctypes.c_int
-            lib.oracle_rate_terms.argtypes = [i64, d, d, d, d, d, d, i64, l64, d, d, ctypes.c_int]
-            lib.oracle_rate_terms.restype = ctypes.c_int
-            lib.oracle_max_threads.argtypes = []
-            lib.oracle_max_threads.restype = ctypes.c_int
-            _lib = lib
+            _lib = _typed(ctypes.CDLL(build()))
     return _lib
+
+
+def load_variant(src_text: str, workdir: str):
+    """Compile a modified copy of the oracle's C source (for tests that plant a
+    mistake in the oracle) and return its library handle, to pass as lib=."""
+    src = os.path.join(workdir, "variant.c")
+    with open(src, "w") as f:
+        f.write(src_text)
+    return _typed(ctypes.CDLL(build(force=True, src=src, so=os.path.join(workdir, "libvariant.so"))))
+
+
+def source_text() -> str:
+    with open(_SRC) as f:
+        return f.read()
 
 
 def _p(a):
@@ -78,7 +95,7 @@ def max_threads() -> int:
     return int(_load().oracle_max_threads())
 
 
-def evaluate(x, y, t, r, params, want: int = 2, threads: int = 0):
+def evaluate(x, y, t, r, params, want: int = 2, threads: int = 0, lib=None):
     """Log-likelihood (want=0), + gradient (1), + Hessian diagonal (2).
 
     Returns a dict with ``loglik`` (float), ``grad`` and ``hdiag`` ([6+N] or
@@ -86,7 +103,7 @@ def evaluate(x, y, t, r, params, want: int = 2, threads: int = 0):
     ``status`` (0 ok, 1 when some lambda_n == 0).  ``threads=0`` uses OpenMP's
     default.  The result does not depend on the thread count.
     """
-    lib = _load()
+    lib = lib or _load()
     x, y, t, r, p = _arr(x), _arr(y), _arr(t), _arr(r), _arr(params)
     n = t.shape[0]
     ll = np.zeros(1)
@@ -117,9 +134,9 @@ def intensity(x, y, t, r, params, xq, yq, tq, threads: int = 0):
     return out
 
 
-def integral(t, r, params) -> float:
+def integral(t, r, params, lib=None) -> float:
     """The integral term Lambda alone (Appendix A Claim, background integrated exactly)."""
-    lib = _load()
+    lib = lib or _load()
     t, r, p = _arr(t), _arr(r), _arr(params)
     return float(lib.oracle_integral(t.shape[0], _p(t), _p(r), _p(p)))
 
