@@ -50,6 +50,9 @@ class Workload:
     params: np.ndarray  # float64 [6]
     sequenced: np.ndarray  # int64 indices of events whose log-rate is free
     tree_cov: np.ndarray = None  # [M, M] V of the sequenced events' tree (in `sequenced` order), or None
+    tree_parent: np.ndarray = None  # [2M-1] parent of each tree node (-1 at the root); nodes 0..M-1 are the
+    #                                 tips in `sequenced` order, internal nodes follow in merge order
+    tree_length: np.ndarray = None  # [2M-1] length of the branch above each node (0 at the root)
 
     @property
     def n(self) -> int:
@@ -132,7 +135,7 @@ def cluster_process(rng, n_immigrants, box, t_max, centres, sigma_hot, frac_unif
     return np.concatenate(xs), np.concatenate(ys), np.concatenate(ts)
 
 
-def coalescent_brownian(rng, m, sigma2=1.0, root_var=0.0, return_cov=False):
+def coalescent_brownian(rng, m, sigma2=1.0, root_var=0.0, return_cov=False, return_tree=False):
     """Tip values of Brownian motion down a random Kingman coalescent tree.
 
     Tips are contemporaneous.  While k lineages remain, the waiting time to the
@@ -172,6 +175,10 @@ def coalescent_brownian(rng, m, sigma2=1.0, root_var=0.0, return_cov=False):
         value[node] = value[parent[node]] + math.sqrt(sigma2 * bl) * rng.standard_normal()
     if not return_cov:
         return value[:m]
+    lengths = np.zeros(2 * m - 1)
+    for node in range(2 * m - 1):
+        if parent[node] >= 0:
+            lengths[node] = height[parent[node]] - height[node]
     # V from the tree: for every internal node, the pairs split by it share the
     # path from the root down to that node
     children = [[] for _ in range(2 * m - 1)]
@@ -189,6 +196,8 @@ def coalescent_brownian(rng, m, sigma2=1.0, root_var=0.0, return_cov=False):
         tips[node] = tips[a] + tips[b]
         tips[a] = tips[b] = None
     cov[np.arange(m), np.arange(m)] = root_var + height[root]
+    if return_tree:
+        return value[:m], cov, parent.copy(), lengths
     return value[:m], cov
 
 
@@ -220,8 +229,9 @@ def make_ebola_like(seed: int = 1001, n: int = 23422, m_seq: int = 1610, box: fl
     r = np.zeros(n)
     seq = rng.choice(n, min(m_seq, n), replace=False)
     cov = np.zeros((0, 0))
+    parent, lengths = np.zeros(0, np.int64), np.zeros(0)
     if len(seq):
-        r[seq], cov = coalescent_brownian(rng, len(seq), return_cov=True)
+        r[seq], cov, parent, lengths = coalescent_brownian(rng, len(seq), return_cov=True, return_tree=True)
     mask = np.zeros(n, bool)
     mask[seq] = True
     params = (0.5, 20.0, 30.0, 0.5, 0.1, 5.0)
@@ -232,6 +242,19 @@ def make_ebola_like(seed: int = 1001, n: int = 23422, m_seq: int = 1610, box: fl
     order = np.argsort(t, kind="stable")
     tips = tip_of[order[w.sequenced]]
     w.tree_cov = np.ascontiguousarray(cov[np.ix_(tips, tips)])
+    # the same tree with its tips renumbered in `sequenced` order
+    m = len(seq)
+    if m:
+        relabel = np.arange(2 * m - 1)
+        relabel[tips] = np.arange(m)  # old tip id -> new tip id
+        new_parent = np.full(2 * m - 1, -1, np.int64)
+        new_length = np.zeros(2 * m - 1)
+        for old_id in range(2 * m - 1):
+            nid = relabel[old_id]
+            pa = parent[old_id]
+            new_parent[nid] = relabel[pa] if pa >= 0 else -1
+            new_length[nid] = lengths[old_id]
+        w.tree_parent, w.tree_length = new_parent, new_length
     return w
 
 
