@@ -204,6 +204,60 @@ int hawkes_hmc_position(int64_t k, double *q, const double *p, const double *min
 int hawkes_hmc_kinetic(int64_t k, const double *p, const double *minv, double *out, void *stream);
 
 /* ------------------------------------------------------------------------
+ * The phylogenetic Brownian prior in O(M) (Section 2.2, Eq. 2; computed by
+ * message passing on the tree as in Section 2.3.1) instead of through a dense
+ * M x M precision.  z ~ N(0, sigma^2 V) with V_ij = root_var + (branch length
+ * from the root to the most recent common ancestor of tips i and j).
+ *
+ * Tree encoding: nodes 0..m-1 are the tips, in the order of z (tip j carries
+ * z_j, the log-rate of sequenced event j); nodes m..2m-2 are internal.  The
+ * HOST array parent[2m-1] gives each node's parent (-1 at the root, which must
+ * be an internal node); every internal node has exactly two children.
+ * length[2m-1] (DEVICE) holds each node's branch length to its parent (the
+ * root's entry is ignored).  Lengths must be non-negative and V positive
+ * definite; a singular V gives non-finite outputs.
+ * ------------------------------------------------------------------------ */
+#define HAWKES_TREE_MAX_TIPS (1 << 24)
+
+/* Bytes of the plan hawkes_tree_plan writes for m tips (0 if m is out of range). */
+size_t hawkes_tree_plan_size(int64_t m);
+
+/* Builds the traversal plan (children, and the internal nodes grouped by
+ * height so that each level depends only on lower ones) on the HOST from
+ * parent[].  plan is HOST memory of plan_bytes; copy it to the device for
+ * hawkes_tree_prior.  Returns HAWKES_EINVAL if parent[] is not a rooted binary
+ * tree on m tips (two roots, a cycle, a node with three children, a tip with
+ * children), HAWKES_EWORKSPACE if plan_bytes is too small.  Runs on the host
+ * only; O(m). */
+int hawkes_tree_plan(int64_t m, const int64_t *parent, int *plan, size_t plan_bytes);
+
+/* Bytes of DEVICE workspace hawkes_tree_prior needs for m tips. */
+size_t hawkes_tree_workspace_size(int64_t m);
+
+/* log N(z; 0, sigma^2 V) (Eq. 2) and its derivatives, in O(m) on one block:
+ *   plan      DEVICE copy of the hawkes_tree_plan output
+ *   length    DEVICE double[2m-1]; root_var >= 0 (the root's variance over sigma^2); sigma2 > 0
+ *   z         DEVICE double[m]
+ *   logdens   DEVICE double[1] or NULL: the log density, normalising constant included
+ *   pz        DEVICE double[m] or NULL: (sigma^2 V)^-1 z (minus the density's gradient in z)
+ *   pdiag     DEVICE double[m] or NULL: the diagonal of (sigma^2 V)^-1
+ * Enqueued on stream; HAWKES_EINVAL for bad scalars or NULL inputs. */
+int hawkes_tree_prior(int64_t m, const int *plan, const double *length, double root_var, double sigma2,
+                      const double *z, void *ws, size_t ws_bytes, double *logdens, double *pz, double *pdiag,
+                      void *stream);
+
+/* Bytes of DEVICE workspace hawkes_posterior_tree needs for m sequenced events. */
+size_t hawkes_posterior_tree_workspace_size(int64_t m);
+
+/* hawkes_posterior with the phylogenetic prior taken from the tree
+ * (P = (sigma^2 V)^-1 applied by hawkes_tree_prior) instead of a dense
+ * precision; same arguments and results otherwise, m >= 2. */
+int hawkes_posterior_tree(int64_t n, int64_t m, const int *seq_idx, const int *plan, const double *length,
+                          double root_var, double sigma2, const hawkes_prior *prior, const double *q,
+                          const double *loglik, const double *grad, const double *hdiag, void *ws,
+                          size_t ws_bytes, double *logpost, double *grad_q, double *hdiag_q, void *stream);
+
+/* ------------------------------------------------------------------------
  * Learned gradient surrogate (the paper has none; the learned part of this
  * library): a 6 -> 128 -> 128 -> 6 tanh MLP with BF16 weights and FP32
  * accumulation, mapping standardised log-globals to the standardised gradient

@@ -131,6 +131,9 @@ cudaError_t launch_finalize(const Consts &c, const Workspace &ws, const Outputs 
 cudaError_t launch_col32(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_col64(const Consts &c, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_colfinish(const Consts &c, const Workspace &ws, const Outputs &out, cudaStream_t s);
+cudaError_t launch_tree_prior(int64_t m, const int *plan, const double *len, double tau0, double sigma2,
+                              const double *z, double *scratch, double *logdens, double *pz, double *pdiag,
+                              cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // device helpers

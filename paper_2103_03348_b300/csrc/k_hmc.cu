@@ -40,7 +40,7 @@ struct PostConsts {
 };
 
 __global__ void __launch_bounds__(ASM_THREADS) posterior_assemble_kernel(
-    int64_t m, PostConsts pc, const int *__restrict__ seq, const double *__restrict__ prec,
+    int64_t m, PostConsts pc, const int *__restrict__ seq, const double *__restrict__ pdiag, int64_t pstride,
     const double *__restrict__ q, const double *__restrict__ w, const double *__restrict__ loglik,
     const double *__restrict__ grad, const double *__restrict__ hdiag, double *__restrict__ logpost,
     double *__restrict__ grad_q, double *__restrict__ hdiag_q) {
@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(ASM_THREADS) posterior_assemble_kernel(
     for (int64_t j = threadIdx.x; j < m; j += ASM_THREADS) {
         const int i = seq[j];
         if (grad_q) grad_q[6 + j] = grad[6 + i] - w[j];
-        if (hdiag_q) hdiag_q[6 + j] = hdiag[6 + i] - prec[(size_t)j * m + j];
+        if (hdiag_q) hdiag_q[6 + j] = hdiag[6 + i] - pdiag[(size_t)j * pstride];
         quad += rs[j] * w[j];
     }
     quad = block_sum<ASM_THREADS>(quad, sh);
@@ -122,23 +122,31 @@ extern "C" {
 
 size_t hawkes_posterior_workspace_size(int64_t m) { return m < 0 ? 0 : (size_t)(m > 0 ? m : 1) * sizeof(double); }
 
-int hawkes_posterior(int64_t n, int64_t m, const int *seq_idx, const double *prec, const hawkes_prior *prior,
-                     const double *q, const double *loglik, const double *grad, const double *hdiag, void *ws,
-                     size_t ws_bytes, double *logpost, double *grad_q, double *hdiag_q, void *stream) {
+static int post_check(int64_t n, int64_t m, const hawkes_prior *prior, const double *q, const double *loglik,
+                      const double *grad, const double *hdiag, const void *ws, const double *logpost,
+                      const double *grad_q, const double *hdiag_q, hk::PostConsts *pc) {
     if (n < 2 || m < 0 || m > n || !prior || !q || !loglik || !ws || !logpost) return HAWKES_EINVAL;
-    if (m > 0 && (!seq_idx || !prec)) return HAWKES_EINVAL;
     if ((grad == nullptr) != (grad_q == nullptr)) return HAWKES_EINVAL;
     if ((hdiag == nullptr) != (hdiag_q == nullptr)) return HAWKES_EINVAL;
     if (hdiag && !grad) return HAWKES_EINVAL;
-    if (ws_bytes < hawkes_posterior_workspace_size(m)) return HAWKES_EWORKSPACE;
-    hk::PostConsts pc;
     for (int k = 0; k < 6; ++k) {
         if (prior->kind[k] != HAWKES_PRIOR_GAMMA && prior->kind[k] != HAWKES_PRIOR_INVGAMMA) return HAWKES_EINVAL;
         if (!(prior->a[k] > 0) || !(prior->b[k] >= 0)) return HAWKES_EINVAL;
-        pc.kind[k] = prior->kind[k];
-        pc.a[k] = prior->a[k];
-        pc.b[k] = prior->b[k];
+        pc->kind[k] = prior->kind[k];
+        pc->a[k] = prior->a[k];
+        pc->b[k] = prior->b[k];
     }
+    return HAWKES_OK;
+}
+
+int hawkes_posterior(int64_t n, int64_t m, const int *seq_idx, const double *prec, const hawkes_prior *prior,
+                     const double *q, const double *loglik, const double *grad, const double *hdiag, void *ws,
+                     size_t ws_bytes, double *logpost, double *grad_q, double *hdiag_q, void *stream) {
+    hk::PostConsts pc;
+    const int rc = post_check(n, m, prior, q, loglik, grad, hdiag, ws, logpost, grad_q, hdiag_q, &pc);
+    if (rc != HAWKES_OK) return rc;
+    if (m > 0 && (!seq_idx || !prec)) return HAWKES_EINVAL;
+    if (ws_bytes < hawkes_posterior_workspace_size(m)) return HAWKES_EWORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     double *w = (double *)ws;
     const double *rs = q + 6;
@@ -147,7 +155,32 @@ int hawkes_posterior(int64_t n, int64_t m, const int *seq_idx, const double *pre
         hk::prec_matvec_kernel<<<blocks, hk::MV_THREADS, 0, s>>>(m, prec, rs, w);
         if (cudaGetLastError() != cudaSuccess) return HAWKES_ECUDA;
     }
-    hk::posterior_assemble_kernel<<<1, hk::ASM_THREADS, 0, s>>>(m, pc, seq_idx, prec, q, w, loglik, grad, hdiag,
+    hk::posterior_assemble_kernel<<<1, hk::ASM_THREADS, 0, s>>>(m, pc, seq_idx, prec, m + 1, q, w, loglik, grad,
+                                                                hdiag, logpost, grad_q, hdiag_q);
+    return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
+}
+
+size_t hawkes_posterior_tree_workspace_size(int64_t m) {
+    if (m < 2 || m > HAWKES_TREE_MAX_TIPS) return 0;
+    return (size_t)2 * m * sizeof(double) + hawkes_tree_workspace_size(m);
+}
+
+int hawkes_posterior_tree(int64_t n, int64_t m, const int *seq_idx, const int *plan, const double *length,
+                          double root_var, double sigma2, const hawkes_prior *prior, const double *q,
+                          const double *loglik, const double *grad, const double *hdiag, void *ws, size_t ws_bytes,
+                          double *logpost, double *grad_q, double *hdiag_q, void *stream) {
+    hk::PostConsts pc;
+    const int rc = post_check(n, m, prior, q, loglik, grad, hdiag, ws, logpost, grad_q, hdiag_q, &pc);
+    if (rc != HAWKES_OK) return rc;
+    if (m < 2 || m > HAWKES_TREE_MAX_TIPS || !seq_idx || !plan || !length) return HAWKES_EINVAL;
+    if (!(sigma2 > 0) || !(root_var >= 0) || !isfinite(sigma2) || !isfinite(root_var)) return HAWKES_EINVAL;
+    if (ws_bytes < hawkes_posterior_tree_workspace_size(m)) return HAWKES_EWORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *w = (double *)ws, *pd = w + m, *scratch = pd + m;
+    if (hk::launch_tree_prior(m, plan, length, root_var, sigma2, q + 6, scratch, nullptr, w, hdiag ? pd : nullptr,
+                              s) != cudaSuccess)
+        return HAWKES_ECUDA;
+    hk::posterior_assemble_kernel<<<1, hk::ASM_THREADS, 0, s>>>(m, pc, seq_idx, pd, 1, q, w, loglik, grad, hdiag,
                                                                 logpost, grad_q, hdiag_q);
     return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
 }

@@ -6,9 +6,9 @@ r_{s_1..s_M}) lives on the GPU.  Every leapfrog step runs the library's kernels:
 scatter of the sequenced log-rates, the fused likelihood gradient with the
 globals read from q on the device (hawkes_eval_device_params), the posterior
 assembly (priors, log-transform Jacobian, phylogenetic Brownian prior through
-its precision matrix) and the momentum and position updates.  Nothing crosses
-to the host inside a trajectory; each iteration reads back two energies for
-the accept step.
+its dense precision matrix or, in O(M), on the tree) and the momentum and
+position updates.  Nothing crosses to the host inside a trajectory; each
+iteration reads back two energies for the accept step.
 
 Adaptation (Section 2.3.2): a diagonal mass matrix from the running average of
 max(-H_qq, floor) over Hessian-diagonal evaluations made every `mass_every`
@@ -75,6 +75,11 @@ def _lib():
         L.hawkes_posterior.argtypes = [i64, i64, vp, vp, ctypes.POINTER(_Prior), vp, vp, vp, vp,
                                        vp, ctypes.c_size_t, vp, vp, vp, vp]
         L.hawkes_posterior.restype = ctypes.c_int
+        L.hawkes_posterior_tree_workspace_size.argtypes = [i64]
+        L.hawkes_posterior_tree_workspace_size.restype = ctypes.c_size_t
+        L.hawkes_posterior_tree.argtypes = [i64, i64, vp, vp, vp, d, d, ctypes.POINTER(_Prior), vp, vp, vp, vp,
+                                            vp, ctypes.c_size_t, vp, vp, vp, vp]
+        L.hawkes_posterior_tree.restype = ctypes.c_int
         L.hawkes_hmc_scatter_rates.argtypes = [i64, vp, vp, vp, vp]
         L.hawkes_hmc_momentum.argtypes = [i64, vp, vp, d, vp]
         L.hawkes_hmc_position.argtypes = [i64, vp, vp, vp, d, vp]
@@ -97,19 +102,29 @@ def _check(rc):
 class Posterior:
     """log pi(q) and its derivatives for fixed events, priors and tree precision."""
 
-    def __init__(self, x, y, t, r_base, seq_idx, prec, prior: Prior, precision="fp32c"):
+    def __init__(self, x, y, t, r_base, seq_idx, prec, prior: Prior, precision="fp32c", tree=None):
+        """prec: the dense M x M precision (sigma^2 V)^-1 on the device, or None
+        with tree: a tree.TreePrior over the same M sequenced events (O(M) per
+        evaluation instead of O(M^2))."""
         self.x, self.y, self.t = x, y, t
         self.r = r_base.clone()
         self.dev = t.device
         self.n = t.numel()
         self.seq = seq_idx.to(torch.int32).contiguous()
         self.m = self.seq.numel()
-        self.prec = prec.contiguous()
+        self.tree = tree
+        self.prec = prec.contiguous() if prec is not None else None
+        if (tree is None) == (prec is None):
+            raise ValueError("give exactly one of prec and tree")
+        if tree is not None and tree.m != self.m:
+            raise ValueError("the tree's tips must be the sequenced events")
         self.prior = prior
         self.c_prior = prior.as_c()
         self.precision = precision
         L = _lib()
-        self.ws = torch.empty(int(L.hawkes_posterior_workspace_size(self.m)), dtype=torch.uint8, device=self.dev)
+        ws_bytes = (L.hawkes_posterior_tree_workspace_size(self.m) if tree is not None
+                    else L.hawkes_posterior_workspace_size(self.m))
+        self.ws = torch.empty(int(ws_bytes), dtype=torch.uint8, device=self.dev)
         f64 = dict(dtype=torch.float64, device=self.dev)
         self.like = {"loglik": torch.empty((), **f64), "grad": torch.empty(6 + self.n, **f64),
                      "hdiag": torch.empty(6 + self.n, **f64), "status": torch.empty((), dtype=torch.int32, device=self.dev)}
@@ -135,13 +150,22 @@ class Posterior:
         hawkes._call(mode, self.x, self.y, self.t, self.r, q, self.precision, stream=stream, check=False,
                      out=self.like, log_params=True)
         self.calls["hess" if want_hess else "grad"] += 1
-        _check(L.hawkes_posterior(self.n, self.m, _ptr(self.seq), _ptr(self.prec), ctypes.byref(self.c_prior),
-                                  _ptr(q), _ptr(self.like["loglik"]), _ptr(self.like["grad"]),
-                                  _ptr(self.like["hdiag"]) if want_hess else ctypes.c_void_p(0),
-                                  _ptr(self.ws), ctypes.c_size_t(self.ws.numel()), _ptr(out["logpost"]),
-                                  _ptr(out["grad"]), _ptr(out["hdiag"]) if want_hess else ctypes.c_void_p(0),
-                                  ctypes.c_void_p(stream)))
+        self._assemble(q, self.like["grad"], self.like["hdiag"] if want_hess else None, out["logpost"],
+                       out["grad"], out["hdiag"] if want_hess else None, stream)
         return out
+
+    def _assemble(self, q, grad, hdiag, logpost, grad_q, hdiag_q, stream):
+        """Priors, Jacobian and the phylogenetic prior (dense or on the tree) on the device."""
+        L = _lib()
+        common = (ctypes.byref(self.c_prior), _ptr(q), _ptr(self.like["loglik"]), _ptr(grad), _ptr(hdiag),
+                  _ptr(self.ws), ctypes.c_size_t(self.ws.numel()), _ptr(logpost), _ptr(grad_q), _ptr(hdiag_q),
+                  ctypes.c_void_p(stream))
+        if self.tree is None:
+            _check(L.hawkes_posterior(self.n, self.m, _ptr(self.seq), _ptr(self.prec), *common))
+        else:
+            tr = self.tree
+            _check(L.hawkes_posterior_tree(self.n, self.m, _ptr(self.seq), _ptr(tr.plan), _ptr(tr.length),
+                                           tr.root_var, tr.sigma2, *common))
 
     def logpost_only(self, q, out):
         """out['logpost'] = log pi(q) from a log-likelihood-only pass (the exact
@@ -152,10 +176,7 @@ class Posterior:
         hawkes._call("loglik", self.x, self.y, self.t, self.r, q, self.precision, stream=stream, check=False,
                      out=self.like, log_params=True)
         self.calls["loglik"] = self.calls.get("loglik", 0) + 1
-        _check(L.hawkes_posterior(self.n, self.m, _ptr(self.seq), _ptr(self.prec), ctypes.byref(self.c_prior),
-                                  _ptr(q), _ptr(self.like["loglik"]), ctypes.c_void_p(0), ctypes.c_void_p(0),
-                                  _ptr(self.ws), ctypes.c_size_t(self.ws.numel()), _ptr(out["logpost"]),
-                                  ctypes.c_void_p(0), ctypes.c_void_p(0), ctypes.c_void_p(stream)))
+        self._assemble(q, None, None, out["logpost"], None, None, stream)
         return out
 
     def status(self):

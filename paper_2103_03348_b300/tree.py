@@ -1,0 +1,88 @@
+"""The phylogenetic Brownian prior on the sequenced log-rates (Section 2.2,
+Eq. 2) evaluated in O(M) on the tree (Section 2.3.1's dynamic programme),
+through the library's hawkes_tree_plan (host) and hawkes_tree_prior (device).
+
+Tree encoding: nodes 0..M-1 are the tips in the order of the sequenced events;
+nodes M..2M-2 are internal; parent[v] is -1 at the root; length[v] is the
+branch length from v to its parent.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import hawkes
+
+
+def _lib():
+    L = hawkes.lib()
+    if not getattr(L, "_tree_typed", False):
+        vp, i64, d, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+        L.hawkes_tree_plan_size.argtypes = [i64]
+        L.hawkes_tree_plan_size.restype = sz
+        L.hawkes_tree_workspace_size.argtypes = [i64]
+        L.hawkes_tree_workspace_size.restype = sz
+        L.hawkes_tree_plan.argtypes = [i64, vp, vp, sz]
+        L.hawkes_tree_plan.restype = ctypes.c_int
+        L.hawkes_tree_prior.argtypes = [i64, vp, vp, d, d, vp, vp, sz, vp, vp, vp, vp]
+        L.hawkes_tree_prior.restype = ctypes.c_int
+        L.hawkes_posterior_tree_workspace_size.argtypes = [i64]
+        L.hawkes_posterior_tree_workspace_size.restype = sz
+        L._tree_typed = True
+    return L
+
+
+def _check(rc):
+    if rc != hawkes.OK:
+        raise hawkes.HawkesError(rc, hawkes.strerror(rc))
+
+
+def plan(parent) -> np.ndarray:
+    """The host traversal plan (int32) for a parent array of 2M-1 nodes."""
+    L = _lib()
+    par = np.ascontiguousarray(parent, dtype=np.int64)
+    nn = par.size
+    if nn < 3 or nn % 2 == 0:
+        raise hawkes.HawkesError(hawkes.EINVAL, "parent must have 2M-1 entries with M >= 2")
+    m = (nn + 1) // 2
+    size = int(L.hawkes_tree_plan_size(m))
+    if size == 0:
+        raise hawkes.HawkesError(hawkes.EINVAL, "tree too large")
+    out = np.zeros(size // 4, dtype=np.int32)
+    _check(L.hawkes_tree_plan(m, par.ctypes.data_as(ctypes.c_void_p), out.ctypes.data_as(ctypes.c_void_p),
+                              ctypes.c_size_t(size)))
+    return out
+
+
+class TreePrior:
+    """z ~ N(0, sigma2 V) with V from the tree; plan and branch lengths live on the device."""
+
+    def __init__(self, parent, length, root_var: float, sigma2: float, device="cuda"):
+        self.parent = np.asarray(parent, dtype=np.int64)
+        self.m = (self.parent.size + 1) // 2
+        host_plan = plan(self.parent)
+        self.plan = torch.from_numpy(host_plan).to(device)
+        self.length = torch.as_tensor(np.asarray(length, dtype=np.float64), device=device).contiguous()
+        if self.length.numel() != self.parent.size:
+            raise hawkes.HawkesError(hawkes.EINVAL, "length must have 2M-1 entries")
+        self.root_var = float(root_var)
+        self.sigma2 = float(sigma2)
+        self.levels = int(host_plan[0])
+        self.ws = torch.empty(int(_lib().hawkes_tree_workspace_size(self.m)), dtype=torch.uint8, device=device)
+
+    def evaluate(self, z, want=("logdens", "pz", "pdiag")):
+        """{'logdens': log N(z; 0, sigma2 V), 'pz': (sigma2 V)^-1 z, 'pdiag': diag((sigma2 V)^-1)}."""
+        L = _lib()
+        z = z.contiguous()
+        f64 = dict(dtype=torch.float64, device=z.device)
+        out = {"logdens": torch.empty((), **f64) if "logdens" in want else None,
+               "pz": torch.empty(self.m, **f64) if "pz" in want else None,
+               "pdiag": torch.empty(self.m, **f64) if "pdiag" in want else None}
+        p = lambda t: ctypes.c_void_p(t.data_ptr() if t is not None else 0)  # noqa: E731
+        s = ctypes.c_void_p(torch.cuda.current_stream(z.device).cuda_stream)
+        _check(L.hawkes_tree_prior(self.m, p(self.plan), p(self.length), self.root_var, self.sigma2, p(z), p(self.ws),
+                                   ctypes.c_size_t(self.ws.numel()), p(out["logdens"]), p(out["pz"]),
+                                   p(out["pdiag"]), s))
+        return {k: v for k, v in out.items() if v is not None}
