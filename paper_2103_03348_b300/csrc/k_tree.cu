@@ -51,13 +51,21 @@ __host__ __device__ inline TreePlan tree_plan_view(const int *p) {
 
 // mu, dl, gb, dd: scratch of 2m-1 doubles each
 __global__ void __launch_bounds__(TREE_THREADS)
-    tree_prior_kernel(const int *__restrict__ plan, const double *__restrict__ len, double tau0, double sigma2,
-                      const double *__restrict__ z, double *__restrict__ mu, double *__restrict__ dl,
+    tree_prior_kernel(int64_t m_arg, const int *__restrict__ plan, const double *__restrict__ len, double tau0,
+                      double sigma2, const double *__restrict__ z, double *__restrict__ mu, double *__restrict__ dl,
                       double *__restrict__ gb, double *__restrict__ dd, double *__restrict__ logdens,
                       double *__restrict__ pz, double *__restrict__ pdiag) {
     __shared__ double sh[TREE_THREADS];
     const TreePlan T = tree_plan_view(plan);
     const int m = T.m;
+    if ((int64_t)m != m_arg || T.levels < 1 || T.levels > m - 1) {  // a plan for another tree: touch no scratch
+        for (int64_t i = threadIdx.x; i < m_arg; i += TREE_THREADS) {
+            if (pz) pz[i] = NAN;
+            if (pdiag) pdiag[i] = NAN;
+        }
+        if (logdens && threadIdx.x == 0) *logdens = NAN;
+        return;
+    }
     for (int i = threadIdx.x; i < m; i += TREE_THREADS) {
         mu[i] = z[i];
         dl[i] = 0.0;
@@ -115,7 +123,7 @@ cudaError_t launch_tree_prior(int64_t m, const int *plan, const double *len, dou
                               cudaStream_t s) {
     const int64_t nn = 2 * m - 1;
     double *mu = scratch, *dl = mu + nn, *gb = dl + nn, *dd = gb + nn;
-    tree_prior_kernel<<<1, TREE_THREADS, 0, s>>>(plan, len, tau0, sigma2, z, mu, dl, gb, dd, logdens, pz, pdiag);
+    tree_prior_kernel<<<1, TREE_THREADS, 0, s>>>(m, plan, len, tau0, sigma2, z, mu, dl, gb, dd, logdens, pz, pdiag);
     return cudaGetLastError();
 }
 
