@@ -148,6 +148,55 @@ int hawkes_hess_diag_timed(const double *x, const double *y, const double *t, co
                            void *const phase_events[4]);
 
 /* ------------------------------------------------------------------------
+ * Sharded evaluation: the double sum split over k shards (ranks), each with
+ * its own workspace and a copy of the events.  Shard s owns the tiles of 128
+ * events [s*T/k, (s+1)*T/k) (T = ceil(n/128)) as targets of the row pass
+ * (Eq. 1 inner sums) and as sources of the column pass (Eqs. 4-5).  One
+ * exchange sits between the two phases: each shard's row phase writes its
+ * tiles' records (partial sums of the log-likelihood terms and the column
+ * weights B / lambda_n) into its slice of the exchange buffer; the caller
+ * all-gathers the slices so that every shard's buffer holds all records (an
+ * NCCL all-gather across GPUs, or copies between buffers on one GPU); then each
+ * shard's column phase reduces all records in a fixed order and runs its
+ * columns.  Every shard's loglik and global entries [0..6) are identical, the
+ * per-event entries [6+first, 6+end) are written by the shard that owns them,
+ * and the union equals hawkes_hess_diag (or _grad / _loglik) bit for bit.
+ * The paper evaluates on one device and has no counterpart.
+ * ------------------------------------------------------------------------ */
+
+/* Bytes of the exchange buffer (the same for every shard): T records of
+ * (16 + 128) doubles. */
+size_t hawkes_shard_exchange_size(int64_t n);
+
+/* Events [*first_event, *end_event) owned by shard `shard` of n_shards, and
+ * the byte slice [*xbuf_offset, *xbuf_offset + *xbuf_bytes) of the exchange
+ * buffer that its row phase writes (any output may be NULL).  A shard may own
+ * no events when n_shards exceeds T. */
+int hawkes_shard_range(int64_t n, int shard, int n_shards, int64_t *first_event, int64_t *end_event,
+                       size_t *xbuf_offset, size_t *xbuf_bytes);
+
+/* Phase 1 of shard `shard`: validation and packing of all n events, the row
+ * pass over the shard's target tiles, and its records into xbuf (DEVICE,
+ * 16-byte aligned, hawkes_shard_exchange_size(n) bytes; only the shard's
+ * slice is written).  Inputs, params, precision and ws as for
+ * hawkes_hess_diag; mode is a HAWKES_MODE_* value (device-resident parameters
+ * are not offered here).  The shard's workspace must be passed unchanged to
+ * phase 2. */
+int hawkes_shard_rows(const double *x, const double *y, const double *t, const double *r, int64_t n,
+                      const double params[6], int precision, int mode, int shard, int n_shards, void *ws,
+                      size_t ws_bytes, void *xbuf, size_t xbuf_bytes, int *dev_status, void *stream);
+
+/* Phase 2 of shard `shard`, once xbuf holds every shard's records: loglik
+ * and the global entries of grad / hdiag (all shards write the same values),
+ * then the column pass for the shard's source events (entries 6 + [first,
+ * end)).  Same arguments as phase 1 plus the outputs; *dev_status reports the
+ * data-dependent conditions of all shards. */
+int hawkes_shard_cols(const double *x, const double *y, const double *t, const double *r, int64_t n,
+                      const double params[6], int precision, int mode, int shard, int n_shards, void *ws,
+                      size_t ws_bytes, const void *xbuf, size_t xbuf_bytes, double *loglik, double *grad,
+                      double *hdiag, int *dev_status, void *stream);
+
+/* ------------------------------------------------------------------------
  * Adaptively preconditioned HMC (Section 2.3): posterior assembly and leapfrog
  * pieces.  Sampler coordinates q = (log mu0, log tau_x, log tau_t, log theta0,
  * log omega, log h, r_{s_1}, ..., r_{s_M}) with s_j the sequenced events.

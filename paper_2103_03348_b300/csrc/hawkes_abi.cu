@@ -119,15 +119,26 @@ cudaError_t launch_setup(const Consts &c, const ParamSource &ps, const Workspace
     return cudaGetLastError();
 }
 
-static int run(const double *x, const double *y, const double *t, const double *r, int64_t n,
-               const double *params, const double *params_dev, int log_params, int precision, void *wsp,
-               size_t ws_bytes, int mode, double *loglik, double *grad, double *hdiag, int *dev_status, void *stream,
-               void *const *events = nullptr) {
+// One evaluation's constants, carved workspace and outputs.
+struct Call {
+    Consts c;
+    Workspace ws;
+    Inputs in;
+    Outputs out;
+    ParamSource ps;
+    cudaStream_t s;
+    bool rates;  // the column pass runs
+};
+
+static int prepare(const double *x, const double *y, const double *t, const double *r, int64_t n,
+                   const double *params, const double *params_dev, int log_params, int precision, void *wsp,
+                   size_t ws_bytes, int mode, double *loglik, double *grad, double *hdiag, int *dev_status,
+                   void *stream, Call *k) {
     if (n < 2 || n > HAWKES_MAX_EVENTS) return HAWKES_EINVAL;
     if (precision != HAWKES_FP64 && precision != HAWKES_FP32C && precision != HAWKES_FP32C_BAND) return HAWKES_EINVAL;
     // modes 3 and 4: gradient / Hessian diagonal of the six globals only (no column pass)
     if (mode < 0 || mode > 4) return HAWKES_EINVAL;
-    const bool rates = mode == MODE_GRAD || mode == MODE_HESS;
+    k->rates = mode == MODE_GRAD || mode == MODE_HESS;
     if (mode == 3) mode = MODE_GRAD;
     if (mode == 4) mode = MODE_HESS;
     if (!x || !y || !t || !r || !(params || params_dev) || !wsp || !dev_status) return HAWKES_EINVAL;
@@ -137,52 +148,122 @@ static int run(const double *x, const double *y, const double *t, const double *
     if (((uintptr_t)wsp & 255) != 0) return HAWKES_EINVAL;
     if (params && !params_valid(params)) return HAWKES_EINVAL;
     const Geometry g = make_geometry(n);
-    Workspace ws;
-    const size_t need = carve(wsp, g, precision, &ws);
+    const size_t need = carve(wsp, g, precision, &k->ws);
     if (ws_bytes < need) return HAWKES_EWORKSPACE;
 
-    Consts c;
+    Consts &c = k->c;
     memset(&c, 0, sizeof(c));
     c.g = g;
     c.mode = mode;
     c.fp32c = precision == HAWKES_FP32C || precision == HAWKES_FP32C_BAND;
     c.band = precision == HAWKES_FP32C_BAND;
-    c.d = ws.derived;
-    ParamSource ps;
-    memset(&ps, 0, sizeof(ps));
+    c.t0 = 0;
+    c.t1 = g.tiles;
+    c.d = k->ws.derived;
+    memset(&k->ps, 0, sizeof(k->ps));
     if (params) {
-        for (int k = 0; k < 6; ++k) ps.v[k] = params[k];
+        for (int j = 0; j < 6; ++j) k->ps.v[j] = params[j];
     } else {
-        ps.dev = params_dev;
-        ps.log_scale = log_params ? 1 : 0;
+        k->ps.dev = params_dev;
+        k->ps.log_scale = log_params ? 1 : 0;
     }
-    const Inputs in = {x, y, t, r};
-    const Outputs out = {loglik, mode >= MODE_GRAD ? grad : nullptr, mode == MODE_HESS ? hdiag : nullptr, dev_status};
-    cudaStream_t s = (cudaStream_t)stream;
+    k->in = {x, y, t, r};
+    k->out = {loglik, mode >= MODE_GRAD ? grad : nullptr, mode == MODE_HESS ? hdiag : nullptr, dev_status};
+    k->s = (cudaStream_t)stream;
+    return HAWKES_OK;
+}
 
+static bool mark(void *const *events, int j, cudaStream_t s) {
+    return !(events && events[j]) || cudaEventRecord((cudaEvent_t)events[j], s) == cudaSuccess;
+}
+
+// Validation, packing (all events), then the row pass, row combine, FP64
+// fix-up and row epilogue for the target tiles [t0, t1).
+static int phase_rows(const Call &k, void *const *events) {
+    const Consts &c = k.c;
+    const Workspace &ws = k.ws;
+    cudaStream_t s = k.s;
     if (cudaMemsetAsync(ws.hdr, 0, 8 * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
-    if (cudaMemsetAsync(ws.hash, 0xFF, (size_t)g.hash_size * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
-    if (cudaMemsetAsync(ws.cnt, 0, (size_t)g.npad * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
-    if (launch_setup(c, ps, ws, s) != cudaSuccess) return HAWKES_ECUDA;
-    if (launch_prep(c, in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
-    if (launch_pack(c, in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
-    auto mark = [&](int k) -> bool {
-        return !(events && events[k]) || cudaEventRecord((cudaEvent_t)events[k], s) == cudaSuccess;
-    };
-    if (!mark(0)) return HAWKES_ECUDA;
-    if ((c.fp32c ? launch_row32(c, ws, s) : launch_row64(c, ws, s)) != cudaSuccess) return HAWKES_ECUDA;
-    if (!mark(1)) return HAWKES_ECUDA;
-    if (launch_combine(c, ws, s) != cudaSuccess) return HAWKES_ECUDA;
-    if (c.fp32c && launch_fixup(c, in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
-    if (launch_epilogue(c, in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
-    if (launch_finalize(c, ws, out, s) != cudaSuccess) return HAWKES_ECUDA;
-    if (mode >= MODE_GRAD && rates) {
-        if (!mark(2)) return HAWKES_ECUDA;
-        if ((c.fp32c ? launch_col32(c, in, ws, s) : launch_col64(c, ws, s)) != cudaSuccess) return HAWKES_ECUDA;
-        if (!mark(3)) return HAWKES_ECUDA;
-        if (launch_colfinish(c, ws, out, s) != cudaSuccess) return HAWKES_ECUDA;
+    if (cudaMemsetAsync(ws.hash, 0xFF, (size_t)c.g.hash_size * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
+    if (cudaMemsetAsync(ws.cnt, 0, (size_t)c.g.npad * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
+    if (launch_setup(c, k.ps, ws, s) != cudaSuccess) return HAWKES_ECUDA;
+    if (launch_prep(c, k.in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
+    if (launch_pack(c, k.in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
+    if (!mark(events, 0, s)) return HAWKES_ECUDA;
+    if (c.t1 > c.t0) {
+        if ((c.fp32c ? launch_row32(c, ws, s) : launch_row64(c, ws, s)) != cudaSuccess) return HAWKES_ECUDA;
+    }
+    if (!mark(events, 1, s)) return HAWKES_ECUDA;
+    if (c.t1 > c.t0) {
+        if (launch_combine(c, ws, s) != cudaSuccess) return HAWKES_ECUDA;
+        if (c.fp32c && launch_fixup(c, k.in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
+        if (launch_epilogue(c, k.in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
     }
     return HAWKES_OK;
+}
+
+// The fixed-order reduction over every tile's partials (loglik, global
+// gradient and Hessian diagonal), then the column pass and its finish for the
+// source tiles [t0, t1).
+static int phase_cols(const Call &k, void *const *events) {
+    const Consts &c = k.c;
+    cudaStream_t s = k.s;
+    if (launch_finalize(c, k.ws, k.out, s) != cudaSuccess) return HAWKES_ECUDA;
+    if (c.mode >= MODE_GRAD && k.rates) {
+        if (!mark(events, 2, s)) return HAWKES_ECUDA;
+        if (c.t1 > c.t0) {
+            if ((c.fp32c ? launch_col32(c, k.in, k.ws, s) : launch_col64(c, k.ws, s)) != cudaSuccess)
+                return HAWKES_ECUDA;
+        }
+        if (!mark(events, 3, s)) return HAWKES_ECUDA;
+        if (c.t1 > c.t0 && launch_colfinish(c, k.ws, k.out, s) != cudaSuccess) return HAWKES_ECUDA;
+    }
+    return HAWKES_OK;
+}
+
+static int run(const double *x, const double *y, const double *t, const double *r, int64_t n,
+               const double *params, const double *params_dev, int log_params, int precision, void *wsp,
+               size_t ws_bytes, int mode, double *loglik, double *grad, double *hdiag, int *dev_status, void *stream,
+               void *const *events = nullptr) {
+    Call k;
+    int rc = prepare(x, y, t, r, n, params, params_dev, log_params, precision, wsp, ws_bytes, mode, loglik, grad,
+                     hdiag, dev_status, stream, &k);
+    if (rc != HAWKES_OK) return rc;
+    rc = phase_rows(k, events);
+    if (rc != HAWKES_OK) return rc;
+    return phase_cols(k, events);
+}
+
+// Shard s of k owns tiles [s * tiles / k, (s + 1) * tiles / k).
+static void shard_range(int tiles, int shard, int n_shards, int *t0, int *t1) {
+    *t0 = (int)((int64_t)shard * tiles / n_shards);
+    *t1 = (int)((int64_t)(shard + 1) * tiles / n_shards);
+}
+
+static int shard_phase(const double *x, const double *y, const double *t, const double *r, int64_t n,
+                       const double params[6], int precision, int mode, int shard, int n_shards, void *wsp,
+                       size_t ws_bytes, void *xbuf, size_t xbuf_bytes, double *loglik, double *grad, double *hdiag,
+                       int *dev_status, void *stream, bool second) {
+    if (n_shards < 1 || shard < 0 || shard >= n_shards || !params || !xbuf) return HAWKES_EINVAL;
+    if (((uintptr_t)xbuf & 15) != 0) return HAWKES_EINVAL;
+    if (n < 2 || n > HAWKES_MAX_EVENTS) return HAWKES_EINVAL;
+    const Geometry g = make_geometry(n);
+    if (xbuf_bytes < (size_t)g.tiles * XREC_DOUBLES * sizeof(double)) return HAWKES_EWORKSPACE;
+    // the output pointers are checked (and used) only in the second phase
+    double dummy_out = 0.0;
+    Call k;
+    int rc = prepare(x, y, t, r, n, params, nullptr, 0, precision, wsp, ws_bytes, mode,
+                     second ? loglik : &dummy_out, second ? grad : &dummy_out, second ? hdiag : &dummy_out,
+                     dev_status, stream, &k);
+    if (rc != HAWKES_OK) return rc;
+    shard_range(g.tiles, shard, n_shards, &k.c.t0, &k.c.t1);
+    if (!second) {
+        rc = phase_rows(k, nullptr);
+        if (rc != HAWKES_OK) return rc;
+        return launch_shard_export(k.c, k.ws, (double *)xbuf, k.s) == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
+    }
+    if (launch_shard_import(k.c, k.ws, (const double *)xbuf, k.s) != cudaSuccess) return HAWKES_ECUDA;
+    return phase_cols(k, nullptr);
 }
 
 }  // namespace hk
@@ -232,6 +313,40 @@ int hawkes_eval_device_params(const double *x, const double *y, const double *t,
     if (!params_dev) return HAWKES_EINVAL;
     return hk::run(x, y, t, r, n, nullptr, params_dev, log_params, precision, ws, ws_bytes, mode, loglik, grad,
                    hdiag, dev_status, stream);
+}
+
+size_t hawkes_shard_exchange_size(int64_t n) {
+    if (n < 2 || n > HAWKES_MAX_EVENTS) return 0;
+    return (size_t)hk::make_geometry(n).tiles * hk::XREC_DOUBLES * sizeof(double);
+}
+
+int hawkes_shard_range(int64_t n, int shard, int n_shards, int64_t *first_event, int64_t *end_event,
+                       size_t *xbuf_offset, size_t *xbuf_bytes) {
+    if (n < 2 || n > HAWKES_MAX_EVENTS || n_shards < 1 || shard < 0 || shard >= n_shards) return HAWKES_EINVAL;
+    const hk::Geometry g = hk::make_geometry(n);
+    int t0, t1;
+    hk::shard_range(g.tiles, shard, n_shards, &t0, &t1);
+    const size_t rec = hk::XREC_DOUBLES * sizeof(double);
+    if (first_event) *first_event = (int64_t)t0 * hk::TILE < n ? (int64_t)t0 * hk::TILE : n;
+    if (end_event) *end_event = (int64_t)t1 * hk::TILE < n ? (int64_t)t1 * hk::TILE : n;
+    if (xbuf_offset) *xbuf_offset = (size_t)t0 * rec;
+    if (xbuf_bytes) *xbuf_bytes = (size_t)(t1 - t0) * rec;
+    return HAWKES_OK;
+}
+
+int hawkes_shard_rows(const double *x, const double *y, const double *t, const double *r, int64_t n,
+                      const double params[6], int precision, int mode, int shard, int n_shards, void *ws,
+                      size_t ws_bytes, void *xbuf, size_t xbuf_bytes, int *dev_status, void *stream) {
+    return hk::shard_phase(x, y, t, r, n, params, precision, mode, shard, n_shards, ws, ws_bytes, xbuf, xbuf_bytes,
+                           nullptr, nullptr, nullptr, dev_status, stream, false);
+}
+
+int hawkes_shard_cols(const double *x, const double *y, const double *t, const double *r, int64_t n,
+                      const double params[6], int precision, int mode, int shard, int n_shards, void *ws,
+                      size_t ws_bytes, const void *xbuf, size_t xbuf_bytes, double *loglik, double *grad,
+                      double *hdiag, int *dev_status, void *stream) {
+    return hk::shard_phase(x, y, t, r, n, params, precision, mode, shard, n_shards, ws, ws_bytes, (void *)xbuf,
+                           xbuf_bytes, loglik, grad, hdiag, dev_status, stream, true);
 }
 
 const char *hawkes_strerror(int status) {

@@ -25,6 +25,7 @@ constexpr int TILE = 128;   // events per tile: targets per row block, sources p
 constexpr int NMOM = 10;    // row moments (hess mode)
 constexpr int NACC = 13;    // per-row terms reduced across rows: loglik, 6 gradient, 6 Hessian
 constexpr int ACC_STRIDE = 16;
+constexpr int XREC_DOUBLES = 16 + TILE;  // one tile's record in the shard exchange buffer
 
 constexpr int MODE_LL = 0, MODE_GRAD = 1, MODE_HESS = 2;
 
@@ -71,6 +72,7 @@ struct Derived {
 struct Consts {
     Geometry g;
     int mode, fp32c, band;  // band: FP32C with exact background band skipping
+    int t0, t1;        // the tiles this call owns as targets (row pass) and sources (column pass)
     const Derived *d;  // device: written by setup_kernel
 };
 
@@ -131,6 +133,8 @@ cudaError_t launch_finalize(const Consts &c, const Workspace &ws, const Outputs 
 cudaError_t launch_col32(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_col64(const Consts &c, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_colfinish(const Consts &c, const Workspace &ws, const Outputs &out, cudaStream_t s);
+cudaError_t launch_shard_export(const Consts &c, const Workspace &ws, double *xbuf, cudaStream_t s);
+cudaError_t launch_shard_import(const Consts &c, const Workspace &ws, const double *xbuf, cudaStream_t s);
 cudaError_t launch_tree_prior(int64_t m, const int *plan, const double *len, double tau0, double sigma2,
                               const double *z, double *scratch, double *logdens, double *pz, double *pdiag,
                               cudaStream_t s);

@@ -45,7 +45,7 @@ __device__ __forceinline__ void col_tile(const float4 *sAB, const int *sG, int n
 template <int MODE>
 __global__ void __launch_bounds__(TILE, 4) col32_kernel(Consts c, Inputs in, Workspace ws) {
     const Derived &D = *c.d;
-    const int tile = blockIdx.x, chunk = blockIdx.y;
+    const int tile = c.t0 + blockIdx.x, chunk = blockIdx.y;
     const int m = tile * TILE + threadIdx.x;
     const int n = c.g.n, npad = c.g.npad;
     __shared__ float4 sAB[2][TILE];
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(TILE, 4) col32_kernel(Consts c, Inputs in, Wor
 }
 
 cudaError_t launch_col32(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s) {
-    const dim3 grid(c.g.tiles, c.g.n_chunks);
+    const dim3 grid(c.t1 - c.t0, c.g.n_chunks);
     if (c.mode == MODE_HESS) col32_kernel<MODE_HESS><<<grid, TILE, 0, s>>>(c, in, ws);
     else col32_kernel<MODE_GRAD><<<grid, TILE, 0, s>>>(c, in, ws);
     return cudaGetLastError();

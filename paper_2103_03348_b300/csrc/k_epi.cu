@@ -29,8 +29,8 @@ namespace hk {
 constexpr int CB_THREADS = 256;
 
 __global__ void __launch_bounds__(CB_THREADS) combine_kernel(Consts c, Workspace ws) {
-    const int i = blockIdx.x * CB_THREADS + threadIdx.x;
-    if (i >= c.g.n) return;
+    const int i = c.t0 * TILE + blockIdx.x * CB_THREADS + threadIdx.x;
+    if (i >= c.g.n || i >= c.t1 * TILE) return;
     const int npad = c.g.npad;
     double sg = 0.0, se = 0.0;
     for (int k = 0; k < NMOM; ++k) {
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(CB_THREADS) combine_kernel(Consts c, Workspace
 }
 
 cudaError_t launch_combine(const Consts &c, const Workspace &ws, cudaStream_t s) {
-    combine_kernel<<<(c.g.n + CB_THREADS - 1) / CB_THREADS, CB_THREADS, 0, s>>>(c, ws);
+    combine_kernel<<<((c.t1 - c.t0) * TILE + CB_THREADS - 1) / CB_THREADS, CB_THREADS, 0, s>>>(c, ws);
     return cudaGetLastError();
 }
 
@@ -62,7 +62,8 @@ __global__ void __launch_bounds__(TILE) epilogue_kernel(Consts c, Inputs in, Wor
     const Derived &D = *c.d;
     __shared__ double sh[(TILE / 32) * NACC];
     __shared__ float shf[TILE];
-    const int i = blockIdx.x * TILE + threadIdx.x;
+    const int tile = c.t0 + blockIdx.x;
+    const int i = tile * TILE + threadIdx.x;
     const int n = c.g.n, npad = c.g.npad;
     const bool valid = i < n;
     double acc[NACC];
@@ -157,16 +158,16 @@ __global__ void __launch_bounds__(TILE) epilogue_kernel(Consts c, Inputs in, Wor
     }
     {
         const double v = block_sum_multi<TILE, NACC>(acc, sh);
-        if (threadIdx.x < NACC) ws.blockpart[(size_t)blockIdx.x * ACC_STRIDE + threadIdx.x] = v;
+        if (threadIdx.x < NACC) ws.blockpart[(size_t)tile * ACC_STRIDE + threadIdx.x] = v;
     }
     if (c.fp32c) {
         const float gm = block_max<TILE>(ghat, shf);
-        if (threadIdx.x == 0) ws.tstat32[blockIdx.x].w = gm;
+        if (threadIdx.x == 0) ws.tstat32[tile].w = gm;
     }
 }
 
 cudaError_t launch_epilogue(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s) {
-    epilogue_kernel<<<c.g.tiles, TILE, 0, s>>>(c, in, ws);
+    epilogue_kernel<<<c.t1 - c.t0, TILE, 0, s>>>(c, in, ws);
     return cudaGetLastError();
 }
 
@@ -244,8 +245,8 @@ cudaError_t launch_finalize(const Consts &c, const Workspace &ws, const Outputs 
 }
 
 __global__ void __launch_bounds__(CB_THREADS) colfinish_kernel(Consts c, Workspace ws, Outputs out) {
-    const int m = blockIdx.x * CB_THREADS + threadIdx.x;
-    if (m >= c.g.n) return;
+    const int m = c.t0 * TILE + blockIdx.x * CB_THREADS + threadIdx.x;
+    if (m >= c.g.n || m >= c.t1 * TILE) return;
     const int npad = c.g.npad;
     double c1 = 0.0, c2 = 0.0;
     for (int ch = 0; ch < c.g.n_chunks; ++ch) {
@@ -264,7 +265,7 @@ __global__ void __launch_bounds__(CB_THREADS) colfinish_kernel(Consts c, Workspa
 }
 
 cudaError_t launch_colfinish(const Consts &c, const Workspace &ws, const Outputs &out, cudaStream_t s) {
-    colfinish_kernel<<<(c.g.n + CB_THREADS - 1) / CB_THREADS, CB_THREADS, 0, s>>>(c, ws, out);
+    colfinish_kernel<<<((c.t1 - c.t0) * TILE + CB_THREADS - 1) / CB_THREADS, CB_THREADS, 0, s>>>(c, ws, out);
     return cudaGetLastError();
 }
 

@@ -36,7 +36,7 @@ __device__ __forceinline__ void accumulate64(double (&a)[NMOM], double xs, doubl
 template <int MODE>
 __global__ void __launch_bounds__(TILE) row64_kernel(Consts c, Workspace ws) {
     const Derived &D = *c.d;
-    const int tile = blockIdx.x, chunk = blockIdx.y;
+    const int tile = c.t0 + blockIdx.x, chunk = blockIdx.y;
     const int i = tile * TILE + threadIdx.x;
     const int npad = c.g.npad;
     __shared__ double4_32a sS[TILE];
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(TILE) row64_kernel(Consts c, Workspace ws) {
 }
 
 cudaError_t launch_row64(const Consts &c, const Workspace &ws, cudaStream_t s) {
-    const dim3 grid(c.g.tiles, c.g.n_chunks);
+    const dim3 grid(c.t1 - c.t0, c.g.n_chunks);
     if (c.mode == MODE_HESS) row64_kernel<MODE_HESS><<<grid, TILE, 0, s>>>(c, ws);
     else if (c.mode == MODE_GRAD) row64_kernel<MODE_GRAD><<<grid, TILE, 0, s>>>(c, ws);
     else row64_kernel<MODE_LL><<<grid, TILE, 0, s>>>(c, ws);
@@ -82,7 +82,7 @@ cudaError_t launch_row64(const Consts &c, const Workspace &ws, cudaStream_t s) {
 template <int MODE>
 __global__ void __launch_bounds__(TILE) col64_kernel(Consts c, Workspace ws) {
     const Derived &D = *c.d;
-    const int tile = blockIdx.x, chunk = blockIdx.y;
+    const int tile = c.t0 + blockIdx.x, chunk = blockIdx.y;
     const int m = tile * TILE + threadIdx.x;
     const int npad = c.g.npad;
     __shared__ double4_32a sT[TILE];
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(TILE) col64_kernel(Consts c, Workspace ws) {
 }
 
 cudaError_t launch_col64(const Consts &c, const Workspace &ws, cudaStream_t s) {
-    const dim3 grid(c.g.tiles, c.g.n_chunks);
+    const dim3 grid(c.t1 - c.t0, c.g.n_chunks);
     if (c.mode == MODE_HESS) col64_kernel<MODE_HESS><<<grid, TILE, 0, s>>>(c, ws);
     else col64_kernel<MODE_GRAD><<<grid, TILE, 0, s>>>(c, ws);
     return cudaGetLastError();

@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(TILE, 4) row32_kernel(Consts c, Workspace ws) 
     // holds the tile itself, y = 1 the chunk before it, and so on, wrapping to
     // the later (future, background-only) chunks last: the heavy blocks go
     // first and the light ones fill the tail.
-    const int tile = blockIdx.x;
+    const int tile = c.t0 + blockIdx.x;
     const int chunk = (tile / c.g.chunk_tiles - (int)blockIdx.y + c.g.n_chunks) % c.g.n_chunks;
     const int i = tile * TILE + threadIdx.x;
     const int npad = c.g.npad;
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(TILE, 4) row32_kernel(Consts c, Workspace ws) 
 }
 
 cudaError_t launch_row32(const Consts &c, const Workspace &ws, cudaStream_t s) {
-    const dim3 grid(c.g.tiles, c.g.n_chunks);
+    const dim3 grid(c.t1 - c.t0, c.g.n_chunks);
     if (c.band) {
         if (c.mode == MODE_HESS) row32_kernel<MODE_HESS, true><<<grid, TILE, 0, s>>>(c, ws);
         else if (c.mode == MODE_GRAD) row32_kernel<MODE_GRAD, true><<<grid, TILE, 0, s>>>(c, ws);
