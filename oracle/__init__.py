@@ -30,6 +30,13 @@ _lib = None
 NPAR = 6
 
 
+def build_all(force: bool = False):
+    """Compile every C part of the oracle (the likelihood and the tree prior)."""
+    from . import tree_oracle
+    build(force)
+    tree_oracle.build(force)
+
+
 def build(force: bool = False, src: str = _SRC, so: str = _SO) -> str:
     """Compile the C oracle (default: oracle/_build/liboracle.so; idempotent)."""
     os.makedirs(os.path.dirname(so), exist_ok=True)

@@ -1,14 +1,17 @@
-"""FP64 NumPy oracle of the phylogenetic Brownian prior (Section 2.2, Eq. 2).
+"""Oracle of the phylogenetic Brownian prior (Section 2.2, Eq. 2).
 
 TEST INFRASTRUCTURE: used only by the tests and the bench's CPU legs.
 
 The tips' latent values z are N(0, sigma^2 V).  V_ij is the root variance
 scalar plus the length of the root path that tips i and j share (the time
 from the root to their most recent common ancestor); V_ii is the root
-variance plus the whole root-to-tip path (Section 2.2).  This module writes V
-out entry by entry from that definition, then evaluates Eq. 2 and its
-derivatives with dense linear algebra, the O(M^3) route that Section 2.3.1's
-dynamic programme avoids.
+variance plus the whole root-to-tip path (Section 2.2).  ``tree_cov`` writes V
+out from that definition in NumPy; ``tree_prior`` evaluates Eq. 2 and its
+derivatives by dense algebra on V (the O(M^3) route that Section 2.3.1's
+dynamic programme avoids) in ``tree_oracle.c``, in long double: coalescent
+trees have tip branches of ~1e-7 under a height of ~1, so V's condition number
+reaches ~1e9 and FP64 dense algebra would lose the last digits that the
+comparison needs.
 
 Tree encoding: nodes 0..M-1 are the tips in the order of z, nodes M..2M-2 are
 internal, parent[v] = -1 at the root, length[v] = branch length from v to its
@@ -16,7 +19,43 @@ parent.
 """
 from __future__ import annotations
 
+import ctypes
+import os
+import subprocess
+import threading
+
 import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tree_oracle.c")
+_SO = os.path.join(_HERE, "_build", "libtree_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                        "-std=c99", "-Wall", "-o", tmp, _SRC, "-lm"], check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            d, i64 = ctypes.POINTER(ctypes.c_double), ctypes.c_int64
+            l64 = ctypes.POINTER(ctypes.c_int64)
+            lib.tree_oracle_cov.argtypes = [i64, l64, d, ctypes.c_double, d]
+            lib.tree_oracle_cov.restype = ctypes.c_int
+            lib.tree_oracle_prior.argtypes = [i64, l64, d, ctypes.c_double, ctypes.c_double, d, d, d, d, d]
+            lib.tree_oracle_prior.restype = ctypes.c_int
+            _lib = lib
+    return _lib
 
 
 def root_path(parent, v):
@@ -29,8 +68,8 @@ def root_path(parent, v):
 
 
 def tree_cov(parent, length, root_var=0.0):
-    """V (M x M) from the definition: root_var + total length of the branches
-    that lie on both tips' root paths."""
+    """V (M x M, FP64) from the definition: root_var + total length of the
+    branches that lie on both tips' root paths."""
     parent = np.asarray(parent, np.int64)
     length = np.asarray(length, float)
     m = (parent.size + 1) // 2
@@ -42,18 +81,32 @@ def tree_cov(parent, length, root_var=0.0):
     return root_var + (on * length) @ on.T
 
 
+def _call(parent, length, root_var, sigma2, z, want_prec=False):
+    par = np.ascontiguousarray(parent, dtype=np.int64)
+    ln = np.ascontiguousarray(length, dtype=np.float64)
+    m = (par.size + 1) // 2
+    zz = np.ascontiguousarray(z, dtype=np.float64) if z is not None else None
+    ld = np.zeros(1)
+    pz, pd = np.zeros(m), np.zeros(m)
+    prec = np.zeros((m, m)) if want_prec else None
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None  # noqa: E731
+    rc = _load().tree_oracle_prior(m, par.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), dp(ln), float(root_var),
+                                   float(sigma2), dp(zz), dp(ld) if zz is not None else None,
+                                   dp(pz) if zz is not None else None, dp(pd), dp(prec))
+    if rc != 0:
+        raise np.linalg.LinAlgError("V is not positive definite or the tree is malformed")
+    return float(ld[0]), pz, pd, prec
+
+
 def tree_prior(z, parent, length, root_var, sigma2):
-    """(log N(z; 0, sigma2 V), (sigma2 V)^-1 z, diag((sigma2 V)^-1)) by dense algebra."""
-    z = np.asarray(z, float)
-    cov = sigma2 * tree_cov(parent, length, root_var)
-    m = z.size
-    sign, logdet = np.linalg.slogdet(cov)
-    if sign <= 0:
-        raise np.linalg.LinAlgError("V is not positive definite")
-    prec = np.linalg.inv(cov)
-    pz = prec @ z
-    logdens = -0.5 * m * np.log(2 * np.pi) - 0.5 * logdet - 0.5 * float(z @ pz)
-    return logdens, pz, np.diag(prec).copy()
+    """(log N(z; 0, sigma2 V), (sigma2 V)^-1 z, diag((sigma2 V)^-1)), dense, in long double."""
+    ld, pz, pd, _ = _call(parent, length, root_var, sigma2, z)
+    return ld, pz, pd
+
+
+def precision_matrix(parent, length, root_var=0.0, sigma2=1.0):
+    """(sigma2 V)^-1 (M x M), computed in long double and rounded to FP64."""
+    return _call(parent, length, root_var, sigma2, None, want_prec=True)[3]
 
 
 def simulate(rng, parent, length, root_var, sigma2, n_draws):

@@ -78,7 +78,7 @@ def tree_fixture():
     parent, length = tree9()
     z = np.array([0.4, 0.1, -0.8, 1.3, 1.1, -0.2, 0.6, 0.7, -1.5])
     tau0, s2 = 0.25, 1.8
-    ld, pz, pd = tree_oracle.tree_prior(z, parent, length, tau0, s2)
+    ld, pz, pd = tree_oracle.tree_prior(z, parent, length, tau0, s2)  # long double dense algebra
     write("tree_prior_m9.json", {
         "source": "Section 2.2, Eq. 2: z ~ N(0, sigma^2 V), V_ij = root variance + shared root-path length",
         "inputs": {"parent": [int(v) for v in parent], "length": lst(length), "z": lst(z), "root_var": tau0,
@@ -91,7 +91,7 @@ def posterior_fixture():
     x, y, t, r, params = uniform_events(n=48, seed=7)
     parent, length = tree9()
     seq = np.array([1, 4, 9, 13, 20, 26, 31, 40, 45])
-    prec = np.linalg.inv(tree_oracle.tree_cov(parent, length, 0.0))
+    prec = tree_oracle.precision_matrix(parent, length)
     # the Section 3.2 priors in km and days (kinds 0 = gamma(shape, rate), 1 = inverse gamma(shape, scale))
     kind = [0, 1, 1, 0, 0, 1]
     a = [2.0, 1.0, 2.0, 1.0, 2.0, 2.0]

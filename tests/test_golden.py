@@ -56,7 +56,7 @@ def test_oracle_reproduces_tree_fixture():
 def test_oracle_reproduces_posterior_fixture():
     g = load("posterior_n48_m9.json")
     i, e = g["inputs"], g["expected"]
-    prec = np.linalg.inv(tree_oracle.tree_cov(np.array(i["tree_parent"]), np.array(i["tree_length"]), 0.0))
+    prec = tree_oracle.precision_matrix(np.array(i["tree_parent"]), np.array(i["tree_length"]))
     prior = (np.array(i["prior_kind"]), np.array(i["prior_a"]), np.array(i["prior_b"]))
     lp, gq, hq = hmc_oracle.log_posterior(np.array(i["x"]), np.array(i["y"]), np.array(i["t"]), np.array(i["r"]),
                                           np.array(i["seq"]), prec, prior, np.array(i["q"]))

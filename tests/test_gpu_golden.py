@@ -62,7 +62,7 @@ def test_posterior_fixture(prior_form):
     seq = torch.tensor(i["seq"], device="cuda")
     if prior_form == "dense":
         from oracle import tree_oracle  # the dense precision is an input here, built by the definition
-        prec = np.linalg.inv(tree_oracle.tree_cov(np.array(i["tree_parent"]), np.array(i["tree_length"]), 0.0))
+        prec = tree_oracle.precision_matrix(np.array(i["tree_parent"]), np.array(i["tree_length"]))
         post = hmc.Posterior(dev(i["x"]), dev(i["y"]), dev(i["t"]), dev(i["r"]), seq, dev(prec), prior, "fp64")
     else:
         tp = tree.TreePrior(i["tree_parent"], i["tree_length"], 0.0, 1.0)
