@@ -1,10 +1,12 @@
 """Preconditioned HMC over the phylogenetic Hawkes posterior, reported as ESS/s.
 
     python -m paper_2103_03348_b300.run_hmc [--precision fp32c|fp64] [--iters 2000] [--warmup 200]
+                                            [--prior tree|dense]
 
 Workload: the 23,422-event synthetic pattern with 1,610 sequenced events whose
-log-rates are free (tree covariance from the generator's coalescent tree,
-sigma^2 = 1), the six globals on the log scale, 20 leapfrog steps per iteration,
+log-rates are free (the phylogenetic prior on the generator's coalescent tree,
+sigma^2 = 1, root variance 0, applied in O(M) on the tree, or through its dense
+precision matrix with --prior dense), the six globals on the log scale, 20 leapfrog steps per iteration,
 mass matrix refreshed every 100 iterations from the Hessian diagonal (Section
 2.3.2), start at the generating values.  Prints one JSON line with the
 acceptance rate, sampling time, and min/median/max ESS and ESS/s for the six
@@ -19,17 +21,21 @@ import time
 import numpy as np
 import torch
 
-from . import build, hmc, synth
+from . import build, hmc, synth, tree
 
 
 def run(precision="fp32c", iters=2000, warmup=200, n_steps=20, mass_every=100, eps0=0.05, seed=0, n=23422,
-        m_seq=1610, device="cuda"):
+        m_seq=1610, device="cuda", prior="tree"):
     build.build()
     w = synth.make_ebola_like(n=n, m_seq=m_seq)
-    prec = np.linalg.inv(w.tree_cov)
     d = lambda a: torch.tensor(np.asarray(a, float), dtype=torch.float64, device=device)  # noqa: E731
-    post = hmc.Posterior(d(w.x), d(w.y), d(w.t), d(w.r), torch.tensor(w.sequenced, device=device), d(prec),
-                         hmc.prior_km_days(), precision)
+    seq = torch.tensor(w.sequenced, device=device)
+    if prior == "tree":
+        tp = tree.TreePrior(w.tree_parent, w.tree_length, 0.0, 1.0, device=device)
+        post = hmc.Posterior(d(w.x), d(w.y), d(w.t), d(w.r), seq, None, hmc.prior_km_days(), precision, tree=tp)
+    else:
+        prec = np.linalg.inv(w.tree_cov)
+        post = hmc.Posterior(d(w.x), d(w.y), d(w.t), d(w.r), seq, d(prec), hmc.prior_km_days(), precision)
     q0 = d(np.concatenate([np.log(w.params), w.r[w.sequenced]]))
     t0 = time.perf_counter()
     ch = hmc.sample(post, q0, n_iter=iters, n_warmup=warmup, n_steps=n_steps, eps0=eps0, mass_every=mass_every,
@@ -44,6 +50,7 @@ def run(precision="fp32c", iters=2000, warmup=200, n_steps=20, mass_every=100, e
     calls = ch.grad_calls + ch.hess_calls
     return {
         "workload": w.name, "n_events": w.n, "n_rates": int(len(w.sequenced)), "precision": precision,
+        "phylogenetic_prior": prior,
         "iters": iters, "warmup": warmup, "leapfrog_steps": n_steps, "mass_every": mass_every,
         "step_size": ch.eps, "accept_rate": float(ch.accept.mean()),
         "sampling_seconds": ch.seconds, "warmup_seconds": ch.warmup_seconds, "total_seconds": total,
@@ -63,8 +70,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--prior", default="tree", choices=["tree", "dense"])
     a = ap.parse_args()
-    print(json.dumps(run(a.precision, a.iters, a.warmup, a.steps, seed=a.seed)), flush=True)
+    print(json.dumps(run(a.precision, a.iters, a.warmup, a.steps, seed=a.seed, prior=a.prior)), flush=True)
 
 
 if __name__ == "__main__":
