@@ -307,6 +307,50 @@ int hawkes_posterior_tree(int64_t n, int64_t m, const int *seq_idx, const int *p
                           size_t ws_bytes, double *logpost, double *grad_q, double *hdiag_q, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Posterior-predictive simulation (the forward simulation proposed in the
+ * paper's Discussion: exact simulation of the Hawkes process with exponential
+ * temporal trigger, run in parallel over posterior parameter settings with
+ * counter-based random numbers).  For each of n_samples parameter settings,
+ * the events of (T0, T0 + horizon], T0 = max t, are drawn exactly from the
+ * intensity of Section 2.1 conditioned on the history, through the branching
+ * representation: background events seeded by each past event's kernel, the
+ * remaining children of past events (memorylessness of the exponential
+ * trigger), then generation after generation of children of new events
+ * (theta = 1 for new events).  Events are listed stage by stage, parent by
+ * parent, child by child, so the output does not depend on the launch.
+ * Random numbers: Philox4x32-10, key = seed, counter = (item, draw, stage,
+ * sample_offset + s); the same draws give the same events on any GPU.
+ * ------------------------------------------------------------------------ */
+#define HAWKES_PREDICTIVE_MAX_CAPACITY (1 << 24)
+
+/* Bytes of DEVICE workspace hawkes_predictive needs for n past events. */
+size_t hawkes_predictive_workspace_size(int64_t n);
+
+/*   x, y, t, r_base   DEVICE double[n]: the history (r_base the log-rates of
+ *                     unsequenced events; any order of t)
+ *   seq_idx           DEVICE int[m], distinct event indices of the sequenced events
+ *   q                 DEVICE double[n_samples * q_stride]: row s holds a
+ *                     parameter setting in sampler coordinates (log mu0,
+ *                     log tau_x, log tau_t, log theta0, log omega, log h,
+ *                     r of the m sequenced events); q_stride >= 6 + m
+ *   horizon > 0, seed, sample_offset (added to s in the random counter)
+ *   capacity          events kept per sample, 1..HAWKES_PREDICTIVE_MAX_CAPACITY
+ *   out_x, out_y, out_t  DEVICE double[n_samples * capacity], row s at s * capacity
+ *   out_src           DEVICE int64[n_samples * capacity]: -(n'+1) for background
+ *                     seeded by past event n', n for a child of past event n,
+ *                     n + e for a child of the sample's own event e
+ *   out_count         DEVICE int64[n_samples]: events written
+ *   out_status        DEVICE int[n_samples]: 0 complete; 1 the capacity was
+ *                     reached (the first `capacity` events are written); 2 the
+ *                     parameters are not finite and positive (tau_t may be +inf)
+ * Enqueued on stream; HAWKES_EINVAL for bad arguments. */
+int hawkes_predictive(const double *x, const double *y, const double *t, const double *r_base, int64_t n,
+                      const int *seq_idx, int64_t m, const double *q, int64_t n_samples, int64_t q_stride,
+                      double horizon, uint64_t seed, uint32_t sample_offset, int64_t capacity, void *ws,
+                      size_t ws_bytes, double *out_x, double *out_y, double *out_t, int64_t *out_src,
+                      int64_t *out_count, int *out_status, void *stream);
+
+/* ------------------------------------------------------------------------
  * Learned gradient surrogate (the paper has none; the learned part of this
  * library): a 6 -> 128 -> 128 -> 6 tanh MLP with BF16 weights and FP32
  * accumulation, mapping standardised log-globals to the standardised gradient

@@ -1,0 +1,367 @@
+// Posterior-predictive simulation: the events of (T0, T0 + H] drawn exactly
+// from the intensity of Section 2.1 conditioned on the history, for many
+// parameter settings at once (one block per posterior draw), as the paper's
+// Discussion proposes (exact simulation exploiting the exponential temporal
+// trigger, parallel over parameter settings, counter-based random numbers).
+//
+// Branching representation, listed stage by stage, parent by parent:
+//   stage 0  past event n' seeds Poisson(mu0 m_n') background events,
+//            m_n' = Q((T0 - t_n')/tau_t) - Q((T1 - t_n')/tau_t) (H if tau_t is
+//            infinite, Q the normal upper tail), at N(t_n', tau_t^2) truncated
+//            to the window (uniform if tau_t is infinite), placed at
+//            (x_n', y_n') + tau_x N(0, I);
+//   stage 1  past event n has Poisson(theta0 theta_n e^{-omega (T0 - t_n)}
+//            (1 - e^{-omega H})) children at T0 + Exp(omega) truncated to
+//            (0, H] (memorylessness), placed at (x_n, y_n) + h N(0, I);
+//   stage g  every event e of the previous generation (theta = 1) has
+//            Poisson(theta0 (1 - e^{-omega (T1 - t_e)})) children at
+//            t_e + Exp(omega) truncated to (0, T1 - t_e], at (x_e, y_e) + h N(0, I).
+// Each chunk of 256 items draws its counts, takes a block-wide exclusive scan
+// for the output offsets, and writes its children in order, so the output is
+// independent of the launch shape.
+//
+// Random numbers: Philox4x32-10 (Salmon et al. 2011, written here from its
+// definition), key = 64-bit seed, counter = (item, draw, stage, sample).
+// Draw 0 decides an item's count; draws 2k+1 and 2k+2 give child k its time
+// and place.  Uniforms (a 2^26 + b + 1/2) 2^-53, a = w0 >> 5, b = w1 >> 6.
+// A Poisson mean above 500 is drawn as ceil(mean/500) equal parts (draws
+// 2^31 + p); a mean above four times the capacity saturates the count, which
+// makes the sample report an overflow with its first `capacity` events.
+#include "hawkes_internal.cuh"
+
+namespace hk {
+
+constexpr int PRED_THREADS = 256;
+constexpr double POISSON_PART = 500.0;
+constexpr uint32_t PART_DRAW = 0x80000000u;
+
+struct PhiloxOut {
+    uint32_t w0, w1, w2, w3;
+};
+
+__device__ __forceinline__ PhiloxOut philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                                   uint32_t k1) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        if (i > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        const uint32_t hi0 = __umulhi(M0, c0), lo0 = M0 * c0;
+        const uint32_t hi1 = __umulhi(M1, c2), lo1 = M1 * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return {c0, c1, c2, c3};
+}
+
+__device__ __forceinline__ double u53(uint32_t w0, uint32_t w1) {
+    return ((double)(w0 >> 5) * 67108864.0 + (double)(w1 >> 6) + 0.5) / 9007199254740992.0;
+}
+
+struct Rng {
+    uint32_t k0, k1, sample;
+    __device__ __forceinline__ void two(uint32_t item, uint32_t draw, uint32_t stage, double &a, double &b) const {
+        const PhiloxOut w = philox4x32_10(item, draw, stage, sample, k0, k1);
+        a = u53(w.w0, w.w1);
+        b = u53(w.w2, w.w3);
+    }
+};
+
+// The smallest k with u <= P(K <= k), K ~ Poisson(lam).
+__device__ int64_t poisson_inv(double lam, double u) {
+    if (!(lam > 0.0)) return 0;
+    if (u <= 1.0 - lam) return 0;  // P(K = 0) = e^-lam > 1 - lam
+    double p = exp(-lam), f = p;
+    int64_t k = 0;
+    while (u > f) {
+        ++k;
+        p *= lam / (double)k;
+        f += p;
+        if (p == 0.0 && (double)k > lam) break;
+    }
+    return k;
+}
+
+__device__ int64_t poisson_count(double lam, const Rng &rng, uint32_t item, uint32_t stage, int64_t cap) {
+    if (!(lam > 0.0)) return 0;
+    if (lam > 4.0 * (double)cap) return cap + 1;
+    double u, unused;
+    if (lam <= POISSON_PART) {
+        rng.two(item, 0u, stage, u, unused);
+        return poisson_inv(lam, u);
+    }
+    const int64_t parts = (int64_t)ceil(lam / POISSON_PART);
+    const double sub = lam / (double)parts;
+    int64_t k = 0;
+    for (int64_t j = 0; j < parts; ++j) {
+        rng.two(item, PART_DRAW + (uint32_t)j, stage, u, unused);
+        k += poisson_inv(sub, u);
+    }
+    return k;
+}
+
+__device__ __forceinline__ double upper_tail(double z) { return 0.5 * erfc(z / 1.4142135623730951); }
+
+struct PredArgs {
+    const double *x, *y, *t, *r_base;
+    const int *seq_pos;  // [n]: position among the sequenced events, or -1
+    const double *t0p;   // [1]: T0 = max t
+    int64_t n, m;
+    const double *q;
+    int64_t q_stride;
+    double horizon;
+    uint32_t k0, k1, sample_offset;
+    int64_t cap;
+    double *ox, *oy, *ot;
+    int64_t *osrc, *ocount;
+    int *ostatus;
+};
+
+// inclusive-exclusive block scan of per-thread counts; returns the exclusive
+// prefix and writes the block total into *total
+__device__ int64_t block_scan(int64_t v, int64_t *sh, int64_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t nb = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += nb;
+    }
+    if (lane == 31) sh[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = lane < PRED_THREADS / 32 ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t nb = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += nb;
+        }
+        if (lane < PRED_THREADS / 32) sh[lane] = w;  // inclusive warp prefix
+    }
+    __syncthreads();
+    const int64_t before = (warp > 0 ? sh[warp - 1] : 0) + incl - v;
+    *total = sh[PRED_THREADS / 32 - 1];
+    __syncthreads();
+    return before;
+}
+
+__global__ void __launch_bounds__(PRED_THREADS) predictive_kernel(PredArgs a) {
+    __shared__ int64_t sh_scan[PRED_THREADS / 32];
+    __shared__ int64_t s_count;
+    __shared__ int s_status;
+    const int64_t s = blockIdx.x;
+    const double *qs = a.q + s * a.q_stride;
+    const size_t row = (size_t)s * (size_t)a.cap;
+    double *ox = a.ox + row, *oy = a.oy + row, *ot = a.ot + row;
+    int64_t *osrc = a.osrc + row;
+    const Rng rng{a.k0, a.k1, a.sample_offset + (uint32_t)s};
+
+    const double mu0 = exp(qs[0]), tx = exp(qs[1]), tt = exp(qs[2]), th0 = exp(qs[3]), om = exp(qs[4]),
+                 h = exp(qs[5]);
+    const bool ok = isfinite(mu0) && mu0 > 0 && isfinite(tx) && tx > 0 && tt > 0 && !isnan(tt) && isfinite(th0) &&
+                    th0 > 0 && isfinite(om) && om > 0 && isfinite(h) && h > 0;
+    if (threadIdx.x == 0) {
+        s_count = 0;
+        s_status = ok ? 0 : 2;
+    }
+    __syncthreads();
+    if (!ok) {
+        if (threadIdx.x == 0) {
+            a.ocount[s] = 0;
+            a.ostatus[s] = 2;
+        }
+        return;
+    }
+    const double t0 = *a.t0p, t1 = t0 + a.horizon, H = a.horizon;
+    const bool tt_inf = isinf(tt);
+    const double one_m_h = -expm1(-om * H);
+
+    // stages 0 and 1: one item per past event
+    for (int stage = 0; stage < 2; ++stage) {
+        for (int64_t c0 = 0; c0 < a.n; c0 += PRED_THREADS) {
+            const int64_t i = c0 + threadIdx.x;
+            int64_t K = 0;
+            double lam = 0.0, qa = 0.0, qb = 0.0;
+            if (i < a.n) {
+                const double ti = a.t[i];
+                if (stage == 0) {
+                    if (tt_inf) {
+                        lam = mu0 * H;
+                    } else if ((t0 - ti) / tt <= 39.0) {  // beyond, both tails underflow to 0
+                        qa = upper_tail((t0 - ti) / tt);
+                        qb = upper_tail((t1 - ti) / tt);
+                        lam = mu0 * (qa - qb);
+                    }
+                } else {
+                    const int j = a.seq_pos[i];
+                    const double ri = j >= 0 ? qs[6 + j] : a.r_base[i];
+                    lam = th0 * exp(ri - om * (t0 - ti)) * one_m_h;
+                }
+                K = poisson_count(lam, rng, (uint32_t)i, (uint32_t)stage, a.cap);
+            }
+            int64_t total;
+            const int64_t off = block_scan(K, sh_scan, &total);
+            const int64_t base = s_count;
+            for (int64_t k = 0; k < K; ++k) {
+                const int64_t idx = base + off + k;
+                if (idx >= a.cap) break;
+                double u1, u2, u3, unused;
+                rng.two((uint32_t)i, (uint32_t)(2 * k + 1), (uint32_t)stage, u1, u2);
+                rng.two((uint32_t)i, (uint32_t)(2 * k + 2), (uint32_t)stage, u3, unused);
+                const double rad = sqrt(-2.0 * log(u2)), ang = 6.283185307179586 * u3;
+                const double sd = stage == 0 ? tx : h;
+                double tc;
+                if (stage == 0)
+                    tc = tt_inf ? t0 + u1 * H
+                                : a.t[i] + tt * (1.4142135623730951 * erfcinv(2.0 * (qa - u1 * (qa - qb))));
+                else
+                    tc = t0 - log1p(-u1 * one_m_h) / om;
+                ox[idx] = a.x[i] + sd * rad * cos(ang);
+                oy[idx] = a.y[i] + sd * rad * sin(ang);
+                ot[idx] = tc;
+                osrc[idx] = stage == 0 ? -(i + 1) : i;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                s_count = base + total < a.cap ? base + total : a.cap;
+                if (base + total > a.cap) s_status = 1;
+            }
+            __syncthreads();
+            if (s_status != 0) break;
+        }
+        if (s_status != 0) break;
+    }
+
+    // later generations: the items are the previous generation's events
+    int64_t gs = 0, ge = s_count;
+    for (uint32_t stage = 2; s_status == 0 && gs < ge; ++stage) {
+        for (int64_t c0 = gs; c0 < ge; c0 += PRED_THREADS) {
+            const int64_t e = c0 + threadIdx.x;
+            int64_t K = 0;
+            double et = 0.0, ex = 0.0, ey = 0.0, one_m = 0.0;
+            if (e < ge) {
+                et = ot[e];
+                ex = ox[e];
+                ey = oy[e];
+                one_m = -expm1(-om * (t1 - et));
+                K = poisson_count(th0 * one_m, rng, (uint32_t)e, stage, a.cap);
+            }
+            int64_t total;
+            const int64_t off = block_scan(K, sh_scan, &total);
+            const int64_t base = s_count;
+            for (int64_t k = 0; k < K; ++k) {
+                const int64_t idx = base + off + k;
+                if (idx >= a.cap) break;
+                double u1, u2, u3, unused;
+                rng.two((uint32_t)e, (uint32_t)(2 * k + 1), stage, u1, u2);
+                rng.two((uint32_t)e, (uint32_t)(2 * k + 2), stage, u3, unused);
+                const double rad = sqrt(-2.0 * log(u2)), ang = 6.283185307179586 * u3;
+                ox[idx] = ex + h * rad * cos(ang);
+                oy[idx] = ey + h * rad * sin(ang);
+                ot[idx] = et - log1p(-u1 * one_m) / om;
+                osrc[idx] = a.n + e;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                s_count = base + total < a.cap ? base + total : a.cap;
+                if (base + total > a.cap) s_status = 1;
+            }
+            __syncthreads();
+            if (s_status != 0) break;
+        }
+        gs = ge;
+        ge = s_count;
+    }
+    if (threadIdx.x == 0) {
+        a.ocount[s] = s_count;
+        a.ostatus[s] = s_status;
+    }
+}
+
+// seq_pos[n] = j for seq_idx[j] = n, else -1; t0 = max t (one block)
+__global__ void __launch_bounds__(1024) predictive_prep_kernel(const double *__restrict__ t, int64_t n,
+                                                              const int *__restrict__ seq_idx, int64_t m,
+                                                              int *__restrict__ seq_pos, double *__restrict__ t0) {
+    __shared__ double sh[32];
+    double mx = -INFINITY;
+    for (int64_t i = threadIdx.x; i < n; i += 1024) {
+        seq_pos[i] = -1;
+        mx = fmax(mx, t[i]);
+    }
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < m; j += 1024) {
+        const int i = seq_idx[j];
+        if (i >= 0 && i < n) seq_pos[i] = (int)j;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        mx = sh[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (threadIdx.x == 0) *t0 = mx;
+    }
+}
+
+}  // namespace hk
+
+extern "C" {
+
+size_t hawkes_predictive_workspace_size(int64_t n) {
+    if (n < 1 || n > HAWKES_MAX_EVENTS) return 0;
+    return (((size_t)n * sizeof(int) + 255) & ~(size_t)255) + 256;
+}
+
+int hawkes_predictive(const double *x, const double *y, const double *t, const double *r_base, int64_t n,
+                      const int *seq_idx, int64_t m, const double *q, int64_t n_samples, int64_t q_stride,
+                      double horizon, uint64_t seed, uint32_t sample_offset, int64_t capacity, void *ws,
+                      size_t ws_bytes, double *out_x, double *out_y, double *out_t, int64_t *out_src,
+                      int64_t *out_count, int *out_status, void *stream) {
+    if (n < 1 || n > HAWKES_MAX_EVENTS || m < 0 || m > n || n_samples < 0 || n_samples > 0x7fffffff) return HAWKES_EINVAL;
+    if (!x || !y || !t || !r_base || (m > 0 && !seq_idx) || !ws || !out_count || !out_status) return HAWKES_EINVAL;
+    if (n_samples > 0 && (!q || !out_x || !out_y || !out_t || !out_src)) return HAWKES_EINVAL;
+    if (q_stride < 6 + m || capacity < 1 || capacity > HAWKES_PREDICTIVE_MAX_CAPACITY) return HAWKES_EINVAL;
+    if (!(horizon > 0) || !isfinite(horizon)) return HAWKES_EINVAL;
+    if ((uint64_t)n_samples + sample_offset > 0x100000000ull) return HAWKES_EINVAL;  // sample counters stay distinct
+    if (((uintptr_t)ws & 255) != 0) return HAWKES_EINVAL;
+    if (ws_bytes < hawkes_predictive_workspace_size(n)) return HAWKES_EWORKSPACE;
+    if (n_samples == 0) return HAWKES_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    int *seq_pos = (int *)ws;
+    double *t0 = (double *)((char *)ws + (((size_t)n * sizeof(int) + 255) & ~(size_t)255));
+    hk::predictive_prep_kernel<<<1, 1024, 0, s>>>(t, n, seq_idx, m, seq_pos, t0);
+    if (cudaGetLastError() != cudaSuccess) return HAWKES_ECUDA;
+    hk::PredArgs a;
+    a.x = x;
+    a.y = y;
+    a.t = t;
+    a.r_base = r_base;
+    a.seq_pos = seq_pos;
+    a.t0p = t0;
+    a.n = n;
+    a.m = m;
+    a.q = q;
+    a.q_stride = q_stride;
+    a.horizon = horizon;
+    a.k0 = (uint32_t)(seed & 0xffffffffu);
+    a.k1 = (uint32_t)(seed >> 32);
+    a.sample_offset = sample_offset;
+    a.cap = capacity;
+    a.ox = out_x;
+    a.oy = out_y;
+    a.ot = out_t;
+    a.osrc = out_src;
+    a.ocount = out_count;
+    a.ostatus = out_status;
+    hk::predictive_kernel<<<(unsigned)n_samples, hk::PRED_THREADS, 0, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
+}
+
+}  // extern "C"

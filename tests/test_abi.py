@@ -105,3 +105,28 @@ def test_kernel_count_per_call():
     assert hawkes.kernels_per_call("hess", "fp32c") == 10
     assert hawkes.kernels_per_call("grad", "fp64") == 9
     assert hawkes.kernels_per_call("loglik", "fp32c") == 8
+
+
+def test_predictive_argument_checks(L):
+    """hawkes_predictive refuses bad arguments before touching any pointer."""
+    from paper_2103_03348_b300 import predictive
+    P = predictive._lib()
+    f = ctypes.c_void_p(1 << 20)
+    ws = ctypes.c_size_t(1 << 30)
+    good = dict(n=100, m=5, ns=4, stride=11, horizon=10.0, cap=1000)
+
+    def call(**kw):
+        a = dict(good, **kw)
+        return P.hawkes_predictive(f, f, f, f, a["n"], f, a["m"], f, a["ns"], a["stride"], a["horizon"], 1, 0,
+                                   a["cap"], f, ws, f, f, f, f, f, f, None)
+
+    assert P.hawkes_predictive_workspace_size(0) == 0
+    assert P.hawkes_predictive_workspace_size(100) >= 400
+    assert call(n=0) == hawkes.EINVAL
+    assert call(m=101) == hawkes.EINVAL
+    assert call(stride=10) == hawkes.EINVAL            # q rows shorter than 6 + m
+    assert call(horizon=0.0) == hawkes.EINVAL
+    assert call(horizon=math.inf) == hawkes.EINVAL
+    assert call(cap=0) == hawkes.EINVAL
+    assert call(cap=(1 << 24) + 1) == hawkes.EINVAL
+    assert call(ns=0) == hawkes.OK                     # nothing to do, nothing launched
