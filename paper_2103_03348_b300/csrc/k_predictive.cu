@@ -27,6 +27,14 @@
 // A Poisson mean above 500 is drawn as ceil(mean/500) equal parts (draws
 // 2^31 + p); a mean above four times the capacity saturates the count, which
 // makes the sample report an overflow with its first `capacity` events.
+//
+// Most past events have a tiny mean, and the count is 0 whenever
+// u <= 1 - mean.  So stages 0 and 1 first bound the mean from above in FP32
+// (the arguments rounded outward, and CUDA's documented error of expf and
+// erfcf, a few ulp, covered 200 times over).  If that bound already gives
+// K = 0 (bound < 2^-56, or u <= 1 - bound), the FP64 decision is the same and
+// the FP64 transcendental is skipped.  The outputs are identical to the
+// all-FP64 evaluation.
 #include "hawkes_internal.cuh"
 
 namespace hk {
@@ -106,6 +114,36 @@ __device__ int64_t poisson_count(double lam, const Rng &rng, uint32_t item, uint
 }
 
 __device__ __forceinline__ double upper_tail(double z) { return 0.5 * erfc(z / 1.4142135623730951); }
+
+// Relative slack for an FP32 exp / erfc value and its rounded argument, and
+// absolute slack covering FP32 underflow (the smallest subnormal).
+constexpr float UB_REL = 1.0e-4f;
+constexpr float UB_ABS = 1.5e-45f;
+constexpr double NEGLIGIBLE = 1.3877787807814457e-17;  // 2^-56: 1 - mean rounds to 1
+
+// Upper bound of exp(arg) for an FP64 arg.
+__device__ __forceinline__ float exp_upper(double arg) {
+    const float a = (float)arg;
+    const float up = a + fabsf(a) * 2.4e-7f + 1.0e-30f;  // |rounding| <= 2^-24 |a|, rounded outward
+    return expf(up) * (1.0f + UB_REL) + UB_ABS;
+}
+
+// Upper bound of Q(z) = P(Z > z), z >= 0, for an FP64 z.
+__device__ __forceinline__ float upper_tail_upper(double z) {
+    const float a = (float)z;
+    const float lo = fmaxf(a - a * 2.4e-7f - 1.0e-30f, 0.0f) * 0.70710677f * (1.0f - 2.4e-7f);
+    return 0.5f * erfcf(lo) * (1.0f + UB_REL) + UB_ABS;
+}
+
+// K = 0 is certain for a mean below `bound` when the bound says so; the
+// caller then skips the FP64 mean.  Draws u only when it is needed.
+__device__ __forceinline__ bool surely_zero(double bound, const Rng &rng, uint32_t item, uint32_t stage) {
+    if (!(bound <= POISSON_PART)) return false;  // inf / NaN / large: decide in FP64
+    if (bound < NEGLIGIBLE) return true;
+    double u, unused;
+    rng.two(item, 0u, stage, u, unused);
+    return u <= 1.0 - bound;
+}
 
 struct PredArgs {
     const double *x, *y, *t, *r_base;
@@ -189,20 +227,27 @@ __global__ void __launch_bounds__(PRED_THREADS) predictive_kernel(PredArgs a) {
             double lam = 0.0, qa = 0.0, qb = 0.0;
             if (i < a.n) {
                 const double ti = a.t[i];
+                bool zero = false;
                 if (stage == 0) {
                     if (tt_inf) {
                         lam = mu0 * H;
                     } else if ((t0 - ti) / tt <= 39.0) {  // beyond, both tails underflow to 0
-                        qa = upper_tail((t0 - ti) / tt);
-                        qb = upper_tail((t1 - ti) / tt);
-                        lam = mu0 * (qa - qb);
+                        const double za = (t0 - ti) / tt;
+                        zero = surely_zero(mu0 * (double)upper_tail_upper(za) * (1.0 + 1e-12), rng, (uint32_t)i, 0u);
+                        if (!zero) {
+                            qa = upper_tail(za);
+                            qb = upper_tail((t1 - ti) / tt);
+                            lam = mu0 * (qa - qb);
+                        }
                     }
                 } else {
                     const int j = a.seq_pos[i];
                     const double ri = j >= 0 ? qs[6 + j] : a.r_base[i];
-                    lam = th0 * exp(ri - om * (t0 - ti)) * one_m_h;
+                    const double arg = ri - om * (t0 - ti);
+                    zero = surely_zero(th0 * (double)exp_upper(arg) * one_m_h * (1.0 + 1e-12), rng, (uint32_t)i, 1u);
+                    if (!zero) lam = th0 * exp(arg) * one_m_h;
                 }
-                K = poisson_count(lam, rng, (uint32_t)i, (uint32_t)stage, a.cap);
+                if (!zero) K = poisson_count(lam, rng, (uint32_t)i, (uint32_t)stage, a.cap);
             }
             int64_t total;
             const int64_t off = block_scan(K, sh_scan, &total);
