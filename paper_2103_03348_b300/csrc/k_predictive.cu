@@ -30,11 +30,13 @@
 //
 // Most past events have a tiny mean, and the count is 0 whenever
 // u <= 1 - mean.  So stages 0 and 1 first bound the mean from above in FP32
-// (the arguments rounded outward, and CUDA's documented error of expf and
-// erfcf, a few ulp, covered 200 times over).  If that bound already gives
-// K = 0 (bound < 2^-56, or u <= 1 - bound), the FP64 decision is the same and
-// the FP64 transcendental is skipped.  The outputs are identical to the
-// all-FP64 evaluation.
+// and integer arithmetic only: arguments rounded outward with directed-rounding
+// intrinsics from per-event FP32 copies (T0 - t rounded down, r rounded up),
+// and CUDA's documented error of expf and erfcf (a few ulp) covered 200 times
+// over; 1 - u is bounded below from the random word in integers.  If the bound
+// already gives K = 0 (bound < 2^-56, or 1 - u >= bound), the FP64 decision is
+// the same and nothing in FP64 runs for that event.  The outputs are
+// identical to the all-FP64 evaluation.
 #include "hawkes_internal.cuh"
 
 namespace hk {
@@ -115,39 +117,46 @@ __device__ int64_t poisson_count(double lam, const Rng &rng, uint32_t item, uint
 
 __device__ __forceinline__ double upper_tail(double z) { return 0.5 * erfc(z / 1.4142135623730951); }
 
-// Relative slack for an FP32 exp / erfc value and its rounded argument, and
-// absolute slack covering FP32 underflow (the smallest subnormal).
+// Relative slack for an FP32 exp / erfc value, and absolute slack covering
+// FP32 underflow (the smallest subnormal).
 constexpr float UB_REL = 1.0e-4f;
 constexpr float UB_ABS = 1.5e-45f;
-constexpr double NEGLIGIBLE = 1.3877787807814457e-17;  // 2^-56: 1 - mean rounds to 1
+constexpr float NEGLIGIBLE = 1.3877787807814457e-17f;  // 2^-56: 1 - mean rounds to 1 in FP64
 
-// Upper bound of exp(arg) for an FP64 arg.
-__device__ __forceinline__ float exp_upper(double arg) {
-    const float a = (float)arg;
-    const float up = a + fabsf(a) * 2.4e-7f + 1.0e-30f;  // |rounding| <= 2^-24 |a|, rounded outward
-    return expf(up) * (1.0f + UB_REL) + UB_ABS;
+// Upper bound of 0.5 erfc(za / sqrt 2) for the FP64 path's za = fl((T0 - t) / tau_t),
+// from d_lo <= fl(T0 - t) and inv_tt_lo <= 1 / tau_t.
+__device__ __forceinline__ float tail_upper(float d_lo, float inv_tt_lo) {
+    const float za_lo = fmaxf(__fsub_rd(__fmul_rd(d_lo, inv_tt_lo), 1.0e-6f), 0.0f);
+    const float x_lo = __fmul_rd(za_lo, 0.70710677f);  // the FP32 constant is below 1/sqrt 2
+    return __fadd_ru(__fmul_ru(__fmul_ru(0.5f, erfcf(x_lo)), 1.0f + UB_REL), UB_ABS);
 }
 
-// Upper bound of Q(z) = P(Z > z), z >= 0, for an FP64 z.
-__device__ __forceinline__ float upper_tail_upper(double z) {
-    const float a = (float)z;
-    const float lo = fmaxf(a - a * 2.4e-7f - 1.0e-30f, 0.0f) * 0.70710677f * (1.0f - 2.4e-7f);
-    return 0.5f * erfcf(lo) * (1.0f + UB_REL) + UB_ABS;
+// Upper bound of exp(arg) for the FP64 path's arg = fl(r - omega fl(T0 - t)),
+// from r_up >= r, om_lo <= omega, d_lo <= fl(T0 - t); 1e-4 absorbs FP64 rounding.
+__device__ __forceinline__ float exp_upper(float r_up, float om_lo, float d_lo) {
+    const float arg = __fadd_ru(__fsub_ru(r_up, __fmul_rd(om_lo, d_lo)), 1.0e-4f);
+    return __fadd_ru(__fmul_ru(expf(arg), 1.0f + UB_REL), UB_ABS);
 }
 
-// K = 0 is certain for a mean below `bound` when the bound says so; the
-// caller then skips the FP64 mean.  Draws u only when it is needed.
-__device__ __forceinline__ bool surely_zero(double bound, const Rng &rng, uint32_t item, uint32_t stage) {
-    if (!(bound <= POISSON_PART)) return false;  // inf / NaN / large: decide in FP64
+// True when K = 0 is certain for every mean <= bound (so also for the FP64
+// mean): the bound is negligible, or 1 - u >= bound with 1 - u bounded below
+// from the random words in integers.  Decisions the bound cannot settle
+// (false) go to FP64.
+__device__ __forceinline__ bool surely_zero(float bound, const Rng &rng, uint32_t item, uint32_t stage) {
+    if (!(bound <= (float)POISSON_PART)) return false;  // inf / NaN / large
     if (bound < NEGLIGIBLE) return true;
-    double u, unused;
-    rng.two(item, 0u, stage, u, unused);
-    return u <= 1.0 - bound;
+    const PhiloxOut w = philox4x32_10(item, 0u, stage, rng.sample, rng.k0, rng.k1);
+    // u = (ab + 1/2) 2^-53 with ab = a 2^26 + b, so 1 - u >= (2^53 - 1 - ab) 2^-53
+    const uint64_t ab = ((uint64_t)(w.w0 >> 5) << 26) | (uint64_t)(w.w1 >> 6);
+    const float one_minus_u_lo = __ull2float_rd((1ull << 53) - 1ull - ab) * 1.1102230246251565e-16f;
+    return one_minus_u_lo >= bound;
 }
 
 struct PredArgs {
     const double *x, *y, *t, *r_base;
     const int *seq_pos;  // [n]: position among the sequenced events, or -1
+    const float *d_lo;   // [n]: T0 - t rounded down to FP32
+    const float *rb_up;  // [n]: r_base rounded up to FP32
     const double *t0p;   // [1]: T0 = max t
     int64_t n, m;
     const double *q;
@@ -218,6 +227,11 @@ __global__ void __launch_bounds__(PRED_THREADS) predictive_kernel(PredArgs a) {
     const double t0 = *a.t0p, t1 = t0 + a.horizon, H = a.horizon;
     const bool tt_inf = isinf(tt);
     const double one_m_h = -expm1(-om * H);
+    // outward-rounded FP32 constants for the bounds
+    const float mu0_up = __double2float_ru(mu0 * (1.0 + 1e-15)), th0_up = __double2float_ru(th0 * (1.0 + 1e-15));
+    const float omh_up = __double2float_ru(one_m_h * (1.0 + 1e-15)), om_lo = __double2float_rd(om * (1.0 - 1e-15));
+    const float inv_tt_lo = tt_inf ? 0.0f : __double2float_rd((1.0 / tt) * (1.0 - 1e-15));
+    const float bg_inf_up = __fmul_ru(mu0_up, __double2float_ru(H));
 
     // stages 0 and 1: one item per past event
     for (int stage = 0; stage < 2; ++stage) {
@@ -226,26 +240,30 @@ __global__ void __launch_bounds__(PRED_THREADS) predictive_kernel(PredArgs a) {
             int64_t K = 0;
             double lam = 0.0, qa = 0.0, qb = 0.0;
             if (i < a.n) {
-                const double ti = a.t[i];
-                bool zero = false;
+                const float d_lo = a.d_lo[i];
+                bool zero;
                 if (stage == 0) {
-                    if (tt_inf) {
-                        lam = mu0 * H;
-                    } else if ((t0 - ti) / tt <= 39.0) {  // beyond, both tails underflow to 0
-                        const double za = (t0 - ti) / tt;
-                        zero = surely_zero(mu0 * (double)upper_tail_upper(za) * (1.0 + 1e-12), rng, (uint32_t)i, 0u);
-                        if (!zero) {
-                            qa = upper_tail(za);
+                    const float bound = tt_inf ? bg_inf_up : __fmul_ru(mu0_up, tail_upper(d_lo, inv_tt_lo));
+                    zero = surely_zero(bound, rng, (uint32_t)i, 0u);
+                    if (!zero) {
+                        const double ti = a.t[i];
+                        if (tt_inf) {
+                            lam = mu0 * H;
+                        } else if ((t0 - ti) / tt <= 39.0) {  // beyond, both tails underflow to 0
+                            qa = upper_tail((t0 - ti) / tt);
                             qb = upper_tail((t1 - ti) / tt);
                             lam = mu0 * (qa - qb);
                         }
                     }
                 } else {
                     const int j = a.seq_pos[i];
-                    const double ri = j >= 0 ? qs[6 + j] : a.r_base[i];
-                    const double arg = ri - om * (t0 - ti);
-                    zero = surely_zero(th0 * (double)exp_upper(arg) * one_m_h * (1.0 + 1e-12), rng, (uint32_t)i, 1u);
-                    if (!zero) lam = th0 * exp(arg) * one_m_h;
+                    const float r_up = j >= 0 ? __double2float_ru(qs[6 + j]) : a.rb_up[i];
+                    zero = surely_zero(__fmul_ru(__fmul_ru(th0_up, exp_upper(r_up, om_lo, d_lo)), omh_up), rng,
+                                       (uint32_t)i, 1u);
+                    if (!zero) {
+                        const double ri = j >= 0 ? qs[6 + j] : a.r_base[i];
+                        lam = th0 * exp(ri - om * (t0 - a.t[i])) * one_m_h;
+                    }
                 }
                 if (!zero) K = poisson_count(lam, rng, (uint32_t)i, (uint32_t)stage, a.cap);
             }
@@ -355,13 +373,26 @@ __global__ void __launch_bounds__(1024) predictive_prep_kernel(const double *__r
     }
 }
 
+// d_lo[i] = T0 - t_i rounded down, rb_up[i] = r_base[i] rounded up (FP32)
+__global__ void predictive_pack_kernel(const double *__restrict__ t, const double *__restrict__ r_base, int64_t n,
+                                       const double *__restrict__ t0, float *__restrict__ d_lo,
+                                       float *__restrict__ rb_up) {
+    const double T0 = *t0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        d_lo[i] = __double2float_rd(T0 - t[i]);
+        rb_up[i] = __double2float_ru(r_base[i]);
+    }
+}
+
+static size_t seg(size_t bytes) { return (bytes + 255) & ~(size_t)255; }
+
 }  // namespace hk
 
 extern "C" {
 
 size_t hawkes_predictive_workspace_size(int64_t n) {
     if (n < 1 || n > HAWKES_MAX_EVENTS) return 0;
-    return (((size_t)n * sizeof(int) + 255) & ~(size_t)255) + 256;
+    return hk::seg((size_t)n * sizeof(int)) + 2 * hk::seg((size_t)n * sizeof(float)) + 256;
 }
 
 int hawkes_predictive(const double *x, const double *y, const double *t, const double *r_base, int64_t n,
@@ -379,9 +410,15 @@ int hawkes_predictive(const double *x, const double *y, const double *t, const d
     if (ws_bytes < hawkes_predictive_workspace_size(n)) return HAWKES_EWORKSPACE;
     if (n_samples == 0) return HAWKES_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    int *seq_pos = (int *)ws;
-    double *t0 = (double *)((char *)ws + (((size_t)n * sizeof(int) + 255) & ~(size_t)255));
+    char *base = (char *)ws;
+    int *seq_pos = (int *)base;
+    float *d_lo = (float *)(base + hk::seg((size_t)n * sizeof(int)));
+    float *rb_up = (float *)((char *)d_lo + hk::seg((size_t)n * sizeof(float)));
+    double *t0 = (double *)((char *)rb_up + hk::seg((size_t)n * sizeof(float)));
     hk::predictive_prep_kernel<<<1, 1024, 0, s>>>(t, n, seq_idx, m, seq_pos, t0);
+    if (cudaGetLastError() != cudaSuccess) return HAWKES_ECUDA;
+    const int pack_blocks = (int)((n + 255) / 256 < 1184 ? (n + 255) / 256 : 1184);
+    hk::predictive_pack_kernel<<<pack_blocks, 256, 0, s>>>(t, r_base, n, t0, d_lo, rb_up);
     if (cudaGetLastError() != cudaSuccess) return HAWKES_ECUDA;
     hk::PredArgs a;
     a.x = x;
@@ -389,6 +426,8 @@ int hawkes_predictive(const double *x, const double *y, const double *t, const d
     a.t = t;
     a.r_base = r_base;
     a.seq_pos = seq_pos;
+    a.d_lo = d_lo;
+    a.rb_up = rb_up;
     a.t0p = t0;
     a.n = n;
     a.m = m;
