@@ -393,38 +393,12 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
-def predictive_bench(dev, stream, n_samples=4096, horizon=30.0, capacity=8192):
+def predictive_bench(dev, stream):
     """Posterior-predictive simulation: 30 days ahead of the 23,422-event
     history with 1,610 free log-rates, for 4,096 posterior-like parameter
-    settings (the generating values plus N(0, 0.02^2) in sampler coordinates),
-    one block per setting; CUDA events around each batch."""
-    import torch
-    from paper_2103_03348_b300 import predictive
-    w2 = synth.make("ebola_like")
-    rng = np.random.default_rng(77)
-    q0 = np.concatenate([np.log(w2.params), w2.r[w2.sequenced]])
-    q = torch.tensor(q0[None, :] + 0.02 * rng.standard_normal((n_samples, q0.size)), dtype=torch.float64, device=dev)
-    d = lambda a: torch.tensor(np.asarray(a, float), dtype=torch.float64, device=dev)  # noqa: E731
-    x, y, t, r = d(w2.x), d(w2.y), d(w2.t), d(w2.r)
-    seq = torch.tensor(w2.sequenced, dtype=torch.int32, device=dev)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    times, out = [], None
-    for i in range(4):
-        ev[0].record(stream)
-        out = predictive.simulate(x, y, t, r, seq, q, horizon, 1000 + i, capacity)
-        ev[1].record(stream)
-        ev[1].synchronize()
-        if i > 0:
-            times.append(ev[0].elapsed_time(ev[1]))
-    ms = float(np.mean(times))
-    counts = out["count"].cpu().numpy()
-    status = out["status"].cpu().numpy()
-    return {"workload": f"{w2.name}: {w2.n} past events, {len(w2.sequenced)} free log-rates, {horizon:g} days ahead",
-            "samples": n_samples, "ms_per_batch": ms, "samples_per_s": n_samples / (ms * 1e-3),
-            "events_per_s": float(counts.sum()) / (ms * 1e-3), "mean_events_per_sample": float(counts.mean()),
-            "past_event_terms_per_s": 2.0 * w2.n * n_samples / (ms * 1e-3),
-            "overflowed_samples": int((status == 1).sum()), "capacity": capacity,
-            "rng": "Philox4x32-10, counter = (item, draw, stage, sample)"}
+    settings, one block per setting; CUDA events around each batch."""
+    from paper_2103_03348_b300 import run_predictive
+    return run_predictive.run(samples=4096, horizon=30.0, reps=3, device=str(dev))
 
 
 def main():
