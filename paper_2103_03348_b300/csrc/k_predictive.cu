@@ -146,9 +146,8 @@ __device__ __forceinline__ bool surely_zero(float bound, const Rng &rng, uint32_
     if (!(bound <= (float)POISSON_PART)) return false;  // inf / NaN / large
     if (bound < NEGLIGIBLE) return true;
     const PhiloxOut w = philox4x32_10(item, 0u, stage, rng.sample, rng.k0, rng.k1);
-    // u = (ab + 1/2) 2^-53 with ab = a 2^26 + b, so 1 - u >= (2^53 - 1 - ab) 2^-53
-    const uint64_t ab = ((uint64_t)(w.w0 >> 5) << 26) | (uint64_t)(w.w1 >> 6);
-    const float one_minus_u_lo = __ull2float_rd((1ull << 53) - 1ull - ab) * 1.1102230246251565e-16f;
+    // u = (a 2^26 + b + 1/2) 2^-53 with a < 2^27, b < 2^26, so 1 - u >= (2^27 - 1 - a) 2^-27
+    const float one_minus_u_lo = __uint2float_rd((1u << 27) - 1u - (w.w0 >> 5)) * 7.450580596923828e-09f;
     return one_minus_u_lo >= bound;
 }
 
@@ -197,8 +196,31 @@ __device__ int64_t block_scan(int64_t v, int64_t *sh, int64_t *total) {
     return before;
 }
 
+// Upper bound of 1 - e^{-x} for the FP64 path's x = fl(omega fl(T1 - t)):
+// min(x, 1 - expf(-x) + slack) at x rounded up (expf's few-ulp error on a
+// value <= 1 and the subtraction's rounding stay below 4e-7).
+__device__ __forceinline__ float one_minus_exp_upper(float x_up) {
+    return fminf(x_up, __fadd_ru(__fsub_ru(1.0f, expf(-x_up)), 4.0e-7f));
+}
+
+// Shared state of one chunk of PRED_THREADS items.
+struct Chunk {
+    int64_t off[PRED_THREADS + 1];        // exclusive prefix of the counts; off[PRED_THREADS] = total
+    int64_t k[PRED_THREADS];              // count of each item
+    double pa[PRED_THREADS], pb[PRED_THREADS];  // stage 0: the tails Q(za), Q(zb); later: 1 - e^{-omega (T1 - t_e)}
+    int queue[PRED_THREADS];              // items whose count the FP32 bound left undecided
+    int n_queue;
+    int64_t scan[PRED_THREADS / 32];
+};
+
+// Each chunk: (1) every thread bounds its item's mean in FP32 and settles
+// K = 0 or queues the item; (2) all threads take the queued items in turn for
+// the FP64 mean and the Poisson count; (3) a block scan gives the offsets;
+// (4) all threads take the children in turn, each finding its parent by
+// binary search over the offsets.  Lanes stay busy in the FP64 parts, and the
+// output order (item by item, child by child) does not depend on the launch.
 __global__ void __launch_bounds__(PRED_THREADS) predictive_kernel(PredArgs a) {
-    __shared__ int64_t sh_scan[PRED_THREADS / 32];
+    __shared__ Chunk C;
     __shared__ int64_t s_count;
     __shared__ int s_status;
     const int64_t s = blockIdx.x;
@@ -207,22 +229,22 @@ __global__ void __launch_bounds__(PRED_THREADS) predictive_kernel(PredArgs a) {
     double *ox = a.ox + row, *oy = a.oy + row, *ot = a.ot + row;
     int64_t *osrc = a.osrc + row;
     const Rng rng{a.k0, a.k1, a.sample_offset + (uint32_t)s};
+    const int tid = threadIdx.x;
 
     const double mu0 = exp(qs[0]), tx = exp(qs[1]), tt = exp(qs[2]), th0 = exp(qs[3]), om = exp(qs[4]),
                  h = exp(qs[5]);
     const bool ok = isfinite(mu0) && mu0 > 0 && isfinite(tx) && tx > 0 && tt > 0 && !isnan(tt) && isfinite(th0) &&
                     th0 > 0 && isfinite(om) && om > 0 && isfinite(h) && h > 0;
-    if (threadIdx.x == 0) {
-        s_count = 0;
-        s_status = ok ? 0 : 2;
-    }
-    __syncthreads();
     if (!ok) {
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             a.ocount[s] = 0;
             a.ostatus[s] = 2;
         }
-        return;
+        return;  // uniform across the block
+    }
+    if (tid == 0) {
+        s_count = 0;
+        s_status = 0;
     }
     const double t0 = *a.t0p, t1 = t0 + a.horizon, H = a.horizon;
     const bool tt_inf = isinf(tt);
@@ -230,117 +252,135 @@ __global__ void __launch_bounds__(PRED_THREADS) predictive_kernel(PredArgs a) {
     // outward-rounded FP32 constants for the bounds
     const float mu0_up = __double2float_ru(mu0 * (1.0 + 1e-15)), th0_up = __double2float_ru(th0 * (1.0 + 1e-15));
     const float omh_up = __double2float_ru(one_m_h * (1.0 + 1e-15)), om_lo = __double2float_rd(om * (1.0 - 1e-15));
+    const float om_up = __double2float_ru(om * (1.0 + 1e-15));
     const float inv_tt_lo = tt_inf ? 0.0f : __double2float_rd((1.0 / tt) * (1.0 - 1e-15));
     const float bg_inf_up = __fmul_ru(mu0_up, __double2float_ru(H));
+    __syncthreads();
 
-    // stages 0 and 1: one item per past event
-    for (int stage = 0; stage < 2; ++stage) {
-        for (int64_t c0 = 0; c0 < a.n; c0 += PRED_THREADS) {
-            const int64_t i = c0 + threadIdx.x;
-            int64_t K = 0;
-            double lam = 0.0, qa = 0.0, qb = 0.0;
-            if (i < a.n) {
-                const float d_lo = a.d_lo[i];
-                bool zero;
+    int64_t gs = 0, ge = 0;
+    for (uint32_t stage = 0; s_status == 0; ++stage) {
+        int64_t lo = 0, hi = a.n;  // stages 0 and 1: the past events
+        if (stage >= 2) {          // later stages: the previous generation of the sample's own events
+            lo = gs;
+            hi = ge;
+            if (lo >= hi) break;
+        }
+        for (int64_t c0 = lo; c0 < hi; c0 += PRED_THREADS) {
+            const int64_t item = c0 + tid;
+            if (tid == 0) C.n_queue = 0;
+            C.k[tid] = 0;
+            __syncthreads();
+            // (1) FP32 bound of the mean: K = 0 settled, or queued for FP64
+            if (item < hi) {
+                float bound;
                 if (stage == 0) {
-                    const float bound = tt_inf ? bg_inf_up : __fmul_ru(mu0_up, tail_upper(d_lo, inv_tt_lo));
-                    zero = surely_zero(bound, rng, (uint32_t)i, 0u);
-                    if (!zero) {
-                        const double ti = a.t[i];
-                        if (tt_inf) {
-                            lam = mu0 * H;
-                        } else if ((t0 - ti) / tt <= 39.0) {  // beyond, both tails underflow to 0
-                            qa = upper_tail((t0 - ti) / tt);
-                            qb = upper_tail((t1 - ti) / tt);
-                            lam = mu0 * (qa - qb);
-                        }
-                    }
+                    bound = tt_inf ? bg_inf_up : __fmul_ru(mu0_up, tail_upper(a.d_lo[item], inv_tt_lo));
+                } else if (stage == 1) {
+                    const int j = a.seq_pos[item];
+                    const float r_up = j >= 0 ? __double2float_ru(qs[6 + j]) : a.rb_up[item];
+                    bound = __fmul_ru(__fmul_ru(th0_up, exp_upper(r_up, om_lo, a.d_lo[item])), omh_up);
                 } else {
-                    const int j = a.seq_pos[i];
-                    const float r_up = j >= 0 ? __double2float_ru(qs[6 + j]) : a.rb_up[i];
-                    zero = surely_zero(__fmul_ru(__fmul_ru(th0_up, exp_upper(r_up, om_lo, d_lo)), omh_up), rng,
-                                       (uint32_t)i, 1u);
-                    if (!zero) {
-                        const double ri = j >= 0 ? qs[6 + j] : a.r_base[i];
-                        lam = th0 * exp(ri - om * (t0 - a.t[i])) * one_m_h;
-                    }
+                    const float x_up = __fmul_ru(om_up, __double2float_ru(t1 - ot[item]));
+                    bound = __fmul_ru(th0_up, __fmul_ru(one_minus_exp_upper(x_up), 1.0f + UB_REL));
                 }
-                if (!zero) K = poisson_count(lam, rng, (uint32_t)i, (uint32_t)stage, a.cap);
+                if (!surely_zero(bound, rng, (uint32_t)item, stage)) C.queue[atomicAdd(&C.n_queue, 1)] = tid;
             }
+            __syncthreads();
+            // (2) FP64 means and counts of the queued items
+            for (int qi = tid; qi < C.n_queue; qi += PRED_THREADS) {
+                const int slot = C.queue[qi];
+                const int64_t it = c0 + slot;
+                double lam = 0.0;
+                if (stage == 0) {
+                    double qa = 0.0, qb = 0.0;
+                    if (tt_inf) {
+                        lam = mu0 * H;
+                    } else if ((t0 - a.t[it]) / tt <= 39.0) {  // beyond, both tails underflow to 0
+                        qa = upper_tail((t0 - a.t[it]) / tt);
+                        qb = upper_tail((t1 - a.t[it]) / tt);
+                        lam = mu0 * (qa - qb);
+                    }
+                    C.pa[slot] = qa;
+                    C.pb[slot] = qb;
+                } else if (stage == 1) {
+                    const int j = a.seq_pos[it];
+                    const double ri = j >= 0 ? qs[6 + j] : a.r_base[it];
+                    lam = th0 * exp(ri - om * (t0 - a.t[it])) * one_m_h;
+                } else {
+                    const double one_m = -expm1(-om * (t1 - ot[it]));
+                    C.pa[slot] = one_m;
+                    lam = th0 * one_m;
+                }
+                C.k[slot] = poisson_count(lam, rng, (uint32_t)it, stage, a.cap);
+            }
+            __syncthreads();
+            // (3) offsets
             int64_t total;
-            const int64_t off = block_scan(K, sh_scan, &total);
+            const int64_t off = block_scan(C.k[tid], C.scan, &total);
+            C.off[tid] = off;
+            if (tid == 0) C.off[PRED_THREADS] = total;
+            __syncthreads();
+            // (4) children, spread over all threads
             const int64_t base = s_count;
-            for (int64_t k = 0; k < K; ++k) {
-                const int64_t idx = base + off + k;
-                if (idx >= a.cap) break;
+            const int64_t room = a.cap - base;
+            const int64_t todo = total < room ? total : room;
+            for (int64_t c = tid; c < todo; c += PRED_THREADS) {
+                int lo_j = 0, hi_j = PRED_THREADS;  // the last j with off[j] <= c
+                while (hi_j - lo_j > 1) {
+                    const int mid = (lo_j + hi_j) >> 1;
+                    if (C.off[mid] <= c) lo_j = mid;
+                    else hi_j = mid;
+                }
+                const int j = lo_j;
+                const int64_t it = c0 + j, kk = c - C.off[j], idx = base + c;
                 double u1, u2, u3, unused;
-                rng.two((uint32_t)i, (uint32_t)(2 * k + 1), (uint32_t)stage, u1, u2);
-                rng.two((uint32_t)i, (uint32_t)(2 * k + 2), (uint32_t)stage, u3, unused);
+                rng.two((uint32_t)it, (uint32_t)(2 * kk + 1), stage, u1, u2);
+                rng.two((uint32_t)it, (uint32_t)(2 * kk + 2), stage, u3, unused);
                 const double rad = sqrt(-2.0 * log(u2)), ang = 6.283185307179586 * u3;
-                const double sd = stage == 0 ? tx : h;
-                double tc;
-                if (stage == 0)
-                    tc = tt_inf ? t0 + u1 * H
-                                : a.t[i] + tt * (1.4142135623730951 * erfcinv(2.0 * (qa - u1 * (qa - qb))));
-                else
+                double px, py, tc, sd;
+                int64_t src;
+                if (stage == 0) {
+                    px = a.x[it];
+                    py = a.y[it];
+                    sd = tx;
+                    const double qa = C.pa[j], qb = C.pb[j];
+                    tc = tt_inf ? t0 + u1 * H : a.t[it] + tt * (1.4142135623730951 * erfcinv(2.0 * (qa - u1 * (qa - qb))));
+                    src = -(it + 1);
+                } else if (stage == 1) {
+                    px = a.x[it];
+                    py = a.y[it];
+                    sd = h;
                     tc = t0 - log1p(-u1 * one_m_h) / om;
-                ox[idx] = a.x[i] + sd * rad * cos(ang);
-                oy[idx] = a.y[i] + sd * rad * sin(ang);
+                    src = it;
+                } else {
+                    px = ox[it];
+                    py = oy[it];
+                    sd = h;
+                    tc = ot[it] - log1p(-u1 * C.pa[j]) / om;
+                    src = a.n + it;
+                }
+                ox[idx] = px + sd * rad * cos(ang);
+                oy[idx] = py + sd * rad * sin(ang);
                 ot[idx] = tc;
-                osrc[idx] = stage == 0 ? -(i + 1) : i;
+                osrc[idx] = src;
             }
             __syncthreads();
-            if (threadIdx.x == 0) {
-                s_count = base + total < a.cap ? base + total : a.cap;
-                if (base + total > a.cap) s_status = 1;
-            }
-            __syncthreads();
-            if (s_status != 0) break;
-        }
-        if (s_status != 0) break;
-    }
-
-    // later generations: the items are the previous generation's events
-    int64_t gs = 0, ge = s_count;
-    for (uint32_t stage = 2; s_status == 0 && gs < ge; ++stage) {
-        for (int64_t c0 = gs; c0 < ge; c0 += PRED_THREADS) {
-            const int64_t e = c0 + threadIdx.x;
-            int64_t K = 0;
-            double et = 0.0, ex = 0.0, ey = 0.0, one_m = 0.0;
-            if (e < ge) {
-                et = ot[e];
-                ex = ox[e];
-                ey = oy[e];
-                one_m = -expm1(-om * (t1 - et));
-                K = poisson_count(th0 * one_m, rng, (uint32_t)e, stage, a.cap);
-            }
-            int64_t total;
-            const int64_t off = block_scan(K, sh_scan, &total);
-            const int64_t base = s_count;
-            for (int64_t k = 0; k < K; ++k) {
-                const int64_t idx = base + off + k;
-                if (idx >= a.cap) break;
-                double u1, u2, u3, unused;
-                rng.two((uint32_t)e, (uint32_t)(2 * k + 1), stage, u1, u2);
-                rng.two((uint32_t)e, (uint32_t)(2 * k + 2), stage, u3, unused);
-                const double rad = sqrt(-2.0 * log(u2)), ang = 6.283185307179586 * u3;
-                ox[idx] = ex + h * rad * cos(ang);
-                oy[idx] = ey + h * rad * sin(ang);
-                ot[idx] = et - log1p(-u1 * one_m) / om;
-                osrc[idx] = a.n + e;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                s_count = base + total < a.cap ? base + total : a.cap;
-                if (base + total > a.cap) s_status = 1;
+            if (tid == 0) {
+                s_count = base + todo;
+                if (total > room) s_status = 1;
             }
             __syncthreads();
             if (s_status != 0) break;
         }
-        gs = ge;
-        ge = s_count;
+        if (stage == 1) {
+            gs = 0;
+            ge = s_count;
+        } else if (stage >= 2) {
+            gs = ge;
+            ge = s_count;
+        }
     }
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         a.ocount[s] = s_count;
         a.ostatus[s] = s_status;
     }
