@@ -243,6 +243,27 @@ int hawkes_posterior(int64_t n, int64_t m, const int *seq_idx, const double *pre
  * into the likelihood's full log-rate vector. */
 int hawkes_hmc_scatter_rates(int64_t m, const int *seq_idx, const double *q, double *r, void *stream);
 
+/* The time trend of Section 2.2, theta_s = exp(z_s + beta^T f(t_s)): the
+ * sampler state grows to q = (6 log globals, z[m], beta[k]) and the sequenced
+ * log-rates are r[seq_idx[j]] = z_j + sum_c F[j*k + c] beta_c, with F the
+ * DEVICE m x k matrix (row-major) of the fixed trend features f(t_s).
+ * hawkes_hmc_scatter_rates_trend writes those r (k = 0 is the plain scatter). */
+int hawkes_hmc_scatter_rates_trend(int64_t m, int k, const int *seq_idx, const double *F, const double *q,
+                                   double *r, void *stream);
+
+/* After hawkes_posterior or hawkes_posterior_tree on the same q (whose first
+ * 6 + m entries they handle, with z as the phylogenetic variable), adds the
+ * trend's part: log pi -= |beta|^2 / (2 beta_var) (prior beta ~ N(0, beta_var I)),
+ * grad_q[6+m+c] = sum_j F[j, c] dl/dr_{s_j} - beta_c / beta_var, and
+ * hdiag_q[6+m+c] = sum_j F[j, c]^2 d2l/dr_{s_j}^2 - 1 / beta_var.  The last is
+ * a preconditioner entry, not the exact second derivative: the cross terms
+ * d2l/dr_i dr_j (i != j) are not formed by the evaluation.  grad, hdiag are
+ * the likelihood's DEVICE outputs at r (NULL exactly when grad_q / hdiag_q
+ * are); logpost is updated in place.  Enqueued on stream; m >= 1, beta_var > 0. */
+int hawkes_posterior_add_trend(int64_t m, int k, const int *seq_idx, const double *F, double beta_var,
+                               const double *q, const double *grad, const double *hdiag, double *logpost,
+                               double *grad_q, double *hdiag_q, void *stream);
+
 /* Leapfrog pieces on DEVICE vectors of length k (Section 2.3.2, Hamilton's
  * equations with a diagonal mass matrix M, minv = 1/diag(M)):
  *   hawkes_hmc_momentum: p += a * g      (half or full momentum step, a = eps/2 or eps)

@@ -29,26 +29,40 @@ def log_prior_terms(p, kind, a, b):
     return lp, d1, d2
 
 
-def log_posterior(x, y, t, r_base, seq, prec, prior, q, want_hess=True):
-    """(log pi, grad_q[6+M], hdiag_q[6+M] or None) at q, with the likelihood from the oracle."""
+def log_posterior(x, y, t, r_base, seq, prec, prior, q, want_hess=True, trend=None, beta_var=1.0):
+    """(log pi, grad_q, hdiag_q or None) at q, with the likelihood from the oracle.
+
+    Without a trend q = (log p[6], z[M]) and the sequenced log-rates are r = z.
+    With trend = F ([M, K], the fixed trend features f(t) of the sequenced
+    events, Section 2.2) q = (log p[6], z[M], beta[K]), r_seq = z + F beta and
+    beta ~ N(0, beta_var I).  The beta entries of hdiag_q are the
+    preconditioner sum_j F_jk^2 d2l/dr_j^2 - 1/beta_var: the cross terms
+    d2l/dr_i dr_j (i != j) of the exact second derivative are not formed."""
     q = np.asarray(q, float)
     p = np.exp(q[:6])
     r = np.array(r_base, float)
     seq = np.asarray(seq, np.int64)
-    rs = q[6:]
-    r[seq] = rs
+    m = len(seq)
+    zs = q[6:6 + m]
+    beta = q[6 + m:]
+    F = np.zeros((m, 0)) if trend is None else np.asarray(trend, float).reshape(m, -1)
+    r[seq] = zs + F @ beta
     o = evaluate(x, y, t, r, p, want=2 if want_hess else 1)
     lp, d1, d2 = log_prior_terms(p, *prior)
-    Pr = prec @ rs if len(rs) else np.zeros(0)
-    logpost = o["loglik"] + np.sum(lp + q[:6]) - 0.5 * float(rs @ Pr)
-    g = np.empty(6 + len(rs))
+    Pz = prec @ zs if m else np.zeros(0)
+    logpost = o["loglik"] + np.sum(lp + q[:6]) - 0.5 * float(zs @ Pz) - 0.5 * float(beta @ beta) / beta_var
+    gr = o["grad"][6 + seq]
+    g = np.empty(q.size)
     g[:6] = p * (o["grad"][:6] + d1) + 1.0
-    g[6:] = o["grad"][6 + seq] - Pr
+    g[6:6 + m] = gr - Pz
+    g[6 + m:] = F.T @ gr - beta / beta_var
     h = None
     if want_hess:
-        h = np.empty(6 + len(rs))
+        hr = o["hdiag"][6 + seq]
+        h = np.empty(q.size)
         h[:6] = p * (o["grad"][:6] + d1) + p ** 2 * (o["hdiag"][:6] + d2)
-        h[6:] = o["hdiag"][6 + seq] - np.diag(prec)
+        h[6:6 + m] = hr - np.diag(prec)
+        h[6 + m:] = (F ** 2).T @ hr - 1.0 / beta_var
     return logpost, g, h
 
 

@@ -88,6 +88,49 @@ __global__ void scatter_rates_kernel(int64_t m, const int *__restrict__ seq, con
         r[seq[j]] = q[6 + j];
 }
 
+// r[seq[j]] = z_j + sum_c F[j, c] beta_c with z = q[6..6+m), beta = q[6+m..6+m+k):
+// the sequenced log-rates with the time trend of Section 2.2.
+__global__ void scatter_rates_trend_kernel(int64_t m, int k, const int *__restrict__ seq,
+                                           const double *__restrict__ F, const double *__restrict__ q,
+                                           double *__restrict__ r) {
+    const double *beta = q + 6 + m;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        double v = q[6 + j];
+        for (int c = 0; c < k; ++c) v += F[j * k + c] * beta[c];
+        r[seq[j]] = v;
+    }
+}
+
+// The trend coefficients' entries of the posterior, one block per coefficient c:
+//   d log pi / d beta_c = sum_j F[j, c] dl/dr_{s_j} - beta_c / beta_var,
+//   preconditioner      = sum_j F[j, c]^2 d2l/dr_{s_j}^2 - 1 / beta_var,
+// and block 0 adds the N(0, beta_var I) log prior to log pi.
+__global__ void __launch_bounds__(ASM_THREADS) trend_assemble_kernel(
+    int64_t m, int k, const int *__restrict__ seq, const double *__restrict__ F, double beta_var,
+    const double *__restrict__ q, const double *__restrict__ grad, const double *__restrict__ hdiag,
+    double *__restrict__ logpost, double *__restrict__ grad_q, double *__restrict__ hdiag_q) {
+    __shared__ double sh[ASM_THREADS];
+    const int c = blockIdx.x;
+    const double *beta = q + 6 + m;
+    double g = 0.0, h = 0.0;
+    for (int64_t j = threadIdx.x; j < m; j += ASM_THREADS) {
+        const double f = F[j * k + c];
+        if (grad) g += f * grad[6 + seq[j]];
+        if (hdiag) h += f * f * hdiag[6 + seq[j]];
+    }
+    g = block_sum<ASM_THREADS>(g, sh);
+    if (hdiag) h = block_sum<ASM_THREADS>(h, sh);
+    if (threadIdx.x == 0) {
+        if (grad_q) grad_q[6 + m + c] = g - beta[c] / beta_var;
+        if (hdiag_q) hdiag_q[6 + m + c] = h - 1.0 / beta_var;
+        if (c == 0) {
+            double quad = 0.0;
+            for (int i = 0; i < k; ++i) quad += beta[i] * beta[i];
+            *logpost -= 0.5 * quad / beta_var;
+        }
+    }
+}
+
 // p += a g
 __global__ void momentum_kernel(int64_t k, double *__restrict__ p, const double *__restrict__ g, double a) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < k; j += (int64_t)gridDim.x * blockDim.x)
@@ -182,6 +225,27 @@ int hawkes_posterior_tree(int64_t n, int64_t m, const int *seq_idx, const int *p
         return HAWKES_ECUDA;
     hk::posterior_assemble_kernel<<<1, hk::ASM_THREADS, 0, s>>>(m, pc, seq_idx, pd, 1, q, w, loglik, grad, hdiag,
                                                                 logpost, grad_q, hdiag_q);
+    return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
+}
+
+int hawkes_hmc_scatter_rates_trend(int64_t m, int k, const int *seq_idx, const double *F, const double *q, double *r,
+                                   void *stream) {
+    if (m < 0 || k < 0 || (m > 0 && (!seq_idx || !q || !r)) || (m > 0 && k > 0 && !F)) return HAWKES_EINVAL;
+    if (m == 0) return HAWKES_OK;
+    hk::scatter_rates_trend_kernel<<<hk::grid_for(m), 256, 0, (cudaStream_t)stream>>>(m, k, seq_idx, F, q, r);
+    return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
+}
+
+int hawkes_posterior_add_trend(int64_t m, int k, const int *seq_idx, const double *F, double beta_var,
+                               const double *q, const double *grad, const double *hdiag, double *logpost,
+                               double *grad_q, double *hdiag_q, void *stream) {
+    if (m < 1 || k < 0 || !seq_idx || !q || !logpost || (k > 0 && !F)) return HAWKES_EINVAL;
+    if (!(beta_var > 0) || !isfinite(beta_var)) return HAWKES_EINVAL;
+    if ((grad == nullptr) != (grad_q == nullptr) || (hdiag == nullptr) != (hdiag_q == nullptr)) return HAWKES_EINVAL;
+    if (hdiag && !grad) return HAWKES_EINVAL;
+    if (k == 0) return HAWKES_OK;
+    hk::trend_assemble_kernel<<<k, hk::ASM_THREADS, 0, (cudaStream_t)stream>>>(m, k, seq_idx, F, beta_var, q, grad,
+                                                                               hdiag, logpost, grad_q, hdiag_q);
     return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
 }
 

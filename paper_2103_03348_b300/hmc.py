@@ -66,6 +66,14 @@ def prior_km_days() -> Prior:
                  b=(2.0, 10.0 * KM_PER_DEGREE, half_year, 0.001, half_year, 0.5 * KM_PER_DEGREE))
 
 
+def trend_features(t_seq, degree: int = 1) -> np.ndarray:
+    """[M, degree] polynomial trend features of the sequenced events' times,
+    standardised: f_d(t) = u^d with u = (t - mean) / sd (Section 2.2's f)."""
+    t_seq = np.asarray(t_seq, float)
+    u = (t_seq - t_seq.mean()) / (t_seq.std() if t_seq.std() > 0 else 1.0)
+    return np.stack([u ** d for d in range(1, degree + 1)], axis=1)
+
+
 def _lib():
     L = hawkes.lib()
     if not getattr(L, "_hmc_typed", False):
@@ -81,6 +89,10 @@ def _lib():
                                             vp, ctypes.c_size_t, vp, vp, vp, vp]
         L.hawkes_posterior_tree.restype = ctypes.c_int
         L.hawkes_hmc_scatter_rates.argtypes = [i64, vp, vp, vp, vp]
+        L.hawkes_hmc_scatter_rates_trend.argtypes = [i64, ctypes.c_int, vp, vp, vp, vp, vp]
+        L.hawkes_hmc_scatter_rates_trend.restype = ctypes.c_int
+        L.hawkes_posterior_add_trend.argtypes = [i64, ctypes.c_int, vp, vp, d, vp, vp, vp, vp, vp, vp, vp]
+        L.hawkes_posterior_add_trend.restype = ctypes.c_int
         L.hawkes_hmc_momentum.argtypes = [i64, vp, vp, d, vp]
         L.hawkes_hmc_position.argtypes = [i64, vp, vp, vp, d, vp]
         L.hawkes_hmc_kinetic.argtypes = [i64, vp, vp, vp, vp]
@@ -102,10 +114,14 @@ def _check(rc):
 class Posterior:
     """log pi(q) and its derivatives for fixed events, priors and tree precision."""
 
-    def __init__(self, x, y, t, r_base, seq_idx, prec, prior: Prior, precision="fp32c", tree=None):
+    def __init__(self, x, y, t, r_base, seq_idx, prec, prior: Prior, precision="fp32c", tree=None, trend=None,
+                 beta_var=1.0):
         """prec: the dense M x M precision (sigma^2 V)^-1 on the device, or None
         with tree: a tree.TreePrior over the same M sequenced events (O(M) per
-        evaluation instead of O(M^2))."""
+        evaluation instead of O(M^2)).  trend: optional device [M, K] matrix
+        F of trend features f(t_s) (Section 2.2): the state becomes
+        (log globals, z[M], beta[K]) with r_s = z_s + F_s beta and
+        beta ~ N(0, beta_var I)."""
         self.x, self.y, self.t = x, y, t
         self.r = r_base.clone()
         self.dev = t.device
@@ -128,7 +144,12 @@ class Posterior:
         f64 = dict(dtype=torch.float64, device=self.dev)
         self.like = {"loglik": torch.empty((), **f64), "grad": torch.empty(6 + self.n, **f64),
                      "hdiag": torch.empty(6 + self.n, **f64), "status": torch.empty((), dtype=torch.int32, device=self.dev)}
-        self.dim = 6 + self.m
+        self.trend = trend.to(torch.float64).contiguous() if trend is not None else None
+        self.k = int(self.trend.shape[1]) if self.trend is not None else 0
+        if self.trend is not None and (self.trend.shape[0] != self.m or self.m == 0):
+            raise ValueError("trend must be [M, K] over the M >= 1 sequenced events")
+        self.beta_var = float(beta_var)
+        self.dim = 6 + self.m + self.k
         self.calls = {"grad": 0, "hess": 0}
 
     def evaluate(self, q, want_hess=False, out=None):
@@ -144,7 +165,7 @@ class Posterior:
             f64 = dict(dtype=torch.float64, device=self.dev)
             out = {"logpost": torch.empty((), **f64), "grad": torch.empty(self.dim, **f64),
                    "hdiag": torch.empty(self.dim, **f64)}
-        _check(L.hawkes_hmc_scatter_rates(self.m, _ptr(self.seq), _ptr(q), _ptr(self.r), ctypes.c_void_p(stream)))
+        self._scatter(q, stream)
         # with no free log-rates the column pass is skipped (globals-only modes)
         mode = ("hess" if want_hess else "grad") if self.m > 0 else ("hess_globals" if want_hess else "grad_globals")
         hawkes._call(mode, self.x, self.y, self.t, self.r, q, self.precision, stream=stream, check=False,
@@ -153,6 +174,14 @@ class Posterior:
         self._assemble(q, self.like["grad"], self.like["hdiag"] if want_hess else None, out["logpost"],
                        out["grad"], out["hdiag"] if want_hess else None, stream)
         return out
+
+    def _scatter(self, q, stream):
+        L = _lib()
+        if self.trend is None:
+            _check(L.hawkes_hmc_scatter_rates(self.m, _ptr(self.seq), _ptr(q), _ptr(self.r), ctypes.c_void_p(stream)))
+        else:
+            _check(L.hawkes_hmc_scatter_rates_trend(self.m, self.k, _ptr(self.seq), _ptr(self.trend), _ptr(q),
+                                                    _ptr(self.r), ctypes.c_void_p(stream)))
 
     def _assemble(self, q, grad, hdiag, logpost, grad_q, hdiag_q, stream):
         """Priors, Jacobian and the phylogenetic prior (dense or on the tree) on the device."""
@@ -166,13 +195,17 @@ class Posterior:
             tr = self.tree
             _check(L.hawkes_posterior_tree(self.n, self.m, _ptr(self.seq), _ptr(tr.plan), _ptr(tr.length),
                                            tr.root_var, tr.sigma2, *common))
+        if self.trend is not None:
+            _check(L.hawkes_posterior_add_trend(self.m, self.k, _ptr(self.seq), _ptr(self.trend), self.beta_var,
+                                                _ptr(q), _ptr(grad), _ptr(hdiag), _ptr(logpost), _ptr(grad_q),
+                                                _ptr(hdiag_q), ctypes.c_void_p(stream)))
 
     def logpost_only(self, q, out):
         """out['logpost'] = log pi(q) from a log-likelihood-only pass (the exact
         accept step of surrogate trajectories)."""
         L = _lib()
         stream = torch.cuda.current_stream(self.dev).cuda_stream
-        _check(L.hawkes_hmc_scatter_rates(self.m, _ptr(self.seq), _ptr(q), _ptr(self.r), ctypes.c_void_p(stream)))
+        self._scatter(q, stream)
         hawkes._call("loglik", self.x, self.y, self.t, self.r, q, self.precision, stream=stream, check=False,
                      out=self.like, log_params=True)
         self.calls["loglik"] = self.calls.get("loglik", 0) + 1

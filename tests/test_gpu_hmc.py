@@ -2,7 +2,7 @@
 import numpy as np
 import pytest
 
-from oracle import hmc_oracle
+from oracle import hmc_oracle, tree_oracle
 from paper_2103_03348_b300 import synth
 from parity_util import FP64_TOL, norm_rel, scaled_err
 
@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 
 def problem(n=600, m=40, seed=11):
     w = synth.make_ebola_like(seed=seed, n=n, m_seq=m, box=120.0, t_max=120.0, n_hot=4)
-    prec = np.linalg.inv(w.tree_cov)
+    prec = tree_oracle.precision_matrix(w.tree_parent, w.tree_length)
     return w, prec
 
 
@@ -116,3 +116,54 @@ def test_short_chain_on_hawkes_posterior():
     assert np.all(np.isfinite(ch.logpost))
     assert 0.4 < ch.accept.mean() <= 1.0
     assert 0.8 * 300 * 20 <= post.calls["grad"] <= 300 * 20  # divergent warm-up trajectories stop early
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+@pytest.mark.parametrize("prior_form", ["dense", "tree"])
+def test_posterior_with_trend_parity(precision, prior_form):
+    """theta_s = exp(z_s + beta^T f(t_s)) (Section 2.2): state (log globals, z, beta)."""
+    from paper_2103_03348_b300 import build, hmc, tree
+    build.build()
+    w, prec = problem()
+    F = hmc.trend_features(w.t[w.sequenced], degree=2)
+    d = lambda a: torch.tensor(np.asarray(a, float), dtype=torch.float64, device="cuda")  # noqa: E731
+    seq = torch.tensor(w.sequenced, device="cuda")
+    kw = dict(trend=d(F), beta_var=0.25)
+    if prior_form == "dense":
+        post = hmc.Posterior(d(w.x), d(w.y), d(w.t), d(w.r), seq, d(prec), hmc.prior_km_days(), precision, **kw)
+    else:
+        tp = tree.TreePrior(w.tree_parent, w.tree_length, 0.0, 1.0)
+        post = hmc.Posterior(d(w.x), d(w.y), d(w.t), d(w.r), seq, None, hmc.prior_km_days(), precision, tree=tp,
+                             **kw)
+    assert post.dim == 6 + len(w.sequenced) + 2
+    q = np.concatenate([np.log(w.params), w.r[w.sequenced], [0.2, -0.05]])
+    q[6:6 + len(w.sequenced)] += np.random.default_rng(3).normal(0, 0.2, len(w.sequenced))
+    ev = post.evaluate(d(q), want_hess=True)
+    lp, g, h = ev["logpost"].item(), ev["grad"].cpu().numpy(), ev["hdiag"].cpu().numpy()
+    ref = hmc_oracle.log_posterior(w.x, w.y, w.t, w.r, w.sequenced, prec, hmc.prior_km_days().as_tuple(), q,
+                                   trend=F, beta_var=0.25)
+    if precision == "fp64":
+        assert abs(lp - ref[0]) <= FP64_TOL * abs(ref[0])
+        assert scaled_err(g, ref[1]) <= FP64_TOL and scaled_err(h, ref[2]) <= FP64_TOL
+    else:
+        assert abs(lp - ref[0]) <= 1e-5 * abs(ref[0])
+        assert norm_rel(g, ref[1]) <= 1e-5 and norm_rel(h, ref[2]) <= 1e-4
+    lp_only = {"logpost": torch.empty((), dtype=torch.float64, device="cuda")}
+    post.logpost_only(d(q), lp_only)
+    assert abs(lp_only["logpost"].item() - lp) <= 1e-12 * abs(lp)
+
+
+def test_short_chain_with_trend():
+    from paper_2103_03348_b300 import build, hmc, tree
+    build.build()
+    w, prec = problem()
+    F = hmc.trend_features(w.t[w.sequenced], degree=1)
+    d = lambda a: torch.tensor(np.asarray(a, float), dtype=torch.float64, device="cuda")  # noqa: E731
+    tp = tree.TreePrior(w.tree_parent, w.tree_length, 0.0, 1.0)
+    post = hmc.Posterior(d(w.x), d(w.y), d(w.t), d(w.r), torch.tensor(w.sequenced, device="cuda"), None,
+                         hmc.prior_km_days(), "fp32c", tree=tp, trend=d(F), beta_var=1.0)
+    q0 = d(np.concatenate([np.log(w.params), w.r[w.sequenced], [0.0]]))
+    ch = hmc.sample(post, q0, n_iter=60, n_warmup=30, n_steps=10, eps0=0.05, mass_every=20, seed=2)
+    assert ch.draws.shape[1] == post.dim
+    assert np.all(np.isfinite(ch.draws)) and ch.accept.mean() > 0.3
+    assert np.std(ch.draws[:, -1]) > 0  # beta moves

@@ -122,3 +122,48 @@ def test_product_ess_matches_oracle():
     for rho, seed in ((0.3, 1), (0.95, 2)):
         x = ar1(rho, 3000, seed)
         assert abs(hmc.ess(x) / hmc_oracle.ess_geyer(x) - 1) < 1e-9
+
+
+def test_log_posterior_with_trend_finite_differences():
+    """r_seq = z + F beta (Section 2.2's trend): the gradient in every
+    coordinate, including beta, and the Hessian diagonal in the globals and z
+    match central differences; the beta entries of the diagonal are the
+    stated preconditioner."""
+    w, prec, prior, q = small_problem()
+    m = len(w.sequenced)
+    ts = w.t[w.sequenced]
+    F = np.stack([(ts - ts.mean()) / ts.std(), ((ts - ts.mean()) / ts.std()) ** 2 - 1.0], axis=1)
+    beta = np.array([0.15, -0.1])
+    qt = np.concatenate([q, beta])
+    bv = 0.5
+    lp, g, h = hmc_oracle.log_posterior(w.x, w.y, w.t, w.r, w.sequenced, prec, prior, qt, trend=F, beta_var=bv)
+
+    def f(qq):
+        return hmc_oracle.log_posterior(w.x, w.y, w.t, w.r, w.sequenced, prec, prior, qq, want_hess=False,
+                                        trend=F, beta_var=bv)
+
+    for k in range(len(qt)):
+        def dd(hh, k=k):
+            qp, qm = qt.copy(), qt.copy()
+            qp[k] += hh
+            qm[k] -= hh
+            a, b = f(qp), f(qm)
+            return (a[0] - b[0]) / (2 * hh), (a[1][k] - b[1][k]) / (2 * hh)
+
+        (g1, h1), (g2, h2) = dd(1e-4), dd(5e-5)
+        g_fd, h_fd = (4 * g2 - g1) / 3, (4 * h2 - h1) / 3
+        assert abs(g[k] - g_fd) <= 1e-7 * max(1.0, abs(g_fd)), (k, g[k], g_fd)
+        if k < 6 + m:
+            assert abs(h[k] - h_fd) <= 1e-6 * max(1.0, abs(h_fd)), (k, h[k], h_fd)
+    # the beta preconditioner from the rate diagonal at the same point
+    r = w.r.copy()
+    r[w.sequenced] = qt[6:6 + m] + F @ beta
+    import oracle
+    hr = oracle.evaluate(w.x, w.y, w.t, r, np.exp(qt[:6]), want=2)["hdiag"][6 + w.sequenced]
+    np.testing.assert_allclose(h[6 + m:], (F ** 2).T @ hr - 1.0 / bv, rtol=1e-13)
+    # zero features: the trend only adds its Gaussian prior
+    lp0, g0, _ = hmc_oracle.log_posterior(w.x, w.y, w.t, w.r, w.sequenced, prec, prior, q)
+    lpz, gz, _ = hmc_oracle.log_posterior(w.x, w.y, w.t, w.r, w.sequenced, prec, prior, qt, trend=0 * F, beta_var=bv)
+    assert abs(lpz - (lp0 - 0.5 * beta @ beta / bv)) <= 1e-12 * abs(lp0)
+    np.testing.assert_allclose(gz[:6 + m], g0, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(gz[6 + m:], -beta / bv, rtol=1e-13)
