@@ -33,29 +33,46 @@ _lock = threading.Lock()
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    os.makedirs(os.path.dirname(_SO), exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
-        tmp = _SO + f".tmp{os.getpid()}"
+def build(force: bool = False, src: str = _SRC, so: str = _SO) -> str:
+    os.makedirs(os.path.dirname(so), exist_ok=True)
+    if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+        tmp = so + f".tmp{os.getpid()}"
         subprocess.run(["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
-                        "-std=c99", "-Wall", "-o", tmp, _SRC, "-lm"], check=True)
-        os.replace(tmp, _SO)
-    return _SO
+                        "-std=c99", "-Wall", "-o", tmp, src, "-lm"], check=True)
+        os.replace(tmp, so)
+    return so
+
+
+def _typed(lib):
+    d, i64 = ctypes.POINTER(ctypes.c_double), ctypes.c_int64
+    l64 = ctypes.POINTER(ctypes.c_int64)
+    lib.tree_oracle_cov.argtypes = [i64, l64, d, ctypes.c_double, d]
+    lib.tree_oracle_cov.restype = ctypes.c_int
+    lib.tree_oracle_prior.argtypes = [i64, l64, d, ctypes.c_double, ctypes.c_double, d, d, d, d, d]
+    lib.tree_oracle_prior.restype = ctypes.c_int
+    return lib
 
 
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            d, i64 = ctypes.POINTER(ctypes.c_double), ctypes.c_int64
-            l64 = ctypes.POINTER(ctypes.c_int64)
-            lib.tree_oracle_cov.argtypes = [i64, l64, d, ctypes.c_double, d]
-            lib.tree_oracle_cov.restype = ctypes.c_int
-            lib.tree_oracle_prior.argtypes = [i64, l64, d, ctypes.c_double, ctypes.c_double, d, d, d, d, d]
-            lib.tree_oracle_prior.restype = ctypes.c_int
-            _lib = lib
+            _lib = _typed(ctypes.CDLL(build()))
     return _lib
+
+
+def source_text() -> str:
+    with open(_SRC) as f:
+        return f.read()
+
+
+def load_variant(src_text: str, workdir: str):
+    """Compile a modified copy of the C source (tests that plant a mistake in
+    the oracle) and return its library, to pass as lib=."""
+    src = os.path.join(workdir, "tree_variant.c")
+    with open(src, "w") as f:
+        f.write(src_text)
+    return _typed(ctypes.CDLL(build(force=True, src=src, so=os.path.join(workdir, "libtree_variant.so"))))
 
 
 def root_path(parent, v):
@@ -81,7 +98,7 @@ def tree_cov(parent, length, root_var=0.0):
     return root_var + (on * length) @ on.T
 
 
-def _call(parent, length, root_var, sigma2, z, want_prec=False):
+def _call(parent, length, root_var, sigma2, z, want_prec=False, lib=None):
     par = np.ascontiguousarray(parent, dtype=np.int64)
     ln = np.ascontiguousarray(length, dtype=np.float64)
     m = (par.size + 1) // 2
@@ -90,7 +107,7 @@ def _call(parent, length, root_var, sigma2, z, want_prec=False):
     pz, pd = np.zeros(m), np.zeros(m)
     prec = np.zeros((m, m)) if want_prec else None
     dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None  # noqa: E731
-    rc = _load().tree_oracle_prior(m, par.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), dp(ln), float(root_var),
+    rc = (lib or _load()).tree_oracle_prior(m, par.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), dp(ln), float(root_var),
                                    float(sigma2), dp(zz), dp(ld) if zz is not None else None,
                                    dp(pz) if zz is not None else None, dp(pd), dp(prec))
     if rc != 0:
@@ -98,9 +115,9 @@ def _call(parent, length, root_var, sigma2, z, want_prec=False):
     return float(ld[0]), pz, pd, prec
 
 
-def tree_prior(z, parent, length, root_var, sigma2):
+def tree_prior(z, parent, length, root_var, sigma2, lib=None):
     """(log N(z; 0, sigma2 V), (sigma2 V)^-1 z, diag((sigma2 V)^-1)), dense, in long double."""
-    ld, pz, pd, _ = _call(parent, length, root_var, sigma2, z)
+    ld, pz, pd, _ = _call(parent, length, root_var, sigma2, z, lib=lib)
     return ld, pz, pd
 
 
