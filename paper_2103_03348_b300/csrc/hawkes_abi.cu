@@ -109,6 +109,15 @@ __global__ void setup_kernel(ParamSource ps, int fp32c, Derived *out, int *hdr) 
         d.cbt = 0.0f;
         d.hh = 0.0f;
     }
+    d.i_mu0 = 1.0 / d.mu0;
+    d.i_tx = 1.0 / d.tx;
+    d.i_tt = d.tt_inf ? 0.0 : 1.0 / d.tt;
+    d.i_th0 = 1.0 / d.th0;
+    d.i_om = 1.0 / d.om;
+    d.i_h = 1.0 / d.h;
+    d.i_sx2 = 1.0 / (d.sx * d.sx);
+    d.i_st = 1.0 / d.st;
+    d.i_st2 = d.i_st * d.i_st;
     d.valid = ok ? 1 : 0;
     if (!ok) atomicOr(&hdr[0], ST_BADPARAM);
     *out = d;

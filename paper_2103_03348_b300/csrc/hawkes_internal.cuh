@@ -66,6 +66,9 @@ struct Derived {
     double ibx, ibt, ih;  // FP64:  G = exp(-ibx d^2 - ibt dt^2), E = exp(r - om dt - ih d^2)
     float cbt, hh;        // FP32C: G = 2^-(d~^2 + cbt dt~^2), E = 2^(r^_s - t~_n - hh d~^2)
     int tt_inf, valid;
+    // reciprocals for the row epilogue (FP64 division is costly): 1/mu0, 1/tau_x,
+    // 1/tau_t (0 when infinite), 1/theta0, 1/omega, 1/h, 1/sx^2, 1/st, 1/st^2
+    double i_mu0, i_tx, i_tt, i_th0, i_om, i_h, i_sx2, i_st, i_st2;
 };
 
 // Per-call constants known on the host (passed by value to every kernel).

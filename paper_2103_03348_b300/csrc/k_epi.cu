@@ -74,35 +74,36 @@ __global__ void __launch_bounds__(TILE) epilogue_kernel(Consts c, Inputs in, Wor
     if (valid) {
         const int mode = c.mode;
         auto M = [&](int k) { return ws.mom[(size_t)k * npad + i]; };
-        const double sx2 = D.sx * D.sx, st = D.st, st2 = D.st * D.st;
         const double SG = M(MO_G), SE = M(MO_E);
         const double lam = D.A * SG + D.B * SE;
         double q1[6] = {0, 0, 0, 0, 0, 0}, q2[6] = {0, 0, 0, 0, 0, 0};
         double ll = 0.0;
         if (lam > 0.0) {
             ll = log(lam);
+            const double il = 1.0 / lam;
             if (mode >= MODE_GRAD) {
-                const double a = D.A / lam, b = D.B / lam;
-                const double GD2 = M(MO_GD2) / sx2, GT2 = M(MO_GT2) / st2;
-                const double ET = M(MO_ET) / st, ED2 = M(MO_ED2) / sx2;
-                const double tx = D.tx, tt = D.tt, om = D.om, h = D.h;
-                q1[0] = a * SG / D.mu0;
-                q1[1] = a * (GD2 / (tx * tx * tx) - 2.0 * SG / tx);
-                q1[2] = D.tt_inf ? 0.0 : a * (GT2 / (tt * tt * tt) - SG / tt);
-                q1[3] = b * SE / D.th0;
-                q1[4] = b * (SE / om - ET);
-                q1[5] = b * (ED2 / (h * h * h) - 2.0 * SE / h);
+                const double a = D.A * il, b = D.B * il;
+                const double GD2 = M(MO_GD2) * D.i_sx2, GT2 = M(MO_GT2) * D.i_st2;
+                const double ET = M(MO_ET) * D.i_st, ED2 = M(MO_ED2) * D.i_sx2;
+                const double ix = D.i_tx, it = D.i_tt, ih = D.i_h;
+                const double ix2 = ix * ix, it2 = it * it, ih2 = ih * ih;
+                q1[0] = a * SG * D.i_mu0;
+                q1[1] = a * (GD2 * ix2 * ix - 2.0 * SG * ix);
+                q1[2] = D.tt_inf ? 0.0 : a * (GT2 * it2 * it - SG * it);
+                q1[3] = b * SE * D.i_th0;
+                q1[4] = b * (SE * D.i_om - ET);
+                q1[5] = b * (ED2 * ih2 * ih - 2.0 * SE * ih);
                 if (mode == MODE_HESS) {
-                    const double GD4 = M(MO_GD4) / (sx2 * sx2), GT4 = M(MO_GT4) / (st2 * st2);
-                    const double ET2 = M(MO_ET2) / st2, ED4 = M(MO_ED4) / (sx2 * sx2);
-                    const double tx2 = tx * tx, tt2 = tt * tt, h2 = h * h;
+                    const double GD4 = M(MO_GD4) * D.i_sx2 * D.i_sx2, GT4 = M(MO_GT4) * D.i_st2 * D.i_st2;
+                    const double ET2 = M(MO_ET2) * D.i_st2, ED4 = M(MO_ED4) * D.i_sx2 * D.i_sx2;
+                    const double ix4 = ix2 * ix2, it4 = it2 * it2, ih4 = ih2 * ih2;
                     double s2[6];
                     s2[0] = 0.0;
-                    s2[1] = a * (GD4 / (tx2 * tx2 * tx2) - 7.0 * GD2 / (tx2 * tx2) + 6.0 * SG / tx2);
-                    s2[2] = D.tt_inf ? 0.0 : a * (GT4 / (tt2 * tt2 * tt2) - 5.0 * GT2 / (tt2 * tt2) + 2.0 * SG / tt2);
+                    s2[1] = a * (GD4 * ix4 * ix2 - 7.0 * GD2 * ix4 + 6.0 * SG * ix2);
+                    s2[2] = D.tt_inf ? 0.0 : a * (GT4 * it4 * it2 - 5.0 * GT2 * it4 + 2.0 * SG * it2);
                     s2[3] = 0.0;
-                    s2[4] = b * (ET2 - 2.0 * ET / om);
-                    s2[5] = b * (ED4 / (h2 * h2 * h2) - 7.0 * ED2 / (h2 * h2) + 6.0 * SE / h2);
+                    s2[4] = b * (ET2 - 2.0 * ET * D.i_om);
+                    s2[5] = b * (ED4 * ih4 * ih2 - 7.0 * ED2 * ih4 + 6.0 * SE * ih2);
 #pragma unroll
                     for (int p = 0; p < 6; ++p) q2[p] = s2[p] - q1[p] * q1[p];
                     if (D.tt_inf) q2[2] = 0.0;
@@ -112,9 +113,9 @@ __global__ void __launch_bounds__(TILE) epilogue_kernel(Consts c, Inputs in, Wor
                 // column weight g^ = log2(B / lambda_n) - t~_n (t~_n as packed)
                 const float *f = reinterpret_cast<const float *>(ws.src32);
                 const float tt_n = -f[8 * (i >> 1) + 4 + (i & 1)];
-                ghat = (float)(log2(D.B / lam) - (double)tt_n);
+                ghat = (float)(log2(D.B * il) - (double)tt_n);
             } else {
-                ws.w64[i] = D.B / lam;
+                ws.w64[i] = D.B * il;
             }
         } else {
             atomicOr(&ws.hdr[0], ST_ZERO);
@@ -135,12 +136,12 @@ __global__ void __launch_bounds__(TILE) epilogue_kernel(Consts c, Inputs in, Wor
         if (D.tt_inf) {
             dL[0] = tN;
         } else {
-            const double tt = D.tt, za = a_ / tt, zb = b_ / tt;
+            const double it = D.i_tt, za = a_ * it, zb = b_ * it;
             const double pa = std_pdf(za), pb = std_pdf(zb);
             dL[0] = std_cdf(za) - std_cdf(zb);
-            dL[2] = D.mu0 * (-(a_ / (tt * tt)) * pa + (b_ / (tt * tt)) * pb);
-            const double tt3 = tt * tt * tt, tt5 = tt3 * tt * tt;
-            d2L[2] = D.mu0 * (pa * (2.0 * a_ / tt3 - a_ * a_ * a_ / tt5) - pb * (2.0 * b_ / tt3 - b_ * b_ * b_ / tt5));
+            const double it2 = it * it, it3 = it2 * it, it5 = it3 * it2;
+            dL[2] = D.mu0 * (-(a_ * it2) * pa + (b_ * it2) * pb);
+            d2L[2] = D.mu0 * (pa * (2.0 * a_ * it3 - a_ * a_ * a_ * it5) - pb * (2.0 * b_ * it3 - b_ * b_ * b_ * it5));
         }
         L = D.mu0 * dL[0] + D.th0 * th * one_m;
         dL[3] = th * one_m;
