@@ -130,3 +130,14 @@ def test_predictive_argument_checks(L):
     assert call(cap=0) == hawkes.EINVAL
     assert call(cap=(1 << 24) + 1) == hawkes.EINVAL
     assert call(ns=0) == hawkes.OK                     # nothing to do, nothing launched
+
+
+def test_peak_microbenchmark_arguments(L):
+    from paper_2103_03348_b300 import peaks
+    P = peaks._lib()
+    assert P.hawkes_peak_ops(0, 10, 100) == 10 * 256 * 100 * 8 * 2
+    assert P.hawkes_peak_ops(2, 10, 100) == 10 * 256 * 100 * 8
+    assert P.hawkes_peak_ops(3, 10, 100) == 0
+    assert P.hawkes_peak_launch(5, 10, 100, ctypes.c_void_p(8), None) == hawkes.EINVAL
+    assert P.hawkes_peak_launch(0, 0, 100, ctypes.c_void_p(8), None) == hawkes.EINVAL
+    assert P.hawkes_peak_launch(0, 10, 100, None, None) == hawkes.EINVAL
