@@ -427,7 +427,7 @@ int hawkes_hess_diag_noalloc(const double *x, const double *y, const double *t, 
 /* ALU throughput microbenchmarks (the denominators of the roofline; the paper
  * has no counterpart): which = 0 packed FP32 FMA (f32x2), 1 MUFU exp2, 2 FP64
  * FMA.  hawkes_peak_launch enqueues blocks x 256 threads, each running
- * independent chains for iters steps (sink: DEVICE float[1], written only to
+ * independent chains for iters steps, a multiple of 8 (sink: DEVICE float[1], written only to
  * keep the work live); the caller times it on its stream.  hawkes_peak_ops
  * gives the lane operations one launch performs (0 for bad arguments). */
 int64_t hawkes_peak_ops(int which, int64_t blocks, int iters);

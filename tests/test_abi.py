@@ -135,9 +135,10 @@ def test_predictive_argument_checks(L):
 def test_peak_microbenchmark_arguments(L):
     from paper_2103_03348_b300 import peaks
     P = peaks._lib()
-    assert P.hawkes_peak_ops(0, 10, 100) == 10 * 256 * 100 * 8 * 2
-    assert P.hawkes_peak_ops(2, 10, 100) == 10 * 256 * 100 * 8
-    assert P.hawkes_peak_ops(3, 10, 100) == 0
+    assert P.hawkes_peak_ops(0, 10, 104) == 10 * 256 * 104 * 8 * 2
+    assert P.hawkes_peak_ops(2, 10, 104) == 10 * 256 * 104 * 8
+    assert P.hawkes_peak_ops(3, 10, 104) == 0
+    assert P.hawkes_peak_ops(0, 10, 100) == 0  # not a multiple of the unroll
     assert P.hawkes_peak_launch(5, 10, 100, ctypes.c_void_p(8), None) == hawkes.EINVAL
     assert P.hawkes_peak_launch(0, 0, 100, ctypes.c_void_p(8), None) == hawkes.EINVAL
     assert P.hawkes_peak_launch(0, 10, 100, None, None) == hawkes.EINVAL
