@@ -66,11 +66,14 @@ def prior_km_days() -> Prior:
                  b=(2.0, 10.0 * KM_PER_DEGREE, half_year, 0.001, half_year, 0.5 * KM_PER_DEGREE))
 
 
-def trend_features(t_seq, degree: int = 1) -> np.ndarray:
-    """[M, degree] polynomial trend features of the sequenced events' times,
-    standardised: f_d(t) = u^d with u = (t - mean) / sd (Section 2.2's f)."""
+def trend_features(t_seq, degree: int = 1, standardise: bool = True) -> np.ndarray:
+    """[M, degree] polynomial trend features f(t) of the sequenced events'
+    times (Section 2.2).  standardise=False with degree 1 is the paper's
+    choice f(t) = t (Section 3.2, with beta ~ N(0, 10^2): beta_var = 100);
+    the default uses u = (t - mean) / sd and f_d = u^d, which keeps the
+    coefficients on a common scale."""
     t_seq = np.asarray(t_seq, float)
-    u = (t_seq - t_seq.mean()) / (t_seq.std() if t_seq.std() > 0 else 1.0)
+    u = (t_seq - t_seq.mean()) / (t_seq.std() if t_seq.std() > 0 else 1.0) if standardise else t_seq
     return np.stack([u ** d for d in range(1, degree + 1)], axis=1)
 
 
