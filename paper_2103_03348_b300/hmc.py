@@ -285,12 +285,55 @@ class Chain:
     mass_t: object = None      # device mass matrix at the end
 
 
+class TrajectoryGraph:
+    """One leapfrog trajectory of fixed step size and length, captured once as
+    a CUDA graph and replayed per iteration: every kernel of the n_steps
+    likelihood evaluations, posterior assemblies and momentum/position
+    updates is enqueued by one launch, with no Python or driver overhead per
+    kernel.  Works on static buffers: set q, p and g (the gradient at q), then
+    replay; the trajectory's end state is in q, p and out, and the kinetic
+    energy at the end in k1.  minv is read from device memory at replay, so
+    mass updates made in place take effect."""
+
+    def __init__(self, post, eps, n_steps, minv):
+        dev = minv.device
+        f64 = dict(dtype=torch.float64, device=dev)
+        dim = minv.numel()
+        self.post, self.n_steps = post, n_steps
+        self.q, self.p, self.g = torch.zeros(dim, **f64), torch.zeros(dim, **f64), torch.zeros(dim, **f64)
+        self.out = {"logpost": torch.empty((), **f64), "grad": torch.empty(dim, **f64),
+                    "hdiag": torch.empty(dim, **f64)}
+        self.k1 = torch.empty((), **f64)
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):  # one eager run first, so every lazily made buffer exists
+            self._body(eps, minv)
+        torch.cuda.current_stream(dev).wait_stream(side)
+        torch.cuda.synchronize(dev)
+        self.graph = torch.cuda.CUDAGraph()
+        calls = dict(post.calls)
+        with torch.cuda.graph(self.graph):
+            self._body(eps, minv)
+        post.calls.update(calls)  # capture enqueues nothing: count replays instead
+
+    def _body(self, eps, minv):
+        leapfrog(self.post, self.q, self.p, self.g, eps, self.n_steps, minv, self.out)
+        kinetic(self.p, minv, self.k1)
+
+    def replay(self):
+        self.graph.replay()
+        self.post.calls["grad"] += self.n_steps
+        return self.out
+
+
 def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_every=100, target_accept=0.8,
-           mass_floor=1e-2, seed=0, keep=None, record=None):
+           mass_floor=1e-2, seed=0, keep=None, record=None, use_graph=True):
     """Run n_warmup + n_iter HMC iterations from q0 (device tensor); returns a Chain.
 
     keep: optional index array of coordinates to store (all by default);
-    record: optional callback given every leapfrog position and its gradient."""
+    record: optional callback given every leapfrog position and its gradient;
+    use_graph: after warm-up (step size fixed) replay each trajectory as one
+    captured CUDA graph (not with record, which needs every position)."""
     dev = q0.device
     gen = torch.Generator(device=dev)
     gen.manual_seed(seed)
@@ -303,7 +346,8 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
     cur = {k: v.clone() for k, v in cur.items()}
     mass = torch.clamp(-cur["hdiag"], min=mass_floor)
     n_mass = 1
-    minv = 1.0 / mass
+    minv = 1.0 / mass  # updated in place from here on (a captured trajectory reads it)
+    graph = None
     scratch = {"logpost": torch.empty((), **f64), "grad": torch.empty(dim, **f64), "hdiag": torch.empty(dim, **f64)}
     k0, k1 = torch.empty((), **f64), torch.empty((), **f64)
     da = DualAveraging(eps0, target_accept)
@@ -322,17 +366,27 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
         torch.randn(dim, generator=gen, out=p, dtype=torch.float64, device=dev)
         p.mul_(torch.sqrt(mass))
         kinetic(p, minv, k0)
-        qn = q.clone()
-        ev = leapfrog(post, qn, p, cur["grad"], eps, n_steps, minv, scratch, record)
-        kinetic(p, minv, k1)
+        if use_graph and record is None and it >= n_warmup:
+            if graph is None:
+                graph = TrajectoryGraph(post, eps, n_steps, minv)
+            graph.q.copy_(q)
+            graph.p.copy_(p)
+            graph.g.copy_(cur["grad"])
+            ev = graph.replay()
+            qn, k1_t = graph.q, graph.k1
+        else:
+            qn = q.clone()
+            ev = leapfrog(post, qn, p, cur["grad"], eps, n_steps, minv, scratch, record)
+            kinetic(p, minv, k1)
+            k1_t = k1
         h0 = -cur["logpost"].item() + k0.item()
         lp1 = ev["logpost"].item()
-        h1 = -lp1 + k1.item()
+        h1 = -lp1 + k1_t.item()
         ok_num = math.isfinite(lp1) and post.status() == hawkes.OK
         a = min(1.0, math.exp(min(0.0, h0 - h1))) if ok_num and math.isfinite(h1) else 0.0
         accepted = rng.uniform() < a
         if accepted:
-            q = qn
+            q = qn.clone() if graph is not None and qn is graph.q else qn
             cur["logpost"].copy_(ev["logpost"])
             cur["grad"].copy_(ev["grad"])
         if it < n_warmup:
@@ -342,7 +396,7 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
             new = torch.clamp(-hd["hdiag"], min=mass_floor)
             mass = (n_mass * mass + new) / (n_mass + 1)  # running average of the Hessian-based masses
             n_mass += 1
-            minv = 1.0 / mass
+            torch.reciprocal(mass, out=minv)
             cur["logpost"].copy_(hd["logpost"])
             cur["grad"].copy_(hd["grad"])
         if it >= n_warmup:

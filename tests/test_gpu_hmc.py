@@ -167,3 +167,21 @@ def test_short_chain_with_trend():
     assert ch.draws.shape[1] == post.dim
     assert np.all(np.isfinite(ch.draws)) and ch.accept.mean() > 0.3
     assert np.std(ch.draws[:, -1]) > 0  # beta moves
+
+
+def test_graph_replayed_trajectories_equal_eager_ones():
+    """After warm-up each trajectory replays as one captured CUDA graph; the
+    kernels and their inputs are the same, so the chain is identical bit for
+    bit to the eagerly launched one (same seed)."""
+    from paper_2103_03348_b300 import build, hmc, tree
+    build.build()
+    w, prec = problem()
+    d = lambda a: torch.tensor(np.asarray(a, float), dtype=torch.float64, device="cuda")  # noqa: E731
+    tp = tree.TreePrior(w.tree_parent, w.tree_length, 0.0, 1.0)
+    post = hmc.Posterior(d(w.x), d(w.y), d(w.t), d(w.r), torch.tensor(w.sequenced, device="cuda"), None,
+                         hmc.prior_km_days(), "fp32c", tree=tp)
+    q0 = d(np.concatenate([np.log(w.params), w.r[w.sequenced]]))
+    a = hmc.sample(post, q0, n_iter=40, n_warmup=20, n_steps=8, eps0=0.05, mass_every=15, seed=3, use_graph=False)
+    b = hmc.sample(post, q0, n_iter=40, n_warmup=20, n_steps=8, eps0=0.05, mass_every=15, seed=3, use_graph=True)
+    assert np.array_equal(a.draws, b.draws) and np.array_equal(a.accept, b.accept)
+    assert a.grad_calls == b.grad_calls
