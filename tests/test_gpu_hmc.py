@@ -178,10 +178,13 @@ def test_graph_replayed_trajectories_equal_eager_ones():
     w, prec = problem()
     d = lambda a: torch.tensor(np.asarray(a, float), dtype=torch.float64, device="cuda")  # noqa: E731
     tp = tree.TreePrior(w.tree_parent, w.tree_length, 0.0, 1.0)
-    post = hmc.Posterior(d(w.x), d(w.y), d(w.t), d(w.r), torch.tensor(w.sequenced, device="cuda"), None,
-                         hmc.prior_km_days(), "fp32c", tree=tp)
+
+    def make():
+        return hmc.Posterior(d(w.x), d(w.y), d(w.t), d(w.r), torch.tensor(w.sequenced, device="cuda"), None,
+                             hmc.prior_km_days(), "fp32c", tree=tp)
+
     q0 = d(np.concatenate([np.log(w.params), w.r[w.sequenced]]))
-    a = hmc.sample(post, q0, n_iter=40, n_warmup=20, n_steps=8, eps0=0.05, mass_every=15, seed=3, use_graph=False)
-    b = hmc.sample(post, q0, n_iter=40, n_warmup=20, n_steps=8, eps0=0.05, mass_every=15, seed=3, use_graph=True)
+    a = hmc.sample(make(), q0, n_iter=40, n_warmup=20, n_steps=8, eps0=0.05, mass_every=15, seed=3, use_graph=False)
+    b = hmc.sample(make(), q0, n_iter=40, n_warmup=20, n_steps=8, eps0=0.05, mass_every=15, seed=3, use_graph=True)
     assert np.array_equal(a.draws, b.draws) and np.array_equal(a.accept, b.accept)
     assert a.grad_calls == b.grad_calls
