@@ -115,7 +115,8 @@ def test_short_chain_on_hawkes_posterior():
     ch = hmc.sample(post, q0, n_iter=150, n_warmup=150, n_steps=20, eps0=0.02, mass_every=50, seed=5)
     assert np.all(np.isfinite(ch.logpost))
     assert 0.4 < ch.accept.mean() <= 1.0
-    assert 0.8 * 300 * 20 <= post.calls["grad"] <= 300 * 20  # divergent warm-up trajectories stop early
+    # divergent warm-up trajectories stop early; one eager trajectory precedes the graph capture
+    assert 0.8 * 300 * 20 <= post.calls["grad"] <= 301 * 20
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32c"])
@@ -187,4 +188,4 @@ def test_graph_replayed_trajectories_equal_eager_ones():
     a = hmc.sample(make(), q0, n_iter=40, n_warmup=20, n_steps=8, eps0=0.05, mass_every=15, seed=3, use_graph=False)
     b = hmc.sample(make(), q0, n_iter=40, n_warmup=20, n_steps=8, eps0=0.05, mass_every=15, seed=3, use_graph=True)
     assert np.array_equal(a.draws, b.draws) and np.array_equal(a.accept, b.accept)
-    assert a.grad_calls == b.grad_calls
+    assert b.grad_calls == a.grad_calls + 8  # one eager trajectory before the capture
