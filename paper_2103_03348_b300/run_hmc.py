@@ -1,6 +1,6 @@
 """Preconditioned HMC over the phylogenetic Hawkes posterior, reported as ESS/s.
 
-    python -m paper_2103_03348_b300.run_hmc [--precision fp32c|fp64] [--iters 2000] [--warmup 200]
+    python -m paper_2103_03348_b300.run_hmc [--precision fp32c_band|fp32c|fp64] [--iters 2000] [--warmup 200]
                                             [--prior tree|dense]
 
 Workload: the 23,422-event synthetic pattern with 1,610 sequenced events whose
@@ -24,7 +24,7 @@ import torch
 from . import build, hmc, synth, tree
 
 
-def run(precision="fp32c", iters=2000, warmup=200, n_steps=20, mass_every=100, eps0=0.05, seed=0, n=23422,
+def run(precision="fp32c_band", iters=2000, warmup=200, n_steps=20, mass_every=100, eps0=0.05, seed=0, n=23422,
         m_seq=1610, device="cuda", prior="tree"):
     build.build()
     w = synth.make_ebola_like(n=n, m_seq=m_seq)
@@ -65,7 +65,7 @@ def run(precision="fp32c", iters=2000, warmup=200, n_steps=20, mass_every=100, e
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--precision", default="fp32c", choices=["fp32c", "fp64"])
+    ap.add_argument("--precision", default="fp32c_band", choices=["fp32c_band", "fp32c", "fp64"])
     ap.add_argument("--iters", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--steps", type=int, default=20)
