@@ -45,6 +45,8 @@ __global__ void __launch_bounds__(ASM_THREADS) posterior_assemble_kernel(
     const double *__restrict__ grad, const double *__restrict__ hdiag, double *__restrict__ logpost,
     double *__restrict__ grad_q, double *__restrict__ hdiag_q) {
     __shared__ double sh[ASM_THREADS];
+    __shared__ double s_lp[6];
+    __shared__ int s_ok[6];
     const double *rs = q + 6;  // the sequenced log-rates
     double quad = 0.0;
     for (int64_t j = threadIdx.x; j < m; j += ASM_THREADS) {
@@ -53,29 +55,35 @@ __global__ void __launch_bounds__(ASM_THREADS) posterior_assemble_kernel(
         if (hdiag_q) hdiag_q[6 + j] = hdiag[6 + i] - pdiag[(size_t)j * pstride];
         quad += rs[j] * w[j];
     }
-    quad = block_sum<ASM_THREADS>(quad, sh);
+    // one thread per global: its prior, the log-transform Jacobian and the chain rule
+    if (threadIdx.x < 6) {
+        const int k = threadIdx.x;
+        const double lq = q[k], p = exp(lq), ip = 1.0 / p, a = pc.a[k], b = pc.b[k];
+        double lpr, d1, d2;
+        if (pc.kind[k] == HAWKES_PRIOR_GAMMA) {
+            lpr = (a - 1.0) * lq - b * p;
+            d1 = (a - 1.0) * ip - b;
+            d2 = -(a - 1.0) * ip * ip;
+        } else {  // inverse gamma
+            lpr = -(a + 1.0) * lq - b * ip;
+            d1 = -(a + 1.0) * ip + b * ip * ip;
+            d2 = (a + 1.0) * ip * ip - 2.0 * b * ip * ip * ip;
+        }
+        s_lp[k] = lpr + lq;  // log p_k = q_k
+        s_ok[k] = isfinite(p) && p > 0.0;
+        if (grad_q) {
+            const double gk = grad[k] + d1;
+            grad_q[k] = p * gk + 1.0;
+            if (hdiag_q) hdiag_q[k] = p * gk + p * p * (hdiag[k] + d2);
+        }
+    }
+    quad = block_sum<ASM_THREADS>(quad, sh);  // its barriers also publish s_lp, s_ok
     if (threadIdx.x == 0) {
         double lp = *loglik - 0.5 * quad;
         bool ok = true;
         for (int k = 0; k < 6; ++k) {
-            const double p = exp(q[k]), a = pc.a[k], b = pc.b[k];
-            if (!isfinite(p) || !(p > 0.0)) ok = false;
-            double lpr, d1, d2;
-            if (pc.kind[k] == HAWKES_PRIOR_GAMMA) {
-                lpr = (a - 1.0) * log(p) - b * p;
-                d1 = (a - 1.0) / p - b;
-                d2 = -(a - 1.0) / (p * p);
-            } else {  // inverse gamma
-                lpr = -(a + 1.0) * log(p) - b / p;
-                d1 = -(a + 1.0) / p + b / (p * p);
-                d2 = (a + 1.0) / (p * p) - 2.0 * b / (p * p * p);
-            }
-            lp += lpr + log(p);
-            if (grad_q) {
-                const double gk = grad[k] + d1;
-                grad_q[k] = p * gk + 1.0;
-                if (hdiag_q) hdiag_q[k] = p * gk + p * p * (hdiag[k] + d2);
-            }
+            lp += s_lp[k];
+            ok = ok && s_ok[k];
         }
         *logpost = ok ? lp : -INFINITY;
     }

@@ -20,6 +20,10 @@
 // contrast gradients, and each contrast above a node sees that node's m
 // through the product of the l_other / s factors on the way up).
 // One block sweeps the internal nodes level by level, children before parents.
+// FP64 division is costly on this part and the block runs on one SM, so each
+// node takes one reciprocal 1/s_v in the upward sweep and keeps it for the
+// downward one; the logarithms of log |V| are taken only when the density is
+// requested.
 #include <stdlib.h>
 #include <string.h>
 
@@ -49,12 +53,12 @@ __host__ __device__ inline TreePlan tree_plan_view(const int *p) {
     return t;
 }
 
-// mu, dl, gb, dd: scratch of 2m-1 doubles each
+// mu, dl, gb, dd, is: scratch of 2m-1 doubles each (is_v = 1 / s_v)
 __global__ void __launch_bounds__(TREE_THREADS)
     tree_prior_kernel(int64_t m_arg, const int *__restrict__ plan, const double *__restrict__ len, double tau0,
                       double sigma2, const double *__restrict__ z, double *__restrict__ mu, double *__restrict__ dl,
-                      double *__restrict__ gb, double *__restrict__ dd, double *__restrict__ logdens,
-                      double *__restrict__ pz, double *__restrict__ pdiag) {
+                      double *__restrict__ gb, double *__restrict__ dd, double *__restrict__ is,
+                      double *__restrict__ logdens, double *__restrict__ pz, double *__restrict__ pdiag) {
     __shared__ double sh[TREE_THREADS];
     const TreePlan T = tree_plan_view(plan);
     const int m = T.m;
@@ -71,27 +75,34 @@ __global__ void __launch_bounds__(TREE_THREADS)
         dl[i] = 0.0;
     }
     __syncthreads();
+    const bool want_density = logdens != nullptr;
     double quad = 0.0, logdet = 0.0;
     for (int L = 0; L < T.levels; ++L) {
         for (int k = T.offs[L] + threadIdx.x; k < T.offs[L + 1]; k += TREE_THREADS) {
             const int v = T.order[k], a = T.ca[v], b = T.cb[v];
-            const double la = len[a] + dl[a], lb = len[b] + dl[b], s = la + lb;
+            const double la = len[a] + dl[a], lb = len[b] + dl[b], s = la + lb, r = 1.0 / s;
             const double u = mu[a] - mu[b];
-            mu[v] = (mu[a] * lb + mu[b] * la) / s;
-            dl[v] = la * lb / s;
-            quad += u * u / s;
-            logdet += log(s);
+            mu[v] = (mu[a] * lb + mu[b] * la) * r;
+            dl[v] = la * lb * r;
+            is[v] = r;
+            if (want_density) {
+                quad += u * u * r;
+                logdet += log(s);
+            }
         }
         __syncthreads();
     }
     const int root = T.order[m - 2];
     const double droot = dl[root] + tau0;
-    quad = block_sum<TREE_THREADS>(quad, sh);
-    logdet = block_sum<TREE_THREADS>(logdet, sh);
+    if (want_density) {
+        quad = block_sum<TREE_THREADS>(quad, sh);
+        logdet = block_sum<TREE_THREADS>(logdet, sh);
+    }
     if (threadIdx.x == 0) {
-        gb[root] = mu[root] / droot;
-        dd[root] = 1.0 / droot;
-        if (logdens) {
+        const double ir = 1.0 / droot;
+        gb[root] = mu[root] * ir;
+        dd[root] = ir;
+        if (want_density) {
             quad += mu[root] * mu[root] / droot;
             logdet += log(droot);
             const double LOG_2PI = 1.8378770664093454836;
@@ -102,19 +113,20 @@ __global__ void __launch_bounds__(TREE_THREADS)
     for (int L = T.levels - 1; L >= 0; --L) {
         for (int k = T.offs[L] + threadIdx.x; k < T.offs[L + 1]; k += TREE_THREADS) {
             const int v = T.order[k], a = T.ca[v], b = T.cb[v];
-            const double la = len[a] + dl[a], lb = len[b] + dl[b], s = la + lb;
-            const double uu = (mu[a] - mu[b]) / s, g = gb[v], D = dd[v];
-            const double fa = lb / s, fb = la / s;
+            const double r = is[v], la = len[a] + dl[a], lb = len[b] + dl[b];
+            const double uu = (mu[a] - mu[b]) * r, g = gb[v], D = dd[v];
+            const double fa = lb * r, fb = la * r;
             gb[a] = fa * g + uu;
             gb[b] = fb * g - uu;
-            dd[a] = 1.0 / s + fa * fa * D;
-            dd[b] = 1.0 / s + fb * fb * D;
+            dd[a] = r + fa * fa * D;
+            dd[b] = r + fb * fb * D;
         }
         __syncthreads();
     }
+    const double is2 = 1.0 / sigma2;
     for (int i = threadIdx.x; i < m; i += TREE_THREADS) {
-        if (pz) pz[i] = gb[i] / sigma2;        // (sigma^2 V)^-1 z
-        if (pdiag) pdiag[i] = dd[i] / sigma2;  // diag((sigma^2 V)^-1)
+        if (pz) pz[i] = gb[i] * is2;        // (sigma^2 V)^-1 z
+        if (pdiag) pdiag[i] = dd[i] * is2;  // diag((sigma^2 V)^-1)
     }
 }
 
@@ -122,8 +134,9 @@ cudaError_t launch_tree_prior(int64_t m, const int *plan, const double *len, dou
                               const double *z, double *scratch, double *logdens, double *pz, double *pdiag,
                               cudaStream_t s) {
     const int64_t nn = 2 * m - 1;
-    double *mu = scratch, *dl = mu + nn, *gb = dl + nn, *dd = gb + nn;
-    tree_prior_kernel<<<1, TREE_THREADS, 0, s>>>(m, plan, len, tau0, sigma2, z, mu, dl, gb, dd, logdens, pz, pdiag);
+    double *mu = scratch, *dl = mu + nn, *gb = dl + nn, *dd = gb + nn, *is = dd + nn;
+    tree_prior_kernel<<<1, TREE_THREADS, 0, s>>>(m, plan, len, tau0, sigma2, z, mu, dl, gb, dd, is, logdens, pz,
+                                                 pdiag);
     return cudaGetLastError();
 }
 
@@ -138,7 +151,7 @@ size_t hawkes_tree_plan_size(int64_t m) {
 
 size_t hawkes_tree_workspace_size(int64_t m) {
     if (m < 2 || m > HAWKES_TREE_MAX_TIPS) return 0;
-    return (size_t)4 * (2 * m - 1) * sizeof(double);
+    return (size_t)5 * (2 * m - 1) * sizeof(double);
 }
 
 int hawkes_tree_plan(int64_t m, const int64_t *parent, int *plan, size_t plan_bytes) {
