@@ -53,14 +53,28 @@ __host__ __device__ inline TreePlan tree_plan_view(const int *p) {
     return t;
 }
 
-// mu, dl, gb, dd, is: scratch of 2m-1 doubles each (is_v = 1 / s_v)
+// Trees of up to TREE_SMEM_MAX_TIPS tips run with every array staged in shared
+// memory (the sweeps are a chain of dependent loads per level, which shared
+// memory serves in a few cycles); larger trees use the caller's scratch.
+constexpr int TREE_SMEM_MAX_TIPS = 1860;  // dynamic + the static 8 KB reduction buffer <= 227 KB
+
+__host__ __device__ inline size_t tree_smem_bytes(int64_t m) {
+    // 6 doubles (mu, dl, gb, dd, 1/s, length) and 2 ints (children) per node,
+    // then the level order (m - 1) and the level offsets (at most m)
+    return (size_t)(2 * m - 1) * (6 * sizeof(double) + 2 * sizeof(int)) + (size_t)(2 * m) * sizeof(int) + 64;
+}
+
+// STAGED: the plan and lengths are copied into shared memory and the state
+// arrays live there; otherwise mu, dl, gb, dd, is are the global scratch
+// (2m-1 doubles each; is_v = 1 / s_v).
+template <bool STAGED>
 __global__ void __launch_bounds__(TREE_THREADS)
-    tree_prior_kernel(int64_t m_arg, const int *__restrict__ plan, const double *__restrict__ len, double tau0,
-                      double sigma2, const double *__restrict__ z, double *__restrict__ mu, double *__restrict__ dl,
-                      double *__restrict__ gb, double *__restrict__ dd, double *__restrict__ is,
-                      double *__restrict__ logdens, double *__restrict__ pz, double *__restrict__ pdiag) {
+    tree_prior_kernel(int64_t m_arg, const int *__restrict__ plan, const double *__restrict__ len_g, double tau0,
+                      double sigma2, const double *__restrict__ z, double *mu, double *dl, double *gb, double *dd,
+                      double *is, double *__restrict__ logdens, double *__restrict__ pz, double *__restrict__ pdiag) {
+    extern __shared__ __align__(16) unsigned char tree_smem[];
     __shared__ double sh[TREE_THREADS];
-    const TreePlan T = tree_plan_view(plan);
+    TreePlan T = tree_plan_view(plan);
     const int m = T.m;
     if ((int64_t)m != m_arg || T.levels < 1 || T.levels > m - 1) {  // a plan for another tree: touch no scratch
         for (int64_t i = threadIdx.x; i < m_arg; i += TREE_THREADS) {
@@ -69,6 +83,30 @@ __global__ void __launch_bounds__(TREE_THREADS)
         }
         if (logdens && threadIdx.x == 0) *logdens = NAN;
         return;
+    }
+    const int nn = 2 * m - 1;
+    const double *len = len_g;
+    if (STAGED) {
+        double *base = reinterpret_cast<double *>(tree_smem);
+        mu = base;
+        dl = mu + nn;
+        gb = dl + nn;
+        dd = gb + nn;
+        is = dd + nn;
+        double *len_s = is + nn;
+        int *ca = reinterpret_cast<int *>(len_s + nn), *cb = ca + nn, *order = cb + nn, *offs = order + (m - 1);
+        for (int v = threadIdx.x; v < nn; v += TREE_THREADS) {
+            len_s[v] = len_g[v];
+            ca[v] = T.ca[v];
+            cb[v] = T.cb[v];
+        }
+        for (int k = threadIdx.x; k < m - 1; k += TREE_THREADS) order[k] = T.order[k];
+        for (int k = threadIdx.x; k <= T.levels; k += TREE_THREADS) offs[k] = T.offs[k];
+        len = len_s;
+        T.ca = ca;
+        T.cb = cb;
+        T.order = order;
+        T.offs = offs;
     }
     for (int i = threadIdx.x; i < m; i += TREE_THREADS) {
         mu[i] = z[i];
@@ -135,8 +173,22 @@ cudaError_t launch_tree_prior(int64_t m, const int *plan, const double *len, dou
                               cudaStream_t s) {
     const int64_t nn = 2 * m - 1;
     double *mu = scratch, *dl = mu + nn, *gb = dl + nn, *dd = gb + nn, *is = dd + nn;
-    tree_prior_kernel<<<1, TREE_THREADS, 0, s>>>(m, plan, len, tau0, sigma2, z, mu, dl, gb, dd, is, logdens, pz,
-                                                 pdiag);
+    if (m <= TREE_SMEM_MAX_TIPS) {
+        const size_t bytes = tree_smem_bytes(m);
+        static int attr_set = 0;  // the opt-in limit is a per-function attribute: set once
+        if (!attr_set) {
+            const cudaError_t e = cudaFuncSetAttribute(tree_prior_kernel<true>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)tree_smem_bytes(TREE_SMEM_MAX_TIPS));
+            if (e != cudaSuccess) return e;
+            attr_set = 1;
+        }
+        tree_prior_kernel<true><<<1, TREE_THREADS, bytes, s>>>(m, plan, len, tau0, sigma2, z, mu, dl, gb, dd, is,
+                                                               logdens, pz, pdiag);
+    } else {
+        tree_prior_kernel<false><<<1, TREE_THREADS, 0, s>>>(m, plan, len, tau0, sigma2, z, mu, dl, gb, dd, is,
+                                                            logdens, pz, pdiag);
+    }
     return cudaGetLastError();
 }
 
