@@ -239,6 +239,15 @@ int hawkes_posterior(int64_t n, int64_t m, const int *seq_idx, const double *pre
                      const double *hdiag, void *ws, size_t ws_bytes, double *logpost, double *grad_q,
                      double *hdiag_q, void *stream);
 
+/* The assembly of hawkes_posterior_tree from a prior evaluated separately:
+ * pz = (sigma^2 V)^-1 z and pdiag = its diagonal (DEVICE double[m], from
+ * hawkes_tree_prior on z = q[6..6+m)), so that the prior can run on another
+ * stream while the likelihood is evaluated.  pdiag may be NULL when hdiag is.
+ * Other arguments and results as hawkes_posterior. */
+int hawkes_posterior_assemble(int64_t n, int64_t m, const int *seq_idx, const double *pz, const double *pdiag,
+                              const hawkes_prior *prior, const double *q, const double *loglik, const double *grad,
+                              const double *hdiag, double *logpost, double *grad_q, double *hdiag_q, void *stream);
+
 /* r[seq_idx[j]] = q[6 + j] for j < m (DEVICE vectors): the sampler's log-rates
  * into the likelihood's full log-rate vector. */
 int hawkes_hmc_scatter_rates(int64_t m, const int *seq_idx, const double *q, double *r, void *stream);

@@ -174,9 +174,9 @@ extern "C" {
 size_t hawkes_posterior_workspace_size(int64_t m) { return m < 0 ? 0 : (size_t)(m > 0 ? m : 1) * sizeof(double); }
 
 static int post_check(int64_t n, int64_t m, const hawkes_prior *prior, const double *q, const double *loglik,
-                      const double *grad, const double *hdiag, const void *ws, const double *logpost,
-                      const double *grad_q, const double *hdiag_q, hk::PostConsts *pc) {
-    if (n < 2 || m < 0 || m > n || !prior || !q || !loglik || !ws || !logpost) return HAWKES_EINVAL;
+                      const double *grad, const double *hdiag, const double *logpost, const double *grad_q,
+                      const double *hdiag_q, hk::PostConsts *pc) {
+    if (n < 2 || m < 0 || m > n || !prior || !q || !loglik || !logpost) return HAWKES_EINVAL;
     if ((grad == nullptr) != (grad_q == nullptr)) return HAWKES_EINVAL;
     if ((hdiag == nullptr) != (hdiag_q == nullptr)) return HAWKES_EINVAL;
     if (hdiag && !grad) return HAWKES_EINVAL;
@@ -194,8 +194,9 @@ int hawkes_posterior(int64_t n, int64_t m, const int *seq_idx, const double *pre
                      const double *q, const double *loglik, const double *grad, const double *hdiag, void *ws,
                      size_t ws_bytes, double *logpost, double *grad_q, double *hdiag_q, void *stream) {
     hk::PostConsts pc;
-    const int rc = post_check(n, m, prior, q, loglik, grad, hdiag, ws, logpost, grad_q, hdiag_q, &pc);
+    const int rc = post_check(n, m, prior, q, loglik, grad, hdiag, logpost, grad_q, hdiag_q, &pc);
     if (rc != HAWKES_OK) return rc;
+    if (!ws) return HAWKES_EINVAL;
     if (m > 0 && (!seq_idx || !prec)) return HAWKES_EINVAL;
     if (ws_bytes < hawkes_posterior_workspace_size(m)) return HAWKES_EWORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
@@ -221,8 +222,9 @@ int hawkes_posterior_tree(int64_t n, int64_t m, const int *seq_idx, const int *p
                           const double *loglik, const double *grad, const double *hdiag, void *ws, size_t ws_bytes,
                           double *logpost, double *grad_q, double *hdiag_q, void *stream) {
     hk::PostConsts pc;
-    const int rc = post_check(n, m, prior, q, loglik, grad, hdiag, ws, logpost, grad_q, hdiag_q, &pc);
+    const int rc = post_check(n, m, prior, q, loglik, grad, hdiag, logpost, grad_q, hdiag_q, &pc);
     if (rc != HAWKES_OK) return rc;
+    if (!ws) return HAWKES_EINVAL;
     if (m < 2 || m > HAWKES_TREE_MAX_TIPS || !seq_idx || !plan || !length) return HAWKES_EINVAL;
     if (!(sigma2 > 0) || !(root_var >= 0) || !isfinite(sigma2) || !isfinite(root_var)) return HAWKES_EINVAL;
     if (ws_bytes < hawkes_posterior_tree_workspace_size(m)) return HAWKES_EWORKSPACE;
@@ -233,6 +235,18 @@ int hawkes_posterior_tree(int64_t n, int64_t m, const int *seq_idx, const int *p
         return HAWKES_ECUDA;
     hk::posterior_assemble_kernel<<<1, hk::ASM_THREADS, 0, s>>>(m, pc, seq_idx, pd, 1, q, w, loglik, grad, hdiag,
                                                                 logpost, grad_q, hdiag_q);
+    return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
+}
+
+int hawkes_posterior_assemble(int64_t n, int64_t m, const int *seq_idx, const double *pz, const double *pdiag,
+                               const hawkes_prior *prior, const double *q, const double *loglik, const double *grad,
+                               const double *hdiag, double *logpost, double *grad_q, double *hdiag_q, void *stream) {
+    hk::PostConsts pc;
+    const int rc = post_check(n, m, prior, q, loglik, grad, hdiag, logpost, grad_q, hdiag_q, &pc);
+    if (rc != HAWKES_OK) return rc;
+    if (m > 0 && (!seq_idx || !pz || (hdiag && !pdiag))) return HAWKES_EINVAL;
+    hk::posterior_assemble_kernel<<<1, hk::ASM_THREADS, 0, (cudaStream_t)stream>>>(
+        m, pc, seq_idx, pdiag, 1, q, pz, loglik, grad, hdiag, logpost, grad_q, hdiag_q);
     return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
 }
 

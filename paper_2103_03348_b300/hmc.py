@@ -91,6 +91,9 @@ def _lib():
         L.hawkes_posterior_tree.argtypes = [i64, i64, vp, vp, vp, d, d, ctypes.POINTER(_Prior), vp, vp, vp, vp,
                                             vp, ctypes.c_size_t, vp, vp, vp, vp]
         L.hawkes_posterior_tree.restype = ctypes.c_int
+        L.hawkes_posterior_assemble.argtypes = [i64, i64, vp, vp, vp, ctypes.POINTER(_Prior), vp, vp, vp, vp, vp,
+                                                vp, vp, vp]
+        L.hawkes_posterior_assemble.restype = ctypes.c_int
         L.hawkes_hmc_scatter_rates.argtypes = [i64, vp, vp, vp, vp]
         L.hawkes_hmc_scatter_rates_trend.argtypes = [i64, ctypes.c_int, vp, vp, vp, vp, vp]
         L.hawkes_hmc_scatter_rates_trend.restype = ctypes.c_int
@@ -153,6 +156,12 @@ class Posterior:
             raise ValueError("trend must be [M, K] over the M >= 1 sequenced events")
         self.beta_var = float(beta_var)
         self.dim = 6 + self.m + self.k
+        if tree is not None:
+            # the tree prior runs on a side stream, concurrently with the likelihood
+            self.side = torch.cuda.Stream(device=t.device)
+            self.fork, self.join = torch.cuda.Event(), torch.cuda.Event()
+            self.pz = torch.empty(self.m, dtype=torch.float64, device=t.device)
+            self.pd = torch.empty(self.m, dtype=torch.float64, device=t.device)
         self.calls = {"grad": 0, "hess": 0}
 
     def evaluate(self, q, want_hess=False, out=None):
@@ -169,6 +178,7 @@ class Posterior:
             out = {"logpost": torch.empty((), **f64), "grad": torch.empty(self.dim, **f64),
                    "hdiag": torch.empty(self.dim, **f64)}
         self._scatter(q, stream)
+        self._prior_async(q, want_hess)
         # with no free log-rates the column pass is skipped (globals-only modes)
         mode = ("hess" if want_hess else "grad") if self.m > 0 else ("hess_globals" if want_hess else "grad_globals")
         hawkes._call(mode, self.x, self.y, self.t, self.r, q, self.precision, stream=stream, check=False,
@@ -186,18 +196,33 @@ class Posterior:
             _check(L.hawkes_hmc_scatter_rates_trend(self.m, self.k, _ptr(self.seq), _ptr(self.trend), _ptr(q),
                                                     _ptr(self.r), ctypes.c_void_p(stream)))
 
+    def _prior_async(self, q, want_diag):
+        """Tree prior: (sigma^2 V)^-1 z (and its diagonal) on the side stream,
+        forked after the state update; _assemble joins it."""
+        if self.tree is None:
+            return
+        cur = torch.cuda.current_stream(self.dev)
+        self.fork.record(cur)
+        self.side.wait_event(self.fork)
+        with torch.cuda.stream(self.side):
+            self.tree.evaluate(q[6:6 + self.m], out={"pz": self.pz, "pdiag": self.pd if want_diag else None})
+        self.join.record(self.side)
+
     def _assemble(self, q, grad, hdiag, logpost, grad_q, hdiag_q, stream):
         """Priors, Jacobian and the phylogenetic prior (dense or on the tree) on the device."""
         L = _lib()
-        common = (ctypes.byref(self.c_prior), _ptr(q), _ptr(self.like["loglik"]), _ptr(grad), _ptr(hdiag),
-                  _ptr(self.ws), ctypes.c_size_t(self.ws.numel()), _ptr(logpost), _ptr(grad_q), _ptr(hdiag_q),
-                  ctypes.c_void_p(stream))
         if self.tree is None:
-            _check(L.hawkes_posterior(self.n, self.m, _ptr(self.seq), _ptr(self.prec), *common))
+            _check(L.hawkes_posterior(self.n, self.m, _ptr(self.seq), _ptr(self.prec), ctypes.byref(self.c_prior),
+                                      _ptr(q), _ptr(self.like["loglik"]), _ptr(grad), _ptr(hdiag), _ptr(self.ws),
+                                      ctypes.c_size_t(self.ws.numel()), _ptr(logpost), _ptr(grad_q), _ptr(hdiag_q),
+                                      ctypes.c_void_p(stream)))
         else:
-            tr = self.tree
-            _check(L.hawkes_posterior_tree(self.n, self.m, _ptr(self.seq), _ptr(tr.plan), _ptr(tr.length),
-                                           tr.root_var, tr.sigma2, *common))
+            torch.cuda.current_stream(self.dev).wait_event(self.join)
+            _check(L.hawkes_posterior_assemble(self.n, self.m, _ptr(self.seq), _ptr(self.pz),
+                                               _ptr(self.pd) if hdiag is not None else None,
+                                               ctypes.byref(self.c_prior), _ptr(q), _ptr(self.like["loglik"]),
+                                               _ptr(grad), _ptr(hdiag), _ptr(logpost), _ptr(grad_q), _ptr(hdiag_q),
+                                               ctypes.c_void_p(stream)))
         if self.trend is not None:
             _check(L.hawkes_posterior_add_trend(self.m, self.k, _ptr(self.seq), _ptr(self.trend), self.beta_var,
                                                 _ptr(q), _ptr(grad), _ptr(hdiag), _ptr(logpost), _ptr(grad_q),
@@ -209,6 +234,7 @@ class Posterior:
         L = _lib()
         stream = torch.cuda.current_stream(self.dev).cuda_stream
         self._scatter(q, stream)
+        self._prior_async(q, False)
         hawkes._call("loglik", self.x, self.y, self.t, self.r, q, self.precision, stream=stream, check=False,
                      out=self.like, log_params=True)
         self.calls["loglik"] = self.calls.get("loglik", 0) + 1

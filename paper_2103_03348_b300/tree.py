@@ -72,14 +72,20 @@ class TreePrior:
         self.levels = int(host_plan[0])
         self.ws = torch.empty(int(_lib().hawkes_tree_workspace_size(self.m)), dtype=torch.uint8, device=device)
 
-    def evaluate(self, z, want=("logdens", "pz", "pdiag")):
-        """{'logdens': log N(z; 0, sigma2 V), 'pz': (sigma2 V)^-1 z, 'pdiag': diag((sigma2 V)^-1)}."""
+    def evaluate(self, z, want=("logdens", "pz", "pdiag"), out=None):
+        """{'logdens': log N(z; 0, sigma2 V), 'pz': (sigma2 V)^-1 z, 'pdiag': diag((sigma2 V)^-1)}.
+
+        out: optional dict of preallocated device tensors (a missing or None
+        entry is not computed); enqueued on the current stream."""
         L = _lib()
         z = z.contiguous()
         f64 = dict(dtype=torch.float64, device=z.device)
-        out = {"logdens": torch.empty((), **f64) if "logdens" in want else None,
-               "pz": torch.empty(self.m, **f64) if "pz" in want else None,
-               "pdiag": torch.empty(self.m, **f64) if "pdiag" in want else None}
+        if out is None:
+            out = {"logdens": torch.empty((), **f64) if "logdens" in want else None,
+                   "pz": torch.empty(self.m, **f64) if "pz" in want else None,
+                   "pdiag": torch.empty(self.m, **f64) if "pdiag" in want else None}
+        else:
+            out = {k: out.get(k) for k in ("logdens", "pz", "pdiag")}
         p = lambda t: ctypes.c_void_p(t.data_ptr() if t is not None else 0)  # noqa: E731
         s = ctypes.c_void_p(torch.cuda.current_stream(z.device).cuda_stream)
         _check(L.hawkes_tree_prior(self.m, p(self.plan), p(self.length), self.root_var, self.sigma2, p(z), p(self.ws),
