@@ -123,6 +123,14 @@ int hawkes_hess_diag(const double *x, const double *y, const double *t, const do
 enum { HAWKES_MODE_LOGLIK = 0, HAWKES_MODE_GRAD = 1, HAWKES_MODE_HESS = 2,
        HAWKES_MODE_GRAD_GLOBALS = 3, HAWKES_MODE_HESS_GLOBALS = 4 };
 
+/* Flag OR-ed into the mode of hawkes_eval_device_params: x, y, t, n and the
+ * precision are those of an earlier call on this same workspace (whose
+ * contents the caller has left alone), so their validation, tie groups,
+ * location groups and tile bounds are reused instead of recomputed; only r
+ * and the parameters may differ.  Results are identical to a call without
+ * the flag.  A sampler over fixed events sets it after its first call. */
+#define HAWKES_MODE_REUSE_EVENTS 16
+
 /* The three evaluations with the parameter vector in DEVICE memory, so that a
  * caller whose parameters are produced on the GPU (a sampler's state) needs no
  * host round trip between evaluations.  params_dev: DEVICE double[6] in the

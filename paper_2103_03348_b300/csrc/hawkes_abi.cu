@@ -77,8 +77,9 @@ static bool params_valid(const double *p) {
 // One thread derives every parameter-dependent constant in FP64.  Parameters
 // that are not finite and positive (tau_t may be +inf) set ST_BADPARAM, and
 // finalize then reports HAWKES_EINVAL with NaN outputs.
-__global__ void setup_kernel(ParamSource ps, int fp32c, Derived *out, int *hdr) {
+__global__ void setup_kernel(ParamSource ps, int fp32c, int reuse, Derived *out, int *hdr) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (reuse) hdr[0] |= hdr[3];  // the event checks of the call that prepared these events
     double p[6];
     bool ok = true;
     for (int k = 0; k < 6; ++k) {
@@ -123,8 +124,8 @@ __global__ void setup_kernel(ParamSource ps, int fp32c, Derived *out, int *hdr) 
     *out = d;
 }
 
-cudaError_t launch_setup(const Consts &c, const ParamSource &ps, const Workspace &ws, cudaStream_t s) {
-    setup_kernel<<<1, 32, 0, s>>>(ps, c.fp32c, ws.derived, ws.hdr);
+cudaError_t launch_setup(const Consts &c, const ParamSource &ps, const Workspace &ws, cudaStream_t s, int reuse) {
+    setup_kernel<<<1, 32, 0, s>>>(ps, c.fp32c, reuse, ws.derived, ws.hdr);
     return cudaGetLastError();
 }
 
@@ -136,7 +137,8 @@ struct Call {
     Outputs out;
     ParamSource ps;
     cudaStream_t s;
-    bool rates;  // the column pass runs
+    bool rates;   // the column pass runs
+    bool reuse;   // x, y, t and the workspace are those of an earlier call: skip their preparation
 };
 
 static int prepare(const double *x, const double *y, const double *t, const double *r, int64_t n,
@@ -145,6 +147,8 @@ static int prepare(const double *x, const double *y, const double *t, const doub
                    void *stream, Call *k) {
     if (n < 2 || n > HAWKES_MAX_EVENTS) return HAWKES_EINVAL;
     if (precision != HAWKES_FP64 && precision != HAWKES_FP32C && precision != HAWKES_FP32C_BAND) return HAWKES_EINVAL;
+    k->reuse = (mode & HAWKES_MODE_REUSE_EVENTS) != 0;
+    mode &= ~HAWKES_MODE_REUSE_EVENTS;
     // modes 3 and 4: gradient / Hessian diagonal of the six globals only (no column pass)
     if (mode < 0 || mode > 4) return HAWKES_EINVAL;
     k->rates = mode == MODE_GRAD || mode == MODE_HESS;
@@ -192,11 +196,16 @@ static int phase_rows(const Call &k, void *const *events) {
     const Consts &c = k.c;
     const Workspace &ws = k.ws;
     cudaStream_t s = k.s;
-    if (cudaMemsetAsync(ws.hdr, 0, 8 * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
-    if (cudaMemsetAsync(ws.hash, 0xFF, (size_t)c.g.hash_size * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
-    if (cudaMemsetAsync(ws.cnt, 0, (size_t)c.g.npad * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
-    if (launch_setup(c, k.ps, ws, s) != cudaSuccess) return HAWKES_ECUDA;
-    if (launch_prep(c, k.in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
+    if (k.reuse) {  // status and fix-up count only; hdr[3] keeps the event checks
+        if (cudaMemsetAsync(ws.hdr, 0, 2 * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
+        if (launch_setup(c, k.ps, ws, s, 1) != cudaSuccess) return HAWKES_ECUDA;
+    } else {
+        if (cudaMemsetAsync(ws.hdr, 0, 8 * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
+        if (cudaMemsetAsync(ws.hash, 0xFF, (size_t)c.g.hash_size * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
+        if (cudaMemsetAsync(ws.cnt, 0, (size_t)c.g.npad * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
+        if (launch_setup(c, k.ps, ws, s, 0) != cudaSuccess) return HAWKES_ECUDA;
+        if (launch_prep(c, k.in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
+    }
     if (launch_pack(c, k.in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
     if (!mark(events, 0, s)) return HAWKES_ECUDA;
     if (c.t1 > c.t0) {

@@ -124,7 +124,7 @@ struct Outputs {
 };
 
 // launchers (return cudaGetLastError())
-cudaError_t launch_setup(const Consts &c, const ParamSource &ps, const Workspace &ws, cudaStream_t s);
+cudaError_t launch_setup(const Consts &c, const ParamSource &ps, const Workspace &ws, cudaStream_t s, int reuse);
 cudaError_t launch_prep(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_pack(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_row32(const Consts &c, const Workspace &ws, cudaStream_t s);

@@ -40,8 +40,8 @@ __global__ void __launch_bounds__(TILE) prep_kernel(Consts c, Inputs in, Workspa
     if (valid) {
         xi = in.x[i];
         yi = in.y[i];
-        const double ti = in.t[i], ri = in.r[i];
-        if (!isfinite(xi) || !isfinite(yi) || !isfinite(ti) || !isfinite(ri)) bad |= ST_NONFINITE;
+        const double ti = in.t[i];
+        if (!isfinite(xi) || !isfinite(yi) || !isfinite(ti)) bad |= ST_NONFINITE;  // r: checked by pack
         if (i > 0 && !(in.t[i - 1] <= ti)) bad |= ST_UNSORTED;
         // tie-group start: first index j <= i with t_j == t_i (lower bound on a sorted prefix)
         int lo = 0, hi = i;
@@ -68,7 +68,10 @@ __global__ void __launch_bounds__(TILE) prep_kernel(Consts c, Inputs in, Workspa
         ws.gidx[i] = n;      // padding: never a causal source, never a target
         ws.loc[i] = -1 - i;  // padding: a location of its own
     }
-    if (bad) atomicOr(&ws.hdr[0], bad);
+    if (bad) {
+        atomicOr(&ws.hdr[0], bad);
+        atomicOr(&ws.hdr[3], bad);  // kept for calls that reuse these events
+    }
 
     // per-tile bounds of x and y (valid events only)
     double4_32a box;
@@ -158,6 +161,7 @@ __global__ void __launch_bounds__(TILE) pack_kernel(Consts c, Inputs in, Workspa
     __shared__ int shi[TILE];
 
     const int dup = valid ? (ws.cnt[ws.loc[i]] >= 2) : 0;
+    if (valid && !isfinite(in.r[i])) atomicOr(&ws.hdr[0], ST_NONFINITE);
 
     float tmin = INFINITY, tmax = -INFINITY, rtmax = -INFINITY;
     if (c.fp32c) {

@@ -142,11 +142,16 @@ def _raise_status(code: int):
 MODES = {"loglik": 0, "grad": 1, "hess": 2, "grad_globals": 3, "hess_globals": 4}
 
 
+REUSE_EVENTS = 16  # HAWKES_MODE_REUSE_EVENTS
+
+
 def _call(mode: str, x, y, t, r, params, precision="fp32c", stream=None, workspace=None, check=True, out=None,
-          phase_events=None, log_params=False):
+          phase_events=None, log_params=False, reuse_events=False):
     """One evaluation.  params: a 6-sequence or CPU tensor (passed as a host
     vector), or a CUDA float64 tensor whose first six entries are read on the
-    device (their logarithms when log_params) with no host round trip."""
+    device (their logarithms when log_params) with no host round trip.
+    reuse_events (device params only): x, y, t and the workspace are those of
+    an earlier call, whose event preparation is reused."""
     n = _check_events(x, y, t, r)
     p = PRECISIONS[precision]
     dev = t.device
@@ -177,7 +182,8 @@ def _call(mode: str, x, y, t, r, params, precision="fp32c", stream=None, workspa
             rc = L.hawkes_eval_device_params(
                 ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(t.data_ptr()),
                 ctypes.c_void_p(r.data_ptr()), ctypes.c_int64(n), ctypes.c_void_p(params.data_ptr()),
-                int(bool(log_params)), p, MODES[mode], ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()),
+                int(bool(log_params)), p, MODES[mode] | (REUSE_EVENTS if reuse_events else 0),
+                ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()),
                 *ptrs, st_p, ctypes.c_void_p(int(stream)))
         if rc != OK:
             raise HawkesError(rc, strerror(rc))

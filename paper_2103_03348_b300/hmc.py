@@ -150,6 +150,9 @@ class Posterior:
         f64 = dict(dtype=torch.float64, device=self.dev)
         self.like = {"loglik": torch.empty((), **f64), "grad": torch.empty(6 + self.n, **f64),
                      "hdiag": torch.empty(6 + self.n, **f64), "status": torch.empty((), dtype=torch.int32, device=self.dev)}
+        # a workspace of its own: after the first evaluation the events' preparation is reused
+        self.like_ws = torch.empty(hawkes.workspace_size(self.n, precision), dtype=torch.uint8, device=self.dev)
+        self.prepared = False
         self.trend = trend.to(torch.float64).contiguous() if trend is not None else None
         self.k = int(self.trend.shape[1]) if self.trend is not None else 0
         if self.trend is not None and (self.trend.shape[0] != self.m or self.m == 0):
@@ -182,7 +185,8 @@ class Posterior:
         # with no free log-rates the column pass is skipped (globals-only modes)
         mode = ("hess" if want_hess else "grad") if self.m > 0 else ("hess_globals" if want_hess else "grad_globals")
         hawkes._call(mode, self.x, self.y, self.t, self.r, q, self.precision, stream=stream, check=False,
-                     out=self.like, log_params=True)
+                     out=self.like, log_params=True, workspace=self.like_ws, reuse_events=self.prepared)
+        self.prepared = True
         self.calls["hess" if want_hess else "grad"] += 1
         self._assemble(q, self.like["grad"], self.like["hdiag"] if want_hess else None, out["logpost"],
                        out["grad"], out["hdiag"] if want_hess else None, stream)
@@ -236,7 +240,8 @@ class Posterior:
         self._scatter(q, stream)
         self._prior_async(q, False)
         hawkes._call("loglik", self.x, self.y, self.t, self.r, q, self.precision, stream=stream, check=False,
-                     out=self.like, log_params=True)
+                     out=self.like, log_params=True, workspace=self.like_ws, reuse_events=self.prepared)
+        self.prepared = True
         self.calls["loglik"] = self.calls.get("loglik", 0) + 1
         self._assemble(q, None, None, out["logpost"], None, None, stream)
         return out

@@ -265,3 +265,34 @@ def test_million_events_ragged():
     assert np.max(np.abs(g[6 + idx] - g_ref) / np.maximum(np.abs(g_ref), 1e-3 * scale_g)) <= 2e-3
     assert np.linalg.norm(g[6 + idx] - g_ref) <= 1e-4 * np.linalg.norm(g_ref)
     assert np.linalg.norm(h[6 + idx] - h_ref) <= 1e-4 * np.linalg.norm(h_ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_reused_event_preparation(prec):
+    """HAWKES_MODE_REUSE_EVENTS: a second call on the same events and workspace
+    skips their preparation and gives the same results bit for bit, with new
+    log-rates and parameters; a non-finite log-rate is still reported, and so
+    is the earlier call's unsorted-time status."""
+    H = hawkes_mod()
+    w = synth.make_uniform(12, 3001, r_sd=0.4)
+    x, y, t, r = dev(w.x), dev(w.y), dev(w.t), dev(w.r)
+    ws = torch.empty(H.workspace_size(w.n, prec), dtype=torch.uint8, device="cuda")
+    q = torch.tensor(np.log(w.params), dtype=torch.float64, device="cuda")
+    H._call("hess", x, y, t, r, q, prec, workspace=ws, log_params=True)
+    r2 = dev(w.r + 0.1)
+    q2 = q + 0.05
+    a = H._call("hess", x, y, t, r2, q2, prec, workspace=ws, log_params=True, reuse_events=True)
+    a = {k: v.clone() for k, v in a.items()}
+    b = H._call("hess", x, y, t, r2, q2, prec, log_params=True)  # fresh workspace, full preparation
+    for k in ("loglik", "grad", "hdiag"):
+        assert torch.equal(a[k], b[k]), k
+    rn = w.r.copy()
+    rn[17] = np.nan
+    out = H._call("hess", x, y, t, dev(rn), q2, prec, workspace=ws, log_params=True, reuse_events=True, check=False)
+    assert int(out["status"].item()) == H.ENONFINITE
+    tu = w.t.copy()
+    tu[[5, 6]] = tu[[6, 5]]
+    ws2 = torch.empty_like(ws)
+    H._call("hess", x, y, dev(tu), r, q, prec, workspace=ws2, log_params=True, check=False)
+    out = H._call("hess", x, y, dev(tu), r, q, prec, workspace=ws2, log_params=True, reuse_events=True, check=False)
+    assert int(out["status"].item()) == H.EUNSORTED
