@@ -175,13 +175,17 @@ cudaError_t launch_tree_prior(int64_t m, const int *plan, const double *len, dou
     double *mu = scratch, *dl = mu + nn, *gb = dl + nn, *dd = gb + nn, *is = dd + nn;
     if (m <= TREE_SMEM_MAX_TIPS) {
         const size_t bytes = tree_smem_bytes(m);
-        static int attr_set = 0;  // the opt-in limit is a per-function attribute: set once
-        if (!attr_set) {
+        // the opt-in limit is a per-function, per-device attribute: set once per device
+        // (outside any stream capture, since the first launch on a device is eager)
+        static int attr_set[64] = {0};
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return cudaGetLastError();
+        if (dev < 0 || dev >= 64 || !attr_set[dev]) {
             const cudaError_t e = cudaFuncSetAttribute(tree_prior_kernel<true>,
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                        (int)tree_smem_bytes(TREE_SMEM_MAX_TIPS));
             if (e != cudaSuccess) return e;
-            attr_set = 1;
+            if (dev >= 0 && dev < 64) attr_set[dev] = 1;
         }
         tree_prior_kernel<true><<<1, TREE_THREADS, bytes, s>>>(m, plan, len, tau0, sigma2, z, mu, dl, gb, dd, is,
                                                                logdens, pz, pdiag);
