@@ -119,6 +119,8 @@ __global__ void setup_kernel(ParamSource ps, int fp32c, int reuse, Derived *out,
     d.i_sx2 = 1.0 / (d.sx * d.sx);
     d.i_st = 1.0 / d.st;
     d.i_st2 = d.i_st * d.i_st;
+    d.ln_b = log(d.B);
+    d.log2_b = log2(d.B);
     d.valid = ok ? 1 : 0;
     if (!ok) atomicOr(&hdr[0], ST_BADPARAM);
     *out = d;

@@ -69,6 +69,7 @@ struct Derived {
     // reciprocals for the row epilogue (FP64 division is costly): 1/mu0, 1/tau_x,
     // 1/tau_t (0 when infinite), 1/theta0, 1/omega, 1/h, 1/sx^2, 1/st, 1/st^2
     double i_mu0, i_tx, i_tt, i_th0, i_om, i_h, i_sx2, i_st, i_st2;
+    double ln_b, log2_b;  // log B and log2 B: column weights in the log domain, log(B / lambda) = ln_b - log lambda
 };
 
 // Per-call constants known on the host (passed by value to every kernel).
@@ -105,7 +106,7 @@ struct Workspace {
     double *rowpart;     // [n_chunks * NMOM * npad]
     double *mom;         // [NMOM * npad]
     int *flagged;        // [npad]
-    double *w64;         // [npad]  FP64 column weight B / lambda_n
+    double *w64;         // [npad]  FP64 column weight, in logs: log(B / lambda_n)
     double *dLr;         // [npad]  dLambda / dr_m
     double *blockpart;   // [tiles * ACC_STRIDE]
     float *sufmax;       // [tiles] suffix max of the column weight bound (FP32C)

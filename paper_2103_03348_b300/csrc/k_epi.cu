@@ -80,46 +80,53 @@ __global__ void __launch_bounds__(TILE) epilogue_kernel(Consts c, Inputs in, Wor
         double ll = 0.0;
         if (lam > 0.0) {
             ll = log(lam);
-            const double il = 1.0 / lam;
             if (mode >= MODE_GRAD) {
-                const double a = D.A * il, b = D.B * il;
-                const double GD2 = M(MO_GD2) * D.i_sx2, GT2 = M(MO_GT2) * D.i_st2;
-                const double ET = M(MO_ET) * D.i_st, ED2 = M(MO_ED2) * D.i_sx2;
+                // Every ratio is (A or B times a moment) / lambda, multiplied in that order:
+                // A S_G <= lambda and B S_E <= lambda, so nothing overflows however small
+                // lambda is (A / lambda alone can).  Below 1e-300, divide instead of
+                // multiplying by 1 / lambda, which could overflow.
+                const double il = 1.0 / lam;
+                const bool tiny = !(lam > 1e-300);
+                auto over = [&](double v) { return tiny ? v / lam : v * il; };
+                const double AG = D.A * SG, BE = D.B * SE;
+                const double AGD2 = D.A * (M(MO_GD2) * D.i_sx2), AGT2 = D.A * (M(MO_GT2) * D.i_st2);
+                const double BET = D.B * (M(MO_ET) * D.i_st), BED2 = D.B * (M(MO_ED2) * D.i_sx2);
                 const double ix = D.i_tx, it = D.i_tt, ih = D.i_h;
                 const double ix2 = ix * ix, it2 = it * it, ih2 = ih * ih;
-                q1[0] = a * SG * D.i_mu0;
-                q1[1] = a * (GD2 * ix2 * ix - 2.0 * SG * ix);
-                q1[2] = D.tt_inf ? 0.0 : a * (GT2 * it2 * it - SG * it);
-                q1[3] = b * SE * D.i_th0;
-                q1[4] = b * (SE * D.i_om - ET);
-                q1[5] = b * (ED2 * ih2 * ih - 2.0 * SE * ih);
+                q1[0] = over(AG) * D.i_mu0;
+                q1[1] = over(AGD2 * ix2 * ix - 2.0 * AG * ix);
+                q1[2] = D.tt_inf ? 0.0 : over(AGT2 * it2 * it - AG * it);
+                q1[3] = over(BE) * D.i_th0;
+                q1[4] = over(BE * D.i_om - BET);
+                q1[5] = over(BED2 * ih2 * ih - 2.0 * BE * ih);
                 if (mode == MODE_HESS) {
-                    const double GD4 = M(MO_GD4) * D.i_sx2 * D.i_sx2, GT4 = M(MO_GT4) * D.i_st2 * D.i_st2;
-                    const double ET2 = M(MO_ET2) * D.i_st2, ED4 = M(MO_ED4) * D.i_sx2 * D.i_sx2;
+                    const double AGD4 = D.A * (M(MO_GD4) * D.i_sx2 * D.i_sx2);
+                    const double AGT4 = D.A * (M(MO_GT4) * D.i_st2 * D.i_st2);
+                    const double BET2 = D.B * (M(MO_ET2) * D.i_st2), BED4 = D.B * (M(MO_ED4) * D.i_sx2 * D.i_sx2);
                     const double ix4 = ix2 * ix2, it4 = it2 * it2, ih4 = ih2 * ih2;
                     double s2[6];
                     s2[0] = 0.0;
-                    s2[1] = a * (GD4 * ix4 * ix2 - 7.0 * GD2 * ix4 + 6.0 * SG * ix2);
-                    s2[2] = D.tt_inf ? 0.0 : a * (GT4 * it4 * it2 - 5.0 * GT2 * it4 + 2.0 * SG * it2);
+                    s2[1] = over(AGD4 * ix4 * ix2 - 7.0 * AGD2 * ix4 + 6.0 * AG * ix2);
+                    s2[2] = D.tt_inf ? 0.0 : over(AGT4 * it4 * it2 - 5.0 * AGT2 * it4 + 2.0 * AG * it2);
                     s2[3] = 0.0;
-                    s2[4] = b * (ET2 - 2.0 * ET * D.i_om);
-                    s2[5] = b * (ED4 * ih4 * ih2 - 7.0 * ED2 * ih4 + 6.0 * SE * ih2);
+                    s2[4] = over(BET2 - 2.0 * BET * D.i_om);
+                    s2[5] = over(BED4 * ih4 * ih2 - 7.0 * BED2 * ih4 + 6.0 * BE * ih2);
 #pragma unroll
                     for (int p = 0; p < 6; ++p) q2[p] = s2[p] - q1[p] * q1[p];
                     if (D.tt_inf) q2[2] = 0.0;
                 }
             }
             if (c.fp32c) {
-                // column weight g^ = log2(B / lambda_n) - t~_n (t~_n as packed)
+                // column weight g^ = log2(B / lambda_n) - t~_n (t~_n as packed), formed in logs
                 const float *f = reinterpret_cast<const float *>(ws.src32);
                 const float tt_n = -f[8 * (i >> 1) + 4 + (i & 1)];
-                ghat = (float)(log2(D.B * il) - (double)tt_n);
+                ghat = (float)((D.log2_b - ll * LOG2E) - (double)tt_n);
             } else {
-                ws.w64[i] = D.B * il;
+                ws.w64[i] = D.ln_b - ll;  // log(B / lambda_n)
             }
         } else {
             atomicOr(&ws.hdr[0], ST_ZERO);
-            if (!c.fp32c) ws.w64[i] = 0.0;
+            if (!c.fp32c) ws.w64[i] = -INFINITY;  // weight 0
         }
         if (c.fp32c) {
             float *f = reinterpret_cast<float *>(ws.src32);

@@ -78,7 +78,8 @@ cudaError_t launch_row64(const Consts &c, const Workspace &ws, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Column pass in FP64: v_nm = (B / lambda_n) exp(r_m - omega (t_n - t_m) - d^2/(2h^2)).
+// Column pass in FP64: v_nm = exp(log(B / lambda_n) + r_m - omega (t_n - t_m) - d^2/(2h^2)),
+// the weight kept in the log domain so that a tiny lambda_n cannot overflow it.
 template <int MODE>
 __global__ void __launch_bounds__(TILE) col64_kernel(Consts c, Workspace ws) {
     const Derived &D = *c.d;
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(TILE) col64_kernel(Consts c, Workspace ws) {
             if (m < sG[j]) {
                 const double4_32a t = sT[j];
                 const double dx = t.x - me.x, dy = t.y - me.y, dt = t.z - me.z;
-                const double v = sW[j] * exp(me.w - D.om * dt - D.ih * (dx * dx + dy * dy));
+                const double v = exp(sW[j] + me.w - D.om * dt - D.ih * (dx * dx + dy * dy));
                 c1 += v;
                 if (MODE == MODE_HESS) c2 += v * v;
             }

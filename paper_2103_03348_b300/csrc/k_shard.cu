@@ -11,7 +11,7 @@
 //   [NACC]         the shard's status bits (bit pattern of an int)
 //   [NACC + 1]     FP32C: the tile's largest column weight exponent g^ (float bits)
 //   [16, 16 + TILE) the tile's column weights: FP32C g^_n = log2(B / lambda_n) - t~_n
-//                  (float bits), FP64 B / lambda_n
+//                  (float bits), FP64 log(B / lambda_n)
 // An all-gather of the records gives every shard what the unsharded call
 // holds after its row epilogue, so every per-tile kernel that follows sees
 // identical inputs and the outputs match the unsharded call bit for bit.
