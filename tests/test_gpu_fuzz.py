@@ -2,7 +2,14 @@
 (2 to 700 events, ragged tails), parameters spread over orders of magnitude,
 clustered and uniform events, exact ties in time and repeated locations, and
 spread log-rates.  FP64 is held to 1e-10, FP32C and its band-skipping form to
-the stated FP32C bars; the band form must also equal FP32C bit for bit."""
+the stated FP32C bars; the band form must also equal FP32C bit for bit.
+
+One regime is looser by nature: an intensity below ~1e-290 means its FP64
+pair terms are subnormal (exp of about -709), with short mantissas on both
+sides; the row's Hessian term is a difference s2 - q1^2 that cancels by
+orders of magnitude, so the two summation orders then differ around 1e-7
+(seen on the tau_x entry).  There the Hessian diagonal's bar is 1e-6; the
+log-likelihood and gradient keep 1e-10."""
 import math
 
 import numpy as np
@@ -63,8 +70,10 @@ def test_random_problem(seed):
     if not np.isfinite(ref["loglik"]):
         pytest.skip("an event with zero intensity (the status test covers it)")
     ll, g, h = gpu(x, y, t, r, params, "fp64")
+    subnormal_rows = ref["lam"].min() < 1e-290
     assert rel(ll, ref["loglik"]) <= FP64_TOL
-    assert scaled_err(g, ref["grad"]) <= FP64_TOL and scaled_err(h, ref["hdiag"]) <= FP64_TOL
+    assert scaled_err(g, ref["grad"]) <= FP64_TOL
+    assert scaled_err(h, ref["hdiag"]) <= (1e-6 if subnormal_rows else FP64_TOL)
     ll, g, h = gpu(x, y, t, r, params, "fp32c")
     assert rel(ll, ref["loglik"]) <= FP32C_LL_TOL, (ll, ref["loglik"], params)
     assert norm_rel(g, ref["grad"]) <= FP32C_GNORM_TOL, (norm_rel(g, ref["grad"]), params)
