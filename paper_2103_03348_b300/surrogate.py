@@ -252,7 +252,7 @@ def sample(post, sur, q0, mass, eps, n_iter, n_steps=20, seed=0, monitor_every=1
     """Surrogate-trajectory HMC with the exact Metropolis accept.
 
     Every `monitor_every` iterations the exact gradient at the current state
-    judges the surrogate (relative error).  If the acceptance rate over the last
+    measures the surrogate's relative error.  If the acceptance rate over the last
     `fallback_window` iterations drops below `fallback_rate`, the remaining
     iterations use exact gradients."""
     dev = q0.device

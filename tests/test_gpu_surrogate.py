@@ -127,7 +127,7 @@ def test_surrogate_hmc_gains_over_exact_hmc():
     n_iter = 300
     ch_s = S.sample(post, sur, warm.last_q, warm.mass_t, warm.eps, n_iter, n_steps=20, seed=2, monitor_every=100)
     assert not ch_s.fell_back and ch_s.accept.mean() > 0.5
-    assert max(ch_s.monitor_errors) < 0.1  # the exact kernel judges the surrogate along the chain
+    assert max(ch_s.monitor_errors) < 0.1  # the exact kernel measures the surrogate's error along the chain
     ch_e = hmc.sample(post, warm.last_q, n_iter=n_iter, n_warmup=0, n_steps=20, eps0=warm.eps, seed=2,
                       mass_every=10 ** 9)
     ess_s = hmc.ess_all(ch_s.draws).min()
