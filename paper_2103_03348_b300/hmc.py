@@ -21,6 +21,7 @@ from __future__ import annotations
 import ctypes
 import dataclasses
 import math
+import os
 import time
 
 import numpy as np
@@ -357,43 +358,79 @@ class TrajectoryGraph:
         return self.out
 
 
+def save_state(path, state: dict):
+    """Write a sampler checkpoint atomically (a temporary file, then a rename)."""
+    tmp = f"{path}.tmp"
+    torch.save(state, tmp)
+    os.replace(tmp, path)
+
+
+def load_state(path) -> dict:
+    return torch.load(path, map_location="cpu", weights_only=False)
+
+
 def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_every=100, target_accept=0.8,
-           mass_floor=1e-2, seed=0, keep=None, record=None, use_graph=True):
+           mass_floor=1e-2, seed=0, keep=None, record=None, use_graph=True, checkpoint=None, checkpoint_every=0,
+           resume=None):
     """Run n_warmup + n_iter HMC iterations from q0 (device tensor); returns a Chain.
 
     keep: optional index array of coordinates to store (all by default);
     record: optional callback given every leapfrog position and its gradient;
     use_graph: after warm-up (step size fixed) replay each trajectory as one
-    captured CUDA graph (not with record, which needs every position)."""
+    captured CUDA graph (not with record, which needs every position);
+    checkpoint, checkpoint_every: write the whole sampler state (position,
+    gradient, mass, step size and its adaptation, both random streams, draws so
+    far, counters) to `checkpoint` every that many iterations;
+    resume: a checkpoint to continue from; the chain then equals the one that
+    was never interrupted, bit for bit (the other arguments must match)."""
     dev = q0.device
     gen = torch.Generator(device=dev)
     gen.manual_seed(seed)
     rng = np.random.default_rng(seed)
     dim = q0.numel()
     f64 = dict(dtype=torch.float64, device=dev)
-    q = q0.clone()
     p = torch.empty(dim, **f64)
-    cur = post.evaluate(q, want_hess=True)
-    cur = {k: v.clone() for k, v in cur.items()}
-    mass = torch.clamp(-cur["hdiag"], min=mass_floor)
-    n_mass = 1
-    minv = 1.0 / mass  # updated in place from here on (a captured trajectory reads it)
+    keep = np.arange(dim) if keep is None else np.asarray(keep)
+    keep_t = torch.as_tensor(keep, device=dev)
+    total = n_warmup + n_iter
+    da = DualAveraging(eps0, target_accept)
+    if resume is None:
+        q = q0.clone()
+        cur = post.evaluate(q, want_hess=True)
+        cur = {k: v.clone() for k, v in cur.items()}
+        mass = torch.clamp(-cur["hdiag"], min=mass_floor)
+        n_mass = 1
+        minv = 1.0 / mass  # updated in place from here on (a captured trajectory reads it)
+        eps = eps0
+        draws = np.empty((n_iter, len(keep)))
+        lps, acc, aprob = np.empty(n_iter), np.zeros(n_iter, bool), np.empty(n_iter)
+        start, spent_warm, spent_samp = 0, 0.0, 0.0
+    else:
+        st = load_state(resume)
+        if (st["n_iter"], st["n_warmup"], st["n_steps"], st["dim"]) != (n_iter, n_warmup, n_steps, dim):
+            raise ValueError("the checkpoint belongs to a chain with other settings")
+        q = st["q"].to(dev)
+        cur = {"logpost": st["logpost"].to(dev), "grad": st["grad"].to(dev)}
+        mass, minv = st["mass"].to(dev), st["minv"].to(dev)
+        n_mass, eps = st["n_mass"], st["eps"]
+        da.__dict__.update(st["dual_averaging"])
+        gen.set_state(st["gen_state"])
+        rng.bit_generator.state = st["rng_state"]
+        draws, lps, acc, aprob = st["draws"], st["lps"], st["acc"], st["aprob"]
+        post.calls.update(st["calls"])
+        start, spent_warm, spent_samp = st["it"], st["spent_warm"], st["spent_samp"]
     graph = None
     scratch = {"logpost": torch.empty((), **f64), "grad": torch.empty(dim, **f64), "hdiag": torch.empty(dim, **f64)}
     k0, k1 = torch.empty((), **f64), torch.empty((), **f64)
-    da = DualAveraging(eps0, target_accept)
-    eps = eps0
-    keep = np.arange(dim) if keep is None else np.asarray(keep)
-    keep_t = torch.as_tensor(keep, device=dev)
-    draws = np.empty((n_iter, len(keep)))
-    lps, acc, aprob = np.empty(n_iter), np.zeros(n_iter, bool), np.empty(n_iter)
-    t_start = time.perf_counter()
-    t_sample = None
-    for it in range(n_warmup + n_iter):
+    torch.cuda.synchronize()
+    t_seg = time.perf_counter()  # start of the current warm-up or sampling segment
+    for it in range(start, total):
         if it == n_warmup:
             eps = da.final() if n_warmup > 0 else eps
             torch.cuda.synchronize()
-            t_sample = time.perf_counter()
+            now = time.perf_counter()
+            spent_warm += now - t_seg
+            t_seg = now
         torch.randn(dim, generator=gen, out=p, dtype=torch.float64, device=dev)
         p.mul_(torch.sqrt(mass))
         kinetic(p, minv, k0)
@@ -436,12 +473,34 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
             lps[j] = cur["logpost"].item()
             acc[j] = accepted
             aprob[j] = a
+        if checkpoint and checkpoint_every and (it + 1) % checkpoint_every == 0 and it + 1 < total:
+            torch.cuda.synchronize()
+            now = time.perf_counter()
+            seg = now - t_seg
+            save_state(checkpoint, {
+                "it": it + 1, "n_iter": n_iter, "n_warmup": n_warmup, "n_steps": n_steps, "dim": dim,
+                "q": q.cpu(), "logpost": cur["logpost"].cpu(), "grad": cur["grad"].cpu(),
+                "mass": mass.cpu(), "minv": minv.cpu(), "n_mass": n_mass, "eps": eps,
+                "dual_averaging": dict(da.__dict__), "gen_state": gen.get_state(),
+                "rng_state": rng.bit_generator.state, "draws": draws, "lps": lps, "acc": acc, "aprob": aprob,
+                "calls": dict(post.calls),
+                "spent_warm": spent_warm + (seg if it < n_warmup else 0.0),
+                "spent_samp": spent_samp + (seg if it >= n_warmup else 0.0)})
+            # the checkpoint's own cost is left out of both phases
+            if it < n_warmup:
+                spent_warm += seg
+            else:
+                spent_samp += seg
+            t_seg = time.perf_counter()
     torch.cuda.synchronize()
-    t_end = time.perf_counter()
-    if t_sample is None:  # warm-up only: report the adapted step size
-        t_sample = t_end
+    now = time.perf_counter()
+    if total > n_warmup and max(start, n_warmup) < total:
+        spent_samp += now - t_seg
+    else:
+        spent_warm += now - t_seg
+    if n_iter == 0:  # warm-up only: report the adapted step size
         eps = da.final() if n_warmup > 0 else eps
-    return Chain(draws, lps, acc, aprob, eps, mass.cpu().numpy(), t_end - t_sample, t_sample - t_start,
+    return Chain(draws, lps, acc, aprob, eps, mass.cpu().numpy(), spent_samp, spent_warm,
                  post.calls["grad"], post.calls["hess"], q, mass)
 
 

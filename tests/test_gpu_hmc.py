@@ -189,3 +189,27 @@ def test_graph_replayed_trajectories_equal_eager_ones():
     b = hmc.sample(make(), q0, n_iter=40, n_warmup=20, n_steps=8, eps0=0.05, mass_every=15, seed=3, use_graph=True)
     assert np.array_equal(a.draws, b.draws) and np.array_equal(a.accept, b.accept)
     assert b.grad_calls == a.grad_calls + 8  # one eager trajectory before the capture
+
+
+def test_checkpoint_resume_equals_uninterrupted_chain(tmp_path):
+    """A chain checkpointed in warm-up and again in sampling, then resumed from
+    each checkpoint, ends exactly where the uninterrupted chain ends."""
+    from paper_2103_03348_b300 import build, hmc, tree
+    build.build()
+    w, prec = problem()
+    d = lambda a: torch.tensor(np.asarray(a, float), dtype=torch.float64, device="cuda")  # noqa: E731
+    tp = tree.TreePrior(w.tree_parent, w.tree_length, 0.0, 1.0)
+
+    def make():
+        return hmc.Posterior(d(w.x), d(w.y), d(w.t), d(w.r), torch.tensor(w.sequenced, device="cuda"), None,
+                             hmc.prior_km_days(), "fp32c", tree=tp)
+
+    q0 = d(np.concatenate([np.log(w.params), w.r[w.sequenced]]))
+    kw = dict(n_iter=15, n_warmup=30, n_steps=6, eps0=0.05, mass_every=12, seed=9)
+    full = hmc.sample(make(), q0, **kw)
+    for every in (25, 35):  # the last checkpoint falls in warm-up (25), then in sampling (35)
+        ck = str(tmp_path / f"ck{every}.pt")
+        hmc.sample(make(), q0, checkpoint=ck, checkpoint_every=every, **kw)
+        resumed = hmc.sample(make(), q0, resume=ck, **kw)
+        assert np.array_equal(resumed.draws, full.draws) and np.array_equal(resumed.accept, full.accept)
+        assert resumed.eps == full.eps and np.array_equal(resumed.mass, full.mass)
