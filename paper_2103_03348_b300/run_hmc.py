@@ -1,7 +1,7 @@
 """Preconditioned HMC over the phylogenetic Hawkes posterior, reported as ESS/s.
 
     python -m paper_2103_03348_b300.run_hmc [--precision fp32c_band|fp32c|fp64] [--iters 2000] [--warmup 200]
-                                            [--prior tree|dense]
+                                            [--prior tree|dense] [--checkpoint PATH [--every K]] [--resume PATH]
 
 Workload: the 23,422-event synthetic pattern with 1,610 sequenced events whose
 log-rates are free (the phylogenetic prior on the generator's coalescent tree,
@@ -25,7 +25,7 @@ from . import build, hmc, synth, tree
 
 
 def run(precision="fp32c_band", iters=2000, warmup=200, n_steps=20, mass_every=100, eps0=0.05, seed=0, n=23422,
-        m_seq=1610, device="cuda", prior="tree"):
+        m_seq=1610, device="cuda", prior="tree", checkpoint=None, checkpoint_every=0, resume=None):
     build.build()
     w = synth.make_ebola_like(n=n, m_seq=m_seq)
     d = lambda a: torch.tensor(np.asarray(a, float), dtype=torch.float64, device=device)  # noqa: E731
@@ -39,7 +39,7 @@ def run(precision="fp32c_band", iters=2000, warmup=200, n_steps=20, mass_every=1
     q0 = d(np.concatenate([np.log(w.params), w.r[w.sequenced]]))
     t0 = time.perf_counter()
     ch = hmc.sample(post, q0, n_iter=iters, n_warmup=warmup, n_steps=n_steps, eps0=eps0, mass_every=mass_every,
-                    seed=seed)
+                    seed=seed, checkpoint=checkpoint, checkpoint_every=checkpoint_every, resume=resume)
     total = time.perf_counter() - t0
     ess = hmc.ess_all(ch.draws)
     eg, er = ess[:6], ess[6:]
@@ -71,8 +71,12 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--prior", default="tree", choices=["tree", "dense"])
+    ap.add_argument("--checkpoint", default=None, help="write the sampler state here every --every iterations")
+    ap.add_argument("--every", type=int, default=200)
+    ap.add_argument("--resume", default=None, help="continue the chain from this checkpoint")
     a = ap.parse_args()
-    print(json.dumps(run(a.precision, a.iters, a.warmup, a.steps, seed=a.seed, prior=a.prior)), flush=True)
+    print(json.dumps(run(a.precision, a.iters, a.warmup, a.steps, seed=a.seed, prior=a.prior, checkpoint=a.checkpoint,
+                         checkpoint_every=a.every if a.checkpoint else 0, resume=a.resume)), flush=True)
 
 
 if __name__ == "__main__":
