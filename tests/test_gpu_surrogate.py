@@ -135,3 +135,9 @@ def test_surrogate_hmc_gains_over_exact_hmc():
     calls_e = ch_e.grad_calls + ch_e.hess_calls
     assert ess_s / ch_s.exact_loglik_calls > 5 * ess_e / calls_e, (ess_s, ch_s.exact_loglik_calls, ess_e, calls_e)
     assert ess_s / ch_s.seconds > 2 * ess_e / ch_e.seconds, (ess_s, ch_s.seconds, ess_e, ch_e.seconds)
+    # equal accuracy: both chains target the same posterior, so their means of the
+    # six log-globals agree within the combined Monte Carlo standard errors
+    es, ee = hmc.ess_all(ch_s.draws), hmc.ess_all(ch_e.draws)
+    mcse = np.sqrt(ch_s.draws.var(0) / es + ch_e.draws.var(0) / ee)
+    gap = np.abs(ch_s.draws.mean(0) - ch_e.draws.mean(0))
+    assert np.all(gap <= 4.5 * mcse), (gap, mcse)
