@@ -145,6 +145,23 @@ int hawkes_eval_device_params(const double *x, const double *y, const double *t,
                               size_t ws_bytes, double *loglik, double *grad, double *hdiag, int *dev_status,
                               void *stream);
 
+/* hawkes_eval_device_params for modes HAWKES_MODE_GRAD / HAWKES_MODE_HESS (the
+ * HAWKES_MODE_REUSE_EVENTS flag allowed) with the rate entries wanted only for
+ * the sources rate_idx[0..k_rates) (DEVICE int, distinct, any order, each in
+ * [0, n); sorted indices make the FP32C pass cheapest):
+ * the column pass then costs O(n k) instead of O(n^2) in FP32C (FP64 covers
+ * every source and writes the subset).  Entries 6 + rate_idx[j] of grad and
+ * hdiag are written; the other rate entries are left as they were; loglik and
+ * entries [0, 6) as usual.  An index outside [0, n) is skipped and gives
+ * *dev_status = HAWKES_EINVAL (the outputs are then not valid).  Returns
+ * HAWKES_EINVAL for k_rates < 0 or > n, a NULL rate_idx with k_rates > 0, or
+ * another mode.  The paper's samplers move the rates of the M
+ * sequenced events only (Section 2.3.2), which this serves. */
+int hawkes_eval_rates_subset(const double *x, const double *y, const double *t, const double *r, int64_t n,
+                             const double *params_dev, int log_params, int precision, int mode, const int *rate_idx,
+                             int64_t k_rates, void *ws, size_t ws_bytes, double *loglik, double *grad, double *hdiag,
+                             int *dev_status, void *stream);
+
 /* hawkes_hess_diag with phase markers, for profiling.  phase_events holds four
  * cudaEvent_t handles (as void*, created by the caller; any may be NULL) that
  * are recorded on the stream: [0] before and [1] after the row pass (the

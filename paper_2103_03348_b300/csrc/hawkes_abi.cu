@@ -141,6 +141,9 @@ struct Call {
     cudaStream_t s;
     bool rates;   // the column pass runs
     bool reuse;   // x, y, t and the workspace are those of an earlier call: skip their preparation
+    bool subset = false;            // rate entries only for rate_idx[0..k_rates)
+    const int *rate_idx = nullptr;
+    int k_rates = 0;
 };
 
 static int prepare(const double *x, const double *y, const double *t, const double *r, int64_t n,
@@ -231,6 +234,18 @@ static int phase_cols(const Call &k, void *const *events) {
     if (launch_finalize(c, k.ws, k.out, s) != cudaSuccess) return HAWKES_ECUDA;
     if (c.mode >= MODE_GRAD && k.rates) {
         if (!mark(events, 2, s)) return HAWKES_ECUDA;
+        if (k.subset) {  // a subset of the sources (FP64 covers all of them and writes the subset)
+            if (k.k_rates > 0) {
+                if ((c.fp32c ? launch_col32_subset(c, k.in, k.ws, k.rate_idx, k.k_rates, s)
+                             : launch_col64(c, k.ws, s)) != cudaSuccess)
+                    return HAWKES_ECUDA;
+            }
+            if (!mark(events, 3, s)) return HAWKES_ECUDA;
+            if (k.k_rates > 0 &&
+                launch_colfinish_subset(c, k.ws, k.out, k.rate_idx, k.k_rates, c.fp32c, s) != cudaSuccess)
+                return HAWKES_ECUDA;
+            return HAWKES_OK;
+        }
         if (c.t1 > c.t0) {
             if ((c.fp32c ? launch_col32(c, k.in, k.ws, s) : launch_col64(c, k.ws, s)) != cudaSuccess)
                 return HAWKES_ECUDA;
@@ -367,6 +382,25 @@ int hawkes_shard_cols(const double *x, const double *y, const double *t, const d
                       double *hdiag, int *dev_status, void *stream) {
     return hk::shard_phase(x, y, t, r, n, params, precision, mode, shard, n_shards, ws, ws_bytes, (void *)xbuf,
                            xbuf_bytes, loglik, grad, hdiag, dev_status, stream, true);
+}
+
+int hawkes_eval_rates_subset(const double *x, const double *y, const double *t, const double *r, int64_t n,
+                             const double *params_dev, int log_params, int precision, int mode, const int *rate_idx,
+                             int64_t k_rates, void *ws, size_t ws_bytes, double *loglik, double *grad, double *hdiag,
+                             int *dev_status, void *stream) {
+    if (!params_dev || k_rates < 0 || k_rates > n || (k_rates > 0 && !rate_idx)) return HAWKES_EINVAL;
+    const int base = mode & ~HAWKES_MODE_REUSE_EVENTS;
+    if (base != HAWKES_MODE_GRAD && base != HAWKES_MODE_HESS) return HAWKES_EINVAL;
+    hk::Call k;
+    int rc = hk::prepare(x, y, t, r, n, nullptr, params_dev, log_params, precision, ws, ws_bytes, mode, loglik, grad,
+                         hdiag, dev_status, stream, &k);
+    if (rc != HAWKES_OK) return rc;
+    k.subset = true;
+    k.rate_idx = rate_idx;
+    k.k_rates = (int)k_rates;
+    rc = hk::phase_rows(k, nullptr);
+    if (rc != HAWKES_OK) return rc;
+    return hk::phase_cols(k, nullptr);
 }
 
 const char *hawkes_strerror(int status) {

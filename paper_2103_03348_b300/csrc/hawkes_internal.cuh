@@ -137,6 +137,10 @@ cudaError_t launch_finalize(const Consts &c, const Workspace &ws, const Outputs 
 cudaError_t launch_col32(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_col64(const Consts &c, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_colfinish(const Consts &c, const Workspace &ws, const Outputs &out, cudaStream_t s);
+cudaError_t launch_col32_subset(const Consts &c, const Inputs &in, const Workspace &ws, const int *rate_idx,
+                                int k_rates, cudaStream_t s);
+cudaError_t launch_colfinish_subset(const Consts &c, const Workspace &ws, const Outputs &out, const int *rate_idx,
+                                    int k_rates, int by_position, cudaStream_t s);
 cudaError_t launch_shard_export(const Consts &c, const Workspace &ws, double *xbuf, cudaStream_t s);
 cudaError_t launch_shard_import(const Consts &c, const Workspace &ws, const double *xbuf, cudaStream_t s);
 cudaError_t launch_tree_prior(int64_t m, const int *plan, const double *len, double tau0, double sigma2,

@@ -15,6 +15,8 @@
 // source (tie-group index), or when 2^(max g^ + max r^) < 2^-128 so that every
 // term underflows to exactly 0 in FP32; the sweep stops once the suffix max of
 // g^ shows that all later tiles underflow too.  Precision as in the row pass.
+#include <climits>
+
 #include "hawkes_internal.cuh"
 
 namespace hk {
@@ -98,6 +100,99 @@ __global__ void __launch_bounds__(TILE, 4) col32_kernel(Consts c, Inputs in, Wor
     }
     ws.colpart[((size_t)chunk * 2 + 0) * npad + m] = (double)s1 - (double)k1;
     if (MODE == MODE_HESS) ws.colpart[((size_t)chunk * 2 + 1) * npad + m] = (double)s2 - (double)k2;
+}
+
+// The same pass for a subset of sources only (a sampler whose free log-rates are
+// those of M sequenced events needs O(N M) work, not O(N^2)).  Block k owns
+// sources rate_idx[128k .. 128k+128) (any order); its tile statistics (lowest
+// and highest source index, largest r^) are reduced at the start, and the
+// target sweep, chunking and skip rules are those of col32_kernel.  The
+// partials go to colpart[chunk][.][j] for the subset position j.
+template <int MODE>
+__global__ void __launch_bounds__(TILE, 4) col32_subset_kernel(Consts c, Inputs in, Workspace ws,
+                                                               const int *__restrict__ rate_idx, int k_rates) {
+    const Derived &D = *c.d;
+    const int j = blockIdx.x * TILE + threadIdx.x, chunk = blockIdx.y;
+    const int n = c.g.n, npad = c.g.npad;
+    const int raw = j < k_rates ? rate_idx[j] : -1;
+    const bool valid = raw >= 0 && raw < n;  // an index outside [0, n) is skipped and reported
+    if (j < k_rates && !valid && chunk == 0) atomicOr(&ws.hdr[0], ST_BADPARAM);
+    const int m = valid ? raw : 0;
+    __shared__ float4 sAB[2][TILE];
+    __shared__ int sG[2][TILE];
+    __shared__ float shf[TILE];
+    __shared__ int shi[TILE];
+
+    float2 xm, ym, rm;
+    float r = -1.0e9f;
+    {
+        const float *f = reinterpret_cast<const float *>(ws.src32);
+        const int p = m >> 1, l = m & 1;
+        xm = splat(valid ? -f[8 * p + 0 + l] : 1.0e9f);
+        ym = splat(valid ? -f[8 * p + 2 + l] : 1.0e9f);
+        if (valid && m < n) r = (float)(in.r[m] * LOG2E + (in.t[m] - ws.centre[2]) * D.st);
+        rm = splat(r);
+    }
+    // tile statistics of this block's sources (uniform for the block)
+    const float rmax = block_max<TILE>(r, shf);
+    shi[threadIdx.x] = valid ? m : INT_MAX;
+    __syncthreads();
+    for (int w = TILE / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) shi[threadIdx.x] = min(shi[threadIdx.x], shi[threadIdx.x + w]);
+        __syncthreads();
+    }
+    const int m_first = shi[0];
+    __syncthreads();
+    shi[threadIdx.x] = valid ? m : -1;
+    __syncthreads();
+    for (int w = TILE / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) shi[threadIdx.x] = max(shi[threadIdx.x], shi[threadIdx.x + w]);
+        __syncthreads();
+    }
+    const int m_last = shi[0];
+    const float2 nhh2 = splat(-D.hh);
+
+    float2 run1 = make_float2(0.f, 0.f), run2 = make_float2(0.f, 0.f);
+    float s1 = 0.f, k1 = 0.f, s2 = 0.f, k2 = 0.f;
+
+    const int tile0 = m_first / TILE;
+    const int ub = tile0 + chunk * c.g.chunk_tiles;
+    const int ue = min(c.g.tiles, ub + c.g.chunk_tiles);
+    int buf = 0;
+    for (int u = ub; u < ue; ++u) {
+        if (ws.sufmax[u] + rmax < EXP2_DEAD) break;  // this and every later tile underflow
+        const int4 tiU = ws.tinfo[u];
+        const float4 stU = ws.tstat32[u];
+        if (tiU.y <= m_first) continue;               // no target of u follows any source
+        if (stU.w + rmax < EXP2_DEAD) continue;       // every term underflows
+        const int u0 = u * TILE;
+        sAB[buf][threadIdx.x] = ws.src32[(size_t)u0 + threadIdx.x];
+        sG[buf][threadIdx.x] = ws.gidx[(size_t)u0 + threadIdx.x];
+        __syncthreads();
+        const int npairs = (tiU.w + 1) >> 1;
+        const bool all_causal = m_last < tiU.x;
+        if (all_causal) col_tile<MODE, false>(sAB[buf], sG[buf], npairs, xm, ym, rm, m, nhh2, run1, run2);
+        else col_tile<MODE, true>(sAB[buf], sG[buf], npairs, xm, ym, rm, valid ? m : INT_MAX, nhh2, run1, run2);
+        kahan(s1, k1, __fadd_rn(run1.x, run1.y));
+        run1 = make_float2(0.f, 0.f);
+        if (MODE == MODE_HESS) {
+            kahan(s2, k2, __fadd_rn(run2.x, run2.y));
+            run2 = make_float2(0.f, 0.f);
+        }
+        buf ^= 1;
+    }
+    if (valid) {
+        ws.colpart[((size_t)chunk * 2 + 0) * npad + j] = (double)s1 - (double)k1;
+        if (MODE == MODE_HESS) ws.colpart[((size_t)chunk * 2 + 1) * npad + j] = (double)s2 - (double)k2;
+    }
+}
+
+cudaError_t launch_col32_subset(const Consts &c, const Inputs &in, const Workspace &ws, const int *rate_idx,
+                                int k_rates, cudaStream_t s) {
+    const dim3 grid((k_rates + TILE - 1) / TILE, c.g.n_chunks);
+    if (c.mode == MODE_HESS) col32_subset_kernel<MODE_HESS><<<grid, TILE, 0, s>>>(c, in, ws, rate_idx, k_rates);
+    else col32_subset_kernel<MODE_GRAD><<<grid, TILE, 0, s>>>(c, in, ws, rate_idx, k_rates);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_col32(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s) {

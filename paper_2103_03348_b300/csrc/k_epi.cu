@@ -272,6 +272,46 @@ __global__ void __launch_bounds__(CB_THREADS) colfinish_kernel(Consts c, Workspa
     if (out.hdiag) out.hdiag[6 + m] = hd;
 }
 
+// The finish for a subset of sources: entry 6 + rate_idx[j] of grad / hdiag,
+// with the partials at subset position j (FP32C subset pass) or at the event
+// index (FP64, whose column pass covers every source).  An index outside
+// [0, n) is reported here, after finalize (which has written the status).
+__global__ void __launch_bounds__(CB_THREADS) colfinish_subset_kernel(Consts c, Workspace ws, Outputs out,
+                                                                      const int *__restrict__ rate_idx, int k_rates,
+                                                                      int by_position) {
+    const int j = blockIdx.x * CB_THREADS + threadIdx.x;
+    const int bits = ws.hdr[0];
+    if (j == 0 && (bits & ST_BADPARAM)) *out.dev_status = HAWKES_EINVAL;
+    if (j >= k_rates) return;
+    const int m = rate_idx[j];
+    if (m < 0 || m >= c.g.n) {
+        *out.dev_status = HAWKES_EINVAL;
+        return;
+    }
+    const int npad = c.g.npad, at = by_position ? j : m;
+    double c1 = 0.0, c2 = 0.0;
+    for (int ch = 0; ch < c.g.n_chunks; ++ch) {
+        c1 += ws.colpart[((size_t)ch * 2 + 0) * npad + at];
+        if (c.mode == MODE_HESS) c2 += ws.colpart[((size_t)ch * 2 + 1) * npad + at];
+    }
+    const double dl = ws.dLr[m];
+    double g = c1 - dl, hd = c1 - c2 - dl;
+    if (bits != 0) {
+        const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+        g = qnan;
+        hd = qnan;
+    }
+    if (out.grad) out.grad[6 + m] = g;
+    if (out.hdiag) out.hdiag[6 + m] = hd;
+}
+
+cudaError_t launch_colfinish_subset(const Consts &c, const Workspace &ws, const Outputs &out, const int *rate_idx,
+                                    int k_rates, int by_position, cudaStream_t s) {
+    colfinish_subset_kernel<<<(k_rates + CB_THREADS - 1) / CB_THREADS, CB_THREADS, 0, s>>>(c, ws, out, rate_idx,
+                                                                                           k_rates, by_position);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_colfinish(const Consts &c, const Workspace &ws, const Outputs &out, cudaStream_t s) {
     colfinish_kernel<<<((c.t1 - c.t0) * TILE + CB_THREADS - 1) / CB_THREADS, CB_THREADS, 0, s>>>(c, ws, out);
     return cudaGetLastError();

@@ -66,6 +66,9 @@ def lib():
             L.hawkes_eval_device_params.argtypes = [vp, vp, vp, vp, i64, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                     vp, sz, vp, vp, vp, ip, vp]
             L.hawkes_eval_device_params.restype = ctypes.c_int
+            L.hawkes_eval_rates_subset.argtypes = [vp, vp, vp, vp, i64, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   vp, i64, vp, sz, vp, vp, vp, vp, vp]
+            L.hawkes_eval_rates_subset.restype = ctypes.c_int
             L.hawkes_hess_diag_timed.restype = ctypes.c_int
             L.hawkes_strerror.argtypes = [ctypes.c_int]
             L.hawkes_strerror.restype = ctypes.c_char_p
@@ -146,12 +149,14 @@ REUSE_EVENTS = 16  # HAWKES_MODE_REUSE_EVENTS
 
 
 def _call(mode: str, x, y, t, r, params, precision="fp32c", stream=None, workspace=None, check=True, out=None,
-          phase_events=None, log_params=False, reuse_events=False):
+          phase_events=None, log_params=False, reuse_events=False, rate_idx=None):
     """One evaluation.  params: a 6-sequence or CPU tensor (passed as a host
     vector), or a CUDA float64 tensor whose first six entries are read on the
     device (their logarithms when log_params) with no host round trip.
     reuse_events (device params only): x, y, t and the workspace are those of
-    an earlier call, whose event preparation is reused."""
+    an earlier call, whose event preparation is reused.
+    rate_idx (device params, modes grad / hess): a device int32 tensor of the
+    sources whose rate entries are wanted; only those entries are written."""
     n = _check_events(x, y, t, r)
     p = PRECISIONS[precision]
     dev = t.device
@@ -168,6 +173,12 @@ def _call(mode: str, x, y, t, r, params, precision="fp32c", stream=None, workspa
     elif isinstance(stream, torch.cuda.Stream):
         stream = stream.cuda_stream
     L = lib()
+    if rate_idx is not None:
+        if not (isinstance(params, torch.Tensor) and params.is_cuda) or mode not in ("grad", "hess"):
+            raise ValueError("rate_idx needs device params and mode grad or hess")
+        if rate_idx.dtype != torch.int32 or rate_idx.dim() != 1 or not rate_idx.is_contiguous() \
+                or rate_idx.device != dev:
+            raise TypeError("rate_idx must be a contiguous 1-D int32 tensor on the events' device")
     if isinstance(params, torch.Tensor) and params.is_cuda:
         if params.dtype != torch.float64 or not params.is_contiguous() or params.numel() < 6:
             raise TypeError("device params must be a contiguous float64 CUDA tensor with at least 6 entries")
@@ -178,13 +189,17 @@ def _call(mode: str, x, y, t, r, params, precision="fp32c", stream=None, workspa
             ptrs[2] = ctypes.c_void_p(0)
         if mode == "loglik":
             ptrs[1] = ctypes.c_void_p(0)
+        common = (ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                  ctypes.c_void_p(r.data_ptr()), ctypes.c_int64(n), ctypes.c_void_p(params.data_ptr()),
+                  int(bool(log_params)), p, MODES[mode] | (REUSE_EVENTS if reuse_events else 0))
         with torch.cuda.device(dev):
-            rc = L.hawkes_eval_device_params(
-                ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(t.data_ptr()),
-                ctypes.c_void_p(r.data_ptr()), ctypes.c_int64(n), ctypes.c_void_p(params.data_ptr()),
-                int(bool(log_params)), p, MODES[mode] | (REUSE_EVENTS if reuse_events else 0),
-                ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()),
-                *ptrs, st_p, ctypes.c_void_p(int(stream)))
+            if rate_idx is not None:
+                rc = L.hawkes_eval_rates_subset(*common, ctypes.c_void_p(rate_idx.data_ptr()),
+                                                ctypes.c_int64(rate_idx.numel()), ctypes.c_void_p(ws.data_ptr()),
+                                                ctypes.c_size_t(ws.numel()), *ptrs, st_p, ctypes.c_void_p(int(stream)))
+            else:
+                rc = L.hawkes_eval_device_params(*common, ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()),
+                                                 *ptrs, st_p, ctypes.c_void_p(int(stream)))
         if rc != OK:
             raise HawkesError(rc, strerror(rc))
         if check:

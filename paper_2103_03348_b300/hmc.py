@@ -185,8 +185,10 @@ class Posterior:
         self._prior_async(q, want_hess)
         # with no free log-rates the column pass is skipped (globals-only modes)
         mode = ("hess" if want_hess else "grad") if self.m > 0 else ("hess_globals" if want_hess else "grad_globals")
+        # the rate entries are needed for the sequenced events only: O(N M) column work
         hawkes._call(mode, self.x, self.y, self.t, self.r, q, self.precision, stream=stream, check=False,
-                     out=self.like, log_params=True, workspace=self.like_ws, reuse_events=self.prepared)
+                     out=self.like, log_params=True, workspace=self.like_ws, reuse_events=self.prepared,
+                     rate_idx=self.seq if self.m > 0 else None)
         self.prepared = True
         self.calls["hess" if want_hess else "grad"] += 1
         self._assemble(q, self.like["grad"], self.like["hdiag"] if want_hess else None, out["logpost"],
