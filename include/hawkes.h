@@ -40,6 +40,17 @@
  *                exceeds the background's temporal Gaussian (Section 2.1 with a
  *                finite tau_t).  Those terms are exactly 0 in FP32, so the results
  *                equal HAWKES_FP32C's bit for bit; only the work is smaller.
+ *                HAWKES_FP32C_ST: FP32C on space-time tiles.  Inside each slab
+ *                of 4096 time-consecutive events the events are regrouped by
+ *                the Morton code of their location, so each group of 32
+ *                events is compact in space and time; the pairs of groups
+ *                whose terms all lie below 2^-126 (background: spatial and
+ *                temporal gap; excitation and column pass: spatial gap,
+ *                largest log-rate and time offset) are skipped, as their FP32
+ *                terms are exactly 0.  The sums run in another order than
+ *                HAWKES_FP32C's, so the results agree with it to rounding
+ *                (the FP32C accuracy bars hold).  The workspace is larger and
+ *                the shard entry points refuse this precision.
  *   ws, ws_bytes DEVICE workspace owned by the caller, at least
  *                hawkes_workspace_size(n, precision) bytes, 256-byte aligned.
  *                The library allocates nothing.  Calls that may overlap on the
@@ -73,7 +84,7 @@
 extern "C" {
 #endif
 
-typedef enum { HAWKES_FP64 = 0, HAWKES_FP32C = 1, HAWKES_FP32C_BAND = 2 } hawkes_precision;
+typedef enum { HAWKES_FP64 = 0, HAWKES_FP32C = 1, HAWKES_FP32C_BAND = 2, HAWKES_FP32C_ST = 3 } hawkes_precision;
 
 typedef enum {
     HAWKES_OK = 0,

@@ -51,7 +51,8 @@ size_t carve(void *base, const Geometry &g, int precision, Workspace *w) {
     w->gidx = (int *)take(np * sizeof(int));
     w->tinfo = (int4 *)take(nt * sizeof(int4));
     w->tbox = (double4_32a *)take(nt * sizeof(double4_32a));
-    const bool f32 = precision == HAWKES_FP32C || precision == HAWKES_FP32C_BAND;
+    const bool f32 = precision == HAWKES_FP32C || precision == HAWKES_FP32C_BAND || precision == HAWKES_FP32C_ST;
+    const bool st = precision == HAWKES_FP32C_ST;
     w->src32 = f32 ? (float4 *)take(np * sizeof(float4)) : nullptr;
     w->tstat32 = f32 ? (float4 *)take(nt * sizeof(float4)) : nullptr;
     w->sufmax = f32 ? (float *)take(nt * sizeof(float)) : nullptr;
@@ -63,6 +64,17 @@ size_t carve(void *base, const Geometry &g, int precision, Workspace *w) {
     w->dLr = (double *)take(np * sizeof(double));
     w->blockpart = (double *)take(nt * ACC_STRIDE * sizeof(double));
     w->colpart = (double *)take((size_t)g.n_chunks * 2 * np * sizeof(double));
+    w->bbox = (double *)take(4 * sizeof(double));
+    w->perm = st ? (int *)take(np * sizeof(int)) : nullptr;
+    w->inv = st ? (int *)take(np * sizeof(int)) : nullptr;
+    w->gidx_o = st ? (int *)take(np * sizeof(int)) : nullptr;
+    w->loc_o = st ? (int *)take(np * sizeof(int)) : nullptr;
+    w->xp = st ? (double *)take(np * sizeof(double)) : nullptr;
+    w->yp = st ? (double *)take(np * sizeof(double)) : nullptr;
+    w->tp = st ? (double *)take(np * sizeof(double)) : nullptr;
+    w->rp = st ? (double *)take(np * sizeof(double)) : nullptr;
+    w->grp = st ? (GroupStat *)take(np / GROUP * sizeof(GroupStat)) : nullptr;
+    w->trank = st ? (int2 *)take(nt * sizeof(int2)) : nullptr;
     return off;
 }
 
@@ -135,7 +147,8 @@ cudaError_t launch_setup(const Consts &c, const ParamSource &ps, const Workspace
 struct Call {
     Consts c;
     Workspace ws;
-    Inputs in;
+    Inputs in;   // as given (time order)
+    Inputs inw;  // what the kernels after prep read: the FP32C_ST position-order copies, else in
     Outputs out;
     ParamSource ps;
     cudaStream_t s;
@@ -151,7 +164,9 @@ static int prepare(const double *x, const double *y, const double *t, const doub
                    size_t ws_bytes, int mode, double *loglik, double *grad, double *hdiag, int *dev_status,
                    void *stream, Call *k) {
     if (n < 2 || n > HAWKES_MAX_EVENTS) return HAWKES_EINVAL;
-    if (precision != HAWKES_FP64 && precision != HAWKES_FP32C && precision != HAWKES_FP32C_BAND) return HAWKES_EINVAL;
+    if (precision != HAWKES_FP64 && precision != HAWKES_FP32C && precision != HAWKES_FP32C_BAND &&
+        precision != HAWKES_FP32C_ST)
+        return HAWKES_EINVAL;
     k->reuse = (mode & HAWKES_MODE_REUSE_EVENTS) != 0;
     mode &= ~HAWKES_MODE_REUSE_EVENTS;
     // modes 3 and 4: gradient / Hessian diagonal of the six globals only (no column pass)
@@ -173,8 +188,9 @@ static int prepare(const double *x, const double *y, const double *t, const doub
     memset(&c, 0, sizeof(c));
     c.g = g;
     c.mode = mode;
-    c.fp32c = precision == HAWKES_FP32C || precision == HAWKES_FP32C_BAND;
+    c.fp32c = precision == HAWKES_FP32C || precision == HAWKES_FP32C_BAND || precision == HAWKES_FP32C_ST;
     c.band = precision == HAWKES_FP32C_BAND;
+    c.st = precision == HAWKES_FP32C_ST;
     c.t0 = 0;
     c.t1 = g.tiles;
     c.d = k->ws.derived;
@@ -186,6 +202,7 @@ static int prepare(const double *x, const double *y, const double *t, const doub
         k->ps.log_scale = log_params ? 1 : 0;
     }
     k->in = {x, y, t, r};
+    k->inw = c.st ? Inputs{k->ws.xp, k->ws.yp, k->ws.tp, k->ws.rp} : k->in;
     k->out = {loglik, mode >= MODE_GRAD ? grad : nullptr, mode == MODE_HESS ? hdiag : nullptr, dev_status};
     k->s = (cudaStream_t)stream;
     return HAWKES_OK;
@@ -209,9 +226,17 @@ static int phase_rows(const Call &k, void *const *events) {
         if (cudaMemsetAsync(ws.hash, 0xFF, (size_t)c.g.hash_size * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
         if (cudaMemsetAsync(ws.cnt, 0, (size_t)c.g.npad * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
         if (launch_setup(c, k.ps, ws, s, 0) != cudaSuccess) return HAWKES_ECUDA;
-        if (launch_prep(c, k.in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
+        if (c.st) {  // prep's per-event indices in time order, then regrouped by position
+            Workspace wt = ws;
+            wt.gidx = ws.gidx_o;
+            wt.loc = ws.loc_o;
+            if (launch_prep(c, k.in, wt, s) != cudaSuccess) return HAWKES_ECUDA;
+            if (launch_order(c, k.in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
+        } else {
+            if (launch_prep(c, k.in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
+        }
     }
-    if (launch_pack(c, k.in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
+    if (launch_pack(c, k.inw, ws, k.in.r, s) != cudaSuccess) return HAWKES_ECUDA;
     if (!mark(events, 0, s)) return HAWKES_ECUDA;
     if (c.t1 > c.t0) {
         if ((c.fp32c ? launch_row32(c, ws, s) : launch_row64(c, ws, s)) != cudaSuccess) return HAWKES_ECUDA;
@@ -219,8 +244,8 @@ static int phase_rows(const Call &k, void *const *events) {
     if (!mark(events, 1, s)) return HAWKES_ECUDA;
     if (c.t1 > c.t0) {
         if (launch_combine(c, ws, s) != cudaSuccess) return HAWKES_ECUDA;
-        if (c.fp32c && launch_fixup(c, k.in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
-        if (launch_epilogue(c, k.in, ws, s) != cudaSuccess) return HAWKES_ECUDA;
+        if (c.fp32c && launch_fixup(c, k.inw, ws, s) != cudaSuccess) return HAWKES_ECUDA;
+        if (launch_epilogue(c, k.inw, ws, s) != cudaSuccess) return HAWKES_ECUDA;
     }
     return HAWKES_OK;
 }
@@ -236,7 +261,7 @@ static int phase_cols(const Call &k, void *const *events) {
         if (!mark(events, 2, s)) return HAWKES_ECUDA;
         if (k.subset) {  // a subset of the sources (FP64 covers all of them and writes the subset)
             if (k.k_rates > 0) {
-                if ((c.fp32c ? launch_col32_subset(c, k.in, k.ws, k.rate_idx, k.k_rates, s)
+                if ((c.fp32c ? launch_col32_subset(c, k.inw, k.ws, k.rate_idx, k.k_rates, s)
                              : launch_col64(c, k.ws, s)) != cudaSuccess)
                     return HAWKES_ECUDA;
             }
@@ -247,7 +272,7 @@ static int phase_cols(const Call &k, void *const *events) {
             return HAWKES_OK;
         }
         if (c.t1 > c.t0) {
-            if ((c.fp32c ? launch_col32(c, k.in, k.ws, s) : launch_col64(c, k.ws, s)) != cudaSuccess)
+            if ((c.fp32c ? launch_col32(c, k.inw, k.ws, s) : launch_col64(c, k.ws, s)) != cudaSuccess)
                 return HAWKES_ECUDA;
         }
         if (!mark(events, 3, s)) return HAWKES_ECUDA;
@@ -280,6 +305,7 @@ static int shard_phase(const double *x, const double *y, const double *t, const 
                        size_t ws_bytes, void *xbuf, size_t xbuf_bytes, double *loglik, double *grad, double *hdiag,
                        int *dev_status, void *stream, bool second) {
     if (n_shards < 1 || shard < 0 || shard >= n_shards || !params || !xbuf) return HAWKES_EINVAL;
+    if (precision == HAWKES_FP32C_ST) return HAWKES_EINVAL;  // shards own tiles of the time order
     if (((uintptr_t)xbuf & 15) != 0) return HAWKES_EINVAL;
     if (n < 2 || n > HAWKES_MAX_EVENTS) return HAWKES_EINVAL;
     const Geometry g = make_geometry(n);
@@ -307,7 +333,9 @@ extern "C" {
 
 size_t hawkes_workspace_size(int64_t n, int precision) {
     if (n < 2 || n > HAWKES_MAX_EVENTS) return 0;
-    if (precision != HAWKES_FP64 && precision != HAWKES_FP32C && precision != HAWKES_FP32C_BAND) return 0;
+    if (precision != HAWKES_FP64 && precision != HAWKES_FP32C && precision != HAWKES_FP32C_BAND &&
+        precision != HAWKES_FP32C_ST)
+        return 0;
     hk::Workspace w;
     return hk::carve(nullptr, hk::make_geometry(n), precision, &w);
 }

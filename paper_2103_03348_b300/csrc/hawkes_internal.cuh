@@ -2,6 +2,8 @@
 //
 // Data flow of one call (all enqueued on the caller's stream, no host sync):
 //   prep     validate, per-event tie-group start, exact-location dedup, centre
+//   order    FP32C_ST only: regroup each slab of time-consecutive events by a
+//            Morton key of (x, y), so that tiles are compact in space and time
 //   pack     FP32 scaled source pairs + per-tile statistics (FP32C), FP64 copy
 //   row      per (target tile, source chunk): moment sums of the pair terms
 //            (Eq. 1's inner sum and its parameter derivatives)
@@ -22,6 +24,9 @@
 namespace hk {
 
 constexpr int TILE = 128;   // events per tile: targets per row block, sources per shared-memory subtile
+constexpr int GROUP = 32;   // events per group (one warp's targets or sources) in FP32C_ST
+constexpr int SLAB_TILES = 32;                   // FP32C_ST: tiles per slab of time-consecutive events
+constexpr int SLAB_EVENTS = SLAB_TILES * TILE;  // 4096: sorted by Morton key in shared memory
 constexpr int NMOM = 10;    // row moments (hess mode)
 constexpr int NACC = 13;    // per-row terms reduced across rows: loglik, 6 gradient, 6 Hessian
 constexpr int ACC_STRIDE = 16;
@@ -76,6 +81,7 @@ struct Derived {
 struct Consts {
     Geometry g;
     int mode, fp32c, band;  // band: FP32C with exact background band skipping
+    int st;            // FP32C_ST: space-time tiles (events permuted inside slabs), group pruning
     int t0, t1;        // the tiles this call owns as targets (row pass) and sources (column pass)
     const Derived *d;  // device: written by setup_kernel
 };
@@ -88,6 +94,17 @@ struct ParamSource {
     int log_scale;
 };
 
+// FP32C_ST statistics of a group of 32 consecutive events (in tile order), in
+// the scaled FP32 units of the packed sources:
+//   box = (x~ min, x~ max, y~ min, y~ max)
+//   tr  = (t~ min, t~ max, max r^, max g^)   (g^ written by the epilogue)
+//   ix  = (min gidx, max gidx, min rank, max rank), rank = time-order index
+struct GroupStat {
+    float4 box;
+    float4 tr;
+    int4 ix;
+};
+
 // Workspace carving.  Offsets are multiples of 256 bytes.
 struct Workspace {
     int *hdr;            // [0] status bits, [1] flagged rows, [2] ticket, [3] spare
@@ -97,7 +114,7 @@ struct Workspace {
     int *cnt;            // [npad]  members of each exact-location group (indexed by representative)
     int *loc;            // [npad]  representative index of the event's location
     int *gidx;           // [npad]  first index with the same time (tie-group start)
-    int4 *tinfo;         // [tiles] gfirst, glast, has_dup, valid count
+    int4 *tinfo;         // [tiles] min and max gidx of the tile's events, has_dup, valid count
     double4_32a *tbox;       // [tiles] xmin, xmax, ymin, ymax (prep)
     float4 *src32;       // [npad]  pairs: (-x0,-x1,-y0,-y1),(-t0,-t1,r^0,r^1), r^ = r~ + t~;
                          //         the r^ slot later holds the column weight g^ = log2(B/lambda) - t~
@@ -111,6 +128,15 @@ struct Workspace {
     double *blockpart;   // [tiles * ACC_STRIDE]
     float *sufmax;       // [tiles] suffix max of the column weight bound (FP32C)
     double *colpart;     // [n_chunks * 2 * npad]
+    double *bbox;        // [4]: x min, x max, y min, y max of the events (prep)
+    // FP32C_ST only (NULL otherwise).  Position k holds event perm[k] (time
+    // order); gidx and loc above are then indexed by position.
+    int *perm;           // [npad]  position -> time-order index (identity on padding)
+    int *inv;            // [npad]  time-order index -> position
+    int *gidx_o, *loc_o; // [npad]  prep's tie-group starts and location groups, time order
+    double *xp, *yp, *tp, *rp;  // [npad] the events in position order
+    GroupStat *grp;      // [npad / GROUP]
+    int2 *trank;         // [tiles] min, max rank of the tile's events
 };
 
 size_t carve(void *base, const Geometry &g, int precision, Workspace *ws);  // returns total bytes; base may be NULL
@@ -127,7 +153,9 @@ struct Outputs {
 // launchers (return cudaGetLastError())
 cudaError_t launch_setup(const Consts &c, const ParamSource &ps, const Workspace &ws, cudaStream_t s, int reuse);
 cudaError_t launch_prep(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s);
-cudaError_t launch_pack(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s);
+cudaError_t launch_order(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s);
+cudaError_t launch_pack(const Consts &c, const Inputs &in, const Workspace &ws, const double *r_time_order,
+                        cudaStream_t s);
 cudaError_t launch_row32(const Consts &c, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_row64(const Consts &c, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_combine(const Consts &c, const Workspace &ws, cudaStream_t s);
@@ -224,6 +252,77 @@ __device__ __forceinline__ float block_max(float v, float *sh) {
     const float r = sh[0];
     __syncthreads();
     return r;
+}
+
+// Warp-wide min / max (every lane gets the result).
+__device__ __forceinline__ float warp_minf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_maxf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ int warp_mini(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ int warp_maxi(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// ---- FP32C_ST pruning bounds between two groups (or unions of groups) ----
+// Every bound is taken over the FP32 values the pair loops use, so a pruned
+// group pair holds only terms that ex2.approx.ftz would flush to exactly 0.
+
+__device__ __forceinline__ bool group_empty(const GroupStat &a) { return a.ix.z > a.ix.w; }
+
+__device__ __forceinline__ GroupStat group_union(const GroupStat &a, const GroupStat &b) {
+    GroupStat u;
+    u.box = make_float4(fminf(a.box.x, b.box.x), fmaxf(a.box.y, b.box.y), fminf(a.box.z, b.box.z),
+                        fmaxf(a.box.w, b.box.w));
+    u.tr = make_float4(fminf(a.tr.x, b.tr.x), fmaxf(a.tr.y, b.tr.y), fmaxf(a.tr.z, b.tr.z), fmaxf(a.tr.w, b.tr.w));
+    u.ix = make_int4(min(a.ix.x, b.ix.x), max(a.ix.y, b.ix.y), min(a.ix.z, b.ix.z), max(a.ix.w, b.ix.w));
+    return u;
+}
+
+// smallest squared scaled distance between two boxes (0 when they overlap)
+__device__ __forceinline__ float box_gap2(const float4 a, const float4 b) {
+    const float gx = fmaxf(fmaxf(b.x - a.y, a.x - b.y), 0.0f);
+    const float gy = fmaxf(fmaxf(b.z - a.w, a.z - b.w), 0.0f);
+    return gx * gx + gy * gy;
+}
+
+// background terms between targets W and sources S: 2^-(d~^2 + cbt dt~^2)
+__device__ __forceinline__ bool bg_alive(const GroupStat &W, const GroupStat &S, float cbt) {
+    const float gt = fmaxf(fmaxf(S.tr.x - W.tr.y, W.tr.x - S.tr.y), 0.0f);
+    const float q = box_gap2(W.box, S.box) + (cbt > 0.0f ? cbt * gt * gt : 0.0f);
+    return !(q > BG_DEAD);
+}
+
+// a bound e on an exponent below which every term is 0, with a relative
+// allowance for the rounding of the terms that make it up
+__device__ __forceinline__ bool exp2_alive(float e, float scale) {
+    return e >= EXP2_DEAD - 1.0e-5f * fminf(scale, 1.0e30f);  // e = -inf or NaN: dead
+}
+
+// excitation terms of the row pass: 2^(r^_s - t~_n - hh d~^2), s strictly earlier than n
+__device__ __forceinline__ bool exc_alive(const GroupStat &W, const GroupStat &S, float hh) {
+    if (S.ix.z >= W.ix.y) return false;  // no source precedes any target (rank vs tie-group start)
+    const float d = hh * box_gap2(W.box, S.box);
+    return exp2_alive(S.tr.z - W.tr.x - d, fabsf(S.tr.z) + fabsf(W.tr.x) + d);
+}
+
+// column terms: 2^(g^_n + r^_m - hh d~^2) for sources W and targets G
+__device__ __forceinline__ bool col_alive(const GroupStat &W, const GroupStat &G, float hh) {
+    if (G.ix.y <= W.ix.z) return false;  // no target follows any source
+    const float d = hh * box_gap2(W.box, G.box);
+    return exp2_alive(W.tr.z + G.tr.w - d, fabsf(W.tr.z) + fabsf(G.tr.w) + d);
 }
 
 #endif  // __CUDACC__

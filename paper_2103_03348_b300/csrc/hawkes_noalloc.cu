@@ -10,8 +10,8 @@
 // inputs (x, y, t, r) and the outputs (loglik, grad, hdiag, dev_status).
 //
 // How: the scratch is the file-scope array below, sized for up to
-// HAWKES_NOALLOC_MAX_EVENTS events at either precision (the largest workspace
-// for n <= 4096 is 12.6 MiB).  Every GPU that loads the library holds these
+// HAWKES_NOALLOC_MAX_EVENTS events at any precision (the largest workspace
+// for n <= 4096 is 12.7 MiB).  Every GPU that loads the library holds these
 // 16 MiB until the process exits.  Host code cannot use the array's name as a
 // device address, so the first call on each device (with that device current)
 // looks the address up with cudaGetSymbolAddress, checks it, and caches it;

@@ -169,6 +169,10 @@ __global__ void __launch_bounds__(TILE) epilogue_kernel(Consts c, Inputs in, Wor
         if (threadIdx.x < NACC) ws.blockpart[(size_t)tile * ACC_STRIDE + threadIdx.x] = v;
     }
     if (c.fp32c) {
+        if (c.st) {  // per-group bound for the column pass's pruning
+            const float wm = warp_maxf(ghat);
+            if ((threadIdx.x & 31) == 0) ws.grp[i / GROUP].tr.w = wm;
+        }
         const float gm = block_max<TILE>(ghat, shf);
         if (threadIdx.x == 0) ws.tstat32[tile].w = gm;
     }
@@ -268,8 +272,9 @@ __global__ void __launch_bounds__(CB_THREADS) colfinish_kernel(Consts c, Workspa
         g = qnan;
         hd = qnan;
     }
-    if (out.grad) out.grad[6 + m] = g;
-    if (out.hdiag) out.hdiag[6 + m] = hd;
+    const int o = c.st ? ws.perm[m] : m;  // outputs in time order
+    if (out.grad) out.grad[6 + o] = g;
+    if (out.hdiag) out.hdiag[6 + o] = hd;
 }
 
 // The finish for a subset of sources: entry 6 + rate_idx[j] of grad / hdiag,
@@ -288,13 +293,13 @@ __global__ void __launch_bounds__(CB_THREADS) colfinish_subset_kernel(Consts c, 
         *out.dev_status = HAWKES_EINVAL;
         return;
     }
-    const int npad = c.g.npad, at = by_position ? j : m;
+    const int npad = c.g.npad, at = by_position ? j : (c.st ? ws.inv[m] : m);
     double c1 = 0.0, c2 = 0.0;
     for (int ch = 0; ch < c.g.n_chunks; ++ch) {
         c1 += ws.colpart[((size_t)ch * 2 + 0) * npad + at];
         if (c.mode == MODE_HESS) c2 += ws.colpart[((size_t)ch * 2 + 1) * npad + at];
     }
-    const double dl = ws.dLr[m];
+    const double dl = ws.dLr[c.st ? ws.inv[m] : m];
     double g = c1 - dl, hd = c1 - c2 - dl;
     if (bits != 0) {
         const double qnan = __longlong_as_double(0x7ff8000000000000LL);

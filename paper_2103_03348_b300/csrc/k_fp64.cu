@@ -144,8 +144,10 @@ __global__ void __launch_bounds__(FIX_THREADS) fixup_kernel(Consts c, Inputs in,
         double a[NMOM];
 #pragma unroll
         for (int k = 0; k < NMOM; ++k) a[k] = 0.0;
+        // FP32C_ST: the causal test compares time-order ranks
         for (int j = threadIdx.x; j < n; j += FIX_THREADS)
-            accumulate64<MODE_HESS>(a, in.x[j], in.y[j], in.t[j], in.r[j], ws.loc[j] != locn, j < gn, xn, yn, tn, D);
+            accumulate64<MODE_HESS>(a, in.x[j], in.y[j], in.t[j], in.r[j], ws.loc[j] != locn,
+                                    (c.st ? ws.perm[j] : j) < gn, xn, yn, tn, D);
         // raw units -> FP32C scaled units
         const double scale[NMOM] = {1.0, sx2, st2, sx2 * sx2, st2 * st2, 1.0, st, st2, sx2, sx2 * sx2};
 #pragma unroll

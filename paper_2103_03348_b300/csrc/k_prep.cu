@@ -9,12 +9,20 @@
 //     representative and cnt[rep] the group size;
 //   * per-tile x/y bounds; the last block to finish (atomic ticket, no waiting)
 //     reduces them in fixed order to the centre used by the FP32 coordinates.
+// order (FP32C_ST only): the events of each slab of 4096 time-consecutive
+// events are sorted by the Morton code of their cell on a 65536 x 65536 grid
+// over the events' bounding square, so every tile of 128 positions covers a
+// compact region of space inside the slab's time window; the permuted copies
+// of x, y, t and of the tie-group and location indices are gathered.
 // pack (one block per tile):
 //   * FP32C: scaled, centred FP32 sources stored as pairs for f32x2 arithmetic,
 //     ((-x0,-x1,-y0,-y1),(-t0,-t1,r^0,r^1)) with r^ = r~ + t~, and per-tile
 //     statistics;
 //   * FP64: (x, y, t, r) as double4_32a;
-//   * per-tile first/last tie-group start and duplicate-location flag.
+//   * per-tile lowest/highest tie-group start and duplicate-location flag;
+//   * FP32C_ST: per-group (32 events) bounds for pruning, per-tile rank range.
+#include <climits>
+
 #include "hawkes_internal.cuh"
 
 namespace hk {
@@ -142,6 +150,7 @@ __global__ void __launch_bounds__(TILE) prep_kernel(Consts c, Inputs in, Workspa
         }
         if (threadIdx.x == 0) {
             const double4_32a bb = shb[0];
+            ws.bbox[0] = bb.x; ws.bbox[1] = bb.y; ws.bbox[2] = bb.z; ws.bbox[3] = bb.w;
             const double t0 = in.t[0], t1 = in.t[n - 1];
             ws.centre[0] = isfinite(bb.x + bb.y) ? 0.5 * (bb.x + bb.y) : 0.0;
             ws.centre[1] = isfinite(bb.z + bb.w) ? 0.5 * (bb.z + bb.w) : 0.0;
@@ -152,7 +161,7 @@ __global__ void __launch_bounds__(TILE) prep_kernel(Consts c, Inputs in, Workspa
     }
 }
 
-__global__ void __launch_bounds__(TILE) pack_kernel(Consts c, Inputs in, Workspace ws) {
+__global__ void __launch_bounds__(TILE) pack_kernel(Consts c, Inputs in, Workspace ws, const double *r_time_order) {
     const Derived &D = *c.d;
     const int n = c.g.n;
     const int i = blockIdx.x * TILE + threadIdx.x;
@@ -160,10 +169,17 @@ __global__ void __launch_bounds__(TILE) pack_kernel(Consts c, Inputs in, Workspa
     __shared__ float shf[TILE];
     __shared__ int shi[TILE];
 
+    // FP32C_ST: position i holds event perm[i]; its log-rate is gathered here
+    double ri = 0.0;
+    if (valid) {
+        ri = c.st ? r_time_order[ws.perm[i]] : in.r[i];
+        if (c.st) ws.rp[i] = ri;
+    }
     const int dup = valid ? (ws.cnt[ws.loc[i]] >= 2) : 0;
-    if (valid && !isfinite(in.r[i])) atomicOr(&ws.hdr[0], ST_NONFINITE);
+    if (valid && !isfinite(ri)) atomicOr(&ws.hdr[0], ST_NONFINITE);
 
     float tmin = INFINITY, tmax = -INFINITY, rtmax = -INFINITY;
+    float xw = 0.0f, yw = 0.0f;  // scaled coordinates (FP32C_ST group bounds)
     if (c.fp32c) {
         const double xc = ws.centre[0], yc = ws.centre[1], tc = ws.centre[2];
         float xs, ys, ts, rs;
@@ -174,10 +190,12 @@ __global__ void __launch_bounds__(TILE) pack_kernel(Consts c, Inputs in, Workspa
             ys = -(float)((in.y[i] - yc) * D.sx);
             const double tsc = (in.t[i] - tc) * D.st;
             ts = -(float)tsc;
-            rs = (float)(in.r[i] * LOG2E + tsc);
+            rs = (float)(ri * LOG2E + tsc);
             tmin = (float)tsc;
             tmax = (float)tsc;
             rtmax = rs;
+            xw = -xs;
+            yw = -ys;
         } else {
             // padding source: far away in space and time, contributes exact zeros
             xs = -1.0e9f; ys = -1.0e9f; ts = -1.0e9f; rs = -1.0e9f;
@@ -189,8 +207,21 @@ __global__ void __launch_bounds__(TILE) pack_kernel(Consts c, Inputs in, Workspa
         f[8 * p + 4 + l] = ts;
         f[8 * p + 6 + l] = rs;
     } else {
-        if (valid) ws.src64[i] = make_double4_32a(in.x[i], in.y[i], in.t[i], in.r[i]);
+        if (valid) ws.src64[i] = make_double4_32a(in.x[i], in.y[i], in.t[i], ri);
         else ws.src64[i] = make_double4_32a(0.0, 0.0, 0.0, 0.0);  // never read: loops stop at n
+    }
+
+    if (c.st) {
+        // group bounds (one warp = one group of 32 positions); empty groups get
+        // empty bounds (min > max), which every pruning test treats as dead
+        const int gi = valid ? ws.gidx[i] : INT_MAX, rk = valid ? ws.perm[i] : INT_MAX;
+        GroupStat gs;
+        gs.box = make_float4(warp_minf(valid ? xw : INFINITY), warp_maxf(valid ? xw : -INFINITY),
+                             warp_minf(valid ? yw : INFINITY), warp_maxf(valid ? yw : -INFINITY));
+        gs.tr = make_float4(warp_minf(tmin), warp_maxf(tmax), warp_maxf(rtmax), -INFINITY);
+        gs.ix = make_int4(warp_mini(gi), warp_maxi(valid ? gi : INT_MIN), warp_mini(rk),
+                          warp_maxi(valid ? rk : INT_MIN));
+        if ((threadIdx.x & 31) == 0) ws.grp[i / GROUP] = gs;
     }
 
     // per-tile statistics (FP32C scaled time bounds and max(r~ + t~))
@@ -204,11 +235,129 @@ __global__ void __launch_bounds__(TILE) pack_kernel(Consts c, Inputs in, Workspa
         if (threadIdx.x < w) shi[threadIdx.x] |= shi[threadIdx.x + w];
         __syncthreads();
     }
+    const int has_dup = shi[0];
+    __syncthreads();
+    const int first = blockIdx.x * TILE;
+    const int lastv = min(n, first + TILE) - 1;
+    int g_lo = 0, g_hi = 0, k_lo = 0, k_hi = 0;
+    if (c.st) {
+        // permuted positions: tie-group and rank ranges by reduction
+        const int gi = valid ? ws.gidx[i] : INT_MAX, rk = valid ? ws.perm[i] : INT_MAX;
+        shi[threadIdx.x] = gi;
+        __syncthreads();
+        for (int w = TILE / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) shi[threadIdx.x] = min(shi[threadIdx.x], shi[threadIdx.x + w]);
+            __syncthreads();
+        }
+        g_lo = shi[0];
+        __syncthreads();
+        shi[threadIdx.x] = valid ? gi : INT_MIN;
+        __syncthreads();
+        for (int w = TILE / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) shi[threadIdx.x] = max(shi[threadIdx.x], shi[threadIdx.x + w]);
+            __syncthreads();
+        }
+        g_hi = shi[0];
+        __syncthreads();
+        shi[threadIdx.x] = rk;
+        __syncthreads();
+        for (int w = TILE / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) shi[threadIdx.x] = min(shi[threadIdx.x], shi[threadIdx.x + w]);
+            __syncthreads();
+        }
+        k_lo = shi[0];
+        __syncthreads();
+        shi[threadIdx.x] = valid ? rk : INT_MIN;
+        __syncthreads();
+        for (int w = TILE / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) shi[threadIdx.x] = max(shi[threadIdx.x], shi[threadIdx.x + w]);
+            __syncthreads();
+        }
+        k_hi = shi[0];
+    } else {
+        // time order: gidx is non-decreasing
+        g_lo = ws.gidx[first];
+        g_hi = ws.gidx[lastv];
+    }
     if (threadIdx.x == 0) {
-        const int first = blockIdx.x * TILE;
-        const int lastv = min(n, first + TILE) - 1;
-        ws.tinfo[blockIdx.x] = make_int4(ws.gidx[first], ws.gidx[lastv], shi[0], lastv - first + 1);
+        ws.tinfo[blockIdx.x] = make_int4(g_lo, g_hi, has_dup, lastv - first + 1);
         if (c.fp32c) ws.tstat32[blockIdx.x] = make_float4(tmin, tmax, rtmax, -INFINITY);
+        if (c.st) ws.trank[blockIdx.x] = make_int2(k_lo, k_hi);
+    }
+}
+
+// Morton code of a cell (16 bits per axis, interleaved: x in the even bits).
+__device__ __forceinline__ unsigned spread16(unsigned v) {
+    v &= 0xffffu;
+    v = (v | (v << 8)) & 0x00ff00ffu;
+    v = (v | (v << 4)) & 0x0f0f0f0fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+
+constexpr int ORDER_THREADS = 1024;
+
+// One block per slab: keys (Morton code << 32 | slot) sorted ascending in
+// shared memory by a bitonic network; unique keys make the order deterministic.
+__global__ void __launch_bounds__(ORDER_THREADS) order_sort_kernel(Consts c, Inputs in, Workspace ws) {
+    __shared__ unsigned long long keys[SLAB_EVENTS];
+    const int n = c.g.n;
+    const int e0 = blockIdx.x * SLAB_EVENTS;
+    const int cnt = min(n - e0, SLAB_EVENTS);
+    const double x0 = ws.bbox[0], x1 = ws.bbox[1], y0 = ws.bbox[2], y1 = ws.bbox[3];
+    const double span = fmax(x1 - x0, y1 - y0);  // one scale for both axes: square cells
+    const double sc = (isfinite(span) && span > 0.0) ? 65535.0 / span : 0.0;
+    for (int k = threadIdx.x; k < SLAB_EVENTS; k += ORDER_THREADS) {
+        unsigned long long key = ~0ULL;  // empty slots sort last
+        if (k < cnt) {
+            // fmax / fmin map NaN to the bound, so non-finite inputs (reported by prep) stay in range
+            const unsigned ix = (unsigned)fmin(fmax((in.x[e0 + k] - x0) * sc, 0.0), 65535.0);
+            const unsigned iy = (unsigned)fmin(fmax((in.y[e0 + k] - y0) * sc, 0.0), 65535.0);
+            key = ((unsigned long long)(spread16(ix) | (spread16(iy) << 1)) << 32) | (unsigned)k;
+        }
+        keys[k] = key;
+    }
+    __syncthreads();
+    for (int size = 2; size <= SLAB_EVENTS; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int q = threadIdx.x; q < SLAB_EVENTS / 2; q += ORDER_THREADS) {
+                const int lo = 2 * q - (q & (stride - 1));
+                const int hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const unsigned long long a = keys[lo], b = keys[hi];
+                if ((a > b) == up) {
+                    keys[lo] = b;
+                    keys[hi] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int k = threadIdx.x; k < cnt; k += ORDER_THREADS) ws.perm[e0 + k] = e0 + (int)(keys[k] & 0xffffffffu);
+}
+
+// Position-order copies of the events and of prep's per-event indices.
+__global__ void __launch_bounds__(TILE) order_gather_kernel(Consts c, Inputs in, Workspace ws) {
+    const int n = c.g.n;
+    const int k = blockIdx.x * TILE + threadIdx.x;  // < npad
+    if (k < n) {
+        const int o = ws.perm[k];
+        ws.inv[o] = k;
+        ws.xp[k] = in.x[o];
+        ws.yp[k] = in.y[o];
+        ws.tp[k] = in.t[o];
+        ws.gidx[k] = ws.gidx_o[o];
+        ws.loc[k] = ws.loc_o[o];
+    } else {
+        ws.perm[k] = k;
+        ws.inv[k] = k;
+        ws.xp[k] = 0.0;
+        ws.yp[k] = 0.0;
+        ws.tp[k] = 0.0;
+        ws.rp[k] = 0.0;
+        ws.gidx[k] = n;      // padding: never a causal source, never a target
+        ws.loc[k] = -1 - k;  // padding: a location of its own
     }
 }
 
@@ -217,8 +366,17 @@ cudaError_t launch_prep(const Consts &c, const Inputs &in, const Workspace &ws, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s) {
-    pack_kernel<<<c.g.tiles, TILE, 0, s>>>(c, in, ws);
+cudaError_t launch_order(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s) {
+    const int slabs = (c.g.n + SLAB_EVENTS - 1) / SLAB_EVENTS;
+    order_sort_kernel<<<slabs, ORDER_THREADS, 0, s>>>(c, in, ws);
+    if (cudaGetLastError() != cudaSuccess) return cudaErrorLaunchFailure;
+    order_gather_kernel<<<c.g.tiles, TILE, 0, s>>>(c, in, ws);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const Consts &c, const Inputs &in, const Workspace &ws, const double *r_time_order,
+                        cudaStream_t s) {
+    pack_kernel<<<c.g.tiles, TILE, 0, s>>>(c, in, ws, r_time_order);
     return cudaGetLastError();
 }
 

@@ -27,9 +27,9 @@ import torch
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libhawkes.so")
 
-FP64, FP32C, FP32C_BAND = 0, 1, 2
-PRECISIONS = {"fp64": FP64, "fp32c": FP32C, "fp32c_band": FP32C_BAND, FP64: FP64, FP32C: FP32C,
-              FP32C_BAND: FP32C_BAND}
+FP64, FP32C, FP32C_BAND, FP32C_ST = 0, 1, 2, 3
+PRECISIONS = {"fp64": FP64, "fp32c": FP32C, "fp32c_band": FP32C_BAND, "fp32c_st": FP32C_ST, FP64: FP64, FP32C: FP32C,
+              FP32C_BAND: FP32C_BAND, FP32C_ST: FP32C_ST}
 
 OK, EINVAL, EUNSORTED, ENONFINITE, EWORKSPACE, ECUDA, EZERO, ESCRATCH = range(8)
 
@@ -89,7 +89,9 @@ def workspace_size(n: int, precision="fp32c") -> int:
 def kernels_per_call(mode: str, precision="fp32c") -> int:
     """Number of kernels one call launches (memsets excluded)."""
     p = PRECISIONS[precision]
-    k = 7 + (1 if p in (FP32C, FP32C_BAND) else 0)  # setup, prep, pack, row, combine, [fixup], epilogue, finalize
+    k = 7 + (1 if p != FP64 else 0)  # setup, prep, pack, row, combine, [fixup], epilogue, finalize
+    if p == FP32C_ST:
+        k += 2  # order: slab sort, gather
     if mode in ("grad", "hess"):
         k += 2  # column pass, column finish
     return k

@@ -327,9 +327,12 @@ class TrajectoryGraph:
     kernel.  Works on static buffers: set q, p and g (the gradient at q), then
     replay; the trajectory's end state is in q, p and out, and the kinetic
     energy at the end in k1.  minv is read from device memory at replay, so
-    mass updates made in place take effect."""
+    mass updates made in place take effect.  The eager run that precedes the
+    capture starts from (q0, p0, g0), a state of the chain: from an arbitrary
+    state (all zeros: every global 1 in its unit) the likelihood can take its
+    slowest path (rows redone in FP64)."""
 
-    def __init__(self, post, eps, n_steps, minv):
+    def __init__(self, post, eps, n_steps, minv, q0, p0, g0):
         dev = minv.device
         f64 = dict(dtype=torch.float64, device=dev)
         dim = minv.numel()
@@ -338,6 +341,9 @@ class TrajectoryGraph:
         self.out = {"logpost": torch.empty((), **f64), "grad": torch.empty(dim, **f64),
                     "hdiag": torch.empty(dim, **f64)}
         self.k1 = torch.empty((), **f64)
+        self.q.copy_(q0)
+        self.p.copy_(p0)
+        self.g.copy_(g0)
         side = torch.cuda.Stream(device=dev)
         side.wait_stream(torch.cuda.current_stream(dev))
         with torch.cuda.stream(side):  # one eager run first, so every lazily made buffer exists
@@ -438,7 +444,7 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
         kinetic(p, minv, k0)
         if use_graph and record is None and it >= n_warmup:
             if graph is None:
-                graph = TrajectoryGraph(post, eps, n_steps, minv)
+                graph = TrajectoryGraph(post, eps, n_steps, minv, q, p, cur["grad"])
             graph.q.copy_(q)
             graph.p.copy_(p)
             graph.g.copy_(cur["grad"])

@@ -1,6 +1,7 @@
 """Preconditioned HMC over the phylogenetic Hawkes posterior, reported as ESS/s.
 
-    python -m paper_2103_03348_b300.run_hmc [--precision fp32c_band|fp32c|fp64] [--iters 2000] [--warmup 200]
+    python -m paper_2103_03348_b300.run_hmc [--precision fp32c_st|fp32c_band|fp32c|fp64] [--iters 2000]
+                                            [--warmup 200]
                                             [--prior tree|dense] [--checkpoint PATH [--every K]] [--resume PATH]
 
 Workload: the 23,422-event synthetic pattern with 1,610 sequenced events whose
@@ -65,7 +66,7 @@ def run(precision="fp32c_band", iters=2000, warmup=200, n_steps=20, mass_every=1
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--precision", default="fp32c_band", choices=["fp32c_band", "fp32c", "fp64"])
+    ap.add_argument("--precision", default="fp32c_band", choices=["fp32c_st", "fp32c_band", "fp32c", "fp64"])
     ap.add_argument("--iters", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--steps", type=int, default=20)

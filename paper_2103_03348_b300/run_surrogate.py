@@ -74,7 +74,7 @@ def main():
     ap.add_argument("--exact-iters", type=int, default=50)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--precision", default="fp32c_band", choices=["fp32c", "fp32c_band", "fp64"])
+    ap.add_argument("--precision", default="fp32c_band", choices=["fp32c", "fp32c_band", "fp32c_st", "fp64"])
     a = ap.parse_args()
     print(json.dumps(run(a.n, a.pairs, a.iters, a.exact_iters, a.steps, a.seed, precision=a.precision)), flush=True)
 

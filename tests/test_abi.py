@@ -81,7 +81,7 @@ def test_argument_errors(L, fn):
     assert _call(L, fn, n=1) == EINVAL
     assert _call(L, fn, n=0) == EINVAL
     assert _call(L, fn, n=-5) == EINVAL
-    assert _call(L, fn, precision=3) == EINVAL
+    assert _call(L, fn, precision=4) == EINVAL
     for bad in [(0.0, 0.1, 0.05, 0.3, 10.0, 0.02), (0.5, -0.1, 0.05, 0.3, 10.0, 0.02),
                 (0.5, 0.1, 0.05, 0.3, math.nan, 0.02), (0.5, 0.1, 0.05, 0.3, 10.0, math.inf),
                 (0.5, 0.1, -math.inf, 0.3, 10.0, 0.02), (0.5, 0.1, 0.05, 0.0, 10.0, 0.02)]:

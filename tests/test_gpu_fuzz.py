@@ -2,7 +2,8 @@
 (2 to 700 events, ragged tails), parameters spread over orders of magnitude,
 clustered and uniform events, exact ties in time and repeated locations, and
 spread log-rates.  FP64 is held to 1e-10, FP32C and its band-skipping form to
-the stated FP32C bars; the band form must also equal FP32C bit for bit.
+the stated FP32C bars; the band form must also equal FP32C bit for bit, and the
+space-time form meets the FP32C bars.
 
 One regime is looser by nature: an intensity below ~1e-290 means its FP64
 pair terms are subnormal (exp of about -709), with short mantissas on both
@@ -80,3 +81,8 @@ def test_random_problem(seed):
     assert norm_rel(h, ref["hdiag"]) <= FP32C_HNORM_TOL, (norm_rel(h, ref["hdiag"]), params)
     llb, gb, hb = gpu(x, y, t, r, params, "fp32c_band")
     assert llb == ll and np.array_equal(gb, g) and np.array_equal(hb, h)
+    # space-time tiles: the same FP32 terms in another order, with dead group pairs skipped
+    ll, g, h = gpu(x, y, t, r, params, "fp32c_st")
+    assert rel(ll, ref["loglik"]) <= FP32C_LL_TOL, (ll, ref["loglik"], params)
+    assert norm_rel(g, ref["grad"]) <= FP32C_GNORM_TOL, (norm_rel(g, ref["grad"]), params)
+    assert norm_rel(h, ref["hdiag"]) <= FP32C_HNORM_TOL, (norm_rel(h, ref["hdiag"]), params)

@@ -23,7 +23,7 @@ def dev(a):
     return torch.tensor(np.asarray(a, float), dtype=torch.float64, device="cuda")
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32c", "fp32c_band"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32c", "fp32c_band", "fp32c_st"])
 @pytest.mark.parametrize("name", ["loglik_hand_n7.json", "loglik_uniform_n96.json"])
 def test_likelihood_fixture(name, precision):
     from paper_2103_03348_b300 import build, hawkes

@@ -48,7 +48,7 @@ def oracle_of(w, params=None):
     return _ORACLE_CACHE[key]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32c", "fp32c_st"])
 @pytest.mark.parametrize("name", ["unit_square", "ebola_like"])
 def test_workload_parity(name, prec):
     w = synth.make(name)
@@ -57,7 +57,7 @@ def test_workload_parity(name, prec):
     check(prec, ll, g, h, ref, label=name)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32c", "fp32c_st"])
 def test_modes_agree(prec):
     w = synth.make("unit_square")
     ll0, _, _ = gpu_eval(w, w.params, prec, "loglik")
@@ -67,7 +67,7 @@ def test_modes_agree(prec):
     np.testing.assert_allclose(g1, g2, rtol=1e-13, atol=1e-13 * np.abs(g2).max())
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32c", "fp32c_st"])
 @pytest.mark.parametrize("n", [2, 3, 127, 128, 129, 255, 257, 1000, 4099])
 def test_ragged_sizes(n, prec):
     w = synth.make_uniform(100 + n, n, box=1.0, t_max=1.0, r_sd=0.5, params=(0.5, 0.2, 0.1, 0.3, 5.0, 0.05))
@@ -76,7 +76,7 @@ def test_ragged_sizes(n, prec):
     check(prec, ll, g, h, ref, label=f"uniform N={n}")
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32c", "fp32c_st"])
 def test_paper_background_without_temporal_bandwidth(prec):
     w = synth.make("unit_square")
     p = np.array(w.params)
@@ -101,7 +101,7 @@ def tie_and_duplicate_pattern(seed=5, n=700):
     return x[o], y[o], t[o], r[o]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32c", "fp32c_st"])
 def test_ties_and_duplicate_locations(prec):
     x, y, t, r = tie_and_duplicate_pattern()
     p = np.array([0.5, 0.2, 0.1, 0.3, 5.0, 0.05])
@@ -110,7 +110,7 @@ def test_ties_and_duplicate_locations(prec):
     check(prec, ll, g, h, ref, label="ties+duplicates")
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32c", "fp32c_st"])
 @pytest.mark.parametrize("far", [6.0, 9.0])
 def test_near_zero_intensity_rows(prec, far):
     # two events far from everything else: their intensities fall to about
@@ -129,7 +129,7 @@ def test_near_zero_intensity_rows(prec, far):
     check(prec, ll, g, h, ref, label=f"isolated far={far}")
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32c", "fp32c_st"])
 def test_zero_intensity_status(prec):
     H = hawkes_mod()
     p = np.array([0.5, 0.01, 0.05, 0.3, 10.0, 0.01])
@@ -143,7 +143,7 @@ def test_zero_intensity_status(prec):
     del H
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32c", "fp32c_st"])
 def test_invalid_data_status(prec):
     w = synth.make_uniform(9, 300, r_sd=0.2)
     t_bad = w.t.copy()
@@ -162,7 +162,7 @@ def test_invalid_data_status(prec):
     check(prec, ll, g, h, ref, label="after error")
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32c", "fp32c_st"])
 def test_bitwise_deterministic(prec):
     w = synth.make("unit_square")
     a = gpu_eval(w, w.params, prec)
@@ -267,7 +267,7 @@ def test_million_events_ragged():
     assert np.linalg.norm(h[6 + idx] - h_ref) <= 1e-4 * np.linalg.norm(h_ref)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32c", "fp32c_st"])
 def test_reused_event_preparation(prec):
     """HAWKES_MODE_REUSE_EVENTS: a second call on the same events and workspace
     skips their preparation and gives the same results bit for bit, with new

@@ -8,7 +8,11 @@ Checked against the full evaluation on the same inputs and against the oracle:
     pass covers every source);
   * FP32C subset entries: the same Kahan-compensated FP32 sums, cut into
     chunks at different tile boundaries, so they agree with the full call to
-    rounding (1e-5 scaled) and with the oracle to the FP32C bars;
+    rounding and with the oracle to the FP32C bars.  Each tile adds up to 64
+    packed pair terms in plain FP32 before compensation (relative error up to
+    ~64 * 2^-24 = 4e-6 of the tile's sum); the gradient entry is held to 1e-5
+    (scaled), the Hessian entry c1 - c2 - dLambda, which cancels by up to an
+    order of magnitude, to 1e-4;
   * every other rate entry is left as it was;
   * an index outside [0, n) gives status EINVAL; k = 0 writes no rate entry."""
 import numpy as np
@@ -22,6 +26,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 SENTINEL = 12345.0
+G_TOL, H_TOL = 1e-5, 1e-4  # subset against full FP32C call (see above)
 
 
 def lib():
@@ -69,12 +74,12 @@ def test_subset_matches_full_and_oracle(prec, mode):
     assert np.all(g_s[6 + rest] == SENTINEL)
     if mode == "hess":
         assert np.array_equal(h_s[:6], h_f[:6]) and np.all(h_s[6 + rest] == SENTINEL)
-    pairs = [(g_s, g_f)] + ([(h_s, h_f)] if mode == "hess" else [])
-    for a, b in pairs:
+    pairs = [(g_s, g_f, G_TOL)] + ([(h_s, h_f, H_TOL)] if mode == "hess" else [])
+    for a, b, tol in pairs:
         if prec == "fp64":
             assert np.array_equal(a[6 + idx], b[6 + idx])
         else:
-            assert scaled_err(a[6 + idx], b[6 + idx]) <= 1e-5
+            assert scaled_err(a[6 + idx], b[6 + idx]) <= tol
     if prec != "fp64":
         ref = oracle.evaluate(w.x, w.y, w.t, w.r, w.params, want=2 if mode == "hess" else 1)
         assert scaled_err(g_s[6 + idx], ref["grad"][6 + idx]) <= FP32C_RATE_TOL
@@ -93,8 +98,8 @@ def test_subset_of_the_sampler_shape():
     ll_f, g_f, h_f, _ = run(H, w, "fp32c", "hess", None)
     ll_s, g_s, h_s, st = run(H, w, "fp32c", "hess", idx)
     assert st == 0 and ll_s == ll_f
-    assert scaled_err(g_s[6 + idx], g_f[6 + idx]) <= 1e-5
-    assert scaled_err(h_s[6 + idx], h_f[6 + idx]) <= 1e-5
+    assert scaled_err(g_s[6 + idx], g_f[6 + idx]) <= G_TOL
+    assert scaled_err(h_s[6 + idx], h_f[6 + idx]) <= H_TOL
     ref = oracle.evaluate(w.x, w.y, w.t, w.r, w.params, want=2)
     assert scaled_err(g_s[6 + idx], ref["grad"][6 + idx]) <= FP32C_RATE_TOL
     assert norm_rel(h_s[6 + idx], ref["hdiag"][6 + idx]) <= FP32C_HNORM_TOL
@@ -111,7 +116,7 @@ def test_subset_edge_cases():
     assert np.all(g[6:] == SENTINEL) and np.all(h[6:] == SENTINEL)
     # every source, and the last source alone (no later target: its sum is 0)
     ll, g, h, st = run(H, w, "fp32c", "hess", np.arange(n))
-    assert st == 0 and scaled_err(g[6:], g_f[6:]) <= 1e-5 and scaled_err(h[6:], h_f[6:]) <= 1e-5
+    assert st == 0 and scaled_err(g[6:], g_f[6:]) <= G_TOL and scaled_err(h[6:], h_f[6:]) <= H_TOL
     ll, g, h, st = run(H, w, "fp32c", "hess", np.array([n - 1]))
     assert st == 0 and g[6 + n - 1] == g_f[6 + n - 1] and h[6 + n - 1] == h_f[6 + n - 1]
     # an index outside [0, n): status EINVAL, in both precisions
