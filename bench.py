@@ -319,6 +319,19 @@ def run_ours(args, rank, world, local_rank):
         if i > 0:
             band_ms.append(ev[0].elapsed_time(ev[1]))
 
+    # the same evaluation on space-time tiles (events regrouped by location inside
+    # time slabs; group pairs whose FP32 terms all underflow are skipped; results
+    # equal FP32C's up to summation order), event preparation included
+    st_ms = []
+    for i in range(max(3, min(args.steps, 50)) + 1):
+        flush.zero_()
+        ev[0].record(stream)
+        hawkes._call("hess", x, y, t, r, w.params, "fp32c_st", stream=stream, check=False)
+        ev[1].record(stream)
+        ev[1].synchronize()
+        if i > 0:
+            st_ms.append(ev[0].elapsed_time(ev[1]))
+
     # FP64 GPU path on the same workload (speedup of FP32C over it)
     fp64_ms = []
     for i in range(3):
@@ -330,13 +343,14 @@ def run_ours(args, rank, world, local_rank):
             fp64_ms.append(ev[0].elapsed_time(ev[1]))
 
     # HMC ESS/s: a short preconditioned chain on the 23,422-event workload with
-    # 1,610 free log-rates (the full 2,000-iteration run is run_hmc's job); band
-    # skipping gives FP32C's results bit for bit, with less work
+    # 1,610 free log-rates (the full 2,000-iteration run is run_hmc's job), on
+    # space-time tiles
     hmc_summary = None
     if not args.no_hmc:
         from paper_2103_03348_b300 import run_hmc
-        h = run_hmc.run("fp32c_band", iters=args.hmc_iters, warmup=args.hmc_warmup, device=str(dev))
-        hmc_summary = {k: h[k] for k in ("workload", "n_events", "n_rates", "iters", "warmup", "leapfrog_steps",
+        h = run_hmc.run("fp32c_st", iters=args.hmc_iters, warmup=args.hmc_warmup, device=str(dev))
+        hmc_summary = {k: h[k] for k in ("workload", "n_events", "n_rates", "precision", "iters", "warmup",
+                                         "leapfrog_steps",
                                          "accept_rate", "sampling_seconds", "ms_per_gradient",
                                          "ess_globals", "ess_rates", "ess_per_s_globals", "ess_per_s_rates")}
 
@@ -393,6 +407,13 @@ def run_ours(args, rank, world, local_rank):
                       "ms_per_step": float(np.mean(band_ms)),
                       "pair_interactions_per_s": world * pairs / (float(np.mean(band_ms)) * 1e-3),
                       "speedup_over_fp32c": ms / float(np.mean(band_ms))},
+        "spacetime": {"precision": "fp32c_st (events regrouped by Morton code inside slabs of 4,096; group pairs "
+                                   "whose FP32 terms all underflow are skipped; results equal fp32c's up to "
+                                   "summation order)",
+                      "ms_per_step": float(np.mean(st_ms)),
+                      "pair_interactions_per_s": world * pairs / (float(np.mean(st_ms)) * 1e-3),
+                      "speedup_over_fp32c": ms / float(np.mean(st_ms)),
+                      "speedup_over_band": float(np.mean(band_ms)) / float(np.mean(st_ms))},
         "fp64_gpu_path": {"ms_per_step": float(np.mean(fp64_ms)),
                           "speedup_fp32c_over_fp64": float(np.mean(fp64_ms)) / ms},
         "wall_s_timed_region": wall,

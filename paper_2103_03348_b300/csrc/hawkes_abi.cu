@@ -42,7 +42,9 @@ size_t carve(void *base, const Geometry &g, int precision, Workspace *w) {
         return base ? (void *)((char *)base + o) : nullptr;
     };
     const size_t np = (size_t)g.npad, nt = (size_t)g.tiles;
-    w->hdr = (int *)take(8 * sizeof(int));
+    // the header and, after it, the validation bits kept for calls that reuse the events
+    w->hdr = (int *)take((8 + 1) * sizeof(int));
+    w->evbits = base ? w->hdr + 8 : nullptr;
     w->derived = (Derived *)take(sizeof(Derived));
     w->centre = (double *)take(4 * sizeof(double));
     w->hash = (int *)take((size_t)g.hash_size * sizeof(int));
@@ -54,13 +56,13 @@ size_t carve(void *base, const Geometry &g, int precision, Workspace *w) {
     const bool f32 = precision == HAWKES_FP32C || precision == HAWKES_FP32C_BAND || precision == HAWKES_FP32C_ST;
     const bool st = precision == HAWKES_FP32C_ST;
     w->src32 = f32 ? (float4 *)take(np * sizeof(float4)) : nullptr;
+    w->tgt32 = f32 ? (float4 *)take(np * sizeof(float4)) : nullptr;
     w->tstat32 = f32 ? (float4 *)take(nt * sizeof(float4)) : nullptr;
     w->sufmax = f32 ? (float *)take(nt * sizeof(float)) : nullptr;
     w->src64 = f32 ? nullptr : (double4_32a *)take(np * sizeof(double4_32a));
     w->w64 = f32 ? nullptr : (double *)take(np * sizeof(double));
     w->rowpart = (double *)take((size_t)g.n_chunks * NMOM * np * sizeof(double));
     w->mom = (double *)take((size_t)NMOM * np * sizeof(double));
-    w->flagged = (int *)take(np * sizeof(int));
     w->dLr = (double *)take(np * sizeof(double));
     w->blockpart = (double *)take(nt * ACC_STRIDE * sizeof(double));
     w->colpart = (double *)take((size_t)g.n_chunks * 2 * np * sizeof(double));
@@ -89,9 +91,9 @@ static bool params_valid(const double *p) {
 // One thread derives every parameter-dependent constant in FP64.  Parameters
 // that are not finite and positive (tau_t may be +inf) set ST_BADPARAM, and
 // finalize then reports HAWKES_EINVAL with NaN outputs.
-__global__ void setup_kernel(ParamSource ps, int fp32c, int reuse, Derived *out, int *hdr) {
+__global__ void setup_kernel(ParamSource ps, int fp32c, int reuse, Derived *out, int *hdr, const int *evbits) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    if (reuse) hdr[0] |= hdr[3];  // the event checks of the call that prepared these events
+    if (reuse) hdr[0] |= *evbits;  // the event checks of the call that prepared these events
     double p[6];
     bool ok = true;
     for (int k = 0; k < 6; ++k) {
@@ -139,7 +141,7 @@ __global__ void setup_kernel(ParamSource ps, int fp32c, int reuse, Derived *out,
 }
 
 cudaError_t launch_setup(const Consts &c, const ParamSource &ps, const Workspace &ws, cudaStream_t s, int reuse) {
-    setup_kernel<<<1, 32, 0, s>>>(ps, c.fp32c, reuse, ws.derived, ws.hdr);
+    setup_kernel<<<1, 32, 0, s>>>(ps, c.fp32c, reuse, ws.derived, ws.hdr, ws.evbits);
     return cudaGetLastError();
 }
 
@@ -218,11 +220,12 @@ static int phase_rows(const Call &k, void *const *events) {
     const Consts &c = k.c;
     const Workspace &ws = k.ws;
     cudaStream_t s = k.s;
-    if (k.reuse) {  // status and fix-up count only; hdr[3] keeps the event checks
-        if (cudaMemsetAsync(ws.hdr, 0, 2 * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
+    const size_t hdr_ints = 8;  // the header; evbits follows
+    if (k.reuse) {  // evbits keeps the event checks of the call that prepared the events
+        if (cudaMemsetAsync(ws.hdr, 0, hdr_ints * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
         if (launch_setup(c, k.ps, ws, s, 1) != cudaSuccess) return HAWKES_ECUDA;
     } else {
-        if (cudaMemsetAsync(ws.hdr, 0, 8 * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
+        if (cudaMemsetAsync(ws.hdr, 0, (hdr_ints + 1) * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
         if (cudaMemsetAsync(ws.hash, 0xFF, (size_t)c.g.hash_size * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
         if (cudaMemsetAsync(ws.cnt, 0, (size_t)c.g.npad * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
         if (launch_setup(c, k.ps, ws, s, 0) != cudaSuccess) return HAWKES_ECUDA;
@@ -243,9 +246,12 @@ static int phase_rows(const Call &k, void *const *events) {
     }
     if (!mark(events, 1, s)) return HAWKES_ECUDA;
     if (c.t1 > c.t0) {
-        if (launch_combine(c, ws, s) != cudaSuccess) return HAWKES_ECUDA;
-        if (c.fp32c && launch_fixup(c, k.inw, ws, s) != cudaSuccess) return HAWKES_ECUDA;
-        if (launch_epilogue(c, k.inw, ws, s) != cudaSuccess) return HAWKES_ECUDA;
+        if (c.fp32c) {  // combine, FP64 fix-up of tiny rows and epilogue, one block per tile
+            if (launch_finish(c, k.inw, ws, s) != cudaSuccess) return HAWKES_ECUDA;
+        } else {
+            if (launch_combine(c, ws, s) != cudaSuccess) return HAWKES_ECUDA;
+            if (launch_epilogue(c, k.inw, ws, s) != cudaSuccess) return HAWKES_ECUDA;
+        }
     }
     return HAWKES_OK;
 }

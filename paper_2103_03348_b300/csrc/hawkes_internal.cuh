@@ -11,6 +11,7 @@
 //   fixup    FP32C only: rows whose FP32 sum is below 2^-60 redone in FP64
 //   epilogue per row: lambda_n, log lambda_n, derivative terms, the integral
 //            term (Appendix A) per event, column-pass weights; block partials
+//            (FP32C: combine, fixup and epilogue run as one kernel, finish)
 //   finalize one block: deterministic sum of block partials -> outputs
 //   col      per (source tile, target chunk): Eq. 4 / Eq. 5 column sums
 //   colfin   per source: combine column partials, subtract dLambda/dr_m
@@ -107,7 +108,8 @@ struct GroupStat {
 
 // Workspace carving.  Offsets are multiples of 256 bytes.
 struct Workspace {
-    int *hdr;            // [0] status bits, [1] flagged rows, [2] ticket, [3] spare
+    int *hdr;            // [0] status bits, [2] prep's last-block ticket; cleared every call
+    int *evbits;         // [1] prep's validation bits, kept for calls that reuse the events (follows hdr)
     Derived *derived;    // [1]  constants derived from the parameters
     double *centre;      // [4]: xc, yc, tc, tN
     int *hash;           // [hash_size]
@@ -116,13 +118,14 @@ struct Workspace {
     int *gidx;           // [npad]  first index with the same time (tie-group start)
     int4 *tinfo;         // [tiles] min and max gidx of the tile's events, has_dup, valid count
     double4_32a *tbox;       // [tiles] xmin, xmax, ymin, ymax (prep)
-    float4 *src32;       // [npad]  pairs: (-x0,-x1,-y0,-y1),(-t0,-t1,r^0,r^1), r^ = r~ + t~;
-                         //         the r^ slot later holds the column weight g^ = log2(B/lambda) - t~
+    float4 *src32;       // [npad]  pairs: (-x0,-x1,-y0,-y1),(-t0,-t1,r^0,r^1), r^ = r~ + t~ (read-only
+                         //         after pack: row blocks of other tiles read it while a tile finishes)
+    float4 *tgt32;       // [npad]  the column pass's targets: (-x0,-x1,-y0,-y1),(-t0,-t1,g^0,g^1) with the
+                         //         column weight g^ = log2(B/lambda) - t~, written by the tile finish
     float4 *tstat32;     // [tiles] t~min, t~max, max r^, max g^
     double4_32a *src64;      // [npad]  (x, y, t, r) FP64 (FP64 path)
     double *rowpart;     // [n_chunks * NMOM * npad]
     double *mom;         // [NMOM * npad]
-    int *flagged;        // [npad]
     double *w64;         // [npad]  FP64 column weight, in logs: log(B / lambda_n)
     double *dLr;         // [npad]  dLambda / dr_m
     double *blockpart;   // [tiles * ACC_STRIDE]
@@ -157,9 +160,9 @@ cudaError_t launch_order(const Consts &c, const Inputs &in, const Workspace &ws,
 cudaError_t launch_pack(const Consts &c, const Inputs &in, const Workspace &ws, const double *r_time_order,
                         cudaStream_t s);
 cudaError_t launch_row32(const Consts &c, const Workspace &ws, cudaStream_t s);
+cudaError_t launch_finish(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_row64(const Consts &c, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_combine(const Consts &c, const Workspace &ws, cudaStream_t s);
-cudaError_t launch_fixup(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_epilogue(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_finalize(const Consts &c, const Workspace &ws, const Outputs &out, cudaStream_t s);
 cudaError_t launch_col32(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s);
@@ -167,6 +170,10 @@ cudaError_t launch_col64(const Consts &c, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_colfinish(const Consts &c, const Workspace &ws, const Outputs &out, cudaStream_t s);
 cudaError_t launch_col32_subset(const Consts &c, const Inputs &in, const Workspace &ws, const int *rate_idx,
                                 int k_rates, cudaStream_t s);
+cudaError_t launch_row32_st(const Consts &c, const Workspace &ws, cudaStream_t s);
+cudaError_t launch_col32_st(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s);
+cudaError_t launch_col32_subset_st(const Consts &c, const Inputs &in, const Workspace &ws, const int *rate_idx,
+                                   int k_rates, cudaStream_t s);
 cudaError_t launch_colfinish_subset(const Consts &c, const Workspace &ws, const Outputs &out, const int *rate_idx,
                                     int k_rates, int by_position, cudaStream_t s);
 cudaError_t launch_shard_export(const Consts &c, const Workspace &ws, double *xbuf, cudaStream_t s);

@@ -1,7 +1,8 @@
 // Row finish, integral term and deterministic reductions (steps a3, a4).
 //
-// combine   mom[k][i] = sum over chunks of the row partials (fixed order, FP64);
-//           FP32C rows with tiny sums are listed for the FP64 fix-up.
+// combine   FP64 path: mom[k][i] = sum over chunks of the row partials (fixed
+//           order); FP32C does this (and the fix-up of tiny rows) at the end
+//           of the row kernel (rows_finish.cuh).
 // epilogue  per event n, in FP64:
 //             lambda_n = A sum G + B sum E                          (Eq. 1 inner sum)
 //             q1_p = (d lambda_n / dp) / lambda_n,  q2_p = (d2 lambda_n / dp2) / lambda_n - q1_p^2
@@ -22,7 +23,7 @@
 //   omega:  B (S_E/omega - MO_ET),        second B (MO_ET2 - 2 MO_ET/omega)
 //   h:      B (MO_ED2/h^3 - 2 S_E/h),     second B (MO_ED4/h^6 - 7 MO_ED2/h^4 + 6 S_E/h^2)
 // (from f(s) = s^-k exp(-q/(2 s^2)): f'/f = q/s^3 - k/s, f''/f = (f'/f)^2 - 3q/s^4 + k/s^2).
-#include "hawkes_internal.cuh"
+#include "rows_finish.cuh"
 
 namespace hk {
 
@@ -32,7 +33,6 @@ __global__ void __launch_bounds__(CB_THREADS) combine_kernel(Consts c, Workspace
     const int i = c.t0 * TILE + blockIdx.x * CB_THREADS + threadIdx.x;
     if (i >= c.g.n || i >= c.t1 * TILE) return;
     const int npad = c.g.npad;
-    double sg = 0.0, se = 0.0;
     for (int k = 0; k < NMOM; ++k) {
         const bool used = c.mode == MODE_HESS ||
                           (c.mode == MODE_GRAD && (k == MO_G || k == MO_GD2 || k == MO_GT2 || k == MO_E || k == MO_ET || k == MO_ED2)) ||
@@ -41,12 +41,6 @@ __global__ void __launch_bounds__(CB_THREADS) combine_kernel(Consts c, Workspace
         double s = 0.0;
         for (int ch = 0; ch < c.g.n_chunks; ++ch) s += ws.rowpart[((size_t)ch * NMOM + k) * npad + i];
         ws.mom[(size_t)k * npad + i] = s;
-        if (k == MO_G) sg = s;
-        if (k == MO_E) se = s;
-    }
-    if (c.fp32c && sg < (double)TINY_ROW && se < (double)TINY_ROW) {
-        const int slot = atomicAdd(&ws.hdr[1], 1);
-        ws.flagged[slot] = i;
     }
 }
 
@@ -55,8 +49,6 @@ cudaError_t launch_combine(const Consts &c, const Workspace &ws, cudaStream_t s)
     return cudaGetLastError();
 }
 
-__device__ __forceinline__ double std_pdf(double z) { return 0.3989422804014327 * exp(-0.5 * z * z); }
-__device__ __forceinline__ double std_cdf(double z) { return 0.5 * erfc(-z * 0.7071067811865476); }
 
 __global__ void __launch_bounds__(TILE) epilogue_kernel(Consts c, Inputs in, Workspace ws) {
     const Derived &D = *c.d;
@@ -72,97 +64,10 @@ __global__ void __launch_bounds__(TILE) epilogue_kernel(Consts c, Inputs in, Wor
     float ghat = -INFINITY;
 
     if (valid) {
-        const int mode = c.mode;
-        auto M = [&](int k) { return ws.mom[(size_t)k * npad + i]; };
-        const double SG = M(MO_G), SE = M(MO_E);
-        const double lam = D.A * SG + D.B * SE;
-        double q1[6] = {0, 0, 0, 0, 0, 0}, q2[6] = {0, 0, 0, 0, 0, 0};
-        double ll = 0.0;
-        if (lam > 0.0) {
-            ll = log(lam);
-            if (mode >= MODE_GRAD) {
-                // Every ratio is (A or B times a moment) / lambda, multiplied in that order:
-                // A S_G <= lambda and B S_E <= lambda, so nothing overflows however small
-                // lambda is (A / lambda alone can).  Below 1e-300, divide instead of
-                // multiplying by 1 / lambda, which could overflow.
-                const double il = 1.0 / lam;
-                const bool tiny = !(lam > 1e-300);
-                auto over = [&](double v) { return tiny ? v / lam : v * il; };
-                const double AG = D.A * SG, BE = D.B * SE;
-                const double AGD2 = D.A * (M(MO_GD2) * D.i_sx2), AGT2 = D.A * (M(MO_GT2) * D.i_st2);
-                const double BET = D.B * (M(MO_ET) * D.i_st), BED2 = D.B * (M(MO_ED2) * D.i_sx2);
-                const double ix = D.i_tx, it = D.i_tt, ih = D.i_h;
-                const double ix2 = ix * ix, it2 = it * it, ih2 = ih * ih;
-                q1[0] = over(AG) * D.i_mu0;
-                q1[1] = over(AGD2 * ix2 * ix - 2.0 * AG * ix);
-                q1[2] = D.tt_inf ? 0.0 : over(AGT2 * it2 * it - AG * it);
-                q1[3] = over(BE) * D.i_th0;
-                q1[4] = over(BE * D.i_om - BET);
-                q1[5] = over(BED2 * ih2 * ih - 2.0 * BE * ih);
-                if (mode == MODE_HESS) {
-                    const double AGD4 = D.A * (M(MO_GD4) * D.i_sx2 * D.i_sx2);
-                    const double AGT4 = D.A * (M(MO_GT4) * D.i_st2 * D.i_st2);
-                    const double BET2 = D.B * (M(MO_ET2) * D.i_st2), BED4 = D.B * (M(MO_ED4) * D.i_sx2 * D.i_sx2);
-                    const double ix4 = ix2 * ix2, it4 = it2 * it2, ih4 = ih2 * ih2;
-                    double s2[6];
-                    s2[0] = 0.0;
-                    s2[1] = over(AGD4 * ix4 * ix2 - 7.0 * AGD2 * ix4 + 6.0 * AG * ix2);
-                    s2[2] = D.tt_inf ? 0.0 : over(AGT4 * it4 * it2 - 5.0 * AGT2 * it4 + 2.0 * AG * it2);
-                    s2[3] = 0.0;
-                    s2[4] = over(BET2 - 2.0 * BET * D.i_om);
-                    s2[5] = over(BED4 * ih4 * ih2 - 7.0 * BED2 * ih4 + 6.0 * BE * ih2);
+        double Mo[NMOM];
 #pragma unroll
-                    for (int p = 0; p < 6; ++p) q2[p] = s2[p] - q1[p] * q1[p];
-                    if (D.tt_inf) q2[2] = 0.0;
-                }
-            }
-            if (c.fp32c) {
-                // column weight g^ = log2(B / lambda_n) - t~_n (t~_n as packed), formed in logs
-                const float *f = reinterpret_cast<const float *>(ws.src32);
-                const float tt_n = -f[8 * (i >> 1) + 4 + (i & 1)];
-                ghat = (float)((D.log2_b - ll * LOG2E) - (double)tt_n);
-            } else {
-                ws.w64[i] = D.ln_b - ll;  // log(B / lambda_n)
-            }
-        } else {
-            atomicOr(&ws.hdr[0], ST_ZERO);
-            if (!c.fp32c) ws.w64[i] = -INFINITY;  // weight 0
-        }
-        if (c.fp32c) {
-            float *f = reinterpret_cast<float *>(ws.src32);
-            f[8 * (i >> 1) + 6 + (i & 1)] = ghat;
-        }
-
-        // this event's share of the integral term and its derivatives
-        const double tN = ws.centre[3];
-        const double ti = in.t[i], a_ = tN - ti, b_ = -ti;
-        const double th = exp(in.r[i]);
-        const double dec = exp(-D.om * a_);
-        const double one_m = -expm1(-D.om * a_);
-        double L = 0.0, dL[6] = {0, 0, 0, 0, 0, 0}, d2L[6] = {0, 0, 0, 0, 0, 0};
-        if (D.tt_inf) {
-            dL[0] = tN;
-        } else {
-            const double it = D.i_tt, za = a_ * it, zb = b_ * it;
-            const double pa = std_pdf(za), pb = std_pdf(zb);
-            dL[0] = std_cdf(za) - std_cdf(zb);
-            const double it2 = it * it, it3 = it2 * it, it5 = it3 * it2;
-            dL[2] = D.mu0 * (-(a_ * it2) * pa + (b_ * it2) * pb);
-            d2L[2] = D.mu0 * (pa * (2.0 * a_ * it3 - a_ * a_ * a_ * it5) - pb * (2.0 * b_ * it3 - b_ * b_ * b_ * it5));
-        }
-        L = D.mu0 * dL[0] + D.th0 * th * one_m;
-        dL[3] = th * one_m;
-        dL[4] = D.th0 * th * a_ * dec;
-        d2L[4] = -D.th0 * th * a_ * a_ * dec;
-        ws.dLr[i] = D.th0 * th * one_m;
-
-        acc[0] = ll - L;
-#pragma unroll
-        for (int p = 0; p < 6; ++p) {
-            acc[1 + p] = q1[p] - dL[p];
-            acc[7 + p] = q2[p] - d2L[p];
-        }
-        if (lam <= 0.0) acc[0] = 0.0;  // the status carries the -inf
+        for (int k = 0; k < NMOM; ++k) Mo[k] = ws.mom[(size_t)k * npad + i];
+        epilogue_row(c, D, in, ws, i, Mo, acc, ghat);
     }
     {
         const double v = block_sum_multi<TILE, NACC>(acc, sh);
@@ -176,6 +81,16 @@ __global__ void __launch_bounds__(TILE) epilogue_kernel(Consts c, Inputs in, Wor
         const float gm = block_max<TILE>(ghat, shf);
         if (threadIdx.x == 0) ws.tstat32[tile].w = gm;
     }
+}
+
+// FP32C: one block per target tile finishes its rows (rows_finish.cuh).
+__global__ void __launch_bounds__(TILE) finish_kernel(Consts c, Inputs in, Workspace ws) {
+    finish_tile_fp32c(c, in, ws, c.t0 + blockIdx.x);
+}
+
+cudaError_t launch_finish(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s) {
+    finish_kernel<<<c.t1 - c.t0, TILE, 0, s>>>(c, in, ws);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_epilogue(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s) {

@@ -1,5 +1,4 @@
-// FP64 row and column passes, and the FP64 recomputation of near-zero rows of
-// the FP32C path.
+// FP64 row and column passes.
 //
 // The FP64 path evaluates every pair with libm-accurate exp() and accumulates
 // the same moments as the FP32C row pass, in FP64 and raw units:
@@ -9,29 +8,9 @@
 // excitation (those terms are zero by the indicator).  On B300 FP64 runs at
 // 1/64 of the FP32 rate, which is why this path is the precision reference on
 // the GPU and not the fast path.
-#include "hawkes_internal.cuh"
+#include "rows_finish.cuh"
 
 namespace hk {
-
-template <int MODE>
-__device__ __forceinline__ void accumulate64(double (&a)[NMOM], double xs, double ys, double ts, double rs,
-                                             bool bg_on, bool ex_on, double xn, double yn, double tn,
-                                             const Derived &D) {
-    const double dx = xn - xs, dy = yn - ys, dt = tn - ts;
-    const double d2 = dx * dx + dy * dy, dt2 = dt * dt;
-    if (bg_on) {
-        const double g = exp(-D.ibx * d2 - D.ibt * dt2);
-        a[MO_G] += g;
-        if (MODE >= MODE_GRAD) { a[MO_GD2] += g * d2; a[MO_GT2] += g * dt2; }
-        if (MODE == MODE_HESS) { a[MO_GD4] += g * d2 * d2; a[MO_GT4] += g * dt2 * dt2; }
-    }
-    if (ex_on) {
-        const double e = exp(rs - D.om * dt - D.ih * d2);
-        a[MO_E] += e;
-        if (MODE >= MODE_GRAD) { a[MO_ET] += e * dt; a[MO_ED2] += e * d2; }
-        if (MODE == MODE_HESS) { a[MO_ET2] += e * dt2; a[MO_ED4] += e * d2 * d2; }
-    }
-}
 
 template <int MODE>
 __global__ void __launch_bounds__(TILE) row64_kernel(Consts c, Workspace ws) {
@@ -122,44 +101,6 @@ cudaError_t launch_col64(const Consts &c, const Workspace &ws, cudaStream_t s) {
     const dim3 grid(c.t1 - c.t0, c.g.n_chunks);
     if (c.mode == MODE_HESS) col64_kernel<MODE_HESS><<<grid, TILE, 0, s>>>(c, ws);
     else col64_kernel<MODE_GRAD><<<grid, TILE, 0, s>>>(c, ws);
-    return cudaGetLastError();
-}
-
-// FP32C rows whose FP32 background and excitation sums both fell below 2^-60
-// (combine flags them) are recomputed here in FP64 over all sources, one
-// block per flagged row, and written back in the FP32C scaled units.
-constexpr int FIX_THREADS = 256;
-constexpr int FIX_BLOCKS = 64;
-
-__global__ void __launch_bounds__(FIX_THREADS) fixup_kernel(Consts c, Inputs in, Workspace ws) {
-    const Derived &D = *c.d;
-    __shared__ double sh[FIX_THREADS];
-    const int nflag = ws.hdr[1];
-    const int n = c.g.n, npad = c.g.npad;
-    const double sx2 = D.sx * D.sx, st = D.st, st2 = D.st * D.st;
-    for (int e = blockIdx.x; e < nflag; e += gridDim.x) {
-        const int i = ws.flagged[e];
-        const double xn = in.x[i], yn = in.y[i], tn = in.t[i];
-        const int locn = ws.loc[i], gn = ws.gidx[i];
-        double a[NMOM];
-#pragma unroll
-        for (int k = 0; k < NMOM; ++k) a[k] = 0.0;
-        // FP32C_ST: the causal test compares time-order ranks
-        for (int j = threadIdx.x; j < n; j += FIX_THREADS)
-            accumulate64<MODE_HESS>(a, in.x[j], in.y[j], in.t[j], in.r[j], ws.loc[j] != locn,
-                                    (c.st ? ws.perm[j] : j) < gn, xn, yn, tn, D);
-        // raw units -> FP32C scaled units
-        const double scale[NMOM] = {1.0, sx2, st2, sx2 * sx2, st2 * st2, 1.0, st, st2, sx2, sx2 * sx2};
-#pragma unroll
-        for (int k = 0; k < NMOM; ++k) {
-            const double v = block_sum<FIX_THREADS>(a[k], sh);
-            if (threadIdx.x == 0) ws.mom[(size_t)k * npad + i] = v * scale[k];
-        }
-    }
-}
-
-cudaError_t launch_fixup(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s) {
-    fixup_kernel<<<FIX_BLOCKS, FIX_THREADS, 0, s>>>(c, in, ws);
     return cudaGetLastError();
 }
 

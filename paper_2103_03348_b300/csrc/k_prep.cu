@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(TILE) prep_kernel(Consts c, Inputs in, Workspa
     }
     if (bad) {
         atomicOr(&ws.hdr[0], bad);
-        atomicOr(&ws.hdr[3], bad);  // kept for calls that reuse these events
+        atomicOr(ws.evbits, bad);  // kept for calls that reuse these events
     }
 
     // per-tile bounds of x and y (valid events only)

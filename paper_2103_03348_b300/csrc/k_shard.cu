@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(TILE) shard_export_kernel(Consts c, Workspace 
     if (threadIdx.x == NACC) rec[NACC] = __longlong_as_double((long long)ws.hdr[0]);
     if (threadIdx.x == NACC + 1) rec[NACC + 1] = c.fp32c ? float_bits(ws.tstat32[tile].w) : 0.0;
     if (c.fp32c) {
-        const float *f = reinterpret_cast<const float *>(ws.src32);
+        const float *f = reinterpret_cast<const float *>(ws.tgt32);
         rec[16 + threadIdx.x] = float_bits(f[8 * (i >> 1) + 6 + (i & 1)]);
     } else {
         rec[16 + threadIdx.x] = ws.w64[i];
@@ -53,8 +53,14 @@ __global__ void __launch_bounds__(TILE) shard_import_kernel(Consts c, Workspace 
     }
     if (threadIdx.x == NACC + 1 && c.fp32c) ws.tstat32[tile].w = bits_float(rec[NACC + 1]);
     if (c.fp32c) {
-        float *f = reinterpret_cast<float *>(ws.src32);
-        f[8 * (i >> 1) + 6 + (i & 1)] = bits_float(rec[16 + threadIdx.x]);
+        // the column pass's packed targets: coordinates from this shard's own packing
+        const float *f = reinterpret_cast<const float *>(ws.src32);
+        float *o = reinterpret_cast<float *>(ws.tgt32);
+        const int p = i >> 1, l = i & 1;
+        o[8 * p + 0 + l] = f[8 * p + 0 + l];
+        o[8 * p + 2 + l] = f[8 * p + 2 + l];
+        o[8 * p + 4 + l] = f[8 * p + 4 + l];
+        o[8 * p + 6 + l] = bits_float(rec[16 + threadIdx.x]);
     } else {
         ws.w64[i] = rec[16 + threadIdx.x];
     }

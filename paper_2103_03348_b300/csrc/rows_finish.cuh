@@ -1,0 +1,222 @@
+// Row finishing shared by the FP64 path (k_fp64.cu, k_epi.cu) and the FP32C
+// finish kernel (k_epi.cu): the FP64 pair terms (also used to redo tiny FP32C
+// rows), the per-row epilogue, and the FP32C tile finish.
+#pragma once
+
+#include "hawkes_internal.cuh"
+
+namespace hk {
+
+template <int MODE>
+__device__ __forceinline__ void accumulate64(double (&a)[NMOM], double xs, double ys, double ts, double rs,
+                                             bool bg_on, bool ex_on, double xn, double yn, double tn,
+                                             const Derived &D) {
+    const double dx = xn - xs, dy = yn - ys, dt = tn - ts;
+    const double d2 = dx * dx + dy * dy, dt2 = dt * dt;
+    if (bg_on) {
+        const double g = exp(-D.ibx * d2 - D.ibt * dt2);
+        a[MO_G] += g;
+        if (MODE >= MODE_GRAD) { a[MO_GD2] += g * d2; a[MO_GT2] += g * dt2; }
+        if (MODE == MODE_HESS) { a[MO_GD4] += g * d2 * d2; a[MO_GT4] += g * dt2 * dt2; }
+    }
+    if (ex_on) {
+        const double e = exp(rs - D.om * dt - D.ih * d2);
+        a[MO_E] += e;
+        if (MODE >= MODE_GRAD) { a[MO_ET] += e * dt; a[MO_ED2] += e * d2; }
+        if (MODE == MODE_HESS) { a[MO_ET2] += e * dt2; a[MO_ED4] += e * d2 * d2; }
+    }
+}
+
+__device__ __forceinline__ double std_pdf(double z) { return 0.3989422804014327 * exp(-0.5 * z * z); }
+__device__ __forceinline__ double std_cdf(double z) { return 0.5 * erfc(-z * 0.7071067811865476); }
+
+// The row epilogue of event i (one thread): lambda_n and its derivative terms
+// from the moments Mo (Eq. 1 and its parameter derivatives), the FP32C column
+// weight g^ (returned in ghat) or the FP64 weight, and the event's share of the integral term (Appendix A Claim) with
+// its derivatives and dLambda/dr_i; acc receives the 13 per-row terms.
+__device__ __forceinline__ void epilogue_row(const Consts &c, const Derived &D, const Inputs &in, const Workspace &ws,
+                                             int i, const double (&Mo)[NMOM], double (&acc)[NACC], float &ghat) {
+    const int mode = c.mode;
+    const double SG = Mo[MO_G], SE = Mo[MO_E];
+    const double lam = D.A * SG + D.B * SE;
+    double q1[6] = {0, 0, 0, 0, 0, 0}, q2[6] = {0, 0, 0, 0, 0, 0};
+    double ll = 0.0;
+    if (lam > 0.0) {
+        ll = log(lam);
+        if (mode >= MODE_GRAD) {
+            // Every ratio is (A or B times a moment) / lambda, multiplied in that order:
+            // A S_G <= lambda and B S_E <= lambda, so nothing overflows however small
+            // lambda is (A / lambda alone can).  Below 1e-300, divide instead of
+            // multiplying by 1 / lambda, which could overflow.
+            const double il = 1.0 / lam;
+            const bool tiny = !(lam > 1e-300);
+            auto over = [&](double v) { return tiny ? v / lam : v * il; };
+            const double AG = D.A * SG, BE = D.B * SE;
+            const double AGD2 = D.A * (Mo[MO_GD2] * D.i_sx2), AGT2 = D.A * (Mo[MO_GT2] * D.i_st2);
+            const double BET = D.B * (Mo[MO_ET] * D.i_st), BED2 = D.B * (Mo[MO_ED2] * D.i_sx2);
+            const double ix = D.i_tx, it = D.i_tt, ih = D.i_h;
+            const double ix2 = ix * ix, it2 = it * it, ih2 = ih * ih;
+            q1[0] = over(AG) * D.i_mu0;
+            q1[1] = over(AGD2 * ix2 * ix - 2.0 * AG * ix);
+            q1[2] = D.tt_inf ? 0.0 : over(AGT2 * it2 * it - AG * it);
+            q1[3] = over(BE) * D.i_th0;
+            q1[4] = over(BE * D.i_om - BET);
+            q1[5] = over(BED2 * ih2 * ih - 2.0 * BE * ih);
+            if (mode == MODE_HESS) {
+                const double AGD4 = D.A * (Mo[MO_GD4] * D.i_sx2 * D.i_sx2);
+                const double AGT4 = D.A * (Mo[MO_GT4] * D.i_st2 * D.i_st2);
+                const double BET2 = D.B * (Mo[MO_ET2] * D.i_st2), BED4 = D.B * (Mo[MO_ED4] * D.i_sx2 * D.i_sx2);
+                const double ix4 = ix2 * ix2, it4 = it2 * it2, ih4 = ih2 * ih2;
+                double s2[6];
+                s2[0] = 0.0;
+                s2[1] = over(AGD4 * ix4 * ix2 - 7.0 * AGD2 * ix4 + 6.0 * AG * ix2);
+                s2[2] = D.tt_inf ? 0.0 : over(AGT4 * it4 * it2 - 5.0 * AGT2 * it4 + 2.0 * AG * it2);
+                s2[3] = 0.0;
+                s2[4] = over(BET2 - 2.0 * BET * D.i_om);
+                s2[5] = over(BED4 * ih4 * ih2 - 7.0 * BED2 * ih4 + 6.0 * BE * ih2);
+#pragma unroll
+                for (int p = 0; p < 6; ++p) q2[p] = s2[p] - q1[p] * q1[p];
+                if (D.tt_inf) q2[2] = 0.0;
+            }
+        }
+        if (c.fp32c) {
+            // column weight g^ = log2(B / lambda_n) - t~_n (t~_n as packed), formed in logs
+            const float *f = reinterpret_cast<const float *>(ws.src32);
+            const float tt_n = -f[8 * (i >> 1) + 4 + (i & 1)];
+            ghat = (float)((D.log2_b - ll * LOG2E) - (double)tt_n);
+        } else {
+            ws.w64[i] = D.ln_b - ll;  // log(B / lambda_n)
+        }
+    } else {
+        atomicOr(&ws.hdr[0], ST_ZERO);
+        if (!c.fp32c) ws.w64[i] = -INFINITY;  // weight 0
+    }
+
+    // this event's share of the integral term and its derivatives
+    const double tN = ws.centre[3];
+    const double ti = in.t[i], a_ = tN - ti, b_ = -ti;
+    const double th = exp(in.r[i]);
+    const double dec = exp(-D.om * a_);
+    const double one_m = -expm1(-D.om * a_);
+    double L = 0.0, dL[6] = {0, 0, 0, 0, 0, 0}, d2L[6] = {0, 0, 0, 0, 0, 0};
+    if (D.tt_inf) {
+        dL[0] = tN;
+    } else {
+        const double it = D.i_tt, za = a_ * it, zb = b_ * it;
+        const double pa = std_pdf(za), pb = std_pdf(zb);
+        dL[0] = std_cdf(za) - std_cdf(zb);
+        const double it2 = it * it, it3 = it2 * it, it5 = it3 * it2;
+        dL[2] = D.mu0 * (-(a_ * it2) * pa + (b_ * it2) * pb);
+        d2L[2] = D.mu0 * (pa * (2.0 * a_ * it3 - a_ * a_ * a_ * it5) - pb * (2.0 * b_ * it3 - b_ * b_ * b_ * it5));
+    }
+    L = D.mu0 * dL[0] + D.th0 * th * one_m;
+    dL[3] = th * one_m;
+    dL[4] = D.th0 * th * a_ * dec;
+    d2L[4] = -D.th0 * th * a_ * a_ * dec;
+    ws.dLr[i] = D.th0 * th * one_m;
+
+    acc[0] = ll - L;
+#pragma unroll
+    for (int p = 0; p < 6; ++p) {
+        acc[1 + p] = q1[p] - dL[p];
+        acc[7 + p] = q2[p] - d2L[p];
+    }
+    if (lam <= 0.0) acc[0] = 0.0;  // the status carries the -inf
+}
+
+__host__ __device__ constexpr bool row_mom_used(int mode, int k) {
+    return mode == MODE_HESS ? true
+         : mode == MODE_GRAD ? (k == MO_G || k == MO_GD2 || k == MO_GT2 || k == MO_E || k == MO_ET || k == MO_ED2)
+                             : (k == MO_G || k == MO_E);
+}
+
+// FP32C: the rows of target tile `tile`, finished by one block of TILE
+// threads (one row each) after the row pass:
+//   * the chunk partials summed in FP64 in chunk order;
+//   * rows whose FP32 background and excitation sums are both below 2^-60
+//     (terms under 2^-126 were flushed to zero in FP32) redone in FP64 over
+//     all sources, the block cooperating on one row at a time;
+//   * the row epilogue, the tile's 13 block sums, and the tile (and, on
+//     space-time tiles, group) maxima of the column weight g^.
+__device__ __forceinline__ void finish_tile_fp32c(const Consts &c, const Inputs &in, const Workspace &ws, int tile) {
+    const Derived &D = *c.d;
+    __shared__ double fsh[TILE];
+    __shared__ float fshf[TILE];
+    __shared__ int ftiny[TILE];
+    __shared__ int fcnt[TILE / 32];
+    const int i = tile * TILE + threadIdx.x;
+    const int n = c.g.n, npad = c.g.npad;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool valid = i < n;
+    double Mo[NMOM];
+#pragma unroll
+    for (int k = 0; k < NMOM; ++k) {
+        double s = 0.0;
+        if (valid && row_mom_used(c.mode, k)) {
+            for (int ch = 0; ch < c.g.n_chunks; ++ch) s += ws.rowpart[((size_t)ch * NMOM + k) * npad + i];
+        }
+        Mo[k] = s;
+    }
+    // rows to redo in FP64, listed in thread order
+    const bool tiny = valid && Mo[MO_G] < (double)TINY_ROW && Mo[MO_E] < (double)TINY_ROW;
+    const unsigned bal = __ballot_sync(0xffffffffu, tiny);
+    if (lane == 0) fcnt[warp] = __popc(bal);
+    __syncthreads();
+    int off = 0, ntiny = 0;
+#pragma unroll
+    for (int w = 0; w < TILE / 32; ++w) {
+        if (w < warp) off += fcnt[w];
+        ntiny += fcnt[w];
+    }
+    if (tiny) ftiny[off + __popc(bal & ((1u << lane) - 1u))] = threadIdx.x;
+    __syncthreads();
+    if (ntiny > 0) {
+        const double sx2 = D.sx * D.sx, st = D.st, st2 = D.st * D.st;
+        // raw units -> FP32C scaled units
+        const double scale[NMOM] = {1.0, sx2, st2, sx2 * sx2, st2 * st2, 1.0, st, st2, sx2, sx2 * sx2};
+        for (int q = 0; q < ntiny; ++q) {
+            const int owner = ftiny[q], row = tile * TILE + owner;
+            const double xn = in.x[row], yn = in.y[row], tn = in.t[row];
+            const int locn = ws.loc[row], gn = ws.gidx[row];
+            double a[NMOM];
+#pragma unroll
+            for (int k = 0; k < NMOM; ++k) a[k] = 0.0;
+            // FP32C_ST: the causal test compares time-order ranks
+            for (int j = threadIdx.x; j < n; j += TILE)
+                accumulate64<MODE_HESS>(a, in.x[j], in.y[j], in.t[j], in.r[j], ws.loc[j] != locn,
+                                        (c.st ? ws.perm[j] : j) < gn, xn, yn, tn, D);
+#pragma unroll
+            for (int k = 0; k < NMOM; ++k) {
+                const double v = block_sum<TILE>(a[k], fsh);
+                if (threadIdx.x == owner) Mo[k] = v * scale[k];
+            }
+        }
+    }
+    double acc[NACC];
+#pragma unroll
+    for (int k = 0; k < NACC; ++k) acc[k] = 0.0;
+    float ghat = -INFINITY;
+    if (valid) epilogue_row(c, D, in, ws, i, Mo, acc, ghat);
+    {
+        // the column pass's packed targets: the coordinates as packed, g^ in the fourth slot
+        const float *f = reinterpret_cast<const float *>(ws.src32);
+        float *o = reinterpret_cast<float *>(ws.tgt32);
+        const int p = i >> 1, l = i & 1;
+        o[8 * p + 0 + l] = f[8 * p + 0 + l];
+        o[8 * p + 2 + l] = f[8 * p + 2 + l];
+        o[8 * p + 4 + l] = f[8 * p + 4 + l];
+        o[8 * p + 6 + l] = ghat;
+    }
+    {
+        const double v = block_sum_multi<TILE, NACC>(acc, fsh);
+        if (threadIdx.x < NACC) ws.blockpart[(size_t)tile * ACC_STRIDE + threadIdx.x] = v;
+    }
+    if (c.st) {  // per-group bound for the column pass's pruning
+        const float wm = warp_maxf(ghat);
+        if (lane == 0) ws.grp[i / GROUP].tr.w = wm;
+    }
+    const float gm = block_max<TILE>(ghat, fshf);
+    if (threadIdx.x == 0) ws.tstat32[tile].w = gm;
+}
+
+}  // namespace hk

@@ -89,7 +89,9 @@ def workspace_size(n: int, precision="fp32c") -> int:
 def kernels_per_call(mode: str, precision="fp32c") -> int:
     """Number of kernels one call launches (memsets excluded)."""
     p = PRECISIONS[precision]
-    k = 7 + (1 if p != FP64 else 0)  # setup, prep, pack, row, combine, [fixup], epilogue, finalize
+    # FP64: setup, prep, pack, row, combine, epilogue, finalize; FP32C: setup, prep,
+    # pack, row, finish (combine, FP64 fix-up of tiny rows, epilogue), finalize
+    k = 7 if p == FP64 else 6
     if p == FP32C_ST:
         k += 2  # order: slab sort, gather
     if mode in ("grad", "hess"):

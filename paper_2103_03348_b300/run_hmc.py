@@ -25,7 +25,7 @@ import torch
 from . import build, hmc, synth, tree
 
 
-def run(precision="fp32c_band", iters=2000, warmup=200, n_steps=20, mass_every=100, eps0=0.05, seed=0, n=23422,
+def run(precision="fp32c_st", iters=2000, warmup=200, n_steps=20, mass_every=100, eps0=0.05, seed=0, n=23422,
         m_seq=1610, device="cuda", prior="tree", checkpoint=None, checkpoint_every=0, resume=None):
     build.build()
     w = synth.make_ebola_like(n=n, m_seq=m_seq)
@@ -66,7 +66,7 @@ def run(precision="fp32c_band", iters=2000, warmup=200, n_steps=20, mass_every=1
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--precision", default="fp32c_band", choices=["fp32c_st", "fp32c_band", "fp32c", "fp64"])
+    ap.add_argument("--precision", default="fp32c_st", choices=["fp32c_st", "fp32c_band", "fp32c", "fp64"])
     ap.add_argument("--iters", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--steps", type=int, default=20)

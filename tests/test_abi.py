@@ -102,9 +102,11 @@ def test_hess_diag_accepts_null_loglik_and_grad_only_after_checks(L):
 
 
 def test_kernel_count_per_call():
-    assert hawkes.kernels_per_call("hess", "fp32c") == 10
+    # FP32C: setup, prep, pack, row, finish, finalize [, column, column finish]
+    assert hawkes.kernels_per_call("hess", "fp32c") == 8
     assert hawkes.kernels_per_call("grad", "fp64") == 9
-    assert hawkes.kernels_per_call("loglik", "fp32c") == 8
+    assert hawkes.kernels_per_call("loglik", "fp32c") == 6
+    assert hawkes.kernels_per_call("hess", "fp32c_st") == 10  # and the slab sort and gather
 
 
 def test_predictive_argument_checks(L):
