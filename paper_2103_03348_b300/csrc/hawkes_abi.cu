@@ -65,6 +65,7 @@ size_t carve(void *base, const Geometry &g, int precision, Workspace *w) {
     w->mom = (double *)take((size_t)NMOM * np * sizeof(double));
     w->dLr = (double *)take(np * sizeof(double));
     w->blockpart = (double *)take(nt * ACC_STRIDE * sizeof(double));
+    w->ipart = f32 ? (double *)take(nt * ACC_STRIDE * sizeof(double)) : nullptr;
     w->colpart = (double *)take((size_t)g.n_chunks * 2 * np * sizeof(double));
     w->bbox = (double *)take(4 * sizeof(double));
     w->perm = st ? (int *)take(np * sizeof(int)) : nullptr;
@@ -88,56 +89,68 @@ static bool params_valid(const double *p) {
     return true;
 }
 
-// One thread derives every parameter-dependent constant in FP64.  Parameters
-// that are not finite and positive (tau_t may be +inf) set ST_BADPARAM, and
-// finalize then reports HAWKES_EINVAL with NaN outputs.
+// Every parameter-dependent constant, derived in FP64 by one warp: lane k < 6
+// reads (and exponentiates) parameter k, then lanes compute independent
+// groups of constants side by side, so the serial chain is a few operations
+// long.  Parameters that are not finite and positive (tau_t may be +inf) set
+// ST_BADPARAM, and finalize then reports HAWKES_EINVAL with NaN outputs.
 __global__ void setup_kernel(ParamSource ps, int fp32c, int reuse, Derived *out, int *hdr, const int *evbits) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    if (reuse) hdr[0] |= *evbits;  // the event checks of the call that prepared these events
+    if (blockIdx.x != 0) return;
+    const int lane = threadIdx.x;
+    double pv = 0.0;
+    if (lane < 6) pv = ps.dev ? (ps.log_scale ? exp(ps.dev[lane]) : ps.dev[lane]) : ps.v[lane];
     double p[6];
-    bool ok = true;
-    for (int k = 0; k < 6; ++k) {
-        p[k] = ps.dev ? (ps.log_scale ? exp(ps.dev[k]) : ps.dev[k]) : ps.v[k];
-        if (k == 2 && isinf(p[k]) && p[k] > 0) continue;
-        if (!isfinite(p[k]) || !(p[k] > 0)) ok = false;
-    }
-    Derived d;
-    d.mu0 = p[0]; d.tx = p[1]; d.tt = p[2]; d.th0 = p[3]; d.om = p[4]; d.h = p[5];
-    d.tt_inf = isinf(d.tt) ? 1 : 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) p[k] = __shfl_sync(0xffffffffu, pv, k);
+    const double mu0 = p[0], tx = p[1], tt = p[2], th0 = p[3], om = p[4], h = p[5];
+    const int tt_inf = isinf(tt) ? 1 : 0;
     const double two_pi = 6.283185307179586476925286766559;
-    d.A = d.tt_inf ? d.mu0 / (two_pi * d.tx * d.tx) : d.mu0 / (two_pi * sqrt(two_pi) * d.tx * d.tx * d.tt);
-    d.B = d.th0 * d.om / (two_pi * d.h * d.h);
-    // FP64 pair constants (also used by the FP32C fix-up rows)
-    d.ibx = 1.0 / (2.0 * d.tx * d.tx);
-    d.ibt = d.tt_inf ? 0.0 : 1.0 / (2.0 * d.tt * d.tt);
-    d.ih = 1.0 / (2.0 * d.h * d.h);
-    if (fp32c) {
+    const double B = th0 * om / (two_pi * h * h);
+    const double sx = fp32c ? sqrt(LOG2E / 2.0) / tx : 1.0;
+    const double st = fp32c ? om * LOG2E : 1.0;
+    switch (lane) {
+        case 0: {
+            if (reuse) hdr[0] |= *evbits;  // the event checks of the call that prepared these events
+            bool ok = true;
+            for (int k = 0; k < 6; ++k) {
+                if (k == 2 && isinf(p[k]) && p[k] > 0) continue;
+                if (!isfinite(p[k]) || !(p[k] > 0)) ok = false;
+            }
+            out->mu0 = mu0; out->tx = tx; out->tt = tt; out->th0 = th0; out->om = om; out->h = h;
+            out->tt_inf = tt_inf;
+            out->valid = ok ? 1 : 0;
+            if (!ok) atomicOr(&hdr[0], ST_BADPARAM);
+            break;
+        }
+        case 1: out->A = tt_inf ? mu0 / (two_pi * tx * tx) : mu0 / (two_pi * sqrt(two_pi) * tx * tx * tt); break;
+        case 2: out->B = B; break;
+        case 3: out->ln_b = log(B); break;
+        case 4: out->log2_b = log2(B); break;
+        // FP64 pair constants (also used by the FP32C fix-up rows)
+        case 5: out->ibx = 1.0 / (2.0 * tx * tx); break;
+        case 6: out->ibt = tt_inf ? 0.0 : 1.0 / (2.0 * tt * tt); break;
+        case 7: out->ih = 1.0 / (2.0 * h * h); break;
         // x~ = (x - xc) sqrt(log2(e)/2) / tau_x makes the background's spatial exponent -d~^2;
         // t~ = (t - tc) omega log2(e) makes the excitation's temporal exponent -dt~.
-        d.sx = sqrt(LOG2E / 2.0) / d.tx;
-        d.st = d.om * LOG2E;
-        d.cbt = d.tt_inf ? 0.0f : (float)(LOG2E / (2.0 * d.tt * d.tt) / (d.st * d.st));
-        d.hh = (float)((d.tx / d.h) * (d.tx / d.h));
-    } else {
-        d.sx = 1.0;
-        d.st = 1.0;
-        d.cbt = 0.0f;
-        d.hh = 0.0f;
+        case 8: out->sx = sx; out->i_sx2 = 1.0 / (sx * sx); break;
+        case 9: {
+            out->st = st;
+            const double i_st = 1.0 / st;
+            out->i_st = i_st;
+            out->i_st2 = i_st * i_st;
+            break;
+        }
+        case 10: out->cbt = (fp32c && !tt_inf) ? (float)(LOG2E / (2.0 * tt * tt) / (st * st)) : 0.0f; break;
+        case 11: out->hh = fp32c ? (float)((tx / h) * (tx / h)) : 0.0f; break;
+        // reciprocals for the row epilogue
+        case 12: out->i_mu0 = 1.0 / mu0; break;
+        case 13: out->i_tx = 1.0 / tx; break;
+        case 14: out->i_tt = tt_inf ? 0.0 : 1.0 / tt; break;
+        case 15: out->i_th0 = 1.0 / th0; break;
+        case 16: out->i_om = 1.0 / om; break;
+        case 17: out->i_h = 1.0 / h; break;
+        default: break;
     }
-    d.i_mu0 = 1.0 / d.mu0;
-    d.i_tx = 1.0 / d.tx;
-    d.i_tt = d.tt_inf ? 0.0 : 1.0 / d.tt;
-    d.i_th0 = 1.0 / d.th0;
-    d.i_om = 1.0 / d.om;
-    d.i_h = 1.0 / d.h;
-    d.i_sx2 = 1.0 / (d.sx * d.sx);
-    d.i_st = 1.0 / d.st;
-    d.i_st2 = d.i_st * d.i_st;
-    d.ln_b = log(d.B);
-    d.log2_b = log2(d.B);
-    d.valid = ok ? 1 : 0;
-    if (!ok) atomicOr(&hdr[0], ST_BADPARAM);
-    *out = d;
 }
 
 cudaError_t launch_setup(const Consts &c, const ParamSource &ps, const Workspace &ws, cudaStream_t s, int reuse) {
@@ -242,7 +255,7 @@ static int phase_rows(const Call &k, void *const *events) {
     if (launch_pack(c, k.inw, ws, k.in.r, s) != cudaSuccess) return HAWKES_ECUDA;
     if (!mark(events, 0, s)) return HAWKES_ECUDA;
     if (c.t1 > c.t0) {
-        if ((c.fp32c ? launch_row32(c, ws, s) : launch_row64(c, ws, s)) != cudaSuccess) return HAWKES_ECUDA;
+        if ((c.fp32c ? launch_row32(c, k.inw, ws, s) : launch_row64(c, ws, s)) != cudaSuccess) return HAWKES_ECUDA;
     }
     if (!mark(events, 1, s)) return HAWKES_ECUDA;
     if (c.t1 > c.t0) {

@@ -129,6 +129,7 @@ struct Workspace {
     double *w64;         // [npad]  FP64 column weight, in logs: log(B / lambda_n)
     double *dLr;         // [npad]  dLambda / dr_m
     double *blockpart;   // [tiles * ACC_STRIDE]
+    double *ipart;       // [tiles * ACC_STRIDE] FP32C: the integral-term sums of each tile (row pass)
     float *sufmax;       // [tiles] suffix max of the column weight bound (FP32C)
     double *colpart;     // [n_chunks * 2 * npad]
     double *bbox;        // [4]: x min, x max, y min, y max of the events (prep)
@@ -159,7 +160,7 @@ cudaError_t launch_prep(const Consts &c, const Inputs &in, const Workspace &ws, 
 cudaError_t launch_order(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_pack(const Consts &c, const Inputs &in, const Workspace &ws, const double *r_time_order,
                         cudaStream_t s);
-cudaError_t launch_row32(const Consts &c, const Workspace &ws, cudaStream_t s);
+cudaError_t launch_row32(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_finish(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_row64(const Consts &c, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_combine(const Consts &c, const Workspace &ws, cudaStream_t s);
@@ -170,7 +171,7 @@ cudaError_t launch_col64(const Consts &c, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_colfinish(const Consts &c, const Workspace &ws, const Outputs &out, cudaStream_t s);
 cudaError_t launch_col32_subset(const Consts &c, const Inputs &in, const Workspace &ws, const int *rate_idx,
                                 int k_rates, cudaStream_t s);
-cudaError_t launch_row32_st(const Consts &c, const Workspace &ws, cudaStream_t s);
+cudaError_t launch_row32_st(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_col32_st(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s);
 cudaError_t launch_col32_subset_st(const Consts &c, const Inputs &in, const Workspace &ws, const int *rate_idx,
                                    int k_rates, cudaStream_t s);

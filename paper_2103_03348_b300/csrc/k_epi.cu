@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(TILE) epilogue_kernel(Consts c, Inputs in, Wor
         double Mo[NMOM];
 #pragma unroll
         for (int k = 0; k < NMOM; ++k) Mo[k] = ws.mom[(size_t)k * npad + i];
-        epilogue_row(c, D, in, ws, i, Mo, acc, ghat);
+        epilogue_row<true>(c, D, in, ws, i, Mo, acc, ghat);
     }
     {
         const double v = block_sum_multi<TILE, NACC>(acc, sh);
@@ -142,23 +142,27 @@ __global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(Consts c, Workspa
     if (c.fp32c && c.mode >= MODE_GRAD) {
         // suffix max of the per-tile column weight bound, for the column sweep's stop test:
         // each thread owns a contiguous segment of tiles; segment maxima are scanned in shared memory
-        __shared__ float seg[FIN_THREADS];
+        // (max is exact, so the scan order does not matter)
+        __shared__ float wmax[FIN_THREADS / 32];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         const int len = (tiles + FIN_THREADS - 1) / FIN_THREADS;
         const int b0 = threadIdx.x * len, b1 = min(tiles, b0 + len);
         float m = -INFINITY;
         for (int b = b0; b < b1; ++b) m = fmaxf(m, ws.tstat32[b].w);
-        seg[threadIdx.x] = m;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            float run = -INFINITY;
-            for (int k = FIN_THREADS - 1; k >= 0; --k) {
-                const float v = seg[k];
-                seg[k] = run;  // max over the later segments
-                run = fmaxf(run, v);
-            }
+        // inclusive suffix max within the warp, then over the later warps
+        float v = m;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const float u = __shfl_down_sync(0xffffffffu, v, o);
+            if (lane + o < 32) v = fmaxf(v, u);
         }
+        if (lane == 0) wmax[warp] = v;
         __syncthreads();
-        float run = seg[threadIdx.x];
+        float later = -INFINITY;
+        for (int w = warp + 1; w < FIN_THREADS / 32; ++w) later = fmaxf(later, wmax[w]);
+        float excl = __shfl_down_sync(0xffffffffu, v, 1);  // max over the later segments of this warp
+        if (lane == 31) excl = -INFINITY;
+        float run = fmaxf(excl, later);
         for (int b = b1 - 1; b >= b0; --b) {
             run = fmaxf(run, ws.tstat32[b].w);
             ws.sufmax[b] = run;

@@ -27,11 +27,12 @@
 //     tiles that straddle the causal boundary, and tiles that both hold events
 //     with a duplicated location.
 #include "row32_pair.cuh"
+#include "rows_finish.cuh"
 
 namespace hk {
 
 template <int MODE, bool BAND>
-__global__ void __launch_bounds__(TILE, 4) row32_kernel(Consts c, Workspace ws) {
+__global__ void __launch_bounds__(TILE, 4) row32_kernel(Consts c, Inputs in, Workspace ws) {
     const Derived &D = *c.d;
     // Chunk order: blocks are dispatched y-major, so y = 0 takes the chunk that
     // holds the tile itself, y = 1 the chunk before it, and so on, wrapping to
@@ -118,19 +119,21 @@ __global__ void __launch_bounds__(TILE, 4) row32_kernel(Consts c, Workspace ws) 
         if (mom_used(MODE, k))
             ws.rowpart[((size_t)chunk * NMOM + k) * npad + i] = (double)ks[k] - (double)kc[k];
     }
+    // one block per tile also computes the tile's integral-term shares (FP64)
+    if (blockIdx.y == 0) integral_tile(c, in, ws, tile);
 }
 
-cudaError_t launch_row32(const Consts &c, const Workspace &ws, cudaStream_t s) {
+cudaError_t launch_row32(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s) {
     const dim3 grid(c.t1 - c.t0, c.g.n_chunks);
-    if (c.st) return launch_row32_st(c, ws, s);
+    if (c.st) return launch_row32_st(c, in, ws, s);
     if (c.band) {
-        if (c.mode == MODE_HESS) row32_kernel<MODE_HESS, true><<<grid, TILE, 0, s>>>(c, ws);
-        else if (c.mode == MODE_GRAD) row32_kernel<MODE_GRAD, true><<<grid, TILE, 0, s>>>(c, ws);
-        else row32_kernel<MODE_LL, true><<<grid, TILE, 0, s>>>(c, ws);
+        if (c.mode == MODE_HESS) row32_kernel<MODE_HESS, true><<<grid, TILE, 0, s>>>(c, in, ws);
+        else if (c.mode == MODE_GRAD) row32_kernel<MODE_GRAD, true><<<grid, TILE, 0, s>>>(c, in, ws);
+        else row32_kernel<MODE_LL, true><<<grid, TILE, 0, s>>>(c, in, ws);
     } else {
-        if (c.mode == MODE_HESS) row32_kernel<MODE_HESS, false><<<grid, TILE, 0, s>>>(c, ws);
-        else if (c.mode == MODE_GRAD) row32_kernel<MODE_GRAD, false><<<grid, TILE, 0, s>>>(c, ws);
-        else row32_kernel<MODE_LL, false><<<grid, TILE, 0, s>>>(c, ws);
+        if (c.mode == MODE_HESS) row32_kernel<MODE_HESS, false><<<grid, TILE, 0, s>>>(c, in, ws);
+        else if (c.mode == MODE_GRAD) row32_kernel<MODE_GRAD, false><<<grid, TILE, 0, s>>>(c, in, ws);
+        else row32_kernel<MODE_LL, false><<<grid, TILE, 0, s>>>(c, in, ws);
     }
     return cudaGetLastError();
 }

@@ -1,6 +1,7 @@
 // FP32C_ST row pass (space-time tiles): see row32_st_kernel below; the pair
 // arithmetic is that of the time-order row pass (row32_pair.cuh).
 #include "row32_pair.cuh"
+#include "rows_finish.cuh"
 
 namespace hk {
 
@@ -16,7 +17,7 @@ namespace hk {
 constexpr int GPT = TILE / GROUP;  // groups per tile
 
 template <int MODE>
-__global__ void __launch_bounds__(TILE, 4) row32_st_kernel(Consts c, Workspace ws) {
+__global__ void __launch_bounds__(TILE, 4) row32_st_kernel(Consts c, Inputs in, Workspace ws) {
     const Derived &D = *c.d;
     const int tile = c.t0 + blockIdx.x;
     const int chunk = (tile / c.g.chunk_tiles - (int)blockIdx.y + c.g.n_chunks) % c.g.n_chunks;
@@ -136,13 +137,15 @@ __global__ void __launch_bounds__(TILE, 4) row32_st_kernel(Consts c, Workspace w
         if (mom_used(MODE, k))
             ws.rowpart[((size_t)chunk * NMOM + k) * npad + i] = (double)ks[k] - (double)kc[k];
     }
+    // one block per tile also computes the tile's integral-term shares (FP64)
+    if (blockIdx.y == 0) integral_tile(c, in, ws, tile);
 }
 
-cudaError_t launch_row32_st(const Consts &c, const Workspace &ws, cudaStream_t s) {
+cudaError_t launch_row32_st(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s) {
     const dim3 grid(c.t1 - c.t0, c.g.n_chunks);
-    if (c.mode == MODE_HESS) row32_st_kernel<MODE_HESS><<<grid, TILE, 0, s>>>(c, ws);
-    else if (c.mode == MODE_GRAD) row32_st_kernel<MODE_GRAD><<<grid, TILE, 0, s>>>(c, ws);
-    else row32_st_kernel<MODE_LL><<<grid, TILE, 0, s>>>(c, ws);
+    if (c.mode == MODE_HESS) row32_st_kernel<MODE_HESS><<<grid, TILE, 0, s>>>(c, in, ws);
+    else if (c.mode == MODE_GRAD) row32_st_kernel<MODE_GRAD><<<grid, TILE, 0, s>>>(c, in, ws);
+    else row32_st_kernel<MODE_LL><<<grid, TILE, 0, s>>>(c, in, ws);
     return cudaGetLastError();
 }
 

@@ -30,10 +30,47 @@ __device__ __forceinline__ void accumulate64(double (&a)[NMOM], double xs, doubl
 __device__ __forceinline__ double std_pdf(double z) { return 0.3989422804014327 * exp(-0.5 * z * z); }
 __device__ __forceinline__ double std_cdf(double z) { return 0.5 * erfc(-z * 0.7071067811865476); }
 
+// This event's share of the integral term (Appendix A Claim, the background
+// integrated exactly over [0, t_N]) and its derivatives, subtracted from
+// acc[0], acc[1..6] and acc[7..12]; dLambda/dr_i goes to dLr[i].  It depends
+// on the parameters and the event alone, not on the row sums.
+__device__ __forceinline__ void integral_row(const Derived &D, const Inputs &in, const Workspace &ws, int i,
+                                             double (&acc)[NACC]) {
+    const double tN = ws.centre[3];
+    const double ti = in.t[i], a_ = tN - ti, b_ = -ti;
+    const double th = exp(in.r[i]);
+    const double dec = exp(-D.om * a_);
+    const double one_m = -expm1(-D.om * a_);
+    double L = 0.0, dL[6] = {0, 0, 0, 0, 0, 0}, d2L[6] = {0, 0, 0, 0, 0, 0};
+    if (D.tt_inf) {
+        dL[0] = tN;
+    } else {
+        const double it = D.i_tt, za = a_ * it, zb = b_ * it;
+        const double pa = std_pdf(za), pb = std_pdf(zb);
+        dL[0] = std_cdf(za) - std_cdf(zb);
+        const double it2 = it * it, it3 = it2 * it, it5 = it3 * it2;
+        dL[2] = D.mu0 * (-(a_ * it2) * pa + (b_ * it2) * pb);
+        d2L[2] = D.mu0 * (pa * (2.0 * a_ * it3 - a_ * a_ * a_ * it5) - pb * (2.0 * b_ * it3 - b_ * b_ * b_ * it5));
+    }
+    L = D.mu0 * dL[0] + D.th0 * th * one_m;
+    dL[3] = th * one_m;
+    dL[4] = D.th0 * th * a_ * dec;
+    d2L[4] = -D.th0 * th * a_ * a_ * dec;
+    ws.dLr[i] = D.th0 * th * one_m;
+    acc[0] -= L;
+#pragma unroll
+    for (int p = 0; p < 6; ++p) {
+        acc[1 + p] -= dL[p];
+        acc[7 + p] -= d2L[p];
+    }
+}
+
 // The row epilogue of event i (one thread): lambda_n and its derivative terms
-// from the moments Mo (Eq. 1 and its parameter derivatives), the FP32C column
-// weight g^ (returned in ghat) or the FP64 weight, and the event's share of the integral term (Appendix A Claim) with
-// its derivatives and dLambda/dr_i; acc receives the 13 per-row terms.
+// from the moments Mo (Eq. 1 and its parameter derivatives) into acc (the
+// 13 per-row terms: log lambda_n, the six q1 and the six q2), the FP32C column
+// weight g^ (returned in ghat) or the FP64 weight, and with INTEGRAL the
+// event's share of the integral term subtracted (integral_row).
+template <bool INTEGRAL>
 __device__ __forceinline__ void epilogue_row(const Consts &c, const Derived &D, const Inputs &in, const Workspace &ws,
                                              int i, const double (&Mo)[NMOM], double (&acc)[NACC], float &ghat) {
     const int mode = c.mode;
@@ -92,35 +129,13 @@ __device__ __forceinline__ void epilogue_row(const Consts &c, const Derived &D, 
         if (!c.fp32c) ws.w64[i] = -INFINITY;  // weight 0
     }
 
-    // this event's share of the integral term and its derivatives
-    const double tN = ws.centre[3];
-    const double ti = in.t[i], a_ = tN - ti, b_ = -ti;
-    const double th = exp(in.r[i]);
-    const double dec = exp(-D.om * a_);
-    const double one_m = -expm1(-D.om * a_);
-    double L = 0.0, dL[6] = {0, 0, 0, 0, 0, 0}, d2L[6] = {0, 0, 0, 0, 0, 0};
-    if (D.tt_inf) {
-        dL[0] = tN;
-    } else {
-        const double it = D.i_tt, za = a_ * it, zb = b_ * it;
-        const double pa = std_pdf(za), pb = std_pdf(zb);
-        dL[0] = std_cdf(za) - std_cdf(zb);
-        const double it2 = it * it, it3 = it2 * it, it5 = it3 * it2;
-        dL[2] = D.mu0 * (-(a_ * it2) * pa + (b_ * it2) * pb);
-        d2L[2] = D.mu0 * (pa * (2.0 * a_ * it3 - a_ * a_ * a_ * it5) - pb * (2.0 * b_ * it3 - b_ * b_ * b_ * it5));
-    }
-    L = D.mu0 * dL[0] + D.th0 * th * one_m;
-    dL[3] = th * one_m;
-    dL[4] = D.th0 * th * a_ * dec;
-    d2L[4] = -D.th0 * th * a_ * a_ * dec;
-    ws.dLr[i] = D.th0 * th * one_m;
-
-    acc[0] = ll - L;
+    acc[0] = ll;
 #pragma unroll
     for (int p = 0; p < 6; ++p) {
-        acc[1 + p] = q1[p] - dL[p];
-        acc[7 + p] = q2[p] - d2L[p];
+        acc[1 + p] = q1[p];
+        acc[7 + p] = q2[p];
     }
+    if (INTEGRAL) integral_row(D, in, ws, i, acc);
     if (lam <= 0.0) acc[0] = 0.0;  // the status carries the -inf
 }
 
@@ -196,7 +211,7 @@ __device__ __forceinline__ void finish_tile_fp32c(const Consts &c, const Inputs 
 #pragma unroll
     for (int k = 0; k < NACC; ++k) acc[k] = 0.0;
     float ghat = -INFINITY;
-    if (valid) epilogue_row(c, D, in, ws, i, Mo, acc, ghat);
+    if (valid) epilogue_row<false>(c, D, in, ws, i, Mo, acc, ghat);  // the integral term came with the row pass
     {
         // the column pass's packed targets: the coordinates as packed, g^ in the fourth slot
         const float *f = reinterpret_cast<const float *>(ws.src32);
@@ -209,7 +224,8 @@ __device__ __forceinline__ void finish_tile_fp32c(const Consts &c, const Inputs 
     }
     {
         const double v = block_sum_multi<TILE, NACC>(acc, fsh);
-        if (threadIdx.x < NACC) ws.blockpart[(size_t)tile * ACC_STRIDE + threadIdx.x] = v;
+        if (threadIdx.x < NACC)
+            ws.blockpart[(size_t)tile * ACC_STRIDE + threadIdx.x] = v + ws.ipart[(size_t)tile * ACC_STRIDE + threadIdx.x];
     }
     if (c.st) {  // per-group bound for the column pass's pruning
         const float wm = warp_maxf(ghat);
@@ -217,6 +233,22 @@ __device__ __forceinline__ void finish_tile_fp32c(const Consts &c, const Inputs 
     }
     const float gm = block_max<TILE>(ghat, fshf);
     if (threadIdx.x == 0) ws.tstat32[tile].w = gm;
+}
+
+// FP32C: the integral-term shares of tile `tile`'s events (FP64), summed over
+// the tile into ipart, with dLambda/dr per event.  Called by one row block
+// per tile after its pair loop, so this FP64 work runs beside other blocks'
+// FP32 pair arithmetic instead of in the finish kernel.
+static __device__ __noinline__ void integral_tile(const Consts &c, const Inputs &in, const Workspace &ws, int tile) {
+    __shared__ double ish[(TILE / 32) * NACC];
+    const Derived &D = *c.d;
+    const int i = tile * TILE + threadIdx.x;
+    double a[NACC];
+#pragma unroll
+    for (int k = 0; k < NACC; ++k) a[k] = 0.0;
+    if (i < c.g.n) integral_row(D, in, ws, i, a);
+    const double v = block_sum_multi<TILE, NACC>(a, ish);
+    if (threadIdx.x < NACC) ws.ipart[(size_t)tile * ACC_STRIDE + threadIdx.x] = v;
 }
 
 }  // namespace hk
