@@ -95,6 +95,7 @@ static bool params_valid(const double *p) {
 // long.  Parameters that are not finite and positive (tau_t may be +inf) set
 // ST_BADPARAM, and finalize then reports HAWKES_EINVAL with NaN outputs.
 __global__ void setup_kernel(ParamSource ps, int fp32c, int reuse, Derived *out, int *hdr, const int *evbits) {
+    pdl_wait();
     if (blockIdx.x != 0) return;
     const int lane = threadIdx.x;
     double pv = 0.0;
@@ -108,9 +109,11 @@ __global__ void setup_kernel(ParamSource ps, int fp32c, int reuse, Derived *out,
     const double B = th0 * om / (two_pi * h * h);
     const double sx = fp32c ? sqrt(LOG2E / 2.0) / tx : 1.0;
     const double st = fp32c ? om * LOG2E : 1.0;
+    // the call's header: status bits (with the event checks of the call that
+    // prepared these events, when they are reused), the rest cleared
+    if (lane > 0 && lane < 8) hdr[lane] = 0;
     switch (lane) {
         case 0: {
-            if (reuse) hdr[0] |= *evbits;  // the event checks of the call that prepared these events
             bool ok = true;
             for (int k = 0; k < 6; ++k) {
                 if (k == 2 && isinf(p[k]) && p[k] > 0) continue;
@@ -119,7 +122,7 @@ __global__ void setup_kernel(ParamSource ps, int fp32c, int reuse, Derived *out,
             out->mu0 = mu0; out->tx = tx; out->tt = tt; out->th0 = th0; out->om = om; out->h = h;
             out->tt_inf = tt_inf;
             out->valid = ok ? 1 : 0;
-            if (!ok) atomicOr(&hdr[0], ST_BADPARAM);
+            hdr[0] = (reuse ? *evbits : 0) | (ok ? 0 : ST_BADPARAM);
             break;
         }
         case 1: out->A = tt_inf ? mu0 / (two_pi * tx * tx) : mu0 / (two_pi * sqrt(two_pi) * tx * tx * tt); break;
@@ -154,7 +157,7 @@ __global__ void setup_kernel(ParamSource ps, int fp32c, int reuse, Derived *out,
 }
 
 cudaError_t launch_setup(const Consts &c, const ParamSource &ps, const Workspace &ws, cudaStream_t s, int reuse) {
-    setup_kernel<<<1, 32, 0, s>>>(ps, c.fp32c, reuse, ws.derived, ws.hdr, ws.evbits);
+    launch_pdl(setup_kernel, 1, 32, 0, s, ps, c.fp32c, reuse, ws.derived, ws.hdr, ws.evbits);
     return cudaGetLastError();
 }
 
@@ -234,8 +237,7 @@ static int phase_rows(const Call &k, void *const *events) {
     const Workspace &ws = k.ws;
     cudaStream_t s = k.s;
     const size_t hdr_ints = 8;  // the header; evbits follows
-    if (k.reuse) {  // evbits keeps the event checks of the call that prepared the events
-        if (cudaMemsetAsync(ws.hdr, 0, hdr_ints * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;
+    if (k.reuse) {  // setup clears the header; evbits keeps the event checks of the call that prepared the events
         if (launch_setup(c, k.ps, ws, s, 1) != cudaSuccess) return HAWKES_ECUDA;
     } else {
         if (cudaMemsetAsync(ws.hdr, 0, (hdr_ints + 1) * sizeof(int), s) != cudaSuccess) return HAWKES_ECUDA;

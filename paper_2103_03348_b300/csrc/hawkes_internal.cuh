@@ -20,7 +20,31 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "hawkes.h"
+
+// Kernel launch with programmatic dependent launch allowed: in a stream (and
+// in a graph captured from it) the next kernel is set up while this one
+// drains, so a chain of short kernels loses less time between launches.
+// Every kernel launched this way starts with hk::pdl_wait(), which holds it
+// until everything before it on the stream has completed and is visible, so
+// the ordering is that of a plain launch.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 namespace hk {
 
@@ -187,6 +211,11 @@ cudaError_t launch_tree_prior(int64_t m, const int *plan, const double *len, dou
 // device helpers
 // ---------------------------------------------------------------------------
 #ifdef __CUDACC__
+
+// Wait for the preceding kernel of the stream (programmatic dependent launch;
+// a no-op for a plain launch).  The first statement of every kernel started
+// with launch_pdl.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 __device__ __forceinline__ float ex2_ftz(float x) {
     float y;

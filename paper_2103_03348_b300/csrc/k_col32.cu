@@ -23,6 +23,7 @@ namespace hk {
 
 template <int MODE>
 __global__ void __launch_bounds__(TILE, 4) col32_kernel(Consts c, Inputs in, Workspace ws) {
+    pdl_wait();
     const Derived &D = *c.d;
     const int tile = c.t0 + blockIdx.x, chunk = blockIdx.y;
     const int m = tile * TILE + threadIdx.x;
@@ -88,6 +89,7 @@ __global__ void __launch_bounds__(TILE, 4) col32_kernel(Consts c, Inputs in, Wor
 template <int MODE>
 __global__ void __launch_bounds__(TILE, 4) col32_subset_kernel(Consts c, Inputs in, Workspace ws,
                                                                const int *__restrict__ rate_idx, int k_rates) {
+    pdl_wait();
     const Derived &D = *c.d;
     const int j = blockIdx.x * TILE + threadIdx.x, chunk = blockIdx.y;
     const int n = c.g.n, npad = c.g.npad;
@@ -168,16 +170,16 @@ cudaError_t launch_col32_subset(const Consts &c, const Inputs &in, const Workspa
                                 int k_rates, cudaStream_t s) {
     if (c.st) return launch_col32_subset_st(c, in, ws, rate_idx, k_rates, s);
     const dim3 grid((k_rates + TILE - 1) / TILE, c.g.n_chunks);
-    if (c.mode == MODE_HESS) col32_subset_kernel<MODE_HESS><<<grid, TILE, 0, s>>>(c, in, ws, rate_idx, k_rates);
-    else col32_subset_kernel<MODE_GRAD><<<grid, TILE, 0, s>>>(c, in, ws, rate_idx, k_rates);
+    if (c.mode == MODE_HESS) launch_pdl(col32_subset_kernel<MODE_HESS>, grid, TILE, 0, s, c, in, ws, rate_idx, k_rates);
+    else launch_pdl(col32_subset_kernel<MODE_GRAD>, grid, TILE, 0, s, c, in, ws, rate_idx, k_rates);
     return cudaGetLastError();
 }
 
 cudaError_t launch_col32(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s) {
     const dim3 grid(c.t1 - c.t0, c.g.n_chunks);
     if (c.st) return launch_col32_st(c, in, ws, s);
-    if (c.mode == MODE_HESS) col32_kernel<MODE_HESS><<<grid, TILE, 0, s>>>(c, in, ws);
-    else col32_kernel<MODE_GRAD><<<grid, TILE, 0, s>>>(c, in, ws);
+    if (c.mode == MODE_HESS) launch_pdl(col32_kernel<MODE_HESS>, grid, TILE, 0, s, c, in, ws);
+    else launch_pdl(col32_kernel<MODE_GRAD>, grid, TILE, 0, s, c, in, ws);
     return cudaGetLastError();
 }
 

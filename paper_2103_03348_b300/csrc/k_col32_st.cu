@@ -93,6 +93,7 @@ __device__ __forceinline__ void col_sweep_st(const Workspace &ws, int ub, int ue
 
 template <int MODE>
 __global__ void __launch_bounds__(TILE, 4) col32_st_kernel(Consts c, Inputs in, Workspace ws) {
+    pdl_wait();
     const Derived &D = *c.d;
     const int tile = c.t0 + blockIdx.x, chunk = blockIdx.y;
     const int m = tile * TILE + threadIdx.x;  // position
@@ -133,6 +134,7 @@ __global__ void __launch_bounds__(TILE, 4) col32_st_kernel(Consts c, Inputs in, 
 template <int MODE>
 __global__ void __launch_bounds__(TILE, 4) col32_subset_st_kernel(Consts c, Inputs in, Workspace ws,
                                                                   const int *__restrict__ rate_idx, int k_rates) {
+    pdl_wait();
     const Derived &D = *c.d;
     const int j = blockIdx.x * TILE + threadIdx.x, chunk = blockIdx.y;
     const int n = c.g.n, npad = c.g.npad;
@@ -189,16 +191,16 @@ __global__ void __launch_bounds__(TILE, 4) col32_subset_st_kernel(Consts c, Inpu
 
 cudaError_t launch_col32_st(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s) {
     const dim3 grid(c.t1 - c.t0, c.g.n_chunks);
-    if (c.mode == MODE_HESS) col32_st_kernel<MODE_HESS><<<grid, TILE, 0, s>>>(c, in, ws);
-    else col32_st_kernel<MODE_GRAD><<<grid, TILE, 0, s>>>(c, in, ws);
+    if (c.mode == MODE_HESS) launch_pdl(col32_st_kernel<MODE_HESS>, grid, TILE, 0, s, c, in, ws);
+    else launch_pdl(col32_st_kernel<MODE_GRAD>, grid, TILE, 0, s, c, in, ws);
     return cudaGetLastError();
 }
 
 cudaError_t launch_col32_subset_st(const Consts &c, const Inputs &in, const Workspace &ws, const int *rate_idx,
                                    int k_rates, cudaStream_t s) {
     const dim3 grid((k_rates + TILE - 1) / TILE, c.g.n_chunks);
-    if (c.mode == MODE_HESS) col32_subset_st_kernel<MODE_HESS><<<grid, TILE, 0, s>>>(c, in, ws, rate_idx, k_rates);
-    else col32_subset_st_kernel<MODE_GRAD><<<grid, TILE, 0, s>>>(c, in, ws, rate_idx, k_rates);
+    if (c.mode == MODE_HESS) launch_pdl(col32_subset_st_kernel<MODE_HESS>, grid, TILE, 0, s, c, in, ws, rate_idx, k_rates);
+    else launch_pdl(col32_subset_st_kernel<MODE_GRAD>, grid, TILE, 0, s, c, in, ws, rate_idx, k_rates);
     return cudaGetLastError();
 }
 

@@ -30,6 +30,7 @@ namespace hk {
 constexpr int CB_THREADS = 256;
 
 __global__ void __launch_bounds__(CB_THREADS) combine_kernel(Consts c, Workspace ws) {
+    pdl_wait();
     const int i = c.t0 * TILE + blockIdx.x * CB_THREADS + threadIdx.x;
     if (i >= c.g.n || i >= c.t1 * TILE) return;
     const int npad = c.g.npad;
@@ -45,12 +46,13 @@ __global__ void __launch_bounds__(CB_THREADS) combine_kernel(Consts c, Workspace
 }
 
 cudaError_t launch_combine(const Consts &c, const Workspace &ws, cudaStream_t s) {
-    combine_kernel<<<((c.t1 - c.t0) * TILE + CB_THREADS - 1) / CB_THREADS, CB_THREADS, 0, s>>>(c, ws);
+    launch_pdl(combine_kernel, ((c.t1 - c.t0) * TILE + CB_THREADS - 1) / CB_THREADS, CB_THREADS, 0, s, c, ws);
     return cudaGetLastError();
 }
 
 
 __global__ void __launch_bounds__(TILE) epilogue_kernel(Consts c, Inputs in, Workspace ws) {
+    pdl_wait();
     const Derived &D = *c.d;
     __shared__ double sh[(TILE / 32) * NACC];
     __shared__ float shf[TILE];
@@ -85,22 +87,24 @@ __global__ void __launch_bounds__(TILE) epilogue_kernel(Consts c, Inputs in, Wor
 
 // FP32C: one block per target tile finishes its rows (rows_finish.cuh).
 __global__ void __launch_bounds__(TILE) finish_kernel(Consts c, Inputs in, Workspace ws) {
+    pdl_wait();
     finish_tile_fp32c(c, in, ws, c.t0 + blockIdx.x);
 }
 
 cudaError_t launch_finish(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s) {
-    finish_kernel<<<c.t1 - c.t0, TILE, 0, s>>>(c, in, ws);
+    launch_pdl(finish_kernel, c.t1 - c.t0, TILE, 0, s, c, in, ws);
     return cudaGetLastError();
 }
 
 cudaError_t launch_epilogue(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s) {
-    epilogue_kernel<<<c.t1 - c.t0, TILE, 0, s>>>(c, in, ws);
+    launch_pdl(epilogue_kernel, c.t1 - c.t0, TILE, 0, s, c, in, ws);
     return cudaGetLastError();
 }
 
 constexpr int FIN_THREADS = 256;
 
 __global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(Consts c, Workspace ws, Outputs out) {
+    pdl_wait();
     const Derived &D = *c.d;
     __shared__ double sh[(FIN_THREADS / 32) * NACC];
     __shared__ double tot[NACC];
@@ -171,11 +175,12 @@ __global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(Consts c, Workspa
 }
 
 cudaError_t launch_finalize(const Consts &c, const Workspace &ws, const Outputs &out, cudaStream_t s) {
-    finalize_kernel<<<1, FIN_THREADS, 0, s>>>(c, ws, out);
+    launch_pdl(finalize_kernel, 1, FIN_THREADS, 0, s, c, ws, out);
     return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(CB_THREADS) colfinish_kernel(Consts c, Workspace ws, Outputs out) {
+    pdl_wait();
     const int m = c.t0 * TILE + blockIdx.x * CB_THREADS + threadIdx.x;
     if (m >= c.g.n || m >= c.t1 * TILE) return;
     const int npad = c.g.npad;
@@ -203,6 +208,7 @@ __global__ void __launch_bounds__(CB_THREADS) colfinish_kernel(Consts c, Workspa
 __global__ void __launch_bounds__(CB_THREADS) colfinish_subset_kernel(Consts c, Workspace ws, Outputs out,
                                                                       const int *__restrict__ rate_idx, int k_rates,
                                                                       int by_position) {
+    pdl_wait();
     const int j = blockIdx.x * CB_THREADS + threadIdx.x;
     const int bits = ws.hdr[0];
     if (j == 0 && (bits & ST_BADPARAM)) *out.dev_status = HAWKES_EINVAL;
@@ -231,13 +237,13 @@ __global__ void __launch_bounds__(CB_THREADS) colfinish_subset_kernel(Consts c, 
 
 cudaError_t launch_colfinish_subset(const Consts &c, const Workspace &ws, const Outputs &out, const int *rate_idx,
                                     int k_rates, int by_position, cudaStream_t s) {
-    colfinish_subset_kernel<<<(k_rates + CB_THREADS - 1) / CB_THREADS, CB_THREADS, 0, s>>>(c, ws, out, rate_idx,
+    launch_pdl(colfinish_subset_kernel, (k_rates + CB_THREADS - 1) / CB_THREADS, CB_THREADS, 0, s, c, ws, out, rate_idx,
                                                                                            k_rates, by_position);
     return cudaGetLastError();
 }
 
 cudaError_t launch_colfinish(const Consts &c, const Workspace &ws, const Outputs &out, cudaStream_t s) {
-    colfinish_kernel<<<((c.t1 - c.t0) * TILE + CB_THREADS - 1) / CB_THREADS, CB_THREADS, 0, s>>>(c, ws, out);
+    launch_pdl(colfinish_kernel, ((c.t1 - c.t0) * TILE + CB_THREADS - 1) / CB_THREADS, CB_THREADS, 0, s, c, ws, out);
     return cudaGetLastError();
 }
 

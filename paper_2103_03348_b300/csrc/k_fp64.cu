@@ -14,6 +14,7 @@ namespace hk {
 
 template <int MODE>
 __global__ void __launch_bounds__(TILE) row64_kernel(Consts c, Workspace ws) {
+    pdl_wait();
     const Derived &D = *c.d;
     const int tile = c.t0 + blockIdx.x, chunk = blockIdx.y;
     const int i = tile * TILE + threadIdx.x;
@@ -51,9 +52,9 @@ __global__ void __launch_bounds__(TILE) row64_kernel(Consts c, Workspace ws) {
 
 cudaError_t launch_row64(const Consts &c, const Workspace &ws, cudaStream_t s) {
     const dim3 grid(c.t1 - c.t0, c.g.n_chunks);
-    if (c.mode == MODE_HESS) row64_kernel<MODE_HESS><<<grid, TILE, 0, s>>>(c, ws);
-    else if (c.mode == MODE_GRAD) row64_kernel<MODE_GRAD><<<grid, TILE, 0, s>>>(c, ws);
-    else row64_kernel<MODE_LL><<<grid, TILE, 0, s>>>(c, ws);
+    if (c.mode == MODE_HESS) launch_pdl(row64_kernel<MODE_HESS>, grid, TILE, 0, s, c, ws);
+    else if (c.mode == MODE_GRAD) launch_pdl(row64_kernel<MODE_GRAD>, grid, TILE, 0, s, c, ws);
+    else launch_pdl(row64_kernel<MODE_LL>, grid, TILE, 0, s, c, ws);
     return cudaGetLastError();
 }
 
@@ -61,6 +62,7 @@ cudaError_t launch_row64(const Consts &c, const Workspace &ws, cudaStream_t s) {
 // the weight kept in the log domain so that a tiny lambda_n cannot overflow it.
 template <int MODE>
 __global__ void __launch_bounds__(TILE) col64_kernel(Consts c, Workspace ws) {
+    pdl_wait();
     const Derived &D = *c.d;
     const int tile = c.t0 + blockIdx.x, chunk = blockIdx.y;
     const int m = tile * TILE + threadIdx.x;
@@ -99,8 +101,8 @@ __global__ void __launch_bounds__(TILE) col64_kernel(Consts c, Workspace ws) {
 
 cudaError_t launch_col64(const Consts &c, const Workspace &ws, cudaStream_t s) {
     const dim3 grid(c.t1 - c.t0, c.g.n_chunks);
-    if (c.mode == MODE_HESS) col64_kernel<MODE_HESS><<<grid, TILE, 0, s>>>(c, ws);
-    else col64_kernel<MODE_GRAD><<<grid, TILE, 0, s>>>(c, ws);
+    if (c.mode == MODE_HESS) launch_pdl(col64_kernel<MODE_HESS>, grid, TILE, 0, s, c, ws);
+    else launch_pdl(col64_kernel<MODE_GRAD>, grid, TILE, 0, s, c, ws);
     return cudaGetLastError();
 }
 

@@ -23,6 +23,7 @@ constexpr int MV_THREADS = 256;  // 8 warps, one matrix row per warp
 // w = P r_S (row-major M x M, FP64): one warp per row, lanes stride the columns.
 __global__ void __launch_bounds__(MV_THREADS) prec_matvec_kernel(int64_t m, const double *__restrict__ prec,
                                                                  const double *__restrict__ rs, double *__restrict__ w) {
+    pdl_wait();
     const int warp = (blockIdx.x * MV_THREADS + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= m) return;
@@ -44,6 +45,7 @@ __global__ void __launch_bounds__(ASM_THREADS) posterior_assemble_kernel(
     const double *__restrict__ q, const double *__restrict__ w, const double *__restrict__ loglik,
     const double *__restrict__ grad, const double *__restrict__ hdiag, double *__restrict__ logpost,
     double *__restrict__ grad_q, double *__restrict__ hdiag_q) {
+    pdl_wait();
     __shared__ double sh[ASM_THREADS];
     __shared__ double s_lp[6];
     __shared__ int s_ok[6];
@@ -92,6 +94,7 @@ __global__ void __launch_bounds__(ASM_THREADS) posterior_assemble_kernel(
 // r[seq[j]] = q[6 + j]: the sampler's log-rates into the likelihood's full vector.
 __global__ void scatter_rates_kernel(int64_t m, const int *__restrict__ seq, const double *__restrict__ q,
                                      double *__restrict__ r) {
+    pdl_wait();
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
         r[seq[j]] = q[6 + j];
 }
@@ -101,6 +104,7 @@ __global__ void scatter_rates_kernel(int64_t m, const int *__restrict__ seq, con
 __global__ void scatter_rates_trend_kernel(int64_t m, int k, const int *__restrict__ seq,
                                            const double *__restrict__ F, const double *__restrict__ q,
                                            double *__restrict__ r) {
+    pdl_wait();
     const double *beta = q + 6 + m;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
         double v = q[6 + j];
@@ -117,6 +121,7 @@ __global__ void __launch_bounds__(ASM_THREADS) trend_assemble_kernel(
     int64_t m, int k, const int *__restrict__ seq, const double *__restrict__ F, double beta_var,
     const double *__restrict__ q, const double *__restrict__ grad, const double *__restrict__ hdiag,
     double *__restrict__ logpost, double *__restrict__ grad_q, double *__restrict__ hdiag_q) {
+    pdl_wait();
     __shared__ double sh[ASM_THREADS];
     const int c = blockIdx.x;
     const double *beta = q + 6 + m;
@@ -141,6 +146,7 @@ __global__ void __launch_bounds__(ASM_THREADS) trend_assemble_kernel(
 
 // p += a g
 __global__ void momentum_kernel(int64_t k, double *__restrict__ p, const double *__restrict__ g, double a) {
+    pdl_wait();
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < k; j += (int64_t)gridDim.x * blockDim.x)
         p[j] += a * g[j];
 }
@@ -148,6 +154,7 @@ __global__ void momentum_kernel(int64_t k, double *__restrict__ p, const double 
 // q += eps minv p
 __global__ void position_kernel(int64_t k, double *__restrict__ q, const double *__restrict__ p,
                                 const double *__restrict__ minv, double eps) {
+    pdl_wait();
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < k; j += (int64_t)gridDim.x * blockDim.x)
         q[j] += eps * minv[j] * p[j];
 }
@@ -155,6 +162,7 @@ __global__ void position_kernel(int64_t k, double *__restrict__ q, const double 
 // out = 1/2 sum_j minv_j p_j^2 (single block, fixed order)
 __global__ void __launch_bounds__(ASM_THREADS) kinetic_kernel(int64_t k, const double *__restrict__ p,
                                                               const double *__restrict__ minv, double *__restrict__ out) {
+    pdl_wait();
     __shared__ double sh[ASM_THREADS];
     double s = 0.0;
     for (int64_t j = threadIdx.x; j < k; j += ASM_THREADS) s += minv[j] * p[j] * p[j];
@@ -204,10 +212,10 @@ int hawkes_posterior(int64_t n, int64_t m, const int *seq_idx, const double *pre
     const double *rs = q + 6;
     if (m > 0) {
         const int blocks = (int)((m * 32 + hk::MV_THREADS - 1) / hk::MV_THREADS);
-        hk::prec_matvec_kernel<<<blocks, hk::MV_THREADS, 0, s>>>(m, prec, rs, w);
+        launch_pdl(hk::prec_matvec_kernel, blocks, hk::MV_THREADS, 0, s, m, prec, rs, w);
         if (cudaGetLastError() != cudaSuccess) return HAWKES_ECUDA;
     }
-    hk::posterior_assemble_kernel<<<1, hk::ASM_THREADS, 0, s>>>(m, pc, seq_idx, prec, m + 1, q, w, loglik, grad,
+    launch_pdl(hk::posterior_assemble_kernel, 1, hk::ASM_THREADS, 0, s, m, pc, seq_idx, prec, m + 1, q, w, loglik, grad,
                                                                 hdiag, logpost, grad_q, hdiag_q);
     return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
 }
@@ -233,7 +241,7 @@ int hawkes_posterior_tree(int64_t n, int64_t m, const int *seq_idx, const int *p
     if (hk::launch_tree_prior(m, plan, length, root_var, sigma2, q + 6, scratch, nullptr, w, hdiag ? pd : nullptr,
                               s) != cudaSuccess)
         return HAWKES_ECUDA;
-    hk::posterior_assemble_kernel<<<1, hk::ASM_THREADS, 0, s>>>(m, pc, seq_idx, pd, 1, q, w, loglik, grad, hdiag,
+    launch_pdl(hk::posterior_assemble_kernel, 1, hk::ASM_THREADS, 0, s, m, pc, seq_idx, pd, 1, q, w, loglik, grad, hdiag,
                                                                 logpost, grad_q, hdiag_q);
     return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
 }
@@ -245,7 +253,7 @@ int hawkes_posterior_assemble(int64_t n, int64_t m, const int *seq_idx, const do
     const int rc = post_check(n, m, prior, q, loglik, grad, hdiag, logpost, grad_q, hdiag_q, &pc);
     if (rc != HAWKES_OK) return rc;
     if (m > 0 && (!seq_idx || !pz || (hdiag && !pdiag))) return HAWKES_EINVAL;
-    hk::posterior_assemble_kernel<<<1, hk::ASM_THREADS, 0, (cudaStream_t)stream>>>(
+    launch_pdl(hk::posterior_assemble_kernel, 1, hk::ASM_THREADS, 0, (cudaStream_t)stream,
         m, pc, seq_idx, pdiag, 1, q, pz, loglik, grad, hdiag, logpost, grad_q, hdiag_q);
     return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
 }
@@ -254,7 +262,7 @@ int hawkes_hmc_scatter_rates_trend(int64_t m, int k, const int *seq_idx, const d
                                    void *stream) {
     if (m < 0 || k < 0 || (m > 0 && (!seq_idx || !q || !r)) || (m > 0 && k > 0 && !F)) return HAWKES_EINVAL;
     if (m == 0) return HAWKES_OK;
-    hk::scatter_rates_trend_kernel<<<hk::grid_for(m), 256, 0, (cudaStream_t)stream>>>(m, k, seq_idx, F, q, r);
+    launch_pdl(hk::scatter_rates_trend_kernel, hk::grid_for(m), 256, 0, (cudaStream_t)stream, m, k, seq_idx, F, q, r);
     return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
 }
 
@@ -266,7 +274,7 @@ int hawkes_posterior_add_trend(int64_t m, int k, const int *seq_idx, const doubl
     if ((grad == nullptr) != (grad_q == nullptr) || (hdiag == nullptr) != (hdiag_q == nullptr)) return HAWKES_EINVAL;
     if (hdiag && !grad) return HAWKES_EINVAL;
     if (k == 0) return HAWKES_OK;
-    hk::trend_assemble_kernel<<<k, hk::ASM_THREADS, 0, (cudaStream_t)stream>>>(m, k, seq_idx, F, beta_var, q, grad,
+    launch_pdl(hk::trend_assemble_kernel, k, hk::ASM_THREADS, 0, (cudaStream_t)stream, m, k, seq_idx, F, beta_var, q, grad,
                                                                                hdiag, logpost, grad_q, hdiag_q);
     return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
 }
@@ -274,25 +282,25 @@ int hawkes_posterior_add_trend(int64_t m, int k, const int *seq_idx, const doubl
 int hawkes_hmc_scatter_rates(int64_t m, const int *seq_idx, const double *q, double *r, void *stream) {
     if (m < 0 || (m > 0 && (!seq_idx || !q || !r))) return HAWKES_EINVAL;
     if (m == 0) return HAWKES_OK;
-    hk::scatter_rates_kernel<<<hk::grid_for(m), 256, 0, (cudaStream_t)stream>>>(m, seq_idx, q, r);
+    launch_pdl(hk::scatter_rates_kernel, hk::grid_for(m), 256, 0, (cudaStream_t)stream, m, seq_idx, q, r);
     return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
 }
 
 int hawkes_hmc_momentum(int64_t k, double *p, const double *g, double a, void *stream) {
     if (k < 1 || !p || !g) return HAWKES_EINVAL;
-    hk::momentum_kernel<<<hk::grid_for(k), 256, 0, (cudaStream_t)stream>>>(k, p, g, a);
+    launch_pdl(hk::momentum_kernel, hk::grid_for(k), 256, 0, (cudaStream_t)stream, k, p, g, a);
     return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
 }
 
 int hawkes_hmc_position(int64_t k, double *q, const double *p, const double *minv, double eps, void *stream) {
     if (k < 1 || !q || !p || !minv) return HAWKES_EINVAL;
-    hk::position_kernel<<<hk::grid_for(k), 256, 0, (cudaStream_t)stream>>>(k, q, p, minv, eps);
+    launch_pdl(hk::position_kernel, hk::grid_for(k), 256, 0, (cudaStream_t)stream, k, q, p, minv, eps);
     return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
 }
 
 int hawkes_hmc_kinetic(int64_t k, const double *p, const double *minv, double *out, void *stream) {
     if (k < 1 || !p || !minv || !out) return HAWKES_EINVAL;
-    hk::kinetic_kernel<<<1, hk::ASM_THREADS, 0, (cudaStream_t)stream>>>(k, p, minv, out);
+    launch_pdl(hk::kinetic_kernel, 1, hk::ASM_THREADS, 0, (cudaStream_t)stream, k, p, minv, out);
     return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
 }
 

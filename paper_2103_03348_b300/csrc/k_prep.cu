@@ -38,6 +38,7 @@ __device__ __forceinline__ uint64_t mix64(uint64_t k) {
 }
 
 __global__ void __launch_bounds__(TILE) prep_kernel(Consts c, Inputs in, Workspace ws) {
+    pdl_wait();
     const int n = c.g.n;
     const int i = blockIdx.x * TILE + threadIdx.x;
     __shared__ double sh[TILE];
@@ -162,6 +163,7 @@ __global__ void __launch_bounds__(TILE) prep_kernel(Consts c, Inputs in, Workspa
 }
 
 __global__ void __launch_bounds__(TILE) pack_kernel(Consts c, Inputs in, Workspace ws, const double *r_time_order) {
+    pdl_wait();
     const Derived &D = *c.d;
     const int n = c.g.n;
     const int i = blockIdx.x * TILE + threadIdx.x;
@@ -301,6 +303,7 @@ constexpr int ORDER_THREADS = 1024;
 // One block per slab: keys (Morton code << 32 | slot) sorted ascending in
 // shared memory by a bitonic network; unique keys make the order deterministic.
 __global__ void __launch_bounds__(ORDER_THREADS) order_sort_kernel(Consts c, Inputs in, Workspace ws) {
+    pdl_wait();
     __shared__ unsigned long long keys[SLAB_EVENTS];
     const int n = c.g.n;
     const int e0 = blockIdx.x * SLAB_EVENTS;
@@ -339,6 +342,7 @@ __global__ void __launch_bounds__(ORDER_THREADS) order_sort_kernel(Consts c, Inp
 
 // Position-order copies of the events and of prep's per-event indices.
 __global__ void __launch_bounds__(TILE) order_gather_kernel(Consts c, Inputs in, Workspace ws) {
+    pdl_wait();
     const int n = c.g.n;
     const int k = blockIdx.x * TILE + threadIdx.x;  // < npad
     if (k < n) {
@@ -362,21 +366,21 @@ __global__ void __launch_bounds__(TILE) order_gather_kernel(Consts c, Inputs in,
 }
 
 cudaError_t launch_prep(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s) {
-    prep_kernel<<<c.g.tiles, TILE, 0, s>>>(c, in, ws);
+    launch_pdl(prep_kernel, c.g.tiles, TILE, 0, s, c, in, ws);
     return cudaGetLastError();
 }
 
 cudaError_t launch_order(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s) {
     const int slabs = (c.g.n + SLAB_EVENTS - 1) / SLAB_EVENTS;
-    order_sort_kernel<<<slabs, ORDER_THREADS, 0, s>>>(c, in, ws);
+    launch_pdl(order_sort_kernel, slabs, ORDER_THREADS, 0, s, c, in, ws);
     if (cudaGetLastError() != cudaSuccess) return cudaErrorLaunchFailure;
-    order_gather_kernel<<<c.g.tiles, TILE, 0, s>>>(c, in, ws);
+    launch_pdl(order_gather_kernel, c.g.tiles, TILE, 0, s, c, in, ws);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pack(const Consts &c, const Inputs &in, const Workspace &ws, const double *r_time_order,
                         cudaStream_t s) {
-    pack_kernel<<<c.g.tiles, TILE, 0, s>>>(c, in, ws, r_time_order);
+    launch_pdl(pack_kernel, c.g.tiles, TILE, 0, s, c, in, ws, r_time_order);
     return cudaGetLastError();
 }
 

@@ -33,6 +33,7 @@ namespace hk {
 
 template <int MODE, bool BAND>
 __global__ void __launch_bounds__(TILE, 4) row32_kernel(Consts c, Inputs in, Workspace ws) {
+    pdl_wait();
     const Derived &D = *c.d;
     // Chunk order: blocks are dispatched y-major, so y = 0 takes the chunk that
     // holds the tile itself, y = 1 the chunk before it, and so on, wrapping to
@@ -127,13 +128,13 @@ cudaError_t launch_row32(const Consts &c, const Inputs &in, const Workspace &ws,
     const dim3 grid(c.t1 - c.t0, c.g.n_chunks);
     if (c.st) return launch_row32_st(c, in, ws, s);
     if (c.band) {
-        if (c.mode == MODE_HESS) row32_kernel<MODE_HESS, true><<<grid, TILE, 0, s>>>(c, in, ws);
-        else if (c.mode == MODE_GRAD) row32_kernel<MODE_GRAD, true><<<grid, TILE, 0, s>>>(c, in, ws);
-        else row32_kernel<MODE_LL, true><<<grid, TILE, 0, s>>>(c, in, ws);
+        if (c.mode == MODE_HESS) launch_pdl(row32_kernel<MODE_HESS, true>, grid, TILE, 0, s, c, in, ws);
+        else if (c.mode == MODE_GRAD) launch_pdl(row32_kernel<MODE_GRAD, true>, grid, TILE, 0, s, c, in, ws);
+        else launch_pdl(row32_kernel<MODE_LL, true>, grid, TILE, 0, s, c, in, ws);
     } else {
-        if (c.mode == MODE_HESS) row32_kernel<MODE_HESS, false><<<grid, TILE, 0, s>>>(c, in, ws);
-        else if (c.mode == MODE_GRAD) row32_kernel<MODE_GRAD, false><<<grid, TILE, 0, s>>>(c, in, ws);
-        else row32_kernel<MODE_LL, false><<<grid, TILE, 0, s>>>(c, in, ws);
+        if (c.mode == MODE_HESS) launch_pdl(row32_kernel<MODE_HESS, false>, grid, TILE, 0, s, c, in, ws);
+        else if (c.mode == MODE_GRAD) launch_pdl(row32_kernel<MODE_GRAD, false>, grid, TILE, 0, s, c, in, ws);
+        else launch_pdl(row32_kernel<MODE_LL, false>, grid, TILE, 0, s, c, in, ws);
     }
     return cudaGetLastError();
 }

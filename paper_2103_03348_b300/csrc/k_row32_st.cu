@@ -18,6 +18,7 @@ constexpr int GPT = TILE / GROUP;  // groups per tile
 
 template <int MODE>
 __global__ void __launch_bounds__(TILE, 4) row32_st_kernel(Consts c, Inputs in, Workspace ws) {
+    pdl_wait();
     const Derived &D = *c.d;
     const int tile = c.t0 + blockIdx.x;
     const int chunk = (tile / c.g.chunk_tiles - (int)blockIdx.y + c.g.n_chunks) % c.g.n_chunks;
@@ -143,9 +144,9 @@ __global__ void __launch_bounds__(TILE, 4) row32_st_kernel(Consts c, Inputs in, 
 
 cudaError_t launch_row32_st(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s) {
     const dim3 grid(c.t1 - c.t0, c.g.n_chunks);
-    if (c.mode == MODE_HESS) row32_st_kernel<MODE_HESS><<<grid, TILE, 0, s>>>(c, in, ws);
-    else if (c.mode == MODE_GRAD) row32_st_kernel<MODE_GRAD><<<grid, TILE, 0, s>>>(c, in, ws);
-    else row32_st_kernel<MODE_LL><<<grid, TILE, 0, s>>>(c, in, ws);
+    if (c.mode == MODE_HESS) launch_pdl(row32_st_kernel<MODE_HESS>, grid, TILE, 0, s, c, in, ws);
+    else if (c.mode == MODE_GRAD) launch_pdl(row32_st_kernel<MODE_GRAD>, grid, TILE, 0, s, c, in, ws);
+    else launch_pdl(row32_st_kernel<MODE_LL>, grid, TILE, 0, s, c, in, ws);
     return cudaGetLastError();
 }
 

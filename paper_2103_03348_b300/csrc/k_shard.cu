@@ -27,6 +27,7 @@ __device__ __forceinline__ float bits_float(double v) { return __uint_as_float((
 
 // one block per owned tile
 __global__ void __launch_bounds__(TILE) shard_export_kernel(Consts c, Workspace ws, double *__restrict__ xbuf) {
+    pdl_wait();
     const int tile = c.t0 + blockIdx.x;
     double *rec = xbuf + (size_t)tile * XREC_DOUBLES;
     const int i = tile * TILE + threadIdx.x;
@@ -43,6 +44,7 @@ __global__ void __launch_bounds__(TILE) shard_export_kernel(Consts c, Workspace 
 
 // one block per tile of the whole problem
 __global__ void __launch_bounds__(TILE) shard_import_kernel(Consts c, Workspace ws, const double *__restrict__ xbuf) {
+    pdl_wait();
     const int tile = blockIdx.x;
     const double *rec = xbuf + (size_t)tile * XREC_DOUBLES;
     const int i = tile * TILE + threadIdx.x;
@@ -68,12 +70,12 @@ __global__ void __launch_bounds__(TILE) shard_import_kernel(Consts c, Workspace 
 
 cudaError_t launch_shard_export(const Consts &c, const Workspace &ws, double *xbuf, cudaStream_t s) {
     if (c.t1 <= c.t0) return cudaSuccess;
-    shard_export_kernel<<<c.t1 - c.t0, TILE, 0, s>>>(c, ws, xbuf);
+    launch_pdl(shard_export_kernel, c.t1 - c.t0, TILE, 0, s, c, ws, xbuf);
     return cudaGetLastError();
 }
 
 cudaError_t launch_shard_import(const Consts &c, const Workspace &ws, const double *xbuf, cudaStream_t s) {
-    shard_import_kernel<<<c.g.tiles, TILE, 0, s>>>(c, ws, xbuf);
+    launch_pdl(shard_import_kernel, c.g.tiles, TILE, 0, s, c, ws, xbuf);
     return cudaGetLastError();
 }
 

@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(TREE_THREADS)
     tree_prior_kernel(int64_t m_arg, const int *__restrict__ plan, const double *__restrict__ len_g, double tau0,
                       double sigma2, const double *__restrict__ z, double *mu, double *dl, double *gb, double *dd,
                       double *is, double *__restrict__ logdens, double *__restrict__ pz, double *__restrict__ pdiag) {
+    pdl_wait();
     extern __shared__ __align__(16) unsigned char tree_smem[];
     __shared__ double sh[TREE_THREADS];
     TreePlan T = tree_plan_view(plan);
@@ -187,10 +188,10 @@ cudaError_t launch_tree_prior(int64_t m, const int *plan, const double *len, dou
             if (e != cudaSuccess) return e;
             if (dev >= 0 && dev < 64) attr_set[dev] = 1;
         }
-        tree_prior_kernel<true><<<1, TREE_THREADS, bytes, s>>>(m, plan, len, tau0, sigma2, z, mu, dl, gb, dd, is,
+        launch_pdl(tree_prior_kernel<true>, 1, TREE_THREADS, bytes, s, m, plan, len, tau0, sigma2, z, mu, dl, gb, dd, is,
                                                                logdens, pz, pdiag);
     } else {
-        tree_prior_kernel<false><<<1, TREE_THREADS, 0, s>>>(m, plan, len, tau0, sigma2, z, mu, dl, gb, dd, is,
+        launch_pdl(tree_prior_kernel<false>, 1, TREE_THREADS, 0, s, m, plan, len, tau0, sigma2, z, mu, dl, gb, dd, is,
                                                             logdens, pz, pdiag);
     }
     return cudaGetLastError();
