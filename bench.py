@@ -241,8 +241,10 @@ def run_ours(args, rank, world, local_rank):
            "status": torch.empty((), dtype=torch.int32, device=dev)}
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]  # step start/end, row start/end, col start/end
 
+    prec = args.kernel_precision  # fp32c unless a --kernel-only profiling run asks for another
+
     def step(timed=True):
-        hawkes._call("hess", x, y, t, r, w.params, "fp32c", stream=stream, check=False, out=out,
+        hawkes._call("hess", x, y, t, r, w.params, prec, stream=stream, check=False, out=out,
                      phase_events=ev[2:6] if timed else None)
 
     from paper_2103_03348_b300 import replicas
@@ -281,7 +283,7 @@ def run_ours(args, rank, world, local_rank):
 
     if args.kernel_only:
         if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms,
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms, "precision": prec,
                               "row_ms": float(np.mean(row_ms)), "col_ms": float(np.mean(col_ms)),
                               "steps": args.steps, "warmup": args.warmup, "kernel_only": True}), flush=True)
         return 0
@@ -445,9 +447,13 @@ def main():
     ap.add_argument("--hmc-warmup", type=int, default=100)
     ap.add_argument("--kernel-only", action="store_true",
                     help="time the resident-input steps only (no e2e, FP64 path or CPU baseline); for profilers")
+    ap.add_argument("--kernel-precision", default="fp32c", choices=["fp32c", "fp32c_band", "fp32c_st"],
+                    help="with --kernel-only: the precision of the timed step (to profile the other FP32C forms)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
+    if args.kernel_precision != "fp32c" and not args.kernel_only:
+        ap.error("--kernel-precision applies to --kernel-only runs")
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
