@@ -186,25 +186,62 @@ __device__ __forceinline__ void finish_tile_fp32c(const Consts &c, const Inputs 
     if (tiny) ftiny[off + __popc(bal & ((1u << lane) - 1u))] = threadIdx.x;
     __syncthreads();
     if (ntiny > 0) {
+        // One warp per listed row.  A term more than 2^80 below the row's largest
+        // term of its kind cannot change the FP64 sum, so an FP32 pass over the
+        // packed sources first finds the largest background and excitation
+        // exponents (base 2, as the row pass forms them); the FP64 pass then
+        // evaluates only the terms within 2^80 of them.  (FP32 exponents are off
+        // by far less than 80 units, and FP64 coordinates keep the kept terms
+        // exact where FP32 ones would cost a far pair its relative accuracy.)
+        __shared__ double fmom[TILE][NMOM];
         const double sx2 = D.sx * D.sx, st = D.st, st2 = D.st * D.st;
         // raw units -> FP32C scaled units
         const double scale[NMOM] = {1.0, sx2, st2, sx2 * sx2, st2 * st2, 1.0, st, st2, sx2, sx2 * sx2};
-        for (int q = 0; q < ntiny; ++q) {
+        const float *f = reinterpret_cast<const float *>(ws.src32);
+        const float cbt = D.cbt, hh = D.hh;
+        constexpr float KEEP = 80.0f;
+        for (int q = warp; q < ntiny; q += TILE / 32) {
             const int owner = ftiny[q], row = tile * TILE + owner;
-            const double xn = in.x[row], yn = in.y[row], tn = in.t[row];
+            const int pr = row >> 1, lr = row & 1;
+            const float xn = -f[8 * pr + lr], yn = -f[8 * pr + 2 + lr], tn = -f[8 * pr + 4 + lr];
             const int locn = ws.loc[row], gn = ws.gidx[row];
+            float mg = -INFINITY, me = -INFINITY;
+            for (int j = lane; j < n; j += 32) {
+                const int p = j >> 1, l = j & 1;
+                const float dx = xn + f[8 * p + l], dy = yn + f[8 * p + 2 + l], dt = tn + f[8 * p + 4 + l];
+                const float d2 = dx * dx + dy * dy;
+                if (ws.loc[j] != locn) mg = fmaxf(mg, -(d2 + cbt * dt * dt));
+                // FP32C_ST: the causal test compares time-order ranks
+                if ((c.st ? ws.perm[j] : j) < gn) me = fmaxf(me, f[8 * p + 6 + l] - tn - hh * d2);
+            }
+            mg = warp_maxf(mg);
+            me = warp_maxf(me);
+            const double xn64 = in.x[row], yn64 = in.y[row], tn64 = in.t[row];
             double a[NMOM];
 #pragma unroll
             for (int k = 0; k < NMOM; ++k) a[k] = 0.0;
-            // FP32C_ST: the causal test compares time-order ranks
-            for (int j = threadIdx.x; j < n; j += TILE)
-                accumulate64<MODE_HESS>(a, in.x[j], in.y[j], in.t[j], in.r[j], ws.loc[j] != locn,
-                                        (c.st ? ws.perm[j] : j) < gn, xn, yn, tn, D);
+            for (int j = lane; j < n; j += 32) {
+                const int p = j >> 1, l = j & 1;
+                const float dx = xn + f[8 * p + l], dy = yn + f[8 * p + 2 + l], dt = tn + f[8 * p + 4 + l];
+                const float d2 = dx * dx + dy * dy;
+                const bool bg_on = ws.loc[j] != locn && -(d2 + cbt * dt * dt) > mg - KEEP;
+                const bool ex_on = (c.st ? ws.perm[j] : j) < gn && f[8 * p + 6 + l] - tn - hh * d2 > me - KEEP;
+                if (bg_on || ex_on)
+                    accumulate64<MODE_HESS>(a, in.x[j], in.y[j], in.t[j], in.r[j], bg_on, ex_on, xn64, yn64, tn64, D);
+            }
+            // warp sums (a fixed butterfly: every lane holds the same total)
 #pragma unroll
             for (int k = 0; k < NMOM; ++k) {
-                const double v = block_sum<TILE>(a[k], fsh);
-                if (threadIdx.x == owner) Mo[k] = v * scale[k];
+                double v = a[k];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) fmom[owner][k] = v * scale[k];
             }
+        }
+        __syncthreads();
+        if (tiny) {
+#pragma unroll
+            for (int k = 0; k < NMOM; ++k) Mo[k] = fmom[threadIdx.x][k];
         }
     }
     double acc[NACC];

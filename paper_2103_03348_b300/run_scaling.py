@@ -5,7 +5,8 @@
 Workload: the hotspot pattern of the 100,000-event benchmark (2,000 x 2,000 km,
 1,500 days, 556 hotspots, log-rates N(0, 0.25)) drawn at each size, so the
 density grows with N.  For each size: loglik, loglik + gradient, and loglik +
-gradient + Hessian diagonal in FP32C, the last also with exact band skipping
+gradient + Hessian diagonal in FP32C, the last also with exact band skipping, on
+space-time tiles
 and, up to 50,000 events, in FP64.  CUDA events around each call, L2 flushed
 between calls, median of `reps`.  One JSON line per size.
 """
@@ -46,7 +47,7 @@ def run(sizes=(10_000, 25_000, 50_000, 100_000, 250_000, 500_000, 1_000_000), re
         x, y, t, r = d(w.x), d(w.y), d(w.t), d(w.r)
         pairs = n * (n - 1)
         res = {"n": n, "pairs": pairs}
-        cases = [("loglik", "fp32c"), ("grad", "fp32c"), ("hess", "fp32c"), ("hess", "fp32c_band")]
+        cases = [("loglik", "fp32c"), ("grad", "fp32c"), ("hess", "fp32c"), ("hess", "fp32c_band"), ("hess", "fp32c_st")]
         if n <= 50_000:
             cases.append(("hess", "fp64"))
         for mode, prec in cases:
