@@ -17,10 +17,12 @@ namespace hk {
 // tie-group starts.
 constexpr int CGPT = TILE / GROUP;
 
+constexpr int CSTAGE = 4;  // listed target tiles staged per barrier (double-buffered)
+
 struct ColShared {
-    float4 ab[2][TILE];
-    int gi[2][TILE];
-    GroupStat gs[2][CGPT];
+    float4 ab[2][CSTAGE][TILE];
+    int gi[2][CSTAGE][TILE];
+    GroupStat gs[2][CSTAGE][CGPT];
     int list[TILE];
     int cnt[CGPT];
 };
@@ -57,33 +59,42 @@ __device__ __forceinline__ void col_sweep_st(const Workspace &ws, int ub, int ue
         }
         if (live) sh.list[off + __popc(bal & ((1u << lane) - 1u))] = u;
         __syncthreads();
-        for (int q = 0; q < total; ++q) {
-            const int uu = sh.list[q];
-            const size_t u0 = (size_t)uu * TILE;
-            sh.ab[buf][threadIdx.x] = ws.tgt32[u0 + threadIdx.x];
-            sh.gi[buf][threadIdx.x] = ws.gidx[u0 + threadIdx.x];
-            if (threadIdx.x < CGPT) sh.gs[buf][threadIdx.x] = ws.grp[(size_t)uu * CGPT + threadIdx.x];
-            __syncthreads();
-            const int cnt = ws.tinfo[uu].w;
-#pragma unroll 1
-            for (int g = 0; g < CGPT; ++g) {
-                const int cntg = min(max(cnt - g * GROUP, 0), GROUP);
-                if (cntg == 0) continue;
-                const GroupStat G = sh.gs[buf][g];
-                if (w_empty || !col_alive(W, G, hh)) continue;  // warp-uniform
-                const int np = (cntg + 1) >> 1;
-                if (W.ix.w < G.ix.x)  // every source precedes every target
-                    col_tile<MODE, false>(sh.ab[buf] + g * GROUP, sh.gi[buf] + g * GROUP, np, xm, ym, rm, rank, nhh2,
-                                          run1, run2);
-                else
-                    col_tile<MODE, true>(sh.ab[buf] + g * GROUP, sh.gi[buf] + g * GROUP, np, xm, ym, rm, rank, nhh2,
-                                         run1, run2);
+        for (int q0 = 0; q0 < total; q0 += CSTAGE) {
+            const int nst = min(CSTAGE, total - q0);
+#pragma unroll
+            for (int kk = 0; kk < CSTAGE; ++kk) {
+                if (kk < nst) {
+                    const int uu = sh.list[q0 + kk];
+                    const size_t u0 = (size_t)uu * TILE;
+                    sh.ab[buf][kk][threadIdx.x] = ws.tgt32[u0 + threadIdx.x];
+                    sh.gi[buf][kk][threadIdx.x] = ws.gidx[u0 + threadIdx.x];
+                    if (threadIdx.x < CGPT) sh.gs[buf][kk][threadIdx.x] = ws.grp[(size_t)uu * CGPT + threadIdx.x];
+                }
             }
-            kahan(s1, k1, __fadd_rn(run1.x, run1.y));
-            run1 = make_float2(0.f, 0.f);
-            if (MODE == MODE_HESS) {
-                kahan(s2, k2, __fadd_rn(run2.x, run2.y));
-                run2 = make_float2(0.f, 0.f);
+            __syncthreads();
+#pragma unroll 1
+            for (int kk = 0; kk < nst; ++kk) {
+                const int cnt = ws.tinfo[sh.list[q0 + kk]].w;
+#pragma unroll 1
+                for (int g = 0; g < CGPT; ++g) {
+                    const int cntg = min(max(cnt - g * GROUP, 0), GROUP);
+                    if (cntg == 0) continue;
+                    const GroupStat G = sh.gs[buf][kk][g];
+                    if (w_empty || !col_alive(W, G, hh)) continue;  // warp-uniform
+                    const int np = (cntg + 1) >> 1;
+                    const float4 *ab = sh.ab[buf][kk] + g * GROUP;
+                    const int *gi = sh.gi[buf][kk] + g * GROUP;
+                    if (W.ix.w < G.ix.x)  // every source precedes every target
+                        col_tile<MODE, false>(ab, gi, np, xm, ym, rm, rank, nhh2, run1, run2);
+                    else
+                        col_tile<MODE, true>(ab, gi, np, xm, ym, rm, rank, nhh2, run1, run2);
+                }
+                kahan(s1, k1, __fadd_rn(run1.x, run1.y));
+                run1 = make_float2(0.f, 0.f);
+                if (MODE == MODE_HESS) {
+                    kahan(s2, k2, __fadd_rn(run2.x, run2.y));
+                    run2 = make_float2(0.f, 0.f);
+                }
             }
             buf ^= 1;
         }

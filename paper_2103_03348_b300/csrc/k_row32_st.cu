@@ -15,6 +15,7 @@ namespace hk {
 // the group statistics).  Pair arithmetic, masks and compensation are those
 // of row32_kernel; the causal mask compares time-order ranks.
 constexpr int GPT = TILE / GROUP;  // groups per tile
+constexpr int STAGE = 4;           // listed source tiles staged per barrier
 
 template <int MODE>
 __global__ void __launch_bounds__(TILE, 4) row32_st_kernel(Consts c, Inputs in, Workspace ws) {
@@ -25,10 +26,12 @@ __global__ void __launch_bounds__(TILE, 4) row32_st_kernel(Consts c, Inputs in, 
     const int i = tile * TILE + threadIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int npad = c.g.npad;
-    __shared__ float4 sAB[2][TILE];
-    __shared__ int sLoc[2][TILE];
-    __shared__ int sRank[2][TILE];
-    __shared__ GroupStat sGS[2][GPT];
+    // STAGE listed tiles per barrier (double-buffered), so that the warps' unequal
+    // numbers of live groups even out over more work between barriers
+    __shared__ float4 sAB[2][STAGE][TILE];
+    __shared__ int sLoc[2][STAGE][TILE];
+    __shared__ int sRank[2][STAGE][TILE];
+    __shared__ GroupStat sGS[2][STAGE][GPT];
     __shared__ int sList[TILE];
     __shared__ int sFlag[TILE];
     __shared__ int sCnt[GPT];
@@ -86,29 +89,38 @@ __global__ void __launch_bounds__(TILE, 4) row32_st_kernel(Consts c, Inputs in, 
             sFlag[pos] = flag;
         }
         __syncthreads();
-        for (int q = 0; q < total; ++q) {
-            const int su = sList[q], fl = sFlag[q];
-            const size_t s0 = (size_t)su * TILE;
-            sAB[buf][threadIdx.x] = ws.src32[s0 + threadIdx.x];
-            sLoc[buf][threadIdx.x] = ws.loc[s0 + threadIdx.x];
-            sRank[buf][threadIdx.x] = ws.perm[s0 + threadIdx.x];
-            if (threadIdx.x < GPT) sGS[buf][threadIdx.x] = ws.grp[(size_t)su * GPT + threadIdx.x];
+        for (int q0 = 0; q0 < total; q0 += STAGE) {
+            const int nst = min(STAGE, total - q0);
+#pragma unroll
+            for (int kk = 0; kk < STAGE; ++kk) {
+                if (kk < nst) {
+                    const int su = sList[q0 + kk];
+                    const size_t s0 = (size_t)su * TILE;
+                    sAB[buf][kk][threadIdx.x] = ws.src32[s0 + threadIdx.x];
+                    sLoc[buf][kk][threadIdx.x] = ws.loc[s0 + threadIdx.x];
+                    sRank[buf][kk][threadIdx.x] = ws.perm[s0 + threadIdx.x];
+                    if (threadIdx.x < GPT) sGS[buf][kk][threadIdx.x] = ws.grp[(size_t)su * GPT + threadIdx.x];
+                }
+            }
             __syncthreads();
+#pragma unroll 1
+            for (int kk = 0; kk < nst; ++kk) {
+            const int su = sList[q0 + kk], fl = sFlag[q0 + kk];
             const int4 tiS = ws.tinfo[su];
             const bool dup = tiT.z && tiS.z;
 #pragma unroll 1
             for (int g = 0; g < GPT; ++g) {
                 const int cntg = min(max(tiS.w - g * GROUP, 0), GROUP);
                 if (cntg == 0) continue;
-                const GroupStat S = sGS[buf][g];
+                const GroupStat S = sGS[buf][kk][g];
                 // warp-uniform decisions for this warp's 32 targets
                 const bool bgw = (fl & 1) && bg_alive(W, S, cbt);
                 const bool exw = (fl & 2) && exc_alive(W, S, hh);
                 if (!bgw && !exw) continue;
                 const int np = (cntg + 1) >> 1;
-                const float4 *ab = sAB[buf] + g * GROUP;
-                const int *lc = sLoc[buf] + g * GROUP;
-                const int *rk = sRank[buf] + g * GROUP;
+                const float4 *ab = sAB[buf][kk] + g * GROUP;
+                const int *lc = sLoc[buf][kk] + g * GROUP;
+                const int *rk = sRank[buf][kk] + g * GROUP;
                 const bool mask_bg = (su == tile && g == warp) || dup;
                 const bool mask_ex = exw && !(S.ix.w < W.ix.x);
                 if (bgw && exw) {
@@ -128,6 +140,7 @@ __global__ void __launch_bounds__(TILE, 4) row32_st_kernel(Consts c, Inputs in, 
                     kahan(ks[k], kc[k], __fadd_rn(run[k].x, run[k].y));
                     run[k] = make_float2(0.0f, 0.0f);
                 }
+            }
             }
             buf ^= 1;
         }

@@ -25,7 +25,7 @@ def make_post(w, prec, precision):
     return post, hmc
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32c", "fp32c_st"])
 def test_posterior_parity(precision):
     w, prec = problem()
     post, hmc = make_post(w, prec, precision)
@@ -170,7 +170,8 @@ def test_short_chain_with_trend():
     assert np.std(ch.draws[:, -1]) > 0  # beta moves
 
 
-def test_graph_replayed_trajectories_equal_eager_ones():
+@pytest.mark.parametrize("precision", ["fp32c", "fp32c_st"])
+def test_graph_replayed_trajectories_equal_eager_ones(precision):
     """After warm-up each trajectory replays as one captured CUDA graph; the
     kernels and their inputs are the same, so the chain is identical bit for
     bit to the eagerly launched one (same seed)."""
@@ -182,7 +183,7 @@ def test_graph_replayed_trajectories_equal_eager_ones():
 
     def make():
         return hmc.Posterior(d(w.x), d(w.y), d(w.t), d(w.r), torch.tensor(w.sequenced, device="cuda"), None,
-                             hmc.prior_km_days(), "fp32c", tree=tp)
+                             hmc.prior_km_days(), precision, tree=tp)
 
     q0 = d(np.concatenate([np.log(w.params), w.r[w.sequenced]]))
     a = hmc.sample(make(), q0, n_iter=40, n_warmup=20, n_steps=8, eps0=0.05, mass_every=15, seed=3, use_graph=False)
