@@ -409,7 +409,7 @@ def run_ours(args, rank, world, local_rank):
                       "ms_per_step": float(np.mean(band_ms)),
                       "pair_interactions_per_s": world * pairs / (float(np.mean(band_ms)) * 1e-3),
                       "speedup_over_fp32c": ms / float(np.mean(band_ms))},
-        "spacetime": {"precision": "fp32c_st (events regrouped by Morton code inside slabs of 4,096; group pairs "
+        "spacetime": {"precision": "fp32c_st (events regrouped by Hilbert index inside slabs of 4,096; group pairs "
                                    "whose FP32 terms all underflow are skipped; results equal fp32c's up to "
                                    "summation order)",
                       "ms_per_step": float(np.mean(st_ms)),

@@ -42,7 +42,7 @@
  *                equal HAWKES_FP32C's bit for bit; only the work is smaller.
  *                HAWKES_FP32C_ST: FP32C on space-time tiles.  Inside each slab
  *                of 4096 time-consecutive events the events are regrouped by
- *                the Morton code of their location, so each group of 32
+ *                the Hilbert index of their location, so each group of 32
  *                events is compact in space and time; the pairs of groups
  *                whose terms all lie below 2^-126 (background: spatial and
  *                temporal gap; excitation and column pass: spatial gap,

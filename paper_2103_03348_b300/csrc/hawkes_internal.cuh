@@ -3,7 +3,7 @@
 // Data flow of one call (all enqueued on the caller's stream, no host sync):
 //   prep     validate, per-event tie-group start, exact-location dedup, centre
 //   order    FP32C_ST only: regroup each slab of time-consecutive events by a
-//            Morton key of (x, y), so that tiles are compact in space and time
+//            Hilbert index of (x, y), so that tiles are compact in space and time
 //   pack     FP32 scaled source pairs + per-tile statistics (FP32C), FP64 copy
 //   row      per (target tile, source chunk): moment sums of the pair terms
 //            (Eq. 1's inner sum and its parameter derivatives)
@@ -51,7 +51,7 @@ namespace hk {
 constexpr int TILE = 128;   // events per tile: targets per row block, sources per shared-memory subtile
 constexpr int GROUP = 32;   // events per group (one warp's targets or sources) in FP32C_ST
 constexpr int SLAB_TILES = 32;                   // FP32C_ST: tiles per slab of time-consecutive events
-constexpr int SLAB_EVENTS = SLAB_TILES * TILE;  // 4096: sorted by Morton key in shared memory
+constexpr int SLAB_EVENTS = SLAB_TILES * TILE;  // 4096: sorted by Hilbert index in shared memory
 constexpr int NMOM = 10;    // row moments (hess mode)
 constexpr int NACC = 13;    // per-row terms reduced across rows: loglik, 6 gradient, 6 Hessian
 constexpr int ACC_STRIDE = 16;

@@ -10,7 +10,7 @@
 //   * per-tile x/y bounds; the last block to finish (atomic ticket, no waiting)
 //     reduces them in fixed order to the centre used by the FP32 coordinates.
 // order (FP32C_ST only): the events of each slab of 4096 time-consecutive
-// events are sorted by the Morton code of their cell on a 65536 x 65536 grid
+// events are sorted by the Hilbert index of their cell on a 65536 x 65536 grid
 // over the events' bounding square, so every tile of 128 positions covers a
 // compact region of space inside the slab's time window; the permuted copies
 // of x, y, t and of the tie-group and location indices are gathered.
@@ -288,19 +288,34 @@ __global__ void __launch_bounds__(TILE) pack_kernel(Consts c, Inputs in, Workspa
     }
 }
 
-// Morton code of a cell (16 bits per axis, interleaved: x in the even bits).
-__device__ __forceinline__ unsigned spread16(unsigned v) {
-    v &= 0xffffu;
-    v = (v | (v << 8)) & 0x00ff00ffu;
-    v = (v | (v << 4)) & 0x0f0f0f0fu;
-    v = (v | (v << 2)) & 0x33333333u;
-    v = (v | (v << 1)) & 0x55555555u;
-    return v;
+// Position of cell (x, y) of a 65536 x 65536 grid along the Hilbert curve
+// (the usual quadrant-by-quadrant construction: at each scale the quadrant
+// index is added and the cell's coordinates are reflected and swapped into
+// the quadrant's own orientation).  Runs of the curve are more compact than
+// runs of a Morton (bit-interleaved) order, so groups of 32 consecutive
+// positions have smaller boxes.
+__device__ __forceinline__ unsigned hilbert16(unsigned x, unsigned y) {
+    constexpr unsigned N = 65536u;
+    unsigned d = 0;
+    for (unsigned s = N >> 1; s > 0; s >>= 1) {
+        const unsigned rx = (x & s) ? 1u : 0u, ry = (y & s) ? 1u : 0u;
+        d += s * s * ((3u * rx) ^ ry);
+        if (ry == 0) {
+            if (rx == 1) {
+                x = N - 1 - x;
+                y = N - 1 - y;
+            }
+            const unsigned t = x;
+            x = y;
+            y = t;
+        }
+    }
+    return d;
 }
 
 constexpr int ORDER_THREADS = 1024;
 
-// One block per slab: keys (Morton code << 32 | slot) sorted ascending in
+// One block per slab: keys (Hilbert index << 32 | slot) sorted ascending in
 // shared memory by a bitonic network; unique keys make the order deterministic.
 __global__ void __launch_bounds__(ORDER_THREADS) order_sort_kernel(Consts c, Inputs in, Workspace ws) {
     pdl_wait();
@@ -317,7 +332,7 @@ __global__ void __launch_bounds__(ORDER_THREADS) order_sort_kernel(Consts c, Inp
             // fmax / fmin map NaN to the bound, so non-finite inputs (reported by prep) stay in range
             const unsigned ix = (unsigned)fmin(fmax((in.x[e0 + k] - x0) * sc, 0.0), 65535.0);
             const unsigned iy = (unsigned)fmin(fmax((in.y[e0 + k] - y0) * sc, 0.0), 65535.0);
-            key = ((unsigned long long)(spread16(ix) | (spread16(iy) << 1)) << 32) | (unsigned)k;
+            key = ((unsigned long long)hilbert16(ix, iy) << 32) | (unsigned)k;
         }
         keys[k] = key;
     }
