@@ -89,14 +89,17 @@ static bool params_valid(const double *p) {
     return true;
 }
 
-// Every parameter-dependent constant, derived in FP64 by one warp: lane k < 6
-// reads (and exponentiates) parameter k, then lanes compute independent
-// groups of constants side by side, so the serial chain is a few operations
-// long.  Parameters that are not finite and positive (tau_t may be +inf) set
-// ST_BADPARAM, and finalize then reports HAWKES_EINVAL with NaN outputs.
+// Every parameter-dependent constant, derived in FP64.  FP64 is slow on this
+// part (one warp instruction holds an SM's FP64 pipe for about 19 cycles), so
+// the constants are spread over SETUP_BLOCKS one-warp blocks, one group of
+// constants per block and so per SM, each block first reading (and
+// exponentiating) the six parameters on six lanes.  Parameters that are not
+// finite and positive (tau_t may be +inf) set ST_BADPARAM, and finalize then
+// reports HAWKES_EINVAL with NaN outputs.
+constexpr int SETUP_BLOCKS = 18;
+
 __global__ void setup_kernel(ParamSource ps, int fp32c, int reuse, Derived *out, int *hdr, const int *evbits) {
     pdl_wait();
-    if (blockIdx.x != 0) return;
     const int lane = threadIdx.x;
     double pv = 0.0;
     if (lane < 6) pv = ps.dev ? (ps.log_scale ? exp(ps.dev[lane]) : ps.dev[lane]) : ps.v[lane];
@@ -111,8 +114,9 @@ __global__ void setup_kernel(ParamSource ps, int fp32c, int reuse, Derived *out,
     const double st = fp32c ? om * LOG2E : 1.0;
     // the call's header: status bits (with the event checks of the call that
     // prepared these events, when they are reused), the rest cleared
-    if (lane > 0 && lane < 8) hdr[lane] = 0;
-    switch (lane) {
+    if (blockIdx.x == 0 && lane > 0 && lane < 8) hdr[lane] = 0;
+    if (lane != 0) return;
+    switch (blockIdx.x) {  // block-uniform: one group of constants per block
         case 0: {
             bool ok = true;
             for (int k = 0; k < 6; ++k) {
@@ -157,7 +161,7 @@ __global__ void setup_kernel(ParamSource ps, int fp32c, int reuse, Derived *out,
 }
 
 cudaError_t launch_setup(const Consts &c, const ParamSource &ps, const Workspace &ws, cudaStream_t s, int reuse) {
-    launch_pdl(setup_kernel, 1, 32, 0, s, ps, c.fp32c, reuse, ws.derived, ws.hdr, ws.evbits);
+    launch_pdl(setup_kernel, SETUP_BLOCKS, 32, 0, s, ps, c.fp32c, reuse, ws.derived, ws.hdr, ws.evbits);
     return cudaGetLastError();
 }
 

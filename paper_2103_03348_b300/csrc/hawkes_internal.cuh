@@ -148,7 +148,7 @@ struct Workspace {
                          //         column weight g^ = log2(B/lambda) - t~, written by the tile finish
     float4 *tstat32;     // [tiles] t~min, t~max, max r^, max g^
     double4_32a *src64;      // [npad]  (x, y, t, r) FP64 (FP64 path)
-    double *rowpart;     // [n_chunks * NMOM * npad]
+    double *rowpart;     // [n_chunks * NMOM * npad]: FP64 partials (FP64 path), FP32C Kahan pairs as float2
     double *mom;         // [NMOM * npad]
     double *w64;         // [npad]  FP64 column weight, in logs: log(B / lambda_n)
     double *dLr;         // [npad]  dLambda / dr_m

@@ -106,20 +106,20 @@ constexpr int FIN_THREADS = 256;
 __global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(Consts c, Workspace ws, Outputs out) {
     pdl_wait();
     const Derived &D = *c.d;
-    __shared__ double sh[(FIN_THREADS / 32) * NACC];
     __shared__ double tot[NACC];
     const int tiles = c.g.tiles;
     {
-        // each thread sums a fixed strided subset of tiles, then one fixed-order block sum
-        double acc[NACC];
+        // Warp w sums components w and w + 8 over the tiles: each lane a fixed
+        // strided subset, then a fixed shuffle butterfly.  (FP64 instructions
+        // are costly here, and this keeps them to a few per lane.)
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int k = warp; k < NACC; k += FIN_THREADS / 32) {
+            double v = 0.0;
+            for (int b = lane; b < tiles; b += 32) v += ws.blockpart[(size_t)b * ACC_STRIDE + k];
 #pragma unroll
-        for (int k = 0; k < NACC; ++k) acc[k] = 0.0;
-        for (int b = threadIdx.x; b < tiles; b += FIN_THREADS) {
-#pragma unroll
-            for (int k = 0; k < NACC; ++k) acc[k] += ws.blockpart[(size_t)b * ACC_STRIDE + k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) tot[k] = v;
         }
-        const double v = block_sum_multi<FIN_THREADS, NACC>(acc, sh);
-        if (threadIdx.x < NACC) tot[threadIdx.x] = v;
     }
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -118,7 +118,8 @@ __global__ void __launch_bounds__(TILE, 4) row32_kernel(Consts c, Inputs in, Wor
 #pragma unroll
     for (int k = 0; k < NMOM; ++k) {
         if (mom_used(MODE, k))
-            ws.rowpart[((size_t)chunk * NMOM + k) * npad + i] = (double)ks[k] - (double)kc[k];
+            // the Kahan pair (sum, -compensation), combined across chunks in float-float
+            reinterpret_cast<float2 *>(ws.rowpart)[((size_t)chunk * NMOM + k) * npad + i] = make_float2(ks[k], -kc[k]);
     }
     // one block per tile also computes the tile's integral-term shares (FP64)
     if (blockIdx.y == 0) integral_tile(c, in, ws, tile);

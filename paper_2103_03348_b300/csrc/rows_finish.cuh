@@ -163,14 +163,27 @@ __device__ __forceinline__ void finish_tile_fp32c(const Consts &c, const Inputs 
     const int n = c.g.n, npad = c.g.npad;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool valid = i < n;
+    // The chunk partials are FP32 Kahan pairs (sum, -compensation); they are
+    // summed in chunk order in float-float arithmetic (Knuth's two-sum for the
+    // leading part, the low parts and rounding errors carried in a second
+    // float), about 2^-44 relative, and only the total is made FP64: FP64
+    // additions cost an SM's FP64 pipe about 19 cycles per warp instruction.
+    const float2 *part = reinterpret_cast<const float2 *>(ws.rowpart);
     double Mo[NMOM];
 #pragma unroll
     for (int k = 0; k < NMOM; ++k) {
-        double s = 0.0;
+        float hi = 0.0f, lo = 0.0f;
         if (valid && row_mom_used(c.mode, k)) {
-            for (int ch = 0; ch < c.g.n_chunks; ++ch) s += ws.rowpart[((size_t)ch * NMOM + k) * npad + i];
+            for (int ch = 0; ch < c.g.n_chunks; ++ch) {
+                const float2 v = part[((size_t)ch * NMOM + k) * npad + i];
+                const float s = __fadd_rn(hi, v.x);
+                const float bb = __fsub_rn(s, hi);
+                const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v.x, bb));
+                hi = s;
+                lo = __fadd_rn(lo, __fadd_rn(err, v.y));
+            }
         }
-        Mo[k] = s;
+        Mo[k] = (double)hi + (double)lo;
     }
     // rows to redo in FP64, listed in thread order
     const bool tiny = valid && Mo[MO_G] < (double)TINY_ROW && Mo[MO_E] < (double)TINY_ROW;
