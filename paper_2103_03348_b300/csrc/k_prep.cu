@@ -168,8 +168,6 @@ __global__ void __launch_bounds__(TILE) pack_kernel(Consts c, Inputs in, Workspa
     const int n = c.g.n;
     const int i = blockIdx.x * TILE + threadIdx.x;
     const bool valid = i < n;
-    __shared__ float shf[TILE];
-    __shared__ int shi[TILE];
 
     // FP32C_ST: position i holds event perm[i]; its log-rate is gathered here
     double ri = 0.0;
@@ -226,64 +224,46 @@ __global__ void __launch_bounds__(TILE) pack_kernel(Consts c, Inputs in, Workspa
         if ((threadIdx.x & 31) == 0) ws.grp[i / GROUP] = gs;
     }
 
-    // per-tile statistics (FP32C scaled time bounds and max(r~ + t~))
-    tmin = -block_max<TILE>(-tmin, shf);
-    tmax = block_max<TILE>(tmax, shf);
-    rtmax = block_max<TILE>(rtmax, shf);
-    // duplicate flag: any event of the tile shares its location with another event
-    shi[threadIdx.x] = dup;
-    __syncthreads();
-    for (int w = TILE / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) shi[threadIdx.x] |= shi[threadIdx.x + w];
-        __syncthreads();
+    // per-tile statistics: each warp reduces with shuffles, one barrier, then
+    // thread 0 combines the four warps (FP32C scaled time bounds, max(r~ + t~),
+    // duplicate flag; on space-time tiles the tie-group and rank ranges)
+    __shared__ float wf[3][TILE / 32];
+    __shared__ int wi[5][TILE / 32];
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const float a0 = warp_minf(tmin), a1 = warp_maxf(tmax), a2 = warp_maxf(rtmax);
+        const int dupw = __any_sync(0xffffffffu, dup) ? 1 : 0;
+        int b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+        if (c.st) {
+            const int gi = valid ? ws.gidx[i] : INT_MAX, rk = valid ? ws.perm[i] : INT_MAX;
+            b0 = warp_mini(gi);
+            b1 = warp_maxi(valid ? gi : INT_MIN);
+            b2 = warp_mini(rk);
+            b3 = warp_maxi(valid ? rk : INT_MIN);
+        }
+        if (lane == 0) {
+            wf[0][warp] = a0; wf[1][warp] = a1; wf[2][warp] = a2;
+            wi[0][warp] = dupw; wi[1][warp] = b0; wi[2][warp] = b1; wi[3][warp] = b2; wi[4][warp] = b3;
+        }
     }
-    const int has_dup = shi[0];
     __syncthreads();
-    const int first = blockIdx.x * TILE;
-    const int lastv = min(n, first + TILE) - 1;
-    int g_lo = 0, g_hi = 0, k_lo = 0, k_hi = 0;
-    if (c.st) {
-        // permuted positions: tie-group and rank ranges by reduction
-        const int gi = valid ? ws.gidx[i] : INT_MAX, rk = valid ? ws.perm[i] : INT_MAX;
-        shi[threadIdx.x] = gi;
-        __syncthreads();
-        for (int w = TILE / 2; w > 0; w >>= 1) {
-            if (threadIdx.x < w) shi[threadIdx.x] = min(shi[threadIdx.x], shi[threadIdx.x + w]);
-            __syncthreads();
-        }
-        g_lo = shi[0];
-        __syncthreads();
-        shi[threadIdx.x] = valid ? gi : INT_MIN;
-        __syncthreads();
-        for (int w = TILE / 2; w > 0; w >>= 1) {
-            if (threadIdx.x < w) shi[threadIdx.x] = max(shi[threadIdx.x], shi[threadIdx.x + w]);
-            __syncthreads();
-        }
-        g_hi = shi[0];
-        __syncthreads();
-        shi[threadIdx.x] = rk;
-        __syncthreads();
-        for (int w = TILE / 2; w > 0; w >>= 1) {
-            if (threadIdx.x < w) shi[threadIdx.x] = min(shi[threadIdx.x], shi[threadIdx.x + w]);
-            __syncthreads();
-        }
-        k_lo = shi[0];
-        __syncthreads();
-        shi[threadIdx.x] = valid ? rk : INT_MIN;
-        __syncthreads();
-        for (int w = TILE / 2; w > 0; w >>= 1) {
-            if (threadIdx.x < w) shi[threadIdx.x] = max(shi[threadIdx.x], shi[threadIdx.x + w]);
-            __syncthreads();
-        }
-        k_hi = shi[0];
-    } else {
-        // time order: gidx is non-decreasing
-        g_lo = ws.gidx[first];
-        g_hi = ws.gidx[lastv];
-    }
     if (threadIdx.x == 0) {
+        float t0 = wf[0][0], t1 = wf[1][0], rt = wf[2][0];
+        int has_dup = wi[0][0], g_lo = wi[1][0], g_hi = wi[2][0], k_lo = wi[3][0], k_hi = wi[4][0];
+        for (int w = 1; w < TILE / 32; ++w) {
+            t0 = fminf(t0, wf[0][w]); t1 = fmaxf(t1, wf[1][w]); rt = fmaxf(rt, wf[2][w]);
+            has_dup |= wi[0][w];
+            g_lo = min(g_lo, wi[1][w]); g_hi = max(g_hi, wi[2][w]);
+            k_lo = min(k_lo, wi[3][w]); k_hi = max(k_hi, wi[4][w]);
+        }
+        const int first = blockIdx.x * TILE;
+        const int lastv = min(n, first + TILE) - 1;
+        if (!c.st) {  // time order: gidx is non-decreasing
+            g_lo = ws.gidx[first];
+            g_hi = ws.gidx[lastv];
+        }
         ws.tinfo[blockIdx.x] = make_int4(g_lo, g_hi, has_dup, lastv - first + 1);
-        if (c.fp32c) ws.tstat32[blockIdx.x] = make_float4(tmin, tmax, rtmax, -INFINITY);
+        if (c.fp32c) ws.tstat32[blockIdx.x] = make_float4(t0, t1, rt, -INFINITY);
         if (c.st) ws.trank[blockIdx.x] = make_int2(k_lo, k_hi);
     }
 }
