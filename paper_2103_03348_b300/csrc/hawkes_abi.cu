@@ -65,7 +65,7 @@ size_t carve(void *base, const Geometry &g, int precision, Workspace *w) {
     w->mom = (double *)take((size_t)NMOM * np * sizeof(double));
     w->dLr = (double *)take(np * sizeof(double));
     w->blockpart = (double *)take(nt * ACC_STRIDE * sizeof(double));
-    w->ipart = f32 ? (double *)take(nt * ACC_STRIDE * sizeof(double)) : nullptr;
+    w->ipart = f32 ? (double *)take(nt * (TILE / GROUP) * ACC_STRIDE * sizeof(double)) : nullptr;
     w->colpart = (double *)take((size_t)g.n_chunks * 2 * np * sizeof(double));
     w->bbox = (double *)take(4 * sizeof(double));
     w->perm = st ? (int *)take(np * sizeof(int)) : nullptr;

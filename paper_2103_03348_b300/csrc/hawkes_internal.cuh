@@ -153,7 +153,7 @@ struct Workspace {
     double *w64;         // [npad]  FP64 column weight, in logs: log(B / lambda_n)
     double *dLr;         // [npad]  dLambda / dr_m
     double *blockpart;   // [tiles * ACC_STRIDE]
-    double *ipart;       // [tiles * ACC_STRIDE] FP32C: the integral-term sums of each tile (row pass)
+    double *ipart;       // [tiles * 4 * ACC_STRIDE] FP32C: the integral-term sums of each 32-event group (row pass)
     float *sufmax;       // [tiles] suffix max of the column weight bound (FP32C)
     double *colpart;     // [n_chunks * 2 * npad]
     double *bbox;        // [4]: x min, x max, y min, y max of the events (prep)

@@ -121,8 +121,8 @@ __global__ void __launch_bounds__(TILE, 4) row32_kernel(Consts c, Inputs in, Wor
             // the Kahan pair (sum, -compensation), combined across chunks in float-float
             reinterpret_cast<float2 *>(ws.rowpart)[((size_t)chunk * NMOM + k) * npad + i] = make_float2(ks[k], -kc[k]);
     }
-    // one block per tile also computes the tile's integral-term shares (FP64)
-    if (blockIdx.y == 0) integral_tile(c, in, ws, tile);
+    // one block per tile also computes the tile's integral-term shares (FP64), warp by warp
+    if (blockIdx.y == 0) integral_group(c, in, ws, i / GROUP);
 }
 
 cudaError_t launch_row32(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s) {

@@ -275,7 +275,11 @@ __device__ __forceinline__ void finish_tile_fp32c(const Consts &c, const Inputs 
     {
         const double v = block_sum_multi<TILE, NACC>(acc, fsh);
         if (threadIdx.x < NACC)
-            ws.blockpart[(size_t)tile * ACC_STRIDE + threadIdx.x] = v + ws.ipart[(size_t)tile * ACC_STRIDE + threadIdx.x];
+            ws.blockpart[(size_t)tile * ACC_STRIDE + threadIdx.x] =
+                v + (((ws.ipart[((size_t)tile * 4 + 0) * ACC_STRIDE + threadIdx.x] +
+                       ws.ipart[((size_t)tile * 4 + 1) * ACC_STRIDE + threadIdx.x]) +
+                      ws.ipart[((size_t)tile * 4 + 2) * ACC_STRIDE + threadIdx.x]) +
+                     ws.ipart[((size_t)tile * 4 + 3) * ACC_STRIDE + threadIdx.x]);
     }
     if (c.st) {  // per-group bound for the column pass's pruning
         const float wm = warp_maxf(ghat);
@@ -285,20 +289,27 @@ __device__ __forceinline__ void finish_tile_fp32c(const Consts &c, const Inputs 
     if (threadIdx.x == 0) ws.tstat32[tile].w = gm;
 }
 
-// FP32C: the integral-term shares of tile `tile`'s events (FP64), summed over
-// the tile into ipart, with dLambda/dr per event.  Called by one row block
-// per tile after its pair loop, so this FP64 work runs beside other blocks'
-// FP32 pair arithmetic instead of in the finish kernel.
-static __device__ __noinline__ void integral_tile(const Consts &c, const Inputs &in, const Workspace &ws, int tile) {
-    __shared__ double ish[(TILE / 32) * NACC];
+// FP32C: the integral-term shares of one group of 32 events (FP64), summed
+// over the group by the calling warp into ipart[group], with dLambda/dr per
+// event.  Called by the row blocks of one source chunk after their pair loops,
+// so this FP64 work runs beside other blocks' FP32 pair arithmetic instead of
+// in the finish kernel.  Every lane of the warp calls it.
+static __device__ __noinline__ void integral_group(const Consts &c, const Inputs &in, const Workspace &ws, int group) {
     const Derived &D = *c.d;
-    const int i = tile * TILE + threadIdx.x;
+    const int i = group * GROUP + (threadIdx.x & 31);
     double a[NACC];
 #pragma unroll
     for (int k = 0; k < NACC; ++k) a[k] = 0.0;
     if (i < c.g.n) integral_row(D, in, ws, i, a);
-    const double v = block_sum_multi<TILE, NACC>(a, ish);
-    if (threadIdx.x < NACC) ws.ipart[(size_t)tile * ACC_STRIDE + threadIdx.x] = v;
+#pragma unroll
+    for (int k = 0; k < NACC; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a[k] += __shfl_xor_sync(0xffffffffu, a[k], o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int k = 0; k < NACC; ++k) ws.ipart[(size_t)group * ACC_STRIDE + k] = a[k];
+    }
 }
 
 }  // namespace hk
