@@ -10,12 +10,14 @@ namespace hk {
 // warp and owns one target group (32 rows) for one chunk of source tiles, so
 // no warp ever waits for another:
 //   * classify: lane l tests source tile base + l group by group against the
-//     warp's own target group (background live, excitation live, all sources
-//     causal), and the tiles with a live group are listed in order;
-//   * sweep: for each listed tile, each live source group (32 sources) is
-//     staged in the warp's shared buffer (double-buffered, one __syncwarp)
-//     and evaluated with the pair arithmetic, masks and compensation of
-//     row32_kernel; the causal mask compares time-order ranks.
+//     warp's own target group (background live, excitation live, masks
+//     needed), and the live groups of the 32 tiles are listed in order as
+//     items (a warp prefix sum places each lane's items);
+//   * sweep: each item's 32 sources are staged in the warp's shared buffer
+//     (double-buffered, one __syncwarp) while the next item's load into
+//     registers, and evaluated with the pair arithmetic, masks and
+//     compensation of row32_kernel, the runs merged at each tile boundary;
+//     the causal mask compares time-order ranks.
 constexpr int GPT = TILE / GROUP;  // groups per tile
 
 template <int MODE>
@@ -28,9 +30,11 @@ __global__ void __launch_bounds__(GROUP, 16) row32_st_kernel(Consts c, Inputs in
     const int lane = threadIdx.x;
     const int i = tg * GROUP + lane;
     const int npad = c.g.npad;
-    __shared__ int sList[GROUP];
-    __shared__ int sInfo[GROUP];  // per listed tile: bits 0-3 background live, 4-7 excitation live,
-                                  // 8-11 every source precedes every target, 12 duplicates, 13+ count
+    // live (tile, group) items of up to 32 source tiles, in order: the source
+    // group index (bits 0-23), plus bit 24 background, 25 excitation, 26
+    // location mask, 27 causal mask
+    __shared__ int sItem[GROUP * GPT];
+    __shared__ int sItemCnt[GROUP * GPT];  // each item's source count
     __shared__ float4 sAB[2][GROUP];
     __shared__ int sLoc[2][GROUP];
     __shared__ int sRank[2][GROUP];
@@ -59,67 +63,90 @@ __global__ void __launch_bounds__(GROUP, 16) row32_st_kernel(Consts c, Inputs in
     int buf = 0;
     if (!group_empty(W)) {
         for (int base = sb; base < se; base += GROUP) {
-            // classify tiles base .. base + 31 against this warp's targets
+            // classify source tile base + lane group by group against this warp's targets
             const int s = base + lane;
-            int info = 0;
+            int live = 0, flags = 0, cnt = 0;  // flags: 4 bits per group (bg, exc, location mask, causal mask)
             if (s < se) {
                 const int4 tiS = ws.tinfo[s];
+                cnt = tiS.w;
+                const bool dup = dupT && tiS.z;
 #pragma unroll
                 for (int g = 0; g < GPT; ++g) {
                     const GroupStat S = ws.grp[(size_t)s * GPT + g];
-                    if (group_empty(S)) continue;
-                    if (bg_alive(W, S, cbt)) info |= 1 << g;
-                    if (exc_alive(W, S, hh)) info |= 16 << g;
-                    if (S.ix.w < W.ix.x) info |= 256 << g;
+                    if (cnt <= g * GROUP || group_empty(S)) continue;
+                    const bool bgw = bg_alive(W, S, cbt), exw = exc_alive(W, S, hh);
+                    if (!bgw && !exw) continue;
+                    live |= 1 << g;
+                    int f = (bgw ? 1 : 0) | (exw ? 2 : 0);
+                    if ((s == tile && g == gw) || dup) f |= 4;
+                    if (exw && !(S.ix.w < W.ix.x)) f |= 8;
+                    flags |= f << (4 * g);
                 }
-                if (info & 0xff) info |= (tiS.z ? 4096 : 0) | (tiS.w << 13);
-                else info = 0;
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, info != 0);
-            if (info) sList[__popc(bal & ((1u << lane) - 1u))] = s;
-            if (info) sInfo[__popc(bal & ((1u << lane) - 1u))] = info;
-            __syncwarp();
-            const int total = __popc(bal);
-            for (int q = 0; q < total; ++q) {
-                const int su = sList[q], inf = sInfo[q];
-                const int cnt = inf >> 13;
-                const bool dup = dupT && (inf & 4096);
-#pragma unroll 1
-                for (int g = 0; g < GPT; ++g) {
-                    const bool bgw = (inf >> g) & 1, exw = (inf >> (4 + g)) & 1;
-                    const int cntg = min(max(cnt - g * GROUP, 0), GROUP);
-                    if ((!bgw && !exw) || cntg == 0) continue;
-                    const size_t src = (size_t)su * TILE + g * GROUP + lane;
-                    sAB[buf][lane] = ws.src32[src];
-                    sLoc[buf][lane] = ws.loc[src];
-                    sRank[buf][lane] = ws.perm[src];
-                    __syncwarp();
-                    const int np = (cntg + 1) >> 1;
-                    const bool mask_bg = (su == tile && g == gw) || dup;
-                    const bool mask_ex = exw && !((inf >> (8 + g)) & 1);
-                    const float4 *ab = sAB[buf];
-                    const int *lc = sLoc[buf], *rk = sRank[buf];
-                    if (bgw && exw) {
-                        if (mask_bg || mask_ex) row_group<MODE, true, true, true>(ab, lc, rk, np, T, cbt2, nhh2, run);
-                        else row_group<MODE, true, true, false>(ab, lc, rk, np, T, cbt2, nhh2, run);
-                    } else if (bgw) {
-                        if (mask_bg) row_group<MODE, true, false, true>(ab, lc, rk, np, T, cbt2, nhh2, run);
-                        else row_group<MODE, true, false, false>(ab, lc, rk, np, T, cbt2, nhh2, run);
-                    } else {
-                        if (mask_ex) row_group<MODE, false, true, true>(ab, lc, rk, np, T, cbt2, nhh2, run);
-                        else row_group<MODE, false, true, false>(ab, lc, rk, np, T, cbt2, nhh2, run);
-                    }
-                    buf ^= 1;
-                }
+            // exclusive prefix sum of the live counts: each lane's items go in order
+            const int nl = __popc(live);
+            int pre = nl;
 #pragma unroll
-                for (int k = 0; k < NMOM; ++k) {
-                    if (mom_used(MODE, k)) {
-                        kahan(ks[k], kc[k], __fadd_rn(run[k].x, run[k].y));
-                        run[k] = make_float2(0.0f, 0.0f);
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, pre, o);
+                if (lane >= o) pre += v;
+            }
+            const int total = __shfl_sync(0xffffffffu, pre, 31);
+            int pos = pre - nl;
+#pragma unroll
+            for (int g = 0; g < GPT; ++g) {
+                if ((live >> g) & 1) {
+                    const int cntg = min(cnt - g * GROUP, GROUP);
+                    sItem[pos++] = (s * GPT + g) | (((flags >> (4 * g)) & 15) << 24);
+                    sItemCnt[pos - 1] = cntg;
+                }
+            }
+            __syncwarp();
+            float4 pab = make_float4(0.f, 0.f, 0.f, 0.f);
+            int pl = 0, pr = 0;
+            if (total > 0) {
+                const size_t src = (size_t)(sItem[0] & 0xffffff) * GROUP + lane;
+                pab = ws.src32[src]; pl = ws.loc[src]; pr = ws.perm[src];
+            }
+            for (int q = 0; q < total; ++q) {
+                const int cur = sItem[q], cntg = sItemCnt[q];
+                sAB[buf][lane] = pab;
+                sLoc[buf][lane] = pl;
+                sRank[buf][lane] = pr;
+                __syncwarp();
+                int nt = -1;
+                if (q + 1 < total) {  // the next group's loads are in flight during this one's arithmetic
+                    const int ng = sItem[q + 1] & 0xffffff;
+                    nt = ng / GPT;
+                    const size_t src = (size_t)ng * GROUP + lane;
+                    pab = ws.src32[src]; pl = ws.loc[src]; pr = ws.perm[src];
+                }
+                const int f = (cur >> 24) & 15;
+                const int np = (cntg + 1) >> 1;
+                const float4 *ab = sAB[buf];
+                const int *lc = sLoc[buf], *rk = sRank[buf];
+                if ((f & 3) == 3) {
+                    if (f & 12) row_group<MODE, true, true, true>(ab, lc, rk, np, T, cbt2, nhh2, run);
+                    else row_group<MODE, true, true, false>(ab, lc, rk, np, T, cbt2, nhh2, run);
+                } else if (f & 1) {
+                    if (f & 4) row_group<MODE, true, false, true>(ab, lc, rk, np, T, cbt2, nhh2, run);
+                    else row_group<MODE, true, false, false>(ab, lc, rk, np, T, cbt2, nhh2, run);
+                } else {
+                    if (f & 8) row_group<MODE, false, true, true>(ab, lc, rk, np, T, cbt2, nhh2, run);
+                    else row_group<MODE, false, true, false>(ab, lc, rk, np, T, cbt2, nhh2, run);
+                }
+                buf ^= 1;
+                if (nt != (cur & 0xffffff) / GPT) {  // tile boundary: merge the runs
+#pragma unroll
+                    for (int k = 0; k < NMOM; ++k) {
+                        if (mom_used(MODE, k)) {
+                            kahan(ks[k], kc[k], __fadd_rn(run[k].x, run[k].y));
+                            run[k] = make_float2(0.0f, 0.0f);
+                        }
                     }
                 }
             }
-            __syncwarp();  // the list is read until here
+            __syncwarp();  // the items are read until here
         }
     }
 #pragma unroll
