@@ -103,7 +103,7 @@ __device__ __forceinline__ void col_sweep_warp(const Workspace &ws, int ub, int 
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(GROUP, 16) col32_st_kernel(Consts c, Inputs in, Workspace ws) {
+__global__ void __launch_bounds__(GROUP, 24) col32_st_kernel(Consts c, Inputs in, Workspace ws) {
     pdl_wait();
     const Derived &D = *c.d;
     const int sg = c.t0 * CGPT + blockIdx.x;  // source group
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(GROUP, 16) col32_st_kernel(Consts c, Inputs in
 // indices); their positions come from the inverse permutation and their
 // bounds are reduced from the sources themselves.
 template <int MODE>
-__global__ void __launch_bounds__(GROUP, 16) col32_subset_st_kernel(Consts c, Inputs in, Workspace ws,
+__global__ void __launch_bounds__(GROUP, 24) col32_subset_st_kernel(Consts c, Inputs in, Workspace ws,
                                                                    const int *__restrict__ rate_idx, int k_rates) {
     pdl_wait();
     const Derived &D = *c.d;
