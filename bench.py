@@ -262,20 +262,33 @@ def run_ours(args, rank, world, local_rank):
         step()
     torch.cuda.synchronize()
 
-    step_ms, row_ms, col_ms = [], [], []
+    def timed_steps(k, call, phases=False):
+        """k steps enqueued back to back, each bracketed by its own events with an
+        untimed L2 flush before it; one synchronize at the end, so that the host's
+        launch work overlaps the device's and only device time is measured.
+        Returns the per-step milliseconds (and the row / column phase times)."""
+        marks = []
+        for _ in range(k):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(6 if phases else 2)]
+            flush.zero_()  # untimed: evicts the L2 between steps
+            e[0].record(stream)
+            call(e[2:6] if phases else None)
+            e[1].record(stream)
+            marks.append(e)
+        torch.cuda.synchronize()
+        ms_ = [e[0].elapsed_time(e[1]) for e in marks]
+        if not phases:
+            return ms_
+        return ms_, [e[2].elapsed_time(e[3]) for e in marks], [e[4].elapsed_time(e[5]) for e in marks]
+
+    def fused(phase):
+        hawkes._call("hess", x, y, t, r, w.params, prec, stream=stream, check=False, out=out, phase_events=phase)
+
     barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     with ClockSampler(local_rank) as clk:
-        for _ in range(args.steps):
-            flush.zero_()  # untimed: evicts the L2 between steps
-            ev[0].record(stream)
-            step()
-            ev[1].record(stream)
-            ev[1].synchronize()
-            step_ms.append(ev[0].elapsed_time(ev[1]))
-            row_ms.append(ev[2].elapsed_time(ev[3]))
-            col_ms.append(ev[4].elapsed_time(ev[5]))
+        step_ms, row_ms, col_ms = timed_steps(args.steps, fused, phases=True)
     torch.cuda.synchronize()
     barrier()
     wall = time.perf_counter() - wall0
@@ -311,28 +324,22 @@ def run_ours(args, rank, world, local_rank):
     e2e_value = world * pairs / (float(np.mean(e2e_ms)) * 1e-3)
 
     # the same evaluation with exact background band skipping (bit-identical results)
-    band_ms = []
-    for i in range(max(3, min(args.steps, 50)) + 1):
-        flush.zero_()
-        ev[0].record(stream)
-        hawkes._call("hess", x, y, t, r, w.params, "fp32c_band", stream=stream, check=False)
-        ev[1].record(stream)
-        ev[1].synchronize()
-        if i > 0:
-            band_ms.append(ev[0].elapsed_time(ev[1]))
+    k_alt = max(3, min(args.steps, 50))
+    band_out = {k: torch.empty_like(v) for k, v in out.items()}
+    ws_band = torch.empty(hawkes.workspace_size(n, "fp32c_band"), dtype=torch.uint8, device=dev)
+    band = lambda _: hawkes._call("hess", x, y, t, r, w.params, "fp32c_band", stream=stream, check=False,  # noqa: E731
+                                  out=band_out, workspace=ws_band)
+    timed_steps(3, band)  # warm-up
+    band_ms = timed_steps(k_alt, band)
 
     # the same evaluation on space-time tiles (events regrouped by location inside
     # time slabs; group pairs whose FP32 terms all underflow are skipped; results
     # equal FP32C's up to summation order), event preparation included
-    st_ms = []
-    for i in range(max(3, min(args.steps, 50)) + 1):
-        flush.zero_()
-        ev[0].record(stream)
-        hawkes._call("hess", x, y, t, r, w.params, "fp32c_st", stream=stream, check=False)
-        ev[1].record(stream)
-        ev[1].synchronize()
-        if i > 0:
-            st_ms.append(ev[0].elapsed_time(ev[1]))
+    ws_st = torch.empty(hawkes.workspace_size(n, "fp32c_st"), dtype=torch.uint8, device=dev)
+    st = lambda _: hawkes._call("hess", x, y, t, r, w.params, "fp32c_st", stream=stream, check=False,  # noqa: E731
+                                out=band_out, workspace=ws_st)
+    timed_steps(3, st)  # warm-up
+    st_ms = timed_steps(k_alt, st)
 
     # FP64 GPU path on the same workload (speedup of FP32C over it)
     fp64_ms = []
