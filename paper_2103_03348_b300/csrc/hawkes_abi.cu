@@ -96,7 +96,7 @@ static bool params_valid(const double *p) {
 // exponentiating) the six parameters on six lanes.  Parameters that are not
 // finite and positive (tau_t may be +inf) set ST_BADPARAM, and finalize then
 // reports HAWKES_EINVAL with NaN outputs.
-constexpr int SETUP_BLOCKS = 18;
+constexpr int SETUP_BLOCKS = 13 + EP_N;
 
 __global__ void setup_kernel(ParamSource ps, int fp32c, int reuse, Derived *out, int *hdr, const int *evbits) {
     pdl_wait();
@@ -139,24 +139,49 @@ __global__ void setup_kernel(ParamSource ps, int fp32c, int reuse, Derived *out,
         case 7: out->ih = 1.0 / (2.0 * h * h); break;
         // x~ = (x - xc) sqrt(log2(e)/2) / tau_x makes the background's spatial exponent -d~^2;
         // t~ = (t - tc) omega log2(e) makes the excitation's temporal exponent -dt~.
-        case 8: out->sx = sx; out->i_sx2 = 1.0 / (sx * sx); break;
-        case 9: {
-            out->st = st;
-            const double i_st = 1.0 / st;
-            out->i_st = i_st;
-            out->i_st2 = i_st * i_st;
-            break;
-        }
+        case 8: out->sx = sx; break;
+        case 9: out->st = st; break;
         case 10: out->cbt = (fp32c && !tt_inf) ? (float)(LOG2E / (2.0 * tt * tt) / (st * st)) : 0.0f; break;
         case 11: out->hh = fp32c ? (float)((tx / h) * (tx / h)) : 0.0f; break;
-        // reciprocals for the row epilogue
-        case 12: out->i_mu0 = 1.0 / mu0; break;
-        case 13: out->i_tx = 1.0 / tx; break;
-        case 14: out->i_tt = tt_inf ? 0.0 : 1.0 / tt; break;
-        case 15: out->i_th0 = 1.0 / th0; break;
-        case 16: out->i_om = 1.0 / om; break;
-        case 17: out->i_h = 1.0 / h; break;
-        default: break;
+        case 12: out->i_tt = tt_inf ? 0.0 : 1.0 / tt; break;  // the integral term
+        default: {
+            // the row epilogue's coefficients (Derived::ep): A or B times the
+            // moment's unit conversion (1/sx^2 per d~^2, 1/st per dt~) and the
+            // parameter powers of the derivative
+            const int j = blockIdx.x - 13;
+            if (j < 0 || j >= EP_N) break;
+            const double A = tt_inf ? mu0 / (two_pi * tx * tx) : mu0 / (two_pi * sqrt(two_pi) * tx * tx * tt);
+            const double isx2 = 1.0 / (sx * sx), ist = 1.0 / st, ist2 = ist * ist;
+            const double ix = 1.0 / tx, it = tt_inf ? 0.0 : 1.0 / tt, ih = 1.0 / h;
+            const double ix2 = ix * ix, it2 = it * it, ih2 = ih * ih;
+            double v = 0.0;
+            switch (j) {
+                case EP_G0: v = A / mu0; break;
+                case EP_GD2: v = A * isx2 * (ix2 * ix); break;
+                case EP_G1: v = 2.0 * A * ix; break;
+                case EP_GT2: v = A * ist2 * (it2 * it); break;
+                case EP_G2: v = A * it; break;
+                case EP_E3: v = B / th0; break;
+                case EP_E4: v = B / om; break;
+                case EP_ET: v = B * ist; break;
+                case EP_ED2: v = B * isx2 * (ih2 * ih); break;
+                case EP_E5: v = 2.0 * B * ih; break;
+                case EP_GD4: v = A * (isx2 * isx2) * (ix2 * ix2 * ix2); break;
+                case EP_GD2B: v = 7.0 * A * isx2 * (ix2 * ix2); break;
+                case EP_G1B: v = 6.0 * A * ix2; break;
+                case EP_GT4: v = A * (ist2 * ist2) * (it2 * it2 * it2); break;
+                case EP_GT2B: v = 5.0 * A * ist2 * (it2 * it2); break;
+                case EP_G2B: v = 2.0 * A * it2; break;
+                case EP_ET2: v = B * ist2; break;
+                case EP_ETB: v = 2.0 * B * ist / om; break;
+                case EP_ED4: v = B * (isx2 * isx2) * (ih2 * ih2 * ih2); break;
+                case EP_ED2B: v = 7.0 * B * isx2 * (ih2 * ih2); break;
+                case EP_E5B: v = 6.0 * B * ih2; break;
+                default: break;
+            }
+            out->ep[j] = v;
+            break;
+        }
     }
 }
 

@@ -96,10 +96,23 @@ struct Derived {
     double ibx, ibt, ih;  // FP64:  G = exp(-ibx d^2 - ibt dt^2), E = exp(r - om dt - ih d^2)
     float cbt, hh;        // FP32C: G = 2^-(d~^2 + cbt dt~^2), E = 2^(r^_s - t~_n - hh d~^2)
     int tt_inf, valid;
-    // reciprocals for the row epilogue (FP64 division is costly): 1/mu0, 1/tau_x,
-    // 1/tau_t (0 when infinite), 1/theta0, 1/omega, 1/h, 1/sx^2, 1/st, 1/st^2
-    double i_mu0, i_tx, i_tt, i_th0, i_om, i_h, i_sx2, i_st, i_st2;
+    double i_tt;          // 1/tau_t (0 when infinite), for the integral term
     double ln_b, log2_b;  // log B and log2 B: column weights in the log domain, log(B / lambda) = ln_b - log lambda
+    // the row epilogue's coefficients on the moments (scaled units), so that
+    // each row spends one multiply or fused multiply-add per term: lambda_n q1
+    // and lambda_n s2 (the first and second parameter derivatives of lambda_n)
+    // are sums of coefficient x moment
+    double ep[21];
+};
+
+// Indices into Derived::ep.  dlam/dp:  mu0: G0 S_G;  tau_x: GD2 M_GD2 - G1 S_G;
+// tau_t: GT2 M_GT2 - G2 S_G;  theta0: E3 S_E;  omega: E4 S_E - ET M_ET;
+// h: ED2 M_ED2 - E5 S_E.  d2lam/dp2:  tau_x: GD4 M_GD4 - GD2B M_GD2 + G1B S_G;
+// tau_t: GT4 M_GT4 - GT2B M_GT2 + G2B S_G;  omega: ET2 M_ET2 - ETB M_ET;
+// h: ED4 M_ED4 - ED2B M_ED2 + E5B S_E  (mu0 and theta0 enter linearly).
+enum {
+    EP_G0, EP_GD2, EP_G1, EP_GT2, EP_G2, EP_E3, EP_E4, EP_ET, EP_ED2, EP_E5,
+    EP_GD4, EP_GD2B, EP_G1B, EP_GT4, EP_GT2B, EP_G2B, EP_ET2, EP_ETB, EP_ED4, EP_ED2B, EP_E5B, EP_N
 };
 
 // Per-call constants known on the host (passed by value to every kernel).
@@ -252,26 +265,47 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return r;
 }
 
-// Deterministic block sums of K doubles per thread: a fixed warp-shuffle tree,
-// then the warps' partials summed in warp order.  Thread k < K returns total k
-// (other threads return 0).  sh holds (NT / 32) * K doubles.
+// Deterministic warp sums of K <= 16 doubles per lane by reduce-scatter: at
+// each of the offsets 16, 8, 4, 2 a lane keeps half of its slots (the upper
+// half where that bit of its lane index is set), sends the other half to the
+// partner lane and adds what it receives; the last exchange (offset 1) adds
+// the two halves of the warp.  Lane l returns the total of component l >> 1
+// (meaningful for l >> 1 < K; lanes l and l ^ 1 return the same value).  16
+// FP64 additions per lane instead of 5 K for a butterfly per component: FP64
+// instructions are costly on this part.
+template <int K>
+__device__ __forceinline__ double warp_sum_scatter(const double (&v)[K]) {
+    static_assert(K >= 1 && K <= 16, "at most 16 components");
+    const int lane = threadIdx.x & 31;
+    double a[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a[k] = k < K ? v[k] : 0.0;
+#pragma unroll
+    for (int o = 16, m = 8; o >= 2; o >>= 1, m >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int j = 0; j < m; ++j) {
+            const double send = up ? a[j] : a[j + m];
+            const double keep = up ? a[j + m] : a[j];
+            a[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return a[0] + __shfl_xor_sync(0xffffffffu, a[0], 1);
+}
+
+// Deterministic block sums of K <= 16 doubles per thread: each warp's sums by
+// warp_sum_scatter, then the warps' partials summed in warp order.  Thread
+// k < K returns total k (other threads return 0).  sh holds (NT / 32) * K doubles.
 template <int NT, int K>
-__device__ __forceinline__ double block_sum_multi(double (&v)[K], double *sh) {
+__device__ __forceinline__ double block_sum_multi(const double (&v)[K], double *sh) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
-    }
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) sh[warp * K + k] = v[k];
-    }
+    const double w = warp_sum_scatter<K>(v);
+    if ((lane & 1) == 0 && (lane >> 1) < K) sh[warp * K + (lane >> 1)] = w;
     __syncthreads();
     double r = 0.0;
     if (threadIdx.x < K) {
 #pragma unroll
-        for (int w = 0; w < NT / 32; ++w) r += sh[w * K + threadIdx.x];
+        for (int q = 0; q < NT / 32; ++q) r += sh[q * K + threadIdx.x];
     }
     __syncthreads();
     return r;

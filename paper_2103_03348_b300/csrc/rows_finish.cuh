@@ -81,38 +81,36 @@ __device__ __forceinline__ void epilogue_row(const Consts &c, const Derived &D, 
     if (lam > 0.0) {
         ll = log(lam);
         if (mode >= MODE_GRAD) {
-            // Every ratio is (A or B times a moment) / lambda, multiplied in that order:
-            // A S_G <= lambda and B S_E <= lambda, so nothing overflows however small
-            // lambda is (A / lambda alone can).  Below 1e-300, divide instead of
-            // multiplying by 1 / lambda, which could overflow.
-            const double il = 1.0 / lam;
+            // lambda_n q1 and lambda_n s2 as coefficient x moment sums (Derived::ep),
+            // then divided by lambda_n.  Each numerator is (A or B) x moments of
+            // the size of lambda_n's terms; below 1e-300, where 1 / lambda_n could
+            // overflow, numerators and lambda_n are first scaled by 2^600 (exact).
             const bool tiny = !(lam > 1e-300);
-            auto over = [&](double v) { return tiny ? v / lam : v * il; };
-            const double AG = D.A * SG, BE = D.B * SE;
-            const double AGD2 = D.A * (Mo[MO_GD2] * D.i_sx2), AGT2 = D.A * (Mo[MO_GT2] * D.i_st2);
-            const double BET = D.B * (Mo[MO_ET] * D.i_st), BED2 = D.B * (Mo[MO_ED2] * D.i_sx2);
-            const double ix = D.i_tx, it = D.i_tt, ih = D.i_h;
-            const double ix2 = ix * ix, it2 = it * it, ih2 = ih * ih;
-            q1[0] = over(AG) * D.i_mu0;
-            q1[1] = over(AGD2 * ix2 * ix - 2.0 * AG * ix);
-            q1[2] = D.tt_inf ? 0.0 : over(AGT2 * it2 * it - AG * it);
-            q1[3] = over(BE) * D.i_th0;
-            q1[4] = over(BE * D.i_om - BET);
-            q1[5] = over(BED2 * ih2 * ih - 2.0 * BE * ih);
+            const double il = 1.0 / (tiny ? lam * 0x1p600 : lam);  // before the numerators: fewer live values
+            const double *e = D.ep;
+            double n1[6], n2[6] = {0, 0, 0, 0, 0, 0};
+            n1[0] = e[EP_G0] * SG;
+            n1[1] = e[EP_GD2] * Mo[MO_GD2] - e[EP_G1] * SG;
+            n1[2] = e[EP_GT2] * Mo[MO_GT2] - e[EP_G2] * SG;
+            n1[3] = e[EP_E3] * SE;
+            n1[4] = e[EP_E4] * SE - e[EP_ET] * Mo[MO_ET];
+            n1[5] = e[EP_ED2] * Mo[MO_ED2] - e[EP_E5] * SE;
             if (mode == MODE_HESS) {
-                const double AGD4 = D.A * (Mo[MO_GD4] * D.i_sx2 * D.i_sx2);
-                const double AGT4 = D.A * (Mo[MO_GT4] * D.i_st2 * D.i_st2);
-                const double BET2 = D.B * (Mo[MO_ET2] * D.i_st2), BED4 = D.B * (Mo[MO_ED4] * D.i_sx2 * D.i_sx2);
-                const double ix4 = ix2 * ix2, it4 = it2 * it2, ih4 = ih2 * ih2;
-                double s2[6];
-                s2[0] = 0.0;
-                s2[1] = over(AGD4 * ix4 * ix2 - 7.0 * AGD2 * ix4 + 6.0 * AG * ix2);
-                s2[2] = D.tt_inf ? 0.0 : over(AGT4 * it4 * it2 - 5.0 * AGT2 * it4 + 2.0 * AG * it2);
-                s2[3] = 0.0;
-                s2[4] = over(BET2 - 2.0 * BET * D.i_om);
-                s2[5] = over(BED4 * ih4 * ih2 - 7.0 * BED2 * ih4 + 6.0 * BE * ih2);
+                n2[1] = e[EP_GD4] * Mo[MO_GD4] - e[EP_GD2B] * Mo[MO_GD2] + e[EP_G1B] * SG;
+                n2[2] = e[EP_GT4] * Mo[MO_GT4] - e[EP_GT2B] * Mo[MO_GT2] + e[EP_G2B] * SG;
+                n2[4] = e[EP_ET2] * Mo[MO_ET2] - e[EP_ETB] * Mo[MO_ET];
+                n2[5] = e[EP_ED4] * Mo[MO_ED4] - e[EP_ED2B] * Mo[MO_ED2] + e[EP_E5B] * SE;
+            }
+            if (tiny) {
 #pragma unroll
-                for (int p = 0; p < 6; ++p) q2[p] = s2[p] - q1[p] * q1[p];
+                for (int p = 0; p < 6; ++p) { n1[p] *= 0x1p600; n2[p] *= 0x1p600; }
+            }
+#pragma unroll
+            for (int p = 0; p < 6; ++p) { q1[p] = n1[p] * il; n2[p] *= il; }
+            if (D.tt_inf) q1[2] = 0.0;
+            if (mode == MODE_HESS) {
+#pragma unroll
+                for (int p = 0; p < 6; ++p) q2[p] = n2[p] - q1[p] * q1[p];
                 if (D.tt_inf) q2[2] = 0.0;
             }
         }
@@ -301,15 +299,9 @@ static __device__ __noinline__ void integral_group(const Consts &c, const Inputs
 #pragma unroll
     for (int k = 0; k < NACC; ++k) a[k] = 0.0;
     if (i < c.g.n) integral_row(D, in, ws, i, a);
-#pragma unroll
-    for (int k = 0; k < NACC; ++k) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a[k] += __shfl_xor_sync(0xffffffffu, a[k], o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-        for (int k = 0; k < NACC; ++k) ws.ipart[(size_t)group * ACC_STRIDE + k] = a[k];
-    }
+    const double v = warp_sum_scatter<NACC>(a);
+    const int lane = threadIdx.x & 31;
+    if ((lane & 1) == 0 && (lane >> 1) < NACC) ws.ipart[(size_t)group * ACC_STRIDE + (lane >> 1)] = v;
 }
 
 }  // namespace hk
