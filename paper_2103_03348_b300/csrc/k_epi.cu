@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(Consts c, Workspa
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         for (int k = warp; k < NACC; k += FIN_THREADS / 32) {
             double v = 0.0;
+#pragma unroll 8
             for (int b = lane; b < tiles; b += 32) v += ws.blockpart[(size_t)b * ACC_STRIDE + k];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -185,6 +186,7 @@ __global__ void __launch_bounds__(CB_THREADS) colfinish_kernel(Consts c, Workspa
     if (m >= c.g.n || m >= c.t1 * TILE) return;
     const int npad = c.g.npad;
     double c1 = 0.0, c2 = 0.0;
+#pragma unroll 8
     for (int ch = 0; ch < c.g.n_chunks; ++ch) {
         c1 += ws.colpart[((size_t)ch * 2 + 0) * npad + m];
         if (c.mode == MODE_HESS) c2 += ws.colpart[((size_t)ch * 2 + 1) * npad + m];
@@ -220,6 +222,7 @@ __global__ void __launch_bounds__(CB_THREADS) colfinish_subset_kernel(Consts c, 
     }
     const int npad = c.g.npad, at = by_position ? j : (c.st ? ws.inv[m] : m);
     double c1 = 0.0, c2 = 0.0;
+#pragma unroll 8
     for (int ch = 0; ch < c.g.n_chunks; ++ch) {
         c1 += ws.colpart[((size_t)ch * 2 + 0) * npad + at];
         if (c.mode == MODE_HESS) c2 += ws.colpart[((size_t)ch * 2 + 1) * npad + at];

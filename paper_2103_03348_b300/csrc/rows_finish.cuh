@@ -166,23 +166,32 @@ __device__ __forceinline__ void finish_tile_fp32c(const Consts &c, const Inputs 
     // leading part, the low parts and rounding errors carried in a second
     // float), about 2^-44 relative, and only the total is made FP64: FP64
     // additions cost an SM's FP64 pipe about 19 cycles per warp instruction.
+    // Chunks outer, moments inner: each chunk's loads of all moments are in
+    // flight together (the order of each moment's sum is unchanged).
     const float2 *part = reinterpret_cast<const float2 *>(ws.rowpart);
-    double Mo[NMOM];
+    float hi[NMOM], lo[NMOM];
 #pragma unroll
-    for (int k = 0; k < NMOM; ++k) {
-        float hi = 0.0f, lo = 0.0f;
-        if (valid && row_mom_used(c.mode, k)) {
-            for (int ch = 0; ch < c.g.n_chunks; ++ch) {
-                const float2 v = part[((size_t)ch * NMOM + k) * npad + i];
-                const float s = __fadd_rn(hi, v.x);
-                const float bb = __fsub_rn(s, hi);
-                const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v.x, bb));
-                hi = s;
-                lo = __fadd_rn(lo, __fadd_rn(err, v.y));
+    for (int k = 0; k < NMOM; ++k) { hi[k] = 0.0f; lo[k] = 0.0f; }
+    if (valid) {
+        for (int ch = 0; ch < c.g.n_chunks; ++ch) {
+            float2 v[NMOM];
+#pragma unroll
+            for (int k = 0; k < NMOM; ++k)
+                if (row_mom_used(c.mode, k)) v[k] = part[((size_t)ch * NMOM + k) * npad + i];
+#pragma unroll
+            for (int k = 0; k < NMOM; ++k) {
+                if (!row_mom_used(c.mode, k)) continue;
+                const float s = __fadd_rn(hi[k], v[k].x);
+                const float bb = __fsub_rn(s, hi[k]);
+                const float err = __fadd_rn(__fsub_rn(hi[k], __fsub_rn(s, bb)), __fsub_rn(v[k].x, bb));
+                hi[k] = s;
+                lo[k] = __fadd_rn(lo[k], __fadd_rn(err, v[k].y));
             }
         }
-        Mo[k] = (double)hi + (double)lo;
     }
+    double Mo[NMOM];
+#pragma unroll
+    for (int k = 0; k < NMOM; ++k) Mo[k] = (double)hi[k] + (double)lo[k];
     // rows to redo in FP64, listed in thread order
     const bool tiny = valid && Mo[MO_G] < (double)TINY_ROW && Mo[MO_E] < (double)TINY_ROW;
     const unsigned bal = __ballot_sync(0xffffffffu, tiny);
