@@ -295,6 +295,41 @@ __device__ __forceinline__ unsigned hilbert16(unsigned x, unsigned y) {
 
 constexpr int ORDER_THREADS = 1024;
 
+// The bitonic compare-exchanges of one merge size at strides first_stride,
+// first_stride / 2, ..., 1 (all below 128) on a warp's run of 128 keys, key r
+// of this lane at position base + 32 r + lane.  Position p of a pair (p, p +
+// stride) keeps the smaller key when p's bit `size` is clear (an ascending
+// run), the larger one otherwise.
+__device__ __forceinline__ void sort_warp_run(unsigned long long (&k4)[4], int base, int lane, int size,
+                                              int first_stride) {
+#pragma unroll
+    for (int stride = 64; stride > 0; stride >>= 1) {  // unrolled: the register indices are constants
+        if (stride > first_stride) continue;
+        if (stride >= 32) {  // a lane's own keys r and r + stride / 32
+            const int d = stride >> 5;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                if (r & d) continue;
+                const bool up = ((base + 32 * r + lane) & size) == 0;
+                const unsigned long long a = k4[r], b = k4[r + d];
+                if ((a > b) == up) {
+                    k4[r] = b;
+                    k4[r + d] = a;
+                }
+            }
+        } else {  // lanes l and l ^ stride, the lower one at position p
+            const bool lo = (lane & stride) == 0;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const bool up = ((base + 32 * r + lane) & size) == 0;
+                const unsigned long long o = __shfl_xor_sync(0xffffffffu, k4[r], stride);
+                const unsigned long long mn = k4[r] < o ? k4[r] : o, mx = k4[r] < o ? o : k4[r];
+                k4[r] = (lo == up) ? mn : mx;
+            }
+        }
+    }
+}
+
 // One block per slab: keys (Hilbert index << 32 | slot) sorted ascending in
 // shared memory by a bitonic network; unique keys make the order deterministic.
 __global__ void __launch_bounds__(ORDER_THREADS) order_sort_kernel(Consts c, Inputs in, Workspace ws) {
@@ -317,8 +352,23 @@ __global__ void __launch_bounds__(ORDER_THREADS) order_sort_kernel(Consts c, Inp
         keys[k] = key;
     }
     __syncthreads();
-    for (int size = 2; size <= SLAB_EVENTS; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+    // Bitonic sort.  Compare-exchanges at strides of 128 and more go through
+    // shared memory, one barrier each; the strides below 128 stay inside a
+    // warp's run of 128 keys (key r of lane l at position 128 w + 32 r + l),
+    // in registers: strides 64 and 32 pair a lane's own keys, the smaller
+    // ones pair lanes by shuffles, with no barrier.
+    static_assert(SLAB_EVENTS == ORDER_THREADS * 4, "four keys per thread");
+    const int lane = threadIdx.x & 31, base = (threadIdx.x >> 5) * 128;
+    unsigned long long k4[4];
+    // sizes 2 to 128: whole in the warp
+#pragma unroll
+    for (int r = 0; r < 4; ++r) k4[r] = keys[base + 32 * r + lane];
+    for (int size = 2; size <= 128; size <<= 1) sort_warp_run(k4, base, lane, size, size >> 1);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) keys[base + 32 * r + lane] = k4[r];
+    __syncthreads();
+    for (int size = 256; size <= SLAB_EVENTS; size <<= 1) {
+        for (int stride = size >> 1; stride >= 128; stride >>= 1) {
             for (int q = threadIdx.x; q < SLAB_EVENTS / 2; q += ORDER_THREADS) {
                 const int lo = 2 * q - (q & (stride - 1));
                 const int hi = lo + stride;
@@ -331,6 +381,12 @@ __global__ void __launch_bounds__(ORDER_THREADS) order_sort_kernel(Consts c, Inp
             }
             __syncthreads();
         }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) k4[r] = keys[base + 32 * r + lane];
+        sort_warp_run(k4, base, lane, size, 64);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) keys[base + 32 * r + lane] = k4[r];
+        __syncthreads();
     }
     for (int k = threadIdx.x; k < cnt; k += ORDER_THREADS) ws.perm[e0 + k] = e0 + (int)(keys[k] & 0xffffffffu);
 }
