@@ -173,6 +173,7 @@ __device__ __forceinline__ void finish_tile_fp32c(const Consts &c, const Inputs 
 #pragma unroll
     for (int k = 0; k < NMOM; ++k) { hi[k] = 0.0f; lo[k] = 0.0f; }
     if (valid) {
+#pragma unroll 2
         for (int ch = 0; ch < c.g.n_chunks; ++ch) {
             float2 v[NMOM];
 #pragma unroll
