@@ -300,8 +300,7 @@ constexpr int ORDER_THREADS = 1024;
 // of this lane at position base + 32 r + lane.  Position p of a pair (p, p +
 // stride) keeps the smaller key when p's bit `size` is clear (an ascending
 // run), the larger one otherwise.
-__device__ __forceinline__ void sort_warp_run(unsigned long long (&k4)[4], int base, int lane, int size,
-                                              int first_stride) {
+__device__ __forceinline__ void sort_warp_run(unsigned (&k4)[4], int base, int lane, int size, int first_stride) {
 #pragma unroll
     for (int stride = 64; stride > 0; stride >>= 1) {  // unrolled: the register indices are constants
         if (stride > first_stride) continue;
@@ -311,7 +310,7 @@ __device__ __forceinline__ void sort_warp_run(unsigned long long (&k4)[4], int b
             for (int r = 0; r < 4; ++r) {
                 if (r & d) continue;
                 const bool up = ((base + 32 * r + lane) & size) == 0;
-                const unsigned long long a = k4[r], b = k4[r + d];
+                const unsigned a = k4[r], b = k4[r + d];
                 if ((a > b) == up) {
                     k4[r] = b;
                     k4[r + d] = a;
@@ -322,19 +321,22 @@ __device__ __forceinline__ void sort_warp_run(unsigned long long (&k4)[4], int b
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const bool up = ((base + 32 * r + lane) & size) == 0;
-                const unsigned long long o = __shfl_xor_sync(0xffffffffu, k4[r], stride);
-                const unsigned long long mn = k4[r] < o ? k4[r] : o, mx = k4[r] < o ? o : k4[r];
+                const unsigned o = __shfl_xor_sync(0xffffffffu, k4[r], stride);
+                const unsigned mn = min(k4[r], o), mx = max(k4[r], o);
                 k4[r] = (lo == up) ? mn : mx;
             }
         }
     }
 }
 
-// One block per slab: keys (Hilbert index << 32 | slot) sorted ascending in
-// shared memory by a bitonic network; unique keys make the order deterministic.
+// One block per slab: 32-bit keys (the top 20 bits of the Hilbert index, a
+// 1024 x 1024 grid over the bounding square, then the 12-bit slot) sorted
+// ascending in shared memory by a bitonic network; unique keys make the order
+// deterministic, events of one cell keeping their time order.
 __global__ void __launch_bounds__(ORDER_THREADS) order_sort_kernel(Consts c, Inputs in, Workspace ws) {
     pdl_wait();
-    __shared__ unsigned long long keys[SLAB_EVENTS];
+    static_assert(SLAB_EVENTS == 4096, "12-bit slots");
+    __shared__ unsigned keys[SLAB_EVENTS];
     const int n = c.g.n;
     const int e0 = blockIdx.x * SLAB_EVENTS;
     const int cnt = min(n - e0, SLAB_EVENTS);
@@ -342,12 +344,12 @@ __global__ void __launch_bounds__(ORDER_THREADS) order_sort_kernel(Consts c, Inp
     const double span = fmax(x1 - x0, y1 - y0);  // one scale for both axes: square cells
     const double sc = (isfinite(span) && span > 0.0) ? 65535.0 / span : 0.0;
     for (int k = threadIdx.x; k < SLAB_EVENTS; k += ORDER_THREADS) {
-        unsigned long long key = ~0ULL;  // empty slots sort last
+        unsigned key = ~0u;  // empty slots sort last (a full slab has none; below 4096 events slots stay < 4095)
         if (k < cnt) {
             // fmax / fmin map NaN to the bound, so non-finite inputs (reported by prep) stay in range
             const unsigned ix = (unsigned)fmin(fmax((in.x[e0 + k] - x0) * sc, 0.0), 65535.0);
             const unsigned iy = (unsigned)fmin(fmax((in.y[e0 + k] - y0) * sc, 0.0), 65535.0);
-            key = ((unsigned long long)hilbert16(ix, iy) << 32) | (unsigned)k;
+            key = ((hilbert16(ix, iy) >> 12) << 12) | (unsigned)k;
         }
         keys[k] = key;
     }
@@ -359,7 +361,7 @@ __global__ void __launch_bounds__(ORDER_THREADS) order_sort_kernel(Consts c, Inp
     // ones pair lanes by shuffles, with no barrier.
     static_assert(SLAB_EVENTS == ORDER_THREADS * 4, "four keys per thread");
     const int lane = threadIdx.x & 31, base = (threadIdx.x >> 5) * 128;
-    unsigned long long k4[4];
+    unsigned k4[4];
     // sizes 2 to 128: whole in the warp
 #pragma unroll
     for (int r = 0; r < 4; ++r) k4[r] = keys[base + 32 * r + lane];
@@ -373,7 +375,7 @@ __global__ void __launch_bounds__(ORDER_THREADS) order_sort_kernel(Consts c, Inp
                 const int lo = 2 * q - (q & (stride - 1));
                 const int hi = lo + stride;
                 const bool up = (lo & size) == 0;
-                const unsigned long long a = keys[lo], b = keys[hi];
+                const unsigned a = keys[lo], b = keys[hi];
                 if ((a > b) == up) {
                     keys[lo] = b;
                     keys[hi] = a;
@@ -388,7 +390,7 @@ __global__ void __launch_bounds__(ORDER_THREADS) order_sort_kernel(Consts c, Inp
         for (int r = 0; r < 4; ++r) keys[base + 32 * r + lane] = k4[r];
         __syncthreads();
     }
-    for (int k = threadIdx.x; k < cnt; k += ORDER_THREADS) ws.perm[e0 + k] = e0 + (int)(keys[k] & 0xffffffffu);
+    for (int k = threadIdx.x; k < cnt; k += ORDER_THREADS) ws.perm[e0 + k] = e0 + (int)(keys[k] & 0xfffu);
 }
 
 // Position-order copies of the events and of prep's per-event indices.
