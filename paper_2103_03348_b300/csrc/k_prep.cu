@@ -41,7 +41,6 @@ __global__ void __launch_bounds__(TILE) prep_kernel(Consts c, Inputs in, Workspa
     pdl_wait();
     const int n = c.g.n;
     const int i = blockIdx.x * TILE + threadIdx.x;
-    __shared__ double sh[TILE];
     __shared__ bool last;
     int bad = 0;
     double xi = 0.0, yi = 0.0;
@@ -51,12 +50,18 @@ __global__ void __launch_bounds__(TILE) prep_kernel(Consts c, Inputs in, Workspa
         yi = in.y[i];
         const double ti = in.t[i];
         if (!isfinite(xi) || !isfinite(yi) || !isfinite(ti)) bad |= ST_NONFINITE;  // r: checked by pack
-        if (i > 0 && !(in.t[i - 1] <= ti)) bad |= ST_UNSORTED;
-        // tie-group start: first index j <= i with t_j == t_i (lower bound on a sorted prefix)
-        int lo = 0, hi = i;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (in.t[mid] < ti) lo = mid + 1; else hi = mid;
+        const double tp = i > 0 ? in.t[i - 1] : -INFINITY;
+        if (i > 0 && !(tp <= ti)) bad |= ST_UNSORTED;
+        // tie-group start: first index j <= i with t_j == t_i (lower bound on a
+        // sorted prefix); i itself when the previous time is smaller, the usual case
+        int lo = i;
+        if (i > 0 && !(tp < ti)) {
+            lo = 0;
+            int hi = i;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (in.t[mid] < ti) lo = mid + 1; else hi = mid;
+            }
         }
         ws.gidx[i] = lo;
         // exact-location group: -0.0 and +0.0 are the same location
@@ -82,45 +87,28 @@ __global__ void __launch_bounds__(TILE) prep_kernel(Consts c, Inputs in, Workspa
         atomicOr(ws.evbits, bad);  // kept for calls that reuse these events
     }
 
-    // per-tile bounds of x and y (valid events only)
+    // per-tile bounds of x and y (valid events only): warp shuffles, then the
+    // four warps' bounds in shared memory (min and max are exact in any order)
     double4_32a box;
     {
-        double v = valid ? xi : INFINITY;
-        sh[threadIdx.x] = v;
-        __syncthreads();
-        for (int w = TILE / 2; w > 0; w >>= 1) {
-            if (threadIdx.x < w) sh[threadIdx.x] = fmin(sh[threadIdx.x], sh[threadIdx.x + w]);
-            __syncthreads();
+        double bx0 = valid ? xi : INFINITY, bx1 = valid ? xi : -INFINITY;
+        double by0 = valid ? yi : INFINITY, by1 = valid ? yi : -INFINITY;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            bx0 = fmin(bx0, __shfl_xor_sync(0xffffffffu, bx0, o));
+            bx1 = fmax(bx1, __shfl_xor_sync(0xffffffffu, bx1, o));
+            by0 = fmin(by0, __shfl_xor_sync(0xffffffffu, by0, o));
+            by1 = fmax(by1, __shfl_xor_sync(0xffffffffu, by1, o));
         }
-        box.x = sh[0];
+        __shared__ double4_32a wbox[TILE / 32];
+        if ((threadIdx.x & 31) == 0) wbox[threadIdx.x >> 5] = make_double4_32a(bx0, bx1, by0, by1);
         __syncthreads();
-        v = valid ? xi : -INFINITY;
-        sh[threadIdx.x] = v;
-        __syncthreads();
-        for (int w = TILE / 2; w > 0; w >>= 1) {
-            if (threadIdx.x < w) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + w]);
-            __syncthreads();
+        box = wbox[0];
+#pragma unroll
+        for (int w = 1; w < TILE / 32; ++w) {
+            const double4_32a b = wbox[w];
+            box = make_double4_32a(fmin(box.x, b.x), fmax(box.y, b.y), fmin(box.z, b.z), fmax(box.w, b.w));
         }
-        box.y = sh[0];
-        __syncthreads();
-        v = valid ? yi : INFINITY;
-        sh[threadIdx.x] = v;
-        __syncthreads();
-        for (int w = TILE / 2; w > 0; w >>= 1) {
-            if (threadIdx.x < w) sh[threadIdx.x] = fmin(sh[threadIdx.x], sh[threadIdx.x + w]);
-            __syncthreads();
-        }
-        box.z = sh[0];
-        __syncthreads();
-        v = valid ? yi : -INFINITY;
-        sh[threadIdx.x] = v;
-        __syncthreads();
-        for (int w = TILE / 2; w > 0; w >>= 1) {
-            if (threadIdx.x < w) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + w]);
-            __syncthreads();
-        }
-        box.w = sh[0];
-        __syncthreads();
     }
     if (threadIdx.x == 0) {
         ws.tbox[blockIdx.x] = box;
