@@ -145,3 +145,63 @@ def simulate(rng, parent, length, root_var, sigma2, n_draws):
             continue
         val[:, v] = val[:, parent[v]] + np.sqrt(sigma2 * length[v]) * rng.standard_normal(n_draws)
     return val[:, :m]
+
+
+# ---------------------------------------------------------------------------
+# Tree-structured HMC mass matrix on the rate block (Section 2.3.2's
+# preconditioner with the phylogenetic prior's full precision, Eq. 2):
+#     M = diag(1 / minv) outside [z0, z0 + m),  M_z = diag(d) + (sigma2 V)^-1.
+# Dense algebra from these definitions, no tree recursion.
+# ---------------------------------------------------------------------------
+def brownian_from_normals(parent, length, root_var, sigma2, xi_nodes):
+    """The Brownian motion down the tree (Section 2.2) driven by the given node
+    normals: root = sqrt(sigma2 root_var) xi[root], child = parent +
+    sqrt(sigma2 length) xi[child].  Written as path sums: the value at a node
+    is the root's term plus the terms of every branch on its root path.
+    Returns the values at all 2M-1 nodes."""
+    parent = np.asarray(parent, np.int64)
+    length = np.asarray(length, float)
+    xi = np.asarray(xi_nodes, float)
+    root = int(np.flatnonzero(parent < 0)[0])
+    base = np.sqrt(sigma2 * root_var) * xi[root]
+    return np.array([base + sum(np.sqrt(sigma2 * length[e]) * xi[e] for e in root_path(parent, v))
+                     for v in range(parent.size)])
+
+
+def mass_velocity(d, p_z, parent, length, root_var, sigma2):
+    """(diag(d) + C^-1)^-1 p_z with C = sigma2 V, by the Woodbury identity
+        (D + C^-1)^-1 = C - C D^1/2 (I + D^1/2 C D^1/2)^-1 D^1/2 C,
+    which never inverts V: on coalescent trees V's condition number reaches
+    ~1e9, so forming C^-1 in FP64 would lose the digits that the comparison
+    needs, while I + D^1/2 C D^1/2 stays well conditioned for moderate d.
+    Negative d entries count as 0."""
+    C = sigma2 * tree_cov(parent, length, root_var)
+    s = np.sqrt(np.maximum(np.asarray(d, float), 0.0))
+    Cp = C @ np.asarray(p_z, float)
+    K = np.eye(s.size) + s[:, None] * C * s[None, :]
+    return Cp - C @ (s * np.linalg.solve(K, s * Cp))
+
+
+def mass_full_velocity(minv, d, p, z0, parent, length, root_var, sigma2):
+    """M^-1 p for the whole state: minv * p outside the rate block."""
+    p = np.asarray(p, float)
+    v = np.asarray(minv, float) * p
+    m = (np.asarray(parent).size + 1) // 2
+    v[z0:z0 + m] = mass_velocity(d, p[z0:z0 + m], parent, length, root_var, sigma2)
+    return v
+
+
+def mass_momentum(minv, d, xi, z0, parent, length, root_var, sigma2):
+    """The momentum p = A xi with A A^T = M: p_i = xi_i / sqrt(minv_i) outside
+    the block; p_z = sqrt(d) xi_z + (sigma2 V)^-1 w inside, w the Brownian
+    motion driven by xi[k:] (Cov w = sigma2 V, so Cov((sigma2 V)^-1 w) =
+    (sigma2 V)^-1).  (sigma2 V)^-1 w comes from the long-double dense prior."""
+    minv = np.asarray(minv, float)
+    xi = np.asarray(xi, float)
+    k = minv.size
+    m = (np.asarray(parent).size + 1) // 2
+    p = xi[:k] / np.sqrt(minv)
+    w = brownian_from_normals(parent, length, root_var, sigma2, xi[k:])[:m]
+    _, pw, _ = tree_prior(w, parent, length, root_var, sigma2)
+    p[z0:z0 + m] = np.sqrt(np.maximum(np.asarray(d, float), 0.0)) * xi[z0:z0 + m] + pw
+    return p

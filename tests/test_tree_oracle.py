@@ -163,3 +163,84 @@ def test_plan_size_and_bounds(tree_mod):
                                ctypes.c_void_p(8), ctypes.c_size_t(1 << 20), None, None, None, None) == 1
     assert L.hawkes_tree_prior(1, ctypes.c_void_p(8), ctypes.c_void_p(8), 0.0, 1.0, ctypes.c_void_p(8),
                                ctypes.c_void_p(8), ctypes.c_size_t(1 << 20), None, None, None, None) == 1
+
+
+# ---------------------------------------------------------------------------
+# Tree-structured mass matrix oracle (M_z = diag(d) + (sigma2 V)^-1)
+# ---------------------------------------------------------------------------
+def random_tree(rng, m, lo=0.2, hi=1.0):
+    """A random rooted binary tree on m tips by joining random pairs, with
+    branch lengths uniform on [lo, hi] (well conditioned V)."""
+    parent = -np.ones(2 * m - 1, np.int64)
+    live = list(range(m))
+    nxt = m
+    while len(live) > 1:
+        i, j = rng.choice(len(live), 2, replace=False)
+        a, b = live[i], live[j]
+        parent[a] = parent[b] = nxt
+        live = [v for k, v in enumerate(live) if k not in (i, j)] + [nxt]
+        nxt += 1
+    length = rng.uniform(lo, hi, 2 * m - 1)
+    length[nxt - 1] = 0.0
+    return parent, length
+
+
+def test_mass_velocity_two_tip_closed_form():
+    parent, length = np.array([2, 2, -1]), np.array([0.8, 1.5, 0.0])
+    a, b, tau0, s2 = 0.8, 1.5, 0.6, 2.5
+    d = np.array([1.3, 0.4])
+    pz = np.array([0.7, -2.0])
+    # (sigma2 V)^-1 by the 2 x 2 adjugate, then diag(d) + P inverted the same way
+    det_v = s2 * s2 * ((tau0 + a) * (tau0 + b) - tau0 * tau0)
+    P = np.array([[tau0 + b, -tau0], [-tau0, tau0 + a]]) * s2 / det_v
+    Mz = np.diag(d) + P
+    det_m = Mz[0, 0] * Mz[1, 1] - Mz[0, 1] * Mz[1, 0]
+    want = np.array([Mz[1, 1] * pz[0] - Mz[0, 1] * pz[1], -Mz[1, 0] * pz[0] + Mz[0, 0] * pz[1]]) / det_m
+    got = tree_oracle.mass_velocity(d, pz, parent, length, tau0, s2)
+    np.testing.assert_allclose(got, want, rtol=1e-14)
+
+
+@pytest.mark.parametrize("root_var", [0.0, 0.4])
+def test_mass_velocity_equals_the_plain_solve(root_var):
+    rng = np.random.default_rng(41)
+    parent, length = random_tree(rng, 24)
+    s2 = 1.7
+    d = rng.uniform(0.0, 3.0, 24)
+    d[::5] = 0.0
+    pz = rng.standard_normal(24)
+    C = s2 * tree_oracle.tree_cov(parent, length, root_var)
+    want = np.linalg.solve(np.diag(d) + np.linalg.inv(C), pz)
+    got = tree_oracle.mass_velocity(d, pz, parent, length, root_var, s2)
+    np.testing.assert_allclose(got, want, rtol=1e-11, atol=1e-12 * np.abs(want).max())
+    # no curvature: the velocity is the prior covariance times p
+    np.testing.assert_allclose(tree_oracle.mass_velocity(-np.ones(24), pz, parent, length, root_var, s2), C @ pz,
+                               rtol=1e-13, atol=1e-13 * np.abs(C @ pz).max())
+
+
+def test_brownian_from_normals_has_the_tree_covariance():
+    rng = np.random.default_rng(42)
+    parent, length = random_tree(rng, 9)
+    tau0, s2 = 0.3, 1.9
+    nn = parent.size
+    # the map xi -> w is linear: its columns from unit vectors give S with S S^T = Cov(w)
+    S = np.stack([tree_oracle.brownian_from_normals(parent, length, tau0, s2, e)[:9] for e in np.eye(nn)], axis=1)
+    np.testing.assert_allclose(S @ S.T, s2 * tree_oracle.tree_cov(parent, length, tau0), rtol=1e-13, atol=1e-14)
+
+
+def test_mass_momentum_covariance_is_the_mass_matrix():
+    rng = np.random.default_rng(43)
+    m, z0, k = 7, 3, 12
+    parent, length = random_tree(rng, m)
+    tau0, s2 = 0.2, 0.8
+    minv = rng.uniform(0.1, 2.0, k)
+    d = rng.uniform(0.0, 2.0, m)
+    d[1] = 0.0
+    cols = [tree_oracle.mass_momentum(minv, d, e, z0, parent, length, tau0, s2) for e in np.eye(k + parent.size)]
+    A = np.stack(cols, axis=1)
+    M = np.diag(1.0 / minv)
+    M[z0:z0 + m, z0:z0 + m] = np.diag(d) + tree_oracle.precision_matrix(parent, length, tau0, s2)
+    np.testing.assert_allclose(A @ A.T, M, rtol=1e-10, atol=1e-12 * np.abs(M).max())
+    # and the velocity inverts that same M
+    p = rng.standard_normal(k)
+    np.testing.assert_allclose(M @ tree_oracle.mass_full_velocity(minv, d, p, z0, parent, length, tau0, s2), p,
+                               rtol=1e-10, atol=1e-11)
