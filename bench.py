@@ -12,6 +12,7 @@ It prints one JSON line:
   roofline  the row pass (dominant kernel) against the FP32 pipe (ALU bound)
   cpu_baseline  the FP64 oracle on this host's cores, on a bounded sample of rows
   hmc       ESS/s of a short preconditioned HMC chain on the 23,422-event workload
+  hmc_tree_mass  the same chain with the tree-structured mass on the log-rates
   predictive  posterior-predictive simulation 30 days ahead of that workload
             for 4,096 parameter settings (draws/s)
 
@@ -355,14 +356,18 @@ def run_ours(args, rank, world, local_rank):
     # events, 1,610 free log-rates, 20 leapfrog steps, 2,000 iterations after
     # 200 of warm-up, mass from the Hessian diagonal every 100), on space-time
     # tiles; about 12 s
-    hmc_summary = None
+    hmc_summary = hmc_tree_summary = None
     if not args.no_hmc:
         from paper_2103_03348_b300 import run_hmc
         h = run_hmc.run("fp32c_st", iters=args.hmc_iters, warmup=args.hmc_warmup, device=str(dev))
-        hmc_summary = {k: h[k] for k in ("workload", "n_events", "n_rates", "precision", "iters", "warmup",
-                                         "leapfrog_steps",
-                                         "accept_rate", "sampling_seconds", "ms_per_gradient",
-                                         "ess_globals", "ess_rates", "ess_per_s_globals", "ess_per_s_rates")}
+        keys = ("workload", "n_events", "n_rates", "precision", "mass", "iters", "warmup", "leapfrog_steps",
+                "accept_rate", "sampling_seconds", "ms_per_gradient",
+                "ess_globals", "ess_rates", "ess_per_s_globals", "ess_per_s_rates")
+        hmc_summary = {k: h[k] for k in keys}
+        # the same chain with the tree-structured mass on the rates (the prior's
+        # full precision plus the likelihood's curvature); about 13 s more
+        h = run_hmc.run("fp32c_st", iters=args.hmc_iters, warmup=args.hmc_warmup, device=str(dev), mass="tree")
+        hmc_tree_summary = {k: h[k] for k in keys}
 
     pred_summary = None if args.no_predictive else predictive_bench(dev, stream)
     from paper_2103_03348_b300 import peaks
@@ -428,6 +433,7 @@ def run_ours(args, rank, world, local_rank):
                           "speedup_fp32c_over_fp64": float(np.mean(fp64_ms)) / ms},
         "wall_s_timed_region": wall,
         "hmc": hmc_summary,
+        "hmc_tree_mass": hmc_tree_summary,
         "predictive": pred_summary,
     }
     print(json.dumps(line), flush=True)

@@ -373,6 +373,47 @@ int hawkes_posterior_tree(int64_t n, int64_t m, const int *seq_idx, const int *p
                           size_t ws_bytes, double *logpost, double *grad_q, double *hdiag_q, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Tree-structured HMC mass matrix (Section 2.3.2 preconditions the leapfrog
+ * with a diagonal mass from the Hessian; this widens the rate block to the
+ * phylogenetic prior's full precision, Section 2.2 Eq. 2, applied in O(m) on
+ * the tree like Section 2.3.1's dynamic programme).  For a k-dimensional
+ * sampler state whose coordinates [z0, z0 + m) are the sequenced log-rates
+ * (tip j of the tree = coordinate z0 + j):
+ *     M = diag(1 / minv)                       outside the block,
+ *     M_z = diag(d) + (sigma^2 V)^-1           on the block,
+ * with d[m] >= 0 the likelihood's curvature on the rates (entries below 0
+ * or NaN count as 0).  V, plan, length, root_var and sigma2 are as for
+ * hawkes_tree_prior; all arrays are DEVICE memory, enqueued on stream; one
+ * block; no allocation.  Bad scalars, NULL inputs or z0 + m > k give
+ * HAWKES_EINVAL, a short ws HAWKES_EWORKSPACE; a plan built for another m
+ * makes every output NaN.
+ * ------------------------------------------------------------------------ */
+
+/* Bytes of DEVICE workspace the two calls below need for m tips. */
+size_t hawkes_tree_mass_workspace_size(int64_t m);
+
+/* Velocity M^-1 p by one upward and one downward sweep of the tree:
+ *   p        DEVICE double[k], the momentum
+ *   vel      DEVICE double[k] or NULL: M^-1 p
+ *   q        DEVICE double[k] or NULL: the leapfrog position step q += eps M^-1 p
+ *   kinetic  DEVICE double[1] or NULL: p^T M^-1 p / 2
+ * At least one of vel, q, kinetic must be given. */
+int hawkes_tree_mass_velocity(int64_t m, const int *plan, const double *length, double root_var, double sigma2,
+                              const double *dlik, int64_t k, int64_t z0, const double *minv, const double *p,
+                              double *vel, double *q, double eps, double *kinetic, void *ws, size_t ws_bytes,
+                              void *stream);
+
+/* A momentum p ~ N(0, M) (DEVICE double[k]) from standard normals xi (DEVICE
+ * double[k + 2m - 1]): p_i = xi_i / sqrt(minv_i) outside the block and
+ * p_z = sqrt(d) xi_z + (sigma^2 V)^-1 w inside, where w is the Brownian motion
+ * down the tree driven by the node normals xi[k + v] (v = 0..2m-2 in the
+ * tree's node numbering): w_root = sqrt(sigma2 root_var) xi[k + root] and
+ * w_v = w_parent + sqrt(sigma2 length_v) xi[k + v]. */
+int hawkes_tree_mass_momentum(int64_t m, const int *plan, const double *length, double root_var, double sigma2,
+                              const double *dlik, int64_t k, int64_t z0, const double *minv, const double *xi,
+                              double *p, void *ws, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
  * Posterior-predictive simulation (the forward simulation proposed in the
  * paper's Discussion: exact simulation of the Hawkes process with exponential
  * temporal trigger, run in parallel over posterior parameter settings with

@@ -197,6 +197,227 @@ cudaError_t launch_tree_prior(int64_t m, const int *plan, const double *len, dou
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Tree-structured HMC mass matrix on the sequenced log-rates (Section 2.3.2's
+// preconditioner, widened from a diagonal to the phylogenetic prior's full
+// precision).  Inside the rate block [z0, z0 + m) of a k-dimensional state
+//     M_z = diag(d) + (sigma^2 V)^-1,     d >= 0 (the likelihood's curvature),
+// and M = diag(1 / minv) elsewhere.  M_z^-1 p is the posterior mean of the
+// tips of a Brownian motion on the tree (prior N(0, sigma^2 V)) that receives
+// Gaussian evidence in information form, precision d_i and information p_i,
+// at tip i.  One upward sweep folds each node's evidence into a message to its
+// parent across the branch of variance s = sigma^2 len:
+//     J_v = d_v (tip) or J'_a + J'_b,   h_v = p_v (tip) or h'_a + h'_b,
+//     r_v = 1 / (1 + s_v J_v),  J'_v = J_v r_v,  h'_v = h_v r_v,
+// (the root's branch is the root variance, s = sigma^2 root_var, to a parent
+// fixed at 0); the downward sweep gives the means
+//     X_root = s_root h_root r_root,   X_c = (X_parent + s_c h_c) r_c,
+// and X at the tips is M_z^-1 p.  1 + s J >= 1, so the sweeps stay well
+// conditioned however small the branches (V's condition number reaches ~1e9
+// on coalescent trees).  One reciprocal per node.
+constexpr int TMASS_SMEM_MAX_TIPS = 2048;
+
+__host__ __device__ inline size_t tmass_smem_bytes(int64_t m) {
+    // 5 doubles (J / X, h, r, own h, length) and 2 ints (children) per node,
+    // then the level order (m - 1) and the level offsets (at most m)
+    return (size_t)(2 * m - 1) * (5 * sizeof(double) + 2 * sizeof(int)) + (size_t)(2 * m) * sizeof(int) + 64;
+}
+
+template <bool STAGED>
+__global__ void __launch_bounds__(TREE_THREADS)
+    tree_mass_velocity_kernel(int64_t m_arg, const int *__restrict__ plan, const double *__restrict__ len_g,
+                              double tau0, double sigma2, const double *__restrict__ dlik, int64_t k, int64_t z0,
+                              const double *__restrict__ minv, const double *__restrict__ p, double *__restrict__ vel,
+                              double *__restrict__ q, double eps, double *__restrict__ kinetic, double *J, double *H,
+                              double *R, double *HA) {
+    pdl_wait();
+    extern __shared__ __align__(16) unsigned char tree_smem[];
+    __shared__ double sh[TREE_THREADS];
+    TreePlan T = tree_plan_view(plan);
+    const int m = T.m;
+    if ((int64_t)m != m_arg || T.levels < 1 || T.levels > m - 1) {  // a plan for another tree: touch no scratch
+        for (int64_t i = threadIdx.x; i < k; i += TREE_THREADS) {
+            if (vel) vel[i] = NAN;
+            if (q) q[i] = NAN;
+        }
+        if (kinetic && threadIdx.x == 0) *kinetic = NAN;
+        return;
+    }
+    const int nn = 2 * m - 1;
+    const double *len = len_g;
+    if (STAGED) {
+        double *base = reinterpret_cast<double *>(tree_smem);
+        J = base;
+        H = J + nn;
+        R = H + nn;
+        HA = R + nn;
+        double *len_s = HA + nn;
+        int *ca = reinterpret_cast<int *>(len_s + nn), *cb = ca + nn, *order = cb + nn, *offs = order + (m - 1);
+        for (int v = threadIdx.x; v < nn; v += TREE_THREADS) {
+            len_s[v] = len_g[v];
+            ca[v] = T.ca[v];
+            cb[v] = T.cb[v];
+        }
+        for (int j = threadIdx.x; j < m - 1; j += TREE_THREADS) order[j] = T.order[j];
+        for (int j = threadIdx.x; j <= T.levels; j += TREE_THREADS) offs[j] = T.offs[j];
+        len = len_s;
+        T.ca = ca;
+        T.cb = cb;
+        T.order = order;
+        T.offs = offs;
+        __syncthreads();
+    }
+    double kin = 0.0;
+    // coordinates outside the rate block: the diagonal mass
+    for (int64_t i = threadIdx.x; i < k; i += TREE_THREADS) {
+        if (i >= z0 && i < z0 + m) continue;
+        const double v = minv[i] * p[i];
+        if (vel) vel[i] = v;
+        if (q) q[i] += eps * v;
+        kin += p[i] * v;
+    }
+    // tips: evidence (d_i, p_i) and its message across the tip's branch
+    for (int i = threadIdx.x; i < m; i += TREE_THREADS) {
+        const double dv = dlik[i];
+        const double d = dv > 0.0 ? dv : 0.0;  // negative or NaN curvature counts as none
+        const double h = p[z0 + i];
+        const double r = 1.0 / fma(sigma2 * len[i], d, 1.0);
+        J[i] = d * r;
+        H[i] = h * r;
+        R[i] = r;
+        HA[i] = h;
+    }
+    __syncthreads();
+    const int root = T.order[m - 2];
+    for (int L = 0; L < T.levels; ++L) {
+        for (int j = T.offs[L] + threadIdx.x; j < T.offs[L + 1]; j += TREE_THREADS) {
+            const int v = T.order[j], a = T.ca[v], b = T.cb[v];
+            const double Jv = J[a] + J[b], hv = H[a] + H[b];
+            const double s = sigma2 * (v == root ? tau0 : len[v]);
+            const double r = 1.0 / fma(s, Jv, 1.0);
+            J[v] = Jv * r;
+            H[v] = hv * r;
+            R[v] = r;
+            HA[v] = hv;
+        }
+        __syncthreads();
+    }
+    // downward: the means X overwrite the messages J (no longer needed)
+    if (threadIdx.x == 0) J[root] = sigma2 * tau0 * HA[root] * R[root];
+    __syncthreads();
+    for (int L = T.levels - 1; L >= 0; --L) {
+        for (int j = T.offs[L] + threadIdx.x; j < T.offs[L + 1]; j += TREE_THREADS) {
+            const int v = T.order[j], a = T.ca[v], b = T.cb[v];
+            const double xv = J[v];
+            J[a] = fma(sigma2 * len[a], HA[a], xv) * R[a];
+            J[b] = fma(sigma2 * len[b], HA[b], xv) * R[b];
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < m; i += TREE_THREADS) {
+        const double v = J[i];
+        if (vel) vel[z0 + i] = v;
+        if (q) q[z0 + i] += eps * v;
+        kin += p[z0 + i] * v;
+    }
+    if (kinetic) {
+        kin = block_sum<TREE_THREADS>(kin, sh);
+        if (threadIdx.x == 0) *kinetic = 0.5 * kin;
+    }
+}
+
+// Momentum p ~ N(0, M) from standard normals xi[k + 2m - 1]: outside the block
+// p_i = xi_i / sqrt(minv_i); inside, p_z = sqrt(d) xi_z + (sigma^2 V)^-1 w with
+// w ~ N(0, sigma^2 V) the Brownian motion down the tree driven by the node
+// normals xi[k + v] (root: sqrt(sigma^2 root_var) xi; child: parent +
+// sqrt(sigma^2 len) xi), so that Cov(p_z) = diag(d) + (sigma^2 V)^-1.  This
+// kernel writes the first part and w; the prior kernel then applies
+// (sigma^2 V)^-1 to w, and tree_mass_add_kernel adds it.
+__global__ void __launch_bounds__(TREE_THREADS)
+    tree_brownian_kernel(int64_t m_arg, const int *__restrict__ plan, const double *__restrict__ len,
+                         double tau0, double sigma2, const double *__restrict__ dlik, int64_t k, int64_t z0,
+                         const double *__restrict__ minv, const double *__restrict__ xi, double *__restrict__ p,
+                         double *__restrict__ w) {
+    pdl_wait();
+    const TreePlan T = tree_plan_view(plan);
+    const int m = T.m;
+    const bool bad = (int64_t)m != m_arg || T.levels < 1 || T.levels > m - 1;
+    for (int64_t i = threadIdx.x; i < k; i += TREE_THREADS) {
+        if (bad) {
+            p[i] = NAN;
+        } else if (i >= z0 && i < z0 + m) {
+            const double dv = dlik[i - z0];
+            p[i] = sqrt(dv > 0.0 ? dv : 0.0) * xi[i];
+        } else {
+            p[i] = xi[i] * rsqrt(minv[i]);
+        }
+    }
+    if (bad) {
+        for (int64_t i = threadIdx.x; i < m_arg; i += TREE_THREADS) w[i] = NAN;
+        return;
+    }
+    const double *xn = xi + k;
+    const int root = T.order[m - 2];
+    if (threadIdx.x == 0) w[root] = sqrt(sigma2 * tau0) * xn[root];
+    __syncthreads();
+    for (int L = T.levels - 1; L >= 0; --L) {
+        for (int j = T.offs[L] + threadIdx.x; j < T.offs[L + 1]; j += TREE_THREADS) {
+            const int v = T.order[j], a = T.ca[v], b = T.cb[v];
+            const double wv = w[v];
+            w[a] = fma(sqrt(sigma2 * len[a]), xn[a], wv);
+            w[b] = fma(sqrt(sigma2 * len[b]), xn[b], wv);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void tree_mass_add_kernel(int64_t m, int64_t z0, const double *__restrict__ pw, double *__restrict__ p) {
+    pdl_wait();
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < m) p[z0 + i] += pw[i];
+}
+
+cudaError_t launch_tree_mass_velocity(int64_t m, const int *plan, const double *len, double tau0, double sigma2,
+                                      const double *dlik, int64_t k, int64_t z0, const double *minv, const double *p,
+                                      double *vel, double *q, double eps, double *kinetic, double *scratch,
+                                      cudaStream_t s) {
+    const int64_t nn = 2 * m - 1;
+    double *J = scratch, *H = J + nn, *R = H + nn, *HA = R + nn;
+    if (m <= TMASS_SMEM_MAX_TIPS) {
+        static int attr_set[64] = {0};  // per-device opt-in, set on the first (eager) launch
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return cudaGetLastError();
+        if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+            const cudaError_t e = cudaFuncSetAttribute(tree_mass_velocity_kernel<true>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)tmass_smem_bytes(TMASS_SMEM_MAX_TIPS));
+            if (e != cudaSuccess) return e;
+            if (dev >= 0 && dev < 64) attr_set[dev] = 1;
+        }
+        launch_pdl(tree_mass_velocity_kernel<true>, 1, TREE_THREADS, tmass_smem_bytes(m), s, m, plan, len, tau0,
+                   sigma2, dlik, k, z0, minv, p, vel, q, eps, kinetic, J, H, R, HA);
+    } else {
+        launch_pdl(tree_mass_velocity_kernel<false>, 1, TREE_THREADS, 0, s, m, plan, len, tau0, sigma2, dlik, k, z0,
+                   minv, p, vel, q, eps, kinetic, J, H, R, HA);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tree_mass_momentum(int64_t m, const int *plan, const double *len, double tau0, double sigma2,
+                                      const double *dlik, int64_t k, int64_t z0, const double *minv, const double *xi,
+                                      double *p, double *scratch, cudaStream_t s) {
+    const int64_t nn = 2 * m - 1;
+    double *w = scratch, *pw = w + nn, *prior_scratch = pw + m;
+    launch_pdl(tree_brownian_kernel, 1, TREE_THREADS, 0, s, m, plan, len, tau0, sigma2, dlik, k, z0, minv, xi, p, w);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_tree_prior(m, plan, len, tau0, sigma2, w, prior_scratch, nullptr, pw, nullptr, s);
+    if (e != cudaSuccess) return e;
+    launch_pdl(tree_mass_add_kernel, (unsigned)((m + 255) / 256), 256, 0, s, m, z0, (const double *)pw, p);
+    return cudaGetLastError();
+}
+
 }  // namespace hk
 
 extern "C" {
@@ -299,6 +520,48 @@ int hawkes_tree_prior(int64_t m, const int *plan, const double *length, double r
     if (ws_bytes < hawkes_tree_workspace_size(m)) return HAWKES_EWORKSPACE;
     return hk::launch_tree_prior(m, plan, length, root_var, sigma2, z, (double *)ws, logdens, pz, pdiag,
                                  (cudaStream_t)stream) == cudaSuccess
+               ? HAWKES_OK
+               : HAWKES_ECUDA;
+}
+
+size_t hawkes_tree_mass_workspace_size(int64_t m) {
+    if (m < 2 || m > HAWKES_TREE_MAX_TIPS) return 0;
+    // velocity: 4 (2m - 1) doubles; momentum: w (2m - 1), (sigma^2 V)^-1 w (m), the prior's 5 (2m - 1)
+    const size_t nn = (size_t)(2 * m - 1);
+    const size_t a = 4 * nn, b = nn + (size_t)m + 5 * nn;
+    return (a > b ? a : b) * sizeof(double);
+}
+
+static int tree_mass_args(int64_t m, const int *plan, const double *length, double root_var, double sigma2,
+                          const double *dlik, int64_t k, int64_t z0, const double *minv, void *ws, size_t ws_bytes) {
+    if (m < 2 || m > HAWKES_TREE_MAX_TIPS || !plan || !length || !dlik || !minv || !ws) return HAWKES_EINVAL;
+    if (z0 < 0 || k < m || z0 > k - m) return HAWKES_EINVAL;
+    if (!(sigma2 > 0) || !(root_var >= 0) || !isfinite(sigma2) || !isfinite(root_var)) return HAWKES_EINVAL;
+    if (ws_bytes < hawkes_tree_mass_workspace_size(m)) return HAWKES_EWORKSPACE;
+    return HAWKES_OK;
+}
+
+int hawkes_tree_mass_velocity(int64_t m, const int *plan, const double *length, double root_var, double sigma2,
+                              const double *dlik, int64_t k, int64_t z0, const double *minv, const double *p,
+                              double *vel, double *q, double eps, double *kinetic, void *ws, size_t ws_bytes,
+                              void *stream) {
+    const int rc = tree_mass_args(m, plan, length, root_var, sigma2, dlik, k, z0, minv, ws, ws_bytes);
+    if (rc != HAWKES_OK) return rc;
+    if (!p || (!vel && !q && !kinetic) || !isfinite(eps)) return HAWKES_EINVAL;
+    return hk::launch_tree_mass_velocity(m, plan, length, root_var, sigma2, dlik, k, z0, minv, p, vel, q, eps,
+                                         kinetic, (double *)ws, (cudaStream_t)stream) == cudaSuccess
+               ? HAWKES_OK
+               : HAWKES_ECUDA;
+}
+
+int hawkes_tree_mass_momentum(int64_t m, const int *plan, const double *length, double root_var, double sigma2,
+                              const double *dlik, int64_t k, int64_t z0, const double *minv, const double *xi,
+                              double *p, void *ws, size_t ws_bytes, void *stream) {
+    const int rc = tree_mass_args(m, plan, length, root_var, sigma2, dlik, k, z0, minv, ws, ws_bytes);
+    if (rc != HAWKES_OK) return rc;
+    if (!xi || !p) return HAWKES_EINVAL;
+    return hk::launch_tree_mass_momentum(m, plan, length, root_var, sigma2, dlik, k, z0, minv, xi, p, (double *)ws,
+                                         (cudaStream_t)stream) == cudaSuccess
                ? HAWKES_OK
                : HAWKES_ECUDA;
 }

@@ -253,9 +253,25 @@ class Posterior:
         return int(self.like["status"].item())
 
 
+class TreeMassOp:
+    """The tree-structured mass matrix (tree.TreeMass: diag(d) + (sigma2 V)^-1 on
+    the rate block) with the diagonal inverse mass minv elsewhere, in the
+    form leapfrog, kinetic and TrajectoryGraph take in place of minv."""
+
+    def __init__(self, tm, minv):
+        self.tm, self.minv = tm, minv
+
+    def position(self, q, p, eps):
+        self.tm.velocity(p, self.minv, q=q, eps=eps)
+
+    def kinetic(self, p, out):
+        self.tm.velocity(p, self.minv, kinetic=out)
+
+
 def leapfrog(post, q, p, g, eps, n_steps, minv, scratch, record=None):
     """n_steps leapfrog steps from (q, p) with gradient g at q; updates q, p in place.
 
+    minv: the diagonal inverse mass (device tensor) or a TreeMassOp.
     record(q, grad), when given, sees every position of the trajectory with its
     gradient (device tensors, valid until the next step).  Returns the
     evaluation dict at the final position."""
@@ -265,7 +281,10 @@ def leapfrog(post, q, p, g, eps, n_steps, minv, scratch, record=None):
     _check(L.hawkes_hmc_momentum(k, _ptr(p), _ptr(g), 0.5 * eps, s))
     ev = None
     for step in range(n_steps):
-        _check(L.hawkes_hmc_position(k, _ptr(q), _ptr(p), _ptr(minv), eps, s))
+        if isinstance(minv, torch.Tensor):
+            _check(L.hawkes_hmc_position(k, _ptr(q), _ptr(p), _ptr(minv), eps, s))
+        else:
+            minv.position(q, p, eps)
         ev = post.evaluate(q, out=scratch)
         if record is not None:
             record(q, ev["grad"])
@@ -274,6 +293,10 @@ def leapfrog(post, q, p, g, eps, n_steps, minv, scratch, record=None):
 
 
 def kinetic(p, minv, out):
+    """out = p^T M^-1 p / 2 for a diagonal minv tensor or a TreeMassOp."""
+    if not isinstance(minv, torch.Tensor):
+        minv.kinetic(p, out)
+        return out
     L = _lib()
     s = ctypes.c_void_p(torch.cuda.current_stream(p.device).cuda_stream)
     _check(L.hawkes_hmc_kinetic(p.numel(), _ptr(p), _ptr(minv), _ptr(out), s))
@@ -333,9 +356,9 @@ class TrajectoryGraph:
     slowest path (rows redone in FP64)."""
 
     def __init__(self, post, eps, n_steps, minv, q0, p0, g0):
-        dev = minv.device
+        dev = q0.device
         f64 = dict(dtype=torch.float64, device=dev)
-        dim = minv.numel()
+        dim = q0.numel()
         self.post, self.n_steps = post, n_steps
         self.q, self.p, self.g = torch.zeros(dim, **f64), torch.zeros(dim, **f64), torch.zeros(dim, **f64)
         self.out = {"logpost": torch.empty((), **f64), "grad": torch.empty(dim, **f64),
@@ -379,8 +402,15 @@ def load_state(path) -> dict:
 
 def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_every=100, target_accept=0.8,
            mass_floor=1e-2, seed=0, keep=None, record=None, use_graph=True, checkpoint=None, checkpoint_every=0,
-           resume=None):
+           resume=None, mass="diag"):
     """Run n_warmup + n_iter HMC iterations from q0 (device tensor); returns a Chain.
+
+    mass: "diag", the diagonal mass of Section 2.3.2 (a running average of
+    max(-H_diag, mass_floor)); or "tree", for a posterior with a tree prior:
+    the same diagonal outside the rate block and diag(d) + (sigma2 V)^-1 on
+    it, d a running average of the likelihood's own curvature
+    max(-H_diag - diag((sigma2 V)^-1), 0), so that the prior's tree
+    correlations are preconditioned exactly (tree.TreeMass).
 
     keep: optional index array of coordinates to store (all by default);
     record: optional callback given every leapfrog position and its gradient;
@@ -402,6 +432,19 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
     keep_t = torch.as_tensor(keep, device=dev)
     total = n_warmup + n_iter
     da = DualAveraging(eps0, target_accept)
+    if mass not in ("diag", "tree"):
+        raise ValueError("mass must be 'diag' or 'tree'")
+    tm = xi = None
+    if mass == "tree":
+        if getattr(post, "tree", None) is None:
+            raise ValueError("mass='tree' needs a posterior with a tree prior")
+        from . import tree as tree_mod
+        tm = tree_mod.TreeMass(post.tree, dim, z0=6)
+        xi = torch.empty(tm.n_normals, **f64)
+
+    def rate_curvature(hdiag_q):
+        # the log-likelihood's curvature on the rates: the posterior's minus the prior's
+        return torch.clamp(-hdiag_q[6:6 + tm.m] - post.pd, min=0.0)
     if resume is None:
         q = q0.clone()
         cur = post.evaluate(q, want_hess=True)
@@ -409,6 +452,8 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
         mass = torch.clamp(-cur["hdiag"], min=mass_floor)
         n_mass = 1
         minv = 1.0 / mass  # updated in place from here on (a captured trajectory reads it)
+        if tm is not None:
+            tm.d.copy_(rate_curvature(cur["hdiag"]))
         eps = eps0
         draws = np.empty((n_iter, len(keep)))
         lps, acc, aprob = np.empty(n_iter), np.zeros(n_iter, bool), np.empty(n_iter)
@@ -421,12 +466,15 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
         cur = {"logpost": st["logpost"].to(dev), "grad": st["grad"].to(dev)}
         mass, minv = st["mass"].to(dev), st["minv"].to(dev)
         n_mass, eps = st["n_mass"], st["eps"]
+        if tm is not None:
+            tm.d.copy_(st["tree_d"].to(dev))
         da.__dict__.update(st["dual_averaging"])
         gen.set_state(st["gen_state"])
         rng.bit_generator.state = st["rng_state"]
         draws, lps, acc, aprob = st["draws"], st["lps"], st["acc"], st["aprob"]
         post.calls.update(st["calls"])
         start, spent_warm, spent_samp = st["it"], st["spent_warm"], st["spent_samp"]
+    mop = TreeMassOp(tm, minv) if tm is not None else minv  # what leapfrog and kinetic apply
     graph = None
     scratch = {"logpost": torch.empty((), **f64), "grad": torch.empty(dim, **f64), "hdiag": torch.empty(dim, **f64)}
     k0, k1 = torch.empty((), **f64), torch.empty((), **f64)
@@ -439,12 +487,16 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
             now = time.perf_counter()
             spent_warm += now - t_seg
             t_seg = now
-        torch.randn(dim, generator=gen, out=p, dtype=torch.float64, device=dev)
-        p.mul_(torch.sqrt(mass))
-        kinetic(p, minv, k0)
+        if tm is None:
+            torch.randn(dim, generator=gen, out=p, dtype=torch.float64, device=dev)
+            p.mul_(torch.sqrt(mass))
+        else:
+            torch.randn(tm.n_normals, generator=gen, out=xi, dtype=torch.float64, device=dev)
+            tm.momentum(minv, xi, p)
+        kinetic(p, mop, k0)
         if use_graph and record is None and it >= n_warmup:
             if graph is None:
-                graph = TrajectoryGraph(post, eps, n_steps, minv, q, p, cur["grad"])
+                graph = TrajectoryGraph(post, eps, n_steps, mop, q, p, cur["grad"])
             graph.q.copy_(q)
             graph.p.copy_(p)
             graph.g.copy_(cur["grad"])
@@ -452,8 +504,8 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
             qn, k1_t = graph.q, graph.k1
         else:
             qn = q.clone()
-            ev = leapfrog(post, qn, p, cur["grad"], eps, n_steps, minv, scratch, record)
-            kinetic(p, minv, k1)
+            ev = leapfrog(post, qn, p, cur["grad"], eps, n_steps, mop, scratch, record)
+            kinetic(p, mop, k1)
             k1_t = k1
         h0 = -cur["logpost"].item() + k0.item()
         lp1 = ev["logpost"].item()
@@ -470,6 +522,8 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
         if (it + 1) % mass_every == 0:
             hd = post.evaluate(q, want_hess=True)
             new = torch.clamp(-hd["hdiag"], min=mass_floor)
+            if tm is not None:
+                tm.d.mul_(n_mass).add_(rate_curvature(hd["hdiag"])).div_(n_mass + 1)
             mass = (n_mass * mass + new) / (n_mass + 1)  # running average of the Hessian-based masses
             n_mass += 1
             torch.reciprocal(mass, out=minv)
@@ -491,7 +545,7 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
                 "mass": mass.cpu(), "minv": minv.cpu(), "n_mass": n_mass, "eps": eps,
                 "dual_averaging": dict(da.__dict__), "gen_state": gen.get_state(),
                 "rng_state": rng.bit_generator.state, "draws": draws, "lps": lps, "acc": acc, "aprob": aprob,
-                "calls": dict(post.calls),
+                "calls": dict(post.calls), "tree_d": tm.d.cpu() if tm is not None else None,
                 "spent_warm": spent_warm + (seg if it < n_warmup else 0.0),
                 "spent_samp": spent_samp + (seg if it >= n_warmup else 0.0)})
             # the checkpoint's own cost is left out of both phases

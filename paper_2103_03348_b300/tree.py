@@ -30,6 +30,12 @@ def _lib():
         L.hawkes_tree_prior.restype = ctypes.c_int
         L.hawkes_posterior_tree_workspace_size.argtypes = [i64]
         L.hawkes_posterior_tree_workspace_size.restype = sz
+        L.hawkes_tree_mass_workspace_size.argtypes = [i64]
+        L.hawkes_tree_mass_workspace_size.restype = sz
+        L.hawkes_tree_mass_velocity.argtypes = [i64, vp, vp, d, d, vp, i64, i64, vp, vp, vp, vp, d, vp, vp, sz, vp]
+        L.hawkes_tree_mass_velocity.restype = ctypes.c_int
+        L.hawkes_tree_mass_momentum.argtypes = [i64, vp, vp, d, d, vp, i64, i64, vp, vp, vp, vp, sz, vp]
+        L.hawkes_tree_mass_momentum.restype = ctypes.c_int
         L._tree_typed = True
     return L
 
@@ -92,3 +98,42 @@ class TreePrior:
                                    ctypes.c_size_t(self.ws.numel()), p(out["logdens"]), p(out["pz"]),
                                    p(out["pdiag"]), s))
         return {k: v for k, v in out.items() if v is not None}
+
+
+class TreeMass:
+    """The HMC mass matrix with the phylogenetic prior's full precision on the
+    rate block: M = diag(1 / minv) outside coordinates [z0, z0 + m) of a
+    k-dimensional state, M_z = diag(d) + (sigma2 V)^-1 on them, d >= 0 the
+    likelihood's curvature (self.d, a device tensor the caller updates in
+    place).  Both calls are one tree sweep on the device (O(m), no M x M
+    matrix), enqueued on the current stream."""
+
+    def __init__(self, prior: TreePrior, k: int, z0: int = 6):
+        if z0 < 0 or z0 + prior.m > k:
+            raise hawkes.HawkesError(hawkes.EINVAL, "the rate block must lie inside the state")
+        self.prior, self.k, self.z0, self.m = prior, int(k), int(z0), prior.m
+        dev = prior.length.device
+        self.d = torch.zeros(self.m, dtype=torch.float64, device=dev)
+        self.ws = torch.empty(int(_lib().hawkes_tree_mass_workspace_size(self.m)), dtype=torch.uint8, device=dev)
+        self.n_normals = self.k + 2 * self.m - 1
+
+    def velocity(self, p, minv, vel=None, q=None, eps=0.0, kinetic=None):
+        """vel = M^-1 p; q += eps M^-1 p; kinetic = p^T M^-1 p / 2 (each when given)."""
+        t = lambda a: ctypes.c_void_p(a.data_ptr() if a is not None else 0)  # noqa: E731
+        s = ctypes.c_void_p(torch.cuda.current_stream(p.device).cuda_stream)
+        pr = self.prior
+        _check(_lib().hawkes_tree_mass_velocity(self.m, t(pr.plan), t(pr.length), pr.root_var, pr.sigma2, t(self.d),
+                                                self.k, self.z0, t(minv), t(p), t(vel), t(q), float(eps), t(kinetic),
+                                                t(self.ws), ctypes.c_size_t(self.ws.numel()), s))
+
+    def momentum(self, minv, xi, p):
+        """p ~ N(0, M) from xi, k + 2m - 1 standard normals (device)."""
+        if xi.numel() != self.n_normals or p.numel() != self.k:
+            raise hawkes.HawkesError(hawkes.EINVAL, "xi must hold k + 2m - 1 normals and p k entries")
+        t = lambda a: ctypes.c_void_p(a.data_ptr())  # noqa: E731
+        s = ctypes.c_void_p(torch.cuda.current_stream(p.device).cuda_stream)
+        pr = self.prior
+        _check(_lib().hawkes_tree_mass_momentum(self.m, t(pr.plan), t(pr.length), pr.root_var, pr.sigma2, t(self.d),
+                                                self.k, self.z0, t(minv), t(xi), t(p), t(self.ws),
+                                                ctypes.c_size_t(self.ws.numel()), s))
+        return p
