@@ -389,19 +389,28 @@ int hawkes_posterior_tree(int64_t n, int64_t m, const int *seq_idx, const int *p
  * makes every output NaN.
  * ------------------------------------------------------------------------ */
 
-/* Bytes of DEVICE workspace the two calls below need for m tips. */
+/* Bytes of DEVICE workspace the three calls below need for m tips (scratch
+ * only: nothing in it outlives a call). */
 size_t hawkes_tree_mass_workspace_size(int64_t m);
 
-/* Velocity M^-1 p by one upward and one downward sweep of the tree:
+/* The sweep coefficients of M_z for the curvature d (DEVICE double[m]):
+ * fac (DEVICE double[2 (2m - 1)], caller-owned) receives, per tree node v,
+ * r_v = 1 / (1 + s_v J_v) and s_v r_v, where s_v = sigma2 length_v (sigma2
+ * root_var at the root) and J_v is the curvature gathered below v.  Call it
+ * again whenever d changes; hawkes_tree_mass_velocity reads fac. */
+int hawkes_tree_mass_factor(int64_t m, const int *plan, const double *length, double root_var, double sigma2,
+                            const double *dlik, double *fac, void *ws, size_t ws_bytes, void *stream);
+
+/* Velocity M^-1 p by one upward and one downward sweep of the tree, with
+ * the coefficients fac from hawkes_tree_mass_factor:
  *   p        DEVICE double[k], the momentum
  *   vel      DEVICE double[k] or NULL: M^-1 p
  *   q        DEVICE double[k] or NULL: the leapfrog position step q += eps M^-1 p
  *   kinetic  DEVICE double[1] or NULL: p^T M^-1 p / 2
  * At least one of vel, q, kinetic must be given. */
-int hawkes_tree_mass_velocity(int64_t m, const int *plan, const double *length, double root_var, double sigma2,
-                              const double *dlik, int64_t k, int64_t z0, const double *minv, const double *p,
-                              double *vel, double *q, double eps, double *kinetic, void *ws, size_t ws_bytes,
-                              void *stream);
+int hawkes_tree_mass_velocity(int64_t m, const int *plan, const double *fac, int64_t k, int64_t z0,
+                              const double *minv, const double *p, double *vel, double *q, double eps,
+                              double *kinetic, void *ws, size_t ws_bytes, void *stream);
 
 /* A momentum p ~ N(0, M) (DEVICE double[k]) from standard normals xi (DEVICE
  * double[k + 2m - 1]): p_i = xi_i / sqrt(minv_i) outside the block and

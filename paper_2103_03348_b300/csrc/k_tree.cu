@@ -206,31 +206,72 @@ cudaError_t launch_tree_prior(int64_t m, const int *plan, const double *len, dou
 // and M = diag(1 / minv) elsewhere.  M_z^-1 p is the posterior mean of the
 // tips of a Brownian motion on the tree (prior N(0, sigma^2 V)) that receives
 // Gaussian evidence in information form, precision d_i and information p_i,
-// at tip i.  One upward sweep folds each node's evidence into a message to its
+// at tip i.  An upward sweep folds each node's evidence into a message to its
 // parent across the branch of variance s = sigma^2 len:
 //     J_v = d_v (tip) or J'_a + J'_b,   h_v = p_v (tip) or h'_a + h'_b,
 //     r_v = 1 / (1 + s_v J_v),  J'_v = J_v r_v,  h'_v = h_v r_v,
 // (the root's branch is the root variance, s = sigma^2 root_var, to a parent
 // fixed at 0); the downward sweep gives the means
-//     X_root = s_root h_root r_root,   X_c = (X_parent + s_c h_c) r_c,
+//     X_root = s_root h_root r_root,   X_c = X_parent r_c + (s_c r_c) h_c,
 // and X at the tips is M_z^-1 p.  1 + s J >= 1, so the sweeps stay well
 // conditioned however small the branches (V's condition number reaches ~1e9
-// on coalescent trees).  One reciprocal per node.
+// on coalescent trees).  The precisions J, hence r and s r, do not depend on
+// p: tree_mass_factor_kernel computes them once per change of d (one
+// reciprocal per node), and each velocity is then one multiply per node up
+// and one multiply-add per node down, no division.
 constexpr int TMASS_SMEM_MAX_TIPS = 2048;
 
 __host__ __device__ inline size_t tmass_smem_bytes(int64_t m) {
-    // 5 doubles (J / X, h, r, own h, length) and 2 ints (children) per node,
-    // then the level order (m - 1) and the level offsets (at most m)
-    return (size_t)(2 * m - 1) * (5 * sizeof(double) + 2 * sizeof(int)) + (size_t)(2 * m) * sizeof(int) + 64;
+    // 4 doubles (r, s r, own h, message h / mean X) and 2 ints (children) per
+    // node, then the level order (m - 1) and the level offsets (at most m)
+    return (size_t)(2 * m - 1) * (4 * sizeof(double) + 2 * sizeof(int)) + (size_t)(2 * m) * sizeof(int) + 64;
+}
+
+// fac[0, nn) = r_v, fac[nn, 2 nn) = s_v r_v for every node; J is scratch (nn).
+__global__ void __launch_bounds__(TREE_THREADS)
+    tree_mass_factor_kernel(int64_t m_arg, const int *__restrict__ plan, const double *__restrict__ len,
+                            double tau0, double sigma2, const double *__restrict__ dlik, double *__restrict__ fac,
+                            double *__restrict__ J) {
+    pdl_wait();
+    const TreePlan T = tree_plan_view(plan);
+    const int m = T.m;
+    if ((int64_t)m != m_arg || T.levels < 1 || T.levels > m - 1) {  // a plan for another tree
+        for (int64_t v = threadIdx.x; v < 2 * (2 * m_arg - 1); v += TREE_THREADS) fac[v] = NAN;
+        return;
+    }
+    const int nn = 2 * m - 1;
+    double *R = fac, *SR = fac + nn;
+    for (int i = threadIdx.x; i < m; i += TREE_THREADS) {
+        const double dv = dlik[i];
+        const double d = dv > 0.0 ? dv : 0.0;  // negative or NaN curvature counts as none
+        const double sv = sigma2 * len[i];
+        const double r = 1.0 / fma(sv, d, 1.0);
+        J[i] = d * r;
+        R[i] = r;
+        SR[i] = sv * r;
+    }
+    __syncthreads();
+    const int root = T.order[m - 2];
+    for (int L = 0; L < T.levels; ++L) {
+        for (int j = T.offs[L] + threadIdx.x; j < T.offs[L + 1]; j += TREE_THREADS) {
+            const int v = T.order[j];
+            const double Jv = J[T.ca[v]] + J[T.cb[v]];
+            const double sv = sigma2 * (v == root ? tau0 : len[v]);
+            const double r = 1.0 / fma(sv, Jv, 1.0);
+            J[v] = Jv * r;
+            R[v] = r;
+            SR[v] = sv * r;
+        }
+        __syncthreads();
+    }
 }
 
 template <bool STAGED>
 __global__ void __launch_bounds__(TREE_THREADS)
-    tree_mass_velocity_kernel(int64_t m_arg, const int *__restrict__ plan, const double *__restrict__ len_g,
-                              double tau0, double sigma2, const double *__restrict__ dlik, int64_t k, int64_t z0,
-                              const double *__restrict__ minv, const double *__restrict__ p, double *__restrict__ vel,
-                              double *__restrict__ q, double eps, double *__restrict__ kinetic, double *J, double *H,
-                              double *R, double *HA) {
+    tree_mass_velocity_kernel(int64_t m_arg, const int *__restrict__ plan, const double *__restrict__ fac,
+                              int64_t k, int64_t z0, const double *__restrict__ minv, const double *__restrict__ p,
+                              double *__restrict__ vel, double *__restrict__ q, double eps,
+                              double *__restrict__ kinetic, double *H, double *HA) {
     pdl_wait();
     extern __shared__ __align__(16) unsigned char tree_smem[];
     __shared__ double sh[TREE_THREADS];
@@ -245,23 +286,23 @@ __global__ void __launch_bounds__(TREE_THREADS)
         return;
     }
     const int nn = 2 * m - 1;
-    const double *len = len_g;
+    const double *R = fac, *SR = fac + nn;
     if (STAGED) {
         double *base = reinterpret_cast<double *>(tree_smem);
-        J = base;
-        H = J + nn;
-        R = H + nn;
-        HA = R + nn;
-        double *len_s = HA + nn;
-        int *ca = reinterpret_cast<int *>(len_s + nn), *cb = ca + nn, *order = cb + nn, *offs = order + (m - 1);
+        double *R_s = base, *SR_s = R_s + nn;
+        H = SR_s + nn;
+        HA = H + nn;
+        int *ca = reinterpret_cast<int *>(HA + nn), *cb = ca + nn, *order = cb + nn, *offs = order + (m - 1);
         for (int v = threadIdx.x; v < nn; v += TREE_THREADS) {
-            len_s[v] = len_g[v];
+            R_s[v] = fac[v];
+            SR_s[v] = fac[nn + v];
             ca[v] = T.ca[v];
             cb[v] = T.cb[v];
         }
         for (int j = threadIdx.x; j < m - 1; j += TREE_THREADS) order[j] = T.order[j];
         for (int j = threadIdx.x; j <= T.levels; j += TREE_THREADS) offs[j] = T.offs[j];
-        len = len_s;
+        R = R_s;
+        SR = SR_s;
         T.ca = ca;
         T.cb = cb;
         T.order = order;
@@ -277,46 +318,36 @@ __global__ void __launch_bounds__(TREE_THREADS)
         if (q) q[i] += eps * v;
         kin += p[i] * v;
     }
-    // tips: evidence (d_i, p_i) and its message across the tip's branch
     for (int i = threadIdx.x; i < m; i += TREE_THREADS) {
-        const double dv = dlik[i];
-        const double d = dv > 0.0 ? dv : 0.0;  // negative or NaN curvature counts as none
         const double h = p[z0 + i];
-        const double r = 1.0 / fma(sigma2 * len[i], d, 1.0);
-        J[i] = d * r;
-        H[i] = h * r;
-        R[i] = r;
         HA[i] = h;
+        H[i] = h * R[i];
     }
     __syncthreads();
     const int root = T.order[m - 2];
     for (int L = 0; L < T.levels; ++L) {
         for (int j = T.offs[L] + threadIdx.x; j < T.offs[L + 1]; j += TREE_THREADS) {
-            const int v = T.order[j], a = T.ca[v], b = T.cb[v];
-            const double Jv = J[a] + J[b], hv = H[a] + H[b];
-            const double s = sigma2 * (v == root ? tau0 : len[v]);
-            const double r = 1.0 / fma(s, Jv, 1.0);
-            J[v] = Jv * r;
-            H[v] = hv * r;
-            R[v] = r;
+            const int v = T.order[j];
+            const double hv = H[T.ca[v]] + H[T.cb[v]];
             HA[v] = hv;
+            H[v] = hv * R[v];
         }
         __syncthreads();
     }
-    // downward: the means X overwrite the messages J (no longer needed)
-    if (threadIdx.x == 0) J[root] = sigma2 * tau0 * HA[root] * R[root];
+    // downward: the means X overwrite the messages H (no longer needed)
+    if (threadIdx.x == 0) H[root] = SR[root] * HA[root];
     __syncthreads();
     for (int L = T.levels - 1; L >= 0; --L) {
         for (int j = T.offs[L] + threadIdx.x; j < T.offs[L + 1]; j += TREE_THREADS) {
             const int v = T.order[j], a = T.ca[v], b = T.cb[v];
-            const double xv = J[v];
-            J[a] = fma(sigma2 * len[a], HA[a], xv) * R[a];
-            J[b] = fma(sigma2 * len[b], HA[b], xv) * R[b];
+            const double xv = H[v];
+            H[a] = fma(xv, R[a], SR[a] * HA[a]);
+            H[b] = fma(xv, R[b], SR[b] * HA[b]);
         }
         __syncthreads();
     }
     for (int i = threadIdx.x; i < m; i += TREE_THREADS) {
-        const double v = J[i];
+        const double v = H[i];
         if (vel) vel[z0 + i] = v;
         if (q) q[z0 + i] += eps * v;
         kin += p[z0 + i] * v;
@@ -378,12 +409,17 @@ __global__ void tree_mass_add_kernel(int64_t m, int64_t z0, const double *__rest
     if (i < m) p[z0 + i] += pw[i];
 }
 
-cudaError_t launch_tree_mass_velocity(int64_t m, const int *plan, const double *len, double tau0, double sigma2,
-                                      const double *dlik, int64_t k, int64_t z0, const double *minv, const double *p,
-                                      double *vel, double *q, double eps, double *kinetic, double *scratch,
-                                      cudaStream_t s) {
+cudaError_t launch_tree_mass_factor(int64_t m, const int *plan, const double *len, double tau0, double sigma2,
+                                    const double *dlik, double *fac, double *scratch, cudaStream_t s) {
+    launch_pdl(tree_mass_factor_kernel, 1, TREE_THREADS, 0, s, m, plan, len, tau0, sigma2, dlik, fac, scratch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tree_mass_velocity(int64_t m, const int *plan, const double *fac, int64_t k, int64_t z0,
+                                      const double *minv, const double *p, double *vel, double *q, double eps,
+                                      double *kinetic, double *scratch, cudaStream_t s) {
     const int64_t nn = 2 * m - 1;
-    double *J = scratch, *H = J + nn, *R = H + nn, *HA = R + nn;
+    double *H = scratch, *HA = H + nn;
     if (m <= TMASS_SMEM_MAX_TIPS) {
         static int attr_set[64] = {0};  // per-device opt-in, set on the first (eager) launch
         int dev = 0;
@@ -395,11 +431,11 @@ cudaError_t launch_tree_mass_velocity(int64_t m, const int *plan, const double *
             if (e != cudaSuccess) return e;
             if (dev >= 0 && dev < 64) attr_set[dev] = 1;
         }
-        launch_pdl(tree_mass_velocity_kernel<true>, 1, TREE_THREADS, tmass_smem_bytes(m), s, m, plan, len, tau0,
-                   sigma2, dlik, k, z0, minv, p, vel, q, eps, kinetic, J, H, R, HA);
+        launch_pdl(tree_mass_velocity_kernel<true>, 1, TREE_THREADS, tmass_smem_bytes(m), s, m, plan, fac, k, z0, minv,
+                   p, vel, q, eps, kinetic, H, HA);
     } else {
-        launch_pdl(tree_mass_velocity_kernel<false>, 1, TREE_THREADS, 0, s, m, plan, len, tau0, sigma2, dlik, k, z0,
-                   minv, p, vel, q, eps, kinetic, J, H, R, HA);
+        launch_pdl(tree_mass_velocity_kernel<false>, 1, TREE_THREADS, 0, s, m, plan, fac, k, z0, minv, p, vel, q, eps,
+                   kinetic, H, HA);
     }
     return cudaGetLastError();
 }
@@ -526,30 +562,42 @@ int hawkes_tree_prior(int64_t m, const int *plan, const double *length, double r
 
 size_t hawkes_tree_mass_workspace_size(int64_t m) {
     if (m < 2 || m > HAWKES_TREE_MAX_TIPS) return 0;
-    // velocity: 4 (2m - 1) doubles; momentum: w (2m - 1), (sigma^2 V)^-1 w (m), the prior's 5 (2m - 1)
+    // factor and velocity: 2 (2m - 1) doubles; momentum: w (2m - 1), (sigma^2 V)^-1 w (m), the prior's 5 (2m - 1)
     const size_t nn = (size_t)(2 * m - 1);
-    const size_t a = 4 * nn, b = nn + (size_t)m + 5 * nn;
-    return (a > b ? a : b) * sizeof(double);
+    return (nn + (size_t)m + 5 * nn) * sizeof(double);
 }
 
-static int tree_mass_args(int64_t m, const int *plan, const double *length, double root_var, double sigma2,
-                          const double *dlik, int64_t k, int64_t z0, const double *minv, void *ws, size_t ws_bytes) {
-    if (m < 2 || m > HAWKES_TREE_MAX_TIPS || !plan || !length || !dlik || !minv || !ws) return HAWKES_EINVAL;
+static int tree_mass_args(int64_t m, const int *plan, int64_t k, int64_t z0, const double *minv, void *ws,
+                          size_t ws_bytes) {
+    if (m < 2 || m > HAWKES_TREE_MAX_TIPS || !plan || !minv || !ws) return HAWKES_EINVAL;
     if (z0 < 0 || k < m || z0 > k - m) return HAWKES_EINVAL;
-    if (!(sigma2 > 0) || !(root_var >= 0) || !isfinite(sigma2) || !isfinite(root_var)) return HAWKES_EINVAL;
     if (ws_bytes < hawkes_tree_mass_workspace_size(m)) return HAWKES_EWORKSPACE;
     return HAWKES_OK;
 }
 
-int hawkes_tree_mass_velocity(int64_t m, const int *plan, const double *length, double root_var, double sigma2,
-                              const double *dlik, int64_t k, int64_t z0, const double *minv, const double *p,
-                              double *vel, double *q, double eps, double *kinetic, void *ws, size_t ws_bytes,
-                              void *stream) {
-    const int rc = tree_mass_args(m, plan, length, root_var, sigma2, dlik, k, z0, minv, ws, ws_bytes);
+static bool tree_scalars_ok(double root_var, double sigma2) {
+    return sigma2 > 0 && root_var >= 0 && isfinite(sigma2) && isfinite(root_var);
+}
+
+int hawkes_tree_mass_factor(int64_t m, const int *plan, const double *length, double root_var, double sigma2,
+                            const double *dlik, double *fac, void *ws, size_t ws_bytes, void *stream) {
+    if (m < 2 || m > HAWKES_TREE_MAX_TIPS || !plan || !length || !dlik || !fac || !ws) return HAWKES_EINVAL;
+    if (!tree_scalars_ok(root_var, sigma2)) return HAWKES_EINVAL;
+    if (ws_bytes < hawkes_tree_mass_workspace_size(m)) return HAWKES_EWORKSPACE;
+    return hk::launch_tree_mass_factor(m, plan, length, root_var, sigma2, dlik, fac, (double *)ws,
+                                       (cudaStream_t)stream) == cudaSuccess
+               ? HAWKES_OK
+               : HAWKES_ECUDA;
+}
+
+int hawkes_tree_mass_velocity(int64_t m, const int *plan, const double *fac, int64_t k, int64_t z0,
+                              const double *minv, const double *p, double *vel, double *q, double eps,
+                              double *kinetic, void *ws, size_t ws_bytes, void *stream) {
+    const int rc = tree_mass_args(m, plan, k, z0, minv, ws, ws_bytes);
     if (rc != HAWKES_OK) return rc;
-    if (!p || (!vel && !q && !kinetic) || !isfinite(eps)) return HAWKES_EINVAL;
-    return hk::launch_tree_mass_velocity(m, plan, length, root_var, sigma2, dlik, k, z0, minv, p, vel, q, eps,
-                                         kinetic, (double *)ws, (cudaStream_t)stream) == cudaSuccess
+    if (!fac || !p || (!vel && !q && !kinetic) || !isfinite(eps)) return HAWKES_EINVAL;
+    return hk::launch_tree_mass_velocity(m, plan, fac, k, z0, minv, p, vel, q, eps, kinetic, (double *)ws,
+                                         (cudaStream_t)stream) == cudaSuccess
                ? HAWKES_OK
                : HAWKES_ECUDA;
 }
@@ -557,9 +605,9 @@ int hawkes_tree_mass_velocity(int64_t m, const int *plan, const double *length, 
 int hawkes_tree_mass_momentum(int64_t m, const int *plan, const double *length, double root_var, double sigma2,
                               const double *dlik, int64_t k, int64_t z0, const double *minv, const double *xi,
                               double *p, void *ws, size_t ws_bytes, void *stream) {
-    const int rc = tree_mass_args(m, plan, length, root_var, sigma2, dlik, k, z0, minv, ws, ws_bytes);
+    const int rc = tree_mass_args(m, plan, k, z0, minv, ws, ws_bytes);
     if (rc != HAWKES_OK) return rc;
-    if (!xi || !p) return HAWKES_EINVAL;
+    if (!length || !dlik || !xi || !p || !tree_scalars_ok(root_var, sigma2)) return HAWKES_EINVAL;
     return hk::launch_tree_mass_momentum(m, plan, length, root_var, sigma2, dlik, k, z0, minv, xi, p, (double *)ws,
                                          (cudaStream_t)stream) == cudaSuccess
                ? HAWKES_OK

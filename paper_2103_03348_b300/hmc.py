@@ -454,6 +454,7 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
         minv = 1.0 / mass  # updated in place from here on (a captured trajectory reads it)
         if tm is not None:
             tm.d.copy_(rate_curvature(cur["hdiag"]))
+            tm.factor()
         eps = eps0
         draws = np.empty((n_iter, len(keep)))
         lps, acc, aprob = np.empty(n_iter), np.zeros(n_iter, bool), np.empty(n_iter)
@@ -468,6 +469,7 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
         n_mass, eps = st["n_mass"], st["eps"]
         if tm is not None:
             tm.d.copy_(st["tree_d"].to(dev))
+            tm.factor()
         da.__dict__.update(st["dual_averaging"])
         gen.set_state(st["gen_state"])
         rng.bit_generator.state = st["rng_state"]
@@ -524,6 +526,7 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
             new = torch.clamp(-hd["hdiag"], min=mass_floor)
             if tm is not None:
                 tm.d.mul_(n_mass).add_(rate_curvature(hd["hdiag"])).div_(n_mass + 1)
+                tm.factor()  # in place: a captured trajectory reads the new coefficients
             mass = (n_mass * mass + new) / (n_mass + 1)  # running average of the Hessian-based masses
             n_mass += 1
             torch.reciprocal(mass, out=minv)

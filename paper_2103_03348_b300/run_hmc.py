@@ -67,6 +67,7 @@ def run(precision="fp32c_st", iters=2000, warmup=200, n_steps=20, mass_every=100
         "sampling_seconds": ch.seconds, "warmup_seconds": ch.warmup_seconds, "total_seconds": total,
         "ms_per_gradient": 1e3 * total / max(calls, 1), "gradient_calls": ch.grad_calls, "hessian_calls": ch.hess_calls,
         "ess_globals": summ(eg), "ess_rates": summ(er),
+        "ess_each_global": dict(zip(("mu0", "tau_x", "tau_t", "theta0", "omega", "h"), map(float, eg))),
         "ess_per_s_globals": {k: v / ch.seconds for k, v in summ(eg).items()},
         "ess_per_s_rates": {k: v / ch.seconds for k, v in summ(er).items()},
         "posterior_mean_globals": np.exp(ch.draws[:, :6].mean(0)).tolist(),

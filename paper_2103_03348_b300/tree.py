@@ -32,7 +32,9 @@ def _lib():
         L.hawkes_posterior_tree_workspace_size.restype = sz
         L.hawkes_tree_mass_workspace_size.argtypes = [i64]
         L.hawkes_tree_mass_workspace_size.restype = sz
-        L.hawkes_tree_mass_velocity.argtypes = [i64, vp, vp, d, d, vp, i64, i64, vp, vp, vp, vp, d, vp, vp, sz, vp]
+        L.hawkes_tree_mass_factor.argtypes = [i64, vp, vp, d, d, vp, vp, vp, sz, vp]
+        L.hawkes_tree_mass_factor.restype = ctypes.c_int
+        L.hawkes_tree_mass_velocity.argtypes = [i64, vp, vp, i64, i64, vp, vp, vp, vp, d, vp, vp, sz, vp]
         L.hawkes_tree_mass_velocity.restype = ctypes.c_int
         L.hawkes_tree_mass_momentum.argtypes = [i64, vp, vp, d, d, vp, i64, i64, vp, vp, vp, vp, sz, vp]
         L.hawkes_tree_mass_momentum.restype = ctypes.c_int
@@ -105,8 +107,8 @@ class TreeMass:
     rate block: M = diag(1 / minv) outside coordinates [z0, z0 + m) of a
     k-dimensional state, M_z = diag(d) + (sigma2 V)^-1 on them, d >= 0 the
     likelihood's curvature (self.d, a device tensor the caller updates in
-    place).  Both calls are one tree sweep on the device (O(m), no M x M
-    matrix), enqueued on the current stream."""
+    place, calling factor() after each change).  Every call is a tree sweep
+    on the device (O(m), no M x M matrix), enqueued on the current stream."""
 
     def __init__(self, prior: TreePrior, k: int, z0: int = 6):
         if z0 < 0 or z0 + prior.m > k:
@@ -114,17 +116,25 @@ class TreeMass:
         self.prior, self.k, self.z0, self.m = prior, int(k), int(z0), prior.m
         dev = prior.length.device
         self.d = torch.zeros(self.m, dtype=torch.float64, device=dev)
+        self.fac = torch.empty(2 * (2 * self.m - 1), dtype=torch.float64, device=dev)
         self.ws = torch.empty(int(_lib().hawkes_tree_mass_workspace_size(self.m)), dtype=torch.uint8, device=dev)
         self.n_normals = self.k + 2 * self.m - 1
+
+    def factor(self):
+        """The sweep coefficients for the current self.d (call after changing it)."""
+        t = lambda a: ctypes.c_void_p(a.data_ptr())  # noqa: E731
+        s = ctypes.c_void_p(torch.cuda.current_stream(self.d.device).cuda_stream)
+        pr = self.prior
+        _check(_lib().hawkes_tree_mass_factor(self.m, t(pr.plan), t(pr.length), pr.root_var, pr.sigma2, t(self.d),
+                                              t(self.fac), t(self.ws), ctypes.c_size_t(self.ws.numel()), s))
 
     def velocity(self, p, minv, vel=None, q=None, eps=0.0, kinetic=None):
         """vel = M^-1 p; q += eps M^-1 p; kinetic = p^T M^-1 p / 2 (each when given)."""
         t = lambda a: ctypes.c_void_p(a.data_ptr() if a is not None else 0)  # noqa: E731
         s = ctypes.c_void_p(torch.cuda.current_stream(p.device).cuda_stream)
-        pr = self.prior
-        _check(_lib().hawkes_tree_mass_velocity(self.m, t(pr.plan), t(pr.length), pr.root_var, pr.sigma2, t(self.d),
-                                                self.k, self.z0, t(minv), t(p), t(vel), t(q), float(eps), t(kinetic),
-                                                t(self.ws), ctypes.c_size_t(self.ws.numel()), s))
+        _check(_lib().hawkes_tree_mass_velocity(self.m, t(self.prior.plan), t(self.fac), self.k, self.z0, t(minv), t(p),
+                                                t(vel), t(q), float(eps), t(kinetic), t(self.ws),
+                                                ctypes.c_size_t(self.ws.numel()), s))
 
     def momentum(self, minv, xi, p):
         """p ~ N(0, M) from xi, k + 2m - 1 standard normals (device)."""

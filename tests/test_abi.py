@@ -147,7 +147,7 @@ def test_peak_microbenchmark_arguments(L):
 
 
 def test_tree_mass_argument_checks(L):
-    """hawkes_tree_mass_velocity / _momentum refuse bad arguments before any
+    """hawkes_tree_mass_factor / _velocity / _momentum refuse bad arguments before any
     CUDA call (the fake pointers below are never dereferenced)."""
     from paper_2103_03348_b300 import tree
     T = tree._lib()
@@ -155,27 +155,33 @@ def test_tree_mass_argument_checks(L):
     m = 10
     need = int(T.hawkes_tree_mass_workspace_size(m))
     assert T.hawkes_tree_mass_workspace_size(1) == 0
-    assert need >= 4 * (2 * m - 1) * 8
+    assert need >= (6 * (2 * m - 1) + m) * 8
     good = dict(m=m, s2=1.0, rv=0.0, k=16, z0=6, eps=0.1, ws=need)
 
     def vel(vel_=f, q=f, kin=f, **kw):
         a = dict(good, **kw)
-        return T.hawkes_tree_mass_velocity(a["m"], f, f, a["rv"], a["s2"], f, a["k"], a["z0"], f, f, vel_, q,
-                                           a["eps"], kin, f, ctypes.c_size_t(a["ws"]), None)
+        return T.hawkes_tree_mass_velocity(a["m"], f, f, a["k"], a["z0"], f, f, vel_, q, a["eps"], kin, f,
+                                           ctypes.c_size_t(a["ws"]), None)
+
+    def fac(**kw):
+        a = dict(good, **kw)
+        return T.hawkes_tree_mass_factor(a["m"], f, f, a["rv"], a["s2"], f, f, f, ctypes.c_size_t(a["ws"]), None)
 
     def mom(**kw):
         a = dict(good, **kw)
         return T.hawkes_tree_mass_momentum(a["m"], f, f, a["rv"], a["s2"], f, a["k"], a["z0"], f, f, f, f,
                                            ctypes.c_size_t(a["ws"]), None)
 
-    for call in (vel, mom):
+    for call in (vel, mom, fac):
         assert call(m=1) == hawkes.EINVAL
+        assert call(ws=need - 8) == hawkes.EWORKSPACE
+    for call in (vel, mom):
         assert call(k=9) == hawkes.EINVAL               # the block does not fit in the state
         assert call(z0=7) == hawkes.EINVAL              # z0 + m > k
         assert call(z0=-1) == hawkes.EINVAL
+    for call in (mom, fac):
         assert call(s2=0.0) == hawkes.EINVAL
         assert call(rv=-1.0) == hawkes.EINVAL
         assert call(rv=math.nan) == hawkes.EINVAL
-        assert call(ws=need - 8) == hawkes.EWORKSPACE
     assert vel(vel_=None, q=None, kin=None) == hawkes.EINVAL  # nothing to compute
     assert vel(eps=math.inf) == hawkes.EINVAL

@@ -42,6 +42,7 @@ def test_velocity_position_and_kinetic_match_oracle(case):
     q0 = rng.standard_normal(k)
     tm = tree.TreeMass(tree.TreePrior(parent, length, tau0, s2), k, Z0)
     tm.d.copy_(dev(d))
+    tm.factor()
     vel, q, kin, kin2 = dev(np.zeros(k)), dev(q0), dev(0.0), dev(0.0)
     tm.velocity(dev(p), dev(minv), vel=vel, q=q, eps=0.37, kinetic=kin)
     tm.velocity(dev(p), dev(minv), kinetic=kin2)
