@@ -220,3 +220,53 @@ def mass_momentum(minv, d, xi, z0, parent, length, root_var, sigma2):
     _, pw, _ = tree_prior(w, parent, length, root_var, sigma2)
     p[z0:z0 + m] = np.sqrt(np.maximum(np.asarray(d, float), 0.0)) * xi[z0:z0 + m] + pw
     return p
+
+
+def joint_mass_matrix(minv, d, A, B, z0, parent, length, root_var, sigma2):
+    """The dense joint mass: diag(1 / minv), with [[A, B^T], [B, diag(d) + P]] on
+    the coordinates [0, nc) and the rate block [z0, z0 + m); P from the
+    long-double prior.  For well-conditioned trees only (P is rounded to FP64)."""
+    minv = np.asarray(minv, float)
+    A, B = np.atleast_2d(np.asarray(A, float)), np.asarray(B, float)
+    nc = A.shape[0]
+    m = (np.asarray(parent).size + 1) // 2
+    M = np.diag(1.0 / minv)
+    M[:nc, :nc] = A
+    M[z0:z0 + m, z0:z0 + m] = np.diag(np.maximum(np.asarray(d, float), 0.0)) + precision_matrix(
+        parent, length, root_var, sigma2)
+    M[z0:z0 + m, :nc] = B
+    M[:nc, z0:z0 + m] = B.T
+    return M
+
+
+def joint_mass_velocity(minv, d, A, B, p, z0, parent, length, root_var, sigma2):
+    """M^-1 p for the joint mass by block elimination on the rate block:
+    y = M_z^-1 p_z and U = M_z^-1 B by mass_velocity (refined Woodbury, no
+    inverse of V), S = A - B^T U, x_g = S^-1 (p_g - B^T y), x_z = y - U x_g;
+    minv * p elsewhere."""
+    A, B = np.atleast_2d(np.asarray(A, float)), np.asarray(B, float)
+    nc = A.shape[0]
+    m = (np.asarray(parent).size + 1) // 2
+    p = np.asarray(p, float)
+    x = np.asarray(minv, float) * p
+    y = mass_velocity(d, p[z0:z0 + m], parent, length, root_var, sigma2)
+    U = np.column_stack([mass_velocity(d, B[:, j], parent, length, root_var, sigma2) for j in range(nc)])
+    S = A - B.T @ U
+    xg = np.linalg.solve(S, p[:nc] - B.T @ y)
+    x[:nc] = xg
+    x[z0:z0 + m] = y - U @ xg
+    return x
+
+
+def joint_mass_momentum(minv, d, A, B, xi, z0, parent, length, root_var, sigma2):
+    """p ~ N(0, M) for the joint mass from normals xi: p_z as in mass_momentum,
+    then the coupled coordinates from their conditional law given p_z,
+    N(B^T M_z^-1 p_z, S): p_g = U^T p_z + chol(S) xi[:nc]."""
+    A, B = np.atleast_2d(np.asarray(A, float)), np.asarray(B, float)
+    nc = A.shape[0]
+    m = (np.asarray(parent).size + 1) // 2
+    p = mass_momentum(minv, d, xi, z0, parent, length, root_var, sigma2)
+    U = np.column_stack([mass_velocity(d, B[:, j], parent, length, root_var, sigma2) for j in range(nc)])
+    S = A - B.T @ U
+    p[:nc] = U.T @ p[z0:z0 + m] + np.linalg.cholesky(0.5 * (S + S.T)) @ np.asarray(xi, float)[:nc]
+    return p

@@ -244,3 +244,35 @@ def test_mass_momentum_covariance_is_the_mass_matrix():
     p = rng.standard_normal(k)
     np.testing.assert_allclose(M @ tree_oracle.mass_full_velocity(minv, d, p, z0, parent, length, tau0, s2), p,
                                rtol=1e-10, atol=1e-11)
+
+
+def joint_case(rng, m=9, nc=3, z0=4, k=16):
+    parent, length = random_tree(rng, m)
+    G = rng.standard_normal((nc, nc))
+    A = G @ G.T + 4.0 * np.eye(nc)
+    B = 0.3 * rng.standard_normal((m, nc))
+    minv = rng.uniform(0.1, 2.0, k)
+    d = rng.uniform(0.0, 2.0, m)
+    return parent, length, A, B, minv, d, z0, k
+
+
+def test_joint_mass_velocity_equals_the_plain_solve():
+    rng = np.random.default_rng(44)
+    parent, length, A, B, minv, d, z0, k = joint_case(rng)
+    tau0, s2 = 0.3, 1.4
+    M = tree_oracle.joint_mass_matrix(minv, d, A, B, z0, parent, length, tau0, s2)
+    assert np.all(np.linalg.eigvalsh(M) > 0)
+    p = rng.standard_normal(k)
+    got = tree_oracle.joint_mass_velocity(minv, d, A, B, p, z0, parent, length, tau0, s2)
+    np.testing.assert_allclose(got, np.linalg.solve(M, p), rtol=1e-11, atol=1e-12)
+
+
+def test_joint_mass_momentum_covariance_is_the_mass_matrix():
+    rng = np.random.default_rng(45)
+    parent, length, A, B, minv, d, z0, k = joint_case(rng)
+    tau0, s2 = 0.0, 0.9
+    M = tree_oracle.joint_mass_matrix(minv, d, A, B, z0, parent, length, tau0, s2)
+    cols = [tree_oracle.joint_mass_momentum(minv, d, A, B, e, z0, parent, length, tau0, s2)
+            for e in np.eye(k + parent.size)]
+    Am = np.stack(cols, axis=1)
+    np.testing.assert_allclose(Am @ Am.T, M, rtol=1e-10, atol=1e-11 * np.abs(M).max())
