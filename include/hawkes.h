@@ -387,7 +387,18 @@ int hawkes_posterior_tree(int64_t n, int64_t m, const int *seq_idx, const int *p
  * block; no allocation.  Bad scalars, NULL inputs or z0 + m > k give
  * HAWKES_EINVAL, a short ws HAWKES_EWORKSPACE; a plan built for another m
  * makes every output NaN.
+ *
+ * Optionally the first nc coordinates (nc <= z0, nc <= 8: the globals) are
+ * coupled to the rate block, M = [[A, B^T], [B, M_z]] with A nc x nc and
+ * B m x nc.  The caller passes cpl (DEVICE doubles, m nc + 2 nc^2):
+ *     U = M_z^-1 B          m x nc, row i = tip i      (from nc velocity calls)
+ *     S^-1                  nc x nc, row-major, S = A - B^T U (positive definite)
+ *     L                     nc x nc, row-major lower Cholesky factor of S
+ * and then x_g = S^-1 (p_g - U^T p_z), x_z = M_z^-1 p_z - U x_g, and the
+ * momentum's p_g = U^T p_z + L xi_g.  With nc = 0 (cpl may be NULL) the
+ * first coordinates keep the diagonal minv.
  * ------------------------------------------------------------------------ */
+#define HAWKES_TREE_MASS_MAX_COUPLED 8
 
 /* Bytes of DEVICE workspace the three calls below need for m tips (scratch
  * only: nothing in it outlives a call). */
@@ -408,19 +419,21 @@ int hawkes_tree_mass_factor(int64_t m, const int *plan, const double *length, do
  *   q        DEVICE double[k] or NULL: the leapfrog position step q += eps M^-1 p
  *   kinetic  DEVICE double[1] or NULL: p^T M^-1 p / 2
  * At least one of vel, q, kinetic must be given. */
-int hawkes_tree_mass_velocity(int64_t m, const int *plan, const double *fac, int64_t k, int64_t z0,
-                              const double *minv, const double *p, double *vel, double *q, double eps,
-                              double *kinetic, void *ws, size_t ws_bytes, void *stream);
+int hawkes_tree_mass_velocity(int64_t m, const int *plan, const double *fac, int64_t nc, const double *cpl,
+                              int64_t k, int64_t z0, const double *minv, const double *p, double *vel, double *q,
+                              double eps, double *kinetic, void *ws, size_t ws_bytes, void *stream);
 
 /* A momentum p ~ N(0, M) (DEVICE double[k]) from standard normals xi (DEVICE
- * double[k + 2m - 1]): p_i = xi_i / sqrt(minv_i) outside the block and
+ * double[k + 2m - 1]): p_i = xi_i / sqrt(minv_i) outside the block (and the
+ * coupled set, whose p_g is U^T p_z + L xi[0, nc) when nc > 0) and
  * p_z = sqrt(d) xi_z + (sigma^2 V)^-1 w inside, where w is the Brownian motion
  * down the tree driven by the node normals xi[k + v] (v = 0..2m-2 in the
  * tree's node numbering): w_root = sqrt(sigma2 root_var) xi[k + root] and
  * w_v = w_parent + sqrt(sigma2 length_v) xi[k + v]. */
 int hawkes_tree_mass_momentum(int64_t m, const int *plan, const double *length, double root_var, double sigma2,
-                              const double *dlik, int64_t k, int64_t z0, const double *minv, const double *xi,
-                              double *p, void *ws, size_t ws_bytes, void *stream);
+                              const double *dlik, int64_t nc, const double *cpl, int64_t k, int64_t z0,
+                              const double *minv, const double *xi, double *p, void *ws, size_t ws_bytes,
+                              void *stream);
 
 /* ------------------------------------------------------------------------
  * Posterior-predictive simulation (the forward simulation proposed in the

@@ -219,7 +219,17 @@ cudaError_t launch_tree_prior(int64_t m, const int *plan, const double *len, dou
 // p: tree_mass_factor_kernel computes them once per change of d (one
 // reciprocal per node), and each velocity is then one multiply per node up
 // and one multiply-add per node down, no division.
+//
+// Optional coupling of the first nc <= 8 coordinates (the globals) with the
+// rate block: M = [[A, B^T], [B, M_z]] with A (nc x nc) and B (m x nc).  With
+// U = M_z^-1 B and S = A - B^T U (both supplied by the caller in cpl: U row
+// by row, then S^-1, then the lower Cholesky factor of S), the Schur
+// complement gives
+//     x_g = S^-1 (p_g - U^T p_z),   x_z = M_z^-1 p_z - U x_g,
+// one tree sweep as before plus nc dot products; and p ~ N(0, M) is p_z as
+// before, then p_g = U^T p_z + chol(S) xi_g (p_g given p_z is N(U^T p_z, S)).
 constexpr int TMASS_SMEM_MAX_TIPS = 2048;
+constexpr int TMASS_MAX_COUPLED = HAWKES_TREE_MASS_MAX_COUPLED;
 
 __host__ __device__ inline size_t tmass_smem_bytes(int64_t m) {
     // 4 doubles (r, s r, own h, message h / mean X) and 2 ints (children) per
@@ -269,12 +279,14 @@ __global__ void __launch_bounds__(TREE_THREADS)
 template <bool STAGED>
 __global__ void __launch_bounds__(TREE_THREADS)
     tree_mass_velocity_kernel(int64_t m_arg, const int *__restrict__ plan, const double *__restrict__ fac,
-                              int64_t k, int64_t z0, const double *__restrict__ minv, const double *__restrict__ p,
+                              int nc, const double *__restrict__ cpl, int64_t k, int64_t z0,
+                              const double *__restrict__ minv, const double *__restrict__ p,
                               double *__restrict__ vel, double *__restrict__ q, double eps,
                               double *__restrict__ kinetic, double *H, double *HA) {
     pdl_wait();
     extern __shared__ __align__(16) unsigned char tree_smem[];
     __shared__ double sh[TREE_THREADS];
+    __shared__ double s_c[TMASS_MAX_COUPLED], s_xg[TMASS_MAX_COUPLED];
     TreePlan T = tree_plan_view(plan);
     const int m = T.m;
     if ((int64_t)m != m_arg || T.levels < 1 || T.levels > m - 1) {  // a plan for another tree: touch no scratch
@@ -310,9 +322,9 @@ __global__ void __launch_bounds__(TREE_THREADS)
         __syncthreads();
     }
     double kin = 0.0;
-    // coordinates outside the rate block: the diagonal mass
+    // coordinates outside the rate block and the coupled set: the diagonal mass
     for (int64_t i = threadIdx.x; i < k; i += TREE_THREADS) {
-        if (i >= z0 && i < z0 + m) continue;
+        if ((i >= z0 && i < z0 + m) || i < nc) continue;
         const double v = minv[i] * p[i];
         if (vel) vel[i] = v;
         if (q) q[i] += eps * v;
@@ -322,6 +334,19 @@ __global__ void __launch_bounds__(TREE_THREADS)
         const double h = p[z0 + i];
         HA[i] = h;
         H[i] = h * R[i];
+    }
+    if (nc > 0) {  // c = U^T p_z (the barrier inside also orders the tips' writes above)
+        double cv[TMASS_MAX_COUPLED];
+#pragma unroll
+        for (int j = 0; j < TMASS_MAX_COUPLED; ++j) cv[j] = 0.0;
+        for (int i = threadIdx.x; i < m; i += TREE_THREADS) {
+            const double pz = p[z0 + i];
+#pragma unroll
+            for (int j = 0; j < TMASS_MAX_COUPLED; ++j)
+                if (j < nc) cv[j] = fma(cpl[(size_t)i * nc + j], pz, cv[j]);
+        }
+        const double c = block_sum_multi<TREE_THREADS, TMASS_MAX_COUPLED>(cv, sh);
+        if (threadIdx.x < nc) s_c[threadIdx.x] = c;
     }
     __syncthreads();
     const int root = T.order[m - 2];
@@ -346,8 +371,22 @@ __global__ void __launch_bounds__(TREE_THREADS)
         }
         __syncthreads();
     }
+    if (nc > 0) {  // x_g = S^-1 (p_g - U^T p_z), by threads 0..nc-1
+        const double *Sinv = cpl + (size_t)m * nc;
+        if (threadIdx.x < nc) {
+            const int j = threadIdx.x;
+            double x = 0.0;
+            for (int l = 0; l < nc; ++l) x = fma(Sinv[j * nc + l], p[l] - s_c[l], x);
+            s_xg[j] = x;
+            if (vel) vel[j] = x;
+            if (q) q[j] += eps * x;
+            kin += p[j] * x;
+        }
+        __syncthreads();
+    }
     for (int i = threadIdx.x; i < m; i += TREE_THREADS) {
-        const double v = H[i];
+        double v = H[i];
+        for (int j = 0; j < nc; ++j) v = fma(-cpl[(size_t)i * nc + j], s_xg[j], v);  // x_z = M_z^-1 p_z - U x_g
         if (vel) vel[z0 + i] = v;
         if (q) q[z0 + i] += eps * v;
         kin += p[z0 + i] * v;
@@ -355,6 +394,32 @@ __global__ void __launch_bounds__(TREE_THREADS)
     if (kinetic) {
         kin = block_sum<TREE_THREADS>(kin, sh);
         if (threadIdx.x == 0) *kinetic = 0.5 * kin;
+    }
+}
+
+// The coupled coordinates' momentum given the rate block's: p_g = U^T p_z +
+// chol(S) xi_g, xi_g = xi[0, nc).  One block.
+__global__ void __launch_bounds__(TREE_THREADS)
+    tree_mass_couple_momentum_kernel(int64_t m, int64_t z0, int nc, const double *__restrict__ cpl,
+                                     const double *__restrict__ xi, double *__restrict__ p) {
+    pdl_wait();
+    __shared__ double sh[(TREE_THREADS / 32) * TMASS_MAX_COUPLED];
+    double cv[TMASS_MAX_COUPLED];
+#pragma unroll
+    for (int j = 0; j < TMASS_MAX_COUPLED; ++j) cv[j] = 0.0;
+    for (int64_t i = threadIdx.x; i < m; i += TREE_THREADS) {
+        const double pz = p[z0 + i];
+#pragma unroll
+        for (int j = 0; j < TMASS_MAX_COUPLED; ++j)
+            if (j < nc) cv[j] = fma(cpl[(size_t)i * nc + j], pz, cv[j]);
+    }
+    const double c = block_sum_multi<TREE_THREADS, TMASS_MAX_COUPLED>(cv, sh);
+    if (threadIdx.x < nc) {
+        const int j = threadIdx.x;
+        const double *Lc = cpl + (size_t)m * nc + (size_t)nc * nc;
+        double v = c;
+        for (int l = 0; l <= j; ++l) v = fma(Lc[j * nc + l], xi[l], v);
+        p[j] = v;
     }
 }
 
@@ -415,9 +480,9 @@ cudaError_t launch_tree_mass_factor(int64_t m, const int *plan, const double *le
     return cudaGetLastError();
 }
 
-cudaError_t launch_tree_mass_velocity(int64_t m, const int *plan, const double *fac, int64_t k, int64_t z0,
-                                      const double *minv, const double *p, double *vel, double *q, double eps,
-                                      double *kinetic, double *scratch, cudaStream_t s) {
+cudaError_t launch_tree_mass_velocity(int64_t m, const int *plan, const double *fac, int nc, const double *cpl,
+                                      int64_t k, int64_t z0, const double *minv, const double *p, double *vel,
+                                      double *q, double eps, double *kinetic, double *scratch, cudaStream_t s) {
     const int64_t nn = 2 * m - 1;
     double *H = scratch, *HA = H + nn;
     if (m <= TMASS_SMEM_MAX_TIPS) {
@@ -431,18 +496,19 @@ cudaError_t launch_tree_mass_velocity(int64_t m, const int *plan, const double *
             if (e != cudaSuccess) return e;
             if (dev >= 0 && dev < 64) attr_set[dev] = 1;
         }
-        launch_pdl(tree_mass_velocity_kernel<true>, 1, TREE_THREADS, tmass_smem_bytes(m), s, m, plan, fac, k, z0, minv,
-                   p, vel, q, eps, kinetic, H, HA);
+        launch_pdl(tree_mass_velocity_kernel<true>, 1, TREE_THREADS, tmass_smem_bytes(m), s, m, plan, fac, nc, cpl, k,
+                   z0, minv, p, vel, q, eps, kinetic, H, HA);
     } else {
-        launch_pdl(tree_mass_velocity_kernel<false>, 1, TREE_THREADS, 0, s, m, plan, fac, k, z0, minv, p, vel, q, eps,
-                   kinetic, H, HA);
+        launch_pdl(tree_mass_velocity_kernel<false>, 1, TREE_THREADS, 0, s, m, plan, fac, nc, cpl, k, z0, minv, p, vel,
+                   q, eps, kinetic, H, HA);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_tree_mass_momentum(int64_t m, const int *plan, const double *len, double tau0, double sigma2,
-                                      const double *dlik, int64_t k, int64_t z0, const double *minv, const double *xi,
-                                      double *p, double *scratch, cudaStream_t s) {
+                                      const double *dlik, int nc, const double *cpl, int64_t k, int64_t z0,
+                                      const double *minv, const double *xi, double *p, double *scratch,
+                                      cudaStream_t s) {
     const int64_t nn = 2 * m - 1;
     double *w = scratch, *pw = w + nn, *prior_scratch = pw + m;
     launch_pdl(tree_brownian_kernel, 1, TREE_THREADS, 0, s, m, plan, len, tau0, sigma2, dlik, k, z0, minv, xi, p, w);
@@ -451,6 +517,11 @@ cudaError_t launch_tree_mass_momentum(int64_t m, const int *plan, const double *
     e = launch_tree_prior(m, plan, len, tau0, sigma2, w, prior_scratch, nullptr, pw, nullptr, s);
     if (e != cudaSuccess) return e;
     launch_pdl(tree_mass_add_kernel, (unsigned)((m + 255) / 256), 256, 0, s, m, z0, (const double *)pw, p);
+    if (nc > 0) {
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        launch_pdl(tree_mass_couple_momentum_kernel, 1, TREE_THREADS, 0, s, m, z0, nc, cpl, xi, p);
+    }
     return cudaGetLastError();
 }
 
@@ -567,10 +638,11 @@ size_t hawkes_tree_mass_workspace_size(int64_t m) {
     return (nn + (size_t)m + 5 * nn) * sizeof(double);
 }
 
-static int tree_mass_args(int64_t m, const int *plan, int64_t k, int64_t z0, const double *minv, void *ws,
-                          size_t ws_bytes) {
+static int tree_mass_args(int64_t m, const int *plan, int64_t nc, const double *cpl, int64_t k, int64_t z0,
+                          const double *minv, void *ws, size_t ws_bytes) {
     if (m < 2 || m > HAWKES_TREE_MAX_TIPS || !plan || !minv || !ws) return HAWKES_EINVAL;
     if (z0 < 0 || k < m || z0 > k - m) return HAWKES_EINVAL;
+    if (nc < 0 || nc > HAWKES_TREE_MASS_MAX_COUPLED || nc > z0 || (nc > 0 && !cpl)) return HAWKES_EINVAL;
     if (ws_bytes < hawkes_tree_mass_workspace_size(m)) return HAWKES_EWORKSPACE;
     return HAWKES_OK;
 }
@@ -590,26 +662,27 @@ int hawkes_tree_mass_factor(int64_t m, const int *plan, const double *length, do
                : HAWKES_ECUDA;
 }
 
-int hawkes_tree_mass_velocity(int64_t m, const int *plan, const double *fac, int64_t k, int64_t z0,
-                              const double *minv, const double *p, double *vel, double *q, double eps,
-                              double *kinetic, void *ws, size_t ws_bytes, void *stream) {
-    const int rc = tree_mass_args(m, plan, k, z0, minv, ws, ws_bytes);
+int hawkes_tree_mass_velocity(int64_t m, const int *plan, const double *fac, int64_t nc, const double *cpl,
+                              int64_t k, int64_t z0, const double *minv, const double *p, double *vel, double *q,
+                              double eps, double *kinetic, void *ws, size_t ws_bytes, void *stream) {
+    const int rc = tree_mass_args(m, plan, nc, cpl, k, z0, minv, ws, ws_bytes);
     if (rc != HAWKES_OK) return rc;
     if (!fac || !p || (!vel && !q && !kinetic) || !isfinite(eps)) return HAWKES_EINVAL;
-    return hk::launch_tree_mass_velocity(m, plan, fac, k, z0, minv, p, vel, q, eps, kinetic, (double *)ws,
-                                         (cudaStream_t)stream) == cudaSuccess
+    return hk::launch_tree_mass_velocity(m, plan, fac, (int)nc, cpl, k, z0, minv, p, vel, q, eps, kinetic,
+                                         (double *)ws, (cudaStream_t)stream) == cudaSuccess
                ? HAWKES_OK
                : HAWKES_ECUDA;
 }
 
 int hawkes_tree_mass_momentum(int64_t m, const int *plan, const double *length, double root_var, double sigma2,
-                              const double *dlik, int64_t k, int64_t z0, const double *minv, const double *xi,
-                              double *p, void *ws, size_t ws_bytes, void *stream) {
-    const int rc = tree_mass_args(m, plan, k, z0, minv, ws, ws_bytes);
+                              const double *dlik, int64_t nc, const double *cpl, int64_t k, int64_t z0,
+                              const double *minv, const double *xi, double *p, void *ws, size_t ws_bytes,
+                              void *stream) {
+    const int rc = tree_mass_args(m, plan, nc, cpl, k, z0, minv, ws, ws_bytes);
     if (rc != HAWKES_OK) return rc;
     if (!length || !dlik || !xi || !p || !tree_scalars_ok(root_var, sigma2)) return HAWKES_EINVAL;
-    return hk::launch_tree_mass_momentum(m, plan, length, root_var, sigma2, dlik, k, z0, minv, xi, p, (double *)ws,
-                                         (cudaStream_t)stream) == cudaSuccess
+    return hk::launch_tree_mass_momentum(m, plan, length, root_var, sigma2, dlik, (int)nc, cpl, k, z0, minv, xi, p,
+                                         (double *)ws, (cudaStream_t)stream) == cudaSuccess
                ? HAWKES_OK
                : HAWKES_ECUDA;
 }

@@ -402,7 +402,7 @@ def load_state(path) -> dict:
 
 def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_every=100, target_accept=0.8,
            mass_floor=1e-2, seed=0, keep=None, record=None, use_graph=True, checkpoint=None, checkpoint_every=0,
-           resume=None, mass="diag"):
+           resume=None, mass="diag", fd_step=1e-3):
     """Run n_warmup + n_iter HMC iterations from q0 (device tensor); returns a Chain.
 
     mass: "diag", the diagonal mass of Section 2.3.2 (a running average of
@@ -410,7 +410,12 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
     the same diagonal outside the rate block and diag(d) + (sigma2 V)^-1 on
     it, d a running average of the likelihood's own curvature
     max(-H_diag - diag((sigma2 V)^-1), 0), so that the prior's tree
-    correlations are preconditioned exactly (tree.TreeMass).
+    correlations are preconditioned exactly (tree.TreeMass); or
+    "tree_joint": the tree mass on the rates plus a dense block for the six
+    globals and its coupling to the rates, [[A, B^T], [B, M_z]], with A and
+    B running averages of minus the log posterior's Hessian columns along
+    the globals, taken by central differences of the gradient (step fd_step
+    in the log scale; 12 extra gradients per mass update).
 
     keep: optional index array of coordinates to store (all by default);
     record: optional callback given every leapfrog position and its gradient;
@@ -432,15 +437,37 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
     keep_t = torch.as_tensor(keep, device=dev)
     total = n_warmup + n_iter
     da = DualAveraging(eps0, target_accept)
-    if mass not in ("diag", "tree"):
-        raise ValueError("mass must be 'diag' or 'tree'")
+    if mass not in ("diag", "tree", "tree_joint"):
+        raise ValueError("mass must be 'diag', 'tree' or 'tree_joint'")
     tm = xi = None
-    if mass == "tree":
+    joint = None  # running averages of the coupled blocks A (6 x 6) and B (m x 6)
+    if mass != "diag":
         if getattr(post, "tree", None) is None:
-            raise ValueError("mass='tree' needs a posterior with a tree prior")
+            raise ValueError(f"mass='{mass}' needs a posterior with a tree prior")
         from . import tree as tree_mod
-        tm = tree_mod.TreeMass(post.tree, dim, z0=6)
+        tm = tree_mod.TreeMass(post.tree, dim, z0=6, nc=6 if mass == "tree_joint" else 0)
         xi = torch.empty(tm.n_normals, **f64)
+
+    def hessian_columns(qc):
+        """-(d grad / d q_k) for the six globals by central differences: (dim x 6)."""
+        cols = np.empty((dim, 6))
+        qp = torch.empty_like(qc)
+        for kk in range(6):
+            qp.copy_(qc)
+            qp[kk] += fd_step
+            gp = post.evaluate(qp)["grad"].cpu().numpy()
+            qp[kk] -= 2 * fd_step
+            gm = post.evaluate(qp)["grad"].cpu().numpy()
+            cols[:, kk] = -(gp - gm) / (2 * fd_step)
+        return cols
+
+    def update_joint(qc, weight):
+        # the blocks' running average (weight = number of earlier updates), then the coupling
+        cols = hessian_columns(qc)
+        A, B = 0.5 * (cols[:6] + cols[:6].T), cols[6:6 + tm.m]
+        if weight == 0 or joint is None:
+            return {"A": A, "B": B}
+        return {"A": (weight * joint["A"] + A) / (weight + 1), "B": (weight * joint["B"] + B) / (weight + 1)}
 
     def rate_curvature(hdiag_q):
         # the log-likelihood's curvature on the rates: the posterior's minus the prior's
@@ -455,6 +482,9 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
         if tm is not None:
             tm.d.copy_(rate_curvature(cur["hdiag"]))
             tm.factor()
+            if tm.nc:
+                joint = update_joint(q, 0)
+                tm.set_coupling(joint["A"], joint["B"], floor=mass_floor)
         eps = eps0
         draws = np.empty((n_iter, len(keep)))
         lps, acc, aprob = np.empty(n_iter), np.zeros(n_iter, bool), np.empty(n_iter)
@@ -470,6 +500,9 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
         if tm is not None:
             tm.d.copy_(st["tree_d"].to(dev))
             tm.factor()
+            if tm.nc:
+                joint = st["joint"]
+                tm.set_coupling(joint["A"], joint["B"], floor=mass_floor)
         da.__dict__.update(st["dual_averaging"])
         gen.set_state(st["gen_state"])
         rng.bit_generator.state = st["rng_state"]
@@ -527,6 +560,9 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
             if tm is not None:
                 tm.d.mul_(n_mass).add_(rate_curvature(hd["hdiag"])).div_(n_mass + 1)
                 tm.factor()  # in place: a captured trajectory reads the new coefficients
+                if tm.nc:
+                    joint = update_joint(q, n_mass)
+                    tm.set_coupling(joint["A"], joint["B"], floor=mass_floor)
             mass = (n_mass * mass + new) / (n_mass + 1)  # running average of the Hessian-based masses
             n_mass += 1
             torch.reciprocal(mass, out=minv)
@@ -548,7 +584,7 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
                 "mass": mass.cpu(), "minv": minv.cpu(), "n_mass": n_mass, "eps": eps,
                 "dual_averaging": dict(da.__dict__), "gen_state": gen.get_state(),
                 "rng_state": rng.bit_generator.state, "draws": draws, "lps": lps, "acc": acc, "aprob": aprob,
-                "calls": dict(post.calls), "tree_d": tm.d.cpu() if tm is not None else None,
+                "calls": dict(post.calls), "tree_d": tm.d.cpu() if tm is not None else None, "joint": joint,
                 "spent_warm": spent_warm + (seg if it < n_warmup else 0.0),
                 "spent_samp": spent_samp + (seg if it >= n_warmup else 0.0)})
             # the checkpoint's own cost is left out of both phases

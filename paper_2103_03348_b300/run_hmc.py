@@ -13,7 +13,9 @@ mass matrix refreshed every 100 iterations from the Hessian diagonal (Section
 2.3.2), start at the generating values.  With --mass tree the rate block's
 mass is instead diag(d) + (sigma^2 V)^-1, d the likelihood's curvature from the
 same Hessian diagonal: the phylogenetic prior's correlations are then
-preconditioned exactly (tree prior only).  Prints one JSON line with the
+preconditioned exactly (tree prior only); --mass tree_joint adds a dense
+block for the six globals and its coupling to the rates, from central
+differences of the gradient along the globals.  Prints one JSON line with the
 acceptance rate, sampling time, and min/median/max ESS and ESS/s for the six
 globals and for the 1,610 log-rates.
 """
@@ -83,8 +85,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--prior", default="tree", choices=["tree", "dense"])
-    ap.add_argument("--mass", default="diag", choices=["diag", "tree"],
-                    help="diagonal mass (Section 2.3.2), or the tree-structured one on the rates")
+    ap.add_argument("--mass", default="diag", choices=["diag", "tree", "tree_joint"],
+                    help="diagonal mass (Section 2.3.2), the tree-structured one on the rates, or that one with "
+                         "the globals' dense block coupled to the rates")
     ap.add_argument("--checkpoint", default=None, help="write the sampler state here every --every iterations")
     ap.add_argument("--every", type=int, default=200)
     ap.add_argument("--resume", default=None, help="continue the chain from this checkpoint")

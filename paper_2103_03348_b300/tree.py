@@ -34,9 +34,9 @@ def _lib():
         L.hawkes_tree_mass_workspace_size.restype = sz
         L.hawkes_tree_mass_factor.argtypes = [i64, vp, vp, d, d, vp, vp, vp, sz, vp]
         L.hawkes_tree_mass_factor.restype = ctypes.c_int
-        L.hawkes_tree_mass_velocity.argtypes = [i64, vp, vp, i64, i64, vp, vp, vp, vp, d, vp, vp, sz, vp]
+        L.hawkes_tree_mass_velocity.argtypes = [i64, vp, vp, i64, vp, i64, i64, vp, vp, vp, vp, d, vp, vp, sz, vp]
         L.hawkes_tree_mass_velocity.restype = ctypes.c_int
-        L.hawkes_tree_mass_momentum.argtypes = [i64, vp, vp, d, d, vp, i64, i64, vp, vp, vp, vp, sz, vp]
+        L.hawkes_tree_mass_momentum.argtypes = [i64, vp, vp, d, d, vp, i64, vp, i64, i64, vp, vp, vp, vp, sz, vp]
         L.hawkes_tree_mass_momentum.restype = ctypes.c_int
         L._tree_typed = True
     return L
@@ -108,9 +108,12 @@ class TreeMass:
     k-dimensional state, M_z = diag(d) + (sigma2 V)^-1 on them, d >= 0 the
     likelihood's curvature (self.d, a device tensor the caller updates in
     place, calling factor() after each change).  Every call is a tree sweep
-    on the device (O(m), no M x M matrix), enqueued on the current stream."""
+    on the device (O(m), no M x M matrix), enqueued on the current stream.
 
-    def __init__(self, prior: TreePrior, k: int, z0: int = 6):
+    nc > 0 couples the first nc coordinates with the rate block through
+    set_coupling(A, B): M = [[A, B^T], [B, M_z]] (see hawkes.h)."""
+
+    def __init__(self, prior: TreePrior, k: int, z0: int = 6, nc: int = 0):
         if z0 < 0 or z0 + prior.m > k:
             raise hawkes.HawkesError(hawkes.EINVAL, "the rate block must lie inside the state")
         self.prior, self.k, self.z0, self.m = prior, int(k), int(z0), prior.m
@@ -119,6 +122,50 @@ class TreeMass:
         self.fac = torch.empty(2 * (2 * self.m - 1), dtype=torch.float64, device=dev)
         self.ws = torch.empty(int(_lib().hawkes_tree_mass_workspace_size(self.m)), dtype=torch.uint8, device=dev)
         self.n_normals = self.k + 2 * self.m - 1
+        if not 0 <= nc <= min(self.z0, 8):
+            raise hawkes.HawkesError(hawkes.EINVAL, "at most 8 coupled coordinates, all before the rate block")
+        self.nc = int(nc)
+        self.cpl = torch.zeros(max(1, self.m * self.nc + 2 * self.nc * self.nc), dtype=torch.float64, device=dev)
+        self.coupling_shrink = 1.0
+
+    def set_coupling(self, A, B, floor=1e-2):
+        """Couple the first nc coordinates to the rate block with the mass
+        blocks A (nc x nc) and B (m x nc) (host arrays), for the current d
+        (call factor() first).  A is made positive definite by clipping its
+        eigenvalues at floor; B is shrunk by a factor c <= 1 where needed so
+        that S = A - c^2 B^T M_z^-1 B keeps at least a tenth of A's curvature
+        in every direction (self.coupling_shrink = c).  Small host algebra on
+        nc x nc matrices; U = M_z^-1 B comes from nc velocity sweeps."""
+        nc, m = self.nc, self.m
+        A = np.asarray(A, float).reshape(nc, nc)
+        B = np.asarray(B, float).reshape(m, nc)
+        w, Q = np.linalg.eigh(0.5 * (A + A.T))
+        A = (Q * np.maximum(w, floor)) @ Q.T
+        dev = self.d.device
+        U = np.empty((m, nc))
+        minv = torch.ones(self.k, dtype=torch.float64, device=dev)
+        vel = torch.empty(self.k, dtype=torch.float64, device=dev)
+        pb = torch.zeros(self.k, dtype=torch.float64, device=dev)
+        saved, self.nc = self.nc, 0  # the sweeps for U use the uncoupled mass
+        try:
+            for j in range(nc):
+                pb[self.z0:self.z0 + m] = torch.as_tensor(B[:, j], device=dev)
+                self.velocity(pb, minv, vel=vel)
+                U[:, j] = vel[self.z0:self.z0 + m].cpu().numpy()
+        finally:
+            self.nc = saved
+        G = B.T @ U
+        G = 0.5 * (G + G.T)
+        wa, Qa = np.linalg.eigh(A)
+        ih = (Qa / np.sqrt(wa)) @ Qa.T  # A^-1/2
+        lam = float(np.linalg.eigvalsh(ih @ G @ ih).max())
+        c = 1.0 if lam <= 0.9 else float(np.sqrt(0.9 / lam))
+        S = A - c * c * G
+        S = 0.5 * (S + S.T)
+        Lc = np.linalg.cholesky(S)
+        buf = np.concatenate([(c * U).ravel(), np.linalg.inv(S).ravel(), Lc.ravel()])
+        self.cpl[:buf.size].copy_(torch.as_tensor(buf, device=dev))
+        self.coupling_shrink = c
 
     def factor(self):
         """The sweep coefficients for the current self.d (call after changing it)."""
@@ -132,9 +179,9 @@ class TreeMass:
         """vel = M^-1 p; q += eps M^-1 p; kinetic = p^T M^-1 p / 2 (each when given)."""
         t = lambda a: ctypes.c_void_p(a.data_ptr() if a is not None else 0)  # noqa: E731
         s = ctypes.c_void_p(torch.cuda.current_stream(p.device).cuda_stream)
-        _check(_lib().hawkes_tree_mass_velocity(self.m, t(self.prior.plan), t(self.fac), self.k, self.z0, t(minv), t(p),
-                                                t(vel), t(q), float(eps), t(kinetic), t(self.ws),
-                                                ctypes.c_size_t(self.ws.numel()), s))
+        _check(_lib().hawkes_tree_mass_velocity(self.m, t(self.prior.plan), t(self.fac), self.nc, t(self.cpl), self.k,
+                                                self.z0, t(minv), t(p), t(vel), t(q), float(eps), t(kinetic),
+                                                t(self.ws), ctypes.c_size_t(self.ws.numel()), s))
 
     def momentum(self, minv, xi, p):
         """p ~ N(0, M) from xi, k + 2m - 1 standard normals (device)."""
@@ -144,6 +191,6 @@ class TreeMass:
         s = ctypes.c_void_p(torch.cuda.current_stream(p.device).cuda_stream)
         pr = self.prior
         _check(_lib().hawkes_tree_mass_momentum(self.m, t(pr.plan), t(pr.length), pr.root_var, pr.sigma2, t(self.d),
-                                                self.k, self.z0, t(minv), t(xi), t(p), t(self.ws),
-                                                ctypes.c_size_t(self.ws.numel()), s))
+                                                self.nc, t(self.cpl), self.k, self.z0, t(minv), t(xi), t(p),
+                                                t(self.ws), ctypes.c_size_t(self.ws.numel()), s))
         return p

@@ -156,12 +156,12 @@ def test_tree_mass_argument_checks(L):
     need = int(T.hawkes_tree_mass_workspace_size(m))
     assert T.hawkes_tree_mass_workspace_size(1) == 0
     assert need >= (6 * (2 * m - 1) + m) * 8
-    good = dict(m=m, s2=1.0, rv=0.0, k=16, z0=6, eps=0.1, ws=need)
+    good = dict(m=m, s2=1.0, rv=0.0, k=16, z0=6, nc=6, eps=0.1, ws=need)
 
     def vel(vel_=f, q=f, kin=f, **kw):
         a = dict(good, **kw)
-        return T.hawkes_tree_mass_velocity(a["m"], f, f, a["k"], a["z0"], f, f, vel_, q, a["eps"], kin, f,
-                                           ctypes.c_size_t(a["ws"]), None)
+        return T.hawkes_tree_mass_velocity(a["m"], f, f, a["nc"], f, a["k"], a["z0"], f, f, vel_, q, a["eps"], kin,
+                                           f, ctypes.c_size_t(a["ws"]), None)
 
     def fac(**kw):
         a = dict(good, **kw)
@@ -169,13 +169,16 @@ def test_tree_mass_argument_checks(L):
 
     def mom(**kw):
         a = dict(good, **kw)
-        return T.hawkes_tree_mass_momentum(a["m"], f, f, a["rv"], a["s2"], f, a["k"], a["z0"], f, f, f, f,
-                                           ctypes.c_size_t(a["ws"]), None)
+        return T.hawkes_tree_mass_momentum(a["m"], f, f, a["rv"], a["s2"], f, a["nc"], f, a["k"], a["z0"], f, f, f,
+                                           f, ctypes.c_size_t(a["ws"]), None)
 
     for call in (vel, mom, fac):
         assert call(m=1) == hawkes.EINVAL
         assert call(ws=need - 8) == hawkes.EWORKSPACE
     for call in (vel, mom):
+        assert call(nc=7) == hawkes.EINVAL              # coupled coordinates overlap the rate block
+        assert call(nc=-1) == hawkes.EINVAL
+        assert call(nc=9, z0=9, k=20) == hawkes.EINVAL  # more than 8 coupled coordinates
         assert call(k=9) == hawkes.EINVAL               # the block does not fit in the state
         assert call(z0=7) == hawkes.EINVAL              # z0 + m > k
         assert call(z0=-1) == hawkes.EINVAL
