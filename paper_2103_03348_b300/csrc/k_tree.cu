@@ -217,8 +217,9 @@ cudaError_t launch_tree_prior(int64_t m, const int *plan, const double *len, dou
 // conditioned however small the branches (V's condition number reaches ~1e9
 // on coalescent trees).  The precisions J, hence r and s r, do not depend on
 // p: tree_mass_factor_kernel computes them once per change of d (one
-// reciprocal per node), and each velocity is then one multiply per node up
-// and one multiply-add per node down, no division.
+// reciprocal per node), and each velocity then takes an addition and a
+// multiply per node up and a multiply and a multiply-add per branch down,
+// no division.
 //
 // Optional coupling of the first nc <= 8 coordinates (the globals) with the
 // rate block: M = [[A, B^T], [B, M_z]] with A (nc x nc) and B (m x nc).  With
