@@ -302,26 +302,57 @@ def run_ours(args, rank, world, local_rank):
                               "steps": args.steps, "warmup": args.warmup, "kernel_only": True}), flush=True)
         return 0
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: every step uploads x, y, t, r from pinned
+    # host memory and reads loglik, gradient and Hessian diagonal back.  Two device sets of inputs and
+    # outputs and a copy stream let step i+1's upload and step i's read-back run during step i's
+    # evaluation (a set is refilled only once the evaluation that used it has finished); the L2 flush
+    # before each evaluation is inside the timed region here.  Time = first upload to last read-back.
     pin = lambda a: torch.tensor(a, dtype=torch.float64).pin_memory()  # noqa: E731
-    hx, hy, ht, hr = pin(w.x), pin(w.y), pin(w.t), pin(w.r)
-    h_out = [torch.empty(6 + n, dtype=torch.float64).pin_memory() for _ in range(2)]
-    h_ll = torch.empty((), dtype=torch.float64).pin_memory()
+    host_in = (pin(w.x), pin(w.y), pin(w.t), pin(w.r))
     e2e_steps = max(3, min(args.steps, 30))
-    e2e_ms = []
-    for i in range(e2e_steps + 1):
-        flush.zero_()
-        ev[0].record(stream)
-        for hsrc, dsrc in ((hx, x), (hy, y), (ht, t), (hr, r)):
-            dsrc.copy_(hsrc, non_blocking=True)
-        step(False)
-        h_ll.copy_(out["loglik"], non_blocking=True)
-        h_out[0].copy_(out["grad"], non_blocking=True)
-        h_out[1].copy_(out["hdiag"], non_blocking=True)
-        ev[1].record(stream)
-        ev[1].synchronize()
-        if i > 0:
-            e2e_ms.append(ev[0].elapsed_time(ev[1]))
+    sets = [((x, y, t, r), out), (tuple(torch.empty_like(a) for a in (x, y, t, r)),
+                                  {k: torch.empty_like(v) for k, v in out.items()})]
+    host_out = [{k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items() if k != "status"}
+                for _ in range(e2e_steps)]
+    copy_s = torch.cuda.Stream(device=dev)
+    uploaded = [torch.cuda.Event() for _ in range(2)]
+    evaluated = [torch.cuda.Event() for _ in range(2)]
+    t_first, t_last = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def upload(i):
+        dins, _ = sets[i % 2]
+        with torch.cuda.stream(copy_s):
+            if i >= 2:
+                copy_s.wait_event(evaluated[i % 2])  # the set's previous evaluation has read its inputs
+            for hsrc, dsrc in zip(host_in, dins):
+                dsrc.copy_(hsrc, non_blocking=True)
+            uploaded[i % 2].record(copy_s)
+
+    def e2e_pass():
+        torch.cuda.synchronize()
+        t_first.record(copy_s)
+        upload(0)
+        for i in range(e2e_steps):
+            if i + 1 < e2e_steps:
+                upload(i + 1)
+            (dx, dy, dt, dr), dout = sets[i % 2]
+            stream.wait_event(uploaded[i % 2])
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            hawkes._call("hess", dx, dy, dt, dr, w.params, prec, stream=stream, check=False, out=dout)
+            evaluated[i % 2].record(stream)
+            with torch.cuda.stream(copy_s):
+                copy_s.wait_event(evaluated[i % 2])
+                for k, hdst in host_out[i].items():
+                    hdst.copy_(dout[k], non_blocking=True)
+        t_last.record(copy_s)
+        t_last.synchronize()
+        return t_first.elapsed_time(t_last) / e2e_steps
+
+    e2e_pass()  # warm-up: first use of the second set and of the copy stream
+    e2e_ms = [e2e_pass()]
+    if not all(np.array_equal(host_out[-1][k].numpy(), out[k].cpu().numpy()) for k in host_out[-1]):
+        raise RuntimeError("the end-to-end pass read back other results than the resident evaluation")
     e2e_value = world * pairs / (float(np.mean(e2e_ms)) * 1e-3)
 
     # the same evaluation with exact background band skipping (bit-identical results)
