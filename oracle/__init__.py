@@ -152,9 +152,9 @@ def _pi(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
 
 
-def rows(x, y, t, r, params, idx, threads: int = 0):
+def rows(x, y, t, r, params, idx, threads: int = 0, lib=None):
     """lambda_n and per-row derivative sums (d lambda_n/dp, d2 lambda_n/dp2) for the rows in idx."""
-    lib = _load()
+    lib = lib or _load()
     x, y, t, r, p = _arr(x), _arr(y), _arr(t), _arr(r), _arr(params)
     idx = np.ascontiguousarray(idx, dtype=np.int64)
     k = idx.shape[0]
@@ -166,9 +166,9 @@ def rows(x, y, t, r, params, idx, threads: int = 0):
     return lam, d1.reshape(k, NPAR), d2.reshape(k, NPAR)
 
 
-def rate_terms(x, y, t, r, params, lam, idx, threads: int = 0):
+def rate_terms(x, y, t, r, params, lam, idx, threads: int = 0, lib=None):
     """Gradient and Hessian diagonal w.r.t. r_m for the sources in idx, given lambda for later targets."""
-    lib = _load()
+    lib = lib or _load()
     x, y, t, r, p, lam = _arr(x), _arr(y), _arr(t), _arr(r), _arr(params), _arr(lam)
     idx = np.ascontiguousarray(idx, dtype=np.int64)
     k = idx.shape[0]
