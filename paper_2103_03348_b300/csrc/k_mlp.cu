@@ -248,6 +248,69 @@ __global__ void __launch_bounds__(MH) surrogate_momentum_kernel(const __nv_bfloa
     }
 }
 
+// A whole surrogate leapfrog trajectory over the six globals in one block:
+//   p += eps/2 g(q);  n_steps times { q += eps minv p;  p += eps g(q) },
+// the last momentum step halved.  g is the surrogate gradient of
+// surrogate_momentum_kernel, computed with the same operations in the same
+// order, so the trajectory equals the sequence of surrogate_momentum and
+// position launches bit for bit.  Each thread keeps its row of W2 in
+// registers across the n_steps + 1 evaluations; W3 is staged in shared memory.
+__global__ void __launch_bounds__(MH) surrogate_trajectory_kernel(const __nv_bfloat16 *__restrict__ w,
+                                                                  const double *__restrict__ norm,
+                                                                  double *__restrict__ q, double *__restrict__ p,
+                                                                  const double *__restrict__ minv, double eps,
+                                                                  int n_steps) {
+    __shared__ float z[MI], h1[MH], h2[MH], w3s[MO * MH];
+    __shared__ double qs[MI], ps[MI];
+    const int j = threadIdx.x;
+    float w2r[MH], w1r[MI];
+#pragma unroll
+    for (int k = 0; k < MH; ++k) w2r[k] = bf(w, OFF_W2 + j * MH + k);
+#pragma unroll
+    for (int k = 0; k < MI; ++k) w1r[k] = bf(w, OFF_W1 + j * MI + k);
+    const float b1 = bf(w, OFF_B1 + j), b2 = bf(w, OFF_B2 + j);
+    for (int i = j; i < MO * MH; i += MH) w3s[i] = bf(w, OFF_W3 + i);
+    float b3 = 0.0f;
+    double mi = 0.0;
+    if (j < MI) {
+        qs[j] = q[j];
+        ps[j] = p[j];
+        b3 = bf(w, OFF_B3 + j);
+        mi = minv[j];
+    }
+    __syncthreads();
+    for (int step = 0; step <= n_steps; ++step) {
+        if (j < MI) z[j] = (float)((qs[j] - norm[j]) / norm[6 + j]);
+        __syncthreads();
+        float acc = b1;
+#pragma unroll
+        for (int k = 0; k < MI; ++k) acc = fmaf(w1r[k], z[k], acc);
+        h1[j] = tanhf(acc);
+        __syncthreads();
+        acc = b2;
+#pragma unroll
+        for (int k = 0; k < MH; ++k) acc = fmaf(w2r[k], h1[k], acc);
+        h2[j] = tanhf(acc);
+        __syncthreads();
+        if (j < MO) {  // threads 0..5: one warp, so __syncwarp orders their shared-memory updates
+            float y = b3;
+            for (int k = 0; k < MH; ++k) y = fmaf(w3s[j * MH + k], h2[k], y);
+            double g = norm[12 + j] + norm[18 + j] * (double)y;
+#pragma unroll
+            for (int k = 0; k < MI; ++k) g += norm[24 + j * MI + k] * (qs[k] - norm[k]);
+            const double a = (step == 0 || step == n_steps) ? 0.5 * eps : eps;
+            __syncwarp(0x3fu);  // every g is formed from the old q before any q moves
+            ps[j] += a * g;
+            if (step < n_steps) qs[j] += eps * mi * ps[j];
+        }
+        __syncthreads();
+    }
+    if (j < MI) {
+        q[j] = qs[j];
+        p[j] = ps[j];
+    }
+}
+
 }  // namespace hk
 
 extern "C" {
@@ -311,6 +374,14 @@ int hawkes_surrogate_momentum(const void *w_bf16, const double *q, double *p, do
     if (!w_bf16 || !q || !norm || (!p && !g_out)) return HAWKES_EINVAL;
     hk::surrogate_momentum_kernel<<<1, hk::MH, 0, (cudaStream_t)stream>>>((const __nv_bfloat16 *)w_bf16, q, p, a,
                                                                           norm, g_out);
+    return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
+}
+
+int hawkes_surrogate_trajectory(const void *w_bf16, const double *norm, double *q, double *p, const double *minv,
+                                double eps, int n_steps, void *stream) {
+    if (!w_bf16 || !norm || !q || !p || !minv || n_steps < 0 || !(eps == eps)) return HAWKES_EINVAL;
+    hk::surrogate_trajectory_kernel<<<1, hk::MH, 0, (cudaStream_t)stream>>>((const __nv_bfloat16 *)w_bf16, norm, q,
+                                                                            p, minv, eps, n_steps);
     return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
 }
 

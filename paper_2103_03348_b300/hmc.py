@@ -402,7 +402,7 @@ def load_state(path) -> dict:
 
 def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_every=100, target_accept=0.8,
            mass_floor=1e-2, seed=0, keep=None, record=None, use_graph=True, checkpoint=None, checkpoint_every=0,
-           resume=None, mass="diag", fd_step=1e-3):
+           resume=None, mass="diag", fd_step=1e-3, mass0=None):
     """Run n_warmup + n_iter HMC iterations from q0 (device tensor); returns a Chain.
 
     mass: "diag", the diagonal mass of Section 2.3.2 (a running average of
@@ -429,7 +429,10 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
     gradient, mass, step size and its adaptation, both random streams, draws so
     far, counters) to `checkpoint` every that many iterations;
     resume: a checkpoint to continue from; the chain then equals the one that
-    was never interrupted, bit for bit (the other arguments must match)."""
+    was never interrupted, bit for bit (the other arguments must match);
+    mass0: optional diagonal mass (device tensor [dim]) to start from instead
+    of the Hessian diagonal at q0 (mass="diag" only), e.g. another chain's
+    adapted mass, so that two samplers can be compared with the same one."""
     dev = q0.device
     gen = torch.Generator(device=dev)
     gen.manual_seed(seed)
@@ -490,7 +493,12 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
         q = q0.clone()
         cur = post.evaluate(q, want_hess=True)
         cur = {k: v.clone() for k, v in cur.items()}
-        mass = torch.clamp(-cur["hdiag"], min=mass_floor)
+        if mass0 is not None:
+            if tm is not None or mass0.numel() != dim:
+                raise ValueError("mass0 is a diagonal mass over all coordinates (mass='diag')")
+            mass = mass0.to(**f64).clone()
+        else:
+            mass = torch.clamp(-cur["hdiag"], min=mass_floor)
         n_mass = 1
         minv = 1.0 / mass  # updated in place from here on (a captured trajectory reads it)
         if tm is not None:

@@ -40,7 +40,9 @@ def _lib():
         L.hawkes_mlp_loss_grad.argtypes = [vp, vp, vp, i64, vp, ctypes.c_size_t, vp, vp, vp]
         L.hawkes_mlp_adam.argtypes = [vp, vp, vp, vp, vp, f, f, f, f, ctypes.c_int, vp]
         L.hawkes_surrogate_momentum.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp, vp]
-        for fn in (L.hawkes_mlp_forward, L.hawkes_mlp_loss_grad, L.hawkes_mlp_adam, L.hawkes_surrogate_momentum):
+        L.hawkes_surrogate_trajectory.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_int, vp]
+        for fn in (L.hawkes_mlp_forward, L.hawkes_mlp_loss_grad, L.hawkes_mlp_adam, L.hawkes_surrogate_momentum,
+                   L.hawkes_surrogate_trajectory):
             fn.restype = ctypes.c_int
         L._mlp_typed = True
     return L
@@ -225,7 +227,15 @@ def collect_pairs(post, q0, n_pairs, n_steps=20, eps0=0.02, mass_every=50, seed=
 
 
 def surrogate_leapfrog(sur, q, p, eps, n_steps, minv):
-    """Leapfrog trajectory over the six globals driven by the surrogate gradient."""
+    """Leapfrog trajectory over the six globals driven by the surrogate gradient:
+    one launch of the fused trajectory kernel."""
+    _check(_lib().hawkes_surrogate_trajectory(_p(sur.mlp.wb), _p(sur.norm), _p(q), _p(p), _p(minv), eps, n_steps,
+                                              _stream(q.device)))
+
+
+def surrogate_leapfrog_steps(sur, q, p, eps, n_steps, minv):
+    """The same trajectory as one surrogate-momentum and one position launch per
+    step (the fused kernel's definition; tests compare the two)."""
     L = _lib()
     s = _stream(q.device)
     w, nrm = _p(sur.mlp.wb), _p(sur.norm)
@@ -234,6 +244,53 @@ def surrogate_leapfrog(sur, q, p, eps, n_steps, minv):
         _check(L.hawkes_hmc_position(q.numel(), _p(q), _p(p), _p(minv), eps, s))
         _check(L.hawkes_surrogate_momentum(w, _p(q), _p(p), eps if step < n_steps - 1 else 0.5 * eps, nrm,
                                            ctypes.c_void_p(0), s))
+
+
+class _SurrogateIteration:
+    """The device part of one surrogate HMC iteration after the momentum draw,
+    captured once as a CUDA graph: kinetic energy at the start, the fused
+    surrogate trajectory from a copy of q, the exact log posterior at its end
+    point (one log-likelihood pass) and the kinetic energy there.  The four
+    numbers the accept step needs land in one device vector
+    e = [log pi(q), K(p0), log pi(q'), K(p')], read back with one copy."""
+
+    def __init__(self, post, sur, q, p, minv, eps, n_steps, use_graph=True):
+        dev = q.device
+        f64 = dict(dtype=torch.float64, device=dev)
+        self.post, self.sur, self.eps, self.n_steps = post, sur, eps, n_steps
+        self.q, self.p, self.minv = q, p, minv
+        self.qn = torch.empty_like(q)
+        self.e = torch.zeros(4, **f64)
+        self.cur = {"logpost": self.e[0]}
+        self.cand = {"logpost": self.e[2]}
+        self.graph = None
+        if use_graph:
+            side = torch.cuda.Stream(device=dev)
+            side.wait_stream(torch.cuda.current_stream(dev))
+            with torch.cuda.stream(side):  # one eager run first, so every lazily made buffer exists
+                self._body()
+            torch.cuda.current_stream(dev).wait_stream(side)
+            torch.cuda.synchronize(dev)
+            calls = dict(post.calls)
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph):
+                self._body()
+            post.calls.update(calls)
+
+    def _body(self):
+        hmc.kinetic(self.p, self.minv, self.e[1])
+        self.qn.copy_(self.q)
+        surrogate_leapfrog(self.sur, self.qn, self.p, self.eps, self.n_steps, self.minv)
+        self.post.logpost_only(self.qn, self.cand)
+        hmc.kinetic(self.p, self.minv, self.e[3])
+
+    def run(self):
+        if self.graph is not None:
+            self.graph.replay()
+            self.post.calls["loglik"] = self.post.calls.get("loglik", 0) + 1
+        else:
+            self._body()
+        return self.e.cpu().numpy()  # the iteration's one host synchronisation
 
 
 @dataclasses.dataclass
@@ -248,9 +305,13 @@ class SurrogateChain:
 
 
 def sample(post, sur, q0, mass, eps, n_iter, n_steps=20, seed=0, monitor_every=100, fallback_window=50,
-           fallback_rate=0.2):
+           fallback_rate=0.2, use_graph=True):
     """Surrogate-trajectory HMC with the exact Metropolis accept.
 
+    Each iteration draws the momentum, then runs the captured iteration graph
+    (fused surrogate trajectory, exact log posterior at the end point, both
+    kinetic energies) and reads its four energies back in one copy: one host
+    synchronisation per iteration.  The draws stay on the device until the end.
     Every `monitor_every` iterations the exact gradient at the current state
     measures the surrogate's relative error.  If the acceptance rate over the last
     `fallback_window` iterations drops below `fallback_rate`, the remaining
@@ -263,45 +324,51 @@ def sample(post, sur, q0, mass, eps, n_iter, n_steps=20, seed=0, monitor_every=1
     f64 = dict(dtype=torch.float64, device=dev)
     q = q0.clone()
     minv = 1.0 / mass
+    sqrt_mass = torch.sqrt(mass)
     p = torch.empty(dim, **f64)
-    k0, k1 = torch.empty((), **f64), torch.empty((), **f64)
-    cur = {"logpost": torch.empty((), **f64)}
-    post.logpost_only(q, cur)
-    cand = {"logpost": torch.empty((), **f64)}
+    warm_gen = torch.Generator(device=dev)
+    warm_gen.manual_seed(seed + 1)
+    torch.randn(dim, generator=warm_gen, out=p, dtype=torch.float64, device=dev)
+    p.mul_(sqrt_mass)  # a plausible momentum for the eager run that precedes the capture
+    it_dev = _SurrogateIteration(post, sur, q, p, minv, eps, n_steps, use_graph=use_graph)
+    post.logpost_only(q, it_dev.cur)  # log pi at the start (the eager run used e as scratch)
     scratch = {"logpost": torch.empty((), **f64), "grad": torch.empty(dim, **f64), "hdiag": torch.empty(dim, **f64)}
-    draws = np.empty((n_iter, dim))
+    k1 = torch.empty((), **f64)
+    draws_dev = torch.empty(n_iter, dim, **f64)
     acc = np.zeros(n_iter, bool)
     errors, fell_back, fb_at, calls = [], False, -1, 1
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for it in range(n_iter):
         torch.randn(dim, generator=gen, out=p, dtype=torch.float64, device=dev)
-        p.mul_(torch.sqrt(mass))
-        hmc.kinetic(p, minv, k0)
-        qn = q.clone()
+        p.mul_(sqrt_mass)
         if fell_back:
+            hmc.kinetic(p, minv, it_dev.e[1])
+            qn = q.clone()
             g0 = post.evaluate(q, out=scratch)["grad"].clone()
             ev = hmc.leapfrog(post, qn, p, g0, eps, n_steps, minv, scratch)
-            cand["logpost"].copy_(ev["logpost"])
+            it_dev.e[2].copy_(ev["logpost"])
+            hmc.kinetic(p, minv, k1)
+            it_dev.e[3].copy_(k1)
+            e = it_dev.e.cpu().numpy()
         else:
-            surrogate_leapfrog(sur, qn, p, eps, n_steps, minv)
-            post.logpost_only(qn, cand)
+            e = it_dev.run()
+            qn = it_dev.qn
             calls += 1
-        hmc.kinetic(p, minv, k1)
-        h0 = -cur["logpost"].item() + k0.item()
-        lp1 = cand["logpost"].item()
-        h1 = -lp1 + k1.item()
-        a = min(1.0, math.exp(min(0.0, h0 - h1))) if math.isfinite(lp1) and math.isfinite(h1) else 0.0
+        h0 = -e[0] + e[1]
+        h1 = -e[2] + e[3]
+        a = min(1.0, math.exp(min(0.0, h0 - h1))) if math.isfinite(e[2]) and math.isfinite(h1) else 0.0
         if rng.uniform() < a:
-            q = qn
-            cur["logpost"].copy_(cand["logpost"])
+            q.copy_(qn)
+            it_dev.e[0].copy_(it_dev.e[2])
             acc[it] = True
-        draws[it] = q.cpu().numpy()
+        draws_dev[it].copy_(q)
         if monitor_every and (it + 1) % monitor_every == 0 and not fell_back:
             exact = post.evaluate(q, out=scratch)["grad"][:MO]
             errors.append(relative_error(sur.gradient(q)[None], exact[None]))
         if (not fell_back and it + 1 >= fallback_window
                 and acc[it + 1 - fallback_window:it + 1].mean() < fallback_rate):
             fell_back, fb_at = True, it + 1
+    draws = draws_dev.cpu().numpy()
     torch.cuda.synchronize()
     return SurrogateChain(draws, acc, time.perf_counter() - t0, calls, fell_back, fb_at, errors)

@@ -113,31 +113,66 @@ def concentrated_posterior():
     return w, post, d(np.log(w.params))
 
 
+def test_fused_trajectory_equals_step_launches():
+    """The one-launch surrogate trajectory is, bit for bit, the sequence of
+    surrogate-momentum and position launches it replaces."""
+    S = mod()
+    _, wb, _ = weights(7)
+    mlp = S.MLP("cuda")
+    mlp.wb = wb
+    rng = np.random.default_rng(11)
+    norm = np.concatenate([rng.normal(size=6), rng.uniform(0.5, 2, 6), rng.normal(size=6) * 10,
+                           rng.uniform(1, 10, 6), rng.normal(size=36)])
+    sur = S.Surrogate(mlp, torch.tensor(norm, device="cuda"))
+    d = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")  # noqa: E731
+    minv = d(rng.uniform(0.1, 2.0, 6))
+    for n_steps in (0, 1, 20):
+        q0, p0 = rng.normal(size=6), rng.normal(size=6)
+        qa, pa, qb, pb = d(q0), d(p0), d(q0), d(p0)
+        S.surrogate_leapfrog(sur, qa, pa, 0.03, n_steps, minv)
+        S.surrogate_leapfrog_steps(sur, qb, pb, 0.03, n_steps, minv)
+        assert torch.equal(qa, qb) and torch.equal(pa, pb), n_steps
+        if n_steps:
+            assert not torch.equal(qa, d(q0))
+
+
 def test_surrogate_hmc_gains_over_exact_hmc():
     """What the trained network gains: from the same state, with the same mass
     matrix and step size, surrogate trajectories (exact accept) reach the
     effective samples of exact HMC with one exact log-likelihood pass per
-    iteration instead of one gradient pass per leapfrog step."""
+    iteration instead of one gradient pass per leapfrog step.  The criteria
+    are deterministic for fixed seeds (the kernels are bitwise reproducible):
+    effective samples per exact pass, acceptance, the surrogate error the exact
+    kernel measures along the chain, and equal posterior means.  The wall-clock
+    ESS/s ratio is printed, not asserted (the benchmark reports it)."""
     S = mod()
     from paper_2103_03348_b300 import hmc
     w, post, q0 = concentrated_posterior()
-    qp, gp, warm = S.collect_pairs(post, q0, n_pairs=3000, n_steps=20, eps0=0.05, seed=1)
+    # 20,000 exact (q, gradient) pairs, as in the learned part's configuration: a
+    # shorter warm-up covers too little of the posterior's slow mu0-theta0 ridge
+    # (3,000 pairs gave a surrogate chain with a third of the exact chain's ESS
+    # per iteration)
+    qp, gp, warm = S.collect_pairs(post, q0, n_pairs=20000, n_steps=20, eps0=0.05, seed=1)
     sur, rep = S.fit(qp, gp, epochs=200)
-    assert rep["holdout_median_rel_error"] < 0.1, rep
-    n_iter = 300
+    assert rep["holdout_median_rel_error"] < 0.05, rep
+    n_iter = 1000
     ch_s = S.sample(post, sur, warm.last_q, warm.mass_t, warm.eps, n_iter, n_steps=20, seed=2, monitor_every=100)
-    assert not ch_s.fell_back and ch_s.accept.mean() > 0.5
-    assert max(ch_s.monitor_errors) < 0.1  # the exact kernel measures the surrogate's error along the chain
+    assert not ch_s.fell_back and ch_s.accept.mean() > 0.5, ch_s.accept.mean()
+    assert max(ch_s.monitor_errors) < 0.1, ch_s.monitor_errors  # the exact kernel's view of the surrogate error
+    assert ch_s.exact_loglik_calls == n_iter + 1
+    post.calls = {"grad": 0, "hess": 0}
     ch_e = hmc.sample(post, warm.last_q, n_iter=n_iter, n_warmup=0, n_steps=20, eps0=warm.eps, seed=2,
-                      mass_every=10 ** 9)
-    ess_s = hmc.ess_all(ch_s.draws).min()
-    ess_e = hmc.ess_all(ch_e.draws).min()
+                      mass_every=10 ** 9, mass0=warm.mass_t)
+    es, ee = hmc.ess_all(ch_s.draws), hmc.ess_all(ch_e.draws)
     calls_e = ch_e.grad_calls + ch_e.hess_calls
-    assert ess_s / ch_s.exact_loglik_calls > 5 * ess_e / calls_e, (ess_s, ch_s.exact_loglik_calls, ess_e, calls_e)
-    assert ess_s / ch_s.seconds > 2 * ess_e / ch_e.seconds, (ess_s, ch_s.seconds, ess_e, ch_e.seconds)
+    print(f"surrogate: accept {ch_s.accept.mean():.3f}, min ESS {es.min():.1f}, {ch_s.seconds:.2f} s; "
+          f"exact: accept {ch_e.accept.mean():.3f}, min ESS {ee.min():.1f}, {ch_e.seconds:.2f} s; "
+          f"ESS/s ratio {(es.min() / ch_s.seconds) / (ee.min() / ch_e.seconds):.2f}")
+    assert es.min() > 100 and ee.min() > 100, (es, ee)  # both chains mix: the ESS figures are not short-chain noise
+    assert es.min() / ch_s.exact_loglik_calls > 5 * ee.min() / calls_e, (es.min(), ch_s.exact_loglik_calls,
+                                                                         ee.min(), calls_e)
     # equal accuracy: both chains target the same posterior, so their means of the
     # six log-globals agree within the combined Monte Carlo standard errors
-    es, ee = hmc.ess_all(ch_s.draws), hmc.ess_all(ch_e.draws)
     mcse = np.sqrt(ch_s.draws.var(0) / es + ch_e.draws.var(0) / ee)
     gap = np.abs(ch_s.draws.mean(0) - ch_e.draws.mean(0))
     assert np.all(gap <= 4.5 * mcse), (gap, mcse)
