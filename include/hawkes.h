@@ -510,6 +510,28 @@ int hawkes_mlp_adam(float *w_master, void *w_bf16, float *m, float *v, const flo
  * doubles); g_out (DEVICE double[6]) receives g when not NULL. */
 int hawkes_surrogate_momentum(const void *w_bf16, const double *q, double *p, double a, const double *norm,
                               double *g_out, void *stream);
+/* A whole surrogate leapfrog trajectory over the six globals in one launch
+ * (one block): p += eps/2 g(q), then n_steps times q += eps minv p and
+ * p += eps g(q), the last momentum step halved, with g the surrogate gradient
+ * of hawkes_surrogate_momentum.  Equal bit for bit to the sequence of
+ * hawkes_surrogate_momentum and hawkes_hmc_position launches it replaces.
+ * q, p: DEVICE double[6], updated in place; minv: DEVICE double[6], the
+ * diagonal inverse mass; norm as for hawkes_surrogate_momentum; n_steps >= 0.
+ * Returns HAWKES_EINVAL for NULL pointers, a negative n_steps or a NaN eps. */
+int hawkes_surrogate_trajectory(const void *w_bf16, const double *norm, double *q, double *p, const double *minv,
+                                double eps, int n_steps, void *stream);
+
+/* Work count of the space-time passes (measurement for the roofline of
+ * HAWKES_FP32C_ST; the paper has no counterpart).  ws must hold an
+ * HAWKES_FP32C_ST hawkes_hess_diag evaluation of n events (its group records,
+ * constants and column bounds); counts (DEVICE uint64[3], overwritten)
+ * receives the ordered (target, source) pairs inside the group pairs whose
+ * background [0] and excitation [1] terms the row pass evaluates, and the
+ * (source, target) pairs inside the group pairs the column pass evaluates [2],
+ * by the passes' own classification.  Enqueued on stream; the results of the
+ * evaluation are not touched.  HAWKES_EINVAL for bad n, NULL or misaligned
+ * pointers; HAWKES_EWORKSPACE when ws_bytes is too small. */
+int hawkes_st_live_pairs(int64_t n, void *ws, size_t ws_bytes, unsigned long long *counts, void *stream);
 
 /* Largest n accepted by hawkes_hess_diag_noalloc. */
 #define HAWKES_NOALLOC_MAX_EVENTS 4096
@@ -524,14 +546,14 @@ int hawkes_surrogate_momentum(const void *w_bf16, const double *q, double *p, do
  * hawkes_hess_diag with a workspace, for 2 <= n <= HAWKES_NOALLOC_MAX_EVENTS;
  * a larger n returns HAWKES_ESCRATCH without enqueuing anything.  The first
  * call on each device looks up the array's device address (make it before any
- * stream capture).  All calls on a device share the array, so calls that can
+ * stream capture); that address dies with the device's context, so a process
+ * that calls cudaDeviceReset must not call this entry point afterwards.  All calls on a device share the array, so calls that can
  * overlap on the GPU race on it: issue them in order on one stream.  Nothing
  * is allocated. */
 int hawkes_hess_diag_noalloc(const double *x, const double *y, const double *t, const double *r, int64_t n,
                              const double params[6], int precision, double *loglik, double *grad, double *hdiag,
                              int *dev_status, void *stream);
 
-/* Static English description of a hawkes_status code. */
 /* ALU throughput microbenchmarks (the denominators of the roofline; the paper
  * has no counterpart): which = 0 packed FP32 FMA (f32x2), 1 MUFU exp2, 2 FP64
  * FMA.  hawkes_peak_launch enqueues blocks x 256 threads, each running
@@ -541,6 +563,7 @@ int hawkes_hess_diag_noalloc(const double *x, const double *y, const double *t, 
 int64_t hawkes_peak_ops(int which, int64_t blocks, int iters);
 int hawkes_peak_launch(int which, int64_t blocks, int iters, float *sink, void *stream);
 
+/* Static English description of a hawkes_status code. */
 const char *hawkes_strerror(int status);
 
 /* Library version string. */

@@ -16,6 +16,9 @@
 // device address, so the first call on each device (with that device current)
 // looks the address up with cudaGetSymbolAddress, checks it, and caches it;
 // that first call should therefore come before any stream capture.  The
+// cached address belongs to the device's context of that moment: a host
+// program that calls cudaDeviceReset (which unloads this module's device copy
+// of the array) must not call this entry point again in the same process.  The
 // evaluation itself is hawkes_hess_diag with this array as its workspace; its
 // first steps clear what has to start at zero (status words, the location hash
 // table, the group counters) and every other byte is rewritten before it is

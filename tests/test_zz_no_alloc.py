@@ -11,11 +11,9 @@ too (the first call on the device does the one-time address lookup).
 """
 import ctypes
 
-import numpy as np
 import pytest
 
 from paper_2103_03348_b300 import synth
-from parity_util import FP32C_GNORM_TOL, FP32C_LL_TOL, FP64_TOL, norm_rel, rel
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -47,12 +45,15 @@ def _noalloc(L, x, y, t, r, params, precision):
     return rc, ll, g, h, st
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
 def test_noalloc_matches_workspace_call_twice(precision):
+    """Both entry points run the same deterministic kernels on the same inputs,
+    so the results must be equal bit for bit, also on the second call, which
+    reuses the scratch array the first call filled (a large problem first, then
+    a smaller one: stale bytes beyond the smaller one's extent are never read)."""
     hawkes, L = _lib()
     d = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")  # noqa: E731
-    name = "fp64" if precision == 0 else "fp32c"
-    # two different inputs in a row: the second call must not see the first one's leftovers
+    name = ("fp64", "fp32c", "fp32c_band", "fp32c_st")[precision]
     for seed, n in ((31, 4096), (32, 1500)):
         w = synth.make_uniform(seed, n, box=1.0, t_max=1.0, r_sd=0.5, params=(0.5, 0.1, 0.05, 0.3, 10.0, 0.02))
         x, y, t, r = d(w.x), d(w.y), d(w.t), d(w.r)
@@ -61,17 +62,7 @@ def test_noalloc_matches_workspace_call_twice(precision):
         torch.cuda.synchronize()
         assert int(st.item()) == hawkes.OK
         ref_ll, ref_g, ref_h = hawkes.hess_diag(x, y, t, r, w.params, name)
-        a, b = ll.item(), ref_ll.item()
-        ga, gb = g.cpu().numpy(), ref_g.cpu().numpy()
-        ha, hb = h.cpu().numpy(), ref_h.cpu().numpy()
-        if precision == 0:
-            assert rel(a, b) <= FP64_TOL
-            assert np.max(np.abs(ga - gb) / np.maximum(np.abs(gb), 1e-3 * np.abs(gb).max())) <= FP64_TOL
-            assert np.max(np.abs(ha - hb) / np.maximum(np.abs(hb), 1e-3 * np.abs(hb).max())) <= FP64_TOL
-        else:
-            assert rel(a, b) <= FP32C_LL_TOL
-            assert norm_rel(ga, gb) <= FP32C_GNORM_TOL
-            assert norm_rel(ha, hb) <= FP32C_GNORM_TOL
+        assert torch.equal(ll, ref_ll) and torch.equal(g, ref_g) and torch.equal(h, ref_h), (name, n)
 
 
 def test_noalloc_rejects_too_many_events():
