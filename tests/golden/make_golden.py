@@ -1,10 +1,14 @@
 """Writes the golden fixtures in this folder from the oracle alone.
 
-    python tests/golden/make_golden.py
+    python tests/golden/make_golden.py            # the small JSON fixtures
+    python tests/golden/make_golden.py --large    # large_N100000.npz (minutes, all host cores)
 
-Each fixture stores its inputs literally (so it does not depend on a random
-generator's version) and the oracle's FP64 outputs, with the passage of the
-paper that defines them.  Run it again, and commit the diff with the passage
+Each small fixture stores its inputs literally (so it does not depend on a
+random generator's version) and the oracle's FP64 outputs, with the passage of
+the paper that defines them.  The large fixture is the full FP64 evaluation of
+the 100,000-event benchmark workload; it stores a SHA-256 digest of that
+workload's inputs instead of the 3.2 MB of inputs, so a reader regenerates them
+with the seeded generator and checks the digest.  Run it again, and commit the diff with the passage
 that justifies it, only when the oracle's arithmetic changes.
 """
 from __future__ import annotations
@@ -108,7 +112,35 @@ def posterior_fixture():
         "expected": {"logpost": float(lp), "grad": lst(g), "hdiag": lst(h)}})
 
 
+def input_digest(w) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for a in (w.x, w.y, w.t, w.r, np.asarray(w.params, float)):
+        h.update(np.ascontiguousarray(a, dtype=np.float64).tobytes())
+    return h.hexdigest()
+
+
+def large_fixture():
+    """Full FP64 oracle evaluation (loglik, gradient[6+N], Hessian diagonal[6+N],
+    and the intensities lambda[N]) of the 100,000-event workload that the
+    benchmark times."""
+    import time
+    from paper_2103_03348_b300 import synth
+    w = synth.make("large")
+    t0 = time.perf_counter()
+    o = oracle.evaluate(w.x, w.y, w.t, w.r, w.params, want=2)
+    dt = time.perf_counter() - t0
+    np.savez_compressed(os.path.join(HERE, "large_N100000.npz"), loglik=np.float64(o["loglik"]),
+                        Lambda=np.float64(o["Lambda"]), grad=o["grad"], hdiag=o["hdiag"], lam=o["lam"],
+                        input_sha256=np.array(input_digest(w)), source=np.array(LIKELIHOOD_SOURCE),
+                        workload=np.array(w.name), params=np.asarray(w.params, float))
+    print(f"large_N100000.npz: loglik {o['loglik']:.12e}, {dt:.0f} s on {oracle.max_threads()} threads")
+
+
 def main():
+    if "--large" in sys.argv:
+        large_fixture()
+        return
     likelihood_fixture("loglik_hand_n7.json", *hand_events(),
                        note="events 1 and 2 are simultaneous at one location: no excitation and no background "
                             "between them; event 5 is far from the rest")

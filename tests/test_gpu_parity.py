@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 from paper_2103_03348_b300 import synth
-from parity_util import check, rel
+from parity_util import check, error_report, large_reference, rate_condition_scales, rel
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -191,19 +191,36 @@ def test_large_identities(large):
     assert h[0] <= 0 and h[3] <= 0 and np.all(h[6:] - g[6:] <= 1e-9)
 
 
-def test_large_sampled_rates_vs_oracle(large):
-    """64 sampled log-rate gradient and Hessian entries, recomputed one by one by
-    the oracle (sources among the last 1,500 events, whose later targets' exact
-    intensities the oracle can afford)."""
+@pytest.fixture(scope="module")
+def large_ref():
+    w = synth.make("large")
+    return large_reference(w)
+
+
+@pytest.mark.parametrize("prec", ["fp32c", "fp32c_band", "fp32c_st", "fp64"])
+def test_large_full_parity_vs_oracle(large_ref, prec):
+    """The benchmark's workload (100,000 events) in the benchmark's launch
+    configuration against the full FP64 oracle evaluation stored by
+    tests/golden/make_golden.py --large: loglik, the 12 global entries and every
+    one of the 2 x 100,000 log-rate entries, early sources included, at the
+    stated bars (FP64 1e-10 per entry; FP32C 1e-5 on loglik and the gradient
+    norm, 1e-4 per global entry, the log-rate entry guard with its condition
+    scale: a few entries of Eq. 4 cancel to 1/200 of their parts here)."""
+    w = synth.make("large")
+    ll, g, h = gpu_eval(w, w.params, prec)
+    rep = error_report(ll, g, h, large_ref)
+    print(f"N=100000 {prec} vs oracle: {rep}")
+    check(prec, ll, g, h, large_ref, label="N=100000", cond=rate_condition_scales(w.t, w.r, w.params, large_ref))
+
+
+def test_large_sampled_rates_vs_oracle(large, large_ref):
+    """64 log-rate gradient and Hessian entries drawn over the whole range of
+    sources (the earliest, whose column sums are the longest, included),
+    recomputed one by one by oracle.rate_terms from the stored intensities."""
     w, ll, g, h = large
     rng = np.random.default_rng(4)
-    pool = np.arange(w.n - 1500, w.n - 1)
-    idx = np.sort(rng.choice(pool, 64, replace=False))
-    later = np.arange(idx.min(), w.n)
-    lam_later, _, _ = oracle.rows(w.x, w.y, w.t, w.r, w.params, later)
-    lam = np.ones(w.n)
-    lam[later] = lam_later
-    g_ref, h_ref = oracle.rate_terms(w.x, w.y, w.t, w.r, w.params, lam, idx)
+    idx = np.sort(np.concatenate([[0, 1, 2], rng.choice(np.arange(3, w.n - 1), 61, replace=False)]))
+    g_ref, h_ref = oracle.rate_terms(w.x, w.y, w.t, w.r, w.params, large_ref["lam"], idx)
     scale_g = np.abs(g[6:]).max()
     assert np.max(np.abs(g[6 + idx] - g_ref) / np.maximum(np.abs(g_ref), 1e-3 * scale_g)) <= 2e-3
     assert np.linalg.norm(g[6 + idx] - g_ref) <= 1e-4 * np.linalg.norm(g_ref)
