@@ -44,10 +44,10 @@ METRIC = "loglik+grad+Hdiag pair-interactions/s and % FP32 roofline at N=1e5; HM
 UNIT = "pair-interactions/s"
 L2_FLUSH_BYTES = 256 << 20  # larger than the 126 MB L2
 
-# FP32 pipe: 148 SMs x 128 lanes, one FADD/FMUL/FFMA per lane per clock, at the
-# maximum SM clock of 2,032 MHz: 38.49e12 lane-slots/s.
-SMS, LANES, SM_MAX_MHZ = 148, 128, 2032.0
-FP32_PEAK_SLOTS = SMS * LANES * SM_MAX_MHZ * 1e6
+# FP32 pipe: the device's SM count (148 on B300) x 128 lanes, one
+# FADD/FMUL/FFMA per lane per clock, at the maximum SM clock (2,032 MHz on
+# B300, read from nvidia-smi during the timed region): 38.49e12 lane-slots/s.
+LANES, SM_MAX_MHZ_DEFAULT = 128, 2032.0
 
 # Algorithmic FP32 lane-slots per pair (see the design notes): background terms
 # for every ordered pair, excitation and column terms for causal pairs inside
@@ -368,10 +368,15 @@ def run_ours(args, rank, world, local_rank):
     # time slabs; group pairs whose FP32 terms all underflow are skipped; results
     # equal FP32C's up to summation order), event preparation included
     ws_st = torch.empty(hawkes.workspace_size(n, "fp32c_st"), dtype=torch.uint8, device=dev)
-    st = lambda _: hawkes._call("hess", x, y, t, r, w.params, "fp32c_st", stream=stream, check=False,  # noqa: E731
-                                out=band_out, workspace=ws_st)
+    st = lambda ph: hawkes._call("hess", x, y, t, r, w.params, "fp32c_st", stream=stream, check=False,  # noqa: E731
+                                 out=band_out, workspace=ws_st, phase_events=ph)
     timed_steps(3, st)  # warm-up
-    st_ms = timed_steps(k_alt, st)
+    st_ms, st_row_ms, st_col_ms = timed_steps(k_alt, st, phases=True)
+    st_pairs = hawkes.st_live_pairs(n, ws_st, stream=stream)  # the pairs those passes evaluated
+
+    # per-output error of the timed results against the stored full FP64 oracle evaluation
+    parity = {"reference": "tests/golden/large_N100000.npz (full FP64 oracle evaluation of this workload)",
+              "fp32c": parity_report(w, out), "fp32c_st": parity_report(w, band_out)}
 
     # FP64 GPU path on the same workload (speedup of FP32C over it)
     fp64_ms = []
@@ -415,6 +420,9 @@ def run_ours(args, rank, world, local_rank):
     achieved = row_slots / row_t
     clocks = clk.summary()
     traffic = profile_traffic()
+    sms = int(torch.cuda.get_device_properties(dev).multi_processor_count)
+    sm_max_mhz = float(clocks.get("sm_max_mhz") or SM_MAX_MHZ_DEFAULT)
+    FP32_PEAK_SLOTS = sms * LANES * sm_max_mhz * 1e6
     peak_t = FP32_PEAK_SLOTS / 1e12
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -429,12 +437,14 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "alu", "kernel": "row32_kernel (row pass)", "achieved": achieved / 1e12,
                      "peak": peak_t, "unit": "T FP32 lane-slots/s", "frac": achieved / FP32_PEAK_SLOTS,
                      "traffic": traffic,
-                     "peak_source": "148 SMs x 128 FP32 lanes x 2032 MHz (unit counts and maximum clock)",
+                     "peak_source": f"{sms} SMs (device properties) x 128 FP32 lanes x {sm_max_mhz:.0f} MHz "
+                                    f"(maximum SM clock); unit counts, no FP32 figure is measured by the driver",
+                     "sms": sms,
                      "algorithmic_slots_per_launch": row_slots,
                      "row_ms": row_t * 1e3, "col_ms": col_t * 1e3,
                      "col_frac": col_slots / col_t / FP32_PEAK_SLOTS,
                      "step_frac": (row_slots + col_slots) / (ms * 1e-3) / FP32_PEAK_SLOTS,
-                     "frac_at_sampled_clock": (achieved / (SMS * LANES * clocks["sm_mhz"] * 1e6)
+                     "frac_at_sampled_clock": (achieved / (sms * LANES * clocks["sm_mhz"] * 1e6)
                                                if clocks.get("sm_mhz") else None),
                      "band_pairs": pb,
                      "measured_alu_peaks": {"ffma2_T_lane_slots_per_s": alu["ffma2_lane_fma_per_s"] / 1e12,
@@ -442,7 +452,12 @@ def run_ours(args, rank, world, local_rank):
                                             "dfma_T_per_s": alu["dfma_per_s"] / 1e12,
                                             "source": "the library's f32x2 FMA, MUFU exp2 and FP64 FMA chains"},
                      "frac_of_measured_ffma2": achieved / alu["ffma2_lane_fma_per_s"],
-                     "coarse_count_frac": (COARSE_ROW_SLOTS * pairs) / row_t / FP32_PEAK_SLOTS},
+                     "frac_survey": (COARSE_ROW_SLOTS * pairs) / row_t / FP32_PEAK_SLOTS,
+                     "col_frac_survey": (COARSE_COL_SLOTS * pb) / col_t / FP32_PEAK_SLOTS,
+                     "survey_count": "26 FP32 slots per ordered pair (excitation and masks charged to every "
+                                     "pair), 10 per causal column pair in the band"},
+        "parity": parity,
+        "roofline_st": st_roofline(st_pairs, st_row_ms, st_col_ms, FP32_PEAK_SLOTS),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * n,
                 "d2h_bytes_per_step": 8 + 2 * 8 * (6 + n), "ms_per_step": float(np.mean(e2e_ms))},
         "cpu_baseline": cpu,
@@ -469,6 +484,53 @@ def run_ours(args, rank, world, local_rank):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def st_roofline(st_pairs, row_ms, col_ms, peak):
+    """The space-time passes (the path the sampler runs) against the FP32 pipe,
+    counting the pairs inside the group pairs they evaluate: 14 slots per
+    background pair and 7 per excitation pair in the row pass (the per-pair
+    counts of the full evaluation), 8 per column pair."""
+    row_t, col_t = float(np.mean(row_ms)) * 1e-3, float(np.mean(col_ms)) * 1e-3
+    row_slots = ROW_BG_SLOTS * st_pairs["row_background_pairs"] + ROW_EXC_SLOTS * st_pairs["row_excitation_pairs"]
+    col_slots = COL_SLOTS * st_pairs["column_pairs"]
+    return {"bound": "alu", "kernel": "row32_st_kernel (space-time row pass)", "unit": "T FP32 lane-slots/s",
+            "achieved": row_slots / row_t / 1e12, "peak": peak / 1e12, "frac": row_slots / row_t / peak,
+            "row_ms": row_t * 1e3, "col_ms": col_t * 1e3, "col_frac": col_slots / col_t / peak,
+            "algorithmic_slots_per_launch": row_slots, "col_slots_per_launch": col_slots, **st_pairs,
+            "count": "pairs inside the live group pairs, counted on the device by the passes' own "
+                     "classification (hawkes_st_live_pairs)"}
+
+
+def parity_report(w, out):
+    """Relative errors of a device result against the stored oracle evaluation:
+    loglik, and max / median of the scaled entry errors (denominator
+    max(|ref_i|, 1e-3 max|ref|)) of the global and log-rate entries of the
+    gradient and Hessian diagonal; None when the fixture is absent or was made
+    from other inputs."""
+    import hashlib
+    path = os.path.join(ROOT, "tests", "golden", "large_N100000.npz")
+    if not os.path.exists(path):
+        return None
+    z = np.load(path)
+    d = hashlib.sha256()
+    for a in (w.x, w.y, w.t, w.r, np.asarray(w.params, float)):
+        d.update(np.ascontiguousarray(a, dtype=np.float64).tobytes())
+    if str(z["input_sha256"]) != d.hexdigest():
+        return None
+    ll, g, h = float(out["loglik"].item()), out["grad"].cpu().numpy(), out["hdiag"].cpu().numpy()
+
+    def vec(a, b):
+        den = np.maximum(np.abs(b), 1e-3 * np.abs(b).max())
+        e = np.abs(a - b) / den
+        return {"max": float(e.max()), "median": float(np.median(e))}
+
+    nrm = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))  # noqa: E731
+    return {"loglik": abs(ll - float(z["loglik"])) / abs(float(z["loglik"])),
+            "grad_globals": vec(g[:6], z["grad"][:6]), "grad_rates": vec(g[6:], z["grad"][6:]),
+            "grad_norm": nrm(g, z["grad"]),
+            "hdiag_globals": vec(h[:6], z["hdiag"][:6]), "hdiag_rates": vec(h[6:], z["hdiag"][6:]),
+            "hdiag_norm": nrm(h, z["hdiag"])}
 
 
 def predictive_bench(dev, stream):

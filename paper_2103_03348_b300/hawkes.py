@@ -283,3 +283,26 @@ class HawkesLogLik(torch.autograd.Function):
 def version() -> str:
     return lib().hawkes_version().decode()
 
+
+def st_live_pairs(n: int, workspace: torch.Tensor, stream=None) -> dict:
+    """Pairs the HAWKES_FP32C_ST passes evaluate for the evaluation held in
+    `workspace` (a hess evaluation of n events in that precision): background
+    and excitation pairs of the row pass, pairs of the column pass."""
+    L = lib()
+    if not getattr(L, "_st_count_typed", False):
+        L.hawkes_st_live_pairs.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                           ctypes.c_void_p]
+        L.hawkes_st_live_pairs.restype = ctypes.c_int
+        L._st_count_typed = True
+    dev = workspace.device
+    counts = torch.zeros(3, dtype=torch.int64, device=dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev).cuda_stream
+    elif isinstance(stream, torch.cuda.Stream):
+        stream = stream.cuda_stream
+    with torch.cuda.device(dev):
+        rc = L.hawkes_st_live_pairs(int(n), ctypes.c_void_p(workspace.data_ptr()), ctypes.c_size_t(workspace.numel()),
+                                    ctypes.c_void_p(counts.data_ptr()), ctypes.c_void_p(stream))
+    _raise_status(rc)
+    c = [int(v) for v in counts.cpu().tolist()]
+    return {"row_background_pairs": c[0], "row_excitation_pairs": c[1], "column_pairs": c[2]}
