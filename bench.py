@@ -15,6 +15,12 @@ It prints one JSON line:
   hmc_tree_mass  the same chain with the tree-structured mass on the log-rates
   predictive  posterior-predictive simulation 30 days ahead of that workload
             for 4,096 parameter settings (draws/s)
+  surrogate the learned gradient surrogate at 500,000 events: 20,000 exact
+            warm-up pairs, surrogate HMC against exact HMC from the same state
+            (acceptance, surrogate gradient error, ESS/s, gains)
+  parity    per-output errors of the timed results against the stored FP64
+            oracle evaluation of the workload
+  roofline_st  the space-time passes (the sampler's path) over the pairs they evaluate
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -406,6 +412,15 @@ def run_ours(args, rank, world, local_rank):
         hmc_tree_summary = {k: h[k] for k in keys}
 
     pred_summary = None if args.no_predictive else predictive_bench(dev, stream)
+
+    # the learned surrogate at its own configuration: 500,000 events, 20,000 exact
+    # warm-up pairs, surrogate HMC (exact accept) against exact HMC from the same
+    # state with the same mass and step size, on space-time tiles; a few minutes
+    sur_summary = None
+    if world == 1 and not args.no_surrogate:
+        from paper_2103_03348_b300 import run_surrogate
+        sur_summary = run_surrogate.run(n=args.surrogate_n, pairs=20_000, iters=2000, exact_iters=500,
+                                        precision="fp32c_st", device=str(dev))
     from paper_2103_03348_b300 import peaks
     alu = peaks.measure(str(dev))
 
@@ -481,6 +496,7 @@ def run_ours(args, rank, world, local_rank):
         "hmc": hmc_summary,
         "hmc_tree_mass": hmc_tree_summary,
         "predictive": pred_summary,
+        "surrogate": sur_summary,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -550,6 +566,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-hmc", action="store_true", help="skip the short HMC chain (ESS/s)")
     ap.add_argument("--no-predictive", action="store_true", help="skip the posterior-predictive simulation")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate chains (N=500,000)")
+    ap.add_argument("--surrogate-n", type=int, default=500_000, help="events of the surrogate block's workload")
     ap.add_argument("--hmc-iters", type=int, default=2000)
     ap.add_argument("--hmc-warmup", type=int, default=200)
     ap.add_argument("--kernel-only", action="store_true",

@@ -317,6 +317,14 @@ int hawkes_posterior_add_trend(int64_t m, int k, const int *seq_idx, const doubl
 int hawkes_hmc_momentum(int64_t k, double *p, const double *g, double a, void *stream);
 int hawkes_hmc_position(int64_t k, double *q, const double *p, const double *minv, double eps, void *stream);
 int hawkes_hmc_kinetic(int64_t k, const double *p, const double *minv, double *out, void *stream);
+/* The same with a dense mass matrix over k <= 64 coordinates (a posterior over
+ * the six globals alone, whose correlations a diagonal mass cannot follow):
+ * minv is M^-1 (DEVICE double[k*k], row-major).
+ *   hawkes_hmc_position_dense: q += eps * M^-1 p
+ *   hawkes_hmc_kinetic_dense:  *out = 1/2 p^T M^-1 p
+ * HAWKES_EINVAL for k outside [1, 64] or NULL pointers. */
+int hawkes_hmc_position_dense(int64_t k, double *q, const double *p, const double *minv, double eps, void *stream);
+int hawkes_hmc_kinetic_dense(int64_t k, const double *p, const double *minv, double *out, void *stream);
 
 /* ------------------------------------------------------------------------
  * The phylogenetic Brownian prior in O(M) (Section 2.2, Eq. 2; computed by
@@ -520,6 +528,11 @@ int hawkes_surrogate_momentum(const void *w_bf16, const double *q, double *p, do
  * Returns HAWKES_EINVAL for NULL pointers, a negative n_steps or a NaN eps. */
 int hawkes_surrogate_trajectory(const void *w_bf16, const double *norm, double *q, double *p, const double *minv,
                                 double eps, int n_steps, void *stream);
+/* The same trajectory with a dense inverse mass: minv is M^-1 (DEVICE
+ * double[36], row-major) and each position step is q += eps M^-1 p, as in
+ * hawkes_hmc_position_dense (equal bit for bit to those launches). */
+int hawkes_surrogate_trajectory_dense(const void *w_bf16, const double *norm, double *q, double *p,
+                                      const double *minv, double eps, int n_steps, void *stream);
 
 /* Work count of the space-time passes (measurement for the roofline of
  * HAWKES_FP32C_ST; the paper has no counterpart).  ws must hold an

@@ -170,6 +170,48 @@ __global__ void __launch_bounds__(ASM_THREADS) kinetic_kernel(int64_t k, const d
     if (threadIdx.x == 0) *out = 0.5 * s;
 }
 
+// Dense mass matrix over k <= DENSE_MAX coordinates (a posterior over the six
+// globals alone): minv is M^-1, k x k row-major.
+//   position: q += eps M^-1 p        kinetic: out = 1/2 p^T M^-1 p
+// One block; (M^-1 p)_j summed over i in order.
+constexpr int DENSE_MAX = 64;
+
+__global__ void __launch_bounds__(DENSE_MAX) position_dense_kernel(int k, double *__restrict__ q,
+                                                                   const double *__restrict__ p,
+                                                                   const double *__restrict__ minv, double eps) {
+    pdl_wait();
+    __shared__ double ps[DENSE_MAX];
+    const int j = threadIdx.x;
+    if (j < k) ps[j] = p[j];
+    __syncthreads();
+    if (j < k) {
+        double v = 0.0;
+        for (int i = 0; i < k; ++i) v += minv[j * k + i] * ps[i];
+        q[j] += eps * v;
+    }
+}
+
+__global__ void __launch_bounds__(DENSE_MAX) kinetic_dense_kernel(int k, const double *__restrict__ p,
+                                                                  const double *__restrict__ minv,
+                                                                  double *__restrict__ out) {
+    pdl_wait();
+    __shared__ double ps[DENSE_MAX], term[DENSE_MAX];
+    const int j = threadIdx.x;
+    if (j < k) ps[j] = p[j];
+    __syncthreads();
+    if (j < k) {
+        double v = 0.0;
+        for (int i = 0; i < k; ++i) v += minv[j * k + i] * ps[i];
+        term[j] = ps[j] * v;
+    }
+    __syncthreads();
+    if (j == 0) {
+        double s = 0.0;
+        for (int i = 0; i < k; ++i) s += term[i];
+        *out = 0.5 * s;
+    }
+}
+
 static int grid_for(int64_t k) {
     int64_t b = (k + 255) / 256;
     return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
@@ -301,6 +343,18 @@ int hawkes_hmc_position(int64_t k, double *q, const double *p, const double *min
 int hawkes_hmc_kinetic(int64_t k, const double *p, const double *minv, double *out, void *stream) {
     if (k < 1 || !p || !minv || !out) return HAWKES_EINVAL;
     launch_pdl(hk::kinetic_kernel, 1, hk::ASM_THREADS, 0, (cudaStream_t)stream, k, p, minv, out);
+    return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
+}
+
+int hawkes_hmc_position_dense(int64_t k, double *q, const double *p, const double *minv, double eps, void *stream) {
+    if (k < 1 || k > hk::DENSE_MAX || !q || !p || !minv) return HAWKES_EINVAL;
+    launch_pdl(hk::position_dense_kernel, 1, hk::DENSE_MAX, 0, (cudaStream_t)stream, (int)k, q, p, minv, eps);
+    return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
+}
+
+int hawkes_hmc_kinetic_dense(int64_t k, const double *p, const double *minv, double *out, void *stream) {
+    if (k < 1 || k > hk::DENSE_MAX || !p || !minv || !out) return HAWKES_EINVAL;
+    launch_pdl(hk::kinetic_dense_kernel, 1, hk::DENSE_MAX, 0, (cudaStream_t)stream, (int)k, p, minv, out);
     return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
 }
 

@@ -255,6 +255,9 @@ __global__ void __launch_bounds__(MH) surrogate_momentum_kernel(const __nv_bfloa
 // order, so the trajectory equals the sequence of surrogate_momentum and
 // position launches bit for bit.  Each thread keeps its row of W2 in
 // registers across the n_steps + 1 evaluations; W3 is staged in shared memory.
+// DENSE: minv is a dense 6 x 6 inverse mass (row-major) and the position step
+// is q += eps M^-1 p, summed as in the dense position kernel.
+template <bool DENSE>
 __global__ void __launch_bounds__(MH) surrogate_trajectory_kernel(const __nv_bfloat16 *__restrict__ w,
                                                                   const double *__restrict__ norm,
                                                                   double *__restrict__ q, double *__restrict__ p,
@@ -271,12 +274,17 @@ __global__ void __launch_bounds__(MH) surrogate_trajectory_kernel(const __nv_bfl
     const float b1 = bf(w, OFF_B1 + j), b2 = bf(w, OFF_B2 + j);
     for (int i = j; i < MO * MH; i += MH) w3s[i] = bf(w, OFF_W3 + i);
     float b3 = 0.0f;
-    double mi = 0.0;
+    double mi[DENSE ? MI : 1];
     if (j < MI) {
         qs[j] = q[j];
         ps[j] = p[j];
         b3 = bf(w, OFF_B3 + j);
-        mi = minv[j];
+        if (DENSE) {
+#pragma unroll
+            for (int i = 0; i < MI; ++i) mi[i] = minv[j * MI + i];
+        } else {
+            mi[0] = minv[j];
+        }
     }
     __syncthreads();
     for (int step = 0; step <= n_steps; ++step) {
@@ -301,7 +309,17 @@ __global__ void __launch_bounds__(MH) surrogate_trajectory_kernel(const __nv_bfl
             const double a = (step == 0 || step == n_steps) ? 0.5 * eps : eps;
             __syncwarp(0x3fu);  // every g is formed from the old q before any q moves
             ps[j] += a * g;
-            if (step < n_steps) qs[j] += eps * mi * ps[j];
+            if (step < n_steps) {
+                if (DENSE) {
+                    __syncwarp(0x3fu);  // every p is updated before M^-1 p is formed
+                    double v = 0.0;
+#pragma unroll
+                    for (int i = 0; i < MI; ++i) v += mi[i] * ps[i];
+                    qs[j] += eps * v;
+                } else {
+                    qs[j] += eps * mi[0] * ps[j];
+                }
+            }
         }
         __syncthreads();
     }
@@ -380,8 +398,16 @@ int hawkes_surrogate_momentum(const void *w_bf16, const double *q, double *p, do
 int hawkes_surrogate_trajectory(const void *w_bf16, const double *norm, double *q, double *p, const double *minv,
                                 double eps, int n_steps, void *stream) {
     if (!w_bf16 || !norm || !q || !p || !minv || n_steps < 0 || !(eps == eps)) return HAWKES_EINVAL;
-    hk::surrogate_trajectory_kernel<<<1, hk::MH, 0, (cudaStream_t)stream>>>((const __nv_bfloat16 *)w_bf16, norm, q,
-                                                                            p, minv, eps, n_steps);
+    hk::surrogate_trajectory_kernel<false><<<1, hk::MH, 0, (cudaStream_t)stream>>>((const __nv_bfloat16 *)w_bf16,
+                                                                                   norm, q, p, minv, eps, n_steps);
+    return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
+}
+
+int hawkes_surrogate_trajectory_dense(const void *w_bf16, const double *norm, double *q, double *p,
+                                      const double *minv, double eps, int n_steps, void *stream) {
+    if (!w_bf16 || !norm || !q || !p || !minv || n_steps < 0 || !(eps == eps)) return HAWKES_EINVAL;
+    hk::surrogate_trajectory_kernel<true><<<1, hk::MH, 0, (cudaStream_t)stream>>>((const __nv_bfloat16 *)w_bf16,
+                                                                                  norm, q, p, minv, eps, n_steps);
     return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
 }
 

@@ -103,7 +103,10 @@ def _lib():
         L.hawkes_hmc_momentum.argtypes = [i64, vp, vp, d, vp]
         L.hawkes_hmc_position.argtypes = [i64, vp, vp, vp, d, vp]
         L.hawkes_hmc_kinetic.argtypes = [i64, vp, vp, vp, vp]
-        for f in (L.hawkes_hmc_scatter_rates, L.hawkes_hmc_momentum, L.hawkes_hmc_position, L.hawkes_hmc_kinetic):
+        L.hawkes_hmc_position_dense.argtypes = [i64, vp, vp, vp, d, vp]
+        L.hawkes_hmc_kinetic_dense.argtypes = [i64, vp, vp, vp, vp]
+        for f in (L.hawkes_hmc_scatter_rates, L.hawkes_hmc_momentum, L.hawkes_hmc_position, L.hawkes_hmc_kinetic,
+                  L.hawkes_hmc_position_dense, L.hawkes_hmc_kinetic_dense):
             f.restype = ctypes.c_int
         L._hmc_typed = True
     return L
@@ -268,6 +271,44 @@ class TreeMassOp:
         self.tm.velocity(p, self.minv, kinetic=out)
 
 
+class DenseMassOp:
+    """A dense mass matrix M over all dim <= 64 coordinates (a posterior over
+    the six globals alone, whose correlations a diagonal mass cannot follow),
+    in the form leapfrog, kinetic and TrajectoryGraph take in place of minv.
+    M^-1 and the Cholesky factor of M live in device buffers updated in place,
+    so captured trajectories see mass updates."""
+
+    def __init__(self, dim, device, floor=1e-2):
+        if dim > 64:
+            raise ValueError("a dense mass is offered for at most 64 coordinates")
+        f64 = dict(dtype=torch.float64, device=device)
+        self.dim, self.floor = dim, floor
+        self.M = np.eye(dim)
+        self.minv = torch.eye(dim, **f64).reshape(-1).contiguous()
+        self.chol = torch.eye(dim, **f64)
+
+    def set(self, M):
+        """Symmetrise M, clip its eigenvalues at the floor, and refresh M^-1 and chol(M)."""
+        M = 0.5 * (np.asarray(M, float) + np.asarray(M, float).T)
+        w, V = np.linalg.eigh(M)
+        w = np.maximum(w, self.floor)
+        self.M = (V * w) @ V.T
+        self.minv.copy_(torch.as_tensor(((V / w) @ V.T).ravel()))
+        self.chol.copy_(torch.as_tensor(np.linalg.cholesky(self.M)))
+
+    def position(self, q, p, eps):
+        s = ctypes.c_void_p(torch.cuda.current_stream(q.device).cuda_stream)
+        _check(_lib().hawkes_hmc_position_dense(self.dim, _ptr(q), _ptr(p), _ptr(self.minv), eps, s))
+
+    def kinetic(self, p, out):
+        s = ctypes.c_void_p(torch.cuda.current_stream(p.device).cuda_stream)
+        _check(_lib().hawkes_hmc_kinetic_dense(self.dim, _ptr(p), _ptr(self.minv), _ptr(out), s))
+
+    def draw(self, xi, p):
+        """p = chol(M) xi, so that p ~ N(0, M) for xi ~ N(0, I)."""
+        torch.mv(self.chol, xi, out=p)
+
+
 def leapfrog(post, q, p, g, eps, n_steps, minv, scratch, record=None):
     """n_steps leapfrog steps from (q, p) with gradient g at q; updates q, p in place.
 
@@ -389,6 +430,16 @@ class TrajectoryGraph:
         return self.out
 
 
+def jitter_levels(jitter: float):
+    """Step-size factors of a jittered sampler: 1 + jitter * (-1, -1/2, 0, 1/2, 1),
+    or [1] without jitter."""
+    if not jitter:
+        return [1.0]
+    if not 0.0 < jitter < 1.0:
+        raise ValueError("jitter must lie in [0, 1)")
+    return [1.0 + jitter * f for f in (-1.0, -0.5, 0.0, 0.5, 1.0)]
+
+
 def save_state(path, state: dict):
     """Write a sampler checkpoint atomically (a temporary file, then a rename)."""
     tmp = f"{path}.tmp"
@@ -402,7 +453,7 @@ def load_state(path) -> dict:
 
 def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_every=100, target_accept=0.8,
            mass_floor=1e-2, seed=0, keep=None, record=None, use_graph=True, checkpoint=None, checkpoint_every=0,
-           resume=None, mass="diag", fd_step=1e-3, mass0=None):
+           resume=None, mass="diag", fd_step=1e-3, mass0=None, jitter=0.0):
     """Run n_warmup + n_iter HMC iterations from q0 (device tensor); returns a Chain.
 
     mass: "diag", the diagonal mass of Section 2.3.2 (a running average of
@@ -411,6 +462,10 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
     it, d a running average of the likelihood's own curvature
     max(-H_diag - diag((sigma2 V)^-1), 0), so that the prior's tree
     correlations are preconditioned exactly (tree.TreeMass); or
+    "dense": a dense mass over all coordinates (at most 64: a posterior over
+    the six globals alone), the running average of minus the Hessian taken by
+    central differences of the gradient (2 dim extra gradients per update),
+    its eigenvalues clipped at mass_floor; or
     "tree_joint": the tree mass on the rates plus a dense block for the six
     globals and its coupling to the rates, [[A, B^T], [B, M_z]], with A and
     B running averages of minus the log posterior's Hessian columns along
@@ -430,9 +485,14 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
     far, counters) to `checkpoint` every that many iterations;
     resume: a checkpoint to continue from; the chain then equals the one that
     was never interrupted, bit for bit (the other arguments must match);
-    mass0: optional diagonal mass (device tensor [dim]) to start from instead
-    of the Hessian diagonal at q0 (mass="diag" only), e.g. another chain's
-    adapted mass, so that two samplers can be compared with the same one."""
+    mass0: optional mass to start from instead of the Hessian at q0: a
+    diagonal (device tensor [dim]) with mass="diag", another chain's
+    DenseMassOp with mass="dense" (e.g. another chain's adapted mass, so that
+    two samplers can be compared with the same one);
+    jitter: each trajectory's step size is eps times a factor drawn uniformly
+    from the five levels 1 + jitter * (-1, -1/2, 0, 1/2, 1), so that a fixed
+    trajectory length eps * n_steps cannot sit on a multiple of a half period
+    of the dynamics along some direction (one captured graph per level)."""
     dev = q0.device
     gen = torch.Generator(device=dev)
     gen.manual_seed(seed)
@@ -444,22 +504,23 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
     keep_t = torch.as_tensor(keep, device=dev)
     total = n_warmup + n_iter
     da = DualAveraging(eps0, target_accept)
-    if mass not in ("diag", "tree", "tree_joint"):
-        raise ValueError("mass must be 'diag', 'tree' or 'tree_joint'")
+    if mass not in ("diag", "tree", "tree_joint", "dense"):
+        raise ValueError("mass must be 'diag', 'tree', 'tree_joint' or 'dense'")
+    dm = DenseMassOp(dim, dev, floor=mass_floor) if mass == "dense" else None
     tm = xi = None
     joint = None  # running averages of the coupled blocks A (6 x 6) and B (m x 6)
-    if mass != "diag":
+    if mass in ("tree", "tree_joint"):
         if getattr(post, "tree", None) is None:
             raise ValueError(f"mass='{mass}' needs a posterior with a tree prior")
         from . import tree as tree_mod
         tm = tree_mod.TreeMass(post.tree, dim, z0=6, nc=6 if mass == "tree_joint" else 0)
         xi = torch.empty(tm.n_normals, **f64)
 
-    def hessian_columns(qc):
-        """-(d grad / d q_k) for the six globals by central differences: (dim x 6)."""
-        cols = np.empty((dim, 6))
+    def hessian_columns(qc, ncols=6):
+        """-(d grad / d q_k) for the first ncols coordinates by central differences: (dim x ncols)."""
+        cols = np.empty((dim, ncols))
         qp = torch.empty_like(qc)
-        for kk in range(6):
+        for kk in range(ncols):
             qp.copy_(qc)
             qp[kk] += fd_step
             gp = post.evaluate(qp)["grad"].cpu().numpy()
@@ -493,12 +554,19 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
         q = q0.clone()
         cur = post.evaluate(q, want_hess=True)
         cur = {k: v.clone() for k, v in cur.items()}
-        if mass0 is not None:
-            if tm is not None or mass0.numel() != dim:
+        if mass0 is not None and dm is not None:
+            if not isinstance(mass0, DenseMassOp) or mass0.dim != dim:
+                raise ValueError("with mass='dense', mass0 is another chain's DenseMassOp over the same coordinates")
+            dm.set(mass0.M)
+            mass = torch.clamp(-cur["hdiag"], min=mass_floor)
+        elif mass0 is not None:
+            if tm is not None or not isinstance(mass0, torch.Tensor) or mass0.numel() != dim:
                 raise ValueError("mass0 is a diagonal mass over all coordinates (mass='diag')")
             mass = mass0.to(**f64).clone()
         else:
             mass = torch.clamp(-cur["hdiag"], min=mass_floor)
+            if dm is not None:
+                dm.set(hessian_columns(q, dim))
         n_mass = 1
         minv = 1.0 / mass  # updated in place from here on (a captured trajectory reads it)
         if tm is not None:
@@ -533,7 +601,12 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
         draws, lps, acc, aprob = st["draws"], st["lps"], st["acc"], st["aprob"]
         post.calls.update(st["calls"])
         start, spent_warm, spent_samp = st["it"], st["spent_warm"], st["spent_samp"]
-    mop = TreeMassOp(tm, minv) if tm is not None else minv  # what leapfrog and kinetic apply
+    if dm is not None and resume is not None:
+        dm.set(st["dense_M"])
+    mop = TreeMassOp(tm, minv) if tm is not None else (dm if dm is not None else minv)  # what leapfrog applies
+    xi_d = torch.empty(dim, **f64) if dm is not None else None
+    levels = jitter_levels(jitter)
+    graphs = {}  # one captured trajectory per step-size level
     graph = None
     scratch = {"logpost": torch.empty((), **f64), "grad": torch.empty(dim, **f64), "hdiag": torch.empty(dim, **f64)}
     k0, k1 = torch.empty((), **f64), torch.empty((), **f64)
@@ -546,16 +619,22 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
             now = time.perf_counter()
             spent_warm += now - t_seg
             t_seg = now
-        if tm is None:
+        if dm is not None:
+            torch.randn(dim, generator=gen, out=xi_d, dtype=torch.float64, device=dev)
+            dm.draw(xi_d, p)
+        elif tm is None:
             torch.randn(dim, generator=gen, out=p, dtype=torch.float64, device=dev)
             p.mul_(torch.sqrt(mass))
         else:
             torch.randn(tm.n_normals, generator=gen, out=xi, dtype=torch.float64, device=dev)
             tm.momentum(minv, xi, p)
         kinetic(p, mop, k0)
+        lvl = int(rng.integers(len(levels))) if len(levels) > 1 else 0
+        eps_it = eps * levels[lvl]
         if use_graph and record is None and it >= n_warmup:
+            graph = graphs.get(lvl)
             if graph is None:
-                graph = TrajectoryGraph(post, eps, n_steps, mop, q, p, cur["grad"])
+                graph = graphs[lvl] = TrajectoryGraph(post, eps_it, n_steps, mop, q, p, cur["grad"])
             graph.q.copy_(q)
             graph.p.copy_(p)
             graph.g.copy_(cur["grad"])
@@ -563,7 +642,7 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
             qn, k1_t = graph.q, graph.k1
         else:
             qn = q.clone()
-            ev = leapfrog(post, qn, p, cur["grad"], eps, n_steps, mop, scratch, record)
+            ev = leapfrog(post, qn, p, cur["grad"], eps_it, n_steps, mop, scratch, record)
             kinetic(p, mop, k1)
             k1_t = k1
         h0 = -cur["logpost"].item() + k0.item()
@@ -578,7 +657,11 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
             cur["grad"].copy_(ev["grad"])
         if it < n_warmup:
             eps = da.update(a)
-        if (it + 1) % mass_every == 0:
+        if (it + 1) % mass_every == 0 and dm is not None:
+            # running average of minus the Hessian by central differences of the gradient
+            dm.set((n_mass * dm.M + 0.5 * (lambda c: c + c.T)(hessian_columns(q, dim))) / (n_mass + 1))
+            n_mass += 1
+        elif (it + 1) % mass_every == 0:
             hd = post.evaluate(q, want_hess=True)
             new = torch.clamp(-hd["hdiag"], min=mass_floor)
             if tm is not None:
@@ -608,6 +691,7 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
                 "dual_averaging": dict(da.__dict__), "gen_state": gen.get_state(),
                 "rng_state": rng.bit_generator.state, "draws": draws, "lps": lps, "acc": acc, "aprob": aprob,
                 "calls": dict(post.calls), "tree_d": tm.d.cpu() if tm is not None else None, "joint": joint,
+                "dense_M": dm.M.copy() if dm is not None else None,
                 "spent_warm": spent_warm + (seg if it < n_warmup else 0.0),
                 "spent_samp": spent_samp + (seg if it >= n_warmup else 0.0)})
             # the checkpoint's own cost is left out of both phases
@@ -624,6 +708,9 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
         spent_warm += now - t_seg
     if n_iter == 0:  # warm-up only: report the adapted step size
         eps = da.final() if n_warmup > 0 else eps
+    if dm is not None:
+        return Chain(draws, lps, acc, aprob, eps, dm.M.copy(), spent_samp, spent_warm,
+                     post.calls["grad"], post.calls["hess"], q, dm)
     return Chain(draws, lps, acc, aprob, eps, mass.cpu().numpy(), spent_samp, spent_warm,
                  post.calls["grad"], post.calls["hess"], q, mass)
 

@@ -41,8 +41,9 @@ def _lib():
         L.hawkes_mlp_adam.argtypes = [vp, vp, vp, vp, vp, f, f, f, f, ctypes.c_int, vp]
         L.hawkes_surrogate_momentum.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp, vp]
         L.hawkes_surrogate_trajectory.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_int, vp]
+        L.hawkes_surrogate_trajectory_dense.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_int, vp]
         for fn in (L.hawkes_mlp_forward, L.hawkes_mlp_loss_grad, L.hawkes_mlp_adam, L.hawkes_surrogate_momentum,
-                   L.hawkes_surrogate_trajectory):
+                   L.hawkes_surrogate_trajectory, L.hawkes_surrogate_trajectory_dense):
             fn.restype = ctypes.c_int
         L._mlp_typed = True
     return L
@@ -192,10 +193,12 @@ def median_rel_error(pred, exact):
 
 
 def collect_pairs(post, q0, n_pairs, n_steps=20, eps0=0.02, mass_every=50, seed=0, target_accept=0.8,
-                  burn_iters=100):
+                  burn_iters=100, mass="diag", jitter=0.0):
     """Exact HMC warm-up over the globals that records (q, gradient) at every
     leapfrog step after the first `burn_iters` iterations (which move the chain
-    from its start to the posterior); returns (q_pairs, g_pairs, chain state)."""
+    from its start to the posterior); returns (q_pairs, g_pairs, chain state).
+    mass: "diag" (Section 2.3.2) or "dense" (hmc.sample); the chain state's
+    mass_t is then the diagonal tensor or the DenseMassOp."""
     dev = q0.device
     dim = q0.numel()
     n_iter = int(math.ceil(n_pairs / n_steps))
@@ -211,7 +214,8 @@ def collect_pairs(post, q0, n_pairs, n_steps=20, eps0=0.02, mass_every=50, seed=
             gs[i].copy_(g)
         counter[0] += 1
 
-    ch = hmc.sample(post, q0, n_iter=0, n_warmup=n_iter + burn_iters, n_steps=n_steps, eps0=eps0,
+    ch = hmc.sample(post, q0, n_iter=0, n_warmup=n_iter + burn_iters, n_steps=n_steps, eps0=eps0, mass=mass,
+                    jitter=jitter,
                     mass_every=mass_every, seed=seed, target_accept=target_accept, record=record)
     k = min(max(counter[0] - skip, 0), qs.shape[0])
     qs, gs = qs[:k], gs[:k]
@@ -228,7 +232,12 @@ def collect_pairs(post, q0, n_pairs, n_steps=20, eps0=0.02, mass_every=50, seed=
 
 def surrogate_leapfrog(sur, q, p, eps, n_steps, minv):
     """Leapfrog trajectory over the six globals driven by the surrogate gradient:
-    one launch of the fused trajectory kernel."""
+    one launch of the fused trajectory kernel.  minv: the diagonal inverse
+    mass (device tensor) or an hmc.DenseMassOp."""
+    if isinstance(minv, hmc.DenseMassOp):
+        _check(_lib().hawkes_surrogate_trajectory_dense(_p(sur.mlp.wb), _p(sur.norm), _p(q), _p(p), _p(minv.minv),
+                                                        eps, n_steps, _stream(q.device)))
+        return
     _check(_lib().hawkes_surrogate_trajectory(_p(sur.mlp.wb), _p(sur.norm), _p(q), _p(p), _p(minv), eps, n_steps,
                                               _stream(q.device)))
 
@@ -241,7 +250,10 @@ def surrogate_leapfrog_steps(sur, q, p, eps, n_steps, minv):
     w, nrm = _p(sur.mlp.wb), _p(sur.norm)
     _check(L.hawkes_surrogate_momentum(w, _p(q), _p(p), 0.5 * eps, nrm, ctypes.c_void_p(0), s))
     for step in range(n_steps):
-        _check(L.hawkes_hmc_position(q.numel(), _p(q), _p(p), _p(minv), eps, s))
+        if isinstance(minv, hmc.DenseMassOp):
+            minv.position(q, p, eps)
+        else:
+            _check(L.hawkes_hmc_position(q.numel(), _p(q), _p(p), _p(minv), eps, s))
         _check(L.hawkes_surrogate_momentum(w, _p(q), _p(p), eps if step < n_steps - 1 else 0.5 * eps, nrm,
                                            ctypes.c_void_p(0), s))
 
@@ -254,13 +266,13 @@ class _SurrogateIteration:
     numbers the accept step needs land in one device vector
     e = [log pi(q), K(p0), log pi(q'), K(p')], read back with one copy."""
 
-    def __init__(self, post, sur, q, p, minv, eps, n_steps, use_graph=True):
+    def __init__(self, post, sur, q, p, minv, eps, n_steps, use_graph=True, qn=None, e=None):
         dev = q.device
         f64 = dict(dtype=torch.float64, device=dev)
         self.post, self.sur, self.eps, self.n_steps = post, sur, eps, n_steps
         self.q, self.p, self.minv = q, p, minv
-        self.qn = torch.empty_like(q)
-        self.e = torch.zeros(4, **f64)
+        self.qn = torch.empty_like(q) if qn is None else qn  # buffers that several step sizes' graphs share
+        self.e = torch.zeros(4, **f64) if e is None else e
         self.cur = {"logpost": self.e[0]}
         self.cand = {"logpost": self.e[2]}
         self.graph = None
@@ -305,8 +317,10 @@ class SurrogateChain:
 
 
 def sample(post, sur, q0, mass, eps, n_iter, n_steps=20, seed=0, monitor_every=100, fallback_window=50,
-           fallback_rate=0.2, use_graph=True):
-    """Surrogate-trajectory HMC with the exact Metropolis accept.
+           fallback_rate=0.2, use_graph=True, jitter=0.0):
+    """Surrogate-trajectory HMC with the exact Metropolis accept.  mass: the
+    diagonal mass (device tensor) or an hmc.DenseMassOp; jitter: step-size
+    levels as in hmc.sample (one captured iteration per level).
 
     Each iteration draws the momentum, then runs the captured iteration graph
     (fused surrogate trajectory, exact log posterior at the end point, both
@@ -323,15 +337,31 @@ def sample(post, sur, q0, mass, eps, n_iter, n_steps=20, seed=0, monitor_every=1
     rng = np.random.default_rng(seed)
     f64 = dict(dtype=torch.float64, device=dev)
     q = q0.clone()
-    minv = 1.0 / mass
-    sqrt_mass = torch.sqrt(mass)
+    dense = isinstance(mass, hmc.DenseMassOp)
+    minv = mass if dense else 1.0 / mass  # what the trajectory and the kinetic energy apply
+    sqrt_mass = None if dense else torch.sqrt(mass)
+    xi = torch.empty(dim, **f64)
     p = torch.empty(dim, **f64)
+
+    def draw_momentum(g):
+        if dense:
+            torch.randn(dim, generator=g, out=xi, dtype=torch.float64, device=dev)
+            mass.draw(xi, p)
+        else:
+            torch.randn(dim, generator=g, out=p, dtype=torch.float64, device=dev)
+            p.mul_(sqrt_mass)
+
     warm_gen = torch.Generator(device=dev)
     warm_gen.manual_seed(seed + 1)
-    torch.randn(dim, generator=warm_gen, out=p, dtype=torch.float64, device=dev)
-    p.mul_(sqrt_mass)  # a plausible momentum for the eager run that precedes the capture
-    it_dev = _SurrogateIteration(post, sur, q, p, minv, eps, n_steps, use_graph=use_graph)
-    post.logpost_only(q, it_dev.cur)  # log pi at the start (the eager run used e as scratch)
+    draw_momentum(warm_gen)  # a plausible momentum for the eager run that precedes the capture
+    levels = hmc.jitter_levels(jitter)
+    its = []
+    for f in levels:
+        its.append(_SurrogateIteration(post, sur, q, p, minv, eps * f, n_steps, use_graph=use_graph,
+                                       qn=its[0].qn if its else None, e=its[0].e if its else None))
+        draw_momentum(warm_gen)
+    it_dev = its[0]
+    post.logpost_only(q, it_dev.cur)  # log pi at the start (the eager runs used e as scratch)
     scratch = {"logpost": torch.empty((), **f64), "grad": torch.empty(dim, **f64), "hdiag": torch.empty(dim, **f64)}
     k1 = torch.empty((), **f64)
     draws_dev = torch.empty(n_iter, dim, **f64)
@@ -340,19 +370,19 @@ def sample(post, sur, q0, mass, eps, n_iter, n_steps=20, seed=0, monitor_every=1
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for it in range(n_iter):
-        torch.randn(dim, generator=gen, out=p, dtype=torch.float64, device=dev)
-        p.mul_(sqrt_mass)
+        draw_momentum(gen)
+        lvl = int(rng.integers(len(levels))) if len(levels) > 1 else 0
         if fell_back:
             hmc.kinetic(p, minv, it_dev.e[1])
             qn = q.clone()
             g0 = post.evaluate(q, out=scratch)["grad"].clone()
-            ev = hmc.leapfrog(post, qn, p, g0, eps, n_steps, minv, scratch)
+            ev = hmc.leapfrog(post, qn, p, g0, eps * levels[lvl], n_steps, minv, scratch)
             it_dev.e[2].copy_(ev["logpost"])
             hmc.kinetic(p, minv, k1)
             it_dev.e[3].copy_(k1)
             e = it_dev.e.cpu().numpy()
         else:
-            e = it_dev.run()
+            e = its[lvl].run()
             qn = it_dev.qn
             calls += 1
         h0 = -e[0] + e[1]

@@ -108,6 +108,92 @@ def test_sampler_recovers_gaussian_moments():
     assert np.all(np.abs(var / s ** 2 - 1) <= 5 * np.sqrt(2 / ess) + 0.05)
 
 
+class DenseGaussPost(GaussPost):
+    """A correlated Gaussian target (precision P) with known moments."""
+
+    def __init__(self, cov):
+        self.cov = cov
+        self.P = torch.linalg.inv(cov)
+        self.dim = cov.shape[0]
+        self.calls = {"grad": 0, "hess": 0}
+
+    def evaluate(self, q, want_hess=False, out=None):
+        if out is None:
+            out = {"logpost": torch.empty((), dtype=torch.float64, device=q.device),
+                   "grad": torch.empty_like(q), "hdiag": torch.empty_like(q)}
+        Pq = self.P @ q
+        out["logpost"].copy_(-0.5 * torch.dot(q, Pq))
+        out["grad"].copy_(-Pq)
+        if want_hess:
+            out["hdiag"].copy_(-torch.diagonal(self.P))
+        self.calls["hess" if want_hess else "grad"] += 1
+        return out
+
+
+def test_dense_mass_kernels_vs_numpy():
+    """hawkes_hmc_position_dense and hawkes_hmc_kinetic_dense against their
+    definitions, q += eps M^-1 p and 1/2 p^T M^-1 p."""
+    from paper_2103_03348_b300 import build, hmc
+    build.build()
+    rng = np.random.default_rng(8)
+    for k in (1, 6, 33, 64):
+        A = rng.normal(size=(k, k))
+        M = A @ A.T + k * np.eye(k)
+        op = hmc.DenseMassOp(k, "cuda")
+        op.set(M)
+        q0, p0 = rng.normal(size=k), rng.normal(size=k)
+        q = torch.tensor(q0, device="cuda")
+        p = torch.tensor(p0, device="cuda")
+        op.position(q, p, 0.37)
+        mi = np.linalg.inv(M)
+        assert np.allclose(q.cpu().numpy(), q0 + 0.37 * mi @ p0, rtol=1e-12, atol=1e-12)
+        out = torch.empty((), dtype=torch.float64, device="cuda")
+        op.kinetic(p, out)
+        assert abs(out.item() - 0.5 * p0 @ mi @ p0) <= 1e-12 * abs(0.5 * p0 @ mi @ p0)
+        # p = chol(M) xi has covariance M
+        xi = torch.randn(k, 4000, dtype=torch.float64, device="cuda")
+        P = (op.chol @ xi).cpu().numpy()
+        assert np.allclose(np.cov(P), M, rtol=0.0, atol=0.12 * np.abs(M).max())
+
+
+@pytest.mark.parametrize("jitter", [0.0, 0.2])
+def test_dense_mass_sampler_recovers_correlated_gaussian(jitter):
+    """mass='dense' (central-difference Hessian, running average) on a 6-D
+    Gaussian with correlations up to 0.97 and scales over two decades: means
+    and covariances recovered, and the slowest coordinate's ESS above the
+    diagonal mass's from the same start (with and without step-size jitter)."""
+    from paper_2103_03348_b300 import build, hmc
+    build.build()
+    rng = np.random.default_rng(12)
+    sd = np.array([0.05, 0.2, 1.0, 3.0, 0.5, 0.1])
+    C = np.full((6, 6), 0.0)
+    C[0, 3] = C[3, 0] = 0.97
+    C[1, 2] = C[2, 1] = -0.9
+    C[4, 5] = C[5, 4] = 0.8
+    C += np.eye(6)
+    cov = torch.tensor(C * np.outer(sd, sd), device="cuda")
+    post = DenseGaussPost(cov)
+    q0 = torch.tensor(0.5 * sd, device="cuda")
+    ch = hmc.sample(post, q0, n_iter=1500, n_warmup=300, n_steps=10, eps0=0.1, mass_every=50, seed=4, mass="dense",
+                    jitter=jitter)
+    ess = hmc.ess_all(ch.draws)
+    assert 0.5 < ch.accept.mean() <= 1.0
+    s = sd
+    assert np.all(np.abs(ch.draws.mean(0)) <= 5 * s / np.sqrt(ess))
+    # each covariance entry is the mean of z = (q_i - m_i)(q_j - m_j): held to 5 of its
+    # own Monte Carlo standard errors (HMC can be antithetic for the means but not for z)
+    xc = ch.draws - ch.draws.mean(0)
+    for i in range(6):
+        for j in range(i + 1):
+            z = xc[:, i] * xc[:, j]
+            mcse = z.std() / np.sqrt(min(hmc.ess(z), len(z)))
+            assert abs(z.mean() - C[i, j] * s[i] * s[j]) <= 5 * mcse + 1e-3 * s[i] * s[j], (i, j)
+    post.calls = {"grad": 0, "hess": 0}
+    ch_d = hmc.sample(post, q0, n_iter=1500, n_warmup=300, n_steps=10, eps0=0.1, mass_every=50, seed=4,
+                      jitter=jitter)
+    assert ess.min() > 1.5 * hmc.ess_all(ch_d.draws).min()
+
+
 def test_short_chain_on_hawkes_posterior():
     w, prec = problem()
     post, hmc = make_post(w, prec, "fp32c")
@@ -190,6 +276,28 @@ def test_graph_replayed_trajectories_equal_eager_ones(precision):
     b = hmc.sample(make(), q0, n_iter=40, n_warmup=20, n_steps=8, eps0=0.05, mass_every=15, seed=3, use_graph=True)
     assert np.array_equal(a.draws, b.draws) and np.array_equal(a.accept, b.accept)
     assert b.grad_calls == a.grad_calls + 8  # one eager trajectory before the capture
+
+
+def test_jittered_graph_trajectories_equal_eager_ones():
+    """With step-size jitter each level's trajectory is captured once and
+    replayed; the levels are drawn from the chain's own generator, so the
+    replayed chain still equals the eagerly launched one bit for bit."""
+    from paper_2103_03348_b300 import build, hmc, tree
+    build.build()
+    w, prec = problem()
+    d = lambda a: torch.tensor(np.asarray(a, float), dtype=torch.float64, device="cuda")  # noqa: E731
+    tp = tree.TreePrior(w.tree_parent, w.tree_length, 0.0, 1.0)
+
+    def make():
+        return hmc.Posterior(d(w.x), d(w.y), d(w.t), d(w.r), torch.tensor(w.sequenced, device="cuda"), None,
+                             hmc.prior_km_days(), "fp32c_st", tree=tp)
+
+    q0 = d(np.concatenate([np.log(w.params), w.r[w.sequenced]]))
+    kw = dict(n_iter=40, n_warmup=20, n_steps=8, eps0=0.05, mass_every=15, seed=3, jitter=0.2)
+    a = hmc.sample(make(), q0, use_graph=False, **kw)
+    b = hmc.sample(make(), q0, use_graph=True, **kw)
+    assert np.array_equal(a.draws, b.draws) and np.array_equal(a.accept, b.accept)
+    assert b.grad_calls - a.grad_calls in (8, 16, 24, 32, 40)  # one eager trajectory per captured level
 
 
 def test_checkpoint_resume_equals_uninterrupted_chain(tmp_path):

@@ -126,14 +126,19 @@ def test_fused_trajectory_equals_step_launches():
     sur = S.Surrogate(mlp, torch.tensor(norm, device="cuda"))
     d = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")  # noqa: E731
     minv = d(rng.uniform(0.1, 2.0, 6))
-    for n_steps in (0, 1, 20):
-        q0, p0 = rng.normal(size=6), rng.normal(size=6)
-        qa, pa, qb, pb = d(q0), d(p0), d(q0), d(p0)
-        S.surrogate_leapfrog(sur, qa, pa, 0.03, n_steps, minv)
-        S.surrogate_leapfrog_steps(sur, qb, pb, 0.03, n_steps, minv)
-        assert torch.equal(qa, qb) and torch.equal(pa, pb), n_steps
-        if n_steps:
-            assert not torch.equal(qa, d(q0))
+    from paper_2103_03348_b300 import hmc
+    A = rng.normal(size=(6, 6))
+    dense = hmc.DenseMassOp(6, "cuda")
+    dense.set(A @ A.T + 3 * np.eye(6))
+    for mi in (minv, dense):
+        for n_steps in (0, 1, 20):
+            q0, p0 = rng.normal(size=6), rng.normal(size=6)
+            qa, pa, qb, pb = d(q0), d(p0), d(q0), d(p0)
+            S.surrogate_leapfrog(sur, qa, pa, 0.03, n_steps, mi)
+            S.surrogate_leapfrog_steps(sur, qb, pb, 0.03, n_steps, mi)
+            assert torch.equal(qa, qb) and torch.equal(pa, pb), n_steps
+            if n_steps:
+                assert not torch.equal(qa, d(q0))
 
 
 def test_surrogate_hmc_gains_over_exact_hmc():
