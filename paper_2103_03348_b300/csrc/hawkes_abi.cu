@@ -139,7 +139,10 @@ __global__ void setup_kernel(ParamSource ps, int fp32c, int reuse, Derived *out,
         case 7: out->ih = 1.0 / (2.0 * h * h); break;
         // x~ = (x - xc) sqrt(log2(e)/2) / tau_x makes the background's spatial exponent -d~^2;
         // t~ = (t - tc) omega log2(e) makes the excitation's temporal exponent -dt~.
-        case 8: out->sx = sx; break;
+        case 8:
+            out->sx = sx;
+            out->sxh = fp32c ? sqrt(LOG2E / 2.0) / h : 1.0;
+            break;
         case 9: out->st = st; break;
         case 10: out->cbt = (fp32c && !tt_inf) ? (float)(LOG2E / (2.0 * tt * tt) / (st * st)) : 0.0f; break;
         case 11: out->hh = fp32c ? (float)((tx / h) * (tx / h)) : 0.0f; break;
@@ -373,7 +376,7 @@ static int shard_phase(const double *x, const double *y, const double *t, const 
         if (rc != HAWKES_OK) return rc;
         return launch_shard_export(k.c, k.ws, (double *)xbuf, k.s) == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
     }
-    if (launch_shard_import(k.c, k.ws, (const double *)xbuf, k.s) != cudaSuccess) return HAWKES_ECUDA;
+    if (launch_shard_import(k.c, k.inw, k.ws, (const double *)xbuf, k.s) != cudaSuccess) return HAWKES_ECUDA;
     return phase_cols(k, nullptr);
 }
 

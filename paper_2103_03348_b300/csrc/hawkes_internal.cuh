@@ -93,6 +93,7 @@ struct Derived {
     double mu0, tx, tt, th0, om, h;
     double A, B;          // lambda_n = A * sum G + B * sum E
     double sx, st;        // FP32C scaled coordinates: x~ = (x - xc) sx, t~ = (t - tc) st; 1 for FP64
+    double sxh;           // FP32C column pass: x' = (x - xc) sxh, so that hh d~^2 = d'^2 (sxh = sx tau_x / h)
     double ibx, ibt, ih;  // FP64:  G = exp(-ibx d^2 - ibt dt^2), E = exp(r - om dt - ih d^2)
     float cbt, hh;        // FP32C: G = 2^-(d~^2 + cbt dt~^2), E = 2^(r^_s - t~_n - hh d~^2)
     int tt_inf, valid;
@@ -157,8 +158,9 @@ struct Workspace {
     double4_32a *tbox;       // [tiles] xmin, xmax, ymin, ymax (prep)
     float4 *src32;       // [npad]  pairs: (-x0,-x1,-y0,-y1),(-t0,-t1,r^0,r^1), r^ = r~ + t~ (read-only
                          //         after pack: row blocks of other tiles read it while a tile finishes)
-    float4 *tgt32;       // [npad]  the column pass's targets: (-x0,-x1,-y0,-y1),(-t0,-t1,g^0,g^1) with the
-                         //         column weight g^ = log2(B/lambda) - t~, written by the tile finish
+    float4 *tgt32;       // [npad]  the column pass's targets: (-x'0,-x'1,-y'0,-y'1),(-t0,-t1,-g^0,-g^1) in the
+                         //         excitation's scaled coordinates x' = (x - xc) sxh, with the column
+                         //         weight g^ = log2(B/lambda) - t~, written by the tile finish
     float4 *tstat32;     // [tiles] t~min, t~max, max r^, max g^
     double4_32a *src64;      // [npad]  (x, y, t, r) FP64 (FP64 path)
     double *rowpart;     // [n_chunks * NMOM * npad]: FP64 partials (FP64 path), FP32C Kahan pairs as float2
@@ -215,7 +217,8 @@ cudaError_t launch_col32_subset_st(const Consts &c, const Inputs &in, const Work
 cudaError_t launch_colfinish_subset(const Consts &c, const Workspace &ws, const Outputs &out, const int *rate_idx,
                                     int k_rates, int by_position, cudaStream_t s);
 cudaError_t launch_shard_export(const Consts &c, const Workspace &ws, double *xbuf, cudaStream_t s);
-cudaError_t launch_shard_import(const Consts &c, const Workspace &ws, const double *xbuf, cudaStream_t s);
+cudaError_t launch_shard_import(const Consts &c, const Inputs &in, const Workspace &ws, const double *xbuf,
+                                cudaStream_t s);
 cudaError_t launch_tree_prior(int64_t m, const int *plan, const double *len, double tau0, double sigma2,
                               const double *z, double *scratch, double *logdens, double *pz, double *pdiag,
                               cudaStream_t s);
@@ -394,6 +397,27 @@ __device__ __forceinline__ bool col_alive(const GroupStat &W, const GroupStat &G
     if (G.ix.y <= W.ix.z) return false;  // no target follows any source
     const float d = hh * box_gap2(W.box, G.box);
     return exp2_alive(W.tr.z + G.tr.w - d, fabsf(W.tr.z) + fabsf(G.tr.w) + d);
+}
+
+// The column pass's packed target i (position order): (-x'_i, -y'_i) with
+// x' = (x - xc) sxh from the FP64 inputs, so that the excitation's spatial
+// exponent hh d~^2 is d'^2 with no multiply; -t~_i copied from the packed
+// sources; and -g^_i (g^ = -inf for padding and rows without a weight, so
+// that every term of that target is exactly 0).
+__device__ __forceinline__ void pack_target(const Workspace &ws, const Inputs &in, const Derived &D, int i, int n,
+                                            float ghat) {
+    const float *f = reinterpret_cast<const float *>(ws.src32);
+    float *o = reinterpret_cast<float *>(ws.tgt32);
+    const int p = i >> 1, l = i & 1;
+    float xs = 0.0f, ys = 0.0f;
+    if (i < n) {
+        xs = -(float)((in.x[i] - ws.centre[0]) * D.sxh);
+        ys = -(float)((in.y[i] - ws.centre[1]) * D.sxh);
+    }
+    o[8 * p + 0 + l] = xs;
+    o[8 * p + 2 + l] = ys;
+    o[8 * p + 4 + l] = f[8 * p + 4 + l];
+    o[8 * p + 6 + l] = -ghat;
 }
 
 #endif  // __CUDACC__

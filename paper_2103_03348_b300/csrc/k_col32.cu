@@ -6,8 +6,10 @@
 //     C1_m = sum_n v_nm,   C2_m = sum_n v_nm^2
 // because dl/dr_m = C1_m - dLambda/dr_m and d2l/dr_m^2 = C1_m - C2_m - dLambda/dr_m.
 // In the scaled base-2 coordinates of the row pass,
-//     v_nm = 2^(g^_n + r^_m - hh d~^2),  g^_n = log2(B / lambda_n) - t~_n,  r^_m = r~_m + t~_m,
-// where the row finish stored g^_n in the fourth slot of each packed target (tgt32).
+//     v_nm = 2^(g^_n + r^_m - hh d~^2) = 2^(g^_n + r^_m - d'^2),
+//     g^_n = log2(B / lambda_n) - t~_n,  r^_m = r~_m + t~_m,  x' = x~ tau_x / h,
+// where the row finish stored -g^_n in the fourth slot of each packed target
+// (tgt32) and the targets' coordinates in the x' scale.
 //
 // One block of 128 threads owns 128 sources (one per thread) and sweeps a
 // chunk of later target tiles staged in shared memory, two targets per packed
@@ -31,20 +33,22 @@ __global__ void __launch_bounds__(TILE, 4) col32_kernel(Consts c, Inputs in, Wor
     __shared__ float4 sAB[2][TILE];
     __shared__ int sG[2][TILE];
 
-    float2 xm, ym, rm;
+    float2 xm, ym, nrm;
     {
-        const float *f = reinterpret_cast<const float *>(ws.src32);
-        const int p = m >> 1, l = m & 1;
-        xm = splat(-f[8 * p + 0 + l]);
-        ym = splat(-f[8 * p + 2 + l]);
+        // the source in the targets' scaled coordinates x' = (x - xc) sxh, and -r^_m with
         // r^_m = r~_m + t~_m, from the FP64 inputs (as pack forms it)
-        float r = -1.0e9f;
-        if (m < n) r = (float)(in.r[m] * LOG2E + (in.t[m] - ws.centre[2]) * D.st);
-        rm = splat(r);
+        float x = 0.f, y = 0.f, r = -1.0e9f;
+        if (m < n) {
+            x = (float)((in.x[m] - ws.centre[0]) * D.sxh);
+            y = (float)((in.y[m] - ws.centre[1]) * D.sxh);
+            r = (float)(in.r[m] * LOG2E + (in.t[m] - ws.centre[2]) * D.st);
+        }
+        xm = splat(x);
+        ym = splat(y);
+        nrm = splat(-r);
     }
     const int4 tiM = ws.tinfo[tile];
     const float4 stM = ws.tstat32[tile];
-    const float2 nhh2 = splat(-D.hh);
     const int m_first = tile * TILE, m_last = m_first + tiM.w - 1;
 
     float2 run1 = make_float2(0.f, 0.f), run2 = make_float2(0.f, 0.f);
@@ -66,8 +70,8 @@ __global__ void __launch_bounds__(TILE, 4) col32_kernel(Consts c, Inputs in, Wor
         __syncthreads();
         const int npairs = (tiU.w + 1) >> 1;
         const bool all_causal = m_last < tiU.x;
-        if (all_causal) col_tile<MODE, false>(sAB[buf], sG[buf], npairs, xm, ym, rm, m, nhh2, run1, run2);
-        else col_tile<MODE, true>(sAB[buf], sG[buf], npairs, xm, ym, rm, m, nhh2, run1, run2);
+        if (all_causal) col_tile<MODE, false>(sAB[buf], sG[buf], npairs, xm, ym, nrm, m, run1, run2);
+        else col_tile<MODE, true>(sAB[buf], sG[buf], npairs, xm, ym, nrm, m, run1, run2);
         kahan(s1, k1, __fadd_rn(run1.x, run1.y));
         run1 = make_float2(0.f, 0.f);
         if (MODE == MODE_HESS) {
@@ -102,15 +106,19 @@ __global__ void __launch_bounds__(TILE, 4) col32_subset_kernel(Consts c, Inputs 
     __shared__ float shf[TILE];
     __shared__ int shi[TILE];
 
-    float2 xm, ym, rm;
+    float2 xm, ym, nrm;
     float r = -1.0e9f;
     {
-        const float *f = reinterpret_cast<const float *>(ws.src32);
-        const int p = m >> 1, l = m & 1;
-        xm = splat(valid ? -f[8 * p + 0 + l] : 1.0e9f);
-        ym = splat(valid ? -f[8 * p + 2 + l] : 1.0e9f);
-        if (valid && m < n) r = (float)(in.r[m] * LOG2E + (in.t[m] - ws.centre[2]) * D.st);
-        rm = splat(r);
+        // as in col32_kernel; an invalid slot sits far away with r^ = -1e9 (exact zeros)
+        float x = 1.0e9f, y = 1.0e9f;
+        if (valid && m < n) {
+            x = (float)((in.x[m] - ws.centre[0]) * D.sxh);
+            y = (float)((in.y[m] - ws.centre[1]) * D.sxh);
+            r = (float)(in.r[m] * LOG2E + (in.t[m] - ws.centre[2]) * D.st);
+        }
+        xm = splat(x);
+        ym = splat(y);
+        nrm = splat(-r);
     }
     // tile statistics of this block's sources (uniform for the block)
     const float rmax = block_max<TILE>(r, shf);
@@ -129,7 +137,6 @@ __global__ void __launch_bounds__(TILE, 4) col32_subset_kernel(Consts c, Inputs 
         __syncthreads();
     }
     const int m_last = shi[0];
-    const float2 nhh2 = splat(-D.hh);
 
     float2 run1 = make_float2(0.f, 0.f), run2 = make_float2(0.f, 0.f);
     float s1 = 0.f, k1 = 0.f, s2 = 0.f, k2 = 0.f;
@@ -150,8 +157,8 @@ __global__ void __launch_bounds__(TILE, 4) col32_subset_kernel(Consts c, Inputs 
         __syncthreads();
         const int npairs = (tiU.w + 1) >> 1;
         const bool all_causal = m_last < tiU.x;
-        if (all_causal) col_tile<MODE, false>(sAB[buf], sG[buf], npairs, xm, ym, rm, m, nhh2, run1, run2);
-        else col_tile<MODE, true>(sAB[buf], sG[buf], npairs, xm, ym, rm, valid ? m : INT_MAX, nhh2, run1, run2);
+        if (all_causal) col_tile<MODE, false>(sAB[buf], sG[buf], npairs, xm, ym, nrm, m, run1, run2);
+        else col_tile<MODE, true>(sAB[buf], sG[buf], npairs, xm, ym, nrm, valid ? m : INT_MAX, run1, run2);
         kahan(s1, k1, __fadd_rn(run1.x, run1.y));
         run1 = make_float2(0.f, 0.f);
         if (MODE == MODE_HESS) {

@@ -28,7 +28,7 @@ struct ColWarpShared {
 // into registers while the previous item is evaluated.
 template <int MODE>
 __device__ __forceinline__ void col_sweep_warp(const Workspace &ws, int ub, int ue, const GroupStat &W, float2 xm,
-                                               float2 ym, float2 rm, int rank, float2 nhh2, float hh, float &s1,
+                                               float2 ym, float2 nrm, int rank, float hh, float &s1,
                                                float &k1, float &s2, float &k2, ColWarpShared &sh) {
     constexpr int ALLC = 1 << 30;  // item flag: every source precedes every target of the group
     const int lane = threadIdx.x & 31;
@@ -86,8 +86,8 @@ __device__ __forceinline__ void col_sweep_warp(const Workspace &ws, int ub, int 
                 pg = ws.gidx[(size_t)it * GROUP + lane];
             }
             const int np = ((((cur >> 24) & 63) + 1) + 1) >> 1;
-            if (cur & ALLC) col_tile<MODE, false>(sh.ab[buf], sh.gi[buf], np, xm, ym, rm, rank, nhh2, run1, run2);
-            else col_tile<MODE, true>(sh.ab[buf], sh.gi[buf], np, xm, ym, rm, rank, nhh2, run1, run2);
+            if (cur & ALLC) col_tile<MODE, false>(sh.ab[buf], sh.gi[buf], np, xm, ym, nrm, rank, run1, run2);
+            else col_tile<MODE, true>(sh.ab[buf], sh.gi[buf], np, xm, ym, nrm, rank, run1, run2);
             buf ^= 1;
             if (nt != (cur & 0xffffff) / CGPT) {  // tile boundary: merge the runs
                 kahan(s1, k1, __fadd_rn(run1.x, run1.y));
@@ -112,27 +112,29 @@ __global__ void __launch_bounds__(GROUP, 24) col32_st_kernel(Consts c, Inputs in
     const int n = c.g.n, npad = c.g.npad;
     __shared__ ColWarpShared sh;
 
-    float2 xm, ym, rm;
+    float2 xm, ym, nrm;
     {
-        const float *f = reinterpret_cast<const float *>(ws.src32);
-        const int p = m >> 1, l = m & 1;
-        xm = splat(-f[8 * p + 0 + l]);
-        ym = splat(-f[8 * p + 2 + l]);
-        float r = -1.0e9f;
-        if (m < n) r = (float)(in.r[m] * LOG2E + (in.t[m] - ws.centre[2]) * D.st);
-        rm = splat(r);
+        // the source in the targets' scaled coordinates x' = (x - xc) sxh, and -r^_m
+        float x = 0.f, y = 0.f, r = -1.0e9f;
+        if (m < n) {
+            x = (float)((in.x[m] - ws.centre[0]) * D.sxh);
+            y = (float)((in.y[m] - ws.centre[1]) * D.sxh);
+            r = (float)(in.r[m] * LOG2E + (in.t[m] - ws.centre[2]) * D.st);
+        }
+        xm = splat(x);
+        ym = splat(y);
+        nrm = splat(-r);
     }
     const int rank = ws.perm[m];
     const GroupStat W = ws.grp[sg];
     const float hh = D.hh;
-    const float2 nhh2 = splat(-hh);
 
     float s1 = 0.f, k1 = 0.f, s2 = 0.f, k2 = 0.f;
     if (!group_empty(W)) {
         const int start = (tile / SLAB_TILES) * SLAB_TILES;
         const int ub = start + chunk * c.g.chunk_tiles;
         const int ue = min(c.g.tiles, ub + c.g.chunk_tiles);
-        col_sweep_warp<MODE>(ws, ub, ue, W, xm, ym, rm, rank, nhh2, hh, s1, k1, s2, k2, sh);
+        col_sweep_warp<MODE>(ws, ub, ue, W, xm, ym, nrm, rank, hh, s1, k1, s2, k2, sh);
     }
     ws.colpart[((size_t)chunk * 2 + 0) * npad + m] = (double)s1 - (double)k1;
     if (MODE == MODE_HESS) ws.colpart[((size_t)chunk * 2 + 1) * npad + m] = (double)s2 - (double)k2;
@@ -155,15 +157,17 @@ __global__ void __launch_bounds__(GROUP, 24) col32_subset_st_kernel(Consts c, In
     const int m = valid ? ws.inv[raw] : 0;
     __shared__ ColWarpShared sh;
 
-    float xw = 0.f, yw = 0.f, r = -1.0e9f;
+    float xw = 0.f, yw = 0.f, xh = 1.0e9f, yh = 1.0e9f, r = -1.0e9f;
     if (valid) {
         const float *f = reinterpret_cast<const float *>(ws.src32);
         const int p = m >> 1, l = m & 1;
-        xw = -f[8 * p + 0 + l];
+        xw = -f[8 * p + 0 + l];  // the group bounds' scale (x~)
         yw = -f[8 * p + 2 + l];
+        xh = (float)((in.x[m] - ws.centre[0]) * D.sxh);  // the targets' scale (x')
+        yh = (float)((in.y[m] - ws.centre[1]) * D.sxh);
         r = (float)(in.r[m] * LOG2E + (in.t[m] - ws.centre[2]) * D.st);
     }
-    const float2 xm = splat(valid ? xw : 1.0e9f), ym = splat(valid ? yw : 1.0e9f), rm = splat(r);
+    const float2 xm = splat(xh), ym = splat(yh), nrm = splat(-r);
     const int rank = valid ? raw : INT_MAX;  // an invalid slot is masked everywhere
     GroupStat W;
     W.box = make_float4(warp_minf(valid ? xw : INFINITY), warp_maxf(valid ? xw : -INFINITY),
@@ -172,12 +176,11 @@ __global__ void __launch_bounds__(GROUP, 24) col32_subset_st_kernel(Consts c, In
     W.ix = make_int4(0, 0, warp_mini(valid ? raw : INT_MAX), warp_maxi(valid ? raw : INT_MIN));
     const int start = warp_mini(valid ? (m / SLAB_EVENTS) * SLAB_TILES : INT_MAX);
     const float hh = D.hh;
-    const float2 nhh2 = splat(-hh);
     float s1 = 0.f, k1 = 0.f, s2 = 0.f, k2 = 0.f;
     if (start != INT_MAX) {  // warp-uniform: some source is valid
         const int ub = start + chunk * c.g.chunk_tiles;
         const int ue = min(c.g.tiles, ub + c.g.chunk_tiles);
-        col_sweep_warp<MODE>(ws, ub, ue, W, xm, ym, rm, rank, nhh2, hh, s1, k1, s2, k2, sh);
+        col_sweep_warp<MODE>(ws, ub, ue, W, xm, ym, nrm, rank, hh, s1, k1, s2, k2, sh);
     }
     if (valid) {
         ws.colpart[((size_t)chunk * 2 + 0) * npad + j] = (double)s1 - (double)k1;

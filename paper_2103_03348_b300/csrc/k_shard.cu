@@ -36,14 +36,15 @@ __global__ void __launch_bounds__(TILE) shard_export_kernel(Consts c, Workspace 
     if (threadIdx.x == NACC + 1) rec[NACC + 1] = c.fp32c ? float_bits(ws.tstat32[tile].w) : 0.0;
     if (c.fp32c) {
         const float *f = reinterpret_cast<const float *>(ws.tgt32);
-        rec[16 + threadIdx.x] = float_bits(f[8 * (i >> 1) + 6 + (i & 1)]);
+        rec[16 + threadIdx.x] = float_bits(f[8 * (i >> 1) + 6 + (i & 1)]);  // -g^, as packed
     } else {
         rec[16 + threadIdx.x] = ws.w64[i];
     }
 }
 
 // one block per tile of the whole problem
-__global__ void __launch_bounds__(TILE) shard_import_kernel(Consts c, Workspace ws, const double *__restrict__ xbuf) {
+__global__ void __launch_bounds__(TILE) shard_import_kernel(Consts c, Inputs in, Workspace ws,
+                                                            const double *__restrict__ xbuf) {
     pdl_wait();
     const int tile = blockIdx.x;
     const double *rec = xbuf + (size_t)tile * XREC_DOUBLES;
@@ -55,14 +56,8 @@ __global__ void __launch_bounds__(TILE) shard_import_kernel(Consts c, Workspace 
     }
     if (threadIdx.x == NACC + 1 && c.fp32c) ws.tstat32[tile].w = bits_float(rec[NACC + 1]);
     if (c.fp32c) {
-        // the column pass's packed targets: coordinates from this shard's own packing
-        const float *f = reinterpret_cast<const float *>(ws.src32);
-        float *o = reinterpret_cast<float *>(ws.tgt32);
-        const int p = i >> 1, l = i & 1;
-        o[8 * p + 0 + l] = f[8 * p + 0 + l];
-        o[8 * p + 2 + l] = f[8 * p + 2 + l];
-        o[8 * p + 4 + l] = f[8 * p + 4 + l];
-        o[8 * p + 6 + l] = bits_float(rec[16 + threadIdx.x]);
+        // the column pass's packed targets, as the tile finish writes them
+        pack_target(ws, in, *c.d, i, c.g.n, -bits_float(rec[16 + threadIdx.x]));
     } else {
         ws.w64[i] = rec[16 + threadIdx.x];
     }
@@ -74,8 +69,9 @@ cudaError_t launch_shard_export(const Consts &c, const Workspace &ws, double *xb
     return cudaGetLastError();
 }
 
-cudaError_t launch_shard_import(const Consts &c, const Workspace &ws, const double *xbuf, cudaStream_t s) {
-    launch_pdl(shard_import_kernel, c.g.tiles, TILE, 0, s, c, ws, xbuf);
+cudaError_t launch_shard_import(const Consts &c, const Inputs &in, const Workspace &ws, const double *xbuf,
+                                cudaStream_t s) {
+    launch_pdl(shard_import_kernel, c.g.tiles, TILE, 0, s, c, in, ws, xbuf);
     return cudaGetLastError();
 }
 

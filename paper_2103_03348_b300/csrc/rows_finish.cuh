@@ -270,16 +270,7 @@ __device__ __forceinline__ void finish_tile_fp32c(const Consts &c, const Inputs 
     for (int k = 0; k < NACC; ++k) acc[k] = 0.0;
     float ghat = -INFINITY;
     if (valid) epilogue_row<false>(c, D, in, ws, i, Mo, acc, ghat);  // the integral term came with the row pass
-    {
-        // the column pass's packed targets: the coordinates as packed, g^ in the fourth slot
-        const float *f = reinterpret_cast<const float *>(ws.src32);
-        float *o = reinterpret_cast<float *>(ws.tgt32);
-        const int p = i >> 1, l = i & 1;
-        o[8 * p + 0 + l] = f[8 * p + 0 + l];
-        o[8 * p + 2 + l] = f[8 * p + 2 + l];
-        o[8 * p + 4 + l] = f[8 * p + 4 + l];
-        o[8 * p + 6 + l] = ghat;
-    }
+    pack_target(ws, in, D, i, c.g.n, ghat);  // the column pass's packed target
     {
         const double v = block_sum_multi<TILE, NACC>(acc, fsh);
         if (threadIdx.x < NACC)
