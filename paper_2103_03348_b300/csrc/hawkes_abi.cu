@@ -110,8 +110,9 @@ __global__ void setup_kernel(ParamSource ps, int fp32c, int reuse, Derived *out,
     const int tt_inf = isinf(tt) ? 1 : 0;
     const double two_pi = 6.283185307179586476925286766559;
     const double B = th0 * om / (two_pi * h * h);
-    const double sx = fp32c ? sqrt(LOG2E / 2.0) / tx : 1.0;
-    const double st = fp32c ? om * LOG2E : 1.0;
+    const double sx = fp32c ? sqrt(LOG2E / 2.0) / tx : sqrt(0.5) / tx;
+    const double st = fp32c ? om * LOG2E : om;
+    const double sxe = fp32c ? sx : sqrt(0.5) / h;
     // the call's header: status bits (with the event checks of the call that
     // prepared these events, when they are reused), the rest cleared
     if (blockIdx.x == 0 && lane > 0 && lane < 8) hdr[lane] = 0;
@@ -142,6 +143,7 @@ __global__ void setup_kernel(ParamSource ps, int fp32c, int reuse, Derived *out,
         case 8:
             out->sx = sx;
             out->sxh = fp32c ? sqrt(LOG2E / 2.0) / h : 1.0;
+            out->sxe = sxe;
             break;
         case 9: out->st = st; break;
         case 10: out->cbt = (fp32c && !tt_inf) ? (float)(LOG2E / (2.0 * tt * tt) / (st * st)) : 0.0f; break;
@@ -154,7 +156,7 @@ __global__ void setup_kernel(ParamSource ps, int fp32c, int reuse, Derived *out,
             const int j = blockIdx.x - 13;
             if (j < 0 || j >= EP_N) break;
             const double A = tt_inf ? mu0 / (two_pi * tx * tx) : mu0 / (two_pi * sqrt(two_pi) * tx * tx * tt);
-            const double isx2 = 1.0 / (sx * sx), ist = 1.0 / st, ist2 = ist * ist;
+            const double isx2 = 1.0 / (sx * sx), isxe2 = 1.0 / (sxe * sxe), ist = 1.0 / st, ist2 = ist * ist;
             const double ix = 1.0 / tx, it = tt_inf ? 0.0 : 1.0 / tt, ih = 1.0 / h;
             const double ix2 = ix * ix, it2 = it * it, ih2 = ih * ih;
             double v = 0.0;
@@ -167,7 +169,7 @@ __global__ void setup_kernel(ParamSource ps, int fp32c, int reuse, Derived *out,
                 case EP_E3: v = B / th0; break;
                 case EP_E4: v = B / om; break;
                 case EP_ET: v = B * ist; break;
-                case EP_ED2: v = B * isx2 * (ih2 * ih); break;
+                case EP_ED2: v = B * isxe2 * (ih2 * ih); break;
                 case EP_E5: v = 2.0 * B * ih; break;
                 case EP_GD4: v = A * (isx2 * isx2) * (ix2 * ix2 * ix2); break;
                 case EP_GD2B: v = 7.0 * A * isx2 * (ix2 * ix2); break;
@@ -177,8 +179,8 @@ __global__ void setup_kernel(ParamSource ps, int fp32c, int reuse, Derived *out,
                 case EP_G2B: v = 2.0 * A * it2; break;
                 case EP_ET2: v = B * ist2; break;
                 case EP_ETB: v = 2.0 * B * ist / om; break;
-                case EP_ED4: v = B * (isx2 * isx2) * (ih2 * ih2 * ih2); break;
-                case EP_ED2B: v = 7.0 * B * isx2 * (ih2 * ih2); break;
+                case EP_ED4: v = B * (isxe2 * isxe2) * (ih2 * ih2 * ih2); break;
+                case EP_ED2B: v = 7.0 * B * isxe2 * (ih2 * ih2); break;
                 case EP_E5B: v = 6.0 * B * ih2; break;
                 default: break;
             }

@@ -92,7 +92,10 @@ Geometry make_geometry(int64_t n);
 struct Derived {
     double mu0, tx, tt, th0, om, h;
     double A, B;          // lambda_n = A * sum G + B * sum E
-    double sx, st;        // FP32C scaled coordinates: x~ = (x - xc) sx, t~ = (t - tc) st; 1 for FP64
+    double sx, st;        // scaled coordinates x~ = (x - xc) sx, t~ = (t - tc) st of the row moments:
+                          // FP32C sx = sqrt(log2(e)/2) / tau_x, st = omega log2(e); FP64 sx = sqrt(1/2) / tau_x,
+                          // st = omega (moments in the kernels' own units stay far from FP64's subnormals)
+    double sxe;           // the excitation moments' spatial scale: sx (FP32C), sqrt(1/2) / h (FP64)
     double sxh;           // FP32C column pass: x' = (x - xc) sxh, so that hh d~^2 = d'^2 (sxh = sx tau_x / h)
     double ibx, ibt, ih;  // FP64:  G = exp(-ibx d^2 - ibt dt^2), E = exp(r - om dt - ih d^2)
     float cbt, hh;        // FP32C: G = 2^-(d~^2 + cbt dt~^2), E = 2^(r^_s - t~_n - hh d~^2)

@@ -7,23 +7,32 @@
 
 namespace hk {
 
+// The moments are taken in the scaled units of Derived (d~^2 = d^2 sx^2 for the
+// background, d^2 sxe^2 for the excitation, dt~ = dt st): with raw units a
+// small bandwidth would push moments such as G d^4 of a tiny-intensity row
+// into FP64's subnormal range (at tau_x = 6e-4 and an intensity of 1e-302,
+// G d^4 is about 1e-315, with 27 significant bits left), and the Hessian
+// entry, a difference of such moments, would lose them.
 template <int MODE>
 __device__ __forceinline__ void accumulate64(double (&a)[NMOM], double xs, double ys, double ts, double rs,
                                              bool bg_on, bool ex_on, double xn, double yn, double tn,
                                              const Derived &D) {
     const double dx = xn - xs, dy = yn - ys, dt = tn - ts;
     const double d2 = dx * dx + dy * dy, dt2 = dt * dt;
+    const double ut = dt * D.st, ut2 = ut * ut;
     if (bg_on) {
         const double g = exp(-D.ibx * d2 - D.ibt * dt2);
+        const double u2 = d2 * (D.sx * D.sx);
         a[MO_G] += g;
-        if (MODE >= MODE_GRAD) { a[MO_GD2] += g * d2; a[MO_GT2] += g * dt2; }
-        if (MODE == MODE_HESS) { a[MO_GD4] += g * d2 * d2; a[MO_GT4] += g * dt2 * dt2; }
+        if (MODE >= MODE_GRAD) { a[MO_GD2] += g * u2; a[MO_GT2] += g * ut2; }
+        if (MODE == MODE_HESS) { a[MO_GD4] += g * u2 * u2; a[MO_GT4] += g * ut2 * ut2; }
     }
     if (ex_on) {
         const double e = exp(rs - D.om * dt - D.ih * d2);
+        const double v2 = d2 * (D.sxe * D.sxe);
         a[MO_E] += e;
-        if (MODE >= MODE_GRAD) { a[MO_ET] += e * dt; a[MO_ED2] += e * d2; }
-        if (MODE == MODE_HESS) { a[MO_ET2] += e * dt2; a[MO_ED4] += e * d2 * d2; }
+        if (MODE >= MODE_GRAD) { a[MO_ET] += e * ut; a[MO_ED2] += e * v2; }
+        if (MODE == MODE_HESS) { a[MO_ET2] += e * ut2; a[MO_ED4] += e * v2 * v2; }
     }
 }
 
@@ -214,10 +223,7 @@ __device__ __forceinline__ void finish_tile_fp32c(const Consts &c, const Inputs 
         // evaluates only the terms within 2^80 of them.  (FP32 exponents are off
         // by far less than 80 units, and FP64 coordinates keep the kept terms
         // exact where FP32 ones would cost a far pair its relative accuracy.)
-        __shared__ double fmom[TILE][NMOM];
-        const double sx2 = D.sx * D.sx, st = D.st, st2 = D.st * D.st;
-        // raw units -> FP32C scaled units
-        const double scale[NMOM] = {1.0, sx2, st2, sx2 * sx2, st2 * st2, 1.0, st, st2, sx2, sx2 * sx2};
+        __shared__ double fmom[TILE][NMOM];  // in the FP32C scaled units, as accumulate64 forms them
         const float *f = reinterpret_cast<const float *>(ws.src32);
         const float cbt = D.cbt, hh = D.hh;
         constexpr float KEEP = 80.0f;
@@ -256,7 +262,7 @@ __device__ __forceinline__ void finish_tile_fp32c(const Consts &c, const Inputs 
                 double v = a[k];
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0) fmom[owner][k] = v * scale[k];
+                if (lane == 0) fmom[owner][k] = v;
             }
         }
         __syncthreads();

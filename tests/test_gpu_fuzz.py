@@ -5,12 +5,12 @@ spread log-rates.  FP64 is held to 1e-10, FP32C and its band-skipping form to
 the stated FP32C bars; the band form must also equal FP32C bit for bit, and the
 space-time form meets the FP32C bars.
 
-One regime is looser by nature: an intensity below ~1e-290 means its FP64
-pair terms are subnormal (exp of about -709), with short mantissas on both
-sides; the row's Hessian term is a difference s2 - q1^2 that cancels by
-orders of magnitude, so the two summation orders then differ around 1e-7
-(seen on the tau_x entry).  There the Hessian diagonal's bar is 1e-6; the
-log-likelihood and gradient keep 1e-10."""
+Seed 32 has two events whose intensity is about 7e-303 at tau_x = 6e-4: an
+extended-precision (60-digit) evaluation of those rows' Hessian terms agrees
+with the oracle to 2e-13, so the oracle holds there; the GPU's FP64 path once
+took its moments in raw units (G d^4 near 1e-315, deep in FP64's subnormal
+range) and was off by 1e-7 on the tau_x entry.  Its moments are now in the
+kernels' scaled units and every output is held to 1e-10, that case included."""
 import math
 
 import numpy as np
@@ -71,10 +71,9 @@ def test_random_problem(seed):
     if not np.isfinite(ref["loglik"]):
         pytest.skip("an event with zero intensity (the status test covers it)")
     ll, g, h = gpu(x, y, t, r, params, "fp64")
-    subnormal_rows = ref["lam"].min() < 1e-290
     assert rel(ll, ref["loglik"]) <= FP64_TOL
     assert scaled_err(g, ref["grad"]) <= FP64_TOL
-    assert scaled_err(h, ref["hdiag"]) <= (1e-6 if subnormal_rows else FP64_TOL)
+    assert scaled_err(h, ref["hdiag"]) <= FP64_TOL, (scaled_err(h, ref["hdiag"]), ref["lam"].min())
     ll, g, h = gpu(x, y, t, r, params, "fp32c")
     assert rel(ll, ref["loglik"]) <= FP32C_LL_TOL, (ll, ref["loglik"], params)
     assert norm_rel(g, ref["grad"]) <= FP32C_GNORM_TOL, (norm_rel(g, ref["grad"]), params)
