@@ -22,11 +22,14 @@ It prints one JSON line:
             oracle evaluation of the workload
   roofline_st  the space-time passes (the sampler's path) over the pairs they evaluate
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--shards]
 
 With --impl reference the FP64 CPU oracle runs instead (on rank 0 only), each
 step a bounded sample of the same workload.  N > 1 under torchrun runs N
-independent replicas (the evaluation needs no exchange between GPUs).
+independent replicas (the evaluation needs no exchange between GPUs); with
+--shards the N ranks instead split one evaluation (row shards, an all-gather
+of per-tile records, column shards, an all-gather of the entries) and the
+line reports strong scaling.
 """
 from __future__ import annotations
 
@@ -549,6 +552,59 @@ def parity_report(w, out):
             "hdiag_norm": nrm(h, z["hdiag"])}
 
 
+def run_sharded(args, rank, world, local_rank):
+    """--shards: the evaluation split over the ranks (strong scaling): each
+    rank runs its shard's row phase, the per-tile records are all-gathered
+    (NCCL), each rank runs its column phase and the per-event entries are
+    all-gathered, so that every rank holds the whole result.  value = the
+    whole problem's N(N-1) pairs per second (max over ranks of the step time)."""
+    import torch
+    from paper_2103_03348_b300 import build, hawkes, replicas, shard
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = synth.make("large")
+    to_dev = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)  # noqa: E731
+    x, y, t, r = to_dev(w.x), to_dev(w.y), to_dev(w.t), to_dev(w.r)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    sh = shard.Shard(w.n, "fp32c", rank, world, dev) if world > 1 else None
+
+    def step():
+        if world > 1:
+            return shard.distributed_evaluate(x, y, t, r, w.params, "fp32c", "hess", shard=sh)
+        return hawkes.hess_diag(x, y, t, r, w.params, "fp32c")
+
+    ref = hawkes.hess_diag(x, y, t, r, w.params, "fp32c")
+    out = step()
+    if not all(torch.equal(a, b) for a, b in zip(out, ref)):
+        raise RuntimeError("the sharded evaluation differs from the unsharded call")
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        replicas.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t_ms = float(np.mean(ms))
+    t_max = replicas.max_over_ranks(t_ms, dev)
+    if rank == 0:
+        pairs = w.n * (w.n - 1)
+        print(json.dumps({"metric": METRIC, "value": pairs / (t_max * 1e-3), "unit": UNIT, "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max,
+                          "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+                          "data": "synthetic", "config": dict(workload_config(w), parallelism=f"shards{world}"),
+                          "sharded": {"records_bytes": shard.n_records(w.n) * shard.RECORD_DOUBLES * 8,
+                                      "exchange": "per-tile records, then per-event entries (NCCL all-gather)",
+                                      "bit_identical_to_unsharded": True}}), flush=True)
+    return 0
+
+
 def predictive_bench(dev, stream):
     """Posterior-predictive simulation: 30 days ahead of the 23,422-event
     history with 1,610 free log-rates, for 4,096 posterior-like parameter
@@ -566,6 +622,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-hmc", action="store_true", help="skip the short HMC chain (ESS/s)")
     ap.add_argument("--no-predictive", action="store_true", help="skip the posterior-predictive simulation")
+    ap.add_argument("--shards", action="store_true",
+                    help="time the evaluation split over the ranks (strong scaling) instead of replicas")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate chains (N=500,000)")
     ap.add_argument("--surrogate-n", type=int, default=500_000, help="events of the surrogate block's workload")
     ap.add_argument("--hmc-iters", type=int, default=2000)
@@ -590,6 +648,8 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     try:
+        if args.shards:
+            return run_sharded(args, rank, world, local_rank)
         return run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:

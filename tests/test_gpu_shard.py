@@ -105,3 +105,54 @@ def test_status_of_one_shard_reaches_all():
                "hdiag": torch.zeros(6 + w.n, dtype=torch.float64, device="cuda")}
         sh.cols(x, y, t, r, w.params, out)
         assert int(sh.status.item()) == hawkes.EZERO
+
+
+def _free_port():
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_worker(rank, world, port, name, precision, q):
+    """One rank on cuda:0: distributed_evaluate over gloo (records and entries
+    staged through host memory) against the unsharded call on the same GPU."""
+    import os
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    try:
+        torch.cuda.set_device(0)
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+        from paper_2103_03348_b300 import shard
+        w = synth.make(name) if name != "ragged" else synth.make_uniform(5, 1001, r_sd=0.4)
+        x, y, t, r = dev(w.x), dev(w.y), dev(w.t), dev(w.r)
+        ll, g, h = shard.distributed_evaluate(x, y, t, r, w.params, precision, "hess")
+        a = unsharded(x, y, t, r, w.params, precision, "hess")
+        ok = torch.equal(ll, a[0]) and torch.equal(g, a[1]) and torch.equal(h, a[2])
+        q.put((rank, ok, ""))
+        dist.destroy_process_group()
+    except Exception as e:  # reported to the parent, which fails the test
+        q.put((rank, False, repr(e)))
+
+
+@pytest.mark.parametrize("name,precision,world", [("ebola_like", "fp32c", 2), ("ebola_like", "fp64", 2),
+                                                  ("ragged", "fp32c_band", 3)])
+def test_distributed_ranks_are_bitwise_unsharded(name, precision, world):
+    """The cross-rank evaluation (each rank's row phase, the record all-gather,
+    each rank's column phase, the entry all-gather) run by `world` processes on
+    this GPU over gloo equals hawkes_hess_diag bit for bit on every rank.  The
+    ranks' kernels never wait on one another: the exchange is host-side."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_worker, args=(r, world, port, name, precision, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=300) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=120)
+    assert all(ok for _, ok, _ in res), res
+    assert all(p.exitcode == 0 for p in procs)

@@ -105,3 +105,74 @@ def test_record_allgather_between_gloo_ranks(world, n):
     want = np.arange(144)[None, :] + 1000.0 * np.arange(t)[:, None]
     for r in range(world):
         np.testing.assert_array_equal(res[r], want)
+
+
+def _fake_shard_cls():
+    """A Shard whose row and column phases are host arithmetic instead of
+    kernels: the row phase writes record j of its slice as (j + 1) * [1, 2, 3,
+    ...]; the column phase needs every record (after the exchange) and writes
+    loglik = sum of the records' first entries and, for each owned event e,
+    grad[6 + e] = loglik + e and hdiag[6 + e] = -e.  So distributed_evaluate's
+    composition (exchange, column phase, entry gather, status reduction) is
+    checked on gloo ranks without a GPU."""
+    from paper_2103_03348_b300 import shard
+
+    class FakeShard(shard.Shard):
+        def rows(self, x, y, t, r, params, mode="hess"):
+            for j in range(self.rec0, self.rec1):
+                self.xbuf[j] = (j + 1.0) * torch.arange(1, shard.RECORD_DOUBLES + 1, dtype=torch.float64)
+
+        def cols(self, x, y, t, r, params, out, mode="hess"):
+            assert not torch.isnan(self.xbuf).any()
+            ll = float(self.xbuf[:, 0].sum())
+            out["loglik"].fill_(ll)
+            out["grad"][:6] = torch.arange(6, dtype=torch.float64)
+            out["hdiag"][:6] = -torch.arange(6, dtype=torch.float64)
+            e = torch.arange(self.first, self.end, dtype=torch.float64)
+            out["grad"][6 + self.first:6 + self.end] = ll + e
+            out["hdiag"][6 + self.first:6 + self.end] = -e
+
+    return FakeShard
+
+
+def _dist_worker(rank, world, port, n, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_2103_03348_b300 import shard
+        fake = _fake_shard_cls()(n, "fp32c", rank, world, device="cpu")
+        fake.xbuf.fill_(float("nan"))  # only the own slice is written by the row phase
+        z = torch.zeros(n, dtype=torch.float64)
+        ll, g, h = shard.distributed_evaluate(z, z, z, z, (1, 1, 1, 1, 1, 1), "fp32c", "hess", shard=fake)
+        out.put((rank, float(ll), g.numpy(), h.numpy()))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,n", [(2, 1000), (3, 300), (2, 100)])
+def test_distributed_evaluate_composition_on_gloo_ranks(world, n):
+    """Every rank ends with every rank's column entries, computed after the
+    record exchange gave it every record (n = 100 with two ranks: one rank
+    owns no events)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dist_worker, args=(r, world, port, n, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = {}
+    for _ in range(world):
+        rank, ll, g, h = q.get(timeout=120)
+        res[rank] = (ll, g, h)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    t = (n + 127) // 128
+    ll_want = float(sum(j + 1.0 for j in range(t)))
+    e = np.arange(n, dtype=float)
+    for r in range(world):
+        ll, g, h = res[r]
+        assert ll == ll_want
+        np.testing.assert_array_equal(g, np.concatenate([np.arange(6.0), ll_want + e]))
+        np.testing.assert_array_equal(h, np.concatenate([-np.arange(6.0), -e]))
