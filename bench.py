@@ -60,8 +60,10 @@ LANES, SM_MAX_MHZ_DEFAULT = 128, 2032.0
 
 # Algorithmic FP32 lane-slots per pair (see the design notes): background terms
 # for every ordered pair, excitation and column terms for causal pairs inside
-# the exact FP32 underflow band.
-ROW_BG_SLOTS, ROW_EXC_SLOTS, COL_SLOTS = 14, 7, 8
+# the exact FP32 underflow band.  A column pair costs 7: two differences, one
+# add (g^ + r^) and two FMAs for the exponent d'^2 - g^ - r^ in the
+# excitation's scaled coordinates, and the two accumulations.
+ROW_BG_SLOTS, ROW_EXC_SLOTS, COL_SLOTS = 14, 7, 7
 # A coarser count, also reported: every ordered pair charged the full
 # excitation and mask work (26 slots), and 10 per column pair.
 COARSE_ROW_SLOTS, COARSE_COL_SLOTS = 26, 10
