@@ -167,7 +167,7 @@ def test_tree_mass_chain_on_hawkes_posterior():
     assert np.all(np.isfinite(ch.logpost)) and np.all(np.isfinite(ch.draws))
     assert 0.4 < ch.accept.mean() <= 1.0
     with pytest.raises(ValueError):
-        hmc.sample(post, q0, n_iter=1, n_warmup=0, mass="dense")
+        hmc.sample(post, q0, n_iter=1, n_warmup=0, mass="full")
 
 
 # ---------------------------------------------------------------------------
