@@ -21,7 +21,7 @@ namespace hk {
 constexpr int GPT = TILE / GROUP;  // groups per tile
 
 template <int MODE>
-__global__ void __launch_bounds__(GROUP, MODE == MODE_HESS ? 16 : 20) row32_st_kernel(Consts c, Inputs in, Workspace ws) {
+__global__ void __launch_bounds__(GROUP, 20) row32_st_kernel(Consts c, Inputs in, Workspace ws) {
     pdl_wait();
     const Derived &D = *c.d;
     const int tg = c.t0 * GPT + blockIdx.x;  // target group
