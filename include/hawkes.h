@@ -503,13 +503,26 @@ size_t hawkes_mlp_workspace_size(int64_t batch);
 /* y[batch x 6] = MLP(x[batch x 6]). */
 int hawkes_mlp_forward(const void *w_bf16, const float *x, int64_t batch, float *y, void *stream);
 /* Mean squared error over batch x 6 outputs and its gradient w.r.t. every
- * weight (FP32, summed over the batch's 32-sample blocks in a fixed order). */
+ * weight (FP32, summed over the batch's 8-sample blocks in a fixed order). */
 int hawkes_mlp_loss_grad(const void *w_bf16, const float *x, const float *target, int64_t batch, void *ws,
                          size_t ws_bytes, float *grad, float *loss, void *stream);
 /* One Adam step (bias-corrected, step >= 1) on the FP32 master weights and
  * moments m, v; refreshes the BF16 copy (round to nearest even). */
 int hawkes_mlp_adam(float *w_master, void *w_bf16, float *m, float *v, const float *grad, float lr, float beta1,
                     float beta2, float eps, int step, void *stream);
+/* Adam's bias corrections for steps 1..steps, as hawkes_mlp_adam forms them:
+ * table[2 (s - 1)] = 1 - beta1^s, table[2 (s - 1) + 1] = 1 - beta2^s (HOST
+ * float[2 steps]).  Host only. */
+int hawkes_mlp_adam_table(float beta1, float beta2, int steps, float *table);
+/* hawkes_mlp_adam with the step read from DEVICE memory, so that a captured
+ * training step can be replayed: step s = *step + 1, the learning rate *lr
+ * and the bias corrections table[2 (s - 1)], [+1] (DEVICE float[2 max_steps],
+ * from hawkes_mlp_adam_table) are read on the device, and *step is advanced
+ * by one after the update.  A step beyond max_steps leaves the weights alone.
+ * Equal bit for bit to hawkes_mlp_adam at the same step and learning rate. */
+int hawkes_mlp_adam_device(float *w_master, void *w_bf16, float *m, float *v, const float *grad, const float *lr,
+                           const float *table, int max_steps, int *step, float beta1, float beta2, float eps,
+                           void *stream);
 /* Surrogate gradient at one sampler state q[0..5] and, when p is not NULL, the
  * leapfrog momentum update p[0..5] += a * g, with
  *   g = mean_g + A (q - mean_q) + sd_g * MLP((q - mean_q) / sd_q):

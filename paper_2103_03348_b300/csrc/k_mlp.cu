@@ -21,7 +21,7 @@ namespace hk {
 constexpr int MI = 6, MH = 128, MO = 6;
 constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + MH * MI, OFF_W2 = OFF_B1 + MH, OFF_B2 = OFF_W2 + MH * MH;
 constexpr int OFF_W3 = OFF_B2 + MH, OFF_B3 = OFF_W3 + MO * MH, PARAM_COUNT = OFF_B3 + MO;
-constexpr int SB = 32;          // samples per block
+constexpr int SB = 8;           // samples per block: 32 blocks for a minibatch of 256
 constexpr int W2_STRIDE = MH + 1;  // padded rows: row and column walks are bank-conflict free
 
 constexpr size_t mlp_smem_bytes() {
@@ -199,6 +199,12 @@ __global__ void mlp_reduce_kernel(int nblocks, int64_t batch, const float *__res
     }
 }
 
+// Adam's bias corrections for step s (1-based), as hawkes_mlp_adam forms them.
+static inline void adam_bias_corrections(float b1, float b2, int step, float *bc1, float *bc2) {
+    *bc1 = 1.0f - powf(b1, (float)step);
+    *bc2 = 1.0f - powf(b2, (float)step);
+}
+
 // Adam on the FP32 master weights; the BF16 working copy is rounded to nearest even.
 __global__ void mlp_adam_kernel(int64_t count, float *__restrict__ wm, __nv_bfloat16 *__restrict__ wb,
                                 float *__restrict__ m, float *__restrict__ v, const float *__restrict__ g, float lr,
@@ -214,6 +220,31 @@ __global__ void mlp_adam_kernel(int64_t count, float *__restrict__ wm, __nv_bflo
         wb[i] = __float2bfloat16_rn(w);
     }
 }
+
+// The same Adam step with its step number, learning rate and bias corrections
+// read from device memory (step = *step_dev + 1; table[2 (step - 1)], [+1]),
+// so that a captured training graph replays with a fresh step each time.  A
+// step beyond the table leaves the weights alone.
+__global__ void mlp_adam_dev_kernel(int64_t count, float *__restrict__ wm, __nv_bfloat16 *__restrict__ wb,
+                                    float *__restrict__ m, float *__restrict__ v, const float *__restrict__ g,
+                                    const float *__restrict__ lr_dev, const float *__restrict__ table, int max_steps,
+                                    const int *__restrict__ step_dev, float b1, float b2, float eps) {
+    const int s = *step_dev;
+    if (s < 0 || s >= max_steps) return;
+    const float lr = *lr_dev, bc1 = table[2 * s], bc2 = table[2 * s + 1];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float w = wm[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+        wm[i] = w;
+        wb[i] = __float2bfloat16_rn(w);
+    }
+}
+
+__global__ void step_advance_kernel(int *step) { *step += 1; }
 
 // Surrogate gradient at one state, fused with the leapfrog momentum update:
 //   z = (q - mu_q) / sd_q,  g = mu_g + A (q - mu_q) + sd_g * MLP(z),  p += a * g
@@ -381,9 +412,29 @@ int hawkes_mlp_loss_grad(const void *w_bf16, const float *x, const float *target
 int hawkes_mlp_adam(float *w_master, void *w_bf16, float *m, float *v, const float *grad, float lr, float beta1,
                     float beta2, float eps, int step, void *stream) {
     if (!w_master || !w_bf16 || !m || !v || !grad || step < 1 || !(lr > 0)) return HAWKES_EINVAL;
-    const float bc1 = 1.0f - powf(beta1, (float)step), bc2 = 1.0f - powf(beta2, (float)step);
+    float bc1, bc2;
+    hk::adam_bias_corrections(beta1, beta2, step, &bc1, &bc2);
     hk::mlp_adam_kernel<<<(hk::PARAM_COUNT + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
         hk::PARAM_COUNT, w_master, (__nv_bfloat16 *)w_bf16, m, v, grad, lr, beta1, beta2, eps, bc1, bc2);
+    return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
+}
+
+int hawkes_mlp_adam_table(float beta1, float beta2, int steps, float *table) {
+    if (steps < 1 || !table || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f))
+        return HAWKES_EINVAL;
+    for (int s = 1; s <= steps; ++s) hk::adam_bias_corrections(beta1, beta2, s, &table[2 * (s - 1)], &table[2 * s - 1]);
+    return HAWKES_OK;
+}
+
+int hawkes_mlp_adam_device(float *w_master, void *w_bf16, float *m, float *v, const float *grad, const float *lr,
+                           const float *table, int max_steps, int *step, float beta1, float beta2, float eps,
+                           void *stream) {
+    if (!w_master || !w_bf16 || !m || !v || !grad || !lr || !table || !step || max_steps < 1) return HAWKES_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    hk::mlp_adam_dev_kernel<<<(hk::PARAM_COUNT + 255) / 256, 256, 0, s>>>(
+        hk::PARAM_COUNT, w_master, (__nv_bfloat16 *)w_bf16, m, v, grad, lr, table, max_steps, step, beta1, beta2, eps);
+    if (cudaGetLastError() != cudaSuccess) return HAWKES_ECUDA;
+    hk::step_advance_kernel<<<1, 1, 0, s>>>(step);
     return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
 }
 

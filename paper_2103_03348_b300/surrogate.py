@@ -39,11 +39,14 @@ def _lib():
         L.hawkes_mlp_forward.argtypes = [vp, vp, i64, vp, vp]
         L.hawkes_mlp_loss_grad.argtypes = [vp, vp, vp, i64, vp, ctypes.c_size_t, vp, vp, vp]
         L.hawkes_mlp_adam.argtypes = [vp, vp, vp, vp, vp, f, f, f, f, ctypes.c_int, vp]
+        L.hawkes_mlp_adam_table.argtypes = [f, f, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]
+        L.hawkes_mlp_adam_device.argtypes = [vp, vp, vp, vp, vp, vp, vp, ctypes.c_int, vp, f, f, f, vp]
         L.hawkes_surrogate_momentum.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp, vp]
         L.hawkes_surrogate_trajectory.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_int, vp]
         L.hawkes_surrogate_trajectory_dense.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_int, vp]
         for fn in (L.hawkes_mlp_forward, L.hawkes_mlp_loss_grad, L.hawkes_mlp_adam, L.hawkes_surrogate_momentum,
-                   L.hawkes_surrogate_trajectory, L.hawkes_surrogate_trajectory_dense):
+                   L.hawkes_surrogate_trajectory, L.hawkes_surrogate_trajectory_dense, L.hawkes_mlp_adam_table,
+                   L.hawkes_mlp_adam_device):
             fn.restype = ctypes.c_int
         L._mlp_typed = True
     return L
@@ -96,29 +99,68 @@ class MLP:
         _check(_lib().hawkes_mlp_forward(_p(self.wb), _p(x), x.shape[0], _p(y), _stream(self.dev)))
         return y
 
-    def train(self, x, y, epochs=200, batch=256, lr=1e-3, seed=0):
-        """Minibatch Adam on the mean squared error; returns the per-epoch mean loss."""
+    def adam_table(self, first_step, steps, beta1=0.9, beta2=0.999):
+        """Device table of Adam's bias corrections for steps first_step .. first_step + steps - 1."""
+        host = (ctypes.c_float * (2 * (first_step + steps - 1)))()
+        _check(_lib().hawkes_mlp_adam_table(beta1, beta2, first_step + steps - 1, host))
+        t = torch.tensor(np.frombuffer(host, dtype=np.float32), device=self.dev)
+        return t[2 * (first_step - 1):].contiguous()
+
+    def train(self, x, y, epochs=200, batch=256, lr=1e-3, seed=0, use_graph=True):
+        """Minibatch Adam on the mean squared error (cosine-decayed learning rate);
+        returns the per-epoch mean loss.
+
+        Each minibatch step gathers its rows, runs the loss-gradient kernels and
+        a device-step Adam update (step, learning rate and bias corrections read
+        from device memory).  With use_graph the first epoch runs eagerly and the
+        epoch's steps are then captured once as a CUDA graph and replayed for the
+        other epochs (one launch per epoch instead of several per step); the
+        weights equal those of eager training bit for bit."""
         n = x.shape[0]
-        ws = torch.empty(int(_lib().hawkes_mlp_workspace_size(batch)), dtype=torch.uint8, device=self.dev)
+        L = _lib()
+        nb = max((n - batch) // batch + 1, 0) if n >= batch else 0
+        ws = torch.empty(int(L.hawkes_mlp_workspace_size(batch)), dtype=torch.uint8, device=self.dev)
         gen = torch.Generator(device=self.dev)
         gen.manual_seed(seed)
-        history = []
-        L = _lib()
+        perm = torch.empty(n, dtype=torch.int64, device=self.dev)
+        xb = torch.empty(batch, x.shape[1], dtype=x.dtype, device=self.dev)
+        yb = torch.empty(batch, y.shape[1], dtype=y.dtype, device=self.dev)
+        total_steps = epochs * nb
+        table = self.adam_table(self.step + 1, max(total_steps, 1))
+        step_dev = torch.zeros(1, dtype=torch.int32, device=self.dev)
+        lr_dev = torch.empty(1, dtype=torch.float32, device=self.dev)
+        tot = torch.zeros((), dtype=torch.float32, device=self.dev)
+
+        def epoch_body():
+            s = _stream(self.dev)
+            for b in range(nb):
+                idx = perm[b * batch:(b + 1) * batch]
+                torch.index_select(x, 0, idx, out=xb)
+                torch.index_select(y, 0, idx, out=yb)
+                _check(L.hawkes_mlp_loss_grad(_p(self.wb), _p(xb), _p(yb), batch, _p(ws), ctypes.c_size_t(ws.numel()),
+                                              _p(self.grad), _p(self.loss), s))
+                _check(L.hawkes_mlp_adam_device(_p(self.wm), _p(self.wb), _p(self.m), _p(self.v), _p(self.grad),
+                                                _p(lr_dev), _p(table), max(total_steps, 1), _p(step_dev), 0.9, 0.999,
+                                                1e-8, s))
+                tot.add_(self.loss)
+
+        history, graph = [], None
         for ep in range(epochs):
-            perm = torch.randperm(n, generator=gen, device=self.dev)
-            tot = torch.zeros((), dtype=torch.float32, device=self.dev)
-            nb = 0
+            torch.randperm(n, generator=gen, device=self.dev, out=perm)
             lr_ep = lr * 0.5 * (1.0 + math.cos(math.pi * ep / epochs))  # cosine decay
-            for s in range(0, n - batch + 1, batch):
-                idx = perm[s:s + batch]
-                xb, yb = x.index_select(0, idx), y.index_select(0, idx)
-                _check(L.hawkes_mlp_loss_grad(_p(self.wb), _p(xb), _p(yb), batch, _p(ws),
-                                              ctypes.c_size_t(ws.numel()), _p(self.grad), _p(self.loss),
-                                              _stream(self.dev)))
-                self.adam(max(lr_ep, 1e-5))
-                tot += self.loss
-                nb += 1
+            lr_dev.fill_(max(lr_ep, 1e-5))
+            tot.zero_()
+            if graph is not None:
+                graph.replay()
+            elif use_graph and ep > 0 and nb > 0:
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph):
+                    epoch_body()
+                graph.replay()  # capture records the kernels without running them
+            else:
+                epoch_body()
             history.append(float(tot.item()) / max(nb, 1))
+        self.step += total_steps
         return history
 
 

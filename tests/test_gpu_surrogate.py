@@ -75,6 +75,50 @@ def test_adam_step_vs_oracle():
     assert np.array_equal(mlp.wb.float().cpu().numpy(), mo.bf16_round(wm))
 
 
+def test_device_step_adam_equals_host_step_adam():
+    """hawkes_mlp_adam_device (step, learning rate and bias corrections read from
+    device memory) equals hawkes_mlp_adam bit for bit, and advances the step."""
+    S = mod()
+    w32, _, _ = weights(6)
+    rng = np.random.default_rng(15)
+    g = torch.tensor(rng.normal(0, 1e-2, mo.PARAM_COUNT).astype(np.float32), device="cuda")
+    m0 = torch.tensor(rng.normal(0, 1e-3, mo.PARAM_COUNT).astype(np.float32), device="cuda")
+    v0 = torch.tensor(rng.uniform(0, 1e-4, mo.PARAM_COUNT).astype(np.float32), device="cuda")
+    a, b = S.MLP("cuda"), S.MLP("cuda")
+    for net in (a, b):
+        net.wm = torch.tensor(w32, device="cuda")
+        net.m, net.v, net.grad = m0.clone(), v0.clone(), g.clone()
+    a.step = 11
+    a.adam(3e-4)  # step 12
+    L = S._lib()
+    table = b.adam_table(1, 40)
+    step = torch.tensor([11], dtype=torch.int32, device="cuda")
+    lr = torch.tensor([3e-4], dtype=torch.float32, device="cuda")
+    p = lambda t: __import__("ctypes").c_void_p(t.data_ptr())  # noqa: E731
+    assert L.hawkes_mlp_adam_device(p(b.wm), p(b.wb), p(b.m), p(b.v), p(b.grad), p(lr), p(table), 40, p(step), 0.9,
+                                    0.999, 1e-8, S._stream(torch.device("cuda"))) == 0
+    assert int(step.item()) == 12
+    for k in ("wm", "wb", "m", "v"):
+        assert torch.equal(getattr(a, k), getattr(b, k)), k
+
+
+def test_graph_captured_training_equals_eager_training():
+    """Training with each epoch's minibatch steps captured once as a CUDA graph
+    and replayed gives the eager training's weights, moments and losses bit for
+    bit (same seed, same permutations)."""
+    S = mod()
+    rng = np.random.default_rng(21)
+    x = torch.tensor(rng.normal(size=(1000, 6)).astype(np.float32), device="cuda")
+    y = torch.tensor(rng.normal(size=(1000, 6)).astype(np.float32), device="cuda")
+    a, b = S.MLP("cuda", seed=3), S.MLP("cuda", seed=3)
+    ha = a.train(x, y, epochs=6, batch=128, lr=2e-3, seed=5, use_graph=False)
+    hb = b.train(x, y, epochs=6, batch=128, lr=2e-3, seed=5, use_graph=True)
+    assert ha == hb and ha[-1] < ha[0]
+    assert a.step == b.step == 6 * 7
+    for k in ("wm", "wb", "m", "v"):
+        assert torch.equal(getattr(a, k), getattr(b, k)), k
+
+
 def test_surrogate_gradient_kernel_vs_oracle():
     S = mod()
     _, wb, w64 = weights(3)
