@@ -14,7 +14,7 @@ namespace hk {
 template <int MODE, bool MASK>
 __device__ __forceinline__ void col_tile(const float4 *sAB, const int *sG, int npairs, float2 xm, float2 ym,
                                          float2 nrm, int m, float2 &c1, float2 &c2) {
-#pragma unroll 4
+#pragma unroll 8
     for (int p = 0; p < npairs; ++p) {
         const float4 A = sAB[2 * p], B = sAB[2 * p + 1];  // (-x', -y') and (-t~, -g^) of targets 2p, 2p+1
         const float2 dx = add2(xm, make_float2(A.x, A.y));
