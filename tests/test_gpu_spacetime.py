@@ -140,3 +140,34 @@ def test_shards_refuse_spacetime():
     with pytest.raises(Exception):
         shard.evaluate(dev(w.x), dev(w.y), dev(w.t), dev(w.r), w.params, "fp32c_st", 2, "hess")
     assert h.workspace_size(w.n, "fp32c_st") > h.workspace_size(w.n, "fp32c")
+
+
+def test_live_pair_counts():
+    """hawkes_st_live_pairs (the roofline count of the space-time passes): with
+    bandwidths as wide as the domain nothing is pruned and the row pass's
+    background count is every ordered pair (self pairs included, padding
+    excluded), n^2; its excitation and column counts cover at least the causal
+    pairs; with narrow bandwidths on a wide domain every count shrinks (the
+    background's by more than 5x)."""
+    from paper_2103_03348_b300 import build, hawkes, synth
+    build.build()
+    n = 5000
+    wide = synth.make_uniform(3, n, box=10.0, t_max=10.0, r_sd=0.3, params=(0.5, 100.0, 1e4, 0.3, 1e-3, 100.0))
+    narrow = synth.make_uniform(3, n, box=2000.0, t_max=1e4, r_sd=0.3, params=(0.5, 2.0, 1.0, 0.3, 10.0, 2.0))
+    counts = {}
+    for name, w in (("wide", wide), ("narrow", narrow)):
+        d = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")  # noqa: E731
+        ws = torch.empty(hawkes.workspace_size(n, "fp32c_st"), dtype=torch.uint8, device="cuda")
+        hawkes._call("hess", d(w.x), d(w.y), d(w.t), d(w.r), w.params, "fp32c_st", workspace=ws, check=False)
+        counts[name] = hawkes.st_live_pairs(n, ws)
+    c = counts["wide"]
+    assert c["row_background_pairs"] == n * n
+    assert n * (n - 1) // 2 <= c["row_excitation_pairs"] <= n * n
+    assert n * (n - 1) // 2 <= c["column_pairs"] <= n * n
+    c2 = counts["narrow"]
+    # the background prunes by space and time; the excitation and column bounds compare a
+    # group's latest source with its earliest target, and a group spans its slab's time range,
+    # so inside a slab they prune by space alone
+    assert 0 < c2["row_background_pairs"] < c["row_background_pairs"] // 5
+    assert 0 < c2["row_excitation_pairs"] < c["row_excitation_pairs"]
+    assert 0 <= c2["column_pairs"] < c["column_pairs"]
