@@ -66,8 +66,21 @@ def log_posterior(x, y, t, r_base, seq, prec, prior, q, want_hess=True, trend=No
     return logpost, g, h
 
 
+def velocity(p, minv):
+    """M^-1 p for a diagonal inverse mass (a vector) or a dense one (a matrix)."""
+    minv = np.asarray(minv, float)
+    return minv @ p if minv.ndim == 2 else minv * p
+
+
+def kinetic(p, minv):
+    """The kinetic energy 1/2 p^T M^-1 p (diagonal or dense inverse mass)."""
+    p = np.asarray(p, float)
+    return 0.5 * float(p @ velocity(p, minv))
+
+
 def leapfrog(q, p, eps, n_steps, minv, grad_fn):
-    """Leapfrog integration of Hamilton's equations with diagonal inverse mass.
+    """Leapfrog integration of Hamilton's equations, H = -log pi(q) + 1/2 p^T M^-1 p,
+    with a diagonal inverse mass (minv a vector) or a dense one (minv a matrix).
 
     grad_fn(q) -> (log pi, grad).  Returns (q, p, log pi, grad) at the end.
     """
@@ -76,7 +89,7 @@ def leapfrog(q, p, eps, n_steps, minv, grad_fn):
     lp, g = grad_fn(q)
     p = p + 0.5 * eps * g
     for step in range(n_steps):
-        q = q + eps * minv * p
+        q = q + eps * velocity(p, minv)
         lp, g = grad_fn(q)
         p = p + (eps if step < n_steps - 1 else 0.5 * eps) * g
     return q, p, lp, g

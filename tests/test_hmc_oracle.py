@@ -77,6 +77,39 @@ def test_leapfrog_harmonic_oscillator_closed_form():
     assert np.allclose([q[0], p[0]], ref, rtol=1e-13, atol=1e-14)
 
 
+def test_dense_mass_leapfrog_whitened_closed_form():
+    """With a dense mass equal to the target's precision P = L L^T, the whitened
+    coordinates u = L^T q, v = L^-1 p turn every direction into the unit
+    oscillator, so the dense-mass leapfrog is the closed-form map of the
+    one-dimensional test applied in those coordinates."""
+    rng = np.random.default_rng(3)
+    X = rng.normal(size=(6, 6))
+    P = X @ X.T + 0.5 * np.eye(6)
+    L = np.linalg.cholesky(P)
+    eps, steps = 0.27, 13
+    A = np.array([[1 - eps ** 2 / 2, eps], [-eps * (1 - eps ** 2 / 4), 1 - eps ** 2 / 2]])
+    An = np.linalg.matrix_power(A, steps)
+    q0, p0 = rng.normal(size=6), rng.normal(size=6)
+    q, p, _, _ = hmc_oracle.leapfrog(q0, p0, eps, steps, np.linalg.inv(P), lambda x: (-0.5 * x @ P @ x, -P @ x))
+    u0, v0 = L.T @ q0, np.linalg.solve(L, p0)
+    u1, v1 = An[0, 0] * u0 + An[0, 1] * v0, An[1, 0] * u0 + An[1, 1] * v0
+    assert np.allclose(L.T @ q, u1, rtol=1e-12, atol=1e-12)
+    assert np.allclose(np.linalg.solve(L, p), v1, rtol=1e-12, atol=1e-12)
+    # the kinetic energy in whitened coordinates is 1/2 |v|^2
+    assert abs(hmc_oracle.kinetic(p0, np.linalg.inv(P)) - 0.5 * v0 @ v0) <= 1e-12 * (v0 @ v0)
+
+
+def test_dense_leapfrog_with_a_diagonal_matrix_is_the_diagonal_leapfrog():
+    rng = np.random.default_rng(4)
+    prec = np.diag(rng.uniform(0.5, 4.0, 5))
+    minv = rng.uniform(0.3, 2.0, 5)
+    q0, p0 = rng.normal(size=5), rng.normal(size=5)
+    gf = lambda x: (-0.5 * x @ prec @ x, -prec @ x)  # noqa: E731
+    a = hmc_oracle.leapfrog(q0, p0, 0.1, 9, minv, gf)
+    b = hmc_oracle.leapfrog(q0, p0, 0.1, 9, np.diag(minv), gf)
+    assert np.allclose(a[0], b[0], rtol=1e-14, atol=1e-15) and np.allclose(a[1], b[1], rtol=1e-14, atol=1e-15)
+
+
 def test_leapfrog_reversible_and_second_order():
     rng = np.random.default_rng(0)
     prec = np.diag(rng.uniform(0.5, 4.0, 5))
