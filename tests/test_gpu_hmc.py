@@ -70,6 +70,44 @@ def test_leapfrog_trajectory_parity():
     assert abs(ev["logpost"].item() - lp_ref) <= 1e-9 * abs(lp_ref)
 
 
+def test_dense_mass_leapfrog_trajectory_parity():
+    """A 20-step trajectory with a dense mass over the 46 coordinates of a small
+    Hawkes posterior (FP64 likelihood) against the oracle's dense-mass leapfrog."""
+    w, prec = problem()
+    post, hmc = make_post(w, prec, "fp64")
+    prior = hmc.prior_km_days().as_tuple()
+    rng = np.random.default_rng(2)
+    q0 = np.concatenate([np.log(w.params), w.r[w.sequenced]])
+    dim = len(q0)
+    _, _, h0 = hmc_oracle.log_posterior(w.x, w.y, w.t, w.r, w.sequenced, prec, prior, q0)
+    s = np.sqrt(np.maximum(-h0, 1e-2))
+    C = rng.normal(size=(dim, dim)) * 0.1
+    M = np.outer(s, s) * (np.eye(dim) + 0.5 * (C + C.T) @ (C + C.T).T / dim)  # SPD, dense
+    op = hmc.DenseMassOp(dim, "cuda")
+    op.set(M)
+    minv = np.linalg.inv(op.M)
+    p0 = np.linalg.cholesky(op.M) @ rng.normal(size=dim)
+    eps, steps = 0.05, 20
+
+    def gf(q):
+        lp, g, _ = hmc_oracle.log_posterior(w.x, w.y, w.t, w.r, w.sequenced, prec, prior, q, want_hess=False)
+        return lp, g
+
+    q_ref, p_ref, lp_ref, _ = hmc_oracle.leapfrog(q0, p0, eps, steps, minv, gf)
+    d = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")  # noqa: E731
+    q, p = d(q0), d(p0)
+    g0 = post.evaluate(q)["grad"].clone()
+    scratch = {"logpost": torch.empty((), dtype=torch.float64, device="cuda"),
+               "grad": torch.empty(dim, dtype=torch.float64, device="cuda")}
+    ev = hmc.leapfrog(post, q, p, g0, eps, steps, op, scratch)
+    assert np.max(np.abs(q.cpu().numpy() - q_ref)) <= 1e-9
+    assert np.max(np.abs(p.cpu().numpy() - p_ref) / np.maximum(np.abs(p_ref), 1.0)) <= 1e-8
+    assert abs(ev["logpost"].item() - lp_ref) <= 1e-9 * abs(lp_ref)
+    k = torch.empty((), dtype=torch.float64, device="cuda")
+    hmc.kinetic(p, op, k)
+    assert abs(k.item() - hmc_oracle.kinetic(p_ref, minv)) <= 1e-9 * hmc_oracle.kinetic(p_ref, minv)
+
+
 class GaussPost:
     """A Gaussian target with known moments, in the Posterior interface."""
 
