@@ -317,8 +317,9 @@ int hawkes_posterior_add_trend(int64_t m, int k, const int *seq_idx, const doubl
 int hawkes_hmc_momentum(int64_t k, double *p, const double *g, double a, void *stream);
 int hawkes_hmc_position(int64_t k, double *q, const double *p, const double *minv, double eps, void *stream);
 int hawkes_hmc_kinetic(int64_t k, const double *p, const double *minv, double *out, void *stream);
-/* The same with a dense mass matrix over k <= 64 coordinates (a posterior over
- * the six globals alone, whose correlations a diagonal mass cannot follow):
+/* The same pieces with a dense mass matrix (Section 2.3.2's preconditioned HMC,
+ * with M dense) over k <= 64 coordinates (a posterior over the six globals
+ * alone, whose correlations a diagonal mass cannot follow):
  * minv is M^-1 (DEVICE double[k*k], row-major).
  *   hawkes_hmc_position_dense: q += eps * M^-1 p
  *   hawkes_hmc_kinetic_dense:  *out = 1/2 p^T M^-1 p
