@@ -1,5 +1,6 @@
 """FP64 NumPy oracle of the HMC pieces (Section 2.3): the log posterior in
-sampler coordinates, one leapfrog trajectory, and the effective sample size.
+sampler coordinates, one leapfrog trajectory, the Metropolis accept step that
+closes it, and the effective sample size.
 
 TEST INFRASTRUCTURE: used only by the tests and the bench's CPU legs.
 
@@ -93,6 +94,29 @@ def leapfrog(q, p, eps, n_steps, minv, grad_fn):
         lp, g = grad_fn(q)
         p = p + (eps if step < n_steps - 1 else 0.5 * eps) * g
     return q, p, lp, g
+
+
+def accept_probability(lp0, k0, lp1, k1, ok=True):
+    """Metropolis acceptance of an HMC proposal (Section 2.3: the trajectory's end
+    point is a proposal corrected by an accept/reject step).  With the energy
+    H = -log pi(q) + K(p), the proposal is accepted with probability
+    min(1, exp(H0 - H1)).  A proposal whose log posterior or energy is not finite,
+    or whose likelihood evaluation reported an error (ok false), has probability 0."""
+    h0 = -float(lp0) + float(k0)
+    h1 = -float(lp1) + float(k1)
+    if not ok or not np.isfinite(lp1) or not np.isfinite(h1):
+        return 0.0
+    return min(1.0, float(np.exp(min(0.0, h0 - h1))))
+
+
+def metropolis_step(q0, lp0, g0, k0, q1, lp1, g1, k1, u, ok=True):
+    """One accept/reject decision with the uniform draw u in [0, 1): the proposal
+    (q1, lp1, g1) replaces the current state iff u < a.  Returns
+    (q, lp, g, accepted, a)."""
+    a = accept_probability(lp0, k0, lp1, k1, ok)
+    if u < a:
+        return np.array(q1, float), float(lp1), np.array(g1, float), True, a
+    return np.array(q0, float), float(lp0), np.array(g0, float), False, a
 
 
 def ess_geyer(x):

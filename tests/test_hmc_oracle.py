@@ -200,3 +200,51 @@ def test_log_posterior_with_trend_finite_differences():
     assert abs(lpz - (lp0 - 0.5 * beta @ beta / bv)) <= 1e-12 * abs(lp0)
     np.testing.assert_allclose(gz[:6 + m], g0, rtol=1e-13, atol=1e-13)
     np.testing.assert_allclose(gz[6 + m:], -beta / bv, rtol=1e-13)
+
+
+def test_accept_probability_closed_forms():
+    acc = hmc_oracle.accept_probability
+    assert acc(-3.0, 1.0, -3.0, 1.0) == 1.0                       # energy conserved
+    assert abs(acc(0.0, 0.0, -math.log(4.0), 0.0) - 0.25) < 1e-15  # H1 - H0 = log 4
+    assert abs(acc(0.0, 0.5, 0.0, 0.5 + math.log(2.0)) - 0.5) < 1e-15  # the kinetic side enters with H
+    assert acc(0.0, 2.0, 0.0, 0.0) == 1.0                          # energy dropped: always accepted
+    assert acc(0.0, 0.0, 5.0, 0.0) == 1.0                          # higher log posterior, same kinetic
+    for lp1, k1, ok in [(-math.inf, 0.0, True), (math.nan, 0.0, True), (0.0, math.inf, True),
+                        (0.0, math.nan, True), (0.0, 0.0, False)]:
+        assert acc(0.0, 0.0, lp1, k1, ok) == 0.0
+
+
+def test_accept_probability_keeps_a_discrete_target_in_detailed_balance():
+    # Metropolis with a symmetric proposal: T[i, j] = Q[i, j] a(i -> j) off the diagonal.
+    # Detailed balance pi_i T_ij = pi_j T_ji fixes the sign of every term of the energy;
+    # a swapped sign or a dropped kinetic term breaks it.
+    rng = np.random.default_rng(5)
+    pi = rng.uniform(0.1, 1.0, 5)
+    pi /= pi.sum()
+    k = rng.uniform(0.0, 2.0, 5)  # a kinetic energy per state, with pi_i proportional to exp(lp_i - k_i)
+    lp = np.log(pi) + k
+    Q = rng.uniform(0.0, 1.0, (5, 5))
+    Q = Q + Q.T
+    np.fill_diagonal(Q, 0.0)
+    Q /= Q.sum(axis=1).max()
+    T = np.zeros((5, 5))
+    for i in range(5):
+        for j in range(5):
+            if i != j:
+                T[i, j] = Q[i, j] * hmc_oracle.accept_probability(lp[i], k[i], lp[j], k[j])
+        T[i, i] = 1.0 - T[i].sum()
+    F = pi[:, None] * T
+    assert np.allclose(F, F.T, atol=1e-15)
+    assert np.allclose(pi @ T, pi, atol=1e-15)
+
+
+def test_metropolis_step_selects_by_strict_comparison():
+    q0, g0, q1, g1 = np.zeros(3), np.ones(3), np.full(3, 2.0), np.full(3, 3.0)
+    # a = 0.25 exactly
+    lp1 = -math.log(4.0)
+    q, lp, g, ok, a = hmc_oracle.metropolis_step(q0, 0.0, g0, 0.0, q1, lp1, g1, 0.0, u=0.2)
+    assert ok and a == 0.25 and np.array_equal(q, q1) and lp == lp1 and np.array_equal(g, g1)
+    q, lp, g, ok, a = hmc_oracle.metropolis_step(q0, 0.0, g0, 0.0, q1, lp1, g1, 0.0, u=0.25)
+    assert not ok and np.array_equal(q, q0) and lp == 0.0 and np.array_equal(g, g0)
+    q, lp, g, ok, a = hmc_oracle.metropolis_step(q0, 0.0, g0, 0.0, q1, math.nan, g1, 0.0, u=0.0)
+    assert not ok and a == 0.0 and np.array_equal(q, q0)
