@@ -214,23 +214,27 @@ def run_reference(args, rank, world):
 # our arm
 # ---------------------------------------------------------------------------
 def profile_traffic():
-    """DRAM traffic per row-pass launch from the committed ncu summary, if the
-    row kernel's source has not changed since it was captured."""
+    """DRAM traffic per row-pass launch from the committed ncu summary, if none of
+    the row kernel's sources has changed since it was captured (the summary lists
+    a digest per source file)."""
     path = os.path.join(ROOT, "profiles", "row32_large_N100000.txt")
-    src = os.path.join(ROOT, "paper_2103_03348_b300", "csrc", "k_row32.cu")
+    csrc = os.path.join(ROOT, "paper_2103_03348_b300", "csrc")
     try:
-        text = open(path).read()
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        vals = {}
-        for line in text.splitlines():
-            if ":" in line:
-                k, v = line.split(":", 1)
-                vals[k.strip()] = v.strip()
-        if vals.get("source_sha256_16") == digest and "dram_bytes_per_launch" in vals:
-            return float(vals["dram_bytes_per_launch"])
+        digests, traffic = {}, None
+        for line in open(path).read().splitlines():
+            if line.startswith("source_sha256_16 (") and ":" in line:
+                name = line[len("source_sha256_16 ("):line.index(")")]
+                digests[name] = line.split(":", 1)[1].strip()
+            elif line.startswith("dram_bytes_per_launch:"):
+                traffic = float(line.split(":", 1)[1])
+        if traffic is None or "k_row32.cu" not in digests:
+            return None
+        for name, want in digests.items():
+            if hashlib.sha256(open(os.path.join(csrc, name), "rb").read()).hexdigest()[:16] != want:
+                return None
+        return traffic
     except (OSError, ValueError):
-        pass
-    return None
+        return None
 
 
 def run_ours(args, rank, world, local_rank):

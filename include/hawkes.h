@@ -317,6 +317,25 @@ int hawkes_posterior_add_trend(int64_t m, int k, const int *seq_idx, const doubl
 int hawkes_hmc_momentum(int64_t k, double *p, const double *g, double a, void *stream);
 int hawkes_hmc_position(int64_t k, double *q, const double *p, const double *minv, double eps, void *stream);
 int hawkes_hmc_kinetic(int64_t k, const double *p, const double *minv, double *out, void *stream);
+
+/* The Metropolis accept/reject step that closes a trajectory (Section 2.3),
+ * on the device, so that a sampler needs no host round trip per iteration.
+ * With the energy H = -log pi(q) + K(p):
+ *   H0 = -*lp + *k0 (the current state), H1 = -*lp1 + *k1 (the proposal),
+ *   a = min(1, exp(H0 - H1)), or 0 when *lp1 or H1 is not finite or *status
+ *   is non-zero (status may be NULL: no error);
+ *   accepted iff *u < a (u: a uniform draw in [0, 1), a DEVICE double).
+ * When accepted, q[k], *lp and grad[k] (DEVICE, in/out: the current state,
+ * its log posterior and gradient) take the proposal's q1, *lp1 and grad1;
+ * otherwise they are left unchanged.  Optional record slots (NULL: none):
+ * rec_q[i] = the resulting state's q[keep[i]] for i < n_keep (keep: DEVICE
+ * int64 indices; an index outside [0, k) records NaN) and rec[3] = (the
+ * resulting log posterior, a, 1.0 if accepted else 0.0).  All pointers are
+ * DEVICE; the proposal buffers must not alias the state's.  HAWKES_EINVAL for
+ * k < 1, NULL required pointers, n_keep < 0 or aliasing. */
+int hawkes_hmc_accept(int64_t k, const double *u, const double *k0, const double *k1, const double *lp1,
+                      const double *grad1, const double *q1, const int *status, double *q, double *lp, double *grad,
+                      int64_t n_keep, const int64_t *keep, double *rec_q, double *rec, void *stream);
 /* The same pieces with a dense mass matrix (Section 2.3.2's preconditioned HMC,
  * with M dense) over k <= 64 coordinates (a posterior over the six globals
  * alone, whose correlations a diagonal mass cannot follow):

@@ -212,6 +212,53 @@ __global__ void __launch_bounds__(DENSE_MAX) kinetic_dense_kernel(int k, const d
     }
 }
 
+// Metropolis accept/reject closing one trajectory (Section 2.3): with the energy
+// H = -log pi(q) + K(p), the proposal is taken with probability
+// a = min(1, exp(H0 - H1)), and with probability 0 when its log posterior or
+// energy is not finite or its likelihood evaluation reported an error.  The
+// uniform draw u decides (accepted iff u < a).  One block: thread 0 takes the
+// decision, every thread copies its share of the state; the record slot gets
+// the kept coordinates of the resulting state, its log posterior, a and the
+// decision.
+constexpr int ACCEPT_THREADS = 256;
+
+__global__ void __launch_bounds__(ACCEPT_THREADS) accept_kernel(
+    int64_t k, const double *__restrict__ u, const double *__restrict__ k0, const double *__restrict__ k1,
+    const double *__restrict__ lp1, const double *__restrict__ grad1, const double *__restrict__ q1,
+    const int *__restrict__ status, double *__restrict__ q, double *__restrict__ lp, double *__restrict__ grad,
+    int64_t n_keep, const int64_t *__restrict__ keep, double *__restrict__ rec_q, double *__restrict__ rec) {
+    pdl_wait();
+    __shared__ int s_acc;
+    __shared__ double s_lp;
+    if (threadIdx.x == 0) {
+        const double h0 = -lp[0] + k0[0];
+        const double l1 = lp1[0], h1 = -l1 + k1[0];
+        const bool ok = (status == nullptr || status[0] == 0) && isfinite(l1) && isfinite(h1);
+        const double a = ok ? fmin(1.0, exp(fmin(0.0, h0 - h1))) : 0.0;
+        const bool acc = u[0] < a;
+        s_acc = acc ? 1 : 0;
+        s_lp = acc ? l1 : lp[0];
+        if (rec) { rec[0] = s_lp; rec[1] = a; rec[2] = acc ? 1.0 : 0.0; }
+    }
+    __syncthreads();
+    const bool acc = s_acc != 0;
+    // the record reads the proposal when accepted and the unchanged state when not,
+    // so it never reads an entry that this launch writes
+    if (rec_q) {
+        for (int64_t i = threadIdx.x; i < n_keep; i += ACCEPT_THREADS) {
+            const int64_t j = keep[i];
+            rec_q[i] = (j >= 0 && j < k) ? (acc ? q1[j] : q[j]) : nan("");
+        }
+    }
+    if (acc) {
+        for (int64_t j = threadIdx.x; j < k; j += ACCEPT_THREADS) {
+            q[j] = q1[j];
+            grad[j] = grad1[j];
+        }
+        if (threadIdx.x == 0) lp[0] = s_lp;
+    }
+}
+
 static int grid_for(int64_t k) {
     int64_t b = (k + 255) / 256;
     return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
@@ -343,6 +390,17 @@ int hawkes_hmc_position(int64_t k, double *q, const double *p, const double *min
 int hawkes_hmc_kinetic(int64_t k, const double *p, const double *minv, double *out, void *stream) {
     if (k < 1 || !p || !minv || !out) return HAWKES_EINVAL;
     launch_pdl(hk::kinetic_kernel, 1, hk::ASM_THREADS, 0, (cudaStream_t)stream, k, p, minv, out);
+    return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
+}
+
+int hawkes_hmc_accept(int64_t k, const double *u, const double *k0, const double *k1, const double *lp1,
+                      const double *grad1, const double *q1, const int *status, double *q, double *lp, double *grad,
+                      int64_t n_keep, const int64_t *keep, double *rec_q, double *rec, void *stream) {
+    if (k < 1 || !u || !k0 || !k1 || !lp1 || !grad1 || !q1 || !q || !lp || !grad) return HAWKES_EINVAL;
+    if (n_keep < 0 || (n_keep > 0 && rec_q && !keep)) return HAWKES_EINVAL;
+    if (q1 == q || grad1 == grad) return HAWKES_EINVAL;  // the proposal must not alias the state
+    launch_pdl(hk::accept_kernel, 1, hk::ACCEPT_THREADS, 0, (cudaStream_t)stream, k, u, k0, k1, lp1, grad1, q1, status,
+               q, lp, grad, rec_q ? n_keep : (int64_t)0, keep, rec_q, rec);
     return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
 }
 

@@ -32,7 +32,7 @@
 namespace hk {
 
 template <int MODE, bool BAND>
-__global__ void __launch_bounds__(TILE, 4) row32_kernel(Consts c, Inputs in, Workspace ws) {
+__global__ void __launch_bounds__(TILE, 5) row32_kernel(Consts c, Inputs in, Workspace ws) {
     pdl_wait();
     const Derived &D = *c.d;
     // Chunk order: blocks are dispatched y-major, so y = 0 takes the chunk that

@@ -105,8 +105,9 @@ def _lib():
         L.hawkes_hmc_kinetic.argtypes = [i64, vp, vp, vp, vp]
         L.hawkes_hmc_position_dense.argtypes = [i64, vp, vp, vp, d, vp]
         L.hawkes_hmc_kinetic_dense.argtypes = [i64, vp, vp, vp, vp]
+        L.hawkes_hmc_accept.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp, vp]
         for f in (L.hawkes_hmc_scatter_rates, L.hawkes_hmc_momentum, L.hawkes_hmc_position, L.hawkes_hmc_kinetic,
-                  L.hawkes_hmc_position_dense, L.hawkes_hmc_kinetic_dense):
+                  L.hawkes_hmc_position_dense, L.hawkes_hmc_kinetic_dense, L.hawkes_hmc_accept):
             f.restype = ctypes.c_int
         L._hmc_typed = True
     return L
@@ -610,6 +611,27 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
     graph = None
     scratch = {"logpost": torch.empty((), **f64), "grad": torch.empty(dim, **f64), "hdiag": torch.empty(dim, **f64)}
     k0, k1 = torch.empty((), **f64), torch.empty((), **f64)
+    # After warm-up the accept step runs on the device (hawkes_hmc_accept) and each
+    # iteration's record goes to its own device slot, so that an iteration needs no
+    # host round trip; the slots are copied to the host arrays at checkpoints and at
+    # the end.  The uniform draws still come from the host stream, in the same order.
+    L = _lib()
+    stream = lambda: ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)  # noqa: E731
+    keep_d = keep_t.to(torch.int64)
+    rec_q = torch.empty((n_iter, len(keep)), **f64)
+    rec = torch.empty((n_iter, 3), **f64)
+    u_pin = torch.empty(max(n_iter, 1), dtype=torch.float64, pin_memory=True)
+    u_dev = torch.empty(max(n_iter, 1), **f64)
+    status_t = post.like.get("status") if isinstance(getattr(post, "like", None), dict) else None
+    first_slot = max(start, n_warmup) - n_warmup  # the first slot this call fills
+
+    def pull(j1):
+        """Copy device record slots [first_slot, j1) to the host arrays."""
+        if j1 > first_slot:
+            draws[first_slot:j1] = rec_q[first_slot:j1].cpu().numpy()
+            r = rec[first_slot:j1].cpu().numpy()
+            lps[first_slot:j1], aprob[first_slot:j1], acc[first_slot:j1] = r[:, 0], r[:, 1], r[:, 2] != 0.0
+
     torch.cuda.synchronize()
     t_seg = time.perf_counter()  # start of the current warm-up or sampling segment
     for it in range(start, total):
@@ -631,6 +653,10 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
         kinetic(p, mop, k0)
         lvl = int(rng.integers(len(levels))) if len(levels) > 1 else 0
         eps_it = eps * levels[lvl]
+        if it >= n_warmup:
+            j = it - n_warmup
+            u_pin[j] = rng.uniform()  # slot j is written once, so the copy may run later
+            u_dev[j:j + 1].copy_(u_pin[j:j + 1], non_blocking=True)
         if use_graph and record is None and it >= n_warmup:
             graph = graphs.get(lvl)
             if graph is None:
@@ -645,17 +671,21 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
             ev = leapfrog(post, qn, p, cur["grad"], eps_it, n_steps, mop, scratch, record)
             kinetic(p, mop, k1)
             k1_t = k1
-        h0 = -cur["logpost"].item() + k0.item()
-        lp1 = ev["logpost"].item()
-        h1 = -lp1 + k1_t.item()
-        ok_num = math.isfinite(lp1) and post.status() == hawkes.OK
-        a = min(1.0, math.exp(min(0.0, h0 - h1))) if ok_num and math.isfinite(h1) else 0.0
-        accepted = rng.uniform() < a
-        if accepted:
-            q = qn.clone() if graph is not None and qn is graph.q else qn
-            cur["logpost"].copy_(ev["logpost"])
-            cur["grad"].copy_(ev["grad"])
-        if it < n_warmup:
+        if it >= n_warmup:
+            _check(L.hawkes_hmc_accept(dim, _ptr(u_dev[j]), _ptr(k0), _ptr(k1_t), _ptr(ev["logpost"]),
+                                       _ptr(ev["grad"]), _ptr(qn), _ptr(status_t), _ptr(q), _ptr(cur["logpost"]),
+                                       _ptr(cur["grad"]), len(keep), _ptr(keep_d), _ptr(rec_q[j]), _ptr(rec[j]),
+                                       stream()))
+        else:
+            h0 = -cur["logpost"].item() + k0.item()
+            lp1 = ev["logpost"].item()
+            h1 = -lp1 + k1_t.item()
+            ok_num = math.isfinite(lp1) and post.status() == hawkes.OK
+            a = min(1.0, math.exp(min(0.0, h0 - h1))) if ok_num and math.isfinite(h1) else 0.0
+            if rng.uniform() < a:
+                q = qn
+                cur["logpost"].copy_(ev["logpost"])
+                cur["grad"].copy_(ev["grad"])
             eps = da.update(a)
         if (it + 1) % mass_every == 0 and dm is not None:
             # running average of minus the Hessian by central differences of the gradient
@@ -674,13 +704,8 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
             torch.reciprocal(mass, out=minv)
             cur["logpost"].copy_(hd["logpost"])
             cur["grad"].copy_(hd["grad"])
-        if it >= n_warmup:
-            j = it - n_warmup
-            draws[j] = q[keep_t].cpu().numpy()
-            lps[j] = cur["logpost"].item()
-            acc[j] = accepted
-            aprob[j] = a
         if checkpoint and checkpoint_every and (it + 1) % checkpoint_every == 0 and it + 1 < total:
+            pull(it + 1 - n_warmup)
             torch.cuda.synchronize()
             now = time.perf_counter()
             seg = now - t_seg
@@ -700,6 +725,7 @@ def sample(post: Posterior, q0, n_iter, n_warmup, n_steps=20, eps0=0.01, mass_ev
             else:
                 spent_samp += seg
             t_seg = time.perf_counter()
+    pull(n_iter)
     torch.cuda.synchronize()
     now = time.perf_counter()
     if total > n_warmup and max(start, n_warmup) < total:

@@ -1,6 +1,9 @@
-"""GPU HMC pieces (posterior assembly, leapfrog kernels, sampler) vs the oracle."""
+"""GPU HMC pieces (posterior assembly, leapfrog kernels, accept step, sampler) vs the oracle."""
+import math
+
 import numpy as np
 import pytest
+import torch
 
 from oracle import hmc_oracle, tree_oracle
 from paper_2103_03348_b300 import synth
@@ -360,3 +363,59 @@ def test_checkpoint_resume_equals_uninterrupted_chain(tmp_path):
         resumed = hmc.sample(make(), q0, resume=ck, **kw)
         assert np.array_equal(resumed.draws, full.draws) and np.array_equal(resumed.accept, full.accept)
         assert resumed.eps == full.eps and np.array_equal(resumed.mass, full.mass)
+
+
+@pytest.mark.gpu
+def test_device_accept_step_matches_oracle():
+    """hawkes_hmc_accept against oracle.hmc_oracle.metropolis_step: the decision,
+    the resulting state, log posterior and gradient, and the record slots, over
+    random energies and the cases that must reject (non-finite proposal,
+    likelihood error) or sit on the boundary (u == a rejects)."""
+    import ctypes
+    from paper_2103_03348_b300 import build, hmc
+    build.build()
+    L = hmc._lib()
+    rng = np.random.default_rng(17)
+    dev = "cuda"
+    f64 = dict(dtype=torch.float64, device=dev)
+    k = 300
+    keep = np.array([0, 5, 299, 17, 300])  # the last index is out of range: recorded as NaN
+    keep_d = torch.tensor(keep, dtype=torch.int64, device=dev)
+    cases = []
+    for _ in range(60):
+        lp0, k0 = rng.normal(-50.0, 5.0), rng.exponential(5.0)
+        lp1, k1 = lp0 + rng.normal(0.0, 1.5), k0 + rng.normal(0.0, 1.5)
+        cases.append((lp0, k0, lp1, k1, rng.uniform(), 0))
+    cases += [(-1.0, 0.0, -1.0 - math.log(4.0), 0.0, 0.25, 0),  # u == a: rejected
+              (-1.0, 0.0, -1.0 - math.log(4.0), 0.0, 0.2499, 0),
+              (-1.0, 0.0, math.nan, 0.0, 0.0, 0), (-1.0, 0.0, -math.inf, 0.0, 0.0, 0),
+              (-1.0, 0.0, -1.0, math.inf, 0.0, 0), (-1.0, 0.0, 5.0, 0.0, 0.0, 2)]
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for lp0, k0, lp1, k1, u, st in cases:
+        q0, g0 = rng.normal(size=k), rng.normal(size=k)
+        q1, g1 = rng.normal(size=k), rng.normal(size=k)
+        q_d, g_d = torch.tensor(q0, **f64), torch.tensor(g0, **f64)
+        lp_d = torch.tensor(lp0, **f64)
+        rec_q, rec = torch.full((len(keep),), -7.0, **f64), torch.full((3,), -7.0, **f64)
+        args = [torch.tensor(v, **f64) for v in (u, k0, k1, lp1)]
+        q1_d, g1_d = torch.tensor(q1, **f64), torch.tensor(g1, **f64)
+        st_d = torch.tensor(st, dtype=torch.int32, device=dev)
+        rc = L.hawkes_hmc_accept(k, hmc._ptr(args[0]), hmc._ptr(args[1]), hmc._ptr(args[2]), hmc._ptr(args[3]),
+                                 hmc._ptr(g1_d), hmc._ptr(q1_d), hmc._ptr(st_d), hmc._ptr(q_d), hmc._ptr(lp_d),
+                                 hmc._ptr(g_d), len(keep), hmc._ptr(keep_d), hmc._ptr(rec_q), hmc._ptr(rec), s)
+        assert rc == 0
+        torch.cuda.synchronize()
+        q_r, lp_r, g_r, ok_r, a_r = hmc_oracle.metropolis_step(q0, lp0, g0, k0, q1, lp1, g1, k1, u, ok=st == 0)
+        a_d = rec[1].item()
+        assert abs(a_d - a_r) <= 4e-16 * max(a_r, 1e-300)
+        if abs(u - a_r) > 1e-12 or u == a_r:  # a decision on the boundary is taken the same way only when exact
+            assert bool(rec[2].item()) == ok_r
+            assert np.array_equal(q_d.cpu().numpy(), q_r) and np.array_equal(g_d.cpu().numpy(), g_r)
+            assert lp_d.item() == lp_r and rec[0].item() == lp_r
+            want = np.array([q_r[i] if i < k else np.nan for i in keep])
+            assert np.array_equal(rec_q.cpu().numpy(), want, equal_nan=True)
+    # argument checks: aliasing proposal and state, negative keep count
+    rc = L.hawkes_hmc_accept(k, hmc._ptr(args[0]), hmc._ptr(args[1]), hmc._ptr(args[2]), hmc._ptr(args[3]),
+                             hmc._ptr(g1_d), hmc._ptr(q_d), None, hmc._ptr(q_d), hmc._ptr(lp_d), hmc._ptr(g_d),
+                             0, None, None, None, s)
+    assert rc == hmc.hawkes.EINVAL
