@@ -284,6 +284,67 @@ def test_million_events_ragged():
     assert np.linalg.norm(h[6 + idx] - h_ref) <= 1e-4 * np.linalg.norm(h_ref)
 
 
+@pytest.fixture(scope="module")
+def surrogate_workload():
+    return synth.make("surrogate")
+
+
+# a point of the posterior the surrogate's sampler explores (bandwidths well below the generating ones)
+SURROGATE_POSTERIOR_POINT = (0.86, 6.7, 17.9, 0.144, 0.211, 3.59)
+
+
+@pytest.mark.parametrize("point", ["generating", "posterior"])
+def test_surrogate_configuration_at_full_size(surrogate_workload, point):
+    """The learned surrogate's configuration at its full size (500,000 events:
+    uniform background plus 500 hotspots, every log-rate 0), in the launch
+    configuration its sampler uses (space-time tiles, the six globals read on
+    the device as logarithms), at the generating values and at a point of the
+    posterior it samples:
+      * the globals-only gradient (the exact warm-up's call) and the
+        log-likelihood (the accept step's call) agree with the full evaluation
+        to rounding order (the same row sums);
+      * the log-likelihood and the 12 global entries agree with the time-order
+        FP32C path at the FP32C bars (two summation orders of the same terms,
+        both pinned to the oracle at 100,000 events);
+      * the exact identities: 1-homogeneity in (mu0, theta0) and the column
+        sums against the theta0 row sums;
+      * 48 log-rate gradient and Hessian entries of late sources, recomputed one
+        by one by the oracle from intensities the oracle computes."""
+    w = surrogate_workload
+    p = np.array(w.params if point == "generating" else SURROGATE_POSTERIOR_POINT)
+    H = hawkes_mod()
+    x, y, t, r = dev(w.x), dev(w.y), dev(w.t), dev(w.r)
+    ll, g, h = (v.cpu().numpy() for v in H.hess_diag(x, y, t, r, p, "fp32c_st"))
+    ll = float(ll)
+    q = dev(np.log(p))
+    og = H._call("grad_globals", x, y, t, r, q, "fp32c_st", log_params=True)
+    ol = H._call("loglik", x, y, t, r, q, "fp32c_st", log_params=True)
+    assert rel(og["loglik"].item(), ll) <= 1e-14 and rel(ol["loglik"].item(), ll) <= 1e-14
+    np.testing.assert_allclose(og["grad"][:6].cpu().numpy(), g[:6], rtol=1e-13, atol=1e-13 * np.abs(g[:6]).max())
+
+    ll_t, g_t, h_t = gpu_eval(w, p, "fp32c")
+    assert rel(ll, ll_t) <= 1e-6
+    assert np.max(np.abs(g[:6] - g_t[:6]) / np.abs(g_t[:6])) <= 1e-5
+    assert np.max(np.abs(h[:6] - h_t[:6]) / np.abs(h_t[:6])) <= 1e-4
+
+    mu0, th0 = p[0], p[3]
+    Lam = oracle.integral(w.t, w.r, p)
+    assert rel(mu0 * g[0] + th0 * g[3], w.n - Lam) <= 1e-6
+    assert rel(np.sum(g[6:]), th0 * g[3]) <= 1e-5
+
+    rng = np.random.default_rng(9)
+    idx = np.sort(rng.choice(np.arange(w.n - 600, w.n - 1), 48, replace=False))
+    later = np.arange(idx.min(), w.n)
+    lam_later, _, _ = oracle.rows(w.x, w.y, w.t, w.r, p, later)
+    lam = np.ones(w.n)
+    lam[later] = lam_later
+    g_ref, h_ref = oracle.rate_terms(w.x, w.y, w.t, w.r, p, lam, idx)
+    scale_g = np.abs(g[6:]).max()
+    assert np.max(np.abs(g[6 + idx] - g_ref) / np.maximum(np.abs(g_ref), 1e-3 * scale_g)) <= 2e-3
+    assert np.linalg.norm(g[6 + idx] - g_ref) <= 1e-4 * np.linalg.norm(g_ref)
+    assert np.linalg.norm(h[6 + idx] - h_ref) <= 1e-4 * np.linalg.norm(h_ref)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32c", "fp32c_st"])
 def test_reused_event_preparation(prec):
     """HAWKES_MODE_REUSE_EVENTS: a second call on the same events and workspace
