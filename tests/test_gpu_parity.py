@@ -76,6 +76,27 @@ def test_ragged_sizes(n, prec):
     check(prec, ll, g, h, ref, label=f"uniform N={n}")
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32c", "fp32c_band", "fp32c_st"])
+def test_dense_burst_then_sparse_tail(prec):
+    """A dense burst (1,000 events in one time unit) followed by a sparse tail
+    (200 events over 29 units) under fast decay (omega = 3): time-order tiles
+    whose time spans differ by two orders of magnitude, space-time groups that
+    mix both parts, and r^ spreads within a tile from about 4 to about 80
+    (base-2 units); every output against the oracle at its precision's bars.  (|t~|
+    stays below 65 here: much longer spans at this decay put FP32's
+    quantisation of t~ itself above the log-rate bar.)"""
+    rng = np.random.default_rng(22)
+    t = np.sort(np.concatenate([rng.uniform(0.0, 1.0, 1000), rng.uniform(1.0, 30.0, 200)]))
+    x, y = rng.uniform(0.0, 1.0, t.size), rng.uniform(0.0, 1.0, t.size)
+    r = rng.normal(0.0, 0.5, t.size)
+    p = np.array([0.5, 0.2, 0.1, 0.3, 3.0, 0.05])
+    spread = (r + 3.0 * t) * 1.4426950408889634
+    assert np.ptp(spread[:128]) < 10 and np.ptp(spread[-128:]) > 60
+    ref = oracle.evaluate(x, y, t, r, p, want=2)
+    ll, g, h = gpu_eval((x, y, t, r), p, prec)
+    check(prec, ll, g, h, ref, label=f"burst and tail {prec}")
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32c", "fp32c_st"])
 def test_paper_background_without_temporal_bandwidth(prec):
     w = synth.make("unit_square")
