@@ -64,7 +64,8 @@ size_t carve(void *base, const Geometry &g, int precision, Workspace *w) {
     w->rowpart = (double *)take((size_t)g.n_chunks * NMOM * np * sizeof(double));
     w->mom = (double *)take((size_t)NMOM * np * sizeof(double));
     w->dLr = (double *)take(np * sizeof(double));
-    w->blockpart = (double *)take(nt * ACC_STRIDE * sizeof(double));
+    // row-finish partials: one per tile, or one per 32-row group on space-time tiles
+    w->blockpart = (double *)take((st ? np / GROUP : nt) * ACC_STRIDE * sizeof(double));
     w->ipart = f32 ? (double *)take(nt * (TILE / GROUP) * ACC_STRIDE * sizeof(double)) : nullptr;
     w->colpart = (double *)take((size_t)g.n_chunks * 2 * np * sizeof(double));
     w->bbox = (double *)take(4 * sizeof(double));
@@ -243,6 +244,7 @@ static int prepare(const double *x, const double *y, const double *t, const doub
     c.fp32c = precision == HAWKES_FP32C || precision == HAWKES_FP32C_BAND || precision == HAWKES_FP32C_ST;
     c.band = precision == HAWKES_FP32C_BAND;
     c.st = precision == HAWKES_FP32C_ST;
+    c.fin_groups = c.st && g.tiles < FIN_GROUP_TILES;
     c.t0 = 0;
     c.t1 = g.tiles;
     c.d = k->ws.derived;

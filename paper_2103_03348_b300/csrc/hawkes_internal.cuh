@@ -73,6 +73,13 @@ constexpr float BG_DEAD = 130.0f;
 // rows whose FP32 background and excitation sums are both below 2^-60 are
 // recomputed in FP64 (terms below 2^-126 were flushed to zero in FP32)
 constexpr float TINY_ROW = 8.673617379884035e-19f;  // 2^-60
+// FP32C_ST: below this many tiles (about 1.35 per SM of a B300) the rows are
+// finished per 32-row group (four blocks per tile, each a quarter of the chunk
+// loads deep), so that a small problem spreads its finish over the SMs; from
+// it on, per tile (more rows per block to hide the FP64 epilogue's latency).
+// Measured: 183 tiles (23,422 events) 3.5 us faster per group; 274 tiles
+// (35,000 events) 10 us faster per tile.
+constexpr int FIN_GROUP_TILES = 200;
 
 // Moment index (row pass).  Background terms G, excitation terms E (with exp(r)):
 //   0 sum G        1 sum G d^2     2 sum G dt^2    3 sum G d^4     4 sum G dt^4
@@ -124,6 +131,7 @@ struct Consts {
     Geometry g;
     int mode, fp32c, band;  // band: FP32C with exact background band skipping
     int st;            // FP32C_ST: space-time tiles (events permuted inside slabs), group pruning
+    int fin_groups;    // FP32C_ST with few tiles: rows finished per 32-row group (finish_group_st)
     int t0, t1;        // the tiles this call owns as targets (row pass) and sources (column pass)
     const Derived *d;  // device: written by setup_kernel
 };
@@ -170,7 +178,7 @@ struct Workspace {
     double *mom;         // [NMOM * npad]
     double *w64;         // [npad]  FP64 column weight, in logs: log(B / lambda_n)
     double *dLr;         // [npad]  dLambda / dr_m
-    double *blockpart;   // [tiles * ACC_STRIDE]
+    double *blockpart;   // [tiles * ACC_STRIDE], or [groups * ACC_STRIDE] on space-time tiles (room for fin_groups)
     double *ipart;       // [tiles * 4 * ACC_STRIDE] FP32C: the integral-term sums of each 32-event group (row pass)
     float *sufmax;       // [tiles] suffix max of the column weight bound (FP32C)
     double *colpart;     // [n_chunks * 2 * npad]

@@ -91,8 +91,15 @@ __global__ void __launch_bounds__(TILE) finish_kernel(Consts c, Inputs in, Works
     finish_tile_fp32c(c, in, ws, c.t0 + blockIdx.x);
 }
 
+// FP32C_ST with few tiles: one block of FG_WARPS warps per target group finishes its 32 rows (rows_finish.cuh).
+__global__ void __launch_bounds__(FG_WARPS * 32) finish_st_kernel(Consts c, Inputs in, Workspace ws) {
+    pdl_wait();
+    finish_group_st(c, in, ws, c.t0 * (TILE / GROUP) + blockIdx.x);
+}
+
 cudaError_t launch_finish(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s) {
-    launch_pdl(finish_kernel, c.t1 - c.t0, TILE, 0, s, c, in, ws);
+    if (c.fin_groups) launch_pdl(finish_st_kernel, (c.t1 - c.t0) * (TILE / GROUP), FG_WARPS * 32, 0, s, c, in, ws);
+    else launch_pdl(finish_kernel, c.t1 - c.t0, TILE, 0, s, c, in, ws);
     return cudaGetLastError();
 }
 
@@ -108,15 +115,17 @@ __global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(Consts c, Workspa
     const Derived &D = *c.d;
     __shared__ double tot[NACC];
     const int tiles = c.g.tiles;
+    // the block partials: one per tile, or one per 32-row group (finish_group_st)
+    const int nparts = c.fin_groups ? tiles * (TILE / GROUP) : tiles;
     {
-        // Warp w sums components w and w + 8 over the tiles: each lane a fixed
+        // Warp w sums components w and w + 8 over the partials: each lane a fixed
         // strided subset, then a fixed shuffle butterfly.  (FP64 instructions
         // are costly here, and this keeps them to a few per lane.)
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         for (int k = warp; k < NACC; k += FIN_THREADS / 32) {
             double v = 0.0;
 #pragma unroll 8
-            for (int b = lane; b < tiles; b += 32) v += ws.blockpart[(size_t)b * ACC_STRIDE + k];
+            for (int b = lane; b < nparts; b += 32) v += ws.blockpart[(size_t)b * ACC_STRIDE + k];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if (lane == 0) tot[k] = v;
@@ -152,8 +161,14 @@ __global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(Consts c, Workspa
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         const int len = (tiles + FIN_THREADS - 1) / FIN_THREADS;
         const int b0 = threadIdx.x * len, b1 = min(tiles, b0 + len);
+        // a tile's largest g^: the tile statistic, or after a per-group finish the largest of its groups'
+        auto tile_gmax = [&](int b) -> float {
+            if (!c.fin_groups) return ws.tstat32[b].w;
+            const GroupStat *gs = ws.grp + (size_t)b * (TILE / GROUP);
+            return fmaxf(fmaxf(gs[0].tr.w, gs[1].tr.w), fmaxf(gs[2].tr.w, gs[3].tr.w));
+        };
         float m = -INFINITY;
-        for (int b = b0; b < b1; ++b) m = fmaxf(m, ws.tstat32[b].w);
+        for (int b = b0; b < b1; ++b) m = fmaxf(m, tile_gmax(b));
         // inclusive suffix max within the warp, then over the later warps
         float v = m;
 #pragma unroll
@@ -169,7 +184,7 @@ __global__ void __launch_bounds__(FIN_THREADS) finalize_kernel(Consts c, Workspa
         if (lane == 31) excl = -INFINITY;
         float run = fmaxf(excl, later);
         for (int b = b1 - 1; b >= b0; --b) {
-            run = fmaxf(run, ws.tstat32[b].w);
+            run = fmaxf(run, tile_gmax(b));
             ws.sufmax[b] = run;
         }
     }

@@ -152,6 +152,60 @@ __host__ __device__ constexpr bool row_mom_used(int mode, int k) {
                              : (k == MO_G || k == MO_E);
 }
 
+// The FP64 fix-up of a row whose FP32 background and excitation sums are both
+// below 2^-60 (terms under 2^-126 were flushed to zero in FP32): the calling
+// warp recomputes row `row` over all sources in FP64; every lane returns the
+// warp's sums in a (a fixed butterfly), in the FP32C scaled units as
+// accumulate64 forms them.  A term more than 2^80 below the row's largest term
+// of its kind cannot change the FP64 sum, so an FP32 pass over the packed
+// sources first finds the largest background and excitation exponents (base
+// 2, as the row pass forms them); the FP64 pass then evaluates only the terms
+// within 2^80 of them.  (FP32 exponents are off by far less than 80 units, and
+// FP64 coordinates keep the kept terms exact where FP32 ones would cost a far
+// pair its relative accuracy.)
+__device__ __forceinline__ void fixup_row64(const Consts &c, const Inputs &in, const Workspace &ws, int row,
+                                            double (&a)[NMOM]) {
+    const Derived &D = *c.d;
+    const int n = c.g.n;
+    const int lane = threadIdx.x & 31;
+    const float *f = reinterpret_cast<const float *>(ws.src32);
+    const float cbt = D.cbt, hh = D.hh;
+    constexpr float KEEP = 80.0f;
+    const int pr = row >> 1, lr = row & 1;
+    const float xn = -f[8 * pr + lr], yn = -f[8 * pr + 2 + lr], tn = -f[8 * pr + 4 + lr];
+    const int locn = ws.loc[row], gn = ws.gidx[row];
+    float mg = -INFINITY, me = -INFINITY;
+    for (int j = lane; j < n; j += 32) {
+        const int p = j >> 1, l = j & 1;
+        const float dx = xn + f[8 * p + l], dy = yn + f[8 * p + 2 + l], dt = tn + f[8 * p + 4 + l];
+        const float d2 = dx * dx + dy * dy;
+        if (ws.loc[j] != locn) mg = fmaxf(mg, -(d2 + cbt * dt * dt));
+        // FP32C_ST: the causal test compares time-order ranks
+        if ((c.st ? ws.perm[j] : j) < gn) me = fmaxf(me, f[8 * p + 6 + l] - tn - hh * d2);
+    }
+    mg = warp_maxf(mg);
+    me = warp_maxf(me);
+    const double xn64 = in.x[row], yn64 = in.y[row], tn64 = in.t[row];
+#pragma unroll
+    for (int k = 0; k < NMOM; ++k) a[k] = 0.0;
+    for (int j = lane; j < n; j += 32) {
+        const int p = j >> 1, l = j & 1;
+        const float dx = xn + f[8 * p + l], dy = yn + f[8 * p + 2 + l], dt = tn + f[8 * p + 4 + l];
+        const float d2 = dx * dx + dy * dy;
+        const bool bg_on = ws.loc[j] != locn && -(d2 + cbt * dt * dt) > mg - KEEP;
+        const bool ex_on = (c.st ? ws.perm[j] : j) < gn && f[8 * p + 6 + l] - tn - hh * d2 > me - KEEP;
+        if (bg_on || ex_on)
+            accumulate64<MODE_HESS>(a, in.x[j], in.y[j], in.t[j], in.r[j], bg_on, ex_on, xn64, yn64, tn64, D);
+    }
+#pragma unroll
+    for (int k = 0; k < NMOM; ++k) {
+        double v = a[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        a[k] = v;
+    }
+}
+
 // FP32C: the rows of target tile `tile`, finished by one block of TILE
 // threads (one row each) after the row pass:
 //   * the chunk partials summed in FP64 in chunk order;
@@ -159,7 +213,8 @@ __host__ __device__ constexpr bool row_mom_used(int mode, int k) {
 //     (terms under 2^-126 were flushed to zero in FP32) redone in FP64 over
 //     all sources, the block cooperating on one row at a time;
 //   * the row epilogue, the tile's 13 block sums, and the tile (and, on
-//     space-time tiles, group) maxima of the column weight g^.
+//     space-time tiles, group) maxima of the column weight g^.  (Problems of
+//     fewer than FIN_GROUP_TILES space-time tiles use finish_group_st.)
 __device__ __forceinline__ void finish_tile_fp32c(const Consts &c, const Inputs &in, const Workspace &ws, int tile) {
     const Derived &D = *c.d;
     __shared__ double fsh[TILE];
@@ -216,53 +271,15 @@ __device__ __forceinline__ void finish_tile_fp32c(const Consts &c, const Inputs 
     if (tiny) ftiny[off + __popc(bal & ((1u << lane) - 1u))] = threadIdx.x;
     __syncthreads();
     if (ntiny > 0) {
-        // One warp per listed row.  A term more than 2^80 below the row's largest
-        // term of its kind cannot change the FP64 sum, so an FP32 pass over the
-        // packed sources first finds the largest background and excitation
-        // exponents (base 2, as the row pass forms them); the FP64 pass then
-        // evaluates only the terms within 2^80 of them.  (FP32 exponents are off
-        // by far less than 80 units, and FP64 coordinates keep the kept terms
-        // exact where FP32 ones would cost a far pair its relative accuracy.)
+        // One warp per listed row (fixup_row64).
         __shared__ double fmom[TILE][NMOM];  // in the FP32C scaled units, as accumulate64 forms them
-        const float *f = reinterpret_cast<const float *>(ws.src32);
-        const float cbt = D.cbt, hh = D.hh;
-        constexpr float KEEP = 80.0f;
         for (int q = warp; q < ntiny; q += TILE / 32) {
-            const int owner = ftiny[q], row = tile * TILE + owner;
-            const int pr = row >> 1, lr = row & 1;
-            const float xn = -f[8 * pr + lr], yn = -f[8 * pr + 2 + lr], tn = -f[8 * pr + 4 + lr];
-            const int locn = ws.loc[row], gn = ws.gidx[row];
-            float mg = -INFINITY, me = -INFINITY;
-            for (int j = lane; j < n; j += 32) {
-                const int p = j >> 1, l = j & 1;
-                const float dx = xn + f[8 * p + l], dy = yn + f[8 * p + 2 + l], dt = tn + f[8 * p + 4 + l];
-                const float d2 = dx * dx + dy * dy;
-                if (ws.loc[j] != locn) mg = fmaxf(mg, -(d2 + cbt * dt * dt));
-                // FP32C_ST: the causal test compares time-order ranks
-                if ((c.st ? ws.perm[j] : j) < gn) me = fmaxf(me, f[8 * p + 6 + l] - tn - hh * d2);
-            }
-            mg = warp_maxf(mg);
-            me = warp_maxf(me);
-            const double xn64 = in.x[row], yn64 = in.y[row], tn64 = in.t[row];
+            const int owner = ftiny[q];
             double a[NMOM];
+            fixup_row64(c, in, ws, tile * TILE + owner, a);
+            if (lane == 0) {
 #pragma unroll
-            for (int k = 0; k < NMOM; ++k) a[k] = 0.0;
-            for (int j = lane; j < n; j += 32) {
-                const int p = j >> 1, l = j & 1;
-                const float dx = xn + f[8 * p + l], dy = yn + f[8 * p + 2 + l], dt = tn + f[8 * p + 4 + l];
-                const float d2 = dx * dx + dy * dy;
-                const bool bg_on = ws.loc[j] != locn && -(d2 + cbt * dt * dt) > mg - KEEP;
-                const bool ex_on = (c.st ? ws.perm[j] : j) < gn && f[8 * p + 6 + l] - tn - hh * d2 > me - KEEP;
-                if (bg_on || ex_on)
-                    accumulate64<MODE_HESS>(a, in.x[j], in.y[j], in.t[j], in.r[j], bg_on, ex_on, xn64, yn64, tn64, D);
-            }
-            // warp sums (a fixed butterfly: every lane holds the same total)
-#pragma unroll
-            for (int k = 0; k < NMOM; ++k) {
-                double v = a[k];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0) fmom[owner][k] = v;
+                for (int k = 0; k < NMOM; ++k) fmom[owner][k] = a[k];
             }
         }
         __syncthreads();
@@ -292,6 +309,120 @@ __device__ __forceinline__ void finish_tile_fp32c(const Consts &c, const Inputs 
     }
     const float gm = block_max<TILE>(ghat, fshf);
     if (threadIdx.x == 0) ws.tstat32[tile].w = gm;
+}
+
+// FP32C_ST with fewer than FIN_GROUP_TILES tiles: the rows of target group `g`
+// (32 rows), finished by one block of
+// FG_WARPS warps after the row pass (four times the blocks of a per-tile
+// finish, each a quarter of the chunk loads deep):
+//   * warp s sums, for all 32 rows, the chunk partials of the contiguous chunk
+//     range [s C / 4, (s + 1) C / 4) in chunk order in float-float, and warp 0
+//     adds the four ranges in order (two-sum of the leading parts, the low
+//     parts and rounding errors carried in the second float, as above);
+//   * rows whose FP32 background and excitation sums are both below 2^-60
+//     redone in FP64, one warp per row (fixup_row64);
+//   * warp 0: the row epilogue, the packed column targets, the group's 13 sums
+//     (a fixed butterfly) plus its integral shares into blockpart[g], and the
+//     group maximum of g^ for the column pass's pruning.  The finalize sums
+//     blockpart over the groups in order.
+constexpr int FG_WARPS = 4;
+
+__device__ __forceinline__ void finish_group_st(const Consts &c, const Inputs &in, const Workspace &ws, int g) {
+    const Derived &D = *c.d;
+    __shared__ float fhi[FG_WARPS][NMOM][GROUP], flo[FG_WARPS][NMOM][GROUP];
+    __shared__ double fmom[GROUP][NMOM];
+    __shared__ int ftiny[GROUP];
+    __shared__ int fntiny;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = g * GROUP + lane;
+    const int n = c.g.n, npad = c.g.npad;
+    const bool valid = i < n;
+    {
+        const int nc = c.g.n_chunks;
+        const int c0 = warp * nc / FG_WARPS, c1 = (warp + 1) * nc / FG_WARPS;
+        const float2 *part = reinterpret_cast<const float2 *>(ws.rowpart);
+        float hi[NMOM], lo[NMOM];
+#pragma unroll
+        for (int k = 0; k < NMOM; ++k) { hi[k] = 0.0f; lo[k] = 0.0f; }
+        if (valid) {
+#pragma unroll 2
+            for (int ch = c0; ch < c1; ++ch) {
+                float2 v[NMOM];
+#pragma unroll
+                for (int k = 0; k < NMOM; ++k)
+                    if (row_mom_used(c.mode, k)) v[k] = part[((size_t)ch * NMOM + k) * npad + i];
+#pragma unroll
+                for (int k = 0; k < NMOM; ++k) {
+                    if (!row_mom_used(c.mode, k)) continue;
+                    const float s = __fadd_rn(hi[k], v[k].x);
+                    const float bb = __fsub_rn(s, hi[k]);
+                    const float err = __fadd_rn(__fsub_rn(hi[k], __fsub_rn(s, bb)), __fsub_rn(v[k].x, bb));
+                    hi[k] = s;
+                    lo[k] = __fadd_rn(lo[k], __fadd_rn(err, v[k].y));
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NMOM; ++k) {
+            fhi[warp][k][lane] = hi[k];
+            flo[warp][k][lane] = lo[k];
+        }
+    }
+    __syncthreads();
+    double Mo[NMOM];
+    bool tiny = false;
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NMOM; ++k) {
+            float h = fhi[0][k][lane], l = flo[0][k][lane];
+#pragma unroll
+            for (int q = 1; q < FG_WARPS; ++q) {
+                const float b = fhi[q][k][lane];
+                const float s = __fadd_rn(h, b);
+                const float bb = __fsub_rn(s, h);
+                const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+                h = s;
+                l = __fadd_rn(l, __fadd_rn(err, flo[q][k][lane]));
+            }
+            Mo[k] = (double)h + (double)l;
+        }
+        tiny = valid && Mo[MO_G] < (double)TINY_ROW && Mo[MO_E] < (double)TINY_ROW;
+        const unsigned bal = __ballot_sync(0xffffffffu, tiny);
+        if (tiny) ftiny[__popc(bal & ((1u << lane) - 1u))] = lane;
+        if (lane == 0) fntiny = __popc(bal);
+    }
+    __syncthreads();
+    const int ntiny = fntiny;
+    if (ntiny > 0) {
+        for (int q = warp; q < ntiny; q += FG_WARPS) {
+            const int owner = ftiny[q];
+            double a[NMOM];
+            fixup_row64(c, in, ws, g * GROUP + owner, a);
+            if (lane == 0) {
+#pragma unroll
+                for (int k = 0; k < NMOM; ++k) fmom[owner][k] = a[k];
+            }
+        }
+        __syncthreads();
+        if (warp == 0 && tiny) {
+#pragma unroll
+            for (int k = 0; k < NMOM; ++k) Mo[k] = fmom[lane][k];
+        }
+    }
+    if (warp != 0) return;  // no block barrier below
+    double acc[NACC];
+#pragma unroll
+    for (int k = 0; k < NACC; ++k) acc[k] = 0.0;
+    float ghat = -INFINITY;
+    if (valid) epilogue_row<false>(c, D, in, ws, i, Mo, acc, ghat);  // the integral term came with the row pass
+    pack_target(ws, in, D, i, n, ghat);
+    const double w = warp_sum_scatter<NACC>(acc);  // lane 2k holds the group's sum k
+    if ((lane & 1) == 0 && (lane >> 1) < NACC) {
+        const int k = lane >> 1;
+        ws.blockpart[(size_t)g * ACC_STRIDE + k] = w + ws.ipart[(size_t)g * ACC_STRIDE + k];
+    }
+    const float wm = warp_maxf(ghat);
+    if (lane == 0) ws.grp[g].tr.w = wm;
 }
 
 // FP32C: the integral-term shares of one group of 32 events (FP64), summed
