@@ -317,6 +317,18 @@ int hawkes_posterior_add_trend(int64_t m, int k, const int *seq_idx, const doubl
 int hawkes_hmc_momentum(int64_t k, double *p, const double *g, double a, void *stream);
 int hawkes_hmc_position(int64_t k, double *q, const double *p, const double *minv, double eps, void *stream);
 int hawkes_hmc_kinetic(int64_t k, const double *p, const double *minv, double *out, void *stream);
+/* One leapfrog step's state updates in one launch (Section 2.3.2's leapfrog
+ * with a diagonal mass), on DEVICE vectors:
+ *   p += a * g             (the previous step's momentum update, or the first
+ *                           half step; skipped when g is NULL)
+ *   q += eps * minv * p    (the position update)
+ *   r[seq_idx[j]] = q[6 + j] for j < m  (the new sequenced log-rates, as
+ *                           hawkes_hmc_scatter_rates writes them)
+ * Equal bit for bit to hawkes_hmc_momentum, hawkes_hmc_position and
+ * hawkes_hmc_scatter_rates in sequence.  HAWKES_EINVAL for k < 1, m < 0,
+ * 6 + m > k, or NULL q, p, minv (or seq_idx, r when m > 0). */
+int hawkes_hmc_leapfrog_step(int64_t k, double *q, double *p, const double *g, double a, const double *minv,
+                             double eps, int64_t m, const int *seq_idx, double *r, void *stream);
 
 /* The Metropolis accept/reject step that closes a trajectory (Section 2.3),
  * on the device, so that a sampler needs no host round trip per iteration.

@@ -159,6 +159,24 @@ __global__ void position_kernel(int64_t k, double *__restrict__ q, const double 
         q[j] += eps * minv[j] * p[j];
 }
 
+// One leapfrog step's state updates in one launch (diagonal mass): the
+// momentum update p += a g that ends the previous step (or the first half
+// step), the position update q += eps minv p, and the scatter of the new
+// sequenced log-rates r[seq[j]] = q[6 + j] for the next evaluation.  Each
+// entry is one thread's: the same expressions as momentum_kernel,
+// position_kernel and scatter_rates_kernel in sequence, so the results are
+// those of the three launches bit for bit.
+__global__ void leapfrog_step_kernel(int64_t k, double *__restrict__ q, double *__restrict__ p,
+                                     const double *__restrict__ g, double a, const double *__restrict__ minv,
+                                     double eps, int64_t m, const int *__restrict__ seq, double *__restrict__ r) {
+    pdl_wait();
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < k; j += (int64_t)gridDim.x * blockDim.x) {
+        if (g) p[j] += a * g[j];
+        q[j] += eps * minv[j] * p[j];
+        if (j >= 6 && j - 6 < m) r[seq[j - 6]] = q[j];
+    }
+}
+
 // out = 1/2 sum_j minv_j p_j^2 (single block, fixed order)
 __global__ void __launch_bounds__(ASM_THREADS) kinetic_kernel(int64_t k, const double *__restrict__ p,
                                                               const double *__restrict__ minv, double *__restrict__ out) {
@@ -384,6 +402,15 @@ int hawkes_hmc_momentum(int64_t k, double *p, const double *g, double a, void *s
 int hawkes_hmc_position(int64_t k, double *q, const double *p, const double *minv, double eps, void *stream) {
     if (k < 1 || !q || !p || !minv) return HAWKES_EINVAL;
     launch_pdl(hk::position_kernel, hk::grid_for(k), 256, 0, (cudaStream_t)stream, k, q, p, minv, eps);
+    return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
+}
+
+int hawkes_hmc_leapfrog_step(int64_t k, double *q, double *p, const double *g, double a, const double *minv,
+                             double eps, int64_t m, const int *seq_idx, double *r, void *stream) {
+    if (k < 1 || !q || !p || !minv || m < 0 || m > k - 6) return HAWKES_EINVAL;
+    if (m > 0 && (!seq_idx || !r)) return HAWKES_EINVAL;
+    launch_pdl(hk::leapfrog_step_kernel, hk::grid_for(k), 256, 0, (cudaStream_t)stream, k, q, p, g, a, minv, eps, m,
+               seq_idx, r);
     return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ECUDA;
 }
 

@@ -106,8 +106,10 @@ def _lib():
         L.hawkes_hmc_position_dense.argtypes = [i64, vp, vp, vp, d, vp]
         L.hawkes_hmc_kinetic_dense.argtypes = [i64, vp, vp, vp, vp]
         L.hawkes_hmc_accept.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, vp, vp]
+        L.hawkes_hmc_leapfrog_step.argtypes = [i64, vp, vp, vp, d, vp, d, i64, vp, vp, vp]
         for f in (L.hawkes_hmc_scatter_rates, L.hawkes_hmc_momentum, L.hawkes_hmc_position, L.hawkes_hmc_kinetic,
-                  L.hawkes_hmc_position_dense, L.hawkes_hmc_kinetic_dense, L.hawkes_hmc_accept):
+                  L.hawkes_hmc_position_dense, L.hawkes_hmc_kinetic_dense, L.hawkes_hmc_accept,
+                  L.hawkes_hmc_leapfrog_step):
             f.restype = ctypes.c_int
         L._hmc_typed = True
     return L
@@ -172,20 +174,23 @@ class Posterior:
             self.pd = torch.empty(self.m, dtype=torch.float64, device=t.device)
         self.calls = {"grad": 0, "hess": 0}
 
-    def evaluate(self, q, want_hess=False, out=None):
+    def evaluate(self, q, want_hess=False, out=None, scattered=False):
         """Fill out = {'logpost', 'grad', ['hdiag']} (device tensors) at q; returns out.
 
         Everything is enqueued on the current stream: the likelihood reads the
         six globals from q on the device (as logarithms), so no value crosses to
         the host.  A q outside the parameter space gives log pi = -inf (or NaN
-        through the likelihood's NaN outputs), which the sampler rejects."""
+        through the likelihood's NaN outputs), which the sampler rejects.
+        scattered: q's sequenced log-rates are already in the likelihood's rate
+        vector (written by hawkes_hmc_leapfrog_step with scatter_args())."""
         L = _lib()
         stream = torch.cuda.current_stream(self.dev).cuda_stream
         if out is None:
             f64 = dict(dtype=torch.float64, device=self.dev)
             out = {"logpost": torch.empty((), **f64), "grad": torch.empty(self.dim, **f64),
                    "hdiag": torch.empty(self.dim, **f64)}
-        self._scatter(q, stream)
+        if not scattered:
+            self._scatter(q, stream)
         self._prior_async(q, want_hess)
         # with no free log-rates the column pass is skipped (globals-only modes)
         mode = ("hess" if want_hess else "grad") if self.m > 0 else ("hess_globals" if want_hess else "grad_globals")
@@ -198,6 +203,12 @@ class Posterior:
         self._assemble(q, self.like["grad"], self.like["hdiag"] if want_hess else None, out["logpost"],
                        out["grad"], out["hdiag"] if want_hess else None, stream)
         return out
+
+    def scatter_args(self):
+        """(m, seq, r) for hawkes_hmc_leapfrog_step's scatter of the sequenced
+        log-rates into the likelihood's rate vector, or None with the trend
+        (whose rates are not q's entries themselves)."""
+        return None if self.trend is not None else (self.m, self.seq, self.r)
 
     def _scatter(self, q, stream):
         L = _lib()
@@ -316,12 +327,28 @@ def leapfrog(post, q, p, g, eps, n_steps, minv, scratch, record=None):
     minv: the diagonal inverse mass (device tensor) or a TreeMassOp.
     record(q, grad), when given, sees every position of the trajectory with its
     gradient (device tensors, valid until the next step).  Returns the
-    evaluation dict at the final position."""
+    evaluation dict at the final position.  With a diagonal mass and a
+    posterior that offers scatter_args(), each step's momentum update, position
+    update and rate scatter are one launch (hawkes_hmc_leapfrog_step), with the
+    same results as the separate launches."""
     L = _lib()
     k = q.numel()
     s = ctypes.c_void_p(torch.cuda.current_stream(q.device).cuda_stream)
-    _check(L.hawkes_hmc_momentum(k, _ptr(p), _ptr(g), 0.5 * eps, s))
+    sc = post.scatter_args() if isinstance(minv, torch.Tensor) and hasattr(post, "scatter_args") else None
     ev = None
+    if sc is not None:
+        m, seq, r = sc
+        gcur, a = g, 0.5 * eps
+        for step in range(n_steps):
+            _check(L.hawkes_hmc_leapfrog_step(k, _ptr(q), _ptr(p), _ptr(gcur), a, _ptr(minv), eps, m, _ptr(seq),
+                                              _ptr(r), s))
+            ev = post.evaluate(q, out=scratch, scattered=True)
+            if record is not None:
+                record(q, ev["grad"])
+            gcur, a = ev["grad"], eps
+        _check(L.hawkes_hmc_momentum(k, _ptr(p), _ptr(gcur), 0.5 * eps, s))
+        return ev
+    _check(L.hawkes_hmc_momentum(k, _ptr(p), _ptr(g), 0.5 * eps, s))
     for step in range(n_steps):
         if isinstance(minv, torch.Tensor):
             _check(L.hawkes_hmc_position(k, _ptr(q), _ptr(p), _ptr(minv), eps, s))

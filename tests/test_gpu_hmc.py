@@ -419,3 +419,53 @@ def test_device_accept_step_matches_oracle():
                              hmc._ptr(g1_d), hmc._ptr(q_d), None, hmc._ptr(q_d), hmc._ptr(lp_d), hmc._ptr(g_d),
                              0, None, None, None, s)
     assert rc == hmc.hawkes.EINVAL
+
+
+class _SeparateLaunches:
+    """A posterior without scatter_args: leapfrog then takes the separate
+    momentum, position and scatter launches."""
+
+    def __init__(self, post):
+        self.post = post
+
+    def evaluate(self, q, want_hess=False, out=None):
+        return self.post.evaluate(q, want_hess=want_hess, out=out)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c_st"])
+def test_fused_leapfrog_step_equals_separate_launches(precision):
+    """hawkes_hmc_leapfrog_step (momentum, position and rate scatter in one
+    launch) gives the trajectory of hawkes_hmc_momentum, hawkes_hmc_position
+    and hawkes_hmc_scatter_rates in sequence, bit for bit, including every
+    intermediate position seen by record; and its argument checks."""
+    w, prec = problem()
+    post, hmc = make_post(w, prec, precision)
+    d = lambda a: torch.tensor(np.asarray(a, float), dtype=torch.float64, device="cuda")  # noqa: E731
+    rng = np.random.default_rng(3)
+    q0 = np.concatenate([np.log(w.params), w.r[w.sequenced]])
+    p0 = rng.normal(0, 1, q0.size)
+    minv = d(rng.uniform(0.02, 0.2, q0.size))
+    g0 = post.evaluate(d(q0))["grad"].clone()
+    runs = []
+    for target in (post, _SeparateLaunches(post)):
+        q, p = d(q0), d(p0)
+        seen = []
+        scratch = {"logpost": torch.empty((), dtype=torch.float64, device="cuda"),
+                   "grad": torch.empty(q.numel(), dtype=torch.float64, device="cuda")}
+        ev = hmc.leapfrog(target, q, p, g0, 0.05, 6, minv, scratch,
+                          record=lambda qq, gg: seen.append((qq.clone(), gg.clone())))
+        runs.append((q, p, ev["logpost"].clone(), ev["grad"].clone(), seen))
+    (qa, pa, la, ga, sa), (qb, pb, lb, gb, sb) = runs
+    assert torch.equal(qa, qb) and torch.equal(pa, pb) and torch.equal(la, lb) and torch.equal(ga, gb)
+    assert len(sa) == len(sb) == 6
+    assert all(torch.equal(x[0], y[0]) and torch.equal(x[1], y[1]) for x, y in zip(sa, sb))
+    L = hmc._lib()
+    k, m = q0.size, len(w.sequenced)
+    q, p = d(q0), d(p0)
+    args = lambda kk, mm, seq, r: L.hawkes_hmc_leapfrog_step(kk, hmc._ptr(q), hmc._ptr(p), hmc._ptr(g0), 0.1,  # noqa: E731
+                                                             hmc._ptr(minv), 0.1, mm, seq, r, None)
+    seq_p, r_p = hmc._ptr(post.seq), hmc._ptr(post.r)
+    assert args(0, 0, None, None) == hmc.hawkes.EINVAL
+    assert args(k, k - 5, seq_p, r_p) == hmc.hawkes.EINVAL  # 6 + m > k
+    assert args(k, -1, seq_p, r_p) == hmc.hawkes.EINVAL
+    assert args(k, m, None, r_p) == hmc.hawkes.EINVAL
