@@ -142,8 +142,9 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # FP64 oracle on the host (CPU baseline and reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample_rate(w, target_s: float = 12.0, rng_seed: int = 0):
-    """Pairs/s of the FP64 oracle on a bounded row/column sample of the workload.
+def oracle_sample_rate(w, target_s: float = 12.0, rng_seed: int = 0, threads=None):
+    """Pairs/s of the FP64 oracle on a bounded row/column sample of the workload
+    (on `threads` host threads; all of them by default).
 
     A full evaluation visits every (row, source) pair in the row loop and every
     source's later targets in the column loop.  The sample evaluates k whole
@@ -152,14 +153,14 @@ def oracle_sample_rate(w, target_s: float = 12.0, rng_seed: int = 0):
     """
     import oracle
     rng = np.random.default_rng(rng_seed)
-    threads = oracle.max_threads()
+    threads = oracle.max_threads() if threads is None else int(threads)
     lam_stub = np.ones(w.n)  # column sums are timed with unit intensities: same work, values unused
 
     def run(k):
         idx = np.sort(rng.choice(w.n, k, replace=False))
         t0 = time.perf_counter()
-        oracle.rows(w.x, w.y, w.t, w.r, w.params, idx)
-        oracle.rate_terms(w.x, w.y, w.t, w.r, w.params, lam_stub, idx)
+        oracle.rows(w.x, w.y, w.t, w.r, w.params, idx, threads=threads)
+        oracle.rate_terms(w.x, w.y, w.t, w.r, w.params, lam_stub, idx, threads=threads)
         return time.perf_counter() - t0
 
     oracle.build()  # compile/load outside the timed sample
@@ -473,6 +474,9 @@ def run_ours(args, rank, world, local_rank):
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{k} whole rows (all {n} sources, with derivative sums) + {k} whole columns of the "
                          f"N={n} workload in {dt:.1f} s; rate = k(N-1)/time (CPU: {cpu_info()})"}
+        rate1, _, k1, dt1 = oracle_sample_rate(w, target_s=4.0, rng_seed=1, threads=1)
+        cpu["single_thread"] = {"value": rate1, "unit": UNIT, "cores": 1,
+                                "sample": f"{k1} whole rows + {k1} whole columns in {dt1:.1f} s on one thread"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -495,6 +499,13 @@ def run_ours(args, rank, world, local_rank):
                                             "dfma_T_per_s": alu["dfma_per_s"] / 1e12,
                                             "source": "the library's f32x2 FMA, MUFU exp2 and FP64 FMA chains"},
                      "frac_of_measured_ffma2": achieved / alu["ffma2_lane_fma_per_s"],
+                     # the MUFU bound beside the FP32 one: one ex2 per ordered pair (background)
+                     # plus one per causal pair in the band (excitation)
+                     "mufu": {"ex2_per_launch": pairs + pb,
+                              "achieved_T_per_s": (pairs + pb) / row_t / 1e12,
+                              "peak_T_per_s": alu["ex2_per_s"] / 1e12,
+                              "frac": (pairs + pb) / row_t / alu["ex2_per_s"],
+                              "peak_source": "measured MUFU exp2 chain (measured_alu_peaks)"},
                      "frac_survey": (COARSE_ROW_SLOTS * pairs) / row_t / FP32_PEAK_SLOTS,
                      "col_frac_survey": (COARSE_COL_SLOTS * pb) / col_t / FP32_PEAK_SLOTS,
                      "survey_count": "26 FP32 slots per ordered pair (excitation and masks charged to every "
