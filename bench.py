@@ -174,6 +174,52 @@ def oracle_sample_rate(w, target_s: float = 12.0, rng_seed: int = 0, threads=Non
     return k2 * (w.n - 1) / dt2, threads, k2, dt2
 
 
+def small_config_table(dev, stream):
+    """The FP64 oracle in full at the two small configurations (2,000 and 23,422
+    events; one thread and all threads, the 23,422-event single-thread figure
+    on a row/column sample), beside the GPU's FP64 and FP32C evaluations of the
+    same workloads (CUDA events, inputs resident, median of 5 after 2 warm-ups)."""
+    import oracle
+    import torch
+    from paper_2103_03348_b300 import hawkes
+    out = {}
+    for name in ("unit_square", "ebola_like"):
+        wc = synth.make(name)
+        pairs_c = wc.n * (wc.n - 1)
+        row = {"n_events": wc.n}
+        t0 = time.perf_counter()
+        oracle.evaluate(wc.x, wc.y, wc.t, wc.r, np.array(wc.params), want=2)
+        row["oracle_all_threads_s"] = time.perf_counter() - t0
+        row["oracle_threads"] = oracle.max_threads()
+        if wc.n <= 5000:
+            t0 = time.perf_counter()
+            oracle.evaluate(wc.x, wc.y, wc.t, wc.r, np.array(wc.params), want=2, threads=1)
+            row["oracle_one_thread_s"] = time.perf_counter() - t0
+        else:
+            rate1, _, k1, dt1 = oracle_sample_rate(wc, target_s=4.0, rng_seed=2, threads=1)
+            row["oracle_one_thread_s"] = pairs_c / rate1
+            row["oracle_one_thread_note"] = f"extrapolated from {k1} whole rows + columns in {dt1:.1f} s"
+        to_dev = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)  # noqa: E731
+        x, y, t, r = to_dev(wc.x), to_dev(wc.y), to_dev(wc.t), to_dev(wc.r)
+        for prec in ("fp64", "fp32c"):
+            ms_ = []
+            for i in range(7):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                hawkes._call("hess", x, y, t, r, wc.params, prec, stream=stream, check=False)
+                e1.record(stream)
+                e1.synchronize()
+                if i >= 2:
+                    ms_.append(e0.elapsed_time(e1))
+            row[f"gpu_{prec}_ms"] = float(np.median(ms_))
+        row["pairs_per_s"] = {"oracle_all_threads": pairs_c / row["oracle_all_threads_s"],
+                              "oracle_one_thread": pairs_c / row["oracle_one_thread_s"],
+                              "gpu_fp64": pairs_c / (row["gpu_fp64_ms"] * 1e-3),
+                              "gpu_fp32c": pairs_c / (row["gpu_fp32c_ms"] * 1e-3)}
+        out[wc.name] = row
+    return out
+
+
 def cpu_info():
     model = "unknown"
     try:
@@ -477,6 +523,7 @@ def run_ours(args, rank, world, local_rank):
         rate1, _, k1, dt1 = oracle_sample_rate(w, target_s=4.0, rng_seed=1, threads=1)
         cpu["single_thread"] = {"value": rate1, "unit": UNIT, "cores": 1,
                                 "sample": f"{k1} whole rows + {k1} whole columns in {dt1:.1f} s on one thread"}
+        cpu["small_configs"] = small_config_table(dev, stream)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
