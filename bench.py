@@ -174,7 +174,7 @@ def oracle_sample_rate(w, target_s: float = 12.0, rng_seed: int = 0, threads=Non
     return k2 * (w.n - 1) / dt2, threads, k2, dt2
 
 
-def small_config_table(dev, stream):
+def small_config_table(dev, stream, all_threads):
     """The FP64 oracle in full at the two small configurations (2,000 and 23,422
     events; one thread and all threads, the 23,422-event single-thread figure
     on a row/column sample), beside the GPU's FP64 and FP32C evaluations of the
@@ -188,9 +188,9 @@ def small_config_table(dev, stream):
         pairs_c = wc.n * (wc.n - 1)
         row = {"n_events": wc.n}
         t0 = time.perf_counter()
-        oracle.evaluate(wc.x, wc.y, wc.t, wc.r, np.array(wc.params), want=2)
+        oracle.evaluate(wc.x, wc.y, wc.t, wc.r, np.array(wc.params), want=2, threads=all_threads)
         row["oracle_all_threads_s"] = time.perf_counter() - t0
-        row["oracle_threads"] = oracle.max_threads()
+        row["oracle_threads"] = all_threads
         if wc.n <= 5000:
             t0 = time.perf_counter()
             oracle.evaluate(wc.x, wc.y, wc.t, wc.r, np.array(wc.params), want=2, threads=1)
@@ -516,14 +516,18 @@ def run_ours(args, rank, world, local_rank):
     peak_t = FP32_PEAK_SLOTS / 1e12
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        rate, threads, k, dt = oracle_sample_rate(w, target_s=12.0)
+        import oracle
+        # the oracle's OpenMP thread count persists between calls: read the host's count
+        # once, before any one-thread run, and pass it explicitly
+        all_threads = oracle.max_threads()
+        rate, threads, k, dt = oracle_sample_rate(w, target_s=12.0, threads=all_threads)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{k} whole rows (all {n} sources, with derivative sums) + {k} whole columns of the "
                          f"N={n} workload in {dt:.1f} s; rate = k(N-1)/time (CPU: {cpu_info()})"}
         rate1, _, k1, dt1 = oracle_sample_rate(w, target_s=4.0, rng_seed=1, threads=1)
         cpu["single_thread"] = {"value": rate1, "unit": UNIT, "cores": 1,
                                 "sample": f"{k1} whole rows + {k1} whole columns in {dt1:.1f} s on one thread"}
-        cpu["small_configs"] = small_config_table(dev, stream)
+        cpu["small_configs"] = small_config_table(dev, stream, all_threads)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
