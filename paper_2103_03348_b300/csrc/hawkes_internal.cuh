@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <utility>
 
 #include "hawkes.h"
@@ -44,6 +45,37 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+// Blocks of a kernel (at `threads` threads per block, no dynamic shared
+// memory) that are resident on the current device at once: SMs x blocks per
+// SM, for a persistent grid.  A host-side query, cached per kernel, device and
+// block size, so that launches after the first (and launches being captured
+// into a graph) only read the cache.  0 on an error.
+inline int resident_blocks_of(const void *kernel, int threads) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    struct Entry {
+        const void *kernel;
+        int dev, threads, blocks;
+    };
+    static std::mutex mu;
+    static Entry cache[64];
+    static int used = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    for (int k = 0; k < used; ++k)
+        if (cache[k].kernel == kernel && cache[k].dev == dev && cache[k].threads == threads) return cache[k].blocks;
+    int sms = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess) return 0;
+    const int blocks = sms * per_sm;
+    if (used < 64) cache[used++] = Entry{kernel, dev, threads, blocks};
+    return blocks;
+}
+
+template <typename... KArgs>
+inline int resident_blocks(void (*kernel)(KArgs...), int threads) {
+    return resident_blocks_of(reinterpret_cast<const void *>(kernel), threads);
 }
 
 namespace hk {
@@ -80,6 +112,8 @@ constexpr float TINY_ROW = 8.673617379884035e-19f;  // 2^-60
 // Measured: 183 tiles (23,422 events) 3.5 us faster per group; 274 tiles
 // (35,000 events) 10 us faster per tile.
 constexpr int FIN_GROUP_TILES = 200;
+// Header slot of the persistent space-time row pass's work counter.
+constexpr int HDR_ST_ROW_UNITS = 4;
 
 // Moment index (row pass).  Background terms G, excitation terms E (with exp(r)):
 //   0 sum G        1 sum G d^2     2 sum G dt^2    3 sum G d^4     4 sum G dt^4
@@ -157,7 +191,8 @@ struct GroupStat {
 
 // Workspace carving.  Offsets are multiples of 256 bytes.
 struct Workspace {
-    int *hdr;            // [0] status bits, [2] prep's last-block ticket; cleared every call
+    int *hdr;            // [0] status bits, [2] prep's last-block ticket, [4] the space-time row pass's
+                         // work counter (HDR_ST_ROW_UNITS); [1..7] cleared by every call's setup
     int *evbits;         // [1] prep's validation bits, kept for calls that reuse the events (follows hdr)
     Derived *derived;    // [1]  constants derived from the parameters
     double *centre;      // [4]: xc, yc, tc, tN

@@ -6,9 +6,10 @@
 namespace hk {
 
 // FP32C_ST row pass.  Positions hold events permuted inside slabs so that
-// each group of 32 positions is compact in space and time.  One block is one
-// warp and owns one target group (32 rows) for one chunk of source tiles, so
-// no warp ever waits for another:
+// each group of 32 positions is compact in space and time.  One work unit is
+// one target group (32 rows) against one chunk of source tiles, run by one
+// warp, so no warp ever waits for another (the warps are persistent and take
+// units in turn, row32_st_kernel below):
 //   * classify: lane l tests source tile base + l group by group against the
 //     warp's own target group (background live, excitation live, masks
 //     needed), and the live groups of the 32 tiles are listed in order as
@@ -20,13 +21,16 @@ namespace hk {
 //     the causal mask compares time-order ranks.
 constexpr int GPT = TILE / GROUP;  // groups per tile
 
+// One work unit: target group `bx` of the call's range against source chunk
+// rotation `by` (the grid position of a one-warp block before the pass became
+// persistent).
 template <int MODE>
-__global__ void __launch_bounds__(GROUP, 20) row32_st_kernel(Consts c, Inputs in, Workspace ws) {
-    pdl_wait();
+__device__ __forceinline__ void row32_st_unit(const Consts &c, const Inputs &in, const Workspace &ws, int bx,
+                                              int by) {
     const Derived &D = *c.d;
-    const int tg = c.t0 * GPT + blockIdx.x;  // target group
+    const int tg = c.t0 * GPT + bx;  // target group
     const int tile = tg / GPT, gw = tg % GPT;
-    const int chunk = (tile / c.g.chunk_tiles - (int)blockIdx.y + c.g.n_chunks) % c.g.n_chunks;
+    const int chunk = (tile / c.g.chunk_tiles - by + c.g.n_chunks) % c.g.n_chunks;
     const int lane = threadIdx.x;
     const int i = tg * GROUP + lane;
     const int npad = c.g.npad;
@@ -155,16 +159,43 @@ __global__ void __launch_bounds__(GROUP, 20) row32_st_kernel(Consts c, Inputs in
             // the Kahan pair (sum, -compensation), combined across chunks in float-float
             reinterpret_cast<float2 *>(ws.rowpart)[((size_t)chunk * NMOM + k) * npad + i] = make_float2(ks[k], -kc[k]);
     }
-    // one block per target group also computes the group's integral-term shares (FP64)
-    if (blockIdx.y == 0) integral_group(c, in, ws, tg);
+    // the unit of chunk rotation 0 also computes the group's integral-term shares (FP64)
+    if (by == 0) integral_group(c, in, ws, tg);
+}
+
+// Persistent: a grid of as many one-warp blocks as fit on the GPU at once; each
+// takes work units (target group, chunk rotation) from a counter in the call's
+// header, in the order the launch grid dispatched them before (rotation-major:
+// the heavy units first).  A unit's partials go to fixed places, so the result
+// does not depend on which warp takes it (bit for bit the same as one block per
+// unit), and taking a unit is one atomic add: no warp waits for another.
+template <int MODE>
+__global__ void __launch_bounds__(GROUP, 20) row32_st_kernel(Consts c, Inputs in, Workspace ws) {
+    pdl_wait();
+    const int nx = (c.t1 - c.t0) * GPT, total = nx * c.g.n_chunks;
+    for (;;) {
+        int u = 0;
+        if (threadIdx.x == 0) u = atomicAdd(&ws.hdr[HDR_ST_ROW_UNITS], 1);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (u >= total) break;
+        row32_st_unit<MODE>(c, in, ws, u % nx, u / nx);
+        __syncwarp();  // the unit's shared buffers are read until here
+    }
+}
+
+template <int MODE>
+static cudaError_t launch_row32_st_mode(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s) {
+    const int units = (c.t1 - c.t0) * GPT * c.g.n_chunks;
+    const int grid = min(units, resident_blocks(row32_st_kernel<MODE>, GROUP));
+    if (grid < 1) return cudaErrorInvalidConfiguration;
+    launch_pdl(row32_st_kernel<MODE>, grid, GROUP, 0, s, c, in, ws);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_row32_st(const Consts &c, const Inputs &in, const Workspace &ws, cudaStream_t s) {
-    const dim3 grid((c.t1 - c.t0) * GPT, c.g.n_chunks);
-    if (c.mode == MODE_HESS) launch_pdl(row32_st_kernel<MODE_HESS>, grid, GROUP, 0, s, c, in, ws);
-    else if (c.mode == MODE_GRAD) launch_pdl(row32_st_kernel<MODE_GRAD>, grid, GROUP, 0, s, c, in, ws);
-    else launch_pdl(row32_st_kernel<MODE_LL>, grid, GROUP, 0, s, c, in, ws);
-    return cudaGetLastError();
+    if (c.mode == MODE_HESS) return launch_row32_st_mode<MODE_HESS>(c, in, ws, s);
+    if (c.mode == MODE_GRAD) return launch_row32_st_mode<MODE_GRAD>(c, in, ws, s);
+    return launch_row32_st_mode<MODE_LL>(c, in, ws, s);
 }
 
 }  // namespace hk
