@@ -596,7 +596,7 @@ def st_roofline(st_pairs, row_ms, col_ms, peak):
     """The space-time passes (the path the sampler runs) against the FP32 pipe,
     counting the pairs inside the group pairs they evaluate: 14 slots per
     background pair and 7 per excitation pair in the row pass (the per-pair
-    counts of the full evaluation), 8 per column pair."""
+    counts of the full evaluation), 7 per column pair."""
     row_t, col_t = float(np.mean(row_ms)) * 1e-3, float(np.mean(col_ms)) * 1e-3
     row_slots = ROW_BG_SLOTS * st_pairs["row_background_pairs"] + ROW_EXC_SLOTS * st_pairs["row_excitation_pairs"]
     col_slots = COL_SLOTS * st_pairs["column_pairs"]
